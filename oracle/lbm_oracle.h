@@ -1,0 +1,91 @@
+/*
+ * Plain FP64 CPU oracle of the cascaded lattice Boltzmann step with
+ * Strang-split forcing (flow) and Strang-split sources (passive scalar),
+ * arXiv:1806.10247.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link
+ * or call this code: it is used by the tests, by the smoke check and by the
+ * CPU-baseline leg of the benchmark.  It shares no code with the CUDA path.
+ *
+ * Populations are stored structure-of-arrays, f[q][z][y][x], x fastest.
+ * The state held between steps is the pre-collision population set f(t)
+ * (the result of the streaming step, Eq. 22b / Eq. 40b).
+ *
+ * Velocity orderings:
+ *   D2Q9  : the paper's order (Sec. 4, Eq. 15).
+ *   D2Q5  : the paper's order (Sec. 5, Eq. 34).
+ *   D3Q27 : alpha = (ex+1) + 3 (ey+1) + 9 (ez+1)  (the paper gives no D3Q27 order).
+ */
+#ifndef LBM_ORACLE_H
+#define LBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_D2Q9  1
+#define ORC_D3Q27 2
+#define ORC_D2Q5  3
+
+typedef struct {
+    int lattice;            /* ORC_D2Q9 / ORC_D3Q27 / ORC_D2Q5 */
+    int n[3];               /* nx, ny, nz (nz = 1 for the 2D lattices) */
+    int wall[3];            /* per axis: 0 periodic, 1 halfway bounce-back walls at both ends */
+    /* Relaxation parameters.
+     *   D2Q9 : omega[3..8] = omega_3..omega_8 of Eq. 23.
+     *   D2Q5 : omega[1..4] = omega_1^phi..omega_4^phi of Eq. 41.
+     *   D3Q27: omega[1] trace (bulk), omega[2] deviatoric and off-diagonal second
+     *          order (shear), omega[3..6] all central moments of order 3..6. */
+    double omega[9];
+    int generic;            /* D2Q9 only: 1 = generic central-moment procedure instead of Eqs. 23/32 */
+    int as_printed;         /* D2Q5 only: 1 = Eq. 41 with the u^2 phi signs exactly as printed */
+} orc_params;
+
+/* Number of velocities of a lattice (9, 27, 5), 0 if unknown. */
+int orc_q(int lattice);
+/* Spatial dimension of a lattice (2 or 3). */
+int orc_dim(int lattice);
+/* Velocity components e[alpha][3] of a lattice, written into e (q*3 ints). */
+int orc_velocities(int lattice, int *e);
+
+/* Equilibrium populations whose central moments are those of Eq. 20 (flow) or
+ * Eq. 39 (scalar) at the given density/scalar and velocity field.
+ *   rho : [N] density (flow) or scalar phi (D2Q5)
+ *   u   : [3][N] velocity (for D2Q5: the advecting velocity)
+ *   f   : [q][N] output */
+int orc_equilibrium(const orc_params *p, const double *rho, const double *u, double *f);
+
+/* Advance f by nsteps time steps.
+ *   f      : [q][N] in/out, pre-collision populations
+ *   work   : [q][N] scratch (post-collision populations)
+ *   P      : flow: [dim][N] force shape; D2Q5: [N] source shape; NULL = no force/source
+ *   a      : [2*nsteps] envelope values (a_pre, a_post) per step; the force at
+ *            node x in the pre-collision half step is a_pre*P(x) and in the post-
+ *            collision half step a_post*P(x).  NULL = 1,1 each step.
+ *   uadv   : D2Q5 only: [2][N] advecting velocity
+ * Returns 0, or -1 on invalid parameters. */
+int orc_run(const orc_params *p, double *f, double *work, long nsteps,
+            const double *P, const double *a, const double *uadv);
+
+/* Macroscopic fields of f (Eq. 24 / Eq. 42).
+ *   flow : rho[N] = sum f; u[dim][N] = (sum f e + a_pre*P/2)/rho
+ *   D2Q5 : rho[N] = phi = sum g + a_pre*P/2;   u unused
+ * P may be NULL (no force/source); a_pre is then ignored. */
+int orc_moments(const orc_params *p, const double *f, const double *P, double a_pre,
+                double *rho, double *u);
+
+/* One collision (no streaming) of a single node's populations, for the unit
+ * tests: fin[q] -> fout[q], with pre/post force (or source) values and, for
+ * D2Q5, the advecting velocity.  Fpre/Fpost have dim entries (flow) or 1 (D2Q5). */
+int orc_collide_node(const orc_params *p, const double *fin, const double *Fpre,
+                     const double *Fpost, const double *uadv, double *fout);
+
+/* Same collision through the generic central-moment procedure (tensor-product
+ * lattices D2Q9 and D3Q27 only). */
+int orc_collide_node_generic(const orc_params *p, const double *fin, const double *Fpre,
+                             const double *Fpost, double *fout);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,154 @@
+"""Seeded synthetic workloads shaped like the paper's benchmark problems.
+
+This module only draws parameters and tabulates input shapes (numpy, on the
+host).  It holds none of the lattice Boltzmann arithmetic, so both the CUDA
+path and the CPU oracle can take their inputs from it.
+
+Conventions shared with the library: lattice units (dx = dt = 1); a force or
+source is F(x, t) = a(t) * P(x) with a separable shape
+P_c(x, y, z) = (px_c[x] * py_c[y]) * pz_c[z], each table of length 1 (constant
+along that axis) or the axis extent; shear relaxation omega = 1/tau with
+nu = (tau - 1/2)/3 (Sec. 6 preamble); diffusivity D = (tau_phi - 1/2)/3.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+D2Q9, D3Q27, D2Q5 = 1, 2, 3
+SEED = 10247
+
+
+def tau_from_nu(nu: float) -> float:
+    return 3.0 * nu + 0.5
+
+
+@dataclass
+class Workload:
+    """One lattice problem: geometry, relaxation, initial state and forcing."""
+
+    name: str
+    lattice: int
+    shape: tuple                      # (nx, ny, nz)
+    wall: tuple                       # per axis: 1 = halfway bounce-back walls
+    omega: tuple                      # 9 relaxation rates, numbered as in the library header
+    rho0: np.ndarray | float = 1.0    # initial density (flow) or scalar (D2Q5)
+    u0: np.ndarray | tuple = (0.0, 0.0, 0.0)  # initial velocity (flow) or advecting velocity (D2Q5)
+    tables: list | None = None        # per component (px, py, pz)
+    envelope: object = None           # a(t), or None for a == 1
+    steps: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nodes(self) -> int:
+        return int(self.shape[0] * self.shape[1] * self.shape[2])
+
+
+def d2q9_omega(tau: float, w3: float = 1.0, w6: float = 1.0, w7: float = 1.0, w8: float = 1.0):
+    """omega_3..omega_8 of Eq. 23 at their array positions 3..8 (Sec. 6: omega_4 = omega_5 = 1/tau)."""
+    return (0.0, 0.0, 0.0, w3, 1.0 / tau, 1.0 / tau, w6, w7, w8)
+
+
+def d2q5_omega(tau_phi: float, w3: float = 1.0, w4: float = 1.0):
+    """omega_1^phi..omega_4^phi of Eq. 41 at positions 1..4 (omega_1 = omega_2 = 1/tau_phi)."""
+    return (0.0, 1.0 / tau_phi, 1.0 / tau_phi, w3, w4, 0.0, 0.0, 0.0, 0.0)
+
+
+def d3q27_omega(tau: float, bulk: float = 1.0, high=(1.0, 1.0, 1.0, 1.0)):
+    """D3Q27 rates: [1] trace (bulk), [2] shear = 1/tau, [3..6] orders 3..6."""
+    return (0.0, bulk, 1.0 / tau, high[0], high[1], high[2], high[3], 0.0, 0.0)
+
+
+def poiseuille(ny: int = 33, nx: int = 3, tau: float = 0.8, Fx: float = 1e-6) -> Workload:
+    """Body-force driven channel: x periodic, walls at y = -1/2 and ny - 1/2 (Sec. 6.1)."""
+    return Workload(
+        name=f"poiseuille_d2q9_{nx}x{ny}", lattice=D2Q9, shape=(nx, ny, 1), wall=(0, 1, 0),
+        omega=d2q9_omega(tau), rho0=1.0, u0=(0.0, 0.0, 0.0),
+        tables=[(np.array([Fx]), np.array([1.0]), np.array([1.0])),
+                (np.array([0.0]), np.array([1.0]), np.array([1.0]))],
+        steps=10000, meta={"tau": tau, "Fx": Fx, "nu": (tau - 0.5) / 3.0})
+
+
+@dataclass
+class CDECase:
+    """Manufactured-source scalar problem on a periodic N x N grid (one sweep member)."""
+
+    N: int
+    D: float
+    A: float
+    ux: float
+    uy: float
+    lam: float
+    T: int
+
+
+def cde_sweep_params(seed: int = SEED, sizes=(32, 64, 128, 256, 512), T32: int = 400):
+    """Parameters of the diffusive-scaling refinement sweep of the scalar problem.
+
+    D ~ U[0.01, 0.1] and A ~ U[1e-4, 1e-3] are drawn once from the seed; the
+    advecting velocity (0.01, 0.01) and A scale as 32/N and (32/N)^2, the
+    envelope rate is lambda = D (2 pi / N)^2 and the run length T_N = T32 (N/32)^2."""
+    rng = np.random.default_rng(seed)
+    D = float(rng.uniform(0.01, 0.1))
+    A = float(rng.uniform(1e-4, 1e-3))
+    out = []
+    for N in sizes:
+        s = 32.0 / N
+        k = 2.0 * math.pi / N
+        out.append(CDECase(N=N, D=D, A=A * s * s, ux=0.01 * s, uy=0.01 * s, lam=D * k * k,
+                           T=int(round(T32 / (s * s)))))
+    return out
+
+
+def cde_workload(c: CDECase, phi0: float = 1.0) -> Workload:
+    N = c.N
+    x = np.arange(N, dtype=np.float64)
+    px = c.A * np.sin(2.0 * math.pi * x / N)
+    py = np.sin(2.0 * math.pi * x / N)
+    lam = c.lam
+    tau_phi = 3.0 * c.D + 0.5
+    return Workload(
+        name=f"cde_d2q5_{N}x{N}", lattice=D2Q5, shape=(N, N, 1), wall=(0, 0, 0),
+        omega=d2q5_omega(tau_phi), rho0=phi0, u0=(c.ux, c.uy, 0.0),
+        tables=[(px, py, np.array([1.0]))], envelope=lambda t, lam=lam: math.exp(-lam * t),
+        steps=c.T, meta={"D": c.D, "A": c.A, "lam": lam, "tau_phi": tau_phi})
+
+
+def kolmogorov(n: int = 256, F0: float = 1e-5, nu: float = 0.02, noise: float = 1e-4,
+               seed: int = SEED, shape=None) -> Workload:
+    """Periodic 3D Kolmogorov flow: F_x = F0 sin(2 pi y / Ly), rho = 1, seeded velocity noise."""
+    nx, ny, nz = shape if shape is not None else (n, n, n)
+    rng = np.random.default_rng(seed)
+    u0 = noise * rng.standard_normal((3, nx * ny * nz))
+    y = np.arange(ny, dtype=np.float64)
+    py = F0 * np.sin(2.0 * math.pi * y / ny)
+    one = np.array([1.0])
+    zero = np.array([0.0])
+    return Workload(
+        name=f"kolmogorov_d3q27_{nx}x{ny}x{nz}", lattice=D3Q27, shape=(nx, ny, nz), wall=(0, 0, 0),
+        omega=d3q27_omega(tau_from_nu(nu)), rho0=1.0, u0=u0,
+        tables=[(one, py, one), (zero, one, one), (zero, one, one)], steps=1000,
+        meta={"F0": F0, "nu": nu})
+
+
+def duct(n: int = 128, nx: int = 3, F0: float = 1e-6, nu: float = 0.05, seed: int = SEED) -> Workload:
+    """Square duct: x periodic, halfway bounce-back walls in y and z,
+    F_x = F0 (1 + 0.5 sin(2 pi z / Lz))."""
+    z = np.arange(n, dtype=np.float64)
+    pz = F0 * (1.0 + 0.5 * np.sin(2.0 * math.pi * z / n))
+    one = np.array([1.0])
+    zero = np.array([0.0])
+    return Workload(
+        name=f"duct_d3q27_{nx}x{n}x{n}", lattice=D3Q27, shape=(nx, n, n), wall=(0, 1, 1),
+        omega=d3q27_omega(tau_from_nu(nu)), rho0=1.0, u0=(0.0, 0.0, 0.0),
+        tables=[(one, one, pz), (zero, one, one), (zero, one, one)], steps=1000,
+        meta={"F0": F0, "nu": nu})
+
+
+def random_populations(q: int, N: int, weights, seed: int, amp: float = 0.05) -> np.ndarray:
+    """Positive populations near a rest state, for collision-level tests."""
+    rng = np.random.default_rng(seed)
+    w = np.asarray(weights, np.float64)[:, None]
+    return np.ascontiguousarray(w * (1.0 + amp * rng.standard_normal((q, N))))
