@@ -1,0 +1,208 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) cascaded lattice Boltzmann library.
+ *
+ * The library advances lattices with the cascaded (central-moment) lattice
+ * Boltzmann method and the symmetrized (Strang) operator-split force and
+ * source steps of arXiv:1806.10247:
+ *
+ *   one time step  f(t+1) = S F^1/2 C F^1/2 f(t)          (Sec. 3, Eq. 14)
+ *   scalar step    g(t+1) = S R^1/2 C R^1/2 g(t)          (Sec. 5, Eq. StrangLBMCDE)
+ *
+ * on three lattices: D2Q9 flow (Sec. 4), D2Q5 passive scalar with a source
+ * (Sec. 5) and D3Q27 flow (the extension of the 3D method of Appendix A to
+ * D3Q27, by the generic central-moment procedure).  Every step runs on the
+ * GPU in hand-written CUDA kernels; there is no CPU path.
+ *
+ * Conventions for every entry point:
+ *  - Return value: an lbm_status code.  Nothing is thrown across the ABI.
+ *    After a failure lbm_last_error(ctx) describes it (a string owned by the
+ *    context, valid until the next call on that context).
+ *  - Ownership: the library owns the population buffers of a context.  Caller
+ *    pointers are read or written only during the call and never retained;
+ *    fields passed to lbm_set_force / lbm_set_source / lbm_set_velocity are
+ *    copied into library memory.
+ *  - Streams: all device work of a context is issued on the CUDA stream given
+ *    to lbm_create (NULL = the legacy default stream).  Calls that return
+ *    data to host memory synchronise that stream before returning.  A context
+ *    is not thread-safe.
+ *  - Node order: node (x, y, z) has index i = x + nx*(y + ny*z); population
+ *    arrays are [q][N] (structure of arrays), N = nx*ny*nz.
+ *  - Velocity order: D2Q9 as in Sec. 4 Eq. 15; D2Q5 as in Sec. 5 Eq. 34;
+ *    D3Q27: alpha = (ex+1) + 3*(ey+1) + 9*(ez+1).
+ *  - Lattice units: dx = dt = 1, c_s^2 = 1/3.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Lattices. */
+#define LBM_D2Q9 1     /* flow, Sec. 4 */
+#define LBM_D3Q27 2    /* flow, Appendix A extended to D3Q27 */
+#define LBM_D2Q5_CDE 3 /* passive scalar with source, Sec. 5 */
+
+/* Population storage / arithmetic. */
+#define LBM_FP64 0
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_EINVAL -1   /* invalid argument; nothing was changed */
+#define LBM_ENOMEM -2   /* device allocation failed */
+#define LBM_ECUDA -3    /* a CUDA call failed (message in lbm_last_error) */
+#define LBM_EUNSTABLE -4 /* a density/scalar is non-finite or (flow) not positive */
+#define LBM_ESTATE -6   /* call out of order (e.g. stepping before initialisation) */
+
+/* Boundary kinds, one per axis. */
+#define LBM_PERIODIC 0
+#define LBM_BOUNCE_BACK 1 /* stationary halfway bounce-back walls at -1/2 and n-1/2 (Sec. 6.1) */
+
+typedef struct {
+    int axis[3]; /* x, y, z: LBM_PERIODIC or LBM_BOUNCE_BACK */
+} lbm_boundary;
+
+/* Relaxation rates, all in (0, 2).
+ *   D2Q9  : omega[3..8] = omega_3 .. omega_8 of Sec. 4 Eq. 23 (omega_4 = omega_5
+ *           = 1/tau gives nu = (tau - 1/2)/3; the paper uses omega_3 = omega_6 =
+ *           omega_7 = omega_8 = 1, Sec. 6).
+ *   D2Q5  : omega[1..4] = omega_1^phi .. omega_4^phi of Sec. 5 Eq. 41 (omega_1 =
+ *           omega_2 = 1/tau_phi gives D = (tau_phi - 1/2)/3).
+ *   D3Q27 : omega[1] trace of the second-order central moments (bulk),
+ *           omega[2] their deviatoric and off-diagonal parts (shear, 1/tau),
+ *           omega[3..6] every central moment of order 3..6.
+ * Entries not listed for a lattice are ignored. */
+typedef struct {
+    double omega[9];
+} lbm_relax;
+
+/* A force (flow) or source (scalar) shape P, or the advecting velocity of the
+ * scalar lattice.  Per component c:
+ *   LBM_FIELD_SEPARABLE: P_c(x,y,z) = (px_c[x] * py_c[y]) * pz_c[z], evaluated
+ *     in that order; data holds, for each component in turn, px_c (len[0]
+ *     values), py_c (len[1]), pz_c (len[2]); a length of 1 means constant
+ *     along that axis, otherwise it must equal the axis extent.
+ *   LBM_FIELD_FULL: data holds P[c][N] in node order.
+ * data is a host pointer; the values are copied. */
+#define LBM_FIELD_NONE 0
+#define LBM_FIELD_SEPARABLE 1
+#define LBM_FIELD_FULL 2
+
+typedef struct {
+    int kind;
+    int len[3];
+    const double *data;
+} lbm_field;
+
+/* Time envelope a(t) of the force or source: F(x, t) = a(t) P(x).  Each step
+ * t -> t+1 uses a_pre = (a(t) + a(t+1/2))/2 in the pre-collision half step and
+ * a_post = (a(t+1/2) + a(t+1))/2 in the post-collision half step (trapezoid
+ * rule of Sec. 6.3).  Evaluated on the host, three times per step. */
+typedef double (*lbm_envelope_fn)(double t, void *user);
+
+/* Create a context.  Allocates two population buffers of q*N doubles on the
+ * current CUDA device (N = nx*ny*nz; nz must be 1 for the 2D lattices).
+ * `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: LBM_EINVAL (unknown lattice or storage, extent < 1, omega outside
+ * (0,2), bad boundary kind), LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
+int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_relax *relax,
+               const lbm_boundary *bc, int storage, void *stream);
+
+/* Release all device memory of a context (synchronises its stream).  NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message describing the last failure on ctx ("" if none); for ctx == NULL,
+ * the last failure of lbm_create in this process. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Fill the populations with the equilibrium whose central moments are those of
+ * Sec. 4 Eq. 20 (flow) or Sec. 5 Eq. 39 (scalar) — the product of 1D
+ * Maxwellian profiles — and set the step counter to 0.
+ *   rho    : host [N] density (flow) or scalar phi (D2Q5); NULL = rho0 everywhere
+ *   u      : host [dim][N] velocity; NULL = u0 everywhere.  For D2Q5 this is
+ *            the velocity of the equilibrium (normally the advecting velocity).
+ * Errors: LBM_EINVAL (rho0 <= 0 for flow), LBM_ECUDA. */
+int lbm_init_equilibrium(lbm_ctx *ctx, double rho0, const double u0[3], const double *rho,
+                         const double *u);
+
+/* Body force shape of a flow lattice (Sec. 3 Eq. 13; Sec. 4 Eqs. 25-31); dim
+ * components.  kind LBM_FIELD_NONE removes the force.  The force enters the
+ * pre-collision half step as u = (sum f e + a_pre P / 2)/rho (Eq. 25) and the
+ * post-collision change of the first moment as (a_pre + a_post) P / 2
+ * (Eqs. 27-31).  Errors: LBM_EINVAL (scalar lattice, bad lengths), LBM_ECUDA. */
+int lbm_set_force(lbm_ctx *ctx, const lbm_field *shape);
+
+/* Source shape of the scalar lattice (Sec. 5 Eqs. 43-47); one component.
+ * phi = sum g + a_pre S / 2 enters the collision (Eq. 43) and the zeroth
+ * moment changes by (a_pre + a_post) S / 2 (Eqs. 44-47).
+ * Errors: LBM_EINVAL (flow lattice, bad lengths), LBM_ECUDA. */
+int lbm_set_source(lbm_ctx *ctx, const lbm_field *shape);
+
+/* Advecting velocity u(x) of the scalar lattice (Sec. 5 Eq. 33), two
+ * components, constant in time.  Default: zero.
+ * Errors: LBM_EINVAL (flow lattice), LBM_ECUDA. */
+int lbm_set_velocity(lbm_ctx *ctx, const lbm_field *u);
+
+/* Time envelope of the force or source (NULL fn = a(t) = 1). */
+int lbm_set_envelope(lbm_ctx *ctx, lbm_envelope_fn fn, void *user);
+
+/* Advance n >= 0 time steps (n = 0 is a no-op).  Each step is one fused
+ * kernel launch: stream (Eq. 22b / 40b, pull form, with periodic wrap or
+ * halfway bounce-back), moments (Eq. 24 / 42), pre-collision half force or
+ * source (Eq. 25 / 43), cascaded collision (Eq. 23 / 41 / generic D3Q27),
+ * post-collision half step (Eq. 31 / 47) and the post-collision populations
+ * (Eq. 32 / 48).  Asynchronous on the context's stream.
+ * Errors: LBM_ESTATE (not initialised), LBM_EINVAL (n < 0), LBM_ECUDA. */
+int lbm_step(lbm_ctx *ctx, long n);
+
+/* Macroscopic fields of the current state f(t):
+ *   flow : rho[N] = sum f (Eq. 24 / step (vi)); u[dim][N] = (sum f e + h a_pre P/2)/rho
+ *   D2Q5 : rho[N] receives phi = sum g + h a_pre S/2 (Eqs. 42-43); u unused (may be NULL)
+ * with h = 1 if half_forced, else 0 (u^o and phi^o).  where = 0: host
+ * pointers (the call synchronises); where = 1: device pointers (asynchronous).
+ * Errors: LBM_ESTATE, LBM_EINVAL (NULL output), LBM_ECUDA. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int where, int half_forced);
+
+/* Global sums over the lattice, computed on the GPU in FP64 with a fixed
+ * (deterministic) reduction order:
+ *   out[0] = sum rho (flow) or sum phi^o (scalar)
+ *   out[1..3] = sum of sum_alpha f e (flow; zeros for the scalar lattice)
+ *   out[4] = max over nodes and components of |u(t) - u(t_prev)| (flow, half
+ *            forced velocity) or |phi(t) - phi(t_prev)| (scalar), where t_prev is
+ *            the state at the previous lbm_reduce call; +inf on the first call.
+ * out is a host array of 5 doubles; the call synchronises.
+ * Errors: LBM_EUNSTABLE (some density/scalar non-finite or, for flow, <= 0;
+ * out is still written), LBM_ESTATE, LBM_ECUDA. */
+int lbm_reduce(lbm_ctx *ctx, double out[5]);
+
+/* Copy the populations f(t) (the state after the streaming step of step t,
+ * as [q][N] doubles) to dst.  count must equal q*N.  where: 0 host, 1 device.
+ * Errors: LBM_ESTATE, LBM_EINVAL (count), LBM_ECUDA. */
+int lbm_get_populations(lbm_ctx *ctx, double *dst, size_t count, int where);
+
+/* Replace the populations by src ([q][N] doubles, count = q*N) and set the
+ * step counter to `step` (checkpoint restore).  where: 0 host, 1 device.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_set_populations(lbm_ctx *ctx, const double *src, size_t count, int where, long step);
+
+/* Current step counter t. */
+int lbm_get_step(const lbm_ctx *ctx, long *step);
+
+/* Block until all work issued on the context's stream is done. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Number of kernel launches issued by this context since its creation
+ * (every step, initialisation, moments, reduction and copy kernel counts). */
+int lbm_launch_count(const lbm_ctx *ctx, long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,277 @@
+// Lattice-generic kernels: equilibrium fill, conversion between f(t) and the
+// stored (inverse-streamed) layout, macroscopic moments and deterministic
+// FP64 reductions.
+#include "lbm_internal.h"
+#include "lbm_lattices.cuh"
+
+namespace lbmk {
+namespace {
+
+constexpr int kBlock = 256;
+
+int grid_for(long long n, int block = kBlock) { return (int)((n + block - 1) / block); }
+
+// 1D Maxwellian profile with c_s^2 = 1/3 on the velocities -1, 0, +1: the
+// unique populations whose moments of order 0, 1, 2 are 1, u, 1/3 + u^2.
+__device__ __forceinline__ double maxwell1d(int e, double u)
+{
+    double s = (1.0 / 3.0) + u * u;
+    if (e == 0) return 1.0 - s;
+    return 0.5 * (s + (double)e * u);
+}
+
+// Equilibrium populations whose central moments are Eq. 20 (flow; the
+// product of 1D profiles, which reproduces c_s^2 rho per squared direction)
+// or Eq. 39 (D2Q5 scalar: moments phi, phi u, phi (1/3 + u^2)).
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_equilibrium(Geom g, double rho0, double u0x, double u0y, double u0z, const double *__restrict__ rho,
+              const double *__restrict__ u, double *__restrict__ dst)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    double r = rho ? rho[i] : rho0;
+    double ux = u ? u[i] : u0x;
+    double uy = u ? u[g.N + i] : u0y;
+    double uz = (u && L::DIM == 3) ? u[2 * g.N + i] : u0z;
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        double v;
+        if (L::Q == 5) {
+            const int ex = L::ex(a), ey = L::ey(a);
+            if (ex == 0 && ey == 0) v = r * ((1.0 / 3.0) - ux * ux - uy * uy);
+            else if (ex != 0) v = 0.5 * r * ((1.0 / 3.0) + ux * ux + (double)ex * ux);
+            else v = 0.5 * r * ((1.0 / 3.0) + uy * uy + (double)ey * uy);
+        } else {
+            v = r * maxwell1d(L::ex(a), ux) * maxwell1d(L::ey(a), uy);
+            if (L::DIM == 3) v *= maxwell1d(L::ez(a), uz);
+        }
+        dst[a * g.Np + i] = v;
+    }
+}
+
+// stored_a(x - e_a) = f_a(x)  (or stored_opp(a)(x) = f_a(x) beyond a wall):
+// the inverse of the pull, so that pulling the stored layout returns f.
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_scatter(Geom g, const double *__restrict__ plain, double *__restrict__ stored)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        bool opp;
+        int off = pull_off(g, x, y, z, L::ex(a), L::ey(a), L::ez(a), opp);
+        stored[(opp ? L::opp(a) : a) * g.Np + off] = plain[a * g.Np + i];
+    }
+}
+
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_gather(Geom g, const double *__restrict__ stored, double *__restrict__ plain)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double f[L::Q];
+    load_pulled<L>(stored, g, x, y, z, i, f);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) plain[a * g.Np + i] = f[a];
+}
+
+// Macroscopic fields of f(t): Eq. 24 plus h * Eq. 25 (flow), Eq. 42 plus
+// h * Eq. 43 (scalar).  Outputs are dense [N] / [dim][N] arrays.
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_moments(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, double apre, int half,
+          double *__restrict__ rho, double *__restrict__ u)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double f[L::Q];
+    load_pulled<L>(fin, g, x, y, z, i, f);
+    double m0, j[3];
+    zeroth_first<L>(f, m0, j);
+    const bool forced = half && fkind != FK_NONE;
+    if (L::Q == 5) {
+        rho[i] = forced ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
+        return;
+    }
+    rho[i] = m0;
+#pragma unroll
+    for (int d = 0; d < L::DIM; d++) {
+        double jd = forced ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
+        u[d * g.N + i] = jd / m0;
+    }
+}
+
+// Reduction slots.
+enum { R_MASS = 0, R_JX, R_JY, R_JZ, R_DU, R_BAD, R_SLOTS = 8 };
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduces v[R_SLOTS] over the block (sums, except max for R_DU and R_BAD);
+// thread 0 writes the result.  Fixed order: deterministic for a fixed grid.
+__device__ void block_reduce_store(double (&v)[R_SLOTS], double *out)
+{
+    __shared__ double sh[kBlock / 32][R_SLOTS];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < R_SLOTS; s++) v[s] = (s == R_DU || s == R_BAD) ? warp_max(v[s]) : warp_sum(v[s]);
+    if (lane == 0)
+#pragma unroll
+        for (int s = 0; s < R_SLOTS; s++) sh[warp][s] = v[s];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int s = 0; s < R_SLOTS; s++) {
+            double w = lane < kBlock / 32 ? sh[lane][s] : 0.0;
+            v[s] = (s == R_DU || s == R_BAD) ? warp_max(w) : warp_sum(w);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int s = 0; s < R_SLOTS; s++) out[s] = v[s];
+    }
+}
+
+// Per-block partial sums of rho (or phi^o) and momentum, the largest change
+// of the half-forced velocity (or scalar) since the snapshot (the snapshot is
+// then overwritten), and a flag for non-finite or non-positive densities.
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_reduce_partial(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, double apre,
+                 double *__restrict__ snap, int have_snap, double *__restrict__ partials)
+{
+    double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+        int x, y, z;
+        node_xyz(g, i, x, y, z);
+        double f[L::Q];
+        load_pulled<L>(fin, g, x, y, z, i, f);
+        double m0, j[3];
+        zeroth_first<L>(f, m0, j);
+        v[R_MASS] += m0;
+        bool bad = !isfinite(m0) || (L::Q != 5 && !(m0 > 0.0));
+        if (L::Q == 5) {
+            double phi = fkind != FK_NONE ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
+            if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(phi - snap[i]));
+            snap[i] = phi;
+        } else {
+#pragma unroll
+            for (int d = 0; d < L::DIM; d++) {
+                v[R_JX + d] += j[d];
+                double jd = fkind != FK_NONE ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
+                double ud = jd / m0;
+                bad = bad || !isfinite(ud);
+                if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[d * g.N + i]));
+                snap[d * g.N + i] = ud;
+            }
+        }
+        if (bad) v[R_BAD] = 1.0;
+    }
+    block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
+}
+
+__global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restrict__ partials, int nblocks,
+                                                         double *__restrict__ out)
+{
+    double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += kBlock)
+#pragma unroll
+        for (int s = 0; s < R_SLOTS; s++) {
+            double p = partials[(size_t)b * R_SLOTS + s];
+            v[s] = (s == R_DU || s == R_BAD) ? fmax(v[s], p) : v[s] + p;
+        }
+    block_reduce_store(v, out);
+}
+
+template <class Fn>
+cudaError_t by_lattice(int lattice, Fn &&fn)
+{
+    switch (lattice) {
+    case LD2Q9::ID: return fn(LD2Q9{});
+    case LD2Q5::ID: return fn(LD2Q5{});
+    case LD3Q27::ID: return fn(LD3Q27{});
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t equilibrium(int lattice, const Geom &g, double rho0, const double *u0, const double *rho,
+                        const double *u, double *dst, cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_equilibrium<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho0, u0[0], u0[1], u0[2], rho, u, dst);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t scatter_to_stored(int lattice, const Geom &g, const double *plain, double *stored,
+                              cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_scatter<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, plain, stored);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t gather_from_stored(int lattice, const Geom &g, const double *stored, double *plain,
+                               cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_gather<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, stored, plain);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, int half)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_moments<LT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, half,
+                                                                rho, u);
+        return cudaGetLastError();
+    });
+}
+
+int reduce_blocks(const Geom &g)
+{
+    long long b = (g.N + kBlock - 1) / kBlock;
+    return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);  // 152 SMs x 8 resident blocks
+}
+
+cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
+                   int nblocks, double *out)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_reduce_partial<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, snap,
+                                                              have_snap, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_final<<<1, kBlock, 0, a.stream>>>(partials, nblocks, out);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace lbmk

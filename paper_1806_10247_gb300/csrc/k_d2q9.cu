@@ -1,0 +1,107 @@
+// D2Q9 cascaded LB step with Strang-split body force (arXiv:1806.10247 Sec. 4),
+// FP64, one thread per node, pull form: each launch streams f^p(t-1) into
+// f(t) (Eq. 22b, periodic wrap or halfway bounce-back), then applies the
+// pre-collision half force (Eq. 25), the cascaded collision (Eq. 23), the
+// post-collision half force (Eq. 31) and writes f^p(t) = f + K g (Eq. 32).
+#include "lbm_internal.h"
+#include "lbm_lattices.cuh"
+
+namespace lbmk {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Rates9 {
+    double c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, omega_5/4, omega_6/4, omega_7/4, omega_8/4
+};
+
+// Post-collision populations of one node, in place.
+//   Fx, Fy : pre-collision force a_pre P (Eq. 25)
+//   Gx, Gy : first-moment coefficients g_1, g_2 = (F_pre + F_post)/12 (Eqs. 27-31)
+__device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, double Gx, double Gy,
+                                        const Rates9 &w)
+{
+    // Raw moments (Eq. 21) by 1D passes: x-moments of the three rows ey = 0,
+    // +1, -1, then y-moments of those.
+    const double s0 = f[1] + f[3], d0 = f[1] - f[3];  // row ey = 0
+    const double s1 = f[5] + f[6], d1 = f[5] - f[6];  // row ey = +1
+    const double s2 = f[8] + f[7], d2 = f[8] - f[7];  // row ey = -1
+    const double A0 = f[0] + s0, B0 = f[2] + s1, C0 = f[4] + s2;
+    const double rho = A0 + (B0 + C0), jy = B0 - C0, myy = B0 + C0;
+    const double jx = d0 + (d1 + d2), mxy = d1 - d2, mxyy = d1 + d2;
+    const double mxx = s0 + (s1 + s2), mxxy = s1 - s2, mxxyy = s1 + s2;
+
+    // Eq. 25: velocity after the pre-collision half force step.
+    const double rinv = __drcp_rn(rho);
+    const double ux = fma(0.5, Fx, jx) * rinv;
+    const double uy = fma(0.5, Fy, jy) * rinv;
+    const double ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+
+    // Eq. 23: cascaded change of moments.
+    const double g3 = w.c3 * ((2.0 / 3.0) * rho + rho * (ux2 + uy2) - (mxx + myy));
+    const double g4 = w.c4 * (rho * (ux2 - uy2) - (mxx - myy));
+    const double g5 = w.c5 * (rho * uxy - mxy);
+    const double p34 = 3.0 * g3 + g4, m34 = 3.0 * g3 - g4;
+    const double g6 = w.c6 * (2.0 * rho * ux2 * uy + mxxy - 2.0 * ux * mxy - uy * mxx)
+                      - 0.5 * uy * p34 - 2.0 * ux * g5;
+    const double g7 = w.c7 * (2.0 * rho * ux * uy2 + mxyy - 2.0 * uy * mxy - ux * myy)
+                      - 0.5 * ux * m34 - 2.0 * uy * g5;
+    const double g8 = w.c8 * ((1.0 / 9.0) * rho + 3.0 * rho * ux2 * uy2
+                              - (mxxyy - 2.0 * ux * mxyy - 2.0 * uy * mxxy + ux2 * myy + uy2 * mxx
+                                 + 4.0 * uxy * mxy))
+                      - 2.0 * g3 - 0.5 * uy2 * p34 - 0.5 * ux2 * m34 - 4.0 * uxy * g5
+                      - 2.0 * uy * g6 - 2.0 * ux * g7;
+
+    // Eq. 32 with g_0 = 0 and g_1, g_2 from Eq. 31.
+    const double ax = g4 - g3, ay = -g3 - g4, c = 2.0 * g3 + g8;
+    f[0] += -4.0 * (g3 - g8);
+    f[1] += Gx + ax + 2.0 * (g7 - g8);
+    f[2] += Gy + ay + 2.0 * (g6 - g8);
+    f[3] += -Gx + ax - 2.0 * (g7 + g8);
+    f[4] += -Gy + ay - 2.0 * (g6 + g8);
+    f[5] += c + (Gx + Gy) + (g5 - g6 - g7);
+    f[6] += c + (Gy - Gx) + (-g5 - g6 + g7);
+    f[7] += c - (Gx + Gy) + (g5 + g6 + g7);
+    f[8] += c + (Gx - Gy) + (-g5 + g6 - g7);
+}
+
+template <int FK>
+__global__ void __launch_bounds__(kBlock)
+k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev F, double apre,
+       double gsum, Rates9 w)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int x = i % g.nx, y = i / g.nx;
+    double f[9];
+    load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
+    double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
+    if (FK != FK_NONE) {
+        const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
+        Fx = apre * Px;
+        Fy = apre * Py;
+        Gx = gsum * Px;
+        Gy = gsum * Py;
+    }
+    collide(f, Fx, Fy, Gx, Gy, w);
+#pragma unroll
+    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
+}
+
+}  // namespace
+
+cudaError_t d2q9_step(const LaunchArgs &a)
+{
+    Rates9 w{a.omega[3] / 12.0, a.omega[4] / 4.0, a.omega[5] / 4.0,
+             a.omega[6] / 4.0, a.omega[7] / 4.0, a.omega[8] / 4.0};
+    const double gsum = (a.apre + a.apost) / 12.0;
+    const int grid = (a.g.N + kBlock - 1) / kBlock;
+    switch (a.fkind) {
+    case FK_NONE: k_step<FK_NONE><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
+    case FK_CONST: k_step<FK_CONST><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
+    default: k_step<FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmk

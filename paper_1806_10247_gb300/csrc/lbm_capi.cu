@@ -1,0 +1,472 @@
+// C ABI of the library (declared in include/lbm.h): context management,
+// argument validation, field uploads, the host step loop with the force /
+// source envelope, and the data movement entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbmk;
+
+namespace {
+
+struct DeviceField {
+    int kind = FK_NONE;   // FieldKind seen by the kernels
+    double *dev = nullptr;
+    size_t cap = 0;       // doubles allocated at dev
+    FieldDev d{};
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lbm_ctx {
+    int lattice = 0, q = 0, dim = 0, storage = 0;
+    Geom g{};
+    double omega[9] = {0};
+    cudaStream_t stream = nullptr;
+    double *A = nullptr;  // stored populations of the current state
+    double *B = nullptr;  // next state / scratch
+    DeviceField force;    // force (flow) or source (scalar)
+    DeviceField vel;      // advecting velocity (scalar)
+    lbm_envelope_fn env = nullptr;
+    void *env_user = nullptr;
+    long t = 0;
+    bool initialised = false;
+    double *snap = nullptr;
+    bool have_snap = false;
+    double *partials = nullptr;
+    double *red_out = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q27 ? 27 : lattice == LBM_D2Q5_CDE ? 5 : 0; }
+int lattice_dim(int lattice) { return lattice == LBM_D3Q27 ? 3 : 2; }
+
+// Relaxation rates that a lattice uses (the others are ignored).
+bool omega_used(int lattice, int k)
+{
+    if (lattice == LBM_D2Q9) return k >= 3 && k <= 8;
+    if (lattice == LBM_D2Q5_CDE) return k >= 1 && k <= 4;
+    return k >= 1 && k <= 6;
+}
+
+void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost)
+{
+    if (!c->env) {
+        apre = apost = 1.0;
+        return;
+    }
+    const double tt = (double)t;
+    const double a0 = c->env(tt, c->env_user), ah = c->env(tt + 0.5, c->env_user),
+                 a1 = c->env(tt + 1.0, c->env_user);
+    apre = 0.5 * (a0 + ah);
+    apost = 0.5 * (ah + a1);
+}
+
+LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost)
+{
+    LaunchArgs a{};
+    a.g = c->g;
+    a.fin = fin;
+    a.fout = fout;
+    a.fkind = c->force.kind;
+    a.F = c->force.d;
+    a.vkind = c->vel.kind;
+    a.V = c->vel.d;
+    a.apre = apre;
+    a.apost = apost;
+    for (int k = 0; k < 9; k++) a.omega[k] = c->omega[k];
+    a.stream = c->stream;
+    return a;
+}
+
+// Upload a shape with `ncomp` components into `out` (replacing any previous one).
+int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, const char *what)
+{
+    if (f == nullptr || f->kind == LBM_FIELD_NONE) {
+        if (out.dev) cudaFree(out.dev);
+        out = DeviceField{};
+        return LBM_OK;
+    }
+    if (f->data == nullptr) return fail(c, LBM_EINVAL, "%s: data is NULL", what);
+    const int n[3] = {c->g.nx, c->g.ny, c->g.nz};
+    DeviceField nf;
+    size_t count = 0;
+    if (f->kind == LBM_FIELD_SEPARABLE) {
+        for (int d = 0; d < 3; d++)
+            if (!(f->len[d] == 1 || f->len[d] == n[d]))
+                return fail(c, LBM_EINVAL, "%s: table length %d on axis %d must be 1 or %d", what, f->len[d], d, n[d]);
+        const size_t per = (size_t)f->len[0] + f->len[1] + f->len[2];
+        count = per * ncomp;
+        if (f->len[0] == 1 && f->len[1] == 1 && f->len[2] == 1) {
+            // Constant shape: the kernels take the per-component product as a scalar.
+            nf.kind = FK_CONST;
+            for (int cc = 0; cc < ncomp; cc++) {
+                const double *t = f->data + cc * per;
+                nf.d.cval[cc] = (t[0] * t[1]) * t[2];
+            }
+            if (out.dev) cudaFree(out.dev);
+            out = nf;
+            return LBM_OK;
+        }
+        nf.d.sep = 1;
+        nf.d.cstride = (long long)per;
+        for (int d = 0; d < 3; d++) nf.d.len[d] = f->len[d];
+    } else if (f->kind == LBM_FIELD_FULL) {
+        count = (size_t)c->g.N * ncomp;
+        nf.d.sep = 0;
+        nf.d.cstride = c->g.N;
+    } else {
+        return fail(c, LBM_EINVAL, "%s: unknown field kind %d", what, f->kind);
+    }
+    nf.kind = FK_GENERAL;
+    // Reuse the previous device buffer when it is large enough (a shape that is
+    // re-uploaded every step costs one copy, no allocation).
+    const bool reuse = out.dev != nullptr && out.cap >= count;
+    if (reuse) {
+        nf.dev = out.dev;
+        nf.cap = out.cap;
+    } else {
+        CK(cudaMalloc(&nf.dev, count * sizeof(double)), "cudaMalloc(field)");
+        nf.cap = count;
+    }
+    // The copy is complete before returning: the caller may reuse its buffer.
+    cudaError_t e = cudaMemcpyAsync(nf.dev, f->data, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        if (!reuse) cudaFree(nf.dev);
+        return cuda_fail(c, e, "upload field");
+    }
+    nf.d.data = nf.dev;
+    if (out.dev && !reuse) cudaFree(out.dev);
+    out = nf;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_relax *relax,
+               const lbm_boundary *bc, int storage, void *stream)
+{
+    g_create_error.clear();
+    if (out == nullptr) return fail(nullptr, LBM_EINVAL, "lbm_create: out is NULL");
+    *out = nullptr;
+    const int q = lattice_q(lattice);
+    if (q == 0) return fail(nullptr, LBM_EINVAL, "lbm_create: unknown lattice %d", lattice);
+    if (storage != LBM_FP64) return fail(nullptr, LBM_EINVAL, "lbm_create: unsupported storage %d", storage);
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: extents must be >= 1");
+    if (lattice_dim(lattice) == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nz must be 1 for a 2D lattice");
+    const long long N = (long long)nx * ny * nz;
+    if (N > 2147483647LL) return fail(nullptr, LBM_EINVAL, "lbm_create: more than 2^31-1 nodes");
+    if (relax == nullptr) return fail(nullptr, LBM_EINVAL, "lbm_create: relax is NULL");
+    for (int k = 0; k < 9; k++)
+        if (omega_used(lattice, k) && !(relax->omega[k] > 0.0 && relax->omega[k] < 2.0))
+            return fail(nullptr, LBM_EINVAL, "lbm_create: omega[%d] = %g outside (0, 2)", k, relax->omega[k]);
+    int wall[3] = {0, 0, 0};
+    if (bc)
+        for (int d = 0; d < 3; d++) {
+            if (bc->axis[d] != LBM_PERIODIC && bc->axis[d] != LBM_BOUNCE_BACK)
+                return fail(nullptr, LBM_EINVAL, "lbm_create: boundary kind %d on axis %d", bc->axis[d], d);
+            wall[d] = bc->axis[d] == LBM_BOUNCE_BACK;
+        }
+    if (lattice_dim(lattice) == 2 && wall[2]) return fail(nullptr, LBM_EINVAL, "lbm_create: walls on z for a 2D lattice");
+
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "lbm_create: out of host memory");
+    c->lattice = lattice;
+    c->q = q;
+    c->dim = lattice_dim(lattice);
+    c->storage = storage;
+    c->g.nx = nx;
+    c->g.ny = ny;
+    c->g.nz = nz;
+    c->g.N = (int)N;
+    c->g.Np = (N + 31) / 32 * 32;
+    for (int d = 0; d < 3; d++) c->g.wall[d] = wall[d];
+    for (int k = 0; k < 9; k++) c->omega[k] = relax->omega[k];
+    c->stream = (cudaStream_t)stream;
+    const size_t bytes = (size_t)q * c->g.Np * sizeof(double);
+    cudaError_t e = cudaMalloc(&c->A, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->B, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)reduce_blocks(c->g) * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&c->red_out, 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? LBM_ENOMEM : LBM_ECUDA;
+        fail(nullptr, code, "lbm_create: cudaMalloc of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        lbm_destroy(c);
+        return code;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream || c->A) cudaStreamSynchronize(c->stream);
+    cudaFree(c->A);
+    cudaFree(c->B);
+    cudaFree(c->snap);
+    cudaFree(c->partials);
+    cudaFree(c->red_out);
+    cudaFree(c->force.dev);
+    cudaFree(c->vel.dev);
+    delete c;
+}
+
+const char *lbm_last_error(const lbm_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const double *rho, const double *u)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->lattice != LBM_D2Q5_CDE && rho == nullptr && !(rho0 > 0.0))
+        return fail(c, LBM_EINVAL, "lbm_init_equilibrium: rho0 must be positive");
+    double uu[3] = {0.0, 0.0, 0.0};
+    if (u0)
+        for (int d = 0; d < c->dim; d++) uu[d] = u0[d];
+    const size_t N = (size_t)c->g.N;
+    double *drho = nullptr, *du = nullptr;
+    // Per-node inputs are staged in A (q*Np >= (1+dim)*N doubles); the
+    // equilibrium goes to B and the scatter then overwrites A.
+    if (rho || u) {
+        double *stage = c->A;
+        if (rho) {
+            drho = stage;
+            CK(cudaMemcpyAsync(drho, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload rho");
+            stage += N;
+        }
+        if (u) {
+            du = stage;
+            CK(cudaMemcpyAsync(du, u, (size_t)c->dim * N * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+               "upload u");
+        }
+    }
+    CK(equilibrium(c->lattice, c->g, rho0, uu, drho, du, c->B, c->stream), "equilibrium kernel");
+    CK(scatter_to_stored(c->lattice, c->g, c->B, c->A, c->stream), "scatter kernel");
+    c->launches += 2;
+    CK(cudaStreamSynchronize(c->stream), "lbm_init_equilibrium");
+    c->t = 0;
+    c->initialised = true;
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+int lbm_set_force(lbm_ctx *c, const lbm_field *shape)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->lattice == LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_force: scalar lattice (use lbm_set_source)");
+    return upload_field(c, shape, c->dim, c->force, "lbm_set_force");
+}
+
+int lbm_set_source(lbm_ctx *c, const lbm_field *shape)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_source: flow lattice (use lbm_set_force)");
+    return upload_field(c, shape, 1, c->force, "lbm_set_source");
+}
+
+int lbm_set_velocity(lbm_ctx *c, const lbm_field *u)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_velocity: only for the scalar lattice");
+    return upload_field(c, u, 2, c->vel, "lbm_set_velocity");
+}
+
+int lbm_set_envelope(lbm_ctx *c, lbm_envelope_fn fn, void *user)
+{
+    if (!c) return LBM_EINVAL;
+    c->env = fn;
+    c->env_user = user;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, long n)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n < 0");
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step: populations not initialised");
+    for (long k = 0; k < n; k++) {
+        double apre, apost;
+        envelope_pair(c, c->t, apre, apost);
+        LaunchArgs a = launch_args(c, c->A, c->B, apre, apost);
+        cudaError_t e;
+        switch (c->lattice) {
+        case LBM_D2Q9: e = d2q9_step(a); break;
+        case LBM_D2Q5_CDE: e = d2q5_step(a); break;
+        default: e = d3q27_step(a); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+        c->launches++;
+        double *tmp = c->A;
+        c->A = c->B;
+        c->B = tmp;
+        c->t++;
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_moments: populations not initialised");
+    if (rho == nullptr || (c->lattice != LBM_D2Q5_CDE && u == nullptr))
+        return fail(c, LBM_EINVAL, "lbm_moments: NULL output");
+    if (where != 0 && where != 1) return fail(c, LBM_EINVAL, "lbm_moments: where must be 0 or 1");
+    double apre, apost;
+    envelope_pair(c, c->t, apre, apost);
+    LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
+    const size_t N = (size_t)c->g.N;
+    double *drho = rho, *du = u;
+    if (where == 0) {  // stage through the scratch buffer B
+        drho = c->B;
+        du = c->B + N;
+    }
+    CK(moments(c->lattice, a, drho, du, half_forced ? 1 : 0), "moments kernel");
+    c->launches++;
+    if (where == 0) {
+        CK(cudaMemcpyAsync(rho, drho, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy rho");
+        if (c->lattice != LBM_D2Q5_CDE)
+            CK(cudaMemcpyAsync(u, du, (size_t)c->dim * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "copy u");
+        CK(cudaStreamSynchronize(c->stream), "lbm_moments");
+    }
+    return LBM_OK;
+}
+
+int lbm_reduce(lbm_ctx *c, double out[5])
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_reduce: populations not initialised");
+    if (!out) return fail(c, LBM_EINVAL, "lbm_reduce: out is NULL");
+    if (!c->snap) {
+        const int ncomp = c->lattice == LBM_D2Q5_CDE ? 1 : c->dim;
+        CK(cudaMalloc(&c->snap, (size_t)ncomp * c->g.N * sizeof(double)), "cudaMalloc(snapshot)");
+        c->have_snap = false;
+    }
+    double apre, apost;
+    envelope_pair(c, c->t, apre, apost);
+    LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
+    const int nb = reduce_blocks(c->g);
+    CK(reduce(c->lattice, a, c->snap, c->have_snap ? 1 : 0, c->partials, nb, c->red_out), "reduce kernels");
+    c->launches += 2;
+    double r[8];
+    CK(cudaMemcpyAsync(r, c->red_out, sizeof r, cudaMemcpyDeviceToHost, c->stream), "copy reduction");
+    CK(cudaStreamSynchronize(c->stream), "lbm_reduce");
+    out[0] = r[0];
+    out[1] = r[1];
+    out[2] = r[2];
+    out[3] = r[3];
+    out[4] = c->have_snap ? r[4] : std::numeric_limits<double>::infinity();
+    c->have_snap = true;
+    if (r[5] != 0.0) return fail(c, LBM_EUNSTABLE, "lbm_reduce: non-finite or non-positive density/scalar");
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations: populations not initialised");
+    if (!dst || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_get_populations: count must be q*N");
+    CK(gather_from_stored(c->lattice, c->g, c->A, c->B, c->stream), "gather kernel");
+    c->launches++;
+    const size_t N = (size_t)c->g.N;
+    const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpy2DAsync(dst, N * sizeof(double), c->B, (size_t)c->g.Np * sizeof(double), N * sizeof(double),
+                         (size_t)c->q, kind, c->stream),
+       "copy populations");
+    if (!where) CK(cudaStreamSynchronize(c->stream), "lbm_get_populations");
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, long step)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (!src || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_set_populations: count must be q*N");
+    if (step < 0) return fail(c, LBM_EINVAL, "lbm_set_populations: step < 0");
+    const size_t N = (size_t)c->g.N;
+    const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpy2DAsync(c->B, (size_t)c->g.Np * sizeof(double), src, N * sizeof(double), N * sizeof(double),
+                         (size_t)c->q, kind, c->stream),
+       "copy populations");
+    CK(scatter_to_stored(c->lattice, c->g, c->B, c->A, c->stream), "scatter kernel");
+    c->launches++;
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_populations");
+    c->t = step;
+    c->initialised = true;
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+int lbm_get_step(const lbm_ctx *c, long *step)
+{
+    if (!c || !step) return LBM_EINVAL;
+    *step = c->t;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx *c)
+{
+    if (!c) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(c->stream), "lbm_sync");
+    return LBM_OK;
+}
+
+int lbm_launch_count(const lbm_ctx *c, long long *count)
+{
+    if (!c || !count) return LBM_EINVAL;
+    *count = c->launches;
+    return LBM_OK;
+}
+
+}  // extern "C"

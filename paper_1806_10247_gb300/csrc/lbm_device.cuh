@@ -1,0 +1,47 @@
+// Device-side building blocks shared by the lattice kernels: grid geometry
+// and evaluation of force / source / velocity shapes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+// Lattice geometry.  Populations are stored as planes of Np doubles (Np = N
+// rounded up to a multiple of 32, so that every plane starts on a 256-byte
+// boundary); node (x, y, z) sits at offset x + nx*(y + ny*z) in each plane.
+struct Geom {
+    int nx, ny, nz;
+    int N;          // nodes (validated < 2^31 on the host)
+    long long Np;   // plane stride in doubles
+    int wall[3];    // 1 = halfway bounce-back walls on that axis, 0 = periodic
+};
+
+// Kinds of a force / source / velocity shape as seen by a kernel.
+enum FieldKind { FK_NONE = 0, FK_CONST = 1, FK_GENERAL = 2 };
+
+// A shape on the device.  CONST: per-component values in cval.  GENERAL:
+// either separable tables (sep = 1: for component c, px at data + c*cstride,
+// then py, then pz, with lengths len[0..2], 1 meaning constant on that axis)
+// or a full field (sep = 0: data[c*cstride + node]).
+struct FieldDev {
+    const double *data;
+    long long cstride;
+    int len[3];
+    int sep;
+    double cval[3];
+};
+
+__device__ __forceinline__ double field_value(const FieldDev &F, int kind, int c, int x, int y, int z,
+                                              int node)
+{
+    if (kind == FK_CONST) return F.cval[c];
+    const double *t = F.data + c * F.cstride;
+    if (!F.sep) return __ldg(t + node);
+    double px = __ldg(t + (F.len[0] > 1 ? x : 0));
+    double py = __ldg(t + F.len[0] + (F.len[1] > 1 ? y : 0));
+    double pz = __ldg(t + F.len[0] + F.len[1] + (F.len[2] > 1 ? z : 0));
+    return (px * py) * pz;  // the documented evaluation order of a separable shape
+}
+
+}  // namespace lbmk

@@ -1,0 +1,55 @@
+// Host-side interface between the C ABI (lbm_capi.cu) and the per-lattice
+// kernel launchers (k_d2q9.cu, k_d2q5.cu, k_d3q27.cu, k_common.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbmk {
+
+// Everything one launch of a step / moments / reduction kernel needs.
+struct LaunchArgs {
+    Geom g;
+    const double *fin;   // stored populations (the state from which f(t) is pulled)
+    double *fout;        // step: new stored populations
+    int fkind;           // FieldKind of the force (flow) or source (scalar)
+    FieldDev F;
+    int vkind;           // scalar lattice: FieldKind of the advecting velocity
+    FieldDev V;
+    double apre, apost;  // envelope averages of the two half steps
+    double omega[9];
+    cudaStream_t stream;
+};
+
+// Relaxation rates are validated on the host; omega_high_one records whether
+// every rate of order >= 3 equals 1 (enables the reduced collision).
+
+// One fused stream + collide step (pull form): fin -> fout.
+cudaError_t d2q9_step(const LaunchArgs &a);
+cudaError_t d2q5_step(const LaunchArgs &a);
+cudaError_t d3q27_step(const LaunchArgs &a);
+
+// Moments of the current state: rho[N] and u[dim][N] (flow) or phi[N] (scalar);
+// half = 1 adds the pre-collision half force / source.
+cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, int half);
+
+// Per-block partial reductions (see lbm_reduce) into partials[nblocks][8],
+// updating the snapshot; then a single-block pass writes out[8].
+cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
+                   int nblocks, double *out);
+int reduce_blocks(const Geom &g);
+
+// Equilibrium populations at (rho, u) in plain [q][Np] layout into dst.
+// rho/u may be NULL (uniform rho0/u0).
+cudaError_t equilibrium(int lattice, const Geom &g, double rho0, const double *u0, const double *rho,
+                        const double *u, double *dst, cudaStream_t s);
+
+// Conversions between f(t) in plain [q][Np] layout and the stored layout
+// (stored = inverse stream of f(t); f(t) = pull of stored).
+cudaError_t scatter_to_stored(int lattice, const Geom &g, const double *plain, double *stored,
+                              cudaStream_t s);
+cudaError_t gather_from_stored(int lattice, const Geom &g, const double *stored, double *plain,
+                               cudaStream_t s);
+
+}  // namespace lbmk

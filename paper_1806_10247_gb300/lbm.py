@@ -1,0 +1,297 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``_lib/liblbm_gb300.so``.  There is no CPU fallback; if the library has not
+been built, or no CUDA device is present, the calls fail loudly.
+
+The Python names mirror the C entry points (``lbm_create`` ->
+:class:`Lattice`, ``lbm_step`` -> :meth:`Lattice.step`, ...).  Arrays are numpy
+(host) or anything exposing ``data_ptr()`` (device, e.g. a CUDA torch tensor)
+where the C call takes ``where = 1``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+D2Q9, D3Q27, D2Q5_CDE = 1, 2, 3
+FP64 = 0
+PERIODIC, BOUNCE_BACK = 0, 1
+FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL = 0, 1, 2
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, -1, -2, -3, -4, -6
+Q = {D2Q9: 9, D3Q27: 27, D2Q5_CDE: 5}
+DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2}
+
+EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium", "lbm_set_force",
+           "lbm_set_source", "lbm_set_velocity", "lbm_set_envelope", "lbm_step", "lbm_moments",
+           "lbm_reduce", "lbm_get_populations", "lbm_set_populations", "lbm_get_step", "lbm_sync",
+           "lbm_launch_count")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbm error {code}: {msg}")
+        self.code = code
+
+
+class _Relax(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double * 9)]
+
+
+class _Boundary(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int * 3)]
+
+
+class _Field(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("len", ctypes.c_int * 3),
+                ("data", ctypes.POINTER(ctypes.c_double))]
+
+
+ENVELOPE = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library and declare signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise OSError(f"CUDA library not built: {_build.LIB}")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    L.lbm_create.argtypes = [ctypes.POINTER(vp), ip, ip, ip, ip, ctypes.POINTER(_Relax),
+                             ctypes.POINTER(_Boundary), ip, vp]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_init_equilibrium.argtypes = [vp, ctypes.c_double, dp, dp, dp]
+    L.lbm_set_force.argtypes = [vp, ctypes.POINTER(_Field)]
+    L.lbm_set_source.argtypes = [vp, ctypes.POINTER(_Field)]
+    L.lbm_set_velocity.argtypes = [vp, ctypes.POINTER(_Field)]
+    L.lbm_set_envelope.argtypes = [vp, ENVELOPE, vp]
+    L.lbm_step.argtypes = [vp, ctypes.c_long]
+    L.lbm_moments.argtypes = [vp, vp, vp, ip, ip]
+    L.lbm_reduce.argtypes = [vp, dp]
+    L.lbm_get_populations.argtypes = [vp, vp, ctypes.c_size_t, ip]
+    L.lbm_set_populations.argtypes = [vp, vp, ctypes.c_size_t, ip, ctypes.c_long]
+    L.lbm_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
+    L.lbm_sync.argtypes = [vp]
+    L.lbm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    for name in EXPORTS:
+        if name not in ("lbm_destroy", "lbm_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ptr(a):
+    """Address of a numpy array (host) or a CUDA tensor-like object (device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _field(tables=None, full=None):
+    """lbm_field for separable tables [(px, py, pz) per component] or a full [c][N] array."""
+    f = _Field()
+    keep = None
+    if tables is None and full is None:
+        f.kind = FIELD_NONE
+        return f, keep
+    if full is not None:
+        keep = np.ascontiguousarray(full, dtype=np.float64)
+        f.kind = FIELD_FULL
+    else:
+        lens = [len(np.atleast_1d(t)) for t in tables[0]]
+        parts = []
+        for comp in tables:
+            assert [len(np.atleast_1d(t)) for t in comp] == lens, "all components need equal table lengths"
+            parts += [np.atleast_1d(np.asarray(t, np.float64)) for t in comp]
+        keep = np.ascontiguousarray(np.concatenate(parts))
+        f.kind = FIELD_SEPARABLE
+        for d in range(3):
+            f.len[d] = lens[d]
+    f.data = _dp(keep)
+    return f, keep
+
+
+class Lattice:
+    """One lattice on the GPU (an ``lbm_ctx``)."""
+
+    def __init__(self, lattice, shape, omega, wall=(0, 0, 0), storage=FP64, stream=None):
+        L = load()
+        self._L = L
+        self.lattice = lattice
+        self.shape = tuple(int(s) for s in shape)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.q = Q[lattice]
+        self.dim = DIM[lattice]
+        r = _Relax()
+        for k in range(9):
+            r.omega[k] = float(omega[k])
+        b = _Boundary()
+        for d in range(3):
+            b.axis[d] = BOUNCE_BACK if wall[d] else PERIODIC
+        h = ctypes.c_void_p()
+        s = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = L.lbm_create(ctypes.byref(h), int(lattice), *self.shape, ctypes.byref(r), ctypes.byref(b),
+                          int(storage), s)
+        if rc != OK:
+            raise LBMError(rc, L.lbm_last_error(None).decode())
+        self.h = h
+        self._env = None
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LBMError(rc, self._L.lbm_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._L.lbm_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- set-up -------------------------------------------------------------
+    def init_equilibrium(self, rho=1.0, u=(0.0, 0.0, 0.0)):
+        """Equilibrium fill at uniform or per-node (rho, u)."""
+        rho_arr = None
+        u_arr = None
+        rho0 = 1.0
+        u0 = np.zeros(3)
+        if np.ndim(rho) == 0:
+            rho0 = float(rho)
+        else:
+            rho_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, np.float64), (self.N,)))
+        u = np.asarray(u, np.float64)
+        if u.ndim == 1:
+            u0[: len(u)] = u
+        else:
+            u_arr = np.ascontiguousarray(u[: self.dim], dtype=np.float64)
+        self._check(self._L.lbm_init_equilibrium(self.h, rho0, _dp(u0), _dp(rho_arr), _dp(u_arr)))
+
+    def set_force(self, tables=None, full=None):
+        f, keep = _field(tables, full)
+        self._check(self._L.lbm_set_force(self.h, ctypes.byref(f)))
+
+    def set_source(self, tables=None, full=None):
+        f, keep = _field(tables, full)
+        self._check(self._L.lbm_set_source(self.h, ctypes.byref(f)))
+
+    def set_velocity(self, tables=None, full=None):
+        f, keep = _field(tables, full)
+        self._check(self._L.lbm_set_velocity(self.h, ctypes.byref(f)))
+
+    def set_envelope(self, fn):
+        """fn(t) -> a(t), or None for a == 1."""
+        if fn is None:
+            self._env = None
+            self._check(self._L.lbm_set_envelope(self.h, ENVELOPE(), None))
+            return
+        self._env = ENVELOPE(lambda t, user: float(fn(t)))
+        self._check(self._L.lbm_set_envelope(self.h, self._env, None))
+
+    # -- stepping and output -----------------------------------------------
+    def step(self, n=1):
+        self._check(self._L.lbm_step(self.h, int(n)))
+
+    def moments(self, half_forced=True, out=None, where=0):
+        """Host: returns rho [N], u [dim][N] (flow) or phi [N] (scalar).
+        Device (where=1): fills the given (rho, u) device buffers."""
+        if where == 1:
+            rho, u = out
+            self._check(self._L.lbm_moments(self.h, _ptr(rho), _ptr(u), 1, int(bool(half_forced))))
+            return out
+        rho = np.empty(self.N)
+        u = np.empty((self.dim, self.N)) if self.lattice != D2Q5_CDE else None
+        self._check(self._L.lbm_moments(self.h, rho.ctypes.data, None if u is None else u.ctypes.data, 0,
+                                        int(bool(half_forced))))
+        return rho if self.lattice == D2Q5_CDE else (rho, u)
+
+    def reduce(self):
+        """[sum rho, sum jx, sum jy, sum jz, max change since last call]; raises on instability."""
+        out = np.empty(5)
+        self._check(self._L.lbm_reduce(self.h, _dp(out)))
+        return out
+
+    def get_populations(self, out=None, where=0):
+        if where == 1:
+            self._check(self._L.lbm_get_populations(self.h, _ptr(out), self.q * self.N, 1))
+            return out
+        f = np.empty((self.q, self.N))
+        self._check(self._L.lbm_get_populations(self.h, f.ctypes.data, f.size, 0))
+        return f
+
+    def set_populations(self, f, step=0, where=0):
+        if where == 1:
+            self._check(self._L.lbm_set_populations(self.h, _ptr(f), self.q * self.N, 1, int(step)))
+            return
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.size == self.q * self.N
+        self._check(self._L.lbm_set_populations(self.h, f.ctypes.data, f.size, 0, int(step)))
+
+    @property
+    def t(self):
+        v = ctypes.c_long()
+        self._check(self._L.lbm_get_step(self.h, ctypes.byref(v)))
+        return v.value
+
+    def sync(self):
+        self._check(self._L.lbm_sync(self.h))
+
+    def launch_count(self):
+        v = ctypes.c_longlong()
+        self._check(self._L.lbm_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+
+def from_workload(w, stream=None) -> Lattice:
+    """Lattice set up (force/source, velocity, envelope, equilibrium) from a
+    :class:`paper_1806_10247_gb300.workloads.Workload`."""
+    lat = {1: D2Q9, 2: D3Q27, 3: D2Q5_CDE}[w.lattice]
+    L = Lattice(lat, w.shape, w.omega, wall=w.wall, stream=stream)
+    if w.tables is not None:
+        if lat == D2Q5_CDE:
+            L.set_source(tables=w.tables)
+        else:
+            L.set_force(tables=w.tables)
+    if lat == D2Q5_CDE:
+        u = np.asarray(w.u0, np.float64)
+        L.set_velocity(tables=[(np.array([u[0]]), np.array([1.0]), np.array([1.0])),
+                               (np.array([u[1]]), np.array([1.0]), np.array([1.0]))])
+    if w.envelope is not None:
+        L.set_envelope(w.envelope)
+    L.init_equilibrium(w.rho0, w.u0)
+    return L

@@ -1,0 +1,121 @@
+"""GPU checks of the C ABI's state handling: ordering errors, no-op steps,
+checkpoint/restore, device-pointer outputs, reductions and the instability
+flag (raised by host-injected NaN populations, never by a GPU fault)."""
+import numpy as np
+import pytest
+
+from paper_1806_10247_gb300 import lbm
+from paper_1806_10247_gb300 import workloads as W
+from tests.gpu_helpers import compare_state, oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+
+def test_step_before_init_is_a_state_error():
+    L = lbm.Lattice(lbm.D2Q9, (4, 4, 1), W.d2q9_omega(0.8))
+    with pytest.raises(lbm.LBMError) as e:
+        L.step(1)
+    assert e.value.code == lbm.ESTATE
+    with pytest.raises(lbm.LBMError):
+        L.moments()
+
+
+def test_zero_steps_is_a_no_op_and_negative_is_invalid():
+    L = lbm.from_workload(W.poiseuille(ny=9))
+    f0 = L.get_populations()
+    n0 = L.launch_count()
+    L.step(0)
+    assert L.t == 0 and L.launch_count() == n0
+    assert np.array_equal(L.get_populations(), f0)
+    with pytest.raises(lbm.LBMError) as e:
+        L.step(-1)
+    assert e.value.code == lbm.EINVAL
+
+
+def test_checkpoint_restore_is_bitwise_identical():
+    w = W.kolmogorov(shape=(8, 12, 6))
+    A = lbm.from_workload(w)
+    A.step(7)
+    snap = A.get_populations()
+    A.step(13)
+    B = lbm.from_workload(w)
+    B.set_populations(snap, step=7)
+    assert np.array_equal(B.get_populations(), snap)
+    B.step(13)
+    assert B.t == A.t == 20
+    assert np.array_equal(A.get_populations(), B.get_populations())
+
+
+def test_device_outputs_match_host_outputs():
+    torch = pytest.importorskip("torch")
+    w = W.poiseuille(ny=17)
+    L = lbm.from_workload(w)
+    L.step(50)
+    rho_h, u_h = L.moments()
+    rho_d = torch.empty(L.N, dtype=torch.float64, device="cuda")
+    u_d = torch.empty((2, L.N), dtype=torch.float64, device="cuda")
+    L.moments(out=(rho_d, u_d), where=1)
+    L.sync()
+    assert np.array_equal(rho_d.cpu().numpy(), rho_h)
+    assert np.array_equal(u_d.cpu().numpy(), u_h)
+    f_d = torch.empty((9, L.N), dtype=torch.float64, device="cuda")
+    L.get_populations(out=f_d, where=1)
+    L.sync()
+    assert np.array_equal(f_d.cpu().numpy(), L.get_populations())
+
+
+def test_reduce_mass_momentum_and_convergence_metric():
+    w = W.poiseuille()
+    L = lbm.from_workload(w)
+    R = oracle_from_workload(w)
+    r0 = L.reduce()
+    assert np.isinf(r0[4])
+    assert abs(r0[0] - L.N) < 1e-12 * L.N
+    L.step(100)
+    R.run(100)
+    r1 = L.reduce()
+    rho, u = R.moments()
+    f = R.f
+    assert abs(r1[0] - r0[0]) < 1e-13 * L.N
+    jx = (f[1] - f[3] + f[5] - f[6] - f[7] + f[8]).sum()
+    assert abs(r1[1] - jx) < 1e-15 * L.N
+    L.step(100)
+    R.run(100)
+    r2 = L.reduce()
+    _, u2 = R.moments()
+    assert abs(r2[4] - np.abs(u2 - u).max()) <= 1e-12 * np.abs(u2).max()
+
+
+def test_nan_population_raises_unstable():
+    w = W.poiseuille(ny=9)
+    L = lbm.from_workload(w)
+    f = L.get_populations()
+    f[2, 5] = np.nan
+    L.set_populations(f, step=0)
+    L.step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        L.reduce()
+    assert e.value.code == lbm.EUNSTABLE
+
+
+def test_invalid_field_lengths_are_rejected():
+    L = lbm.Lattice(lbm.D2Q9, (6, 4, 1), W.d2q9_omega(0.8))
+    with pytest.raises(lbm.LBMError) as e:
+        L.set_force(tables=[(np.ones(5), np.ones(1), np.ones(1)), (np.ones(5), np.ones(1), np.ones(1))])
+    assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LBMError):
+        L.set_source(tables=[(np.ones(1), np.ones(1), np.ones(1))])
+
+
+def test_source_lattice_restart_matches_uninterrupted_oracle():
+    c = W.cde_sweep_params(sizes=(64,))[0]
+    w = W.cde_workload(c)
+    A = lbm.from_workload(w)
+    A.step(33)
+    snap = A.get_populations()
+    B = lbm.from_workload(w)
+    B.set_populations(snap, step=33)
+    B.step(40)
+    R = oracle_from_workload(w)
+    R.run(73)
+    compare_state(B, R)
