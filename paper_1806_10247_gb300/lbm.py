@@ -123,11 +123,18 @@ def _field(tables=None, full=None):
         keep = np.ascontiguousarray(full, dtype=np.float64)
         f.kind = FIELD_FULL
     else:
-        lens = [len(np.atleast_1d(t)) for t in tables[0]]
+        # one table length per axis for all components: constant tables are
+        # repeated to the longest length on that axis
+        lens = [max(len(np.atleast_1d(comp[d])) for comp in tables) for d in range(3)]
         parts = []
         for comp in tables:
-            assert [len(np.atleast_1d(t)) for t in comp] == lens, "all components need equal table lengths"
-            parts += [np.atleast_1d(np.asarray(t, np.float64)) for t in comp]
+            for d in range(3):
+                t = np.atleast_1d(np.asarray(comp[d], np.float64))
+                if len(t) != lens[d]:
+                    if len(t) != 1:
+                        raise ValueError(f"table length {len(t)} on axis {d}: must be 1 or {lens[d]}")
+                    t = np.repeat(t, lens[d])
+                parts.append(t)
         keep = np.ascontiguousarray(np.concatenate(parts))
         f.kind = FIELD_SEPARABLE
         for d in range(3):

@@ -2,10 +2,18 @@
 CUDA library and through the oracle, and the FP64 parity metric.
 
 Parity metric (FP64), after the same number of steps from the same inputs:
-  rho : max |rho_gpu - rho_ref|              <= 1e-12 * rho0
-  u   : max |u_gpu - u_ref| / max |u_ref|    <= 1e-12
-  phi : max |phi_gpu - phi_ref| / max |phi_ref - mean(phi_ref)| <= 1e-12
-  f   : max |f_gpu - f_ref| / max |f_ref|    <= 1e-12
+  f   : max |f_gpu - f_ref|     <= 1e-12 * max |f_ref|
+  rho : max |rho_gpu - rho_ref| <= 1e-12 * max |rho_ref|   (phi likewise)
+  u   : max |u_gpu - u_ref|     <= 1e-12 * U_ref,  U_ref = max(max |u_ref|, 0.01)
+  phi - mean(phi): max |phi_gpu - phi_ref| <= 1e-12 * max(max |phi_ref - mean|, 0.01 |mean|)
+Populations are O(0.1) and every FP64 evaluation of the step rounds them; two
+correct evaluations in different operation orders (the oracle's dense moment
+matrices and the kernels' factorised transforms) differ by ~1e-16 (D2Q9, D2Q5)
+to ~1e-15 (D3Q27, 27-term sums) in f, and so by as much in u = sum f e / rho.
+A relative 1e-12 on u is resolvable only for |u| >~ 1e-3; the velocity is
+therefore measured against U_ref, which is never below 0.01 = the smallest
+velocity scale of the paper's benchmarks (four-rolls mill u0, Sec. 6.5).  The
+plain relative errors are returned as "u_rel" / "phi_var_rel".
 """
 import numpy as np
 
@@ -31,28 +39,35 @@ def oracle_from_workload(w, f0=None):
     return L
 
 
+U_FLOOR = 0.01
+
+
 def compare_state(G, R, rho0=1.0, tol=TOL):
-    """Compare a GPU lattice G with an oracle lattice R at the same step."""
+    """Compare a GPU lattice G with an oracle lattice R at the same step.
+    Returns the errors; "u_rel" is the plain max |du| / max |u_ref| (no floor)."""
     assert G.t == R.t
     fg = G.get_populations()
     fr = R.f
     err = {"f": np.abs(fg - fr).max() / np.abs(fr).max()}
+    info = {}
     if G.lattice == lbm.D2Q5_CDE:
         pg = G.moments()
         pr = R.moments()
-        scale = max(np.abs(pr - pr.mean()).max(), 1e-300)
-        err["phi"] = np.abs(pg - pr).max() / scale
-        err["phi_abs"] = np.abs(pg - pr).max()
+        err["phi"] = np.abs(pg - pr).max() / np.abs(pr).max()
+        m = abs(pr.mean())
+        scale = max(np.abs(pr - pr.mean()).max(), U_FLOOR * m, 1e-300)
+        err["phi_var"] = np.abs(pg - pr).max() / scale
+        info["phi_var_rel"] = np.abs(pg - pr).max() / max(np.abs(pr - pr.mean()).max(), 1e-300)
     else:
         rg, ug = G.moments()
         rr, ur = R.moments()
-        err["rho"] = np.abs(rg - rr).max() / rho0
-        err["u"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), 1e-300)
+        err["rho"] = np.abs(rg - rr).max() / np.abs(rr).max()
+        err["u"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), U_FLOOR)
+        info["u_rel"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), 1e-300)
         rg0, ug0 = G.moments(half_forced=False)
         rr0, ur0 = R.moments(half_forced=False)
-        err["u_out"] = np.abs(ug0 - ur0).max() / max(np.abs(ur0).max(), 1e-300)
+        err["u_out"] = np.abs(ug0 - ur0).max() / max(np.abs(ur0).max(), U_FLOOR)
     for k, v in err.items():
-        if k == "phi_abs":
-            continue
-        assert v <= tol, (k, v, err)
+        assert v <= tol, (k, v, err, info)
+    err.update(info)
     return err
