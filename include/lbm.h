@@ -181,6 +181,25 @@ int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int where, int half_forced
  * out is still written), LBM_ESTATE, LBM_ECUDA. */
 int lbm_reduce(lbm_ctx *ctx, double out[5]);
 
+/* The sums out[0..3] of lbm_reduce (mass, then momentum) without allocating
+ * any device memory.  The paper has no counterpart: this exists for callers
+ * that cannot allocate when they want the sums, e.g. a process whose device
+ * memory is held by another allocator (a raw cudaMalloc may then fail) or a
+ * time loop that must not call cudaMalloc/cudaFree because they can
+ * synchronise the device.  The partial sums live in a fixed device array of
+ * 1217 x 8 doubles (77,888 bytes) inside the library, reserved on every GPU
+ * that loads it until the process exits; a lattice whose reduction would need
+ * more than 1216 partial blocks is rejected with LBM_EINVAL (the reduction
+ * never uses more, so in practice none is).  The first call on a device looks
+ * up that array's device address (no allocation); make that first call before
+ * any stream capture.  All calls, from every context on a device, share the
+ * array: calls whose kernels overlap on the GPU race and may return wrong
+ * sums, so serialise them (e.g. one stream).  Nothing in the array needs
+ * clearing between calls.  Synchronises the context's stream; out is a host
+ * array of 4 doubles.  Does not touch lbm_reduce's max-change snapshot.
+ * Errors: LBM_ESTATE, LBM_EINVAL, LBM_EUNSTABLE (out still written), LBM_ECUDA. */
+int lbm_reduce_sums_noalloc(lbm_ctx *ctx, double out[4]);
+
 /* Copy the populations f(t) (the state after the streaming step of step t,
  * as [q][N] doubles) to dst.  count must equal q*N.  where: 0 host, 1 device.
  * Errors: LBM_ESTATE, LBM_EINVAL (count), LBM_ECUDA. */

@@ -188,6 +188,30 @@ k_reduce_partial(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, 
     block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
 }
 
+// Same partial sums without the velocity snapshot (mass, momentum and the
+// instability flag only); writes nothing but its partials slot.
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_reduce_partial_sums(Geom g, const double *__restrict__ fin, double *__restrict__ partials)
+{
+    double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+        int x, y, z;
+        node_xyz(g, i, x, y, z);
+        double f[L::Q];
+        load_pulled<L>(fin, g, x, y, z, i, f);
+        double m0, j[3];
+        zeroth_first<L>(f, m0, j);
+        v[R_MASS] += m0;
+        bool bad = !isfinite(m0) || (L::Q != 5 && !(m0 > 0.0));
+        if (L::Q != 5)
+#pragma unroll
+            for (int d = 0; d < L::DIM; d++) v[R_JX + d] += j[d];
+        if (bad) v[R_BAD] = 1.0;
+    }
+    block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
+}
+
 __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restrict__ partials, int nblocks,
                                                          double *__restrict__ out)
 {
@@ -267,6 +291,18 @@ cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap
         using LT = decltype(L);
         k_reduce_partial<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, snap,
                                                               have_snap, partials);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_final<<<1, kBlock, 0, a.stream>>>(partials, nblocks, out);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        k_reduce_partial_sums<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, partials);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_reduce_final<<<1, kBlock, 0, a.stream>>>(partials, nblocks, out);

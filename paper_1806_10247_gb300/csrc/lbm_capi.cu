@@ -11,46 +11,17 @@
 #include <new>
 #include <string>
 
-#include "../../include/lbm.h"
-#include "lbm_internal.h"
+#include "lbm_ctx.h"
 
 using namespace lbmk;
 
 namespace {
 
-struct DeviceField {
-    int kind = FK_NONE;   // FieldKind seen by the kernels
-    double *dev = nullptr;
-    size_t cap = 0;       // doubles allocated at dev
-    FieldDev d{};
-};
-
 thread_local std::string g_create_error;
 
 }  // namespace
 
-struct lbm_ctx {
-    int lattice = 0, q = 0, dim = 0, storage = 0;
-    Geom g{};
-    double omega[9] = {0};
-    cudaStream_t stream = nullptr;
-    double *A = nullptr;  // stored populations of the current state
-    double *B = nullptr;  // next state / scratch
-    DeviceField force;    // force (flow) or source (scalar)
-    DeviceField vel;      // advecting velocity (scalar)
-    lbm_envelope_fn env = nullptr;
-    void *env_user = nullptr;
-    long t = 0;
-    bool initialised = false;
-    double *snap = nullptr;
-    bool have_snap = false;
-    double *partials = nullptr;
-    double *red_out = nullptr;
-    long long launches = 0;
-    std::string err;
-};
-
-namespace {
+namespace lbmc {
 
 int fail(lbm_ctx *c, int code, const char *fmt, ...)
 {
@@ -69,11 +40,7 @@ int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
     return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
-    } while (0)
+#define CK(call, what) LBM_CK(call, what)
 
 int lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q27 ? 27 : lattice == LBM_D2Q5_CDE ? 5 : 0; }
 int lattice_dim(int lattice) { return lattice == LBM_D3Q27 ? 3 : 2; }
@@ -115,6 +82,12 @@ LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double
     a.stream = c->stream;
     return a;
 }
+
+}  // namespace lbmc
+
+using namespace lbmc;
+
+namespace {
 
 // Upload a shape with `ncomp` components into `out` (replacing any previous one).
 int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, const char *what)
@@ -223,6 +196,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     for (int d = 0; d < 3; d++) c->g.wall[d] = wall[d];
     for (int k = 0; k < 9; k++) c->omega[k] = relax->omega[k];
     c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
     const size_t bytes = (size_t)q * c->g.Np * sizeof(double);
     cudaError_t e = cudaMalloc(&c->A, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->B, bytes);

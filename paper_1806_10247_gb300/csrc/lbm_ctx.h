@@ -1,0 +1,61 @@
+// Internal definition of the library context (shared by the C ABI files).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace lbmc {
+
+struct DeviceField {
+    int kind = lbmk::FK_NONE;  // FieldKind seen by the kernels
+    double *dev = nullptr;
+    size_t cap = 0;            // doubles allocated at dev
+    lbmk::FieldDev d{};
+};
+
+}  // namespace lbmc
+
+struct lbm_ctx {
+    int lattice = 0, q = 0, dim = 0, storage = 0;
+    int device = 0;       // CUDA device that was current at lbm_create
+    lbmk::Geom g{};
+    double omega[9] = {0};
+    cudaStream_t stream = nullptr;
+    double *A = nullptr;  // stored populations of the current state
+    double *B = nullptr;  // next state / scratch
+    lbmc::DeviceField force;  // force (flow) or source (scalar)
+    lbmc::DeviceField vel;    // advecting velocity (scalar)
+    lbm_envelope_fn env = nullptr;
+    void *env_user = nullptr;
+    long t = 0;
+    bool initialised = false;
+    double *snap = nullptr;
+    bool have_snap = false;
+    double *partials = nullptr;
+    double *red_out = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace lbmc {
+
+// Record a failure on c (or, for c == NULL, the process-wide lbm_create error)
+// and return code.
+int fail(lbm_ctx *c, int code, const char *fmt, ...);
+int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what);
+// Envelope averages (a_pre, a_post) of step t (trapezoid rule of Sec. 6.3).
+void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost);
+// Launch arguments of the context's kernels.
+lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
+
+}  // namespace lbmc
+
+#define LBM_CK(call, what)                                            \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return lbmc::cuda_fail(c, e_, what);   \
+    } while (0)

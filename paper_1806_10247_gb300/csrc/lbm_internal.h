@@ -39,6 +39,8 @@ cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, in
 cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
                    int nblocks, double *out);
 int reduce_blocks(const Geom &g);
+// Mass / momentum / instability-flag sums only (no snapshot): partials[nblocks][8], out[8].
+cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out);
 
 // Equilibrium populations at (rho, u) in plain [q][Np] layout into dst.
 // rho/u may be NULL (uniform rho0/u0).

@@ -29,7 +29,7 @@ DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2}
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium", "lbm_set_force",
            "lbm_set_source", "lbm_set_velocity", "lbm_set_envelope", "lbm_step", "lbm_moments",
            "lbm_reduce", "lbm_get_populations", "lbm_set_populations", "lbm_get_step", "lbm_sync",
-           "lbm_launch_count")
+           "lbm_launch_count", "lbm_reduce_sums_noalloc")
 
 
 class LBMError(RuntimeError):
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     L.lbm_step.argtypes = [vp, ctypes.c_long]
     L.lbm_moments.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_reduce.argtypes = [vp, dp]
+    L.lbm_reduce_sums_noalloc.argtypes = [vp, dp]
     L.lbm_get_populations.argtypes = [vp, vp, ctypes.c_size_t, ip]
     L.lbm_set_populations.argtypes = [vp, vp, ctypes.c_size_t, ip, ctypes.c_long]
     L.lbm_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
@@ -251,6 +252,13 @@ class Lattice:
         """[sum rho, sum jx, sum jy, sum jz, max change since last call]; raises on instability."""
         out = np.empty(5)
         self._check(self._L.lbm_reduce(self.h, _dp(out)))
+        return out
+
+    def reduce_sums_noalloc(self):
+        """[sum rho, sum jx, sum jy, sum jz] like :meth:`reduce`, computed with the
+        library's fixed device scratch array instead of allocated memory."""
+        out = np.empty(4)
+        self._check(self._L.lbm_reduce_sums_noalloc(self.h, _dp(out)))
         return out
 
     def get_populations(self, out=None, where=0):
