@@ -39,11 +39,12 @@ FALLBACK_HBM_GBS = 6800.0
 # reported only while the kernel source still hashes to the value it was
 # measured on.
 KERNEL_FACTS = {
-    "d2q5_step": {
+    "cde_sweep": {
         "src": ["paper_1806_10247_gb300/csrc/k_d2q5.cu", "paper_1806_10247_gb300/csrc/lbm_lattices.cuh",
+                "paper_1806_10247_gb300/csrc/lbm_internal.h",
                 "paper_1806_10247_gb300/csrc/lbm_device.cuh"],
         "fp64_flops_per_node": None,
-        "traffic_bytes_per_launch_512": None,
+        "traffic_bytes_per_launch": None,
         "traffic_src_sha": None,
     },
 }
@@ -61,6 +62,19 @@ def src_hash(paths):
 
 def sweep_workloads():
     return [W.cde_workload(c) for c in W.cde_sweep_params()]
+
+
+WORKLOADS = {
+    "cde_sweep": ("cde_d2q5_refinement_sweep_fp64", sweep_workloads),
+    "poiseuille": ("poiseuille_d2q9_3x33_fp64", lambda: [W.poiseuille()]),
+    "kolmogorov256": ("kolmogorov_d3q27_256cubed_fp64", lambda: [W.kolmogorov(n=256)]),
+    "kolmogorov512": ("kolmogorov_d3q27_512cubed_fp64", lambda: [W.kolmogorov(n=512)]),
+    "duct128": ("duct_d3q27_128x128x128_fp64", lambda: [W.duct(n=128, nx=128)]),
+    "kolmogorov96": ("kolmogorov_d3q27_96cubed_fp64", lambda: [W.kolmogorov(n=96)]),
+    "channel2048": ("channel_d2q9_2048x1024_fp64", lambda: [W.poiseuille(ny=1024, nx=2048)]),
+}
+Q_OF = {W.D2Q9: 9, W.D2Q5: 5, W.D3Q27: 27}
+L2_BYTES = 129 * 1024 * 1024
 
 
 def load_peaks():
@@ -157,7 +171,8 @@ def time_oracle(workloads, steps, budget_s=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    wl = sweep_workloads()
+    wname, make = WORKLOADS[args.workload]
+    wl = make()
     from oracle import oracle as O
 
     O.build()
@@ -168,7 +183,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec / done * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_block(wl),
+        "data": "synthetic", "config": config_block(wl, wname),
         "cpu_baseline": {"kind": "oracle", "value": v, "unit": "MLUPS", "cores": threads,
                          "sample": f"{done} steps of the whole sweep ({upd} node updates)"},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -176,12 +191,22 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def config_block(wl):
-    return {"workload": "cde_d2q5_refinement_sweep_fp64",
-            "lattices": [w.name for w in wl], "nodes_per_step": sum(w.nodes for w in wl),
-            "seed": W.SEED, "D": wl[0].meta["D"], "A32": wl[0].meta["A"],
-            "l2": "flushed before every timed step (256 MB write); inputs are L2-sized",
-            "parallelism": "replicas (one independent sweep per GPU)"}
+def state_bytes(wl):
+    return sum(2 * 8 * Q_OF[w.lattice] * w.nodes for w in wl)
+
+
+def config_block(wl, name):
+    c = {"workload": name, "lattices": [w.name for w in wl], "nodes_per_step": sum(w.nodes for w in wl),
+         "seed": W.SEED, "launch": "one batched fused stream+collide kernel per time step",
+         "parallelism": "replicas (one independent copy of the workload per GPU)"}
+    if state_bytes(wl) < 2 * L2_BYTES:
+        c["l2"] = "flushed before every timed step (256 MB write); the state fits in L2"
+    else:
+        c["l2"] = "state larger than L2 (no flush needed)"
+    if wl[0].lattice == W.D2Q5:
+        c["D"] = wl[0].meta["D"]
+        c["A32"] = wl[0].meta["A"]
+    return c
 
 
 def main():
@@ -190,6 +215,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cde_sweep", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile", action="store_true",
@@ -219,16 +245,16 @@ def main():
         dist = dist_mod
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = sweep_workloads()
+    wname, make = WORKLOADS[args.workload]
+    wl = make()
+    need_flush = state_bytes(wl) < 2 * L2_BYTES
     stream = torch.cuda.Stream()
-    lats = [lbm.from_workload(w, stream=stream.cuda_stream) for w in wl]
+    e2e_steps = max(3, min(args.steps, 50))
+    env_steps = args.warmup + args.steps + e2e_steps + 20000  # envelope tables cover every step run here
+    lats = [lbm.from_workload(w, stream=stream.cuda_stream, envelope_steps=env_steps) for w in wl]
+    batch = lbm.Batch(lats)  # one fused step kernel for all lattices of the sweep per time step
     nodes = sum(w.nodes for w in wl)
-    big = max(range(len(wl)), key=lambda i: wl[i].nodes)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def one_step():
-        for L in lats:
-            L.step(1)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -237,10 +263,11 @@ def main():
     t0 = time.perf_counter()
     k = 0
     min_warm_s = 0.0 if args.profile else 1.0
-    while k < args.warmup or time.perf_counter() - t0 < min_warm_s:
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        one_step()
+    while k < args.warmup or (time.perf_counter() - t0 < min_warm_s and k < env_steps - args.steps - e2e_steps - 5):
+        if need_flush:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        batch.step(1)
         k += 1
         if k % 50 == 0:
             stream.synchronize()
@@ -250,23 +277,18 @@ def main():
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    evk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches0 = sum(L.launch_count() for L in lats)
+    launches0 = batch.launch_count() + sum(L.launch_count() for L in lats)
     for s in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if need_flush:
+            with torch.cuda.stream(stream):
+                flush.zero_()
         ev[s][0].record(stream)
-        for i, L in enumerate(lats):
-            if i == big:
-                evk[s][0].record(stream)
-            L.step(1)
-            if i == big:
-                evk[s][1].record(stream)
+        batch.step(1)
         ev[s][1].record(stream)
     torch.cuda.synchronize()
-    launches = sum(L.launch_count() for L in lats) - launches0
+    launches = batch.launch_count() + sum(L.launch_count() for L in lats) - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_ms = [a.elapsed_time(b) for a, b in evk]
+    kern_ms = step_ms  # one launch per step: the batched D2Q5 step kernel
     total_ms = sum(step_ms)
     if dist:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -278,21 +300,23 @@ def main():
 
     value = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
 
-    # roofline of the dominant kernel (the 512^2 lattice's fused step)
+    # roofline of the dominant (only) kernel: the batched D2Q5 step over the sweep
     hbm, hbm_src = load_peaks()
     kavg_s = statistics.mean(kern_ms) * 1e-3
-    nb = wl[big].nodes
-    alg_bytes = nb * 80  # 5 populations read + 5 written, FP64
+    nb = nodes
+    q = Q_OF[wl[0].lattice]
+    alg_bytes = nb * 16 * q  # q populations read + q written, FP64
     achieved_gbs = alg_bytes / kavg_s / 1e9
-    facts = KERNEL_FACTS["d2q5_step"]
+    facts = KERNEL_FACTS.get(args.workload, {})
     traffic = None
-    if facts["traffic_bytes_per_launch_512"] is not None and facts["traffic_src_sha"] == src_hash(facts["src"]):
-        traffic = facts["traffic_bytes_per_launch_512"]
+    if facts.get("traffic_bytes_per_launch") is not None and facts["traffic_src_sha"] == src_hash(facts["src"]):
+        traffic = facts["traffic_bytes_per_launch"]
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-            "frac": achieved_gbs / hbm, "traffic": traffic, "kernel": "d2q5_step (512x512)",
+            "frac": achieved_gbs / hbm, "traffic": traffic, "kernel": f"batched step kernel ({wname})",
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
-            "bytes_per_node": 80, "kernel_us": kavg_s * 1e6}
-    if facts["fp64_flops_per_node"] and FP64_PEAK_TFLOPS:
+            "bytes_per_node": 16 * q, "kernel_us": kavg_s * 1e6}
+    facts = KERNEL_FACTS.get(args.workload, {})
+    if facts.get("fp64_flops_per_node") and FP64_PEAK_TFLOPS:
         tf = facts["fp64_flops_per_node"] * nb / kavg_s / 1e12
         roof["fp64"] = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
                         "peak_source": FP64_PEAK_NOTE}
@@ -310,29 +334,38 @@ def main():
         pinned_src = []
         pinned_phi = []
         for w in wl:
-            full = np.ascontiguousarray(
-                (np.asarray(w.tables[0][0])[None, :] * np.asarray(w.tables[0][1])[:, None]).reshape(1, -1))
+            from_tables = [((np.asarray(px)[None, None, :] * np.asarray(py)[None, :, None]) * np.asarray(pz)[:, None, None])
+                           for px, py, pz in w.tables]
+            full = np.ascontiguousarray(np.stack([np.broadcast_to(t, w.shape[::-1]).reshape(-1) for t in from_tables]))
             t_src = torch.empty(full.shape, dtype=torch.float64, pin_memory=True)
             t_src.numpy()[:] = full
             pinned_src.append(t_src)
-            pinned_phi.append(torch.empty(w.nodes, dtype=torch.float64, pin_memory=True))
-        ke = max(3, min(args.steps, 50))
+            pinned_phi.append(torch.empty(w.nodes * (1 if w.lattice == W.D2Q5 else 4), dtype=torch.float64,
+                                          pin_memory=True))
+        ke = e2e_steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            for L, s_, p_ in zip(lats, pinned_src, pinned_phi):
-                L.set_source(full=s_.numpy())
-                L.step(1)
+            for L, s_ in zip(lats, pinned_src):
+                if L.lattice == lbm.D2Q5_CDE:
+                    L.set_source(full=s_.numpy())
+                else:
+                    L.set_force(full=s_.numpy())
+            batch.step(1)
+            for L, p_ in zip(lats, pinned_phi):
                 L._check(L._L.lbm_moments(L.h, p_.data_ptr(), None, 0, 1))
         el = time.perf_counter() - t0
-        e2e = {"value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nodes * 8,
-               "d2h_bytes_per_step": nodes * 8, "steps": ke,
-               "path": "lbm_set_source(host, full field) + lbm_step(1) + lbm_moments(host) per lattice"}
+        ncomp = 1 if wl[0].lattice == W.D2Q5 else (3 if wl[0].lattice == W.D3Q27 else 2)
+        nout = 1 if wl[0].lattice == W.D2Q5 else 1 + ncomp
+        e2e = {"value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nodes * 8 * ncomp,
+               "d2h_bytes_per_step": nodes * 8 * nout, "steps": ke,
+               "path": "per step: lbm_set_source/lbm_set_force(host, full field) per lattice, lbm_batch_step(1), "
+                       "lbm_moments(host) per lattice"}
     except Exception as exc:  # pragma: no cover - reported, not hidden
         e2e = {"value": None, "error": repr(exc)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and state_bytes(wl) < (1 << 30):
         upd, sec, threads, done = time_oracle(wl, None, budget_s=args.cpu_budget)
         cpu = {"value": upd / sec / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": f"{done} steps of the whole sweep ({upd} node updates, {sec:.1f} s)"}
@@ -342,7 +375,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_block(wl), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "config": config_block(wl, wname), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

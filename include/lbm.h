@@ -149,8 +149,15 @@ int lbm_set_source(lbm_ctx *ctx, const lbm_field *shape);
  * Errors: LBM_EINVAL (flow lattice), LBM_ECUDA. */
 int lbm_set_velocity(lbm_ctx *ctx, const lbm_field *u);
 
-/* Time envelope of the force or source (NULL fn = a(t) = 1). */
+/* Time envelope of the force or source as a host callback (NULL fn = a(t) = 1).
+ * Replaces any envelope table. */
 int lbm_set_envelope(lbm_ctx *ctx, lbm_envelope_fn fn, void *user);
+
+/* Time envelope as a table of count >= 3 samples a[k] = a(t0 + k/2) (copied),
+ * used instead of a callback; steps outside the table fail with LBM_EINVAL
+ * (stepping from t needs samples up to t + n + 1).  count = 0 with a = NULL
+ * removes the table.  Same trapezoid averages as lbm_set_envelope. */
+int lbm_set_envelope_table(lbm_ctx *ctx, const double *a, long count, double t0);
 
 /* Advance n >= 0 time steps (n = 0 is a no-op).  Each step is one fused
  * kernel launch: stream (Eq. 22b / 40b, pull form, with periodic wrap or
@@ -219,6 +226,36 @@ int lbm_sync(lbm_ctx *ctx);
 /* Number of kernel launches issued by this context since its creation
  * (every step, initialisation, moments, reduction and copy kernel counts). */
 int lbm_launch_count(const lbm_ctx *ctx, long long *count);
+
+/* ---- Batches: many lattices, one kernel launch per time step ------------
+ *
+ * A batch groups contexts of the same lattice and storage that share one
+ * stream and device (e.g. the members of a parameter sweep).  lbm_batch_step
+ * advances all of them together: each time step is a single kernel launch
+ * over the blocks of every member, each member keeping its own geometry,
+ * relaxation rates, force/source/velocity shape, envelope and step counter.
+ * The result is bit-for-bit that of calling lbm_step on each member.  The
+ * batch keeps pointers to the contexts (they must outlive it) and owns only
+ * its own descriptor buffers. */
+typedef struct lbm_batch lbm_batch;
+
+/* Errors: LBM_EINVAL (count < 1, NULL or repeated context, members differing
+ * in lattice, storage, stream or device), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count);
+
+/* Advance every member by n >= 0 steps (asynchronous on the members' stream).
+ * Errors: LBM_ESTATE (a member not initialised), LBM_EINVAL (n < 0, envelope
+ * table too short), LBM_ECUDA. */
+int lbm_batch_step(lbm_batch *b, long n);
+
+/* Kernel launches issued by lbm_batch_step so far (one per step). */
+int lbm_batch_launch_count(const lbm_batch *b, long long *count);
+
+/* Message of the last failure on b (NULL: the last lbm_batch_create failure). */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Free the batch (synchronises its stream); the member contexts stay valid. */
+void lbm_batch_destroy(lbm_batch *b);
 
 #ifdef __cplusplus
 }

@@ -298,6 +298,30 @@ cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap
     });
 }
 
+void d2q9_batch_coef(const double omega[9], BatchItem &item);
+void d2q5_batch_coef(const double omega[9], BatchItem &item);
+void d3q27_batch_coef(const double omega[9], BatchItem &item);
+cudaError_t d2q9_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
+cudaError_t d2q5_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
+cudaError_t d3q27_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
+
+void batch_coef(int lattice, const double omega[9], BatchItem &item)
+{
+    if (lattice == LD2Q9::ID) d2q9_batch_coef(omega, item);
+    else if (lattice == LD2Q5::ID) d2q5_batch_coef(omega, item);
+    else d3q27_batch_coef(omega, item);
+}
+
+cudaError_t batch_step(int lattice, const BatchItem *items, const int *first_block, int count, int nblocks,
+                       const double2 *pairs, int k, cudaStream_t s)
+{
+    if (lattice == LD2Q9::ID) return d2q9_batch_step(items, first_block, count, nblocks, pairs, k, s);
+    if (lattice == LD2Q5::ID) return d2q5_batch_step(items, first_block, count, nblocks, pairs, k, s);
+    return d3q27_batch_step(items, first_block, count, nblocks, pairs, k, s);
+}
+
+int batch_blocks(const Geom &g) { return (g.N + kBlock - 1) / kBlock; }
+
 cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out)
 {
     return by_lattice(lattice, [&](auto L) {

@@ -50,6 +50,77 @@ __device__ __forceinline__ void collide(double (&g)[5], double S, double H0, dou
     g[4] += c - h2 - h4;
 }
 
+// With a uniform advecting velocity, Eq. 41 is linear in (phi, kx, ky,
+// kxx + kyy, kxx - kyy) with coefficients fixed for the whole launch; they are
+// formed once on the host (Coef5) and the node update needs ~35 FP64
+// operations instead of ~48.  Same values as `collide` up to rounding.
+struct Coef5 {
+    double A1, c1, A2, c2;      // h1 = A1 phi - c1 kx,  h2 = A2 phi - c2 ky
+    double P3, X3, Y3, S3;      // h3 = P3 phi + X3 kx + Y3 ky + S3 (kxx + kyy)
+    double P4, X4, Y4, D4;      // h4 = P4 phi + X4 kx + Y4 ky + D4 (kxx - kyy)
+};
+
+Coef5 make_coef(const Rates5 &w, double ux, double uy)
+{
+    Coef5 k;
+    const double ux2 = ux * ux, uy2 = uy * uy;
+    k.A1 = w.c1 * ux;
+    k.c1 = w.c1;
+    k.A2 = w.c2 * uy;
+    k.c2 = w.c2;
+    // h3 = c3[(2/3) phi - S + 2(ux kx + uy ky) - (ux^2 + uy^2) phi] + ux h1 + uy h2
+    k.P3 = w.c3 * ((2.0 / 3.0) - ux2 - uy2) + w.c1 * ux2 + w.c2 * uy2;
+    k.X3 = ux * (2.0 * w.c3 - w.c1);
+    k.Y3 = uy * (2.0 * w.c3 - w.c2);
+    k.S3 = -w.c3;
+    // h4 = c4[-D + 2(ux kx - uy ky) - (ux^2 - uy^2) phi] + ux h1 - uy h2
+    k.P4 = -w.c4 * (ux2 - uy2) + w.c1 * ux2 - w.c2 * uy2;
+    k.X4 = ux * (2.0 * w.c4 - w.c1);
+    k.Y4 = uy * (w.c2 - 2.0 * w.c4);
+    k.D4 = -w.c4;
+    return k;
+}
+
+__device__ __forceinline__ void collide_uniform(double (&g)[5], double S, double H0, const Coef5 &k)
+{
+    const double kx = g[1] - g[3], ky = g[2] - g[4];
+    const double kxx = g[1] + g[3], kyy = g[2] + g[4];
+    const double Sg = kxx + kyy, Dg = kxx - kyy;
+    const double phi = fma(0.5, S, g[0] + Sg);  // Eqs. 42-43
+    const double h1 = fma(k.A1, phi, -k.c1 * kx);
+    const double h2 = fma(k.A2, phi, -k.c2 * ky);
+    const double h3 = fma(k.P3, phi, fma(k.X3, kx, fma(k.Y3, ky, k.S3 * Sg)));
+    const double h4 = fma(k.P4, phi, fma(k.X4, kx, fma(k.Y4, ky, k.D4 * Dg)));
+    const double c = H0 + h3;  // Eq. 48
+    const double e1 = c + h4, e2 = c - h4;
+    g[0] += fma(-4.0, h3, H0);
+    g[1] += e1 + h1;
+    g[2] += e2 + h2;
+    g[3] += e1 - h1;
+    g[4] += e2 - h2;
+}
+
+template <int SK>
+__global__ void __launch_bounds__(kBlock)
+k_step_uniform(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, double apre,
+               double hsum, Coef5 k)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int x = i % g.nx, y = i / g.nx;
+    double f[5];
+    load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
+    double Spre = 0.0, H0 = 0.0;
+    if (SK != FK_NONE) {
+        const double P = field_value(S, SK, 0, x, y, 0, i);
+        Spre = apre * P;
+        H0 = hsum * P;
+    }
+    collide_uniform(f, Spre, H0, k);
+#pragma unroll
+    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
+}
+
 template <int SK, int VK>
 __global__ void __launch_bounds__(kBlock)
 k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, FieldDev V,
@@ -79,14 +150,72 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
 template <int SK>
 void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
 {
-    switch (a.vkind) {
-    case FK_NONE: k_step<SK, FK_NONE><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w); break;
-    case FK_CONST: k_step<SK, FK_CONST><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w); break;
-    default: k_step<SK, FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w); break;
+    if (a.vkind != FK_GENERAL) {
+        const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0;
+        const double uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
+        k_step_uniform<SK><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, hsum,
+                                                           make_coef(w, ux, uy));
+        return;
     }
+    k_step<SK, FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w);
+}
+
+// Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
+// coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5.
+__global__ void __launch_bounds__(kBlock)
+k_batch(const BatchItem *__restrict__ items, const int *__restrict__ first, int count,
+        const double2 *__restrict__ pairs, int k)
+{
+    const int it = batch_find(first, count);
+    const BatchItem &B = items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const double *fin = B.buf[(B.parity + k) & 1];
+    double *fout = B.buf[(B.parity + k + 1) & 1];
+    const double2 ap = pairs[(size_t)k * count + it];
+    const int x = i % g.nx, y = i / g.nx;
+    double f[5];
+    load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
+    double Spre = 0.0, H0 = 0.0;
+    if (B.fkind != FK_NONE) {
+        const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
+        Spre = ap.x * P;
+        H0 = ap.y * P;
+    }
+    if (B.vkind != FK_GENERAL) {
+        const Coef5 c{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5],
+                      B.coef[6], B.coef[7], B.coef[8], B.coef[9], B.coef[10], B.coef[11]};
+        collide_uniform(f, Spre, H0, c);
+    } else {
+        const Rates5 w{B.coef[12], B.coef[13], B.coef[14], B.coef[15]};
+        const double ux = field_value(B.V, FK_GENERAL, 0, x, y, 0, i);
+        const double uy = field_value(B.V, FK_GENERAL, 1, x, y, 0, i);
+        collide(f, Spre, H0, ux, uy, w);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
 }
 
 }  // namespace
+
+void d2q5_batch_coef(const double omega[9], BatchItem &item)
+{
+    const Rates5 w{omega[1] / 2.0, omega[2] / 2.0, omega[3] / 4.0, omega[4] / 4.0};
+    const double ux = item.vkind == FK_CONST ? item.V.cval[0] : 0.0;
+    const double uy = item.vkind == FK_CONST ? item.V.cval[1] : 0.0;
+    const Coef5 c = make_coef(w, ux, uy);
+    const double v[16] = {c.A1, c.c1, c.A2, c.c2, c.P3, c.X3, c.Y3, c.S3,
+                          c.P4, c.X4, c.Y4, c.D4, w.c1, w.c2, w.c3, w.c4};
+    for (int k = 0; k < 16; k++) item.coef[k] = v[k];
+}
+
+cudaError_t d2q5_batch_step(const BatchItem *items, const int *first, int count, int nblocks,
+                            const double2 *pairs, int k, cudaStream_t s)
+{
+    k_batch<<<nblocks, kBlock, 0, s>>>(items, first, count, pairs, k);
+    return cudaGetLastError();
+}
 
 cudaError_t d2q5_step(const LaunchArgs &a)
 {

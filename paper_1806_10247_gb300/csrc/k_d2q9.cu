@@ -88,7 +88,53 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
 }
 
+// Batched form: one launch for every lattice of a batch; pairs hold
+// (a_pre, (a_pre + a_post)/12) per step and item.
+__global__ void __launch_bounds__(kBlock)
+k_batch(const BatchItem *__restrict__ items, const int *__restrict__ first, int count,
+        const double2 *__restrict__ pairs, int k)
+{
+    const int it = batch_find(first, count);
+    const BatchItem &B = items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const double *fin = B.buf[(B.parity + k) & 1];
+    double *fout = B.buf[(B.parity + k + 1) & 1];
+    const double2 ap = pairs[(size_t)k * count + it];
+    const int x = i % g.nx, y = i / g.nx;
+    double f[9];
+    load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
+    double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
+    const int fk = B.fkind;
+    if (fk != FK_NONE) {
+        const double Px = field_value(B.F, fk, 0, x, y, 0, i), Py = field_value(B.F, fk, 1, x, y, 0, i);
+        Fx = ap.x * Px;
+        Fy = ap.x * Py;
+        Gx = ap.y * Px;
+        Gy = ap.y * Py;
+    }
+    const Rates9 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
+    collide(f, Fx, Fy, Gx, Gy, w);
+#pragma unroll
+    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
+}
+
 }  // namespace
+
+void d2q9_batch_coef(const double omega[9], BatchItem &item)
+{
+    const double c[6] = {omega[3] / 12.0, omega[4] / 4.0, omega[5] / 4.0,
+                         omega[6] / 4.0, omega[7] / 4.0, omega[8] / 4.0};
+    for (int k = 0; k < 6; k++) item.coef[k] = c[k];
+}
+
+cudaError_t d2q9_batch_step(const BatchItem *items, const int *first, int count, int nblocks,
+                            const double2 *pairs, int k, cudaStream_t s)
+{
+    k_batch<<<nblocks, kBlock, 0, s>>>(items, first, count, pairs, k);
+    return cudaGetLastError();
+}
 
 cudaError_t d2q9_step(const LaunchArgs &a)
 {

@@ -169,7 +169,51 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
 }
 
+// Batched form; pairs hold (a_pre, a_post) per step and item.
+__global__ void __launch_bounds__(kBlock)
+k_batch(const BatchItem *__restrict__ items, const int *__restrict__ first, int count,
+        const double2 *__restrict__ pairs, int k)
+{
+    const int it = batch_find(first, count);
+    const BatchItem &B = items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const double *fin = B.buf[(B.parity + k) & 1];
+    double *fout = B.buf[(B.parity + k + 1) & 1];
+    const double2 ap = pairs[(size_t)k * count + it];
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double m[27];
+    load_pulled<LD3Q27>(fin, g, x, y, z, i, m);
+    double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
+    if (B.fkind != FK_NONE) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double P = field_value(B.F, B.fkind, d, x, y, z, i);
+            F[d] = ap.x * P;
+            Fq[d] = ap.y * P;
+        }
+    }
+    const Rates27 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
+    collide(m, F, Fq, w);
+#pragma unroll
+    for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
+}
+
 }  // namespace
+
+void d3q27_batch_coef(const double omega[9], BatchItem &item)
+{
+    for (int k = 0; k < 6; k++) item.coef[k] = omega[k + 1];
+}
+
+cudaError_t d3q27_batch_step(const BatchItem *items, const int *first, int count, int nblocks,
+                             const double2 *pairs, int k, cudaStream_t s)
+{
+    k_batch<<<nblocks, kBlock, 0, s>>>(items, first, count, pairs, k);
+    return cudaGetLastError();
+}
 
 cudaError_t d3q27_step(const LaunchArgs &a)
 {

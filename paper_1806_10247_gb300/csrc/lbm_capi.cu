@@ -55,15 +55,35 @@ bool omega_used(int lattice, int k)
 
 void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost)
 {
-    if (!c->env) {
+    double a0, ah, a1;
+    const double tt = (double)t;
+    if (!c->env_tab.empty()) {
+        // table entries at half-integer times; lbm_step checks the range first
+        long k = (long)((tt - c->env_t0) * 2.0);
+        const long last = (long)c->env_tab.size() - 1;
+        if (k < 0) k = 0;
+        if (k + 2 > last) k = last - 2;
+        a0 = c->env_tab[k];
+        ah = c->env_tab[k + 1];
+        a1 = c->env_tab[k + 2];
+    } else if (c->env) {
+        a0 = c->env(tt, c->env_user);
+        ah = c->env(tt + 0.5, c->env_user);
+        a1 = c->env(tt + 1.0, c->env_user);
+    } else {
         apre = apost = 1.0;
         return;
     }
-    const double tt = (double)t;
-    const double a0 = c->env(tt, c->env_user), ah = c->env(tt + 0.5, c->env_user),
-                 a1 = c->env(tt + 1.0, c->env_user);
     apre = 0.5 * (a0 + ah);
     apost = 0.5 * (ah + a1);
+}
+
+// Whether the envelope can be evaluated for steps t .. t+n-1 (and the moments at t+n).
+bool envelope_covers(const lbm_ctx *c, long t, long n)
+{
+    if (c->env_tab.empty()) return true;
+    const double first = c->env_t0, last = c->env_t0 + 0.5 * (double)(c->env_tab.size() - 1);
+    return (double)t >= first && (double)(t + n) + 1.0 <= last;
 }
 
 LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost)
@@ -121,6 +141,24 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
         nf.d.sep = 1;
         nf.d.cstride = (long long)per;
         for (int d = 0; d < 3; d++) nf.d.len[d] = f->len[d];
+        // Components whose product is identically zero, and axes whose table
+        // is exactly 1.0 for every other component, are skipped by the kernels.
+        nf.d.zmask = 0;
+        for (int cc = 0; cc < ncomp; cc++) {
+            const double *t = f->data + cc * per;
+            for (int d = 0, off = 0; d < 3; off += f->len[d], d++) {
+                bool allzero = true;
+                for (int k = 0; k < f->len[d]; k++) allzero = allzero && t[off + k] == 0.0;
+                if (allzero) nf.d.zmask |= 1 << cc;
+            }
+        }
+        nf.d.axes = 0;
+        for (int d = 0, off = 0; d < 3; off += f->len[d], d++) {
+            bool one = f->len[d] == 1;
+            for (int cc = 0; cc < ncomp && one; cc++)
+                if (!((nf.d.zmask >> cc) & 1)) one = f->data[cc * per + off] == 1.0;
+            if (!one) nf.d.axes |= 1 << d;
+        }
     } else if (f->kind == LBM_FIELD_FULL) {
         count = (size_t)c->g.N * ncomp;
         nf.d.sep = 0;
@@ -297,6 +335,23 @@ int lbm_set_envelope(lbm_ctx *c, lbm_envelope_fn fn, void *user)
     if (!c) return LBM_EINVAL;
     c->env = fn;
     c->env_user = user;
+    c->env_tab.clear();
+    return LBM_OK;
+}
+
+int lbm_set_envelope_table(lbm_ctx *c, const double *a, long count, double t0)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (a == nullptr && count == 0) {
+        c->env_tab.clear();
+        return LBM_OK;
+    }
+    if (a == nullptr || count < 3) return fail(c, LBM_EINVAL, "lbm_set_envelope_table: need at least 3 values");
+    c->env_tab.assign(a, a + count);
+    c->env_t0 = t0;
+    c->env = nullptr;
+    c->env_user = nullptr;
     return LBM_OK;
 }
 
@@ -306,6 +361,8 @@ int lbm_step(lbm_ctx *c, long n)
     c->err.clear();
     if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n < 0");
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step: populations not initialised");
+    if (!envelope_covers(c, c->t, n))
+        return fail(c, LBM_EINVAL, "lbm_step: steps %ld..%ld are outside the envelope table", c->t, c->t + n);
     for (long k = 0; k < n; k++) {
         double apre, apost;
         envelope_pair(c, c->t, apre, apost);

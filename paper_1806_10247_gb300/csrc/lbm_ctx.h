@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
@@ -31,6 +32,8 @@ struct lbm_ctx {
     lbmc::DeviceField vel;    // advecting velocity (scalar)
     lbm_envelope_fn env = nullptr;
     void *env_user = nullptr;
+    std::vector<double> env_tab;  // a(env_t0 + k/2), k = 0..size-1 (used when non-empty)
+    double env_t0 = 0.0;
     long t = 0;
     bool initialised = false;
     double *snap = nullptr;
@@ -49,6 +52,7 @@ int fail(lbm_ctx *c, int code, const char *fmt, ...);
 int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what);
 // Envelope averages (a_pre, a_post) of step t (trapezoid rule of Sec. 6.3).
 void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost);
+bool envelope_covers(const lbm_ctx *c, long t, long n);
 // Launch arguments of the context's kernels.
 lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
 

@@ -24,11 +24,17 @@ enum FieldKind { FK_NONE = 0, FK_CONST = 1, FK_GENERAL = 2 };
 // either separable tables (sep = 1: for component c, px at data + c*cstride,
 // then py, then pz, with lengths len[0..2], 1 meaning constant on that axis)
 // or a full field (sep = 0: data[c*cstride + node]).
+// zmask: bit c set = component c is identically zero.  axes (separable only):
+// bit d set = the axis-d table takes part in the product; a table that is the
+// single value 1.0 for every non-zero component is left out (multiplying by
+// 1.0 is exact, so the value is unchanged).
 struct FieldDev {
     const double *data;
     long long cstride;
     int len[3];
     int sep;
+    int zmask;
+    int axes;
     double cval[3];
 };
 
@@ -36,12 +42,26 @@ __device__ __forceinline__ double field_value(const FieldDev &F, int kind, int c
                                               int node)
 {
     if (kind == FK_CONST) return F.cval[c];
+    if ((F.zmask >> c) & 1) return 0.0;
     const double *t = F.data + c * F.cstride;
     if (!F.sep) return __ldg(t + node);
-    double px = __ldg(t + (F.len[0] > 1 ? x : 0));
-    double py = __ldg(t + F.len[0] + (F.len[1] > 1 ? y : 0));
-    double pz = __ldg(t + F.len[0] + F.len[1] + (F.len[2] > 1 ? z : 0));
-    return (px * py) * pz;  // the documented evaluation order of a separable shape
+    // (px * py) * pz, the documented evaluation order, skipping exact-1 tables
+    double v = 1.0;
+    bool have = false;
+    if (F.axes & 1) {
+        v = __ldg(t + (F.len[0] > 1 ? x : 0));
+        have = true;
+    }
+    if (F.axes & 2) {
+        const double py = __ldg(t + F.len[0] + (F.len[1] > 1 ? y : 0));
+        v = have ? v * py : py;
+        have = true;
+    }
+    if (F.axes & 4) {
+        const double pz = __ldg(t + F.len[0] + F.len[1] + (F.len[2] > 1 ? z : 0));
+        v = have ? v * pz : pz;
+    }
+    return v;
 }
 
 }  // namespace lbmk

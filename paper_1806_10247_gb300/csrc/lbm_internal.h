@@ -25,6 +25,28 @@ struct LaunchArgs {
 // Relaxation rates are validated on the host; omega_high_one records whether
 // every rate of order >= 3 equals 1 (enables the reduced collision).
 
+// One lattice of a batch (lbm_batch_step): everything a batched step kernel
+// needs for it.  Step k of a launch sequence reads buf[(parity + k) & 1] and
+// writes buf[(parity + k + 1) & 1]; its envelope pair is pairs[k * count + item].
+struct BatchItem {
+    Geom g;
+    double *buf[2];
+    int parity;
+    int fkind, vkind;
+    FieldDev F, V;
+    double coef[16];  // lattice-specific collision coefficients (filled by batch_coef)
+};
+
+// Host: fill item.coef from the relaxation rates (and, for the scalar lattice
+// with a uniform advecting velocity, that velocity).
+void batch_coef(int lattice, const double omega[9], BatchItem &item);
+
+// One launch advancing every item of a batch by one step (step index k).
+// first_block[i] = first block of item i (ascending); nblocks = total blocks.
+cudaError_t batch_step(int lattice, const BatchItem *items, const int *first_block, int count, int nblocks,
+                       const double2 *pairs, int k, cudaStream_t s);
+int batch_blocks(const Geom &g);
+
 // One fused stream + collide step (pull form): fin -> fout.
 cudaError_t d2q9_step(const LaunchArgs &a);
 cudaError_t d2q5_step(const LaunchArgs &a);

@@ -93,6 +93,20 @@ __device__ __forceinline__ void zeroth_first(const double (&f)[L::Q], double &m0
     }
 }
 
+// Item of a batched launch that owns this block: the last i with
+// first_block[i] <= blockIdx.x (first_block ascending, first_block[0] = 0).
+__device__ __forceinline__ int batch_find(const int *__restrict__ first_block, int count)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first_block + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ void node_xyz(const Geom &g, int i, int &x, int &y, int &z)
 {
     x = i % g.nx;

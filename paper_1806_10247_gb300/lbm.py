@@ -29,7 +29,8 @@ DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2}
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium", "lbm_set_force",
            "lbm_set_source", "lbm_set_velocity", "lbm_set_envelope", "lbm_step", "lbm_moments",
            "lbm_reduce", "lbm_get_populations", "lbm_set_populations", "lbm_get_step", "lbm_sync",
-           "lbm_launch_count", "lbm_reduce_sums_noalloc")
+           "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
+           "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
 class LBMError(RuntimeError):
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True):
     L.lbm_set_source.argtypes = [vp, ctypes.POINTER(_Field)]
     L.lbm_set_velocity.argtypes = [vp, ctypes.POINTER(_Field)]
     L.lbm_set_envelope.argtypes = [vp, ENVELOPE, vp]
+    L.lbm_set_envelope_table.argtypes = [vp, dp, ctypes.c_long, ctypes.c_double]
     L.lbm_step.argtypes = [vp, ctypes.c_long]
     L.lbm_moments.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_reduce.argtypes = [vp, dp]
@@ -91,8 +93,15 @@ def load(build_if_missing: bool = True):
     L.lbm_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
     L.lbm_sync.argtypes = [vp]
     L.lbm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ip]
+    L.lbm_batch_step.argtypes = [vp, ctypes.c_long]
+    L.lbm_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_batch_last_error.argtypes = [vp]
+    L.lbm_batch_last_error.restype = ctypes.c_char_p
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lbm_destroy", "lbm_last_error"):
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_batch_last_error", "lbm_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -222,8 +231,16 @@ class Lattice:
         f, keep = _field(tables, full)
         self._check(self._L.lbm_set_velocity(self.h, ctypes.byref(f)))
 
-    def set_envelope(self, fn):
-        """fn(t) -> a(t), or None for a == 1."""
+    def set_envelope(self, fn, steps=None):
+        """fn(t) -> a(t), or None for a == 1.  With ``steps``, fn is tabulated
+        once at half-integer times for the next ``steps`` steps (no callbacks
+        while stepping); otherwise the library calls fn back every step."""
+        if fn is not None and steps is not None:
+            t0 = self.t
+            tab = np.array([float(fn(t0 + 0.5 * k)) for k in range(2 * int(steps) + 3)])
+            self._env = None
+            self._check(self._L.lbm_set_envelope_table(self.h, _dp(tab), len(tab), float(t0)))
+            return
         if fn is None:
             self._env = None
             self._check(self._L.lbm_set_envelope(self.h, ENVELOPE(), None))
@@ -292,7 +309,46 @@ class Lattice:
         return v.value
 
 
-def from_workload(w, stream=None) -> Lattice:
+class Batch:
+    """Lattices of one kind stepped together, one kernel launch per step
+    (``lbm_batch_*``).  The member :class:`Lattice` objects must stay alive."""
+
+    def __init__(self, lattices):
+        L = load()
+        self._L = L
+        self.members = list(lattices)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.h.value for m in self.members])
+        h = ctypes.c_void_p()
+        rc = L.lbm_batch_create(ctypes.byref(h), arr, len(self.members))
+        if rc != OK:
+            raise LBMError(rc, L.lbm_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LBMError(rc, self._L.lbm_batch_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._check(self._L.lbm_batch_step(self.h, int(n)))
+
+    def launch_count(self):
+        v = ctypes.c_longlong()
+        self._check(self._L.lbm_batch_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._L.lbm_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_workload(w, stream=None, envelope_steps=None) -> Lattice:
     """Lattice set up (force/source, velocity, envelope, equilibrium) from a
     :class:`paper_1806_10247_gb300.workloads.Workload`."""
     lat = {1: D2Q9, 2: D3Q27, 3: D2Q5_CDE}[w.lattice]
@@ -307,6 +363,6 @@ def from_workload(w, stream=None) -> Lattice:
         L.set_velocity(tables=[(np.array([u[0]]), np.array([1.0]), np.array([1.0])),
                                (np.array([u[1]]), np.array([1.0]), np.array([1.0]))])
     if w.envelope is not None:
-        L.set_envelope(w.envelope)
+        L.set_envelope(w.envelope, steps=envelope_steps)
     L.init_equilibrium(w.rho0, w.u0)
     return L

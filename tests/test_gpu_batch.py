@@ -1,0 +1,102 @@
+"""Batched stepping (one launch per step for many lattices): bit-identical to
+stepping each member alone, and within the parity bar of the oracle; envelope
+tables equal envelope callbacks."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1806_10247_gb300 import lbm
+from paper_1806_10247_gb300 import workloads as W
+from tests.gpu_helpers import compare_state, oracle_from_workload
+from tests.test_gpu_parity import _random_workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(kind):
+    if kind == "d2q5":
+        ws = [W.cde_workload(c) for c in W.cde_sweep_params(sizes=(32, 48, 64, 100))]
+        w, full = _random_workload(W.D2Q5, (37, 21, 1), (1, 1, 0), seed=4, kind="full")
+        ws.append(w)
+        fulls = [None] * 4 + [full]
+    elif kind == "d2q9":
+        ws = [W.poiseuille(ny=n) for n in (9, 33, 65)]
+        w, full = _random_workload(W.D2Q9, (29, 17, 1), (0, 0, 0), seed=5, kind="full")
+        w2, _ = _random_workload(W.D2Q9, (40, 7, 1), (1, 0, 0), seed=6)
+        ws += [w, w2]
+        fulls = [None, None, None, full, None]
+    else:
+        ws = [W.kolmogorov(shape=(12, 10, 8)), W.duct(n=9, nx=4)]
+        w, full = _random_workload(W.D3Q27, (7, 6, 5), (1, 1, 1), seed=8, kind="full")
+        ws.append(w)
+        fulls = [None, None, full]
+    return ws, fulls
+
+
+def _make(w, full, envelope_steps=None):
+    G = lbm.from_workload(w, envelope_steps=envelope_steps)
+    if full is not None:
+        if w.lattice == W.D2Q5:
+            G.set_source(full=full)
+        else:
+            G.set_force(full=full)
+    return G
+
+
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+def test_batch_equals_individual_steps_bitwise(kind):
+    ws, fulls = _members(kind)
+    solo = [_make(w, f) for w, f in zip(ws, fulls)]
+    grouped = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(grouped)
+    for n in (1, 2, 5):
+        B.step(n)
+        for G in solo:
+            G.step(n)
+    assert B.launch_count() == 8
+    for a, b in zip(solo, grouped):
+        assert a.t == b.t == 8
+        assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+def test_batch_matches_oracle(kind):
+    ws, fulls = _members(kind)
+    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(Gs)
+    B.step(13)
+    for w, f, G in zip(ws, fulls, Gs):
+        R = oracle_from_workload(w)
+        if f is not None:
+            R.P = np.ascontiguousarray(f)
+        R.run(13)
+        compare_state(G, R)
+
+
+def test_envelope_table_equals_callback():
+    c = W.cde_sweep_params(sizes=(64,))[0]
+    w = W.cde_workload(c)
+    a = lbm.from_workload(w)
+    b = lbm.from_workload(w, envelope_steps=40)
+    a.step(25)
+    b.step(25)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert np.array_equal(a.moments(), b.moments())
+    with pytest.raises(lbm.LBMError) as e:
+        b.step(30)  # beyond the 40-step table
+    assert e.value.code == lbm.EINVAL
+
+
+def test_batch_rejects_mixed_lattices_and_uninitialised_members():
+    a = lbm.from_workload(W.poiseuille(ny=9))
+    b = lbm.from_workload(W.cde_workload(W.cde_sweep_params(sizes=(32,))[0]))
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([a, b])
+    with pytest.raises(lbm.LBMError):
+        lbm.Batch([a, a])
+    c = lbm.Lattice(lbm.D2Q9, (4, 4, 1), W.d2q9_omega(0.8))
+    B = lbm.Batch([a, c])
+    with pytest.raises(lbm.LBMError) as e:
+        B.step(1)
+    assert e.value.code == lbm.ESTATE
