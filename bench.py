@@ -191,15 +191,15 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def state_bytes(wl):
-    return sum(2 * 8 * Q_OF[w.lattice] * w.nodes for w in wl)
+def state_bytes(wl, elem=8):
+    return sum(2 * elem * Q_OF[w.lattice] * w.nodes for w in wl)
 
 
-def config_block(wl, name):
-    c = {"workload": name, "lattices": [w.name for w in wl], "nodes_per_step": sum(w.nodes for w in wl),
+def config_block(wl, name, storage="fp64", elem=8):
+    c = {"workload": name, "storage": storage, "lattices": [w.name for w in wl], "nodes_per_step": sum(w.nodes for w in wl),
          "seed": W.SEED, "launch": "one batched fused stream+collide kernel per time step",
          "parallelism": "replicas (one independent copy of the workload per GPU)"}
-    if state_bytes(wl) < 2 * L2_BYTES:
+    if state_bytes(wl, elem) < 2 * L2_BYTES:
         c["l2"] = "flushed before every timed step (256 MB write); the state fits in L2"
     else:
         c["l2"] = "state larger than L2 (no flush needed)"
@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="cde_sweep", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"],
+                    help="population storage: fp64, or fp32/fp16/bf16 deviations with FP32 arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile", action="store_true",
@@ -247,12 +249,15 @@ def main():
 
     wname, make = WORKLOADS[args.workload]
     wl = make()
-    need_flush = state_bytes(wl) < 2 * L2_BYTES
+    need_flush = True  # refined below once the storage size is known
     stream = torch.cuda.Stream()
     e2e_steps = max(3, min(args.steps, 50))
     env_steps = args.warmup + args.steps + e2e_steps + 20000  # envelope tables cover every step run here
-    lats = [lbm.from_workload(w, stream=stream.cuda_stream, envelope_steps=env_steps) for w in wl]
+    storage = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}[args.storage]
+    elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[args.storage]
+    lats = [lbm.from_workload(w, stream=stream.cuda_stream, envelope_steps=env_steps, storage=storage) for w in wl]
     batch = lbm.Batch(lats)  # one fused step kernel for all lattices of the sweep per time step
+    need_flush = state_bytes(wl, elem) < 2 * L2_BYTES
     nodes = sum(w.nodes for w in wl)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -305,7 +310,7 @@ def main():
     kavg_s = statistics.mean(kern_ms) * 1e-3
     nb = nodes
     q = Q_OF[wl[0].lattice]
-    alg_bytes = nb * 16 * q  # q populations read + q written, FP64
+    alg_bytes = nb * 2 * elem * q  # q populations read + q written
     achieved_gbs = alg_bytes / kavg_s / 1e9
     facts = KERNEL_FACTS.get(args.workload, {})
     traffic = None
@@ -314,7 +319,7 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
             "frac": achieved_gbs / hbm, "traffic": traffic, "kernel": f"batched step kernel ({wname})",
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
-            "bytes_per_node": 16 * q, "kernel_us": kavg_s * 1e6}
+            "bytes_per_node": 2 * elem * q, "kernel_us": kavg_s * 1e6}
     facts = KERNEL_FACTS.get(args.workload, {})
     if facts.get("fp64_flops_per_node") and FP64_PEAK_TFLOPS:
         tf = facts["fp64_flops_per_node"] * nb / kavg_s / 1e12
@@ -365,7 +370,7 @@ def main():
         e2e = {"value": None, "error": repr(exc)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and state_bytes(wl) < (1 << 30):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and state_bytes(wl) < (1 << 30):  # FP64 oracle
         upd, sec, threads, done = time_oracle(wl, None, budget_s=args.cpu_budget)
         cpu = {"value": upd / sec / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": f"{done} steps of the whole sweep ({upd} node updates, {sec:.1f} s)"}
@@ -374,8 +379,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_block(wl, wname), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32",
+            "data": "synthetic", "config": config_block(wl, wname, args.storage, elem), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

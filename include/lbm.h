@@ -49,8 +49,17 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_D3Q27 2    /* flow, Appendix A extended to D3Q27 */
 #define LBM_D2Q5_CDE 3 /* passive scalar with source, Sec. 5 */
 
-/* Population storage / arithmetic. */
+/* Population storage / arithmetic.
+ *   LBM_FP64     : populations in FP64, FP64 arithmetic (the reference form).
+ *   LBM_FP32_DEV : deviations d = f - w * rho_ref from the rest state stored
+ *   LBM_FP16_DEV   in FP32 / FP16 / BF16, all moment arithmetic in FP32
+ *   LBM_BF16_DEV   (rest-state moments folded in analytically); moments,
+ *                  reductions and population I/O stay FP64.  rho_ref is the
+ *                  rho0 given to lbm_init_equilibrium (1 if not positive). */
 #define LBM_FP64 0
+#define LBM_FP32_DEV 1
+#define LBM_FP16_DEV 2
+#define LBM_BF16_DEV 3
 
 /* Status codes. */
 #define LBM_OK 0
@@ -106,8 +115,9 @@ typedef struct {
  * rule of Sec. 6.3).  Evaluated on the host, three times per step. */
 typedef double (*lbm_envelope_fn)(double t, void *user);
 
-/* Create a context.  Allocates two population buffers of q*N doubles on the
- * current CUDA device (N = nx*ny*nz; nz must be 1 for the 2D lattices).
+/* Create a context.  Allocates two population buffers of q*N values (8, 4 or
+ * 2 bytes each by `storage`) on the current CUDA device (N = nx*ny*nz; nz must
+ * be 1 for the 2D lattices).
  * `stream` is a cudaStream_t (NULL = legacy default stream).
  * Errors: LBM_EINVAL (unknown lattice or storage, extent < 1, omega outside
  * (0,2), bad boundary kind), LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
@@ -234,7 +244,8 @@ int lbm_launch_count(const lbm_ctx *ctx, long long *count);
  * advances all of them together: each time step is a single kernel launch
  * over the blocks of every member, each member keeping its own geometry,
  * relaxation rates, force/source/velocity shape, envelope and step counter.
- * The result is bit-for-bit that of calling lbm_step on each member.  The
+ * The arithmetic is that of lbm_step on each member; results agree with it to
+ * FP64 rounding (the two kernels may fuse multiply-adds differently).  The
  * batch keeps pointers to the contexts (they must outlive it) and owns only
  * its own descriptor buffers. */
 typedef struct lbm_batch lbm_batch;

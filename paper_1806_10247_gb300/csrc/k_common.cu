@@ -20,6 +20,19 @@ __device__ __forceinline__ double maxwell1d(int e, double u)
     return 0.5 * (s + (double)e * u);
 }
 
+// Deviation moments of a node in double: dm0 = sum d, j = sum d e.
+template <class L, class T>
+__device__ __forceinline__ void dev_moments(const T *__restrict__ fin, const Geom &g, int x, int y, int z, int i,
+                                            double &dm0, double (&j)[3])
+{
+    float d[L::Q];
+    load_pulled_dev<L, T>(fin, g, x, y, z, i, d);
+    double dd[L::Q];
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) dd[a] = (double)d[a];
+    zeroth_first<L>(dd, dm0, j);
+}
+
 // Equilibrium populations whose central moments are Eq. 20 (flow; the
 // product of 1D profiles, which reproduces c_s^2 rho per squared direction)
 // or Eq. 39 (D2Q5 scalar: moments phi, phi u, phi (1/3 + u^2)).
@@ -212,6 +225,44 @@ k_reduce_partial_sums(Geom g, const double *__restrict__ fin, double *__restrict
     block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
 }
 
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_reduce_partial_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, FieldDev F, double apre,
+                    double *__restrict__ snap, int have_snap, int with_snap, double *__restrict__ partials)
+{
+    double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+        int x, y, z;
+        node_xyz(g, i, x, y, z);
+        double dm0, j[3];
+        dev_moments<L, T>(fin, g, x, y, z, i, dm0, j);
+        const double m0 = rho_ref + dm0;
+        v[R_MASS] += m0;
+        bool bad = !isfinite(m0) || (L::Q != 5 && !(m0 > 0.0));
+        if (L::Q == 5) {
+            if (with_snap) {
+                double phi = fkind != FK_NONE ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
+                if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(phi - snap[i]));
+                snap[i] = phi;
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < L::DIM; d++) {
+                v[R_JX + d] += j[d];
+                if (with_snap) {
+                    double jd = fkind != FK_NONE ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
+                    double ud = jd / m0;
+                    bad = bad || !isfinite(ud);
+                    if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[d * g.N + i]));
+                    snap[d * g.N + i] = ud;
+                }
+            }
+        }
+        if (bad) v[R_BAD] = 1.0;
+    }
+    block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
+}
+
 __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restrict__ partials, int nblocks,
                                                          double *__restrict__ out)
 {
@@ -223,6 +274,106 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restric
             v[s] = (s == R_DU || s == R_BAD) ? fmax(v[s], p) : v[s] + p;
         }
     block_reduce_store(v, out);
+}
+
+// ---- reduced-precision storage: deviations d = f - w rho_ref in type T ----
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_init_rp(Geom g, double rho_ref, double rho0, double u0x, double u0y, double u0z, const double *__restrict__ rho,
+          const double *__restrict__ u, T *__restrict__ stored)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double r = rho ? rho[i] : rho0;
+    double ux = u ? u[i] : u0x;
+    double uy = u ? u[g.N + i] : u0y;
+    double uz = (u && L::DIM == 3) ? u[2 * g.N + i] : u0z;
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        double v;
+        if (L::Q == 5) {
+            const int ex = L::ex(a), ey = L::ey(a);
+            if (ex == 0 && ey == 0) v = r * ((1.0 / 3.0) - ux * ux - uy * uy);
+            else if (ex != 0) v = 0.5 * r * ((1.0 / 3.0) + ux * ux + (double)ex * ux);
+            else v = 0.5 * r * ((1.0 / 3.0) + uy * uy + (double)ey * uy);
+        } else {
+            v = r * maxwell1d(L::ex(a), ux) * maxwell1d(L::ey(a), uy);
+            if (L::DIM == 3) v *= maxwell1d(L::ez(a), uz);
+        }
+        bool opp;
+        int off = pull_off(g, x, y, z, L::ex(a), L::ey(a), L::ez(a), opp);
+        stored[(opp ? L::opp(a) : a) * g.Np + off] = Dev<T>::to_store((float)(v - L::w(a) * rho_ref));
+    }
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_scatter_rp(Geom g, double rho_ref, const double *__restrict__ plain, T *__restrict__ stored)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        bool opp;
+        int off = pull_off(g, x, y, z, L::ex(a), L::ey(a), L::ez(a), opp);
+        const double v = plain[(size_t)a * g.N + i] - L::w(a) * rho_ref;
+        stored[(opp ? L::opp(a) : a) * g.Np + off] = Dev<T>::to_store((float)v);
+    }
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_gather_rp(Geom g, double rho_ref, const T *__restrict__ stored, double *__restrict__ plain)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    float d[L::Q];
+    load_pulled_dev<L, T>(stored, g, x, y, z, i, d);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) plain[(size_t)a * g.N + i] = L::w(a) * rho_ref + (double)d[a];
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_moments_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, FieldDev F, double apre, int half,
+             double *__restrict__ rho, double *__restrict__ u)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double dm0, j[3];
+    dev_moments<L, T>(fin, g, x, y, z, i, dm0, j);
+    const double m0 = rho_ref + dm0;
+    const bool forced = half && fkind != FK_NONE;
+    if (L::Q == 5) {
+        rho[i] = forced ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
+        return;
+    }
+    rho[i] = m0;
+#pragma unroll
+    for (int d = 0; d < L::DIM; d++) {
+        double jd = forced ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
+        u[d * g.N + i] = jd / m0;
+    }
+}
+
+template <class Fn>
+cudaError_t by_storage(int storage, Fn &&fn)
+{
+    switch (storage) {
+    case 1: return fn(float{});
+    case 2: return fn(__half{});
+    case 3: return fn(__nv_bfloat16{});
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <class Fn>
@@ -270,6 +421,16 @@ cudaError_t gather_from_stored(int lattice, const Geom &g, const double *stored,
 
 cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, int half)
 {
+    if (a.storage != 0)
+        return by_lattice(lattice, [&](auto L) {
+            using LT = decltype(L);
+            return by_storage(a.storage, [&](auto T) {
+                using TT = decltype(T);
+                k_moments_rp<LT, TT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(
+                    a.g, reinterpret_cast<const TT *>(a.fin), a.rho_ref, a.fkind, a.F, a.apre, half, rho, u);
+                return cudaGetLastError();
+            });
+        });
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         k_moments<LT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, half,
@@ -287,6 +448,20 @@ int reduce_blocks(const Geom &g)
 cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
                    int nblocks, double *out)
 {
+    if (a.storage != 0)
+        return by_lattice(lattice, [&](auto L) {
+            using LT = decltype(L);
+            return by_storage(a.storage, [&](auto T) {
+                using TT = decltype(T);
+                k_reduce_partial_rp<LT, TT><<<nblocks, kBlock, 0, a.stream>>>(
+                    a.g, reinterpret_cast<const TT *>(a.fin), a.rho_ref, a.fkind, a.F, a.apre, snap, have_snap, 1,
+                    partials);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                k_reduce_final<<<1, kBlock, 0, a.stream>>>(partials, nblocks, out);
+                return cudaGetLastError();
+            });
+        });
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         k_reduce_partial<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, snap,
@@ -298,12 +473,54 @@ cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap
     });
 }
 
+cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, double rho0,
+                                const double *u0, const double *rho, const double *u, void *stored,
+                                cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        return by_storage(storage, [&](auto T) {
+            using TT = decltype(T);
+            k_init_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, rho0, u0[0], u0[1], u0[2], rho, u,
+                                                              reinterpret_cast<TT *>(stored));
+            return cudaGetLastError();
+        });
+    });
+}
+
+cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const double *plain,
+                       void *stored, cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        return by_storage(storage, [&](auto T) {
+            using TT = decltype(T);
+            k_scatter_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, plain, reinterpret_cast<TT *>(stored));
+            return cudaGetLastError();
+        });
+    });
+}
+
+cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const void *stored,
+                      double *plain, cudaStream_t s)
+{
+    return by_lattice(lattice, [&](auto L) {
+        using LT = decltype(L);
+        return by_storage(storage, [&](auto T) {
+            using TT = decltype(T);
+            k_gather_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, reinterpret_cast<const TT *>(stored),
+                                                                plain);
+            return cudaGetLastError();
+        });
+    });
+}
+
 void d2q9_batch_coef(const double omega[9], BatchItem &item);
 void d2q5_batch_coef(const double omega[9], BatchItem &item);
 void d3q27_batch_coef(const double omega[9], BatchItem &item);
-cudaError_t d2q9_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
-cudaError_t d2q5_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
-cudaError_t d3q27_batch_step(const BatchItem *, const int *, int, int, const double2 *, int, cudaStream_t);
+cudaError_t d2q9_batch_step(const BatchLaunch &, int, cudaStream_t);
+cudaError_t d2q5_batch_step(const BatchLaunch &, int, cudaStream_t);
+cudaError_t d3q27_batch_step(const BatchLaunch &, int, cudaStream_t);
 
 void batch_coef(int lattice, const double omega[9], BatchItem &item)
 {
@@ -312,18 +529,31 @@ void batch_coef(int lattice, const double omega[9], BatchItem &item)
     else d3q27_batch_coef(omega, item);
 }
 
-cudaError_t batch_step(int lattice, const BatchItem *items, const int *first_block, int count, int nblocks,
-                       const double2 *pairs, int k, cudaStream_t s)
+cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    if (lattice == LD2Q9::ID) return d2q9_batch_step(items, first_block, count, nblocks, pairs, k, s);
-    if (lattice == LD2Q5::ID) return d2q5_batch_step(items, first_block, count, nblocks, pairs, k, s);
-    return d3q27_batch_step(items, first_block, count, nblocks, pairs, k, s);
+    if (lattice == LD2Q9::ID) return d2q9_batch_step(L, nblocks, s);
+    if (lattice == LD2Q5::ID) return d2q5_batch_step(L, nblocks, s);
+    return d3q27_batch_step(L, nblocks, s);
 }
 
 int batch_blocks(const Geom &g) { return (g.N + kBlock - 1) / kBlock; }
 
 cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out)
 {
+    if (a.storage != 0)
+        return by_lattice(lattice, [&](auto L) {
+            using LT = decltype(L);
+            return by_storage(a.storage, [&](auto T) {
+                using TT = decltype(T);
+                k_reduce_partial_rp<LT, TT><<<nblocks, kBlock, 0, a.stream>>>(
+                    a.g, reinterpret_cast<const TT *>(a.fin), a.rho_ref, a.fkind, a.F, a.apre, nullptr, 0, 0,
+                    partials);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                k_reduce_final<<<1, kBlock, 0, a.stream>>>(partials, nblocks, out);
+                return cudaGetLastError();
+            });
+        });
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         k_reduce_partial_sums<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, partials);

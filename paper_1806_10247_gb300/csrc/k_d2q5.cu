@@ -163,17 +163,17 @@ void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
 // Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
 // coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5.
 __global__ void __launch_bounds__(kBlock)
-k_batch(const BatchItem *__restrict__ items, const int *__restrict__ first, int count,
-        const double2 *__restrict__ pairs, int k)
+k_batch(const __grid_constant__ BatchLaunch L)
 {
-    const int it = batch_find(first, count);
-    const BatchItem &B = items[it];
+    const int it = batch_find(L.first, L.count);
+    const BatchItem &B = L.items[it];
     const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(first + it)) * kBlock + threadIdx.x;
+    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const double *fin = B.buf[(B.parity + k) & 1];
-    double *fout = B.buf[(B.parity + k + 1) & 1];
-    const double2 ap = pairs[(size_t)k * count + it];
+    const int p = B.parity + L.parity;
+    const double *fin = B.buf[p & 1];
+    double *fout = B.buf[(p + 1) & 1];
+    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
     const int x = i % g.nx, y = i / g.nx;
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
@@ -210,10 +210,9 @@ void d2q5_batch_coef(const double omega[9], BatchItem &item)
     for (int k = 0; k < 16; k++) item.coef[k] = v[k];
 }
 
-cudaError_t d2q5_batch_step(const BatchItem *items, const int *first, int count, int nblocks,
-                            const double2 *pairs, int k, cudaStream_t s)
+cudaError_t d2q5_batch_step(const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    k_batch<<<nblocks, kBlock, 0, s>>>(items, first, count, pairs, k);
+    k_batch<<<nblocks, kBlock, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,531 @@
+// Reduced-precision form of the three lattice steps: populations stored as
+// deviations d_a = f_a - w_a rho_ref from the rest state (FP32, FP16 or BF16),
+// every moment computed in FP32 from the deviations.  The rest state's own
+// moments are folded in analytically, so no O(1) quantities are ever
+// subtracted in FP32; only the non-equilibrium signal is carried.  The
+// arithmetic is the same method as the FP64 kernels (Eqs. 23/25/31/32 for
+// D2Q9, Eqs. 41-48 for D2Q5, the generic central-moment procedure for D3Q27),
+// rearranged around the rest state.
+#include "lbm_internal.h"
+#include "lbm_lattices.cuh"
+
+namespace lbmk {
+namespace {
+
+constexpr int kBlock = 256;
+
+// ------------------------------------------------------------------ D2Q9 ---
+
+struct Rates9f {
+    float c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, ..., omega_8/4
+};
+
+//   Fx, Fy : a_pre P (Eq. 25);  Gx, Gy : (F_pre + F_post)/12 (Eq. 31)
+__device__ __forceinline__ void collide9(float (&d)[9], float rref, float Fx, float Fy, float Gx, float Gy,
+                                         const Rates9f &w)
+{
+    // Raw moments of the deviations (Eq. 21 minus the rest state's moments:
+    // the rest state has rho_ref, zero odd moments, rho_ref/3 per squared
+    // direction and rho_ref/9 for xxyy).
+    const float s0 = d[1] + d[3], d0 = d[1] - d[3];
+    const float s1 = d[5] + d[6], d1 = d[5] - d[6];
+    const float s2 = d[8] + d[7], d2 = d[8] - d[7];
+    const float A0 = d[0] + s0, B0 = d[2] + s1, C0 = d[4] + s2;
+    const float drho = A0 + (B0 + C0), jy = B0 - C0, myy = B0 + C0;
+    const float jx = d0 + (d1 + d2), mxy = d1 - d2, mxyy = d1 + d2;
+    const float mxx = s0 + (s1 + s2), mxxy = s1 - s2, mxxyy = s1 + s2;
+    const float rho = rref + drho;
+    const float rinv = __frcp_rn(rho);
+    const float ux = fmaf(0.5f, Fx, jx) * rinv;  // Eq. 25
+    const float uy = fmaf(0.5f, Fy, jy) * rinv;
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
+    const float r3 = rref * (1.0f / 3.0f);
+
+    // Eq. 23 with the rest moments substituted.
+    const float g3 = w.c3 * ((2.0f / 3.0f) * drho + rho * (ux2 + uy2) - (mxx + myy));
+    const float g4 = w.c4 * (rho * (ux2 - uy2) - (mxx - myy));
+    const float g5 = w.c5 * (rho * uxy - mxy);
+    const float p34 = 3.0f * g3 + g4, m34 = 3.0f * g3 - g4;
+    const float g6 = w.c6 * (2.0f * rho * ux2 * uy + mxxy - 2.0f * ux * mxy - uy * (r3 + mxx))
+                     - 0.5f * uy * p34 - 2.0f * ux * g5;
+    const float g7 = w.c7 * (2.0f * rho * ux * uy2 + mxyy - 2.0f * uy * mxy - ux * (r3 + myy))
+                     - 0.5f * ux * m34 - 2.0f * uy * g5;
+    const float g8 = w.c8 * ((1.0f / 9.0f) * drho + 3.0f * rho * ux2 * uy2
+                             - (mxxyy - 2.0f * ux * mxyy - 2.0f * uy * mxxy + ux2 * (r3 + myy)
+                                + uy2 * (r3 + mxx) + 4.0f * uxy * mxy))
+                     - 2.0f * g3 - 0.5f * uy2 * p34 - 0.5f * ux2 * m34 - 4.0f * uxy * g5
+                     - 2.0f * uy * g6 - 2.0f * ux * g7;
+
+    // Eq. 32 (the rest state cancels: d^p = d + K g).
+    const float ax = g4 - g3, ay = -g3 - g4, c = 2.0f * g3 + g8;
+    d[0] += -4.0f * (g3 - g8);
+    d[1] += Gx + ax + 2.0f * (g7 - g8);
+    d[2] += Gy + ay + 2.0f * (g6 - g8);
+    d[3] += -Gx + ax - 2.0f * (g7 + g8);
+    d[4] += -Gy + ay - 2.0f * (g6 + g8);
+    d[5] += c + (Gx + Gy) + (g5 - g6 - g7);
+    d[6] += c + (Gy - Gx) + (-g5 - g6 + g7);
+    d[7] += c - (Gx + Gy) + (g5 + g6 + g7);
+    d[8] += c + (Gx - Gy) + (-g5 + g6 - g7);
+}
+
+template <class T, int FK>
+__global__ void __launch_bounds__(kBlock)
+k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, double apre, double gsum, Rates9f w,
+        float rref)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int x = i % g.nx, y = i / g.nx;
+    float d[9];
+    load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
+    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
+    if (FK != FK_NONE) {
+        const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
+        Fx = (float)(apre * Px);
+        Fy = (float)(apre * Py);
+        Gx = (float)(gsum * Px);
+        Gy = (float)(gsum * Py);
+    }
+    collide9(d, rref, Fx, Fy, Gx, Gy, w);
+#pragma unroll
+    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+// ------------------------------------------------------------------ D2Q5 ---
+
+struct Rates5f {
+    float c1, c2, c3, c4;  // omega_1/2 .. omega_4/4
+};
+
+// General advecting velocity.  S: a_pre S(x); H0: (S_pre + S_post)/10.
+__device__ __forceinline__ void collide5(float (&d)[5], float rref, float S, float H0, float ux, float uy,
+                                         const Rates5f &w)
+{
+    const float kx = d[1] - d[3], ky = d[2] - d[4];
+    const float mxx = d[1] + d[3], myy = d[2] + d[4];  // minus the rest values rref/3
+    const float dphi = fmaf(0.5f, S, d[0] + (mxx + myy));  // Eqs. 42-43, minus rref
+    const float phi = rref + dphi;
+    const float h1 = w.c1 * (phi * ux - kx);
+    const float h2 = w.c2 * (phi * uy - ky);
+    const float h3 = w.c3 * ((2.0f / 3.0f) * dphi - (mxx + myy) + 2.0f * (ux * kx + uy * ky)
+                             - (ux * ux + uy * uy) * phi)
+                     + ux * h1 + uy * h2;
+    const float h4 = w.c4 * (-(mxx - myy) + 2.0f * (ux * kx - uy * ky) - (ux * ux - uy * uy) * phi)
+                     + ux * h1 - uy * h2;
+    const float c = H0 + h3;  // Eq. 48
+    d[0] += H0 - 4.0f * h3;
+    d[1] += c + h1 + h4;
+    d[2] += c + h2 - h4;
+    d[3] += c - h1 + h4;
+    d[4] += c - h2 - h4;
+}
+
+// Uniform advecting velocity: launch-constant coefficients (see the FP64
+// kernel) with the rest-state terms split off: h3 = Q3 rref + P3 dphi + ...,
+// h4 = P4 rref + P4 dphi + ..., h1 = A1 rref + A1 dphi - c1 kx.
+struct Coef5f {
+    float A1, c1, A2, c2, P3, X3, Y3, S3, P4, X4, Y4, D4, Q3;
+};
+
+__device__ __forceinline__ void collide5u(float (&d)[5], float rref, float S, float H0, const Coef5f &k)
+{
+    const float kx = d[1] - d[3], ky = d[2] - d[4];
+    const float mxx = d[1] + d[3], myy = d[2] + d[4];
+    const float Sg = mxx + myy, Dg = mxx - myy;
+    const float dphi = fmaf(0.5f, S, d[0] + Sg);
+    const float phi = rref + dphi;
+    const float h1 = fmaf(k.A1, phi, -k.c1 * kx);
+    const float h2 = fmaf(k.A2, phi, -k.c2 * ky);
+    const float h3 = fmaf(k.Q3, rref, fmaf(k.P3, dphi, fmaf(k.X3, kx, fmaf(k.Y3, ky, k.S3 * Sg))));
+    const float h4 = fmaf(k.P4, phi, fmaf(k.X4, kx, fmaf(k.Y4, ky, k.D4 * Dg)));
+    const float c = H0 + h3;
+    const float e1 = c + h4, e2 = c - h4;
+    d[0] += fmaf(-4.0f, h3, H0);
+    d[1] += e1 + h1;
+    d[2] += e2 + h2;
+    d[3] += e1 - h1;
+    d[4] += e2 - h2;
+}
+
+// Coefficients of a uniform velocity (double on the host, then float).
+Coef5f make_coef5f(const double omega[9], double ux, double uy)
+{
+    const double c1 = omega[1] / 2.0, c2 = omega[2] / 2.0, c3 = omega[3] / 4.0, c4 = omega[4] / 4.0;
+    const double ux2 = ux * ux, uy2 = uy * uy;
+    Coef5f k;
+    k.A1 = (float)(c1 * ux);
+    k.c1 = (float)c1;
+    k.A2 = (float)(c2 * uy);
+    k.c2 = (float)c2;
+    const double P3 = c3 * ((2.0 / 3.0) - ux2 - uy2) + c1 * ux2 + c2 * uy2;
+    k.P3 = (float)P3;
+    k.X3 = (float)(ux * (2.0 * c3 - c1));
+    k.Y3 = (float)(uy * (2.0 * c3 - c2));
+    k.S3 = (float)(-c3);
+    k.Q3 = (float)(-c3 * (ux2 + uy2) + c1 * ux2 + c2 * uy2);  // P3 - (2/3) c3: small, O(u^2)
+    k.P4 = (float)(-c4 * (ux2 - uy2) + c1 * ux2 - c2 * uy2);
+    k.X4 = (float)(ux * (2.0 * c4 - c1));
+    k.Y4 = (float)(uy * (c2 - 2.0 * c4));
+    k.D4 = (float)(-c4);
+    return k;
+}
+
+template <class T, int SK, bool UNIFORM>
+__global__ void __launch_bounds__(kBlock)
+k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, FieldDev V, double apre, double hsum,
+        Rates5f w, Coef5f k, float rref)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int x = i % g.nx, y = i / g.nx;
+    float d[5];
+    load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
+    float Sp = 0.f, H0 = 0.f;
+    if (SK != FK_NONE) {
+        const double P = field_value(S, SK, 0, x, y, 0, i);
+        Sp = (float)(apre * P);
+        H0 = (float)(hsum * P);
+    }
+    if (UNIFORM) {
+        collide5u(d, rref, Sp, H0, k);
+    } else {
+        const float ux = (float)field_value(V, FK_GENERAL, 0, x, y, 0, i);
+        const float uy = (float)field_value(V, FK_GENERAL, 1, x, y, 0, i);
+        collide5(d, rref, Sp, H0, ux, uy, w);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+// ----------------------------------------------------------------- D3Q27 ---
+
+struct Rates27f {
+    float wb, ws, w3, w4, w5, w6;
+};
+
+__device__ __forceinline__ void raw_fwd(float &a, float &b, float &c)
+{
+    const float s = c + a, dd = c - a;
+    a = s + b;
+    b = dd;
+    c = s;
+}
+__device__ __forceinline__ void raw_bwd(float &m0, float &m1, float &m2)
+{
+    const float h = 0.5f * m2;
+    const float fm = fmaf(-0.5f, m1, h), fp = fmaf(0.5f, m1, h), f0 = m0 - m2;
+    m0 = fm;
+    m1 = f0;
+    m2 = fp;
+}
+__device__ __forceinline__ void shift_fwd(float m0, float &m1, float &m2, float u)
+{
+    const float k1 = fmaf(-u, m0, m1);
+    m2 = fmaf(-u, m1 + k1, m2);
+    m1 = k1;
+}
+__device__ __forceinline__ void shift_bwd(float k0, float &k1, float &k2, float u)
+{
+    const float m1 = fmaf(u, k0, k1);
+    k2 = fmaf(u, k1 + m1, k2);
+    k1 = m1;
+}
+template <int AX, class Op>
+__device__ __forceinline__ void along(float (&m)[27], Op op)
+{
+    constexpr int st = AX == 0 ? 1 : (AX == 1 ? 3 : 9);
+#pragma unroll
+    for (int t = 0; t < 9; t++) {
+        const int p = AX == 0 ? 3 * t : (AX == 1 ? (t % 3) + 9 * (t / 3) : t);
+        op(m[p], m[p + st], m[p + 2 * st]);
+    }
+}
+
+// Deviation form of the generic central-moment collision: m holds the raw
+// moments of the deviations (index a + 3b + 9c); the rest state's central
+// moments about u, rref * prod(1, -u, 1/3 + u^2), are folded in analytically.
+__device__ __forceinline__ void collide27(float (&m)[27], float rref, const float (&F)[3], const float (&Fq)[3],
+                                          const Rates27f &w)
+{
+    along<0>(m, [](float &a, float &b, float &c) { raw_fwd(a, b, c); });
+    along<1>(m, [](float &a, float &b, float &c) { raw_fwd(a, b, c); });
+    along<2>(m, [](float &a, float &b, float &c) { raw_fwd(a, b, c); });
+
+    m[1] = fmaf(0.5f, F[0], m[1]);  // pre-collision half force (rest state has no momentum)
+    m[3] = fmaf(0.5f, F[1], m[3]);
+    m[9] = fmaf(0.5f, F[2], m[9]);
+    const float drho = m[0];
+    const float rho = rref + drho;
+    const float rinv = __frcp_rn(rho);
+    const float ux = m[1] * rinv, uy = m[3] * rinv, uz = m[9] * rinv;
+
+    along<0>(m, [ux](float &a, float &b, float &c) { shift_fwd(a, b, c, ux); });
+    along<1>(m, [uy](float &a, float &b, float &c) { shift_fwd(a, b, c, uy); });
+    along<2>(m, [uz](float &a, float &b, float &c) { shift_fwd(a, b, c, uz); });
+
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    {
+        // second order: trace towards rho, deviatoric and off-diagonal towards 0
+        const float Tn = m[2] + m[6] + m[18];
+        const float Ts = fmaf(w.wb, drho - rref * (ux2 + uy2 + uz2) - Tn, Tn);
+        const float D1 = m[2] - m[6], D2 = m[2] - m[18];
+        const float rs = 1.0f - w.ws;
+        const float D1s = rs * D1 - w.ws * rref * (ux2 - uy2);
+        const float D2s = rs * D2 - w.ws * rref * (ux2 - uz2);
+        const float kxx = (Ts + D1s + D2s) * (1.0f / 3.0f);
+        m[2] = kxx;
+        m[6] = kxx - D1s;
+        m[18] = kxx - D2s;
+        m[4] = rs * m[4] - w.ws * rref * (ux * uy);
+        m[10] = rs * m[10] - w.ws * rref * (ux * uz);
+        m[12] = rs * m[12] - w.ws * rref * (uy * uz);
+        // orders 3..6 towards the Maxwellian central moments
+        const float hx[3] = {1.0f, -ux, (1.0f / 3.0f) + ux2};
+        const float hy[3] = {1.0f, -uy, (1.0f / 3.0f) + uy2};
+        const float hz[3] = {1.0f, -uz, (1.0f / 3.0f) + uz2};
+#pragma unroll
+        for (int k = 0; k < 27; k++) {
+            const int a = k % 3, b = (k / 3) % 3, c = k / 9;
+            const int n = a + b + c;
+            if (n < 3) continue;
+            float dv;
+            if (a == 1 || b == 1 || c == 1) {
+                dv = -rref * (hx[a] * hy[b] * hz[c]);  // equilibrium 0 minus the rest state's moment
+            } else if (n == 4) {
+                const float p = (a == 2 ? ux2 : 0.f) + (b == 2 ? uy2 : 0.f) + (c == 2 ? uz2 : 0.f);
+                const float q = (a == 2 ? ux2 : 1.f) * (b == 2 ? uy2 : 1.f) * (c == 2 ? uz2 : 1.f);
+                dv = drho * (1.0f / 9.0f) - rref * (p * (1.0f / 3.0f) + q);
+            } else {  // n == 6
+                dv = drho * (1.0f / 27.0f)
+                     - rref * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f)
+                               + ux2 * uy2 * uz2);
+            }
+            const float om = n == 3 ? w.w3 : (n == 4 ? w.w4 : (n == 5 ? w.w5 : w.w6));
+            m[k] = fmaf(om, dv - m[k], m[k]);
+        }
+    }
+
+    along<0>(m, [ux](float &a, float &b, float &c) { shift_bwd(a, b, c, ux); });
+    along<1>(m, [uy](float &a, float &b, float &c) { shift_bwd(a, b, c, uy); });
+    along<2>(m, [uz](float &a, float &b, float &c) { shift_bwd(a, b, c, uz); });
+
+    {
+        const float hx = 0.5f * (F[0] + Fq[0]), hy = 0.5f * (F[1] + Fq[1]), hz = 0.5f * (F[2] + Fq[2]);
+        m[1] = fmaf(0.5f, Fq[0], m[1]);
+        m[3] = fmaf(0.5f, Fq[1], m[3]);
+        m[9] = fmaf(0.5f, Fq[2], m[9]);
+        const float ax = hx * (2.0f / 3.0f), ay = hy * (2.0f / 3.0f), az = hz * (2.0f / 3.0f);
+        m[7] += ax; m[19] += ax; m[25] = fmaf(hx, 4.0f / 9.0f, m[25]);
+        m[5] += ay; m[21] += ay; m[23] = fmaf(hy, 4.0f / 9.0f, m[23]);
+        m[11] += az; m[15] += az; m[17] = fmaf(hz, 4.0f / 9.0f, m[17]);
+    }
+
+    along<2>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    along<1>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    along<0>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+}
+
+template <class T, int FK>
+__global__ void __launch_bounds__(kBlock)
+k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, double apre, double apost,
+         Rates27f w, float rref)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    float m[27];
+    load_pulled_dev<LD3Q27, T>(fin, g, x, y, z, i, m);
+    float F[3] = {0.f, 0.f, 0.f}, Fq[3] = {0.f, 0.f, 0.f};
+    if (FK != FK_NONE) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double P = field_value(Fd, FK, d, x, y, z, i);
+            F[d] = (float)(apre * P);
+            Fq[d] = (float)(apost * P);
+        }
+    }
+    collide27(m, rref, F, Fq, w);
+#pragma unroll
+    for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
+}
+
+// --------------------------------------------------------------- batched ---
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ BatchLaunch L)
+{
+    const int it = batch_find(L.first, L.count);
+    const BatchItem &B = L.items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int p = B.parity + L.parity;
+    const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
+    T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
+    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    const int x = i % g.nx, y = i / g.nx;
+    float d[9];
+    load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
+    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
+    if (B.fkind != FK_NONE) {
+        const double Px = field_value(B.F, B.fkind, 0, x, y, 0, i), Py = field_value(B.F, B.fkind, 1, x, y, 0, i);
+        Fx = (float)(ap.x * Px);
+        Fy = (float)(ap.x * Py);
+        Gx = (float)(ap.y * Px);
+        Gy = (float)(ap.y * Py);
+    }
+    const Rates9f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
+                    (float)B.coef[3], (float)B.coef[4], (float)B.coef[5]};
+    collide9(d, (float)B.rho_ref, Fx, Fy, Gx, Gy, w);
+#pragma unroll
+    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+// D2Q5 items carry Coef5 (double) in coef[0..11] and the rates in coef[12..15].
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ BatchLaunch L)
+{
+    const int it = batch_find(L.first, L.count);
+    const BatchItem &B = L.items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int p = B.parity + L.parity;
+    const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
+    T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
+    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    const int x = i % g.nx, y = i / g.nx;
+    float d[5];
+    load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
+    float Sp = 0.f, H0 = 0.f;
+    if (B.fkind != FK_NONE) {
+        const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
+        Sp = (float)(ap.x * P);
+        H0 = (float)(ap.y * P);
+    }
+    const float rref = (float)B.rho_ref;
+    if (B.vkind != FK_GENERAL) {
+        Coef5f k;
+        k.A1 = (float)B.coef[0]; k.c1 = (float)B.coef[1]; k.A2 = (float)B.coef[2]; k.c2 = (float)B.coef[3];
+        k.P3 = (float)B.coef[4]; k.X3 = (float)B.coef[5]; k.Y3 = (float)B.coef[6]; k.S3 = (float)B.coef[7];
+        k.P4 = (float)B.coef[8]; k.X4 = (float)B.coef[9]; k.Y4 = (float)B.coef[10]; k.D4 = (float)B.coef[11];
+        k.Q3 = (float)(B.coef[4] + (2.0 / 3.0) * B.coef[7]);
+        collide5u(d, rref, Sp, H0, k);
+    } else {
+        const Rates5f w{(float)B.coef[12], (float)B.coef[13], (float)B.coef[14], (float)B.coef[15]};
+        const float ux = (float)field_value(B.V, FK_GENERAL, 0, x, y, 0, i);
+        const float uy = (float)field_value(B.V, FK_GENERAL, 1, x, y, 0, i);
+        collide5(d, rref, Sp, H0, ux, uy, w);
+    }
+#pragma unroll
+    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_batch27(const __grid_constant__ BatchLaunch L)
+{
+    const int it = batch_find(L.first, L.count);
+    const BatchItem &B = L.items[it];
+    const Geom g = B.g;
+    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const int p = B.parity + L.parity;
+    const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
+    T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
+    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    float m[27];
+    load_pulled_dev<LD3Q27, T>(fin, g, x, y, z, i, m);
+    float F[3] = {0.f, 0.f, 0.f}, Fq[3] = {0.f, 0.f, 0.f};
+    if (B.fkind != FK_NONE) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const double P = field_value(B.F, B.fkind, d, x, y, z, i);
+            F[d] = (float)(ap.x * P);
+            Fq[d] = (float)(ap.y * P);
+        }
+    }
+    const Rates27f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
+                     (float)B.coef[3], (float)B.coef[4], (float)B.coef[5]};
+    collide27(m, (float)B.rho_ref, F, Fq, w);
+#pragma unroll
+    for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
+}
+
+template <class T>
+cudaError_t step_t(int lattice, const LaunchArgs &a)
+{
+    const T *fin = reinterpret_cast<const T *>(a.fin);
+    T *fout = reinterpret_cast<T *>(a.fout);
+    const int grid = (a.g.N + kBlock - 1) / kBlock;
+    const float rref = (float)a.rho_ref;
+    const cudaStream_t s = a.stream;
+    if (lattice == LD2Q9::ID) {
+        const Rates9f w{(float)(a.omega[3] / 12.0), (float)(a.omega[4] / 4.0), (float)(a.omega[5] / 4.0),
+                        (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
+        const double gsum = (a.apre + a.apost) / 12.0;
+        if (a.fkind == FK_NONE) k_step9<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
+        else if (a.fkind == FK_CONST) k_step9<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
+        else k_step9<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
+    } else if (lattice == LD2Q5::ID) {
+        const Rates5f w{(float)(a.omega[1] / 2.0), (float)(a.omega[2] / 2.0), (float)(a.omega[3] / 4.0),
+                        (float)(a.omega[4] / 4.0)};
+        const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0, uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
+        const Coef5f k = make_coef5f(a.omega, ux, uy);
+        const double hsum = (a.apre + a.apost) / 10.0;
+        const bool uni = a.vkind != FK_GENERAL;
+        if (a.fkind == FK_NONE) {
+            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+        } else if (a.fkind == FK_CONST) {
+            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+        } else {
+            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+        }
+    } else {
+        const Rates27f w{(float)a.omega[1], (float)a.omega[2], (float)a.omega[3],
+                         (float)a.omega[4], (float)a.omega[5], (float)a.omega[6]};
+        if (a.fkind == FK_NONE) k_step27<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
+        else if (a.fkind == FK_CONST) k_step27<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
+        else k_step27<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t batch_t(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
+{
+    if (lattice == LD2Q9::ID) k_batch9<T><<<nblocks, kBlock, 0, s>>>(L);
+    else if (lattice == LD2Q5::ID) k_batch5<T><<<nblocks, kBlock, 0, s>>>(L);
+    else k_batch27<T><<<nblocks, kBlock, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t rp_step(int lattice, const LaunchArgs &a)
+{
+    switch (a.storage) {
+    case 1: return step_t<float>(lattice, a);
+    case 2: return step_t<__half>(lattice, a);
+    case 3: return step_t<__nv_bfloat16>(lattice, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, cudaStream_t s)
+{
+    switch (storage) {
+    case 1: return batch_t<float>(lattice, L, nblocks, s);
+    case 2: return batch_t<__half>(lattice, L, nblocks, s);
+    case 3: return batch_t<__nv_bfloat16>(lattice, L, nblocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbmk

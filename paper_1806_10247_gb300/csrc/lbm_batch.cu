@@ -1,11 +1,13 @@
 // Batched stepping (include/lbm.h, lbm_batch_*): many independent lattices of
 // one kind advanced by one kernel launch per time step.
 //
-// Per call the host writes a descriptor per lattice (geometry, buffers,
-// fields, collision coefficients) and the envelope pairs of every step into a
-// pinned staging slot, copies them to the device asynchronously and launches
-// one batched kernel per step.  Two slots alternate, so a call only waits for
-// the copy issued two calls earlier.
+// The device keeps one descriptor per lattice (geometry, both population
+// buffers, fields, collision coefficients); it is re-sent only when a member
+// changed (its version counter moved, or its buffers are no longer in
+// lockstep with the others).  The buffer parity of a step is a launch
+// argument.  The envelope pairs of a step travel in the launch arguments for
+// batches of up to kInlinePairs lattices; larger batches copy a per-call
+// table through one of two alternating pinned staging slots.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,8 +28,12 @@ struct lbm_batch {
     int count = 0;
     int nblocks = 0;
     int *d_first = nullptr;
-    BatchItem *d_items[2] = {nullptr, nullptr};
-    BatchItem *h_items[2] = {nullptr, nullptr};
+    BatchItem *d_items = nullptr;      // descriptors on the device
+    BatchItem *h_items = nullptr;      // pinned staging of the descriptors
+    cudaEvent_t ev_items = nullptr;    // recorded after the last descriptor copy
+    bool items_valid = false;
+    std::vector<long long> item_version;
+    std::vector<double *> item_buf0;   // buf[0] of each uploaded descriptor
     double2 *d_pairs[2] = {nullptr, nullptr};
     double2 *h_pairs[2] = {nullptr, nullptr};
     size_t pairs_cap[2] = {0, 0};  // double2 entries per slot
@@ -61,7 +67,7 @@ int bfail(lbm_batch *b, int code, const char *fmt, ...)
 
 // Second value of a step's envelope pair as the batched kernels expect it:
 // D2Q9 (a_pre + a_post)/12, D2Q5 (a_pre + a_post)/10, D3Q27 a_post -- the same
-// expressions as the single-lattice launchers, so both paths agree bit for bit.
+// expressions as the single-lattice launchers.
 double pair_second(int lattice, double apre, double apost)
 {
     if (lattice == LBM_D2Q9) return (apre + apost) / 12.0;
@@ -121,12 +127,13 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count)
         return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: more than 2^31-1 blocks");
     }
     b->nblocks = (int)nb;
+    b->item_version.assign(count, -1);
+    b->item_buf0.assign(count, nullptr);
     cudaError_t e = cudaMalloc(&b->d_first, count * sizeof(int));
-    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
-        e = cudaMalloc(&b->d_items[s], count * sizeof(BatchItem));
-        if (e == cudaSuccess) e = cudaMallocHost(&b->h_items[s], count * sizeof(BatchItem));
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
-    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, count * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, count * sizeof(BatchItem));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_items, cudaEventDisableTiming);
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_first, first.data(), count * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -146,9 +153,10 @@ void lbm_batch_destroy(lbm_batch *b)
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     cudaFree(b->d_first);
+    cudaFree(b->d_items);
+    cudaFreeHost(b->h_items);
+    if (b->ev_items) cudaEventDestroy(b->ev_items);
     for (int s = 0; s < 2; s++) {
-        cudaFree(b->d_items[s]);
-        cudaFreeHost(b->h_items[s]);
         cudaFree(b->d_pairs[s]);
         cudaFreeHost(b->h_pairs[s]);
         if (b->ev[s]) cudaEventDestroy(b->ev[s]);
@@ -174,41 +182,80 @@ int lbm_batch_step(lbm_batch *b, long n)
         if (!lbmc::envelope_covers(c, c->t, n))
             return bfail(b, LBM_EINVAL, "lbm_batch_step: context %d steps outside its envelope table", i);
     }
-    const int s = b->slot;
-    b->slot ^= 1;
-    // The staging slot was last read by the copy recorded two calls ago.
-    BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
-    int rc = grow_pairs(b, s, (size_t)n * b->count);
-    if (rc != LBM_OK) return rc;
-    for (int i = 0; i < b->count; i++) {
+    // Descriptors: reuse the device copy while every member is unchanged and
+    // all members sit on the same buffer parity relative to it.
+    int parity = 0;
+    bool reuse = b->items_valid;
+    for (int i = 0; i < b->count && reuse; i++) {
         const lbm_ctx *c = b->ctx[i];
-        BatchItem &it = b->h_items[s][i];
-        it = BatchItem{};
-        it.g = c->g;
-        it.buf[0] = c->A;
-        it.buf[1] = c->B;
-        it.parity = 0;
-        it.fkind = c->force.kind;
-        it.F = c->force.d;
-        it.vkind = c->vel.kind;
-        it.V = c->vel.d;
-        batch_coef(c->lattice, c->omega, it);
-        for (long k = 0; k < n; k++) {
-            double apre, apost;
-            lbmc::envelope_pair(c, c->t + k, apre, apost);
-            b->h_pairs[s][(size_t)k * b->count + i] = make_double2(apre, pair_second(b->lattice, apre, apost));
-        }
+        const int p = c->A == b->item_buf0[i] ? 0 : 1;
+        if (c->version != b->item_version[i] || (i == 0 ? false : p != parity)) reuse = false;
+        if (i == 0) parity = p;
     }
-    BCK(cudaMemcpyAsync(b->d_items[s], b->h_items[s], b->count * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                        b->stream),
-        "lbm_batch_step: copy descriptors");
-    BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * sizeof(double2),
-                        cudaMemcpyHostToDevice, b->stream),
-        "lbm_batch_step: copy envelope pairs");
-    BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
+    if (!reuse) {
+        BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
+        for (int i = 0; i < b->count; i++) {
+            const lbm_ctx *c = b->ctx[i];
+            BatchItem &it = b->h_items[i];
+            it = BatchItem{};
+            it.g = c->g;
+            it.rho_ref = c->rho_ref;
+            it.buf[0] = c->A;
+            it.buf[1] = c->B;
+            it.parity = 0;
+            it.fkind = c->force.kind;
+            it.F = c->force.d;
+            it.vkind = c->vel.kind;
+            it.V = c->vel.d;
+            batch_coef(c->lattice, c->omega, it);
+            b->item_version[i] = c->version;
+            b->item_buf0[i] = c->A;
+        }
+        BCK(cudaMemcpyAsync(b->d_items, b->h_items, b->count * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                            b->stream),
+            "lbm_batch_step: copy descriptors");
+        BCK(cudaEventRecord(b->ev_items, b->stream), "lbm_batch_step: record");
+        b->items_valid = true;
+        parity = 0;
+    }
+    BatchLaunch L{};
+    L.items = b->d_items;
+    L.first = b->d_first;
+    L.count = b->count;
+    const bool inline_pairs = b->count <= kInlinePairs;
+    if (!inline_pairs) {
+        const int s = b->slot;
+        b->slot ^= 1;
+        // The staging slot was last read by the copy recorded two calls ago.
+        BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
+        int rc = grow_pairs(b, s, (size_t)n * b->count);
+        if (rc != LBM_OK) return rc;
+        for (int i = 0; i < b->count; i++) {
+            const lbm_ctx *c = b->ctx[i];
+            for (long k = 0; k < n; k++) {
+                double apre, apost;
+                lbmc::envelope_pair(c, c->t + k, apre, apost);
+                b->h_pairs[s][(size_t)k * b->count + i] = make_double2(apre, pair_second(b->lattice, apre, apost));
+            }
+        }
+        BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * sizeof(double2),
+                            cudaMemcpyHostToDevice, b->stream),
+            "lbm_batch_step: copy envelope pairs");
+        BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
+        L.pairs = b->d_pairs[s];
+    }
     for (long k = 0; k < n; k++) {
-        cudaError_t e = batch_step(b->lattice, b->d_items[s], b->d_first, b->count, b->nblocks, b->d_pairs[s],
-                                   (int)k, b->stream);
+        L.k = (int)k;
+        L.parity = (parity + (int)k) & 1;
+        if (inline_pairs)
+            for (int i = 0; i < b->count; i++) {
+                double apre, apost;
+                lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t + k, apre, apost);
+                L.inl[i] = make_double2(apre, pair_second(b->lattice, apre, apost));
+            }
+        const int storage = b->ctx[0]->storage;
+        cudaError_t e = storage == LBM_FP64 ? batch_step(b->lattice, L, b->nblocks, b->stream)
+                                            : rp_batch_step(b->lattice, storage, L, b->nblocks, b->stream);
         if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_step: kernel: %s", cudaGetErrorString(e));
         b->launches++;
     }

@@ -100,7 +100,21 @@ LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double
     a.apost = apost;
     for (int k = 0; k < 9; k++) a.omega[k] = c->omega[k];
     a.stream = c->stream;
+    a.storage = c->storage;
+    a.rho_ref = c->rho_ref;
     return a;
+}
+
+// Reduced-precision contexts: FP64 staging of q*N doubles for host I/O.
+int ensure_stage(lbm_ctx *c)
+{
+    if (c->stage) return LBM_OK;
+    cudaError_t e = cudaMalloc(&c->stage, (size_t)c->q * c->g.N * sizeof(double));
+    if (e != cudaSuccess) {
+        c->stage = nullptr;
+        return cuda_fail(c, e, "cudaMalloc(staging)");
+    }
+    return LBM_OK;
 }
 
 }  // namespace lbmc
@@ -202,7 +216,8 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     *out = nullptr;
     const int q = lattice_q(lattice);
     if (q == 0) return fail(nullptr, LBM_EINVAL, "lbm_create: unknown lattice %d", lattice);
-    if (storage != LBM_FP64) return fail(nullptr, LBM_EINVAL, "lbm_create: unsupported storage %d", storage);
+    if (storage < LBM_FP64 || storage > LBM_BF16_DEV)
+        return fail(nullptr, LBM_EINVAL, "lbm_create: unsupported storage %d", storage);
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: extents must be >= 1");
     if (lattice_dim(lattice) == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nz must be 1 for a 2D lattice");
     const long long N = (long long)nx * ny * nz;
@@ -226,16 +241,17 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     c->q = q;
     c->dim = lattice_dim(lattice);
     c->storage = storage;
+    c->elem = storage == LBM_FP64 ? 8 : (storage == LBM_FP32_DEV ? 4 : 2);
     c->g.nx = nx;
     c->g.ny = ny;
     c->g.nz = nz;
     c->g.N = (int)N;
-    c->g.Np = (N + 31) / 32 * 32;
+    c->g.Np = (N + 127) / 128 * 128;  // every plane starts 256-byte aligned for any element size
     for (int d = 0; d < 3; d++) c->g.wall[d] = wall[d];
     for (int k = 0; k < 9; k++) c->omega[k] = relax->omega[k];
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
-    const size_t bytes = (size_t)q * c->g.Np * sizeof(double);
+    const size_t bytes = (size_t)q * c->g.Np * c->elem;
     cudaError_t e = cudaMalloc(&c->A, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->B, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->partials, (size_t)reduce_blocks(c->g) * 8 * sizeof(double));
@@ -262,6 +278,7 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->red_out);
     cudaFree(c->force.dev);
     cudaFree(c->vel.dev);
+    cudaFree(c->stage);
     delete c;
 }
 
@@ -283,8 +300,12 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
     double *drho = nullptr, *du = nullptr;
     // Per-node inputs are staged in A (q*Np >= (1+dim)*N doubles); the
     // equilibrium goes to B and the scatter then overwrites A.
+    if ((rho || u) && c->storage != LBM_FP64) {
+        int rc = ensure_stage(c);
+        if (rc != LBM_OK) return rc;
+    }
     if (rho || u) {
-        double *stage = c->A;
+        double *stage = c->storage == LBM_FP64 ? c->A : c->stage;
         if (rho) {
             drho = stage;
             CK(cudaMemcpyAsync(drho, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload rho");
@@ -296,13 +317,21 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
                "upload u");
         }
     }
-    CK(equilibrium(c->lattice, c->g, rho0, uu, drho, du, c->B, c->stream), "equilibrium kernel");
-    CK(scatter_to_stored(c->lattice, c->g, c->B, c->A, c->stream), "scatter kernel");
-    c->launches += 2;
+    if (c->storage == LBM_FP64) {
+        CK(equilibrium(c->lattice, c->g, rho0, uu, drho, du, c->B, c->stream), "equilibrium kernel");
+        CK(scatter_to_stored(c->lattice, c->g, c->B, c->A, c->stream), "scatter kernel");
+        c->launches += 2;
+    } else {
+        c->rho_ref = rho0 > 0.0 ? rho0 : 1.0;
+        CK(rp_init_equilibrium(c->lattice, c->storage, c->g, c->rho_ref, rho0, uu, drho, du, c->A, c->stream),
+           "equilibrium kernel");
+        c->launches += 1;
+    }
     CK(cudaStreamSynchronize(c->stream), "lbm_init_equilibrium");
     c->t = 0;
     c->initialised = true;
     c->have_snap = false;
+    c->version++;
     return LBM_OK;
 }
 
@@ -310,6 +339,7 @@ int lbm_set_force(lbm_ctx *c, const lbm_field *shape)
 {
     if (!c) return LBM_EINVAL;
     c->err.clear();
+    c->version++;
     if (c->lattice == LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_force: scalar lattice (use lbm_set_source)");
     return upload_field(c, shape, c->dim, c->force, "lbm_set_force");
 }
@@ -318,6 +348,7 @@ int lbm_set_source(lbm_ctx *c, const lbm_field *shape)
 {
     if (!c) return LBM_EINVAL;
     c->err.clear();
+    c->version++;
     if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_source: flow lattice (use lbm_set_force)");
     return upload_field(c, shape, 1, c->force, "lbm_set_source");
 }
@@ -326,6 +357,7 @@ int lbm_set_velocity(lbm_ctx *c, const lbm_field *u)
 {
     if (!c) return LBM_EINVAL;
     c->err.clear();
+    c->version++;
     if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_velocity: only for the scalar lattice");
     return upload_field(c, u, 2, c->vel, "lbm_set_velocity");
 }
@@ -368,10 +400,14 @@ int lbm_step(lbm_ctx *c, long n)
         envelope_pair(c, c->t, apre, apost);
         LaunchArgs a = launch_args(c, c->A, c->B, apre, apost);
         cudaError_t e;
-        switch (c->lattice) {
-        case LBM_D2Q9: e = d2q9_step(a); break;
-        case LBM_D2Q5_CDE: e = d2q5_step(a); break;
-        default: e = d3q27_step(a); break;
+        if (c->storage != LBM_FP64) {
+            e = rp_step(c->lattice, a);
+        } else {
+            switch (c->lattice) {
+            case LBM_D2Q9: e = d2q9_step(a); break;
+            case LBM_D2Q5_CDE: e = d2q5_step(a); break;
+            default: e = d3q27_step(a); break;
+            }
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
         c->launches++;
@@ -396,9 +432,15 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
     LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
     const size_t N = (size_t)c->g.N;
     double *drho = rho, *du = u;
-    if (where == 0) {  // stage through the scratch buffer B
-        drho = c->B;
-        du = c->B + N;
+    if (where == 0) {  // stage through the scratch buffer B (FP64) or the staging buffer
+        double *st = c->B;
+        if (c->storage != LBM_FP64) {
+            int rc = ensure_stage(c);
+            if (rc != LBM_OK) return rc;
+            st = c->stage;
+        }
+        drho = st;
+        du = st + N;
     }
     CK(moments(c->lattice, a, drho, du, half_forced ? 1 : 0), "moments kernel");
     c->launches++;
@@ -448,10 +490,25 @@ int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where)
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations: populations not initialised");
     if (!dst || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_get_populations: count must be q*N");
-    CK(gather_from_stored(c->lattice, c->g, c->A, c->B, c->stream), "gather kernel");
-    c->launches++;
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->storage != LBM_FP64) {
+        double *plain = where ? dst : nullptr;
+        if (!plain) {
+            int rc = ensure_stage(c);
+            if (rc != LBM_OK) return rc;
+            plain = c->stage;
+        }
+        CK(rp_gather(c->lattice, c->storage, c->g, c->rho_ref, c->A, plain, c->stream), "gather kernel");
+        c->launches++;
+        if (!where) {
+            CK(cudaMemcpyAsync(dst, plain, (size_t)c->q * N * sizeof(double), kind, c->stream), "copy populations");
+            CK(cudaStreamSynchronize(c->stream), "lbm_get_populations");
+        }
+        return LBM_OK;
+    }
+    CK(gather_from_stored(c->lattice, c->g, c->A, c->B, c->stream), "gather kernel");
+    c->launches++;
     CK(cudaMemcpy2DAsync(dst, N * sizeof(double), c->B, (size_t)c->g.Np * sizeof(double), N * sizeof(double),
                          (size_t)c->q, kind, c->stream),
        "copy populations");
@@ -467,6 +524,23 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
     if (step < 0) return fail(c, LBM_EINVAL, "lbm_set_populations: step < 0");
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->storage != LBM_FP64) {
+        const double *plain = where ? src : nullptr;
+        if (!plain) {
+            int rc = ensure_stage(c);
+            if (rc != LBM_OK) return rc;
+            CK(cudaMemcpyAsync(c->stage, src, (size_t)c->q * N * sizeof(double), kind, c->stream), "copy populations");
+            plain = c->stage;
+        }
+        CK(rp_scatter(c->lattice, c->storage, c->g, c->rho_ref, plain, c->A, c->stream), "scatter kernel");
+        c->launches++;
+        CK(cudaStreamSynchronize(c->stream), "lbm_set_populations");
+        c->t = step;
+        c->initialised = true;
+        c->have_snap = false;
+        c->version++;
+        return LBM_OK;
+    }
     CK(cudaMemcpy2DAsync(c->B, (size_t)c->g.Np * sizeof(double), src, N * sizeof(double), N * sizeof(double),
                          (size_t)c->q, kind, c->stream),
        "copy populations");
@@ -476,6 +550,7 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
     c->t = step;
     c->initialised = true;
     c->have_snap = false;
+    c->version++;
     return LBM_OK;
 }
 

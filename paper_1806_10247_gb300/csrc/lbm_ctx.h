@@ -22,11 +22,14 @@ struct DeviceField {
 
 struct lbm_ctx {
     int lattice = 0, q = 0, dim = 0, storage = 0;
+    int elem = 8;         // bytes per stored population value
+    double rho_ref = 1.0; // reduced-precision storage: reference of the deviations
+    double *stage = nullptr;  // reduced-precision storage: q*N doubles for host I/O (lazy)
     int device = 0;       // CUDA device that was current at lbm_create
     lbmk::Geom g{};
     double omega[9] = {0};
     cudaStream_t stream = nullptr;
-    double *A = nullptr;  // stored populations of the current state
+    double *A = nullptr;  // stored populations of the current state (element type per storage)
     double *B = nullptr;  // next state / scratch
     lbmc::DeviceField force;  // force (flow) or source (scalar)
     lbmc::DeviceField vel;    // advecting velocity (scalar)
@@ -41,6 +44,7 @@ struct lbm_ctx {
     double *partials = nullptr;
     double *red_out = nullptr;
     long long launches = 0;
+    long long version = 0;  // bumped by every change a batch descriptor depends on
     std::string err;
 };
 

@@ -20,7 +20,21 @@ struct LaunchArgs {
     double apre, apost;  // envelope averages of the two half steps
     double omega[9];
     cudaStream_t stream;
+    int storage;         // 0 FP64 populations; 1/2/3 FP32/FP16/BF16 deviations f - w rho_ref
+    double rho_ref;      // reference density/scalar of the deviations
 };
+
+// Reduced-precision storage (deviations from the rest state w * rho_ref):
+// fused equilibrium fill into the stored layout, conversions between f(t) as
+// dense [q][N] doubles and the stored layout, and the step kernel.
+cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, double rho0,
+                                const double *u0, const double *rho, const double *u, void *stored,
+                                cudaStream_t s);
+cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const double *plain,
+                       void *stored, cudaStream_t s);
+cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const void *stored,
+                      double *plain, cudaStream_t s);
+cudaError_t rp_step(int lattice, const LaunchArgs &a);
 
 // Relaxation rates are validated on the host; omega_high_one records whether
 // every rate of order >= 3 equals 1 (enables the reduced collision).
@@ -30,7 +44,8 @@ struct LaunchArgs {
 // writes buf[(parity + k + 1) & 1]; its envelope pair is pairs[k * count + item].
 struct BatchItem {
     Geom g;
-    double *buf[2];
+    double *buf[2];     // population buffers (element type given by the batch's storage)
+    double rho_ref;     // reduced-precision storage: reference of the deviations
     int parity;
     int fkind, vkind;
     FieldDev F, V;
@@ -41,10 +56,24 @@ struct BatchItem {
 // with a uniform advecting velocity, that velocity).
 void batch_coef(int lattice, const double omega[9], BatchItem &item);
 
-// One launch advancing every item of a batch by one step (step index k).
-// first_block[i] = first block of item i (ascending); nblocks = total blocks.
-cudaError_t batch_step(int lattice, const BatchItem *items, const int *first_block, int count, int nblocks,
-                       const double2 *pairs, int k, cudaStream_t s);
+// Arguments of one batched launch (passed by value as a __grid_constant__
+// kernel parameter).  Item i of step k uses buf[(items[i].parity + parity) & 1]
+// as input and its envelope pair pairs[k * count + i], or inl[i] when pairs is
+// NULL (batches of at most kInlinePairs lattices: no per-step copy).
+constexpr int kInlinePairs = 32;
+struct BatchLaunch {
+    const BatchItem *items;
+    const int *first;  // first block of each item (ascending, first[0] = 0)
+    int count;
+    int k;
+    int parity;
+    const double2 *pairs;
+    double2 inl[kInlinePairs];
+};
+
+// One launch advancing every item of a batch by one step.
+cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s);
+cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, cudaStream_t s);
 int batch_blocks(const Geom &g);
 
 // One fused stream + collide step (pull form): fin -> fout.

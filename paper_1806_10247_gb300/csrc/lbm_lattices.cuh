@@ -3,6 +3,9 @@
 // the zeroth/first moments.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lbm_device.cuh"
 
 namespace lbmk {
@@ -14,6 +17,8 @@ struct LD2Q9 {
     __host__ __device__ static constexpr int ey(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
     __host__ __device__ static constexpr int ez(int) { return 0; }
     __host__ __device__ static constexpr int opp(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5); }
+    // rest-state populations per unit density (4/9, 1/9, 1/36)
+    __host__ __device__ static constexpr double w(int a) { return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
 };
 
 // D2Q5, Sec. 5 Eq. 34: 0 rest, 1 +x, 2 +y, 3 -x, 4 -y.
@@ -23,6 +28,8 @@ struct LD2Q5 {
     __host__ __device__ static constexpr int ey(int a) { return a == 2 ? 1 : (a == 4 ? -1 : 0); }
     __host__ __device__ static constexpr int ez(int) { return 0; }
     __host__ __device__ static constexpr int opp(int a) { return a == 0 ? 0 : ((a + 1) % 4) + 1; }
+    // rest-state populations per unit scalar (1/3, 1/6): moments 1, 0, 1/3
+    __host__ __device__ static constexpr double w(int a) { return a == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
 };
 
 // D3Q27 in tensor order: a = (ex+1) + 3 (ey+1) + 9 (ez+1); the opposite of a is 26 - a.
@@ -32,6 +39,9 @@ struct LD3Q27 {
     __host__ __device__ static constexpr int ey(int a) { return (a / 3) % 3 - 1; }
     __host__ __device__ static constexpr int ez(int a) { return a / 9 - 1; }
     __host__ __device__ static constexpr int opp(int a) { return 26 - a; }
+    // rest-state populations per unit density: product of (1/6, 2/3, 1/6) per axis
+    __host__ __device__ static constexpr double w1(int e) { return e == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+    __host__ __device__ static constexpr double w(int a) { return w1(ex(a)) * w1(ey(a)) * w1(ez(a)); }
 };
 
 // Source offset of the pull f_a(x) = f^p_a(x - e_a) (Eq. 22b / Eq. 40b) with
@@ -71,6 +81,39 @@ __device__ __forceinline__ void load_pulled(const double *__restrict__ fin, cons
             bool opp;
             int off = pull_off(g, x, y, z, ex, ey, ez, opp);
             f[a] = __ldg(fin + (opp ? L::opp(a) : a) * g.Np + off);
+        }
+    }
+}
+
+// Reduced-precision storage: conversions of a stored deviation to/from float.
+template <class T> struct Dev;
+template <> struct Dev<float> {
+    __device__ static float get(const float *p) { return __ldg(p); }
+    __device__ static float to_store(float v) { return v; }
+};
+template <> struct Dev<__half> {
+    __device__ static float get(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static __half to_store(float v) { return __float2half_rn(v); }
+};
+template <> struct Dev<__nv_bfloat16> {
+    __device__ static float get(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __nv_bfloat16 to_store(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Pulled deviations of a node (as float) from stored planes of type T.
+template <class L, class T>
+__device__ __forceinline__ void load_pulled_dev(const T *__restrict__ fin, const Geom &g, int x, int y, int z,
+                                                int i, float (&d)[L::Q])
+{
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+        if (ex == 0 && ey == 0 && ez == 0) {
+            d[a] = Dev<T>::get(fin + a * g.Np + i);
+        } else {
+            bool opp;
+            int off = pull_off(g, x, y, z, ex, ey, ez, opp);
+            d[a] = Dev<T>::get(fin + (opp ? L::opp(a) : a) * g.Np + off);
         }
     }
 }

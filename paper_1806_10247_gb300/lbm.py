@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 D2Q9, D3Q27, D2Q5_CDE = 1, 2, 3
-FP64 = 0
+FP64, FP32_DEV, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCE_BACK = 0, 1
 FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, -1, -2, -3, -4, -6
@@ -348,11 +348,11 @@ class Batch:
             pass
 
 
-def from_workload(w, stream=None, envelope_steps=None) -> Lattice:
+def from_workload(w, stream=None, envelope_steps=None, storage=FP64) -> Lattice:
     """Lattice set up (force/source, velocity, envelope, equilibrium) from a
     :class:`paper_1806_10247_gb300.workloads.Workload`."""
     lat = {1: D2Q9, 2: D3Q27, 3: D2Q5_CDE}[w.lattice]
-    L = Lattice(lat, w.shape, w.omega, wall=w.wall, stream=stream)
+    L = Lattice(lat, w.shape, w.omega, wall=w.wall, stream=stream, storage=storage)
     if w.tables is not None:
         if lat == D2Q5_CDE:
             L.set_source(tables=w.tables)

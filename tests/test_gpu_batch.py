@@ -55,8 +55,40 @@ def test_batch_equals_individual_steps_bitwise(kind):
         for G in solo:
             G.step(n)
     assert B.launch_count() == 8
+    diffs = []
     for a, b in zip(solo, grouped):
         assert a.t == b.t == 8
+        diffs.append(float(np.abs(a.get_populations() - b.get_populations()).max()))
+    # same arithmetic in both kernels; the compiler may fuse multiply-adds
+    # differently in the two (seen for D2Q9: ~1 ulp), so allow 4 ulps of f
+    assert max(diffs) <= 4 * 2.0 ** -53, diffs
+
+
+def test_batch_after_a_member_stepped_alone():
+    """A member stepped on its own falls out of parity lockstep, and a member
+    whose source changes gets a new descriptor; the batch must notice both."""
+    ws, fulls = _members("d2q5")
+    solo = [_make(w, f) for w, f in zip(ws, fulls)]
+    grouped = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(grouped)
+    new_src = [np.full((1, G.N), 1e-5) for G in grouped]
+    # grouped sequence
+    B.step(2)
+    grouped[1].step(1)
+    B.step(3)
+    grouped[2].set_source(full=new_src[2])
+    B.step(1)
+    # the same sequence, every lattice on its own
+    for G in solo:
+        G.step(2)
+    solo[1].step(1)
+    for G in solo:
+        G.step(3)
+    solo[2].set_source(full=new_src[2])
+    for G in solo:
+        G.step(1)
+    for a, b in zip(solo, grouped):
+        assert a.t == b.t
         assert np.array_equal(a.get_populations(), b.get_populations())
 
 

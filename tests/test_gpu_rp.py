@@ -1,0 +1,122 @@
+"""Reduced-precision storage (FP32 / FP16 / BF16 deviations from the rest
+state, FP32 moment arithmetic): error against the FP64 oracle per form.
+
+The FP32 form must stay within the 1e-4 relative l2 target; the measured
+errors of every form are written to gpurun_out/rp_errors.json (if that folder
+exists) so that they can be quoted."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1806_10247_gb300 import lbm
+from paper_1806_10247_gb300 import workloads as W
+from tests.gpu_helpers import oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = {"fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
+# relative l2 bounds per form (FP32: the stated target; 16-bit: measured
+# errors with margin, documented alongside the numbers)
+BOUND = {"fp32": 1e-4, "fp16": 5e-2, "bf16": 5e-1}
+RESULTS = {}
+
+
+def _record(key, val):
+    RESULTS[key] = val
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "rp_errors.json"), "w") as f:
+            json.dump(RESULTS, f, indent=1, sort_keys=True)
+
+
+def _l2(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+def _gpu(w, storage, steps):
+    G = lbm.from_workload(w, storage=storage)
+    G.step(steps)
+    return G
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
+def test_poiseuille_reduced_precision(form):
+    w = W.poiseuille()
+    R = oracle_from_workload(w)
+    R.run(10000)
+    _, ur = R.moments()
+    G = _gpu(w, STORAGES[form], 10000)
+    _, ug = G.moments()
+    err = _l2(ug[0], ur[0])
+    _record(f"poiseuille_d2q9_3x33_10k_{form}", err)
+    assert err <= BOUND[form], err
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
+def test_cde_reduced_precision(form):
+    c = W.cde_sweep_params(sizes=(64,))[0]
+    w = W.cde_workload(c)
+    R = oracle_from_workload(w)
+    R.run(c.T)
+    pr = R.moments() - 1.0
+    G = _gpu(w, STORAGES[form], c.T)
+    pg = G.moments() - 1.0
+    err = _l2(pg, pr)
+    _record(f"cde_d2q5_64_T{c.T}_{form}", err)
+    assert err <= BOUND[form], err
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16", "bf16"])
+def test_kolmogorov_reduced_precision(form):
+    w = W.kolmogorov(shape=(24, 24, 24))
+    R = oracle_from_workload(w)
+    R.run(300)
+    _, ur = R.moments()
+    G = _gpu(w, STORAGES[form], 300)
+    _, ug = G.moments()
+    err = _l2(ug, ur)
+    _record(f"kolmogorov_d3q27_24cubed_300_{form}", err)
+    assert err <= BOUND[form], err
+
+
+def test_fp32_cde_keeps_second_order():
+    """Closed-form error of the FP32 form over the 32/64/128 refinement: order ~2."""
+    from tests.test_oracle_d2q5 import _closed_form
+
+    errs = []
+    for c in W.cde_sweep_params(sizes=(32, 64, 128)):
+        w = W.cde_workload(c)
+        G = _gpu(w, lbm.FP32_DEV, c.T)
+        phi = G.moments().reshape(c.N, c.N) - 1.0
+        ref = _closed_form(c, c.T, c.N)
+        errs.append(_l2(phi, ref))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    _record("cde_fp32_closed_form_errors", errs)
+    _record("cde_fp32_orders", orders)
+    assert all(abs(o - 2.0) < 0.2 for o in orders), (errs, orders)
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16"])
+def test_reduced_precision_batch_and_checkpoint(form):
+    ws = [W.cde_workload(c) for c in W.cde_sweep_params(sizes=(32, 64))]
+    solo = [lbm.from_workload(w, storage=STORAGES[form]) for w in ws]
+    grp = [lbm.from_workload(w, storage=STORAGES[form]) for w in ws]
+    B = lbm.Batch(grp)
+    B.step(7)
+    for G in solo:
+        G.step(7)
+    for a, b in zip(solo, grp):
+        assert np.abs(a.get_populations() - b.get_populations()).max() < 1e-6
+    # checkpoint: restoring f(t) and stepping on equals stepping on
+    f = grp[1].get_populations()
+    C = lbm.from_workload(ws[1], storage=STORAGES[form])
+    C.set_populations(f, step=grp[1].t)
+    assert np.abs(C.get_populations() - f).max() < 1e-6
+    r = grp[1].reduce()
+    assert abs(r[0] - ws[1].nodes) < 1e-6 * ws[1].nodes
+    s = grp[1].reduce_sums_noalloc()
+    assert np.allclose(s, r[:4], rtol=1e-12, atol=1e-12)
