@@ -209,6 +209,74 @@ def config_block(wl, name, storage="fp64", elem=8):
     return c
 
 
+def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
+    """The metric's second half: wall time to the solution criterion.
+    * config 1 (Poiseuille D2Q9 3 x 33): steps until max |u(t) - u(t-100)| < 1e-12
+      (checked every 100 steps with lbm_reduce), and the l2 error of the final
+      profile against the parabola of Sec. 6.1;
+    * config 2 (scalar sweep): every member run to its T_N, l2 error against the
+      closed form and the convergence order over the sweep."""
+    codes = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV}
+    out = {}
+    for st in storages:
+        w = W.poiseuille()
+        L = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[st])
+        L.reduce()
+        torch_sync(stream)
+        t0 = time.perf_counter()
+        steps, du = 0, float("inf")
+        while steps < 200000:
+            L.step(100)
+            steps += 100
+            du = L.reduce()[4]
+            if du < 1e-12:
+                break
+        sec = time.perf_counter() - t0
+        _, u = L.moments()
+        ua = np.tile(W.poiseuille_parabola(w.shape[1], w.meta["tau"], w.meta["Fx"])[:, None], (1, w.shape[0]))
+        l2 = float(np.sqrt(np.sum((u[0] - ua.reshape(-1)) ** 2) / np.sum(ua ** 2)))
+        out[f"poiseuille_{st}"] = {"steps": steps, "seconds": sec, "max_du": du, "l2_vs_parabola": l2,
+                                   "criterion": "max |u(t) - u(t-100)| < 1e-12"}
+        L.close()
+        cases = W.cde_sweep_params()
+        errs, total = [], 0.0
+        for c in cases:
+            wc = W.cde_workload(c)
+            G = lbm.from_workload(wc, stream=stream.cuda_stream, envelope_steps=c.T + 2, storage=codes[st])
+            torch_sync(stream)
+            t0 = time.perf_counter()
+            G.step(c.T)
+            G.sync()
+            total += time.perf_counter() - t0
+            phi = G.moments().reshape(c.N, c.N) - 1.0
+            ref = W.cde_closed_form(c, c.T)
+            errs.append(float(np.sqrt(np.sum((phi - ref) ** 2) / np.sum(ref ** 2))))
+            G.close()
+        orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+        out[f"cde_sweep_{st}"] = {"seconds": total, "steps": [c.T for c in cases],
+                                  "l2_vs_closed_form": errs, "orders": orders}
+    return out
+
+
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the slowest rank's time decides)."""
+    import torch
+
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, nodes_per_rank, steps, max_ms):
+    """Node updates of all ranks (one independent workload copy each) per
+    second of the slowest rank, in MLUPS."""
+    return world * nodes_per_rank * steps / (max_ms * 1e-3) / 1e6
+
+
+def torch_sync(stream):
+    stream.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,11 +288,13 @@ def main():
                     help="population storage: fp64, or fp32/fp16/bf16 deviations with FP32 arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no minimum warm-up time, no e2e, no CPU baseline")
     args = ap.parse_args()
     if args.profile:
         args.no_cpu_baseline = True
+        args.no_tts = True
     args.warmup = max(args.warmup, 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -296,14 +366,12 @@ def main():
     kern_ms = step_ms  # one launch per step: the batched D2Q5 step kernel
     total_ms = sum(step_ms)
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, "cuda")
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
 
-    value = world * nodes * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, nodes, args.steps, total_ms)
 
     # roofline of the dominant (only) kernel: the batched D2Q5 step over the sweep
     hbm, hbm_src = load_peaks()
@@ -369,6 +437,13 @@ def main():
     except Exception as exc:  # pragma: no cover - reported, not hidden
         e2e = {"value": None, "error": repr(exc)}
 
+    tts = None
+    if not args.no_tts and args.workload == "cde_sweep":
+        try:
+            tts = time_to_solution(lbm, stream)
+        except Exception as exc:  # pragma: no cover - reported, not hidden
+            tts = {"error": repr(exc)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and state_bytes(wl) < (1 << 30):  # FP64 oracle
         upd, sec, threads, done = time_oracle(wl, None, budget_s=args.cpu_budget)
@@ -381,7 +456,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "fp64" else "f32",
             "data": "synthetic", "config": config_block(wl, wname, args.storage, elem), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "time_to_solution": tts,
         }
         print(json.dumps(line), flush=True)
     if dist:

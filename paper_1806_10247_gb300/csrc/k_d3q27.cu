@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(kBlock)
 k_batch(const __grid_constant__ BatchLaunch L)
 {
     const int it = batch_find(L.first, L.count);
-    const BatchItem &B = L.items[it];
+    __shared__ BatchItem B;
+    stage_to_shared(B, L.items[it]);
+    __syncthreads();
     const Geom g = B.g;
     const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
     if (i >= g.N) return;

@@ -326,8 +326,11 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
     along<0>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
 }
 
+// 4 resident blocks per SM (<= 64 registers): the reduced-precision D3Q27
+// step is memory-bound, so occupancy to cover load latency matters more than
+// registers.
 template <class T, int FK>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 4)
 k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, double apre, double apost,
          Rates27f w, float rref)
 {
@@ -357,7 +360,9 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ BatchLaunch L)
 {
     const int it = batch_find(L.first, L.count);
-    const BatchItem &B = L.items[it];
+    __shared__ BatchItem B;
+    stage_to_shared(B, L.items[it]);
+    __syncthreads();
     const Geom g = B.g;
     const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -388,7 +393,9 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ BatchLaunch L)
 {
     const int it = batch_find(L.first, L.count);
-    const BatchItem &B = L.items[it];
+    __shared__ BatchItem B;
+    stage_to_shared(B, L.items[it]);
+    __syncthreads();
     const Geom g = B.g;
     const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -424,10 +431,12 @@ __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ Batch
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_batch27(const __grid_constant__ BatchLaunch L)
+__global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ BatchLaunch L)
 {
     const int it = batch_find(L.first, L.count);
-    const BatchItem &B = L.items[it];
+    __shared__ BatchItem B;
+    stage_to_shared(B, L.items[it]);
+    __syncthreads();
     const Geom g = B.g;
     const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
     if (i >= g.N) return;

@@ -68,10 +68,24 @@ __device__ __forceinline__ int pull_off(const Geom &g, int x, int y, int z, int 
     return sx + g.nx * (sy + g.ny * sz);
 }
 
+// A node none of whose pull sources leaves the domain: every population comes
+// from the fixed offset -(ex + nx ey + nx ny ez), no wrap or wall test needed.
+__device__ __forceinline__ bool interior(const Geom &g, int x, int y, int z)
+{
+    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && (g.nz == 1 || (z > 0 && z < g.nz - 1));
+}
+
 template <class L>
 __device__ __forceinline__ void load_pulled(const double *__restrict__ fin, const Geom &g, int x, int y,
                                             int z, int i, double (&f)[L::Q])
 {
+    if (interior(g, x, y, z)) {
+        const int sy = g.nx, sz = g.nx * g.ny;
+#pragma unroll
+        for (int a = 0; a < L::Q; a++)
+            f[a] = __ldg(fin + a * g.Np + i - (L::ex(a) + L::ey(a) * sy + L::ez(a) * sz));
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
@@ -91,12 +105,20 @@ template <> struct Dev<float> {
     __device__ static float get(const float *p) { return __ldg(p); }
     __device__ static float to_store(float v) { return v; }
 };
+// 16-bit values are loaded as plain unsigned shorts (a native read-only load
+// the compiler can schedule freely) and reinterpreted.
 template <> struct Dev<__half> {
-    __device__ static float get(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static float get(const __half *p)
+    {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
     __device__ static __half to_store(float v) { return __float2half_rn(v); }
 };
 template <> struct Dev<__nv_bfloat16> {
-    __device__ static float get(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static float get(const __nv_bfloat16 *p)
+    {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
+    }
     __device__ static __nv_bfloat16 to_store(float v) { return __float2bfloat16_rn(v); }
 };
 
@@ -105,6 +127,13 @@ template <class L, class T>
 __device__ __forceinline__ void load_pulled_dev(const T *__restrict__ fin, const Geom &g, int x, int y, int z,
                                                 int i, float (&d)[L::Q])
 {
+    if (interior(g, x, y, z)) {
+        const int sy = g.nx, sz = g.nx * g.ny;
+#pragma unroll
+        for (int a = 0; a < L::Q; a++)
+            d[a] = Dev<T>::get(fin + a * g.Np + i - (L::ex(a) + L::ey(a) * sy + L::ez(a) * sz));
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
@@ -134,6 +163,18 @@ __device__ __forceinline__ void zeroth_first(const double (&f)[L::Q], double &m0
         if (L::ez(a) == 1) j[2] += f[a];
         if (L::ez(a) == -1) j[2] -= f[a];
     }
+}
+
+// Copy an object into shared memory cooperatively (word by word); the caller
+// synchronises.  Used to give every thread of a block one copy of its batch
+// descriptor without repeated global loads.
+template <class Obj>
+__device__ __forceinline__ void stage_to_shared(Obj &dst, const Obj &src)
+{
+    static_assert(sizeof(Obj) % 4 == 0, "word copy");
+    const unsigned *s = reinterpret_cast<const unsigned *>(&src);
+    unsigned *d = reinterpret_cast<unsigned *>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(Obj) / 4); k += blockDim.x) d[k] = __ldg(s + k);
 }
 
 // Item of a batched launch that owns this block: the last i with

@@ -102,6 +102,32 @@ def cde_sweep_params(seed: int = SEED, sizes=(32, 64, 128, 256, 512), T32: int =
     return out
 
 
+def cde_closed_form(c: CDECase, t: float) -> np.ndarray:
+    """Exact solution psi = phi - phi0 of the convection-diffusion equation
+    (Sec. 5, Eq. 33) on the periodic N x N square for the manufactured source
+    S = A sin(kx) sin(ky) e^{-lambda t}, uniform velocity and psi(0) = 0, as an
+    [N][N] array (y, x).  Per Fourier mode kappa:
+    psi_hat(t) = S_hat (e^{-lambda t} - e^{-sigma t}) / (sigma - lambda),
+    sigma = i kappa.u + D |kappa|^2; sin(kx) sin(ky) = (cos k(x-y) - cos k(x+y))/2."""
+    N = c.N
+    k = 2.0 * math.pi / N
+    x = np.arange(N)[None, :]
+    y = np.arange(N)[:, None]
+    out = np.zeros((N, N))
+    for sgn, kap in ((+1, (k, -k)), (-1, (k, k))):
+        sigma = 1j * (kap[0] * c.ux + kap[1] * c.uy) + c.D * (kap[0] ** 2 + kap[1] ** 2)
+        R = (math.exp(-c.lam * t) - np.exp(-sigma * t)) / (sigma - c.lam)
+        out += sgn * 0.5 * c.A * np.real(R * np.exp(1j * (kap[0] * x + kap[1] * y)))
+    return out
+
+
+def poiseuille_parabola(ny: int, tau: float, Fx: float) -> np.ndarray:
+    """Analytic channel profile with walls at y = -1/2 and ny - 1/2 (Sec. 6.1)."""
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(ny, dtype=np.float64)
+    return Fx / (2.0 * nu) * (y + 0.5) * (ny - 0.5 - y)
+
+
 def cde_workload(c: CDECase, phi0: float = 1.0) -> Workload:
     N = c.N
     x = np.arange(N, dtype=np.float64)

@@ -103,20 +103,7 @@ def test_diffusion_rate_and_advection_speed():
 
 
 def _closed_form(c, t, N):
-    """Eq. 33 on the periodic square with S = A sin(kx) sin(ky) e^{-lambda t},
-    uniform u and phi(0) = 1: per Fourier mode
-    phi_hat(t) = S_hat (e^{-lambda t} - e^{-sigma t}) / (sigma - lambda),
-    sigma = i kappa.u + D |kappa|^2."""
-    k = 2 * math.pi / N
-    x = np.arange(N)[None, :]
-    y = np.arange(N)[:, None]
-    out = np.zeros((N, N))
-    # sin(kx) sin(ky) = (cos(k(x-y)) - cos(k(x+y))) / 2
-    for sgn, kap in ((+1, (k, -k)), (-1, (k, k))):
-        sigma = 1j * (kap[0] * c.ux + kap[1] * c.uy) + c.D * (kap[0] ** 2 + kap[1] ** 2)
-        R = (math.exp(-c.lam * t) - np.exp(-sigma * t)) / (sigma - c.lam)
-        out += sgn * 0.5 * c.A * np.real(R * np.exp(1j * (kap[0] * x + kap[1] * y)))
-    return out
+    return W.cde_closed_form(c, t)
 
 
 def _run_cde(c):
