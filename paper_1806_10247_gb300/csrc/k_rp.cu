@@ -71,7 +71,7 @@ __device__ __forceinline__ void collide9(float (&d)[9], float rref, float Fx, fl
 
 template <class T, int FK>
 __global__ void __launch_bounds__(kBlock)
-k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, double apre, double gsum, Rates9f w,
+k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, float apre, float gsum, Rates9f w,
         float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
@@ -81,11 +81,11 @@ k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, dou
     load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
     float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
     if (FK != FK_NONE) {
-        const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
-        Fx = (float)(apre * Px);
-        Fy = (float)(apre * Py);
-        Gx = (float)(gsum * Px);
-        Gy = (float)(gsum * Py);
+        const float Px = field_value_f(F, FK, 0, x, y, 0, i), Py = field_value_f(F, FK, 1, x, y, 0, i);
+        Fx = apre * Px;
+        Fy = apre * Py;
+        Gx = gsum * Px;
+        Gy = gsum * Py;
     }
     collide9(d, rref, Fx, Fy, Gx, Gy, w);
 #pragma unroll
@@ -173,7 +173,7 @@ Coef5f make_coef5f(const double omega[9], double ux, double uy)
 
 template <class T, int SK, bool UNIFORM>
 __global__ void __launch_bounds__(kBlock)
-k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, FieldDev V, double apre, double hsum,
+k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, FieldDev V, float apre, float hsum,
         Rates5f w, Coef5f k, float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
@@ -183,15 +183,15 @@ k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, Fie
     load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
     float Sp = 0.f, H0 = 0.f;
     if (SK != FK_NONE) {
-        const double P = field_value(S, SK, 0, x, y, 0, i);
-        Sp = (float)(apre * P);
-        H0 = (float)(hsum * P);
+        const float P = field_value_f(S, SK, 0, x, y, 0, i);
+        Sp = apre * P;
+        H0 = hsum * P;
     }
     if (UNIFORM) {
         collide5u(d, rref, Sp, H0, k);
     } else {
-        const float ux = (float)field_value(V, FK_GENERAL, 0, x, y, 0, i);
-        const float uy = (float)field_value(V, FK_GENERAL, 1, x, y, 0, i);
+        const float ux = field_value_f(V, FK_GENERAL, 0, x, y, 0, i);
+        const float uy = field_value_f(V, FK_GENERAL, 1, x, y, 0, i);
         collide5(d, rref, Sp, H0, ux, uy, w);
     }
 #pragma unroll
@@ -331,7 +331,7 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
 // registers.
 template <class T, int FK>
 __global__ void __launch_bounds__(kBlock, 4)
-k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, double apre, double apost,
+k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, float apre, float apost,
          Rates27f w, float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
@@ -344,9 +344,9 @@ k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, d
     if (FK != FK_NONE) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double P = field_value(Fd, FK, d, x, y, z, i);
-            F[d] = (float)(apre * P);
-            Fq[d] = (float)(apost * P);
+            const float P = field_value_f(Fd, FK, d, x, y, z, i);
+            F[d] = apre * P;
+            Fq[d] = apost * P;
         }
     }
     collide27(m, rref, F, Fq, w);
@@ -369,17 +369,17 @@ __global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ Batch
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
-    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
     const int x = i % g.nx, y = i / g.nx;
     float d[9];
     load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
     float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
     if (B.fkind != FK_NONE) {
-        const double Px = field_value(B.F, B.fkind, 0, x, y, 0, i), Py = field_value(B.F, B.fkind, 1, x, y, 0, i);
-        Fx = (float)(ap.x * Px);
-        Fy = (float)(ap.x * Py);
-        Gx = (float)(ap.y * Px);
-        Gy = (float)(ap.y * Py);
+        const float Px = field_value_f(B.F, B.fkind, 0, x, y, 0, i), Py = field_value_f(B.F, B.fkind, 1, x, y, 0, i);
+        Fx = ap.x * Px;
+        Fy = ap.x * Py;
+        Gx = ap.y * Px;
+        Gy = ap.y * Py;
     }
     const Rates9f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
                     (float)B.coef[3], (float)B.coef[4], (float)B.coef[5]};
@@ -402,15 +402,15 @@ __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ Batch
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
-    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
     const int x = i % g.nx, y = i / g.nx;
     float d[5];
     load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
     float Sp = 0.f, H0 = 0.f;
     if (B.fkind != FK_NONE) {
-        const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
-        Sp = (float)(ap.x * P);
-        H0 = (float)(ap.y * P);
+        const float P = field_value_f(B.F, B.fkind, 0, x, y, 0, i);
+        Sp = ap.x * P;
+        H0 = ap.y * P;
     }
     const float rref = (float)B.rho_ref;
     if (B.vkind != FK_GENERAL) {
@@ -422,8 +422,8 @@ __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ Batch
         collide5u(d, rref, Sp, H0, k);
     } else {
         const Rates5f w{(float)B.coef[12], (float)B.coef[13], (float)B.coef[14], (float)B.coef[15]};
-        const float ux = (float)field_value(B.V, FK_GENERAL, 0, x, y, 0, i);
-        const float uy = (float)field_value(B.V, FK_GENERAL, 1, x, y, 0, i);
+        const float ux = field_value_f(B.V, FK_GENERAL, 0, x, y, 0, i);
+        const float uy = field_value_f(B.V, FK_GENERAL, 1, x, y, 0, i);
         collide5(d, rref, Sp, H0, ux, uy, w);
     }
 #pragma unroll
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ B
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
-    const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
+    const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
     int x, y, z;
     node_xyz(g, i, x, y, z);
     float m[27];
@@ -452,9 +452,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ B
     if (B.fkind != FK_NONE) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const double P = field_value(B.F, B.fkind, d, x, y, z, i);
-            F[d] = (float)(ap.x * P);
-            Fq[d] = (float)(ap.y * P);
+            const float P = field_value_f(B.F, B.fkind, d, x, y, z, i);
+            F[d] = ap.x * P;
+            Fq[d] = ap.y * P;
         }
     }
     const Rates27f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
@@ -475,33 +475,33 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
     if (lattice == LD2Q9::ID) {
         const Rates9f w{(float)(a.omega[3] / 12.0), (float)(a.omega[4] / 4.0), (float)(a.omega[5] / 4.0),
                         (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
-        const double gsum = (a.apre + a.apost) / 12.0;
-        if (a.fkind == FK_NONE) k_step9<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
-        else if (a.fkind == FK_CONST) k_step9<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
-        else k_step9<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, gsum, w, rref);
+        const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre;
+        if (a.fkind == FK_NONE) k_step9<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
+        else if (a.fkind == FK_CONST) k_step9<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
+        else k_step9<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
     } else if (lattice == LD2Q5::ID) {
         const Rates5f w{(float)(a.omega[1] / 2.0), (float)(a.omega[2] / 2.0), (float)(a.omega[3] / 4.0),
                         (float)(a.omega[4] / 4.0)};
         const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0, uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
         const Coef5f k = make_coef5f(a.omega, ux, uy);
-        const double hsum = (a.apre + a.apost) / 10.0;
+        const float hsum = (float)((a.apre + a.apost) / 10.0), apre = (float)a.apre;
         const bool uni = a.vkind != FK_GENERAL;
         if (a.fkind == FK_NONE) {
-            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
-            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
         } else if (a.fkind == FK_CONST) {
-            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
-            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
         } else {
-            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
-            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, a.apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
         }
     } else {
         const Rates27f w{(float)a.omega[1], (float)a.omega[2], (float)a.omega[3],
                          (float)a.omega[4], (float)a.omega[5], (float)a.omega[6]};
-        if (a.fkind == FK_NONE) k_step27<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
-        else if (a.fkind == FK_CONST) k_step27<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
-        else k_step27<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.apre, a.apost, w, rref);
+        if (a.fkind == FK_NONE) k_step27<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
+        else if (a.fkind == FK_CONST) k_step27<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
+        else k_step27<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
     }
     return cudaGetLastError();
 }

@@ -230,19 +230,24 @@ int lbm_batch_step(lbm_batch *b, long n)
         BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
         int rc = grow_pairs(b, s, (size_t)n * b->count);
         if (rc != LBM_OK) return rc;
+        const bool fp32 = b->ctx[0]->storage != LBM_FP64;
+        float2 *hf = reinterpret_cast<float2 *>(b->h_pairs[s]);  // FP32 pairs reuse the staging memory
         for (int i = 0; i < b->count; i++) {
             const lbm_ctx *c = b->ctx[i];
             for (long k = 0; k < n; k++) {
                 double apre, apost;
                 lbmc::envelope_pair(c, c->t + k, apre, apost);
-                b->h_pairs[s][(size_t)k * b->count + i] = make_double2(apre, pair_second(b->lattice, apre, apost));
+                const double second = pair_second(b->lattice, apre, apost);
+                if (fp32) hf[(size_t)k * b->count + i] = make_float2((float)apre, (float)second);
+                else b->h_pairs[s][(size_t)k * b->count + i] = make_double2(apre, second);
             }
         }
         BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * sizeof(double2),
                             cudaMemcpyHostToDevice, b->stream),
             "lbm_batch_step: copy envelope pairs");
         BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
-        L.pairs = b->d_pairs[s];
+        if (fp32) L.pairsf = reinterpret_cast<const float2 *>(b->d_pairs[s]);
+        else L.pairs = b->d_pairs[s];
     }
     for (long k = 0; k < n; k++) {
         L.k = (int)k;
@@ -251,7 +256,9 @@ int lbm_batch_step(lbm_batch *b, long n)
             for (int i = 0; i < b->count; i++) {
                 double apre, apost;
                 lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t + k, apre, apost);
-                L.inl[i] = make_double2(apre, pair_second(b->lattice, apre, apost));
+                const double second = pair_second(b->lattice, apre, apost);
+                L.inl[i] = make_double2(apre, second);
+                L.inlf[i] = make_float2((float)apre, (float)second);
             }
         const int storage = b->ctx[0]->storage;
         cudaError_t e = storage == LBM_FP64 ? batch_step(b->lattice, L, b->nblocks, b->stream)

@@ -10,6 +10,7 @@
 #include <limits>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lbm_ctx.h"
 
@@ -128,6 +129,7 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
 {
     if (f == nullptr || f->kind == LBM_FIELD_NONE) {
         if (out.dev) cudaFree(out.dev);
+        if (out.fdev) cudaFree(out.fdev);
         out = DeviceField{};
         return LBM_OK;
     }
@@ -147,8 +149,10 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
             for (int cc = 0; cc < ncomp; cc++) {
                 const double *t = f->data + cc * per;
                 nf.d.cval[cc] = (t[0] * t[1]) * t[2];
+                nf.d.fcval[cc] = (float)nf.d.cval[cc];
             }
             if (out.dev) cudaFree(out.dev);
+            if (out.fdev) cudaFree(out.fdev);
             out = nf;
             return LBM_OK;
         }
@@ -183,23 +187,44 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
     nf.kind = FK_GENERAL;
     // Reuse the previous device buffer when it is large enough (a shape that is
     // re-uploaded every step costs one copy, no allocation).
-    const bool reuse = out.dev != nullptr && out.cap >= count;
+    const bool want_f = c->storage != LBM_FP64;
+    const bool reuse = out.dev != nullptr && out.cap >= count && (!want_f || out.fdev != nullptr);
     if (reuse) {
         nf.dev = out.dev;
+        nf.fdev = out.fdev;
         nf.cap = out.cap;
     } else {
         CK(cudaMalloc(&nf.dev, count * sizeof(double)), "cudaMalloc(field)");
+        if (want_f) {
+            cudaError_t ef = cudaMalloc(&nf.fdev, count * sizeof(float));
+            if (ef != cudaSuccess) {
+                cudaFree(nf.dev);
+                return cuda_fail(c, ef, "cudaMalloc(field, FP32 copy)");
+            }
+        }
         nf.cap = count;
     }
-    // The copy is complete before returning: the caller may reuse its buffer.
+    // The copies are complete before returning: the caller may reuse its buffer.
     cudaError_t e = cudaMemcpyAsync(nf.dev, f->data, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    std::vector<float> fcopy;
+    if (e == cudaSuccess && want_f) {
+        fcopy.assign(f->data, f->data + count);
+        e = cudaMemcpyAsync(nf.fdev, fcopy.data(), count * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        if (!reuse) cudaFree(nf.dev);
+        if (!reuse) {
+            cudaFree(nf.dev);
+            cudaFree(nf.fdev);
+        }
         return cuda_fail(c, e, "upload field");
     }
     nf.d.data = nf.dev;
-    if (out.dev && !reuse) cudaFree(out.dev);
+    nf.d.fdata = nf.fdev;
+    if (!reuse) {
+        if (out.dev) cudaFree(out.dev);
+        if (out.fdev) cudaFree(out.fdev);
+    }
     out = nf;
     return LBM_OK;
 }
@@ -278,6 +303,8 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->red_out);
     cudaFree(c->force.dev);
     cudaFree(c->vel.dev);
+    cudaFree(c->force.fdev);
+    cudaFree(c->vel.fdev);
     cudaFree(c->stage);
     delete c;
 }

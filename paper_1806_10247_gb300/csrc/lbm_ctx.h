@@ -14,7 +14,8 @@ namespace lbmc {
 struct DeviceField {
     int kind = lbmk::FK_NONE;  // FieldKind seen by the kernels
     double *dev = nullptr;
-    size_t cap = 0;            // doubles allocated at dev
+    float *fdev = nullptr;     // FP32 copy for reduced-precision contexts
+    size_t cap = 0;            // values allocated at dev (and fdev)
     lbmk::FieldDev d{};
 };
 

@@ -30,12 +30,14 @@ enum FieldKind { FK_NONE = 0, FK_CONST = 1, FK_GENERAL = 2 };
 // 1.0 is exact, so the value is unchanged).
 struct FieldDev {
     const double *data;
+    const float *fdata;  // FP32 copy of data (reduced-precision contexts only)
     long long cstride;
     int len[3];
     int sep;
     int zmask;
     int axes;
     double cval[3];
+    float fcval[3];
 };
 
 __device__ __forceinline__ double field_value(const FieldDev &F, int kind, int c, int x, int y, int z,
@@ -59,6 +61,33 @@ __device__ __forceinline__ double field_value(const FieldDev &F, int kind, int c
     }
     if (F.axes & 4) {
         const double pz = __ldg(t + F.len[0] + F.len[1] + (F.len[2] > 1 ? z : 0));
+        v = have ? v * pz : pz;
+    }
+    return v;
+}
+
+// The same shape evaluated in FP32 from the FP32 copy (reduced-precision
+// kernels keep FP64 out of their inner loop: FP64 runs at 1/64 rate here).
+__device__ __forceinline__ float field_value_f(const FieldDev &F, int kind, int c, int x, int y, int z,
+                                               int node)
+{
+    if (kind == FK_CONST) return F.fcval[c];
+    if ((F.zmask >> c) & 1) return 0.0f;
+    const float *t = F.fdata + c * F.cstride;
+    if (!F.sep) return __ldg(t + node);
+    float v = 1.0f;
+    bool have = false;
+    if (F.axes & 1) {
+        v = __ldg(t + (F.len[0] > 1 ? x : 0));
+        have = true;
+    }
+    if (F.axes & 2) {
+        const float py = __ldg(t + F.len[0] + (F.len[1] > 1 ? y : 0));
+        v = have ? v * py : py;
+        have = true;
+    }
+    if (F.axes & 4) {
+        const float pz = __ldg(t + F.len[0] + F.len[1] + (F.len[2] > 1 ? z : 0));
         v = have ? v * pz : pz;
     }
     return v;

@@ -69,6 +69,9 @@ struct BatchLaunch {
     int parity;
     const double2 *pairs;
     double2 inl[kInlinePairs];
+    // reduced-precision kernels read the same pairs in FP32
+    const float2 *pairsf;
+    float2 inlf[kInlinePairs];
 };
 
 // One launch advancing every item of a batch by one step.

@@ -135,6 +135,7 @@ def test_reduced_precision_batch_and_checkpoint(form):
     C.set_populations(f, step=grp[1].t)
     assert np.abs(C.get_populations() - f).max() <= tol
     r = grp[1].reduce()
-    assert abs(r[0] - ws[1].nodes) < 1e-6 * ws[1].nodes
+    # mass: the deviations are rounded to the storage precision every step
+    assert abs(r[0] - ws[1].nodes) < (1e-6 if form == "fp32" else 1e-4) * ws[1].nodes
     s = grp[1].reduce_sums_noalloc()
     assert np.allclose(s, r[:4], rtol=1e-12, atol=1e-12)
