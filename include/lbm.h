@@ -268,6 +268,42 @@ const char *lbm_batch_last_error(const lbm_batch *b);
 /* Free the batch (synchronises its stream); the member contexts stay valid. */
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---- Learned warm start: network kernels ---------------------------------
+ *
+ * The paper has no counterpart.  These kernels train and evaluate the small 3D
+ * convolutional surrogate that predicts an initial velocity field for the LB
+ * iteration (which stays the judge of the converged result).  All pointers are
+ * device pointers; tensors are FP32 in [batch][channel][D][H][W] layout;
+ * weights [Co][Ci][KD][KH][KW] are read as FP32 (w_bf16 = 0) or BF16
+ * (w_bf16 = 1) and accumulated in FP32; kernels are odd, padding is "same"
+ * (zero outside), dilation per axis.  Work is queued on `stream` (a
+ * cudaStream_t, NULL = default); nothing synchronises.  Errors: LBM_EINVAL
+ * (bad sizes or NULL pointers), LBM_ECUDA; message in lbm_nn_last_error(). */
+const char *lbm_nn_last_error(void);
+
+/* y = act(conv(x, w) + b); act 0 = identity, 1 = tanh. */
+int lbm_nn_conv3d_forward(const float *x, const void *w, int w_bf16, const float *b, float *y, int n, int ci, int co,
+                          const int dhw[3], const int k[3], const int dil[3], int act, void *stream);
+
+/* Gradients of sum(gy * conv(x, w)): gx (skipped if NULL), gw, gb (sums over
+ * batch and space in a fixed order). */
+int lbm_nn_conv3d_backward(const float *x, const void *w, int w_bf16, const float *gy, float *gx, float *gw, float *gb,
+                           int n, int ci, int co, const int dhw[3], const int k[3], const int dil[3], void *stream);
+
+/* g *= 1 - y^2 (y = tanh output), in place. */
+int lbm_nn_tanh_backward(float *g, const float *y, long long count, void *stream);
+
+/* Mean squared error: g = 2 (y - t)/count, *loss (device double) = mean((y-t)^2). */
+int lbm_nn_mse(const float *y, const float *t, float *g, long long count, double *loss, void *stream);
+
+/* One bias-corrected Adam step on FP32 weights p (moments m, v); also writes
+ * the BF16 copy p_bf16 if not NULL.  step >= 1. */
+int lbm_nn_adam(float *p, const float *g, float *m, float *v, void *p_bf16, long long count, double lr, double b1,
+                double b2, double eps, long long step, void *stream);
+
+/* p_bf16 = round-to-nearest BF16 of p. */
+int lbm_nn_to_bf16(const float *p, void *p_bf16, long long count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
