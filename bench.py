@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="run the learned warm-start study (duct sections) instead of the throughput bench")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no minimum warm-up time, no e2e, no CPU baseline")
     args = ap.parse_args()
@@ -310,6 +312,14 @@ def main():
     from paper_1806_10247_gb300 import lbm
 
     torch.cuda.set_device(local)
+    if args.warmstart:
+        from paper_1806_10247_gb300 import surrogate
+
+        res = surrogate.study()
+        if rank == 0:
+            print(json.dumps({"metric": "steps and wall time to the 1e-10 residual, warm vs zero start",
+                              "config": {"workload": "duct_section_warmstart_d3q27"}, "result": res}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist_mod

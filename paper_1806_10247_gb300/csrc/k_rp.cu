@@ -381,9 +381,8 @@ __global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ Batch
         Gx = ap.y * Px;
         Gy = ap.y * Py;
     }
-    const Rates9f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
-                    (float)B.coef[3], (float)B.coef[4], (float)B.coef[5]};
-    collide9(d, (float)B.rho_ref, Fx, Fy, Gx, Gy, w);
+    const Rates9f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
+    collide9(d, B.frho_ref, Fx, Fy, Gx, Gy, w);
 #pragma unroll
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
 }
@@ -412,16 +411,16 @@ __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ Batch
         Sp = ap.x * P;
         H0 = ap.y * P;
     }
-    const float rref = (float)B.rho_ref;
+    const float rref = B.frho_ref;
     if (B.vkind != FK_GENERAL) {
         Coef5f k;
-        k.A1 = (float)B.coef[0]; k.c1 = (float)B.coef[1]; k.A2 = (float)B.coef[2]; k.c2 = (float)B.coef[3];
-        k.P3 = (float)B.coef[4]; k.X3 = (float)B.coef[5]; k.Y3 = (float)B.coef[6]; k.S3 = (float)B.coef[7];
-        k.P4 = (float)B.coef[8]; k.X4 = (float)B.coef[9]; k.Y4 = (float)B.coef[10]; k.D4 = (float)B.coef[11];
-        k.Q3 = (float)(B.coef[4] + (2.0 / 3.0) * B.coef[7]);
+        k.A1 = B.fcoef[0]; k.c1 = B.fcoef[1]; k.A2 = B.fcoef[2]; k.c2 = B.fcoef[3];
+        k.P3 = B.fcoef[4]; k.X3 = B.fcoef[5]; k.Y3 = B.fcoef[6]; k.S3 = B.fcoef[7];
+        k.P4 = B.fcoef[8]; k.X4 = B.fcoef[9]; k.Y4 = B.fcoef[10]; k.D4 = B.fcoef[11];
+        k.Q3 = B.fcoef[16];
         collide5u(d, rref, Sp, H0, k);
     } else {
-        const Rates5f w{(float)B.coef[12], (float)B.coef[13], (float)B.coef[14], (float)B.coef[15]};
+        const Rates5f w{B.fcoef[12], B.fcoef[13], B.fcoef[14], B.fcoef[15]};
         const float ux = field_value_f(B.V, FK_GENERAL, 0, x, y, 0, i);
         const float uy = field_value_f(B.V, FK_GENERAL, 1, x, y, 0, i);
         collide5(d, rref, Sp, H0, ux, uy, w);
@@ -457,9 +456,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ B
             Fq[d] = ap.y * P;
         }
     }
-    const Rates27f w{(float)B.coef[0], (float)B.coef[1], (float)B.coef[2],
-                     (float)B.coef[3], (float)B.coef[4], (float)B.coef[5]};
-    collide27(m, (float)B.rho_ref, F, Fq, w);
+    const Rates27f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
+    collide27(m, B.frho_ref, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
 }

@@ -208,6 +208,9 @@ int lbm_batch_step(lbm_batch *b, long n)
             it.vkind = c->vel.kind;
             it.V = c->vel.d;
             batch_coef(c->lattice, c->omega, it);
+            for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
+            it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
+            it.frho_ref = (float)it.rho_ref;
             b->item_version[i] = c->version;
             b->item_buf0[i] = c->A;
         }

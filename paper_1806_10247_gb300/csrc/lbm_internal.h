@@ -50,6 +50,9 @@ struct BatchItem {
     int fkind, vkind;
     FieldDev F, V;
     double coef[16];  // lattice-specific collision coefficients (filled by batch_coef)
+    float fcoef[20];  // FP32 copies for the reduced-precision kernels (FP64 runs at 1/64 rate);
+                      // D2Q5: [16] holds P3 + (2/3) S3 of the uniform-velocity form
+    float frho_ref;
 };
 
 // Host: fill item.coef from the relaxation rates (and, for the scalar lattice

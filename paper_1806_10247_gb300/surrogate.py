@@ -88,9 +88,11 @@ class ConvNet:
             self.W.append(torch.tensor(w, dtype=torch.float32, device="cuda"))
             self.B.append(torch.zeros(co, dtype=torch.float32, device="cuda"))
             self.Wb.append(torch.empty(self.W[-1].shape, dtype=torch.bfloat16, device="cuda"))
-        for t in self.W + self.B:
-            self.m.append(torch.zeros_like(t))
-            self.v.append(torch.zeros_like(t))
+        # Adam moments, interleaved per layer: m[2l], v[2l] for W[l]; m[2l+1], v[2l+1] for B[l]
+        for w, b in zip(self.W, self.B):
+            for t in (w, b):
+                self.m.append(torch.zeros_like(t))
+                self.v.append(torch.zeros_like(t))
         self.step_count = 0
         self.refresh_bf16()
 
@@ -110,6 +112,8 @@ class ConvNet:
         acts = [x.contiguous()]
         h = acts[0]
         for li, (ci, co, k, dil, act) in enumerate(self.layers):
+            if h.dtype != self.torch.float32 or h.dim() != 5 or h.shape[1] != ci or not h.is_cuda:
+                raise ValueError(f"layer {li}: input {tuple(h.shape)} {h.dtype}, expected [N, {ci}, D, H, W] float32 CUDA")
             N, _, D, H, V = h.shape
             y = self.torch.empty((N, co, D, H, V), dtype=self.torch.float32, device="cuda")
             w, wflag = self._w(li)
@@ -123,6 +127,8 @@ class ConvNet:
         """MSE loss (float) and gradients (list of (gW, gB)) by the backward kernels."""
         torch = self.torch
         y, acts = self.forward(x)
+        if target.shape != y.shape or target.dtype != torch.float32:
+            raise ValueError(f"target {tuple(target.shape)} {target.dtype}, expected {tuple(y.shape)} float32")
         g = torch.empty_like(y)
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         _ck(_nn().lbm_nn_mse(_p(y), _p(target.contiguous()), _p(g), y.numel(), _p(loss), self.stream))
@@ -146,6 +152,13 @@ class ConvNet:
     def adam_step(self, grads, lr=2e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1
         for li, (gw, gb) in enumerate(grads):
+            # every buffer handed to a kernel must match the parameter it updates
+            for t in (gw, self.m[2 * li], self.v[2 * li], self.Wb[li]):
+                if t.numel() != self.W[li].numel():
+                    raise ValueError(f"layer {li}: buffer of {t.numel()} values for {self.W[li].numel()} weights")
+            for t in (gb, self.m[2 * li + 1], self.v[2 * li + 1]):
+                if t.numel() != self.B[li].numel():
+                    raise ValueError(f"layer {li}: buffer of {t.numel()} values for {self.B[li].numel()} biases")
             _ck(_nn().lbm_nn_adam(_p(self.W[li]), _p(gw), _p(self.m[2 * li]), _p(self.v[2 * li]),
                                   _p(self.Wb[li]), self.W[li].numel(), lr, b1, b2, eps, self.step_count, self.stream))
             _ck(_nn().lbm_nn_adam(_p(self.B[li]), _p(gb), _p(self.m[2 * li + 1]), _p(self.v[2 * li + 1]), None,
@@ -295,3 +308,48 @@ def warm_start_study(net: ConvNet, n: int, cases, tol=1e-10, storage=lbm.FP64):
         cold.close()
         warm.close()
     return out
+
+
+def study(n=64, train_count=192, test_count=8, iters=3000, seed=10247, gen_storage=lbm.FP32_DEV,
+          gen_tol=1e-7, tol=1e-10):
+    """The full warm-start experiment: method-generated training fields (FP32
+    storage, residual gen_tol), training on the GPU, then for held-out
+    parameters steps and wall time to the FP64 residual tol from rest and from
+    the prediction (all held-out cases stepped together as one batch each)."""
+    t0 = time.perf_counter()
+    X, Y, params, gen = generate(n, train_count, seed, storage=gen_storage, tol=gen_tol)
+    t_gen = time.perf_counter() - t0
+    net = ConvNet(seed=0, bf16=True)
+    t0 = time.perf_counter()
+    hist = train(net, X, Y, iters=iters, batch=32, lr=2e-3, seed=seed)
+    net.torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    cases = draw_params(test_count, n, seed + 1)
+    cold = [lbm.from_workload(section(n, F0, nu)) for F0, nu in cases]
+    warm = []
+    preds = []
+    t0 = time.perf_counter()
+    for F0, nu in cases:
+        L = lbm.from_workload(section(n, F0, nu))
+        ux = predict(net, n, F0, nu)
+        u = np.zeros((3, n * n))
+        u[0] = ux.T.reshape(-1)
+        L.init_equilibrium(1.0, u)
+        warm.append(L)
+        preds.append(ux)
+    t_pred = time.perf_counter() - t0
+    s_cold, sec_cold = run_to_steady(cold, n, tol=tol)
+    s_warm, sec_warm = run_to_steady(warm, n, tol=tol)
+    rows = []
+    for (F0, nu), c, w, ux, sc, sw in zip(cases, cold, warm, preds, s_cold, s_warm):
+        uc, uw = ux_field(c, n), ux_field(w, n)
+        rows.append({"F0": F0, "nu": nu, "steps_cold": sc, "steps_warm": sw,
+                     "prediction_l2": float(np.sqrt(np.sum((ux.T - uc) ** 2) / np.sum(uc ** 2))),
+                     "converged_fields_l2": float(np.sqrt(np.sum((uc - uw) ** 2) / np.sum(uc ** 2)))})
+    return {"n": n, "train_fields": train_count, "generation_seconds": t_gen,
+            "generation_steps_max": int(max(gen["steps"])), "train_iters": iters, "train_seconds": t_train,
+            "loss_first": hist[0], "loss_last": hist[-1], "prediction_seconds": t_pred,
+            "cold": {"steps_total": int(sum(s_cold)), "seconds": sec_cold},
+            "warm": {"steps_total": int(sum(s_warm)), "seconds": sec_warm + t_pred},
+            "cases": rows}
+

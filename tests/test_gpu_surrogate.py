@@ -58,22 +58,30 @@ def test_bf16_weights_forward_and_gradients():
         assert np.allclose(gw.cpu().numpy(), rw, rtol=1e-3, atol=1e-5 * np.abs(rw).max())
 
 
-def test_adam_matches_oracle():
-    from paper_1806_10247_gb300 import surrogate as G
-
+def test_adam_matches_oracle_every_parameter():
+    """Three Adam steps on every weight and bias of the network against the
+    oracle's update (each parameter keeps its own moment buffers)."""
     net, _ = _pair(bf16=False, seed=2)
-    p0 = net.W[0].cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(5)
-    g = rng.standard_normal(p0.shape)
-    m = np.zeros_like(p0)
-    v = np.zeros_like(p0)
-    p = p0.copy()
-    grads = [(torch.tensor(g, dtype=torch.float32, device="cuda"), torch.zeros_like(net.B[0]))]
-    grads += [(torch.zeros_like(w), torch.zeros_like(b)) for w, b in zip(net.W[1:], net.B[1:])]
+    ref = []
+    grads = []
+    for w, b in zip(net.W, net.B):
+        gw = rng.standard_normal(tuple(w.shape))
+        gb = rng.standard_normal(tuple(b.shape))
+        grads.append((torch.tensor(gw, dtype=torch.float32, device="cuda"),
+                      torch.tensor(gb, dtype=torch.float32, device="cuda")))
+        for p, g in ((w, gw), (b, gb)):
+            p0 = p.cpu().numpy().astype(np.float64)
+            ref.append([p0, g, np.zeros_like(p0), np.zeros_like(p0)])
     for t in (1, 2, 3):
         net.adam_step(grads, lr=1e-2)
-        S.adam_step(p, g, m, v, t, lr=1e-2)
-    assert np.allclose(net.W[0].cpu().numpy(), p, rtol=1e-5, atol=1e-6)
+        for p, g, m, v in ref:
+            S.adam_step(p, g, m, v, t, lr=1e-2)
+    got = []
+    for w, b in zip(net.W, net.B):
+        got += [w.cpu().numpy(), b.cpu().numpy()]
+    for a, (p, _, _, _) in zip(got, ref):
+        assert np.allclose(a, p, rtol=1e-5, atol=1e-6)
 
 
 def test_warm_start_gain_small_duct():
