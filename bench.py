@@ -221,12 +221,14 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
     for st in storages:
         w = W.poiseuille()
         L = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[st])
+        G = lbm.Batch([L])
+        G.set_graph(100)  # 100 steps per CUDA-graph replay between the checks
         L.reduce()
         torch_sync(stream)
         t0 = time.perf_counter()
         steps, du = 0, float("inf")
         while steps < 200000:
-            L.step(100)
+            G.step(100)
             steps += 100
             du = L.reduce()[4]
             if du < 1e-12:
@@ -236,21 +238,26 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
         ua = np.tile(W.poiseuille_parabola(w.shape[1], w.meta["tau"], w.meta["Fx"])[:, None], (1, w.shape[0]))
         l2 = float(np.sqrt(np.sum((u[0] - ua.reshape(-1)) ** 2) / np.sum(ua ** 2)))
         out[f"poiseuille_{st}"] = {"steps": steps, "seconds": sec, "max_du": du, "l2_vs_parabola": l2,
-                                   "criterion": "max |u(t) - u(t-100)| < 1e-12"}
+                                   "criterion": "max |u(t) - u(t-100)| < 1e-12",
+                                   "launch": "CUDA graph of 100 steps between lbm_reduce checks"}
+        G.close()
         L.close()
         cases = W.cde_sweep_params()
         errs, total = [], 0.0
         for c in cases:
             wc = W.cde_workload(c)
             G = lbm.from_workload(wc, stream=stream.cuda_stream, envelope_steps=c.T + 2, storage=codes[st])
+            Bt = lbm.Batch([G])
+            Bt.set_graph(200)
             torch_sync(stream)
             t0 = time.perf_counter()
-            G.step(c.T)
+            Bt.step(c.T)
             G.sync()
             total += time.perf_counter() - t0
             phi = G.moments().reshape(c.N, c.N) - 1.0
             ref = W.cde_closed_form(c, c.T)
             errs.append(float(np.sqrt(np.sum((phi - ref) ** 2) / np.sum(ref ** 2))))
+            Bt.close()
             G.close()
         orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
         out[f"cde_sweep_{st}"] = {"seconds": total, "steps": [c.T for c in cases],

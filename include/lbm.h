@@ -259,8 +259,22 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count);
  * table too short), LBM_ECUDA. */
 int lbm_batch_step(lbm_batch *b, long n);
 
-/* Kernel launches issued by lbm_batch_step so far (one per step). */
+/* Kernel launches issued by lbm_batch_step so far (one per step, whether
+ * launched directly or as a node of a replayed graph). */
 int lbm_batch_launch_count(const lbm_batch *b, long long *count);
+
+/* Replay steps as CUDA graphs of `steps_per_graph` launches each (a positive
+ * even number; 0 turns graphs off, the default).  lbm_batch_step(b, n) then
+ * issues n / steps_per_graph graph replays followed by ordinary launches for
+ * the remainder.  Each graph copies that replay's envelope pairs from pinned
+ * host memory and runs the batched step steps_per_graph times; it is captured
+ * on first use (on a private stream) and again when the members' buffer
+ * parity changes.  With a time-dependent envelope the host waits for the
+ * previous replay before refilling the pinned pairs.  Errors: LBM_EINVAL. */
+int lbm_batch_set_graph(lbm_batch *b, int steps_per_graph);
+
+/* Graph replays issued so far. */
+int lbm_batch_graph_replays(const lbm_batch *b, long long *count);
 
 /* Message of the last failure on b (NULL: the last lbm_batch_create failure). */
 const char *lbm_batch_last_error(const lbm_batch *b);

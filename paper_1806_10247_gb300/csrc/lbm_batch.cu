@@ -40,6 +40,16 @@ struct lbm_batch {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     int slot = 0;
     long long launches = 0;
+    long long graph_replays = 0;
+    // CUDA-graph replay of graph_steps steps (0 = off)
+    int graph_steps = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int gparity = -1;                  // descriptor parity the graph was captured for
+    cudaStream_t gstream = nullptr;    // private stream used only to capture
+    double2 *h_gpairs = nullptr;       // pinned envelope pairs of one replay (double2 or float2)
+    double2 *d_gpairs = nullptr;
+    bool gpairs_filled = false;        // constant envelopes: pairs written once
+    cudaEvent_t ev_graph = nullptr;    // recorded after each replay
     std::string err;
 };
 
@@ -152,6 +162,11 @@ void lbm_batch_destroy(lbm_batch *b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->ev_graph) cudaEventDestroy(b->ev_graph);
+    cudaFreeHost(b->h_gpairs);
+    cudaFree(b->d_gpairs);
     cudaFree(b->d_first);
     cudaFree(b->d_items);
     cudaFreeHost(b->h_items);
@@ -169,6 +184,130 @@ const char *lbm_batch_last_error(const lbm_batch *b)
     return b ? b->err.c_str() : g_batch_create_error.c_str();
 }
 
+namespace {
+
+bool has_envelope(const lbm_batch *b)
+{
+    for (const lbm_ctx *c : b->ctx)
+        if (c->env || !c->env_tab.empty()) return true;
+    return false;
+}
+
+// Make the device descriptors current; returns the buffer parity of the
+// current state relative to them (0 or 1) through *parity.
+int refresh_descriptors(lbm_batch *b, int *parity)
+{
+    int p0 = 0;
+    bool reuse = b->items_valid;
+    for (int i = 0; i < b->count && reuse; i++) {
+        const lbm_ctx *c = b->ctx[i];
+        const int p = c->A == b->item_buf0[i] ? 0 : 1;
+        if (c->version != b->item_version[i] || (i > 0 && p != p0)) reuse = false;
+        if (i == 0) p0 = p;
+    }
+    if (reuse) {
+        *parity = p0;
+        return LBM_OK;
+    }
+    BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
+    for (int i = 0; i < b->count; i++) {
+        const lbm_ctx *c = b->ctx[i];
+        BatchItem &it = b->h_items[i];
+        it = BatchItem{};
+        it.g = c->g;
+        it.rho_ref = c->rho_ref;
+        it.buf[0] = c->A;
+        it.buf[1] = c->B;
+        it.parity = 0;
+        it.fkind = c->force.kind;
+        it.F = c->force.d;
+        it.vkind = c->vel.kind;
+        it.V = c->vel.d;
+        batch_coef(c->lattice, c->omega, it);
+        for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
+        it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
+        it.frho_ref = (float)it.rho_ref;
+        b->item_version[i] = c->version;
+        b->item_buf0[i] = c->A;
+    }
+    BCK(cudaMemcpyAsync(b->d_items, b->h_items, b->count * sizeof(BatchItem), cudaMemcpyHostToDevice, b->stream),
+        "lbm_batch_step: copy descriptors");
+    BCK(cudaEventRecord(b->ev_items, b->stream), "lbm_batch_step: record");
+    b->items_valid = true;
+    *parity = 0;
+    return LBM_OK;
+}
+
+cudaError_t launch_one(lbm_batch *b, const BatchLaunch &L, cudaStream_t s)
+{
+    const int storage = b->ctx[0]->storage;
+    return storage == LBM_FP64 ? batch_step(b->lattice, L, b->nblocks, s)
+                               : rp_batch_step(b->lattice, storage, L, b->nblocks, s);
+}
+
+// Envelope pairs of steps t_i .. t_i + k - 1 of every member into dst (double2
+// for FP64 batches, float2 otherwise), [k][count].
+void fill_pairs(const lbm_batch *b, void *dst, long k)
+{
+    const bool fp32 = b->ctx[0]->storage != LBM_FP64;
+    for (int i = 0; i < b->count; i++) {
+        const lbm_ctx *c = b->ctx[i];
+        for (long s = 0; s < k; s++) {
+            double apre, apost;
+            lbmc::envelope_pair(c, c->t + s, apre, apost);
+            const double second = pair_second(b->lattice, apre, apost);
+            const size_t at = (size_t)s * b->count + i;
+            if (fp32) reinterpret_cast<float2 *>(dst)[at] = make_float2((float)apre, (float)second);
+            else reinterpret_cast<double2 *>(dst)[at] = make_double2(apre, second);
+        }
+    }
+}
+
+// Capture graph_steps batched launches (after one copy of their envelope
+// pairs from pinned memory) for descriptor parity `parity`.
+int capture_graph(lbm_batch *b, int parity)
+{
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    const size_t bytes = (size_t)b->graph_steps * b->count * sizeof(double2);
+    if (!b->gstream) BCK(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking), "graph stream");
+    if (!b->ev_graph) BCK(cudaEventCreateWithFlags(&b->ev_graph, cudaEventDisableTiming), "graph event");
+    if (!b->h_gpairs) {
+        BCK(cudaMallocHost(&b->h_gpairs, bytes), "cudaMallocHost(graph pairs)");
+        BCK(cudaMalloc(&b->d_gpairs, bytes), "cudaMalloc(graph pairs)");
+    }
+    b->gpairs_filled = false;
+    BCK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = cudaMemcpyAsync(b->d_gpairs, b->h_gpairs, bytes, cudaMemcpyHostToDevice, b->gstream);
+    const bool fp32 = b->ctx[0]->storage != LBM_FP64;
+    for (int k = 0; k < b->graph_steps && e == cudaSuccess; k++) {
+        BatchLaunch L{};
+        L.items = b->d_items;
+        L.first = b->d_first;
+        L.count = b->count;
+        L.k = k;
+        L.parity = (parity + k) & 1;
+        if (fp32) L.pairsf = reinterpret_cast<const float2 *>(b->d_gpairs);
+        else L.pairs = b->d_gpairs;
+        e = launch_one(b, L, b->gstream);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->gstream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->gexec = nullptr;
+        return bfail(b, LBM_ECUDA, "lbm_batch_step: graph capture: %s", cudaGetErrorString(e));
+    }
+    b->gparity = parity;
+    return LBM_OK;
+}
+
+}  // namespace
+
 int lbm_batch_step(lbm_batch *b, long n)
 {
     if (!b) return LBM_EINVAL;
@@ -182,45 +321,34 @@ int lbm_batch_step(lbm_batch *b, long n)
         if (!lbmc::envelope_covers(c, c->t, n))
             return bfail(b, LBM_EINVAL, "lbm_batch_step: context %d steps outside its envelope table", i);
     }
-    // Descriptors: reuse the device copy while every member is unchanged and
-    // all members sit on the same buffer parity relative to it.
     int parity = 0;
-    bool reuse = b->items_valid;
-    for (int i = 0; i < b->count && reuse; i++) {
-        const lbm_ctx *c = b->ctx[i];
-        const int p = c->A == b->item_buf0[i] ? 0 : 1;
-        if (c->version != b->item_version[i] || (i == 0 ? false : p != parity)) reuse = false;
-        if (i == 0) parity = p;
-    }
-    if (!reuse) {
-        BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
-        for (int i = 0; i < b->count; i++) {
-            const lbm_ctx *c = b->ctx[i];
-            BatchItem &it = b->h_items[i];
-            it = BatchItem{};
-            it.g = c->g;
-            it.rho_ref = c->rho_ref;
-            it.buf[0] = c->A;
-            it.buf[1] = c->B;
-            it.parity = 0;
-            it.fkind = c->force.kind;
-            it.F = c->force.d;
-            it.vkind = c->vel.kind;
-            it.V = c->vel.d;
-            batch_coef(c->lattice, c->omega, it);
-            for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
-            it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
-            it.frho_ref = (float)it.rho_ref;
-            b->item_version[i] = c->version;
-            b->item_buf0[i] = c->A;
+    int rc = refresh_descriptors(b, &parity);
+    if (rc != LBM_OK) return rc;
+
+    // Whole graph replays first (graph_steps is even: parity is unchanged).
+    if (b->graph_steps > 0 && n >= b->graph_steps) {
+        if (!b->gexec || b->gparity != parity) {
+            rc = capture_graph(b, parity);
+            if (rc != LBM_OK) return rc;
         }
-        BCK(cudaMemcpyAsync(b->d_items, b->h_items, b->count * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                            b->stream),
-            "lbm_batch_step: copy descriptors");
-        BCK(cudaEventRecord(b->ev_items, b->stream), "lbm_batch_step: record");
-        b->items_valid = true;
-        parity = 0;
+        const bool env = has_envelope(b);
+        while (n >= b->graph_steps) {
+            if (env || !b->gpairs_filled) {
+                // the previous replay's copy has read the pinned pairs by the time it completes
+                BCK(cudaEventSynchronize(b->ev_graph), "lbm_batch_step: wait for the previous replay");
+                fill_pairs(b, b->h_gpairs, b->graph_steps);
+                b->gpairs_filled = true;
+            }
+            BCK(cudaGraphLaunch(b->gexec, b->stream), "lbm_batch_step: graph launch");
+            BCK(cudaEventRecord(b->ev_graph, b->stream), "lbm_batch_step: record");
+            b->launches += b->graph_steps;
+            b->graph_replays++;
+            for (lbm_ctx *c : b->ctx) c->t += b->graph_steps;
+            n -= b->graph_steps;
+        }
+        if (n == 0) return LBM_OK;
     }
+
     BatchLaunch L{};
     L.items = b->d_items;
     L.first = b->d_first;
@@ -231,22 +359,13 @@ int lbm_batch_step(lbm_batch *b, long n)
         b->slot ^= 1;
         // The staging slot was last read by the copy recorded two calls ago.
         BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
-        int rc = grow_pairs(b, s, (size_t)n * b->count);
+        rc = grow_pairs(b, s, (size_t)n * b->count);
         if (rc != LBM_OK) return rc;
+        fill_pairs(b, b->h_pairs[s], n);
         const bool fp32 = b->ctx[0]->storage != LBM_FP64;
-        float2 *hf = reinterpret_cast<float2 *>(b->h_pairs[s]);  // FP32 pairs reuse the staging memory
-        for (int i = 0; i < b->count; i++) {
-            const lbm_ctx *c = b->ctx[i];
-            for (long k = 0; k < n; k++) {
-                double apre, apost;
-                lbmc::envelope_pair(c, c->t + k, apre, apost);
-                const double second = pair_second(b->lattice, apre, apost);
-                if (fp32) hf[(size_t)k * b->count + i] = make_float2((float)apre, (float)second);
-                else b->h_pairs[s][(size_t)k * b->count + i] = make_double2(apre, second);
-            }
-        }
-        BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * sizeof(double2),
-                            cudaMemcpyHostToDevice, b->stream),
+        const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+        BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * esz, cudaMemcpyHostToDevice,
+                            b->stream),
             "lbm_batch_step: copy envelope pairs");
         BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
         if (fp32) L.pairsf = reinterpret_cast<const float2 *>(b->d_pairs[s]);
@@ -263,9 +382,7 @@ int lbm_batch_step(lbm_batch *b, long n)
                 L.inl[i] = make_double2(apre, second);
                 L.inlf[i] = make_float2((float)apre, (float)second);
             }
-        const int storage = b->ctx[0]->storage;
-        cudaError_t e = storage == LBM_FP64 ? batch_step(b->lattice, L, b->nblocks, b->stream)
-                                            : rp_batch_step(b->lattice, storage, L, b->nblocks, b->stream);
+        cudaError_t e = launch_one(b, L, b->stream);
         if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_step: kernel: %s", cudaGetErrorString(e));
         b->launches++;
     }
@@ -274,6 +391,34 @@ int lbm_batch_step(lbm_batch *b, long n)
         if (n & 1) std::swap(c->A, c->B);
         c->t += n;
     }
+    return LBM_OK;
+}
+
+int lbm_batch_set_graph(lbm_batch *b, int steps_per_graph)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    if (steps_per_graph < 0 || (steps_per_graph & 1))
+        return bfail(b, LBM_EINVAL, "lbm_batch_set_graph: steps per graph must be 0 or a positive even number");
+    if (steps_per_graph != b->graph_steps) {
+        if (b->gexec) {
+            cudaStreamSynchronize(b->stream);
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        cudaFreeHost(b->h_gpairs);
+        cudaFree(b->d_gpairs);
+        b->h_gpairs = nullptr;
+        b->d_gpairs = nullptr;
+        b->graph_steps = steps_per_graph;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_graph_replays(const lbm_batch *b, long long *count)
+{
+    if (!b || !count) return LBM_EINVAL;
+    *count = b->graph_replays;
     return LBM_OK;
 }
 

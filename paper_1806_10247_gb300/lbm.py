@@ -30,7 +30,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_set_source", "lbm_set_velocity", "lbm_set_envelope", "lbm_step", "lbm_moments",
            "lbm_reduce", "lbm_get_populations", "lbm_set_populations", "lbm_get_step", "lbm_sync",
            "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
-           "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy")
+           "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
+           "lbm_batch_set_graph", "lbm_batch_graph_replays")
 
 
 class LBMError(RuntimeError):
@@ -96,6 +97,8 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ip]
     L.lbm_batch_step.argtypes = [vp, ctypes.c_long]
     L.lbm_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_batch_set_graph.argtypes = [vp, ip]
+    L.lbm_batch_graph_replays.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
     L.lbm_batch_destroy.argtypes = [vp]
@@ -334,6 +337,15 @@ class Batch:
     def launch_count(self):
         v = ctypes.c_longlong()
         self._check(self._L.lbm_batch_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+    def set_graph(self, steps_per_graph):
+        """Replay steps as CUDA graphs of that many launches (even; 0 = off)."""
+        self._check(self._L.lbm_batch_set_graph(self.h, int(steps_per_graph)))
+
+    def graph_replays(self):
+        v = ctypes.c_longlong()
+        self._check(self._L.lbm_batch_graph_replays(self.h, ctypes.byref(v)))
         return v.value
 
     def close(self):
