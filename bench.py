@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -34,22 +35,59 @@ METRIC = "MLUPS and % of HBM roofline per lattice; time-to-steady-state at ≤1e
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# FP64 arithmetic per node of the dominant kernel and its DRAM traffic, from
-# the ncu captures summarised under profiles/ (see the design doc).  The traffic is
-# reported only while the kernel source still hashes to the value it was
-# measured on.
+# Per (workload, storage): FP64 work per node of the step kernel and its DRAM
+# traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), from the
+# ncu captures summarised under profiles/.  FP64 counts are thread-level
+# instructions from ncu's per-opcode table (DFMA, DADD, DMUL); flops count an
+# FMA as two.  The traffic is reported only while the kernel sources still hash
+# to the value it was measured on.
+_H = ["paper_1806_10247_gb300/csrc/lbm_lattices.cuh", "paper_1806_10247_gb300/csrc/lbm_internal.h",
+      "paper_1806_10247_gb300/csrc/lbm_device.cuh"]
 KERNEL_FACTS = {
-    "cde_sweep": {
-        "src": ["paper_1806_10247_gb300/csrc/k_d2q5.cu", "paper_1806_10247_gb300/csrc/lbm_lattices.cuh",
-                "paper_1806_10247_gb300/csrc/lbm_internal.h",
-                "paper_1806_10247_gb300/csrc/lbm_device.cuh"],
-        "fp64_flops_per_node": None,
-        "traffic_bytes_per_launch": None,
-        "traffic_src_sha": None,
+    ("cde_sweep", "fp64"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_d2q5.cu"] + _H,
+        "fp64_inst_per_node": 38, "fp64_flops_per_node": 48,
+        "traffic_bytes_per_launch": 14.002176e6, "traffic_src_sha": "5fe048d974140251",
+        "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md",
+    },
+    ("kolmogorov96", "fp64"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_d3q27.cu"] + _H,
+        "fp64_inst_per_node": 426, "fp64_flops_per_node": 621,
+        "traffic_bytes_per_launch": (191.174144 + 142.945536) * 1e6, "traffic_src_sha": "890a81d687f85b7f",
+        "profile": "profiles/k_batch_d3q27_kolmogorov96_fp64.md",
+    },
+    ("channel2048", "fp64"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_d2q9.cu"] + _H,
+        "fp64_inst_per_node": 134, "fp64_flops_per_node": 171,
+        "traffic_bytes_per_launch": (151.023616 + 105.353728) * 1e6, "traffic_src_sha": "bf2bab403965bd53",
+        "profile": "profiles/k_batch_d2q9_channel2048_fp64.md",
+    },
+    ("kolmogorov96", "fp32"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (95.602176 + 51.792128) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
+        "profile": "profiles/k_batch27_kolmogorov96_fp32_fp16.md",
+    },
+    ("kolmogorov96", "fp16"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (47.818496 + 8.367872) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
+        "profile": "profiles/k_batch27_kolmogorov96_fp32_fp16.md",
+    },
+    ("channel2048", "fp32"): {
+        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (75.518976 + 31.702016) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
+        "profile": "profiles/k_batch9_channel2048_fp32.md",
     },
 }
-FP64_PEAK_TFLOPS = None  # measured FP64 FMA rate of the GB300 (set from the probe)
-FP64_PEAK_NOTE = "recipe nominal 1.25 TFLOP/s"
+# The same FP64 kernels run the 256^3 / 512^3 Kolmogorov workloads.
+for _w in ("kolmogorov256", "kolmogorov512"):
+    KERNEL_FACTS[(_w, "fp64")] = {k: v for k, v in KERNEL_FACTS[("kolmogorov96", "fp64")].items()
+                                  if k != "traffic_bytes_per_launch"}
+# FP64 pipe of the GB300: 2 FMA lanes per clock per SM (the recipe's 1.25 TFLOP/s
+# divided by 2 flop x 152 SMs x 2.07 GHz), 152 SMs, 2.07 GHz maximum SM clock.
+FP64_LANES_PER_SM, N_SMS, SM_GHZ = 2, 152, 2.07
+FP64_PEAK_GINST = FP64_LANES_PER_SM * N_SMS * SM_GHZ          # 629.3 G FP64 instructions/s
+FP64_PEAK_TFLOPS = 2 * FP64_PEAK_GINST / 1e3                  # 1.259 TFLOP/s
+FP64_PEAK_NOTE = "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flop"
 
 
 def src_hash(paths):
@@ -96,7 +134,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        out = os.environ.get("LBM_RESULTS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -397,7 +436,7 @@ def main():
     q = Q_OF[wl[0].lattice]
     alg_bytes = nb * 2 * elem * q  # q populations read + q written
     achieved_gbs = alg_bytes / kavg_s / 1e9
-    facts = KERNEL_FACTS.get(args.workload, {})
+    facts = KERNEL_FACTS.get((args.workload, args.storage), {})
     traffic = None
     if facts.get("traffic_bytes_per_launch") is not None and facts["traffic_src_sha"] == src_hash(facts["src"]):
         traffic = facts["traffic_bytes_per_launch"]
@@ -405,14 +444,18 @@ def main():
             "frac": achieved_gbs / hbm, "traffic": traffic, "kernel": f"batched step kernel ({wname})",
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
             "bytes_per_node": 2 * elem * q, "kernel_us": kavg_s * 1e6}
-    facts = KERNEL_FACTS.get(args.workload, {})
-    if facts.get("fp64_flops_per_node") and FP64_PEAK_TFLOPS:
+    if facts.get("fp64_flops_per_node"):
         tf = facts["fp64_flops_per_node"] * nb / kavg_s / 1e12
-        roof["fp64"] = {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-                        "peak_source": FP64_PEAK_NOTE}
+        gi = facts["fp64_inst_per_node"] * nb / kavg_s / 1e9
+        pipe = {"achieved": gi, "peak": FP64_PEAK_GINST, "unit": "G FP64 instr/s", "frac": gi / FP64_PEAK_GINST,
+                "inst_per_node": facts["fp64_inst_per_node"]}
         if tf / FP64_PEAK_TFLOPS > roof["frac"]:
             roof.update({"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tf / FP64_PEAK_TFLOPS, "hbm_frac": achieved_gbs / hbm})
+                         "frac": tf / FP64_PEAK_TFLOPS, "flops_per_node": facts["fp64_flops_per_node"],
+                         "peak_source": FP64_PEAK_NOTE, "fp64_pipe": pipe,
+                         "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm}})
+    if facts.get("profile"):
+        roof["profile"] = facts["profile"]
 
     # end to end through the public API with host buffers: per step and lattice,
     # upload the step's source field from pinned host memory (lbm_set_source),

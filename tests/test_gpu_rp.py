@@ -2,8 +2,8 @@
 state, FP32 moment arithmetic): error against the FP64 oracle per form.
 
 The FP32 form must stay within the 1e-4 relative l2 target; the measured
-errors of every form are written to gpurun_out/rp_errors.json (if that folder
-exists) so that they can be quoted."""
+errors of every form are written to $LBM_RESULTS_DIR/rp_errors.json (when that
+variable names a folder) so that they can be quoted."""
 import json
 import math
 import os
@@ -42,8 +42,8 @@ def _check(case, form, err):
 
 def _record(key, val):
     RESULTS[key] = val
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "rp_errors.json"), "w") as f:
             json.dump(RESULTS, f, indent=1, sort_keys=True)
 

@@ -97,8 +97,8 @@ def test_warm_start_gain_small_duct():
     assert hist[-1] < 0.2 * hist[0], (hist[0], hist[-1])
     cases = G.draw_params(3, n, seed=99)
     res = G.warm_start_study(net, n, cases)
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "warmstart_small.json"), "w") as f:
             json.dump({"generation": gen, "loss_first": hist[0], "loss_last": hist[-1], "cases": res}, f, indent=1)
     for r in res:
