@@ -33,6 +33,21 @@
  *    along K_1 = e_x, e_y, e_z normalised by sum_alpha e_alpha,x^2 = 18, the
  *    analogue of Eqs. 29-31 and Eq. 12A-13A.  The same procedure applied to
  *    D2Q9 reproduces Eqs. 23, 31, 32, which the tests check.
+ *  - D3Q15 (Appendix A) follows Eq. 6A, Eq. 8A, Eq. 13A and the printed f^p
+ *    expansion, with three corrections (the flag `as_printed` restores the
+ *    first two, used only to show the defects):
+ *    (i) g_9 relaxes the trace of the central second moments towards its
+ *        equilibrium rho (3 c_s^2 rho); the printed bracket lacks that rho,
+ *        so the rest state would not be a fixed point;
+ *    (ii) the printed f^p_12 carries -g_13, but K_13 = e_x e_y e_z is +1 for
+ *        e_12 = (-1, 1, -1); +g_13 is used (the populations are K g);
+ *    (iii) the fourth-order bracket of g_14 contains an undefined product
+ *        "kappa~_xx kappa~_yy" of the dimension rho^2; it is read as the
+ *        product of the post-collision second central moments divided by rho,
+ *        so that at omega = 1 kappa_xxyy relaxes to kappa~_xx kappa~_yy / rho
+ *        (= c_s^4 rho at equilibrium).
+ *    With time-dependent forces g_1..g_3 = (F_pre + F_post)/20 (Eq. 12A: the
+ *    first-moment change is 10 g_1, and it must equal (F_pre + F_post)/2).
  */
 #include "lbm_oracle.h"
 
@@ -55,12 +70,25 @@ static const int D2Q9_E[9][3] = {
 static const int D2Q5_E[5][3] = {
     {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}};
 
+/* D3Q15 particle velocities, Appendix A Eq. a1 (columns of |e_x>, |e_y>, |e_z>). */
+static const int D3Q15_E[15][3] = {
+    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {-1, -1, 1}, {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+
+/* Monomials e_x^a e_y^b e_z^c whose moments span the D3Q15 population space:
+ * the moments behind K_0..K_14 of Eq. 2A (1; e; the second-order products;
+ * e_x e_y^2, e_x^2 e_y, e_x^2 e_z, e_x e_y e_z; e_x^2 e_y^2). */
+static const int D3Q15_X[15][3] = {
+    {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+    {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 2, 0}, {2, 1, 0}, {2, 0, 1}, {1, 1, 1}, {2, 2, 0}};
+
 int orc_q(int lattice)
 {
     switch (lattice) {
     case ORC_D2Q9: return 9;
     case ORC_D3Q27: return 27;
     case ORC_D2Q5: return 5;
+    case ORC_D3Q15: return 15;
     default: return 0;
     }
 }
@@ -71,6 +99,7 @@ int orc_dim(int lattice)
     case ORC_D2Q9: return 2;
     case ORC_D3Q27: return 3;
     case ORC_D2Q5: return 2;
+    case ORC_D3Q15: return 3;
     default: return 0;
     }
 }
@@ -83,6 +112,7 @@ int orc_velocities(int lattice, int *e)
         for (int d = 0; d < 3; d++) {
             if (lattice == ORC_D2Q9) e[3 * a + d] = D2Q9_E[a][d];
             else if (lattice == ORC_D2Q5) e[3 * a + d] = D2Q5_E[a][d];
+            else if (lattice == ORC_D3Q15) e[3 * a + d] = D3Q15_E[a][d];
         }
         if (lattice == ORC_D3Q27) {
             e[3 * a + 0] = a % 3 - 1;
@@ -95,7 +125,8 @@ int orc_velocities(int lattice, int *e)
 
 /* Moment basis of a lattice: monomials e_x^a e_y^b e_z^c.
  * D2Q9: a,b in {0,1,2} (index a + 3b); D3Q27: a,b,c in {0,1,2} (a + 3b + 9c);
- * D2Q5: 1, e_x, e_y, e_x^2, e_y^2 (the monomials behind L_0..L_4 of Eq. 35). */
+ * D2Q5: 1, e_x, e_y, e_x^2, e_y^2 (the monomials behind L_0..L_4 of Eq. 35);
+ * D3Q15: D3Q15_X. */
 typedef struct {
     int q;
     int e[MAXQ][3];
@@ -154,6 +185,8 @@ static int basis_build(int lattice, basis *B)
         if (lattice == ORC_D2Q5) {
             static const int X5[5][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {2, 0, 0}, {0, 2, 0}};
             for (int d = 0; d < 3; d++) B->ex[k][d] = X5[k][d];
+        } else if (lattice == ORC_D3Q15) {
+            for (int d = 0; d < 3; d++) B->ex[k][d] = D3Q15_X[k][d];
         } else {
             B->ex[k][0] = k % 3;
             B->ex[k][1] = (k / 3) % 3;
@@ -201,7 +234,7 @@ static void shift_moments(const basis *B, const double *in, const double s[3], d
             for (int j = 0; j <= b; j++)
                 for (int l = 0; l <= c; l++) {
                     int kk = mindex(B, i, j, l);
-                    if (kk < 0) continue; /* D2Q5: lower monomials are always present */
+                    if (kk < 0) continue; /* D2Q5, D3Q15: the lower monomials are all present */
                     acc += binom(a, i) * binom(b, j) * binom(c, l) * ipow(-s[0], a - i) *
                            ipow(-s[1], b - j) * ipow(-s[2], c - l) * in[kk];
                 }
@@ -210,8 +243,11 @@ static void shift_moments(const basis *B, const double *in, const double s[3], d
 }
 
 /* Central-moment equilibria of Eq. 20 (D2Q9) / Eq. 39 (D2Q5), and their
- * Maxwellian continuation for D3Q27: rho * prod_d (c_s^2 if exponent 2, 1 if 0,
- * 0 if odd) with c_s^2 = 1/3. */
+ * Maxwellian continuation for D3Q27 and D3Q15: rho * prod_d (c_s^2 if exponent
+ * 2, 1 if 0, 0 if odd) with c_s^2 = 1/3.  For D3Q15 these are the central
+ * moments that the collision of Eq. 6A reaches at omega = 1 (with the
+ * readings above), so the equilibrium built from them is the image of an
+ * omega = 1 collision. */
 static double central_eq(const basis *B, int k, double rho)
 {
     double v = rho;
@@ -337,6 +373,104 @@ static void collide_d2q5_paper(const double *om, int as_printed, const double g[
 }
 
 /* ------------------------------------------------------------------------ */
+/* Collision: D3Q15 (Appendix A)                                             */
+/* ------------------------------------------------------------------------ */
+
+static void collide_d3q15_paper(const double *om, int as_printed, const double f[15], const double Fpre[3],
+                                const double Fpost[3], double fp[15])
+{
+    /* Rates of Eq. 6A from the grouped parameters. */
+    const double w4 = om[2], w5 = om[2], w6 = om[2], w7 = om[2], w8 = om[2];
+    const double w9 = om[1];
+    const double w10 = om[3], w11 = om[3], w12 = om[3], w13 = om[3];
+    const double w14 = om[4];
+
+    /* Density and output momentum (Eq. 7A); raw moments (Eq. g8). */
+    double rho = 0, jx = 0, jy = 0, jz = 0;
+    double kxx = 0, kyy = 0, kzz = 0, kxy = 0, kxz = 0, kyz = 0;
+    double kxyy = 0, kxxy = 0, kxxz = 0, kxyz = 0, kxxyy = 0;
+    for (int a = 0; a < 15; a++) {
+        const double ex = D3Q15_E[a][0], ey = D3Q15_E[a][1], ez = D3Q15_E[a][2];
+        rho += f[a];
+        jx += f[a] * ex;
+        jy += f[a] * ey;
+        jz += f[a] * ez;
+        kxx += f[a] * ex * ex;
+        kyy += f[a] * ey * ey;
+        kzz += f[a] * ez * ez;
+        kxy += f[a] * ex * ey;
+        kxz += f[a] * ex * ez;
+        kyz += f[a] * ey * ez;
+        kxyy += f[a] * ex * ey * ey;
+        kxxy += f[a] * ex * ex * ey;
+        kxxz += f[a] * ex * ex * ez;
+        kxyz += f[a] * ex * ey * ez;
+        kxxyy += f[a] * ex * ex * ey * ey;
+    }
+    /* Pre-collision half force step (Eq. 8A). */
+    const double ux = (jx + Fpre[0] / 2.0) / rho;
+    const double uy = (jy + Fpre[1] / 2.0) / rho;
+    const double uz = (jz + Fpre[2] / 2.0) / rho;
+
+    /* Cascaded change of moments, Eq. 6A (corrections (i) and (iii), see the
+     * file header). */
+    const double g4 = w4 / 8.0 * (-kxy + rho * ux * uy);
+    const double g5 = w5 / 8.0 * (-kxz + rho * ux * uz);
+    const double g6 = w6 / 8.0 * (-kyz + rho * uy * uz);
+    const double g7 = w7 / 4.0 * (-(kxx - kyy) + rho * (ux * ux - uy * uy));
+    const double g8 = w8 / 12.0 * (-(kxx + kyy - 2.0 * kzz) + rho * (ux * ux + uy * uy - 2.0 * uz * uz));
+    const double trace_eq = as_printed ? 0.0 : rho;
+    const double g9 = w9 / 18.0 * (trace_eq - (kxx + kyy + kzz) + rho * (ux * ux + uy * uy + uz * uz));
+    const double g10 = w10 / 16.0 * (-kxyy + 2.0 * uy * kxy + ux * kyy - 2.0 * rho * ux * uy * uy)
+                       + uy * g4 + ux / 8.0 * (-g7 + g8 + 3.0 * g9);
+    const double g11 = w11 / 16.0 * (-kxxy + 2.0 * ux * kxy + uy * kxx - 2.0 * rho * ux * ux * uy)
+                       + ux * g4 + uy / 8.0 * (g7 + g8 + 3.0 * g9);
+    const double g12 = w12 / 16.0 * (-kxxz + 2.0 * ux * kxz + uz * kxx - 2.0 * rho * ux * ux * uz)
+                       + ux * g5 + uz / 8.0 * (g7 + g8 + 3.0 * g9);
+    const double g13 = w13 / 8.0 * (-kxyz + ux * kyz + uy * kxz + uz * kxy - 2.0 * rho * ux * uy * uz)
+                       + uz * g4 + uy * g5 + ux * g6;
+    /* Post-collision second central moments: the pre-collision central
+     * moments about u plus the changes K_7, K_8, K_9 make to them (K_4..K_6
+     * leave the diagonal ones unchanged): xx gains 2 g7 + 2 g8 + 6 g9, yy
+     * gains -2 g7 + 2 g8 + 6 g9. */
+    const double cxx = kxx - rho * ux * ux, cyy = kyy - rho * uy * uy;
+    const double cxx_post = cxx + 2.0 * g7 + 2.0 * g8 + 6.0 * g9;
+    const double cyy_post = cyy - 2.0 * g7 + 2.0 * g8 + 6.0 * g9;
+    const double g14 = w14 / 16.0 * (-kxxyy + 2.0 * ux * kxyy + 2.0 * uy * kxxy - ux * ux * kyy - uy * uy * kxx
+                                     - 4.0 * ux * uy * kxy + cxx_post * cyy_post / rho
+                                     + 3.0 * rho * ux * ux * uy * uy)
+                       - 2.0 * ux * uy * g4 + (ux * ux - uy * uy) / 8.0 * g7 - (ux * ux + uy * uy) / 8.0 * g8
+                       + (3.0 / 8.0 * (-ux * ux - uy * uy) - 0.5) * g9 + 2.0 * ux * g10 + 2.0 * uy * g11;
+
+    /* Mass is conserved (g0 = 0); the first-moment change 10 g_d equals the
+     * mean force of the two half steps (Eqs. 10A-13A). */
+    const double g0 = 0.0;
+    const double g1 = (Fpre[0] + Fpost[0]) / 2.0 / 10.0;
+    const double g2 = (Fpre[1] + Fpost[1]) / 2.0 / 10.0;
+    const double g3 = (Fpre[2] + Fpost[2]) / 2.0 / 10.0;
+
+    /* Post-collision populations (the expansion of f + K g ending Appendix A;
+     * correction (ii) in f^p_12). */
+    const double s12 = as_printed ? -1.0 : 1.0;
+    fp[0] = f[0] + (g0 - 2.0 * g9 + 32.0 * g14);
+    fp[1] = f[1] + (g0 + g1 + g7 + g8 - g9 - 8.0 * g10 - 8.0 * g14);
+    fp[2] = f[2] + (g0 - g1 + g7 + g8 - g9 + 8.0 * g10 - 8.0 * g14);
+    fp[3] = f[3] + (g0 + g2 - g7 + g8 - g9 - 8.0 * g11 - 8.0 * g14);
+    fp[4] = f[4] + (g0 - g2 - g7 + g8 - g9 + 8.0 * g11 - 8.0 * g14);
+    fp[5] = f[5] + (g0 + g3 - 2.0 * g8 - g9 - 8.0 * g12 - 8.0 * g14);
+    fp[6] = f[6] + (g0 - g3 - 2.0 * g8 - g9 + 8.0 * g12 - 8.0 * g14);
+    fp[7] = f[7] + (g0 + g1 + g2 + g3 + g4 + g5 + g6 + g9 + 2.0 * g10 + 2.0 * g11 + 2.0 * g12 + g13 + 2.0 * g14);
+    fp[8] = f[8] + (g0 - g1 + g2 + g3 - g4 - g5 + g6 + g9 - 2.0 * g10 + 2.0 * g11 + 2.0 * g12 - g13 + 2.0 * g14);
+    fp[9] = f[9] + (g0 + g1 - g2 + g3 - g4 + g5 - g6 + g9 + 2.0 * g10 - 2.0 * g11 + 2.0 * g12 - g13 + 2.0 * g14);
+    fp[10] = f[10] + (g0 - g1 - g2 + g3 + g4 - g5 - g6 + g9 - 2.0 * g10 - 2.0 * g11 + 2.0 * g12 + g13 + 2.0 * g14);
+    fp[11] = f[11] + (g0 + g1 + g2 - g3 + g4 - g5 - g6 + g9 + 2.0 * g10 + 2.0 * g11 - 2.0 * g12 - g13 + 2.0 * g14);
+    fp[12] = f[12] + (g0 - g1 + g2 - g3 - g4 + g5 - g6 + g9 - 2.0 * g10 + 2.0 * g11 - 2.0 * g12 + s12 * g13
+                      + 2.0 * g14);
+    fp[13] = f[13] + (g0 + g1 - g2 - g3 - g4 - g5 + g6 + g9 + 2.0 * g10 - 2.0 * g11 - 2.0 * g12 + g13 + 2.0 * g14);
+    fp[14] = f[14] + (g0 - g1 - g2 - g3 + g4 + g5 + g6 + g9 - 2.0 * g10 - 2.0 * g11 - 2.0 * g12 - g13 + 2.0 * g14);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Collision: generic central-moment procedure (D2Q9, D3Q27)                 */
 /* ------------------------------------------------------------------------ */
 
@@ -446,6 +580,10 @@ int orc_collide_node(const orc_params *p, const double *fin, const double *Fpre,
         collide_d2q5_paper(p->omega, p->as_printed, fin, Fpre[0], Fpost[0], uadv[0], uadv[1], fout);
         return 0;
     }
+    if (p->lattice == ORC_D3Q15) {
+        collide_d3q15_paper(p->omega, p->as_printed, fin, Fpre, Fpost, fout);
+        return 0;
+    }
     return orc_collide_node_generic(p, fin, Fpre, Fpost, fout);
 }
 
@@ -453,7 +591,7 @@ int orc_collide_node_generic(const orc_params *p, const double *fin, const doubl
                              const double *Fpost, double *fout)
 {
     basis B;
-    if (p->lattice == ORC_D2Q5) return -1;
+    if (p->lattice == ORC_D2Q5 || p->lattice == ORC_D3Q15) return -1;
     if (basis_build(p->lattice, &B)) return -1;
     collide_generic(p->lattice, &B, p->omega, fin, Fpre, Fpost, fout);
     return 0;
@@ -535,6 +673,8 @@ int orc_run(const orc_params *p, double *f, double *work, long nsteps, const dou
             else if (p->lattice == ORC_D2Q5)
                 collide_d2q5_paper(p->omega, p->as_printed, fin, Fpre[0], Fpost[0], uadv[i],
                                    uadv[N + i], fout);
+            else if (p->lattice == ORC_D3Q15)
+                collide_d3q15_paper(p->omega, p->as_printed, fin, Fpre, Fpost, fout);
             else
                 collide_generic(p->lattice, &B, p->omega, fin, Fpre, Fpost, fout);
             for (int k = 0; k < q; k++) work[k * N + i] = fout[k];

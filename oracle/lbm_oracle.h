@@ -15,6 +15,7 @@
  *   D2Q9  : the paper's order (Sec. 4, Eq. 15).
  *   D2Q5  : the paper's order (Sec. 5, Eq. 34).
  *   D3Q27 : alpha = (ex+1) + 3 (ey+1) + 9 (ez+1)  (the paper gives no D3Q27 order).
+ *   D3Q15 : the paper's order (Appendix A, Eq. a1).
  */
 #ifndef LBM_ORACLE_H
 #define LBM_ORACLE_H
@@ -26,22 +27,28 @@ extern "C" {
 #define ORC_D2Q9  1
 #define ORC_D3Q27 2
 #define ORC_D2Q5  3
+#define ORC_D3Q15 4
 
 typedef struct {
-    int lattice;            /* ORC_D2Q9 / ORC_D3Q27 / ORC_D2Q5 */
+    int lattice;            /* ORC_D2Q9 / ORC_D3Q27 / ORC_D2Q5 / ORC_D3Q15 */
     int n[3];               /* nx, ny, nz (nz = 1 for the 2D lattices) */
     int wall[3];            /* per axis: 0 periodic, 1 halfway bounce-back walls at both ends */
     /* Relaxation parameters.
      *   D2Q9 : omega[3..8] = omega_3..omega_8 of Eq. 23.
      *   D2Q5 : omega[1..4] = omega_1^phi..omega_4^phi of Eq. 41.
      *   D3Q27: omega[1] trace (bulk), omega[2] deviatoric and off-diagonal second
-     *          order (shear), omega[3..6] all central moments of order 3..6. */
+     *          order (shear), omega[3..6] all central moments of order 3..6.
+     *   D3Q15: omega[1] = omega_9 (trace), omega[2] = omega_4..omega_8 (shear),
+     *          omega[3] = omega_10..omega_13 (third order), omega[4] = omega_14
+     *          (fourth order), numbered as in Eq. 6A. */
     double omega[9];
     int generic;            /* D2Q9 only: 1 = generic central-moment procedure instead of Eqs. 23/32 */
-    int as_printed;         /* D2Q5 only: 1 = Eq. 41 with the u^2 phi signs exactly as printed */
+    int as_printed;         /* D2Q5: 1 = Eq. 41 with the u^2 phi signs exactly as printed.
+                             * D3Q15: 1 = g_9 of Eq. 6A without its missing rho term and
+                             * the printed sign of g_13 in f^p_12 (Appendix A). */
 } orc_params;
 
-/* Number of velocities of a lattice (9, 27, 5), 0 if unknown. */
+/* Number of velocities of a lattice (9, 27, 5, 15), 0 if unknown. */
 int orc_q(int lattice);
 /* Spatial dimension of a lattice (2 or 3). */
 int orc_dim(int lattice);

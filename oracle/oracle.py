@@ -10,6 +10,8 @@ The oracle follows arXiv:1806.10247:
     sign of its u^2 phi terms corrected, see ``lbm_oracle.c``);
   * D3Q27 flow: the generic central-moment procedure that the paper's
     Appendix A says extends to D3Q27;
+  * D3Q15 flow: Appendix A, Eqs. 6A-13A and the f^p expansion, with the
+    three corrections listed in ``lbm_oracle.c``;
   * streaming with periodic wrap or stationary halfway bounce-back (Sec. 6.1).
 
 Force and source fields enter as F(x, t) = a(t) * P(x): a shape P given on the
@@ -30,9 +32,9 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "liblbm_oracle.so")
 SRC = os.path.join(HERE, "lbm_oracle.c")
 
-D2Q9, D3Q27, D2Q5 = 1, 2, 3
-Q = {D2Q9: 9, D3Q27: 27, D2Q5: 5}
-DIM = {D2Q9: 2, D3Q27: 3, D2Q5: 2}
+D2Q9, D3Q27, D2Q5, D3Q15 = 1, 2, 3, 4
+Q = {D2Q9: 9, D3Q27: 27, D2Q5: 5, D3Q15: 15}
+DIM = {D2Q9: 2, D3Q27: 3, D2Q5: 2, D3Q15: 3}
 
 
 def build(force: bool = False, openmp: bool = True) -> str:

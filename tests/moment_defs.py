@@ -9,9 +9,16 @@ D2Q9_E = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0],
 D2Q5_E = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0]], dtype=float)
 D3Q27_E = np.array([[a % 3 - 1, (a // 3) % 3 - 1, a // 9 - 1] for a in range(27)], dtype=float)
 
+# Appendix A, Eq. a1
+D3Q15_E = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                    [1, 1, 1], [-1, 1, 1], [1, -1, 1], [-1, -1, 1], [1, 1, -1], [-1, 1, -1], [1, -1, -1],
+                    [-1, -1, -1]], dtype=float)
+
 W_D2Q9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 W_D2Q5 = np.array([1 / 3] + [1 / 6] * 4)
 W_D3Q27 = np.array([np.prod([2 / 3 if c == 0 else 1 / 6 for c in e]) for e in D3Q27_E])
+# textbook D3Q15 weights (rest 2/9, axes 1/9, corners 1/72)
+W_D3Q15 = np.array([2 / 9] + [1 / 9] * 6 + [1 / 72] * 8)
 
 
 def central(f, E, u, a, b, c=0):
@@ -48,3 +55,14 @@ def L_d2q5():
     ex, ey = D2Q5_E[:, 0], D2Q5_E[:, 1]
     one = np.ones(5)
     return np.stack([one, ex, ey, 5 * (ex ** 2 + ey ** 2) - 4 * one, ex ** 2 - ey ** 2], axis=1)
+
+
+def K_d3q15():
+    """Columns |K_0>..|K_14> of Eq. 2A."""
+    ex, ey, ez = D3Q15_E[:, 0], D3Q15_E[:, 1], D3Q15_E[:, 2]
+    one = np.ones(15)
+    e2 = ex ** 2 + ey ** 2 + ez ** 2
+    return np.stack([one, ex, ey, ez, ex * ey, ex * ez, ey * ez, ex ** 2 - ey ** 2, e2 - 3 * ez ** 2,
+                     e2 - 2 * one, 5 * ex * e2 - 13 * ex, 5 * ey * e2 - 13 * ey, 5 * ez * e2 - 13 * ez,
+                     ex * ey * ez,
+                     30 * (ex ** 2 * ey ** 2 + ex ** 2 * ez ** 2 + ey ** 2 * ez ** 2) - 40 * e2 + 32 * one], axis=1)
