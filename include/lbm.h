@@ -48,6 +48,7 @@ typedef struct lbm_ctx lbm_ctx;
 #define LBM_D2Q9 1     /* flow, Sec. 4 */
 #define LBM_D3Q27 2    /* flow, Appendix A extended to D3Q27 */
 #define LBM_D2Q5_CDE 3 /* passive scalar with source, Sec. 5 */
+#define LBM_D3Q15 4    /* flow, Appendix A (Eqs. a1, 2A, 6A-13A); FP64 storage only */
 
 /* Population storage / arithmetic.
  *   LBM_FP64     : populations in FP64, FP64 arithmetic (the reference form).
@@ -86,6 +87,13 @@ typedef struct {
  *   D3Q27 : omega[1] trace of the second-order central moments (bulk),
  *           omega[2] their deviatoric and off-diagonal parts (shear, 1/tau),
  *           omega[3..6] every central moment of order 3..6.
+ *   D3Q15 : rates of Appendix A Eq. 6A: omega[1] = omega_9 (trace, bulk),
+ *           omega[2] = omega_4 .. omega_8 (shear, 1/tau), omega[3] = omega_10 ..
+ *           omega_13 (third order), omega[4] = omega_14 (fourth order).
+ *           Readings of the appendix built in: omega_9 relaxes the trace
+ *           towards rho; the populations are exactly f + K g (the printed
+ *           f^p_12 has the sign of g_13 flipped); the fourth-order target is
+ *           the product of the post-collision kappa_xx and kappa_yy over rho.
  * Entries not listed for a lattice are ignored. */
 typedef struct {
     double omega[9];
@@ -259,9 +267,38 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count);
  * table too short), LBM_ECUDA. */
 int lbm_batch_step(lbm_batch *b, long n);
 
-/* Kernel launches issued by lbm_batch_step so far (one per step, whether
- * launched directly or as a node of a replayed graph). */
+/* Kernel launches issued so far: one per step of lbm_batch_step (whether
+ * launched directly or as a node of a replayed graph) plus the trial launches
+ * of lbm_batch_autotune. */
 int lbm_batch_launch_count(const lbm_batch *b, long long *count);
+
+/* Tiling of the batched launch.  The nodes of every member are cut into tiles
+ * of `tile` nodes (128, 256 or 512; one thread per node, `tile` threads per
+ * block), numbered member after member.  persistent = 0: one block per tile;
+ * persistent = 1: a grid of as many blocks as the GPU holds resident at once,
+ * each block taking a contiguous run of tiles (so that it reloads a member's
+ * descriptor only when the run crosses into the next member).  Reduced-
+ * precision batches accept every combination (default 256 / 0); FP64
+ * batches only 256 / 0.  The arithmetic per node does not depend on the
+ * tiling.  A change drops a captured graph.  Errors: LBM_EINVAL. */
+int lbm_batch_set_tiling(lbm_batch *b, int tile, int persistent);
+
+/* Current tiling and the grid (blocks) a launch uses with it.  Any output
+ * pointer may be NULL.  Errors: LBM_EINVAL (b NULL). */
+int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid);
+
+/* Autotuner: runs every tiling the batch accepts for trial_steps launches
+ * (after one warm-up launch each), timed with CUDA events on the batch's
+ * stream, and keeps the fastest (ties: the first tried).  The trials leave
+ * the members' state, step counters and envelope position unchanged: each
+ * reads the current populations and writes only the second buffer, which the
+ * next step overwrites anyway.  *best_us (if not NULL) receives the fastest
+ * average time per launch in microseconds; all_us (if not NULL, 6 entries)
+ * the average of every tiling, at index 2 * j + persistent for the tile sizes
+ * j = 0, 1, 2 (128, 256, 512 nodes), -1 for tilings not tried.  Blocks the
+ * host until the trials finish.  Errors: LBM_EINVAL (trial_steps outside
+ * [1, 1000]), LBM_ESTATE (a member not initialised), LBM_ECUDA. */
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *all_us);
 
 /* Replay steps as CUDA graphs of `steps_per_graph` launches each (a positive
  * even number; 0 turns graphs off, the default).  lbm_batch_step(b, n) then

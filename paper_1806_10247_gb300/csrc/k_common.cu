@@ -1,6 +1,7 @@
 // Lattice-generic kernels: equilibrium fill, conversion between f(t) and the
 // stored (inverse-streamed) layout, macroscopic moments and deterministic
 // FP64 reductions.
+#include "lbm_d3q15.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
 
@@ -34,8 +35,9 @@ __device__ __forceinline__ void dev_moments(const T *__restrict__ fin, const Geo
 }
 
 // Equilibrium populations whose central moments are Eq. 20 (flow; the
-// product of 1D profiles, which reproduces c_s^2 rho per squared direction)
-// or Eq. 39 (D2Q5 scalar: moments phi, phi u, phi (1/3 + u^2)).
+// product of 1D profiles, which reproduces c_s^2 rho per squared direction;
+// for D3Q15 the populations with the Maxwellian moments of its fifteen basis
+// monomials) or Eq. 39 (D2Q5 scalar: moments phi, phi u, phi (1/3 + u^2)).
 template <class L>
 __global__ void __launch_bounds__(kBlock)
 k_equilibrium(Geom g, double rho0, double u0x, double u0y, double u0z, const double *__restrict__ rho,
@@ -50,7 +52,9 @@ k_equilibrium(Geom g, double rho0, double u0x, double u0y, double u0z, const dou
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         double v;
-        if (L::Q == 5) {
+        if (L::Q == 15) {
+            v = d3q15_equilibrium(r, ux, uy, uz, a);
+        } else if (L::Q == 5) {
             const int ex = L::ex(a), ey = L::ey(a);
             if (ex == 0 && ey == 0) v = r * ((1.0 / 3.0) - ux * ux - uy * uy);
             else if (ex != 0) v = 0.5 * r * ((1.0 / 3.0) + ux * ux + (double)ex * ux);
@@ -294,7 +298,9 @@ k_init_rp(Geom g, double rho_ref, double rho0, double u0x, double u0y, double u0
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         double v;
-        if (L::Q == 5) {
+        if (L::Q == 15) {
+            v = d3q15_equilibrium(r, ux, uy, uz, a);
+        } else if (L::Q == 5) {
             const int ex = L::ex(a), ey = L::ey(a);
             if (ex == 0 && ey == 0) v = r * ((1.0 / 3.0) - ux * ux - uy * uy);
             else if (ex != 0) v = 0.5 * r * ((1.0 / 3.0) + ux * ux + (double)ex * ux);
@@ -376,6 +382,7 @@ cudaError_t by_storage(int storage, Fn &&fn)
     }
 }
 
+// Lattices with reduced-precision storage.
 template <class Fn>
 cudaError_t by_lattice(int lattice, Fn &&fn)
 {
@@ -387,12 +394,20 @@ cudaError_t by_lattice(int lattice, Fn &&fn)
     }
 }
 
+// Every lattice (FP64 storage).
+template <class Fn>
+cudaError_t by_lattice64(int lattice, Fn &&fn)
+{
+    if (lattice == LD3Q15::ID) return fn(LD3Q15{});
+    return by_lattice(lattice, fn);
+}
+
 }  // namespace
 
 cudaError_t equilibrium(int lattice, const Geom &g, double rho0, const double *u0, const double *rho,
                         const double *u, double *dst, cudaStream_t s)
 {
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_equilibrium<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho0, u0[0], u0[1], u0[2], rho, u, dst);
         return cudaGetLastError();
@@ -402,7 +417,7 @@ cudaError_t equilibrium(int lattice, const Geom &g, double rho0, const double *u
 cudaError_t scatter_to_stored(int lattice, const Geom &g, const double *plain, double *stored,
                               cudaStream_t s)
 {
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_scatter<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, plain, stored);
         return cudaGetLastError();
@@ -412,7 +427,7 @@ cudaError_t scatter_to_stored(int lattice, const Geom &g, const double *plain, d
 cudaError_t gather_from_stored(int lattice, const Geom &g, const double *stored, double *plain,
                                cudaStream_t s)
 {
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_gather<LT><<<grid_for(g.N), kBlock, 0, s>>>(g, stored, plain);
         return cudaGetLastError();
@@ -431,7 +446,7 @@ cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, in
                 return cudaGetLastError();
             });
         });
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_moments<LT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, half,
                                                                 rho, u);
@@ -462,7 +477,7 @@ cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap
                 return cudaGetLastError();
             });
         });
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_reduce_partial<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, snap,
                                                               have_snap, partials);
@@ -518,14 +533,17 @@ cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, c
 void d2q9_batch_coef(const double omega[9], BatchItem &item);
 void d2q5_batch_coef(const double omega[9], BatchItem &item);
 void d3q27_batch_coef(const double omega[9], BatchItem &item);
+void d3q15_batch_coef(const double omega[9], BatchItem &item);
 cudaError_t d2q9_batch_step(const BatchLaunch &, int, cudaStream_t);
 cudaError_t d2q5_batch_step(const BatchLaunch &, int, cudaStream_t);
 cudaError_t d3q27_batch_step(const BatchLaunch &, int, cudaStream_t);
+cudaError_t d3q15_batch_step(const BatchLaunch &, int, cudaStream_t);
 
 void batch_coef(int lattice, const double omega[9], BatchItem &item)
 {
     if (lattice == LD2Q9::ID) d2q9_batch_coef(omega, item);
     else if (lattice == LD2Q5::ID) d2q5_batch_coef(omega, item);
+    else if (lattice == LD3Q15::ID) d3q15_batch_coef(omega, item);
     else d3q27_batch_coef(omega, item);
 }
 
@@ -533,6 +551,7 @@ cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStrea
 {
     if (lattice == LD2Q9::ID) return d2q9_batch_step(L, nblocks, s);
     if (lattice == LD2Q5::ID) return d2q5_batch_step(L, nblocks, s);
+    if (lattice == LD3Q15::ID) return d3q15_batch_step(L, nblocks, s);
     return d3q27_batch_step(L, nblocks, s);
 }
 
@@ -554,7 +573,7 @@ cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int 
                 return cudaGetLastError();
             });
         });
-    return by_lattice(lattice, [&](auto L) {
+    return by_lattice64(lattice, [&](auto L) {
         using LT = decltype(L);
         k_reduce_partial_sums<LT><<<nblocks, kBlock, 0, a.stream>>>(a.g, a.fin, partials);
         cudaError_t e = cudaGetLastError();

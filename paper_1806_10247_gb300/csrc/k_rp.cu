@@ -355,17 +355,31 @@ k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, f
 }
 
 // --------------------------------------------------------------- batched ---
+//
+// A batched launch covers the tiles of every member lattice (TB nodes per
+// tile, TB threads per block, tiles numbered member after member).  Either
+// each block takes one tile, or (persistent grid) each block takes a
+// contiguous run of tiles, so that consecutive tiles mostly belong to the same
+// member and its descriptor is staged into shared memory once per run.
+
+// Member owning tile `tile`: `cur` if it still does (tiles ascend within a
+// block), else a binary search for the last i with first[i] <= tile.
+__device__ __forceinline__ int tile_item(const int *__restrict__ first, int count, int tile, int cur)
+{
+    if (cur >= 0 && (cur + 1 == count || tile < __ldg(first + cur + 1))) return cur;
+    int lo = cur < 0 ? 0 : cur, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(first + mid) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ BatchLaunch L)
+__device__ __forceinline__ void node9(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
@@ -389,15 +403,9 @@ __global__ void __launch_bounds__(kBlock) k_batch9(const __grid_constant__ Batch
 
 // D2Q5 items carry Coef5 (double) in coef[0..11] and the rates in coef[12..15].
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ BatchLaunch L)
+__device__ __forceinline__ void node5(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
@@ -430,15 +438,9 @@ __global__ void __launch_bounds__(kBlock) k_batch5(const __grid_constant__ Batch
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ BatchLaunch L)
+__device__ __forceinline__ void node27(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
@@ -460,6 +462,49 @@ __global__ void __launch_bounds__(kBlock, 4) k_batch27(const __grid_constant__ B
     collide27(m, B.frho_ref, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
+}
+
+// Tile loop shared by the three lattices; NODE is node9 / node5 / node27.
+template <int TB, class Node>
+__device__ __forceinline__ void batch_tiles(const BatchLaunch &L, Node node)
+{
+    __shared__ BatchItem B;
+    int t0 = blockIdx.x, t1 = blockIdx.x + 1;
+    if (L.chunk > 0) {
+        t0 = blockIdx.x * L.chunk;
+        t1 = min(t0 + L.chunk, L.ntiles);
+    }
+    int cur = -1;
+    for (int tile = t0; tile < t1; tile++) {
+        const int it = tile_item(L.first, L.count, tile, cur);
+        if (it != cur) {  // block-uniform
+            if (cur >= 0) __syncthreads();
+            stage_to_shared(B, L.items[it]);
+            __syncthreads();
+            cur = it;
+        }
+        const int i = (tile - __ldg(L.first + it)) * TB + (int)threadIdx.x;
+        if (i < B.g.N) node(B, L, it, i);
+    }
+}
+
+template <class T, int TB>
+__global__ void __launch_bounds__(TB) k_batch9(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node9<T>(B, L2, it, i); });
+}
+
+template <class T, int TB>
+__global__ void __launch_bounds__(TB) k_batch5(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node5<T>(B, L2, it, i); });
+}
+
+// 1024 / TB blocks per SM keep the D3Q27 kernel at <= 64 registers.
+template <class T, int TB>
+__global__ void __launch_bounds__(TB, 1024 / TB) k_batch27(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node27<T>(B, L2, it, i); });
 }
 
 template <class T>
@@ -504,13 +549,53 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
     return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t batch_t(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
+template <class T, int TB>
+cudaError_t batch_tb(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    if (lattice == LD2Q9::ID) k_batch9<T><<<nblocks, kBlock, 0, s>>>(L);
-    else if (lattice == LD2Q5::ID) k_batch5<T><<<nblocks, kBlock, 0, s>>>(L);
-    else k_batch27<T><<<nblocks, kBlock, 0, s>>>(L);
+    if (lattice == LD2Q9::ID) k_batch9<T, TB><<<nblocks, TB, 0, s>>>(L);
+    else if (lattice == LD2Q5::ID) k_batch5<T, TB><<<nblocks, TB, 0, s>>>(L);
+    else k_batch27<T, TB><<<nblocks, TB, 0, s>>>(L);
     return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t batch_t(int lattice, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
+{
+    switch (tile) {
+    case 128: return batch_tb<T, 128>(lattice, L, nblocks, s);
+    case 256: return batch_tb<T, 256>(lattice, L, nblocks, s);
+    case 512: return batch_tb<T, 512>(lattice, L, nblocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class T, int TB>
+int resident_tb(int lattice)
+{
+    int per_sm = 0;
+    cudaError_t e;
+    if (lattice == LD2Q9::ID) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch9<T, TB>, TB, 0);
+    else if (lattice == LD2Q5::ID) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch5<T, TB>, TB, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch27<T, TB>, TB, 0);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sms;
+}
+
+template <class T>
+int resident_t(int lattice, int tile)
+{
+    switch (tile) {
+    case 128: return resident_tb<T, 128>(lattice);
+    case 256: return resident_tb<T, 256>(lattice);
+    case 512: return resident_tb<T, 512>(lattice);
+    default: return 0;
+    }
 }
 
 }  // namespace
@@ -525,13 +610,23 @@ cudaError_t rp_step(int lattice, const LaunchArgs &a)
     }
 }
 
-cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
     switch (storage) {
-    case 1: return batch_t<float>(lattice, L, nblocks, s);
-    case 2: return batch_t<__half>(lattice, L, nblocks, s);
-    case 3: return batch_t<__nv_bfloat16>(lattice, L, nblocks, s);
+    case 1: return batch_t<float>(lattice, L, nblocks, tile, s);
+    case 2: return batch_t<__half>(lattice, L, nblocks, tile, s);
+    case 3: return batch_t<__nv_bfloat16>(lattice, L, nblocks, tile, s);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+int rp_batch_resident(int lattice, int storage, int tile)
+{
+    switch (storage) {
+    case 1: return resident_t<float>(lattice, tile);
+    case 2: return resident_t<__half>(lattice, tile);
+    case 3: return resident_t<__nv_bfloat16>(lattice, tile);
+    default: return 0;
     }
 }
 

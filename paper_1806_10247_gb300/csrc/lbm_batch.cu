@@ -8,6 +8,13 @@
 // argument.  The envelope pairs of a step travel in the launch arguments for
 // batches of up to kInlinePairs lattices; larger batches copy a per-call
 // table through one of two alternating pinned staging slots.
+//
+// Tiling (reduced-precision batches): the nodes of every member are cut into
+// tiles of 128, 256 or 512 nodes (one thread per node); a launch either gives
+// each tile its own block or runs a persistent grid (as many blocks as are
+// resident on the GPU at once) whose blocks take contiguous runs of tiles.
+// lbm_batch_autotune times every combination on the batch itself and keeps the
+// fastest.  FP64 batches always use 256-node tiles, one block per tile.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,8 +33,12 @@ struct lbm_batch {
     int lattice = 0;
     cudaStream_t stream = nullptr;
     int count = 0;
-    int nblocks = 0;
-    int *d_first = nullptr;
+    // tile sizes kTiles[j]: first tile of each member (device) and the tile count
+    int *d_first[3] = {nullptr, nullptr, nullptr};
+    long long ntiles[3] = {0, 0, 0};
+    int tile_idx = 1;                  // index into kTiles of the tiling in use
+    bool persistent = false;
+    int resident[3] = {0, 0, 0};       // resident blocks on the GPU per tile size (0 = not queried)
     BatchItem *d_items = nullptr;      // descriptors on the device
     BatchItem *h_items = nullptr;      // pinned staging of the descriptors
     cudaEvent_t ev_items = nullptr;    // recorded after the last descriptor copy
@@ -55,6 +66,8 @@ struct lbm_batch {
 
 namespace {
 
+constexpr int kTiles[3] = {128, 256, 512};
+
 thread_local std::string g_batch_create_error;
 
 int bfail(lbm_batch *b, int code, const char *fmt, ...)
@@ -76,8 +89,8 @@ int bfail(lbm_batch *b, int code, const char *fmt, ...)
     } while (0)
 
 // Second value of a step's envelope pair as the batched kernels expect it:
-// D2Q9 (a_pre + a_post)/12, D2Q5 (a_pre + a_post)/10, D3Q27 a_post -- the same
-// expressions as the single-lattice launchers.
+// D2Q9 (a_pre + a_post)/12, D2Q5 (a_pre + a_post)/10, D3Q27 and D3Q15 a_post --
+// the same expressions as the single-lattice launchers.
 double pair_second(int lattice, double apre, double apost)
 {
     if (lattice == LBM_D2Q9) return (apre + apost) / 12.0;
@@ -126,26 +139,30 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count)
     b->lattice = ctxs[0]->lattice;
     b->stream = ctxs[0]->stream;
     b->count = count;
-    std::vector<int> first(count);
-    long long nb = 0;
-    for (int i = 0; i < count; i++) {
-        first[i] = (int)nb;
-        nb += batch_blocks(ctxs[i]->g);
+    std::vector<int> first[3];
+    for (int j = 0; j < 3; j++) {
+        first[j].resize(count);
+        long long nt = 0;
+        for (int i = 0; i < count; i++) {
+            first[j][i] = (int)std::min(nt, 2147483647LL);
+            nt += (ctxs[i]->g.N + kTiles[j] - 1) / kTiles[j];
+        }
+        b->ntiles[j] = nt;
     }
-    if (nb > 2147483647LL) {
+    if (b->ntiles[0] > 2147483647LL) {
         delete b;
-        return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: more than 2^31-1 blocks");
+        return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: more than 2^31-1 tiles of 128 nodes");
     }
-    b->nblocks = (int)nb;
     b->item_version.assign(count, -1);
     b->item_buf0.assign(count, nullptr);
-    cudaError_t e = cudaMalloc(&b->d_first, count * sizeof(int));
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < 3 && e == cudaSuccess; j++) e = cudaMalloc(&b->d_first[j], count * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_items, cudaEventDisableTiming);
     for (int s = 0; s < 2 && e == cudaSuccess; s++) e = cudaEventCreateWithFlags(&b->ev[s], cudaEventDisableTiming);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_first, first.data(), count * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    for (int j = 0; j < 3 && e == cudaSuccess; j++)
+        e = cudaMemcpyAsync(b->d_first[j], first[j].data(), count * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         int code = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
@@ -167,7 +184,7 @@ void lbm_batch_destroy(lbm_batch *b)
     if (b->ev_graph) cudaEventDestroy(b->ev_graph);
     cudaFreeHost(b->h_gpairs);
     cudaFree(b->d_gpairs);
-    cudaFree(b->d_first);
+    for (int j = 0; j < 3; j++) cudaFree(b->d_first[j]);
     cudaFree(b->d_items);
     cudaFreeHost(b->h_items);
     if (b->ev_items) cudaEventDestroy(b->ev_items);
@@ -238,11 +255,37 @@ int refresh_descriptors(lbm_batch *b, int *parity)
     return LBM_OK;
 }
 
+bool reduced_precision(const lbm_batch *b) { return b->ctx[0]->storage != LBM_FP64; }
+
+// One batched launch with the batch's tiling: fills in the tile map of L.
+cudaError_t launch_tiled(lbm_batch *b, BatchLaunch L, int tile_idx, bool persistent, cudaStream_t s)
+{
+    if (!reduced_precision(b)) {
+        L.first = b->d_first[1];
+        L.ntiles = (int)b->ntiles[1];
+        L.chunk = 0;
+        return batch_step(b->lattice, L, (int)b->ntiles[1], s);
+    }
+    const int nt = (int)b->ntiles[tile_idx];
+    int grid = nt;
+    L.first = b->d_first[tile_idx];
+    L.ntiles = nt;
+    L.chunk = 0;
+    if (persistent) {
+        if (b->resident[tile_idx] == 0)
+            b->resident[tile_idx] = rp_batch_resident(b->lattice, b->ctx[0]->storage, kTiles[tile_idx]);
+        const int r = b->resident[tile_idx];
+        if (r > 0 && r < nt) {
+            L.chunk = (nt + r - 1) / r;
+            grid = (nt + L.chunk - 1) / L.chunk;
+        }
+    }
+    return rp_batch_step(b->lattice, b->ctx[0]->storage, L, grid, kTiles[tile_idx], s);
+}
+
 cudaError_t launch_one(lbm_batch *b, const BatchLaunch &L, cudaStream_t s)
 {
-    const int storage = b->ctx[0]->storage;
-    return storage == LBM_FP64 ? batch_step(b->lattice, L, b->nblocks, s)
-                               : rp_batch_step(b->lattice, storage, L, b->nblocks, s);
+    return launch_tiled(b, L, b->tile_idx, b->persistent, s);
 }
 
 // Envelope pairs of steps t_i .. t_i + k - 1 of every member into dst (double2
@@ -260,6 +303,60 @@ void fill_pairs(const lbm_batch *b, void *dst, long k)
             if (fp32) reinterpret_cast<float2 *>(dst)[at] = make_float2((float)apre, (float)second);
             else reinterpret_cast<double2 *>(dst)[at] = make_double2(apre, second);
         }
+    }
+}
+
+// Envelope pairs of the members' next n steps into a device table (through
+// one of the two alternating pinned staging slots), referenced by L.
+int stage_pairs(lbm_batch *b, BatchLaunch &L, long n)
+{
+    const int s = b->slot;
+    b->slot ^= 1;
+    // The staging slot was last read by the copy recorded two calls ago.
+    BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
+    int rc = grow_pairs(b, s, (size_t)n * b->count);
+    if (rc != LBM_OK) return rc;
+    fill_pairs(b, b->h_pairs[s], n);
+    const bool fp32 = reduced_precision(b);
+    const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
+    BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * esz, cudaMemcpyHostToDevice,
+                        b->stream),
+        "lbm_batch_step: copy envelope pairs");
+    BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
+    if (fp32) L.pairsf = reinterpret_cast<const float2 *>(b->d_pairs[s]);
+    else L.pairs = b->d_pairs[s];
+    return LBM_OK;
+}
+
+// Envelope pairs of step t_i + k of every member into the launch arguments.
+void inline_pairs_of_step(const lbm_batch *b, BatchLaunch &L, long k)
+{
+    for (int i = 0; i < b->count; i++) {
+        double apre, apost;
+        lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t + k, apre, apost);
+        const double second = pair_second(b->lattice, apre, apost);
+        L.inl[i] = make_double2(apre, second);
+        L.inlf[i] = make_float2((float)apre, (float)second);
+    }
+}
+
+int check_members(lbm_batch *b, long n, const char *what)
+{
+    for (int i = 0; i < b->count; i++) {
+        const lbm_ctx *c = b->ctx[i];
+        if (!c->initialised) return bfail(b, LBM_ESTATE, "%s: context %d not initialised", what, i);
+        if (!lbmc::envelope_covers(c, c->t, n))
+            return bfail(b, LBM_EINVAL, "%s: context %d steps outside its envelope table", what, i);
+    }
+    return LBM_OK;
+}
+
+void drop_graph(lbm_batch *b)
+{
+    if (b->gexec) {
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
     }
 }
 
@@ -285,7 +382,6 @@ int capture_graph(lbm_batch *b, int parity)
     for (int k = 0; k < b->graph_steps && e == cudaSuccess; k++) {
         BatchLaunch L{};
         L.items = b->d_items;
-        L.first = b->d_first;
         L.count = b->count;
         L.k = k;
         L.parity = (parity + k) & 1;
@@ -315,14 +411,10 @@ int lbm_batch_step(lbm_batch *b, long n)
     if (n < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: n < 0");
     if (n == 0) return LBM_OK;
     if (n > 2147483647L / b->count) return bfail(b, LBM_EINVAL, "lbm_batch_step: n too large");
-    for (int i = 0; i < b->count; i++) {
-        const lbm_ctx *c = b->ctx[i];
-        if (!c->initialised) return bfail(b, LBM_ESTATE, "lbm_batch_step: context %d not initialised", i);
-        if (!lbmc::envelope_covers(c, c->t, n))
-            return bfail(b, LBM_EINVAL, "lbm_batch_step: context %d steps outside its envelope table", i);
-    }
+    int rc = check_members(b, n, "lbm_batch_step");
+    if (rc != LBM_OK) return rc;
     int parity = 0;
-    int rc = refresh_descriptors(b, &parity);
+    rc = refresh_descriptors(b, &parity);
     if (rc != LBM_OK) return rc;
 
     // Whole graph replays first (graph_steps is even: parity is unchanged).
@@ -351,37 +443,16 @@ int lbm_batch_step(lbm_batch *b, long n)
 
     BatchLaunch L{};
     L.items = b->d_items;
-    L.first = b->d_first;
     L.count = b->count;
     const bool inline_pairs = b->count <= kInlinePairs;
     if (!inline_pairs) {
-        const int s = b->slot;
-        b->slot ^= 1;
-        // The staging slot was last read by the copy recorded two calls ago.
-        BCK(cudaEventSynchronize(b->ev[s]), "lbm_batch_step: wait for staging slot");
-        rc = grow_pairs(b, s, (size_t)n * b->count);
+        rc = stage_pairs(b, L, n);
         if (rc != LBM_OK) return rc;
-        fill_pairs(b, b->h_pairs[s], n);
-        const bool fp32 = b->ctx[0]->storage != LBM_FP64;
-        const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
-        BCK(cudaMemcpyAsync(b->d_pairs[s], b->h_pairs[s], (size_t)n * b->count * esz, cudaMemcpyHostToDevice,
-                            b->stream),
-            "lbm_batch_step: copy envelope pairs");
-        BCK(cudaEventRecord(b->ev[s], b->stream), "lbm_batch_step: record");
-        if (fp32) L.pairsf = reinterpret_cast<const float2 *>(b->d_pairs[s]);
-        else L.pairs = b->d_pairs[s];
     }
     for (long k = 0; k < n; k++) {
         L.k = (int)k;
         L.parity = (parity + (int)k) & 1;
-        if (inline_pairs)
-            for (int i = 0; i < b->count; i++) {
-                double apre, apost;
-                lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t + k, apre, apost);
-                const double second = pair_second(b->lattice, apre, apost);
-                L.inl[i] = make_double2(apre, second);
-                L.inlf[i] = make_float2((float)apre, (float)second);
-            }
+        if (inline_pairs) inline_pairs_of_step(b, L, k);
         cudaError_t e = launch_one(b, L, b->stream);
         if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_step: kernel: %s", cudaGetErrorString(e));
         b->launches++;
@@ -412,6 +483,105 @@ int lbm_batch_set_graph(lbm_batch *b, int steps_per_graph)
         b->d_gpairs = nullptr;
         b->graph_steps = steps_per_graph;
     }
+    return LBM_OK;
+}
+
+int lbm_batch_set_tiling(lbm_batch *b, int tile, int persistent)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    int j = -1;
+    for (int k = 0; k < 3; k++)
+        if (kTiles[k] == tile) j = k;
+    if (j < 0 || (persistent != 0 && persistent != 1))
+        return bfail(b, LBM_EINVAL, "lbm_batch_set_tiling: tile must be 128, 256 or 512 and persistent 0 or 1");
+    if (!reduced_precision(b) && (tile != 256 || persistent))
+        return bfail(b, LBM_EINVAL, "lbm_batch_set_tiling: FP64 batches use 256-node tiles, one block per tile");
+    if (j != b->tile_idx || (persistent != 0) != b->persistent) {
+        drop_graph(b);
+        b->tile_idx = j;
+        b->persistent = persistent != 0;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    if (tile) *tile = kTiles[b->tile_idx];
+    if (persistent) *persistent = b->persistent ? 1 : 0;
+    if (grid) {
+        long long g = b->ntiles[b->tile_idx];
+        if (b->persistent) {
+            if (b->resident[b->tile_idx] == 0)
+                b->resident[b->tile_idx] = rp_batch_resident(b->lattice, b->ctx[0]->storage, kTiles[b->tile_idx]);
+            const long long r = b->resident[b->tile_idx];
+            if (r > 0 && r < g) {
+                const long long chunk = (g + r - 1) / r;
+                g = (g + chunk - 1) / chunk;
+            }
+        }
+        *grid = (int)g;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *all_us)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    if (trial_steps < 1 || trial_steps > 1000)
+        return bfail(b, LBM_EINVAL, "lbm_batch_autotune: trial_steps must be in [1, 1000]");
+    int rc = check_members(b, 1, "lbm_batch_autotune");
+    if (rc != LBM_OK) return rc;
+    int parity = 0;
+    rc = refresh_descriptors(b, &parity);
+    if (rc != LBM_OK) return rc;
+    // Trial launches keep the buffer parity: every one reads the current state
+    // and overwrites the other buffer, which holds nothing until the next step.
+    BatchLaunch L{};
+    L.items = b->d_items;
+    L.count = b->count;
+    L.k = 0;
+    L.parity = parity;
+    if (b->count <= kInlinePairs) inline_pairs_of_step(b, L, 0);
+    else if ((rc = stage_pairs(b, L, 1)) != LBM_OK) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(cudaEventCreate(&e0), "lbm_batch_autotune: event");
+    cudaError_t e = cudaEventCreate(&e1);
+    if (all_us)
+        for (int k = 0; k < 6; k++) all_us[k] = -1.0;
+    float best = -1.0f;
+    int best_j = b->tile_idx;
+    bool best_p = b->persistent;
+    for (int j = 0; j < 3 && e == cudaSuccess; j++)
+        for (int p = 0; p < 2 && e == cudaSuccess; p++) {
+            if (!reduced_precision(b) && (j != 1 || p)) continue;
+            e = launch_tiled(b, L, j, p != 0, b->stream);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < trial_steps && e == cudaSuccess; r++) e = launch_tiled(b, L, j, p != 0, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            b->launches += trial_steps + 1;
+            if (e == cudaSuccess && all_us) all_us[2 * j + p] = 1000.0 * ms / trial_steps;
+            if (e == cudaSuccess && (best < 0.0f || ms < best)) {
+                best = ms;
+                best_j = j;
+                best_p = p != 0;
+            }
+        }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_autotune: %s", cudaGetErrorString(e));
+    if (best_j != b->tile_idx || best_p != b->persistent) {
+        drop_graph(b);
+        b->tile_idx = best_j;
+        b->persistent = best_p;
+    }
+    if (best_us) *best_us = 1000.0 * best / trial_steps;
     return LBM_OK;
 }
 

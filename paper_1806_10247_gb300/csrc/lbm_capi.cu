@@ -43,14 +43,18 @@ int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
 
 #define CK(call, what) LBM_CK(call, what)
 
-int lattice_q(int lattice) { return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q27 ? 27 : lattice == LBM_D2Q5_CDE ? 5 : 0; }
-int lattice_dim(int lattice) { return lattice == LBM_D3Q27 ? 3 : 2; }
+int lattice_q(int lattice)
+{
+    return lattice == LBM_D2Q9 ? 9 : lattice == LBM_D3Q27 ? 27 : lattice == LBM_D2Q5_CDE ? 5 : lattice == LBM_D3Q15 ? 15 : 0;
+}
+int lattice_dim(int lattice) { return (lattice == LBM_D3Q27 || lattice == LBM_D3Q15) ? 3 : 2; }
 
 // Relaxation rates that a lattice uses (the others are ignored).
 bool omega_used(int lattice, int k)
 {
     if (lattice == LBM_D2Q9) return k >= 3 && k <= 8;
     if (lattice == LBM_D2Q5_CDE) return k >= 1 && k <= 4;
+    if (lattice == LBM_D3Q15) return k >= 1 && k <= 4;
     return k >= 1 && k <= 6;
 }
 
@@ -243,6 +247,8 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     if (q == 0) return fail(nullptr, LBM_EINVAL, "lbm_create: unknown lattice %d", lattice);
     if (storage < LBM_FP64 || storage > LBM_BF16_DEV)
         return fail(nullptr, LBM_EINVAL, "lbm_create: unsupported storage %d", storage);
+    if (lattice == LBM_D3Q15 && storage != LBM_FP64)
+        return fail(nullptr, LBM_EINVAL, "lbm_create: D3Q15 supports FP64 storage only");
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: extents must be >= 1");
     if (lattice_dim(lattice) == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nz must be 1 for a 2D lattice");
     const long long N = (long long)nx * ny * nz;
@@ -433,6 +439,7 @@ int lbm_step(lbm_ctx *c, long n)
             switch (c->lattice) {
             case LBM_D2Q9: e = d2q9_step(a); break;
             case LBM_D2Q5_CDE: e = d2q5_step(a); break;
+            case LBM_D3Q15: e = d3q15_step(a); break;
             default: e = d3q27_step(a); break;
             }
         }

@@ -66,8 +66,13 @@ void batch_coef(int lattice, const double omega[9], BatchItem &item);
 constexpr int kInlinePairs = 32;
 struct BatchLaunch {
     const BatchItem *items;
-    const int *first;  // first block of each item (ascending, first[0] = 0)
+    const int *first;  // first tile of each item (ascending, first[0] = 0)
     int count;
+    // Reduced-precision kernels only: the launch covers ntiles tiles of the
+    // kernel's tile size; with chunk > 0 block b takes tiles
+    // [b*chunk, min((b+1)*chunk, ntiles)) (persistent grid), else tile b.
+    int ntiles;
+    int chunk;
     int k;
     int parity;
     const double2 *pairs;
@@ -79,12 +84,16 @@ struct BatchLaunch {
 
 // One launch advancing every item of a batch by one step.
 cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s);
-cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, cudaStream_t s);
+// tile = nodes per tile = threads per block: 128, 256 or 512.
+cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
+// Blocks of the reduced-precision batch kernel resident on the whole GPU at once.
+int rp_batch_resident(int lattice, int storage, int tile);
 int batch_blocks(const Geom &g);
 
 // One fused stream + collide step (pull form): fin -> fout.
 cudaError_t d2q9_step(const LaunchArgs &a);
 cudaError_t d2q5_step(const LaunchArgs &a);
+cudaError_t d3q15_step(const LaunchArgs &a);
 cudaError_t d3q27_step(const LaunchArgs &a);
 
 // Moments of the current state: rho[N] and u[dim][N] (flow) or phi[N] (scalar);

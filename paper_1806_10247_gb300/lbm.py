@@ -18,20 +18,21 @@ import numpy as np
 
 from . import build as _build
 
-D2Q9, D3Q27, D2Q5_CDE = 1, 2, 3
+D2Q9, D3Q27, D2Q5_CDE, D3Q15 = 1, 2, 3, 4
 FP64, FP32_DEV, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCE_BACK = 0, 1
 FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL = 0, 1, 2
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, -1, -2, -3, -4, -6
-Q = {D2Q9: 9, D3Q27: 27, D2Q5_CDE: 5}
-DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2}
+Q = {D2Q9: 9, D3Q27: 27, D2Q5_CDE: 5, D3Q15: 15}
+DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2, D3Q15: 3}
 
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium", "lbm_set_force",
            "lbm_set_source", "lbm_set_velocity", "lbm_set_envelope", "lbm_step", "lbm_moments",
            "lbm_reduce", "lbm_get_populations", "lbm_set_populations", "lbm_get_step", "lbm_sync",
            "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
-           "lbm_batch_set_graph", "lbm_batch_graph_replays")
+           "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
+           "lbm_batch_autotune")
 
 
 class LBMError(RuntimeError):
@@ -99,6 +100,9 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.lbm_batch_set_graph.argtypes = [vp, ip]
     L.lbm_batch_graph_replays.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_batch_set_tiling.argtypes = [vp, ip, ip]
+    L.lbm_batch_get_tiling.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.lbm_batch_autotune.argtypes = [vp, ip, dp, dp]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
     L.lbm_batch_destroy.argtypes = [vp]
@@ -348,6 +352,30 @@ class Batch:
         self._check(self._L.lbm_batch_graph_replays(self.h, ctypes.byref(v)))
         return v.value
 
+    def set_tiling(self, tile, persistent=False):
+        """Tile of 128/256/512 nodes per block; persistent grid or one block per tile."""
+        self._check(self._L.lbm_batch_set_tiling(self.h, int(tile), int(bool(persistent))))
+
+    def tiling(self):
+        """(tile, persistent, grid) of the launches."""
+        t, p, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.lbm_batch_get_tiling(self.h, ctypes.byref(t), ctypes.byref(p), ctypes.byref(g)))
+        return t.value, bool(p.value), g.value
+
+    def autotune(self, trial_steps=5, all_timings=False):
+        """Time every tiling on the batch itself and keep the fastest; returns
+        its average microseconds per launch (with all_timings, also a dict
+        {(tile, persistent): microseconds} of every tiling tried).  Leaves the
+        state unchanged."""
+        us = ctypes.c_double()
+        every = (ctypes.c_double * 6)()
+        self._check(self._L.lbm_batch_autotune(self.h, int(trial_steps), ctypes.byref(us), every))
+        if not all_timings:
+            return us.value
+        tried = {(t, bool(p)): every[2 * j + p] for j, t in enumerate((128, 256, 512)) for p in (0, 1)
+                 if every[2 * j + p] >= 0}
+        return us.value, tried
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self._L.lbm_batch_destroy(self.h)
@@ -363,7 +391,7 @@ class Batch:
 def from_workload(w, stream=None, envelope_steps=None, storage=FP64) -> Lattice:
     """Lattice set up (force/source, velocity, envelope, equilibrium) from a
     :class:`paper_1806_10247_gb300.workloads.Workload`."""
-    lat = {1: D2Q9, 2: D3Q27, 3: D2Q5_CDE}[w.lattice]
+    lat = {1: D2Q9, 2: D3Q27, 3: D2Q5_CDE, 4: D3Q15}[w.lattice]
     L = Lattice(lat, w.shape, w.omega, wall=w.wall, stream=stream, storage=storage)
     if w.tables is not None:
         if lat == D2Q5_CDE:

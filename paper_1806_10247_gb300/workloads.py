@@ -17,7 +17,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-D2Q9, D3Q27, D2Q5 = 1, 2, 3
+D2Q9, D3Q27, D2Q5, D3Q15 = 1, 2, 3, 4
 SEED = 10247
 
 
@@ -59,6 +59,12 @@ def d2q5_omega(tau_phi: float, w3: float = 1.0, w4: float = 1.0):
 def d3q27_omega(tau: float, bulk: float = 1.0, high=(1.0, 1.0, 1.0, 1.0)):
     """D3Q27 rates: [1] trace (bulk), [2] shear = 1/tau, [3..6] orders 3..6."""
     return (0.0, bulk, 1.0 / tau, high[0], high[1], high[2], high[3], 0.0, 0.0)
+
+
+def d3q15_omega(tau: float, bulk: float = 1.0, third: float = 1.0, fourth: float = 1.0):
+    """D3Q15 rates (Appendix A, Eq. 6A): [1] omega_9 (trace), [2] omega_4..8 = 1/tau,
+    [3] omega_10..13, [4] omega_14."""
+    return (0.0, bulk, 1.0 / tau, third, fourth, 0.0, 0.0, 0.0, 0.0)
 
 
 def poiseuille(ny: int = 33, nx: int = 3, tau: float = 0.8, Fx: float = 1e-6) -> Workload:
@@ -171,6 +177,59 @@ def duct(n: int = 128, nx: int = 3, F0: float = 1e-6, nu: float = 0.05, seed: in
         omega=d3q27_omega(tau_from_nu(nu)), rho0=1.0, u0=(0.0, 0.0, 0.0),
         tables=[(one, one, pz), (zero, one, one), (zero, one, one)], steps=1000,
         meta={"F0": F0, "nu": nu})
+
+
+def batched_sweep(count: int = 2048, seed: int = SEED, nx_range=(32, 512), ny_range=(32, 256)):
+    """Parameter sweep of many small, unevenly sized 2D lattices.
+
+    `count` force-driven D2Q9 channels (x periodic, halfway bounce-back walls in
+    y) with nx ~ U{32..512}, ny ~ U{32..256}, tau ~ U[0.55, 1.5] and a uniform
+    force F_x log-uniform in [1e-7, 1e-4], redrawn until the channel's
+    centreline speed F ny^2 / (8 nu) stays at or below Mach 0.3 (0.3 c_s,
+    c_s = 1/sqrt(3)); plus `count` periodic D2Q5 scalar lattices of the same
+    sizes with tau_phi = tau, advecting velocity (0.01, 0.01) and a constant
+    source A sin(2 pi x/nx) sin(2 pi y/ny), A log-uniform in [1e-7, 1e-4].
+    Returns (channels, scalars)."""
+    rng = np.random.default_rng([seed, 4])
+    u_max = 0.3 / math.sqrt(3.0)
+    channels, scalars = [], []
+    one = np.array([1.0])
+    for k in range(count):
+        nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+        ny = int(rng.integers(ny_range[0], ny_range[1] + 1))
+        tau = float(rng.uniform(0.55, 1.5))
+        nu = (tau - 0.5) / 3.0
+        while True:
+            F = float(10.0 ** rng.uniform(-7.0, -4.0))
+            if F * ny * ny / (8.0 * nu) <= u_max:
+                break
+        A = float(10.0 ** rng.uniform(-7.0, -4.0))
+        channels.append(Workload(
+            name=f"channel_d2q9_{nx}x{ny}_{k}", lattice=D2Q9, shape=(nx, ny, 1), wall=(0, 1, 0),
+            omega=d2q9_omega(tau), rho0=1.0, u0=(0.0, 0.0, 0.0),
+            tables=[(np.array([F]), one, one), (np.array([0.0]), one, one)],
+            meta={"tau": tau, "Fx": F, "nu": nu}))
+        x = np.arange(nx, dtype=np.float64)
+        y = np.arange(ny, dtype=np.float64)
+        scalars.append(Workload(
+            name=f"scalar_d2q5_{nx}x{ny}_{k}", lattice=D2Q5, shape=(nx, ny, 1), wall=(0, 0, 0),
+            omega=d2q5_omega(tau), rho0=1.0, u0=(0.01, 0.01, 0.0),
+            tables=[(A * np.sin(2.0 * math.pi * x / nx), np.sin(2.0 * math.pi * y / ny), one)],
+            meta={"tau_phi": tau, "A": A, "D": nu}))
+    return channels, scalars
+
+
+def duct15(n: int = 45, nx: int = 3, tau: float = 0.76, F0: float = 1e-7) -> Workload:
+    """The paper's D3Q15 demonstration: a square duct (x periodic, halfway
+    bounce-back walls in y and z) of n x n nodes driven by a constant F_x
+    (Sec. 6.4 with Appendix A; 3 x 45 x 45, tau = 0.76, F = 1e-7)."""
+    one = np.array([1.0])
+    zero = np.array([0.0])
+    return Workload(
+        name=f"duct_d3q15_{nx}x{n}x{n}", lattice=D3Q15, shape=(nx, n, n), wall=(0, 1, 1),
+        omega=d3q15_omega(tau), rho0=1.0, u0=(0.0, 0.0, 0.0),
+        tables=[(np.array([F0]), one, one), (zero, one, one), (zero, one, one)], steps=1000,
+        meta={"F0": F0, "nu": (tau - 0.5) / 3.0, "tau": tau})
 
 
 def random_populations(q: int, N: int, weights, seed: int, amp: float = 0.05) -> np.ndarray:

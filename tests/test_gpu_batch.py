@@ -166,3 +166,105 @@ def test_graph_replays_equal_plain_launches(kind, storage):
     for a, b in zip(solo, grp):
         assert a.t == b.t
         assert np.abs(a.get_populations() - b.get_populations()).max() <= tol
+
+
+def _sweep_members(count=40):
+    """A sweep large enough that a persistent grid holds fewer blocks than the
+    batch has tiles (so that blocks take runs of several tiles)."""
+    ch, sc = W.batched_sweep(count=count, seed=11, nx_range=(32, 200), ny_range=(32, 150))
+    return ch, sc
+
+
+@pytest.mark.parametrize("which", ["d2q9", "d2q5"])
+def test_every_tiling_gives_the_same_populations(which):
+    ch, sc = _sweep_members()
+    ws = ch if which == "d2q9" else sc
+    ref = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ws]
+    B = lbm.Batch(ref)
+    assert B.tiling()[:2] == (256, False)
+    B.step(5)
+    want = [G.get_populations() for G in ref]
+    scale = max(float(np.abs(f).max()) for f in want)
+    for tile in (128, 256, 512):
+        for persistent in (False, True):
+            Gs = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ws]
+            Bt = lbm.Batch(Gs)
+            Bt.set_tiling(tile, persistent)
+            t, p, grid = Bt.tiling()
+            ntiles = sum(-(-w.nodes // tile) for w in ws)
+            assert (t, p) == (tile, persistent)
+            if persistent:
+                assert grid < ntiles  # blocks take runs of tiles
+            else:
+                assert grid == ntiles
+            Bt.step(2)
+            Bt.step(3)
+            for a, G in zip(want, Gs):
+                assert G.t == 5
+                # same per-node arithmetic; allow for multiply-add contraction
+                # differences between the kernel instantiations
+                assert np.abs(G.get_populations() - a).max() <= 1e-6 * scale
+            Bt.close()
+            for G in Gs:
+                G.close()
+
+
+def test_tiled_fp32_batch_matches_oracle():
+    ch, _ = _sweep_members(count=12)
+    Gs = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ch]
+    B = lbm.Batch(Gs)
+    B.set_tiling(128, True)
+    B.step(30)
+    for w, G in list(zip(ch, Gs))[:3]:
+        R = oracle_from_workload(w)
+        R.run(30)
+        _, u = G.moments()
+        _, ur = R.moments()
+        err = float(np.sqrt(np.sum((u - ur) ** 2) / np.sum(ur ** 2)))
+        assert err <= 1e-4, (w.name, err)
+
+
+def test_autotune_leaves_the_state_unchanged_and_picks_a_tiling():
+    ch, _ = _sweep_members()
+    Gs = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ch]
+    twins = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ch]
+    B = lbm.Batch(Gs)
+    Bt = lbm.Batch(twins)
+    B.step(3)
+    Bt.step(3)
+    before = [G.get_populations() for G in Gs]
+    n0 = B.launch_count()
+    us, tried = B.autotune(3, all_timings=True)
+    assert us > 0 and len(tried) == 6 and min(tried.values()) == us
+    assert B.launch_count() == n0 + 6 * (3 + 1)  # six tilings, 3 trials + 1 warm-up each
+    tile, persistent, grid = B.tiling()
+    assert tile in (128, 256, 512) and grid > 0
+    for G, f in zip(Gs, before):
+        assert G.t == 3
+        assert np.array_equal(G.get_populations(), f)
+    # the next steps continue from the unchanged state
+    B.set_graph(4)
+    B.step(4)
+    Bt.step(4)
+    scale = max(float(np.abs(f).max()) for f in before)
+    for a, b in zip(Gs, twins):
+        assert a.t == b.t == 7
+        assert np.abs(a.get_populations() - b.get_populations()).max() <= 1e-6 * scale
+
+
+def test_fp64_batch_tiling_is_fixed():
+    ws, fulls = _members("d2q5")
+    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(Gs)
+    with pytest.raises(lbm.LBMError) as e:
+        B.set_tiling(128, False)
+    assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LBMError):
+        B.set_tiling(256, True)
+    B.set_tiling(256, False)
+    n0 = B.launch_count()
+    B.autotune(2)
+    assert B.launch_count() == n0 + 3
+    assert B.tiling()[:2] == (256, False)
+    with pytest.raises(lbm.LBMError):
+        B.autotune(0)

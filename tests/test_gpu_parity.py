@@ -41,7 +41,7 @@ def test_d2q9_poiseuille_config_10k_steps():
 def _random_omega(rng, lattice):
     if lattice == W.D2Q9:
         return (0, 0, 0) + tuple(rng.uniform(0.5, 1.9, 6))
-    if lattice == W.D2Q5:
+    if lattice in (W.D2Q5, W.D3Q15):
         return (0,) + tuple(rng.uniform(0.5, 1.9, 4)) + (0, 0, 0, 0)
     return (0,) + tuple(rng.uniform(0.5, 1.9, 6)) + (0, 0)
 
@@ -50,7 +50,7 @@ def _random_workload(lattice, shape, wall, seed, kind="separable", env=True):
     rng = np.random.default_rng(seed)
     nx, ny, nz = shape
     N = nx * ny * nz
-    dim = 3 if lattice == W.D3Q27 else 2
+    dim = 3 if lattice in (W.D3Q27, W.D3Q15) else 2
     ncomp = 1 if lattice == W.D2Q5 else dim
     if kind == "separable":
         tables = [(1e-4 * rng.standard_normal(nx), 1 + 0.3 * rng.standard_normal(ny),
@@ -189,7 +189,7 @@ def _one_step_sampled(w, G, samples, seed):
     idx = rng.integers(0, w.nodes, samples)
     worst = 0.0
     scale = np.abs(f_t1).max()
-    dim = 3 if w.lattice == O.D3Q27 else 2
+    dim = 3 if w.lattice in (O.D3Q27, O.D3Q15) else 2
     for i in idx:
         x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
         want = np.empty(q)
