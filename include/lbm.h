@@ -277,10 +277,10 @@ int lbm_batch_launch_count(const lbm_batch *b, long long *count);
  * block), numbered member after member.  persistent = 0: one block per tile;
  * persistent = 1: a grid of as many blocks as the GPU holds resident at once,
  * each block taking a contiguous run of tiles (so that it reloads a member's
- * descriptor only when the run crosses into the next member).  Reduced-
- * precision batches accept every combination (default 256 / 0); FP64
- * batches only 256 / 0.  The arithmetic per node does not depend on the
- * tiling.  A change drops a captured graph.  Errors: LBM_EINVAL. */
+ * descriptor only when the run crosses into the next member).  Default
+ * 256 / 0.  The arithmetic per node does not depend on the tiling (up to the
+ * compiler's multiply-add contraction in the different kernel instances).
+ * A change drops a captured graph.  Errors: LBM_EINVAL. */
 int lbm_batch_set_tiling(lbm_batch *b, int tile, int persistent);
 
 /* Current tiling and the grid (blocks) a launch uses with it.  Any output
@@ -309,6 +309,16 @@ int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *a
  * parity changes.  With a time-dependent envelope the host waits for the
  * previous replay before refilling the pinned pairs.  Errors: LBM_EINVAL. */
 int lbm_batch_set_graph(lbm_batch *b, int steps_per_graph);
+
+/* Macroscopic fields of every member (as lbm_moments, Eqs. 24-25 / 42-43):
+ * rho[i] (and, for flow lattices, u[i] as [dim][N]) receive member i's
+ * fields.  where = 0: host pointers; all members' kernels and copies are
+ * queued on the batch's stream and the call synchronises once at the end
+ * (pinned host buffers make the copies asynchronous DMA).  where = 1: device
+ * pointers, asynchronous.  Each member's second population buffer (or its
+ * staging buffer) holds the fields on the way out.  Errors: LBM_EINVAL (NULL
+ * output), LBM_ESTATE, LBM_ECUDA. */
+int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int where, int half_forced);
 
 /* Graph replays issued so far. */
 int lbm_batch_graph_replays(const lbm_batch *b, long long *count);

@@ -534,10 +534,14 @@ void d2q9_batch_coef(const double omega[9], BatchItem &item);
 void d2q5_batch_coef(const double omega[9], BatchItem &item);
 void d3q27_batch_coef(const double omega[9], BatchItem &item);
 void d3q15_batch_coef(const double omega[9], BatchItem &item);
-cudaError_t d2q9_batch_step(const BatchLaunch &, int, cudaStream_t);
-cudaError_t d2q5_batch_step(const BatchLaunch &, int, cudaStream_t);
-cudaError_t d3q27_batch_step(const BatchLaunch &, int, cudaStream_t);
-cudaError_t d3q15_batch_step(const BatchLaunch &, int, cudaStream_t);
+cudaError_t d2q9_batch_step(const BatchLaunch &, int, int, cudaStream_t);
+cudaError_t d2q5_batch_step(const BatchLaunch &, int, int, cudaStream_t);
+cudaError_t d3q27_batch_step(const BatchLaunch &, int, int, cudaStream_t);
+cudaError_t d3q15_batch_step(const BatchLaunch &, int, int, cudaStream_t);
+int d2q9_batch_resident(int);
+int d2q5_batch_resident(int);
+int d3q27_batch_resident(int);
+int d3q15_batch_resident(int);
 
 void batch_coef(int lattice, const double omega[9], BatchItem &item)
 {
@@ -547,15 +551,29 @@ void batch_coef(int lattice, const double omega[9], BatchItem &item)
     else d3q27_batch_coef(omega, item);
 }
 
-cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
-    if (lattice == LD2Q9::ID) return d2q9_batch_step(L, nblocks, s);
-    if (lattice == LD2Q5::ID) return d2q5_batch_step(L, nblocks, s);
-    if (lattice == LD3Q15::ID) return d3q15_batch_step(L, nblocks, s);
-    return d3q27_batch_step(L, nblocks, s);
+    if (lattice == LD2Q9::ID) return d2q9_batch_step(L, nblocks, tile, s);
+    if (lattice == LD2Q5::ID) return d2q5_batch_step(L, nblocks, tile, s);
+    if (lattice == LD3Q15::ID) return d3q15_batch_step(L, nblocks, tile, s);
+    return d3q27_batch_step(L, nblocks, tile, s);
 }
 
-int batch_blocks(const Geom &g) { return (g.N + kBlock - 1) / kBlock; }
+bool d3q27_high_rates_one(const double omega[9]);
+
+int batch_variant(int lattice, const double omega[9])
+{
+    return (lattice == LD3Q27::ID && d3q27_high_rates_one(omega)) ? 1 : 0;
+}
+
+int batch_resident(int lattice, int tile)
+{
+    if (lattice == LD2Q9::ID) return d2q9_batch_resident(tile);
+    if (lattice == LD2Q5::ID) return d2q5_batch_resident(tile);
+    if (lattice == LD3Q15::ID) return d3q15_batch_resident(tile);
+    return d3q27_batch_resident(tile);
+}
+
 
 cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out)
 {

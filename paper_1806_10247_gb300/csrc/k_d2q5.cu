@@ -10,6 +10,7 @@
 // the collision (the printed plus sign is a typesetting slip).
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
+#include "lbm_tiles.cuh"
 
 namespace lbmk {
 namespace {
@@ -162,16 +163,10 @@ void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
 
 // Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
 // coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5.
-__global__ void __launch_bounds__(kBlock)
-k_batch(const __grid_constant__ BatchLaunch L)
+// One node of a batched launch (member `it`, node i; B staged in shared memory).
+__device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
@@ -199,6 +194,13 @@ k_batch(const __grid_constant__ BatchLaunch L)
     for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
 }
 
+template <int TB, bool PERSIST>
+__global__ void __launch_bounds__(TB)
+k_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+}
+
 }  // namespace
 
 void d2q5_batch_coef(const double omega[9], BatchItem &item)
@@ -212,10 +214,14 @@ void d2q5_batch_coef(const double omega[9], BatchItem &item)
     for (int k = 0; k < 16; k++) item.coef[k] = v[k];
 }
 
-cudaError_t d2q5_batch_step(const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t d2q5_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
-    k_batch<<<nblocks, kBlock, 0, s>>>(L);
-    return cudaGetLastError();
+    LBM_TILED_LAUNCH(k_batch, L, nblocks, tile, s);
+}
+
+int d2q5_batch_resident(int tile)
+{
+    LBM_TILED_RESIDENT(k_batch, tile);
 }
 
 cudaError_t d2q5_step(const LaunchArgs &a)

@@ -5,6 +5,7 @@
 // post-collision half force (Eq. 31) and writes f^p(t) = f + K g (Eq. 32).
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
+#include "lbm_tiles.cuh"
 
 namespace lbmk {
 namespace {
@@ -90,16 +91,10 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
 
 // Batched form: one launch for every lattice of a batch; pairs hold
 // (a_pre, (a_pre + a_post)/12) per step and item.
-__global__ void __launch_bounds__(kBlock)
-k_batch(const __grid_constant__ BatchLaunch L)
+// One node of a batched launch (member `it`, node i; B staged in shared memory).
+__device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
@@ -122,6 +117,13 @@ k_batch(const __grid_constant__ BatchLaunch L)
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
 }
 
+template <int TB, bool PERSIST>
+__global__ void __launch_bounds__(TB)
+k_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+}
+
 }  // namespace
 
 void d2q9_batch_coef(const double omega[9], BatchItem &item)
@@ -131,10 +133,14 @@ void d2q9_batch_coef(const double omega[9], BatchItem &item)
     for (int k = 0; k < 6; k++) item.coef[k] = c[k];
 }
 
-cudaError_t d2q9_batch_step(const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t d2q9_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
-    k_batch<<<nblocks, kBlock, 0, s>>>(L);
-    return cudaGetLastError();
+    LBM_TILED_LAUNCH(k_batch, L, nblocks, tile, s);
+}
+
+int d2q9_batch_resident(int tile)
+{
+    LBM_TILED_RESIDENT(k_batch, tile);
 }
 
 cudaError_t d2q9_step(const LaunchArgs &a)

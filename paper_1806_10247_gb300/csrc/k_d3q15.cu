@@ -17,6 +17,7 @@
 #include "lbm_d3q15.cuh"
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
+#include "lbm_tiles.cuh"
 
 namespace lbmk {
 namespace {
@@ -140,16 +141,10 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
 }
 
 // Batched form; pairs hold (a_pre, a_post) per step and item.
-__global__ void __launch_bounds__(kBlock)
-k_batch(const __grid_constant__ BatchLaunch L)
+// One node of a batched launch (member `it`, node i; B staged in shared memory).
+__device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
@@ -173,6 +168,13 @@ k_batch(const __grid_constant__ BatchLaunch L)
     for (int a = 0; a < 15; a++) fout[a * g.Np + i] = f[a];
 }
 
+template <int TB, bool PERSIST>
+__global__ void __launch_bounds__(TB)
+k_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+}
+
 }  // namespace
 
 void d3q15_batch_coef(const double omega[9], BatchItem &item)
@@ -183,10 +185,14 @@ void d3q15_batch_coef(const double omega[9], BatchItem &item)
     item.coef[3] = omega[4];
 }
 
-cudaError_t d3q15_batch_step(const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t d3q15_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
-    k_batch<<<nblocks, kBlock, 0, s>>>(L);
-    return cudaGetLastError();
+    LBM_TILED_LAUNCH(k_batch, L, nblocks, tile, s);
+}
+
+int d3q15_batch_resident(int tile)
+{
+    LBM_TILED_RESIDENT(k_batch, tile);
 }
 
 cudaError_t d3q15_step(const LaunchArgs &a)

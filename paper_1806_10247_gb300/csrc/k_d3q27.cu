@@ -19,6 +19,7 @@
 // alpha = (ex+1) + 3 (ey+1) + 9 (ez+1) position by position.
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
+#include "lbm_tiles.cuh"
 
 namespace lbmk {
 namespace {
@@ -74,6 +75,33 @@ __device__ __forceinline__ void along(double (&m)[27], Op op)
     }
 }
 
+// Central moments about u (post-collision) -> populations: back-shift, the
+// post-collision force in moment space, inverse raw transform.
+__device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, double uz, const double (&F)[3],
+                                       const double (&Fq)[3])
+{
+    along<0>(m, [ux](double &a, double &b, double &c) { shift_bwd(a, b, c, ux); });
+    along<1>(m, [uy](double &a, double &b, double &c) { shift_bwd(a, b, c, uy); });
+    along<2>(m, [uz](double &a, double &b, double &c) { shift_bwd(a, b, c, uz); });
+
+    // Undo the pre-collision moment shift and add K_1 g_1 in moment space:
+    // e_x changes m_100 by 18 g, m_120 and m_102 by 12 g, m_122 by 8 g.
+    {
+        const double hx = 0.5 * (F[0] + Fq[0]), hy = 0.5 * (F[1] + Fq[1]), hz = 0.5 * (F[2] + Fq[2]);
+        m[1] = fma(0.5, Fq[0], m[1]);
+        m[3] = fma(0.5, Fq[1], m[3]);
+        m[9] = fma(0.5, Fq[2], m[9]);
+        const double ax = hx * (2.0 / 3.0), ay = hy * (2.0 / 3.0), az = hz * (2.0 / 3.0);
+        m[7] += ax; m[19] += ax; m[25] = fma(hx, 4.0 / 9.0, m[25]);
+        m[5] += ay; m[21] += ay; m[23] = fma(hy, 4.0 / 9.0, m[23]);
+        m[11] += az; m[15] += az; m[17] = fma(hz, 4.0 / 9.0, m[17]);
+    }
+
+    along<2>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
+    along<1>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
+    along<0>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
+}
+
 // F: pre-collision force a_pre P; Fq: post-collision force a_post P.
 __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
                                         const Rates27 &w)
@@ -122,29 +150,72 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
         m[26] = fma(w.w6, rho * (1.0 / 27.0) - m[26], m[26]);
     }
 
-    along<0>(m, [ux](double &a, double &b, double &c) { shift_bwd(a, b, c, ux); });
-    along<1>(m, [uy](double &a, double &b, double &c) { shift_bwd(a, b, c, uy); });
-    along<2>(m, [uz](double &a, double &b, double &c) { shift_bwd(a, b, c, uz); });
-
-    // Undo the pre-collision moment shift and add K_1 g_1 in moment space:
-    // e_x changes m_100 by 18 g, m_120 and m_102 by 12 g, m_122 by 8 g.
-    {
-        const double hx = 0.5 * (F[0] + Fq[0]), hy = 0.5 * (F[1] + Fq[1]), hz = 0.5 * (F[2] + Fq[2]);
-        m[1] = fma(0.5, Fq[0], m[1]);
-        m[3] = fma(0.5, Fq[1], m[3]);
-        m[9] = fma(0.5, Fq[2], m[9]);
-        const double ax = hx * (2.0 / 3.0), ay = hy * (2.0 / 3.0), az = hz * (2.0 / 3.0);
-        m[7] += ax; m[19] += ax; m[25] = fma(hx, 4.0 / 9.0, m[25]);
-        m[5] += ay; m[21] += ay; m[23] = fma(hy, 4.0 / 9.0, m[23]);
-        m[11] += az; m[15] += az; m[17] = fma(hz, 4.0 / 9.0, m[17]);
-    }
-
-    along<2>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
-    along<1>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
-    along<0>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
+    finish(m, ux, uy, uz, F, Fq);
 }
 
-template <int FK>
+// The same collision when omega_3 = omega_4 = omega_5 = omega_6 = 1 (the
+// paper's choice for the higher moments, Sec. 6): every central moment of
+// order 3..6 lands exactly on its Maxwellian value, so only the raw moments of
+// order <= 2 are formed (partial transforms) and the forward shift reduces to
+// the six second-order central moments.
+__device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
+                                           const Rates27 &w)
+{
+    along<0>(m, [](double &a, double &b, double &c) { raw_fwd(a, b, c); });
+    // Line (b, c) along x holds M0, M1, M2 at m[3b + 9c + 0..2]; e_y = b - 1, e_z = c - 1.
+    double Y0[3], Y1[3], Y2[3], X0[3], X1[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const double s = m[9 * c + 6] + m[9 * c], d = m[9 * c + 6] - m[9 * c];
+        Y0[c] = s + m[9 * c + 3];
+        Y1[c] = d;
+        Y2[c] = s;
+        X0[c] = (m[9 * c + 7] + m[9 * c + 1]) + m[9 * c + 4];
+        X1[c] = m[9 * c + 7] - m[9 * c + 1];
+    }
+    const double rho = (Y0[2] + Y0[0]) + Y0[1];
+    double jz = Y0[2] - Y0[0];
+    const double kzz = Y0[2] + Y0[0];
+    double jy = (Y1[2] + Y1[0]) + Y1[1];
+    const double kyz = Y1[2] - Y1[0];
+    const double kyy = (Y2[2] + Y2[0]) + Y2[1];
+    double jx = (X0[2] + X0[0]) + X0[1];
+    const double kxz = X0[2] - X0[0];
+    const double kxy = (X1[2] + X1[0]) + X1[1];
+    const double kxx = ((m[2] + m[5]) + (m[8] + m[11])) + ((m[14] + m[17]) + (m[20] + m[23])) + m[26];
+
+    jx = fma(0.5, F[0], jx);
+    jy = fma(0.5, F[1], jy);
+    jz = fma(0.5, F[2], jz);
+    const double rinv = __drcp_rn(rho);
+    const double ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+
+    // Second-order central moments (the first ones vanish) and their relaxation.
+    const double cxx = fma(-jx, ux, kxx), cyy = fma(-jy, uy, kyy), czz = fma(-jz, uz, kzz);
+    const double T = cxx + cyy + czz;
+    const double D1 = cxx - cyy, D2 = cxx - czz;
+    const double Ts = fma(w.wb, rho - T, T);
+    const double rs = 1.0 - w.ws;
+    const double D1s = rs * D1, D2s = rs * D2;
+    const double sxx = (Ts + D1s + D2s) * (1.0 / 3.0);
+#pragma unroll
+    for (int k = 0; k < 27; k++) m[k] = 0.0;
+    m[0] = rho;
+    m[2] = sxx;
+    m[6] = sxx - D1s;
+    m[18] = sxx - D2s;
+    m[4] = rs * fma(-jx, uy, kxy);
+    m[10] = rs * fma(-jx, uz, kxz);
+    m[12] = rs * fma(-jy, uz, kyz);
+    const double e4 = rho * (1.0 / 9.0);
+    m[8] = e4;
+    m[20] = e4;
+    m[24] = e4;
+    m[26] = rho * (1.0 / 27.0);
+    finish(m, ux, uy, uz, F, Fq);
+}
+
+template <int FK, bool W1>
 __global__ void __launch_bounds__(kBlock)
 k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev Fd, double apre,
        double apost, Rates27 w)
@@ -164,22 +235,17 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
             Fq[d] = apost * P;
         }
     }
-    collide(m, F, Fq, w);
+    if (W1) collide_w1(m, F, Fq, w);
+    else collide(m, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
 }
 
 // Batched form; pairs hold (a_pre, a_post) per step and item.
-__global__ void __launch_bounds__(kBlock)
-k_batch(const __grid_constant__ BatchLaunch L)
+// One node of a batched launch (member `it`, node i; B staged in shared memory).
+__device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const int it = batch_find(L.first, L.count);
-    __shared__ BatchItem B;
-    stage_to_shared(B, L.items[it]);
-    __syncthreads();
-    const Geom g = B.g;
-    const int i = (blockIdx.x - __ldg(L.first + it)) * kBlock + threadIdx.x;
-    if (i >= g.N) return;
+    const Geom &g = B.g;
     const int p = B.parity + L.parity;
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
@@ -198,32 +264,58 @@ k_batch(const __grid_constant__ BatchLaunch L)
         }
     }
     const Rates27 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
-    collide(m, F, Fq, w);
+    if (B.variant == 1) collide_w1(m, F, Fq, w);  // uniform over the block's tile
+    else collide(m, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
 }
 
+template <int TB, bool PERSIST>
+__global__ void __launch_bounds__(TB) k_batch(const __grid_constant__ BatchLaunch L)
+{
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+}
+
+bool high_rates_one(const double *om) { return om[3] == 1.0 && om[4] == 1.0 && om[5] == 1.0 && om[6] == 1.0; }
+
 }  // namespace
 
+// coef[0..5] = omega[1..6]
 void d3q27_batch_coef(const double omega[9], BatchItem &item)
 {
     for (int k = 0; k < 6; k++) item.coef[k] = omega[k + 1];
 }
 
-cudaError_t d3q27_batch_step(const BatchLaunch &L, int nblocks, cudaStream_t s)
+cudaError_t d3q27_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)
 {
-    k_batch<<<nblocks, kBlock, 0, s>>>(L);
-    return cudaGetLastError();
+    LBM_TILED_LAUNCH(k_batch, L, nblocks, tile, s);
 }
+
+int d3q27_batch_resident(int tile)
+{
+    LBM_TILED_RESIDENT(k_batch, tile);
+}
+
+bool d3q27_high_rates_one(const double omega[9]) { return high_rates_one(omega); }
 
 cudaError_t d3q27_step(const LaunchArgs &a)
 {
     Rates27 w{a.omega[1], a.omega[2], a.omega[3], a.omega[4], a.omega[5], a.omega[6]};
     const int grid = (a.g.N + kBlock - 1) / kBlock;
+    const bool w1 = high_rates_one(a.omega);
     switch (a.fkind) {
-    case FK_NONE: k_step<FK_NONE><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
-    case FK_CONST: k_step<FK_CONST><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
-    default: k_step<FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
+    case FK_NONE:
+        if (w1) k_step<FK_NONE, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_NONE, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        break;
+    case FK_CONST:
+        if (w1) k_step<FK_CONST, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_CONST, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        break;
+    default:
+        if (w1) k_step<FK_GENERAL, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_GENERAL, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        break;
     }
     return cudaGetLastError();
 }

@@ -8,6 +8,7 @@
 // rearranged around the rest state.
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
+#include "lbm_tiles.cuh"
 
 namespace lbmk {
 namespace {
@@ -242,6 +243,52 @@ __device__ __forceinline__ void along(float (&m)[27], Op op)
     }
 }
 
+// Central moments of the deviations about u (post-collision) -> deviations:
+// back-shift, post-collision force in moment space, inverse raw transform.
+__device__ __forceinline__ void finish27(float (&m)[27], float ux, float uy, float uz, const float (&F)[3],
+                                         const float (&Fq)[3])
+{
+    along<0>(m, [ux](float &a, float &b, float &c) { shift_bwd(a, b, c, ux); });
+    along<1>(m, [uy](float &a, float &b, float &c) { shift_bwd(a, b, c, uy); });
+    along<2>(m, [uz](float &a, float &b, float &c) { shift_bwd(a, b, c, uz); });
+
+    {
+        const float hx = 0.5f * (F[0] + Fq[0]), hy = 0.5f * (F[1] + Fq[1]), hz = 0.5f * (F[2] + Fq[2]);
+        m[1] = fmaf(0.5f, Fq[0], m[1]);
+        m[3] = fmaf(0.5f, Fq[1], m[3]);
+        m[9] = fmaf(0.5f, Fq[2], m[9]);
+        const float ax = hx * (2.0f / 3.0f), ay = hy * (2.0f / 3.0f), az = hz * (2.0f / 3.0f);
+        m[7] += ax; m[19] += ax; m[25] = fmaf(hx, 4.0f / 9.0f, m[25]);
+        m[5] += ay; m[21] += ay; m[23] = fmaf(hy, 4.0f / 9.0f, m[23]);
+        m[11] += az; m[15] += az; m[17] = fmaf(hz, 4.0f / 9.0f, m[17]);
+    }
+
+    along<2>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    along<1>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    along<0>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+}
+
+// Deviation target of the central moment k = a + 3b + 9c of order n >= 3: its
+// Maxwellian value minus the rest state's central moment about u.
+__device__ __forceinline__ float high_target(int k, float drho, float rref, float ux, float uy, float uz)
+{
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const int a = k % 3, b = (k / 3) % 3, c = k / 9;
+    const int n = a + b + c;
+    const float hx[3] = {1.0f, -ux, (1.0f / 3.0f) + ux2};
+    const float hy[3] = {1.0f, -uy, (1.0f / 3.0f) + uy2};
+    const float hz[3] = {1.0f, -uz, (1.0f / 3.0f) + uz2};
+    if (a == 1 || b == 1 || c == 1) return -rref * (hx[a] * hy[b] * hz[c]);  // equilibrium 0
+    if (n == 4) {
+        const float p = (a == 2 ? ux2 : 0.f) + (b == 2 ? uy2 : 0.f) + (c == 2 ? uz2 : 0.f);
+        const float q = (a == 2 ? ux2 : 1.f) * (b == 2 ? uy2 : 1.f) * (c == 2 ? uz2 : 1.f);
+        return drho * (1.0f / 9.0f) - rref * (p * (1.0f / 3.0f) + q);
+    }
+    return drho * (1.0f / 27.0f) -
+           rref * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f) +
+                   ux2 * uy2 * uz2);
+}
+
 // Deviation form of the generic central-moment collision: m holds the raw
 // moments of the deviations (index a + 3b + 9c); the rest state's central
 // moments about u, rref * prod(1, -u, 1/3 + u^2), are folded in analytically.
@@ -281,55 +328,90 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
         m[10] = rs * m[10] - w.ws * rref * (ux * uz);
         m[12] = rs * m[12] - w.ws * rref * (uy * uz);
         // orders 3..6 towards the Maxwellian central moments
-        const float hx[3] = {1.0f, -ux, (1.0f / 3.0f) + ux2};
-        const float hy[3] = {1.0f, -uy, (1.0f / 3.0f) + uy2};
-        const float hz[3] = {1.0f, -uz, (1.0f / 3.0f) + uz2};
 #pragma unroll
         for (int k = 0; k < 27; k++) {
-            const int a = k % 3, b = (k / 3) % 3, c = k / 9;
-            const int n = a + b + c;
+            const int n = k % 3 + (k / 3) % 3 + k / 9;
             if (n < 3) continue;
-            float dv;
-            if (a == 1 || b == 1 || c == 1) {
-                dv = -rref * (hx[a] * hy[b] * hz[c]);  // equilibrium 0 minus the rest state's moment
-            } else if (n == 4) {
-                const float p = (a == 2 ? ux2 : 0.f) + (b == 2 ? uy2 : 0.f) + (c == 2 ? uz2 : 0.f);
-                const float q = (a == 2 ? ux2 : 1.f) * (b == 2 ? uy2 : 1.f) * (c == 2 ? uz2 : 1.f);
-                dv = drho * (1.0f / 9.0f) - rref * (p * (1.0f / 3.0f) + q);
-            } else {  // n == 6
-                dv = drho * (1.0f / 27.0f)
-                     - rref * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f)
-                               + ux2 * uy2 * uz2);
-            }
             const float om = n == 3 ? w.w3 : (n == 4 ? w.w4 : (n == 5 ? w.w5 : w.w6));
-            m[k] = fmaf(om, dv - m[k], m[k]);
+            m[k] = fmaf(om, high_target(k, drho, rref, ux, uy, uz) - m[k], m[k]);
         }
     }
 
-    along<0>(m, [ux](float &a, float &b, float &c) { shift_bwd(a, b, c, ux); });
-    along<1>(m, [uy](float &a, float &b, float &c) { shift_bwd(a, b, c, uy); });
-    along<2>(m, [uz](float &a, float &b, float &c) { shift_bwd(a, b, c, uz); });
+    finish27(m, ux, uy, uz, F, Fq);
+}
 
-    {
-        const float hx = 0.5f * (F[0] + Fq[0]), hy = 0.5f * (F[1] + Fq[1]), hz = 0.5f * (F[2] + Fq[2]);
-        m[1] = fmaf(0.5f, Fq[0], m[1]);
-        m[3] = fmaf(0.5f, Fq[1], m[3]);
-        m[9] = fmaf(0.5f, Fq[2], m[9]);
-        const float ax = hx * (2.0f / 3.0f), ay = hy * (2.0f / 3.0f), az = hz * (2.0f / 3.0f);
-        m[7] += ax; m[19] += ax; m[25] = fmaf(hx, 4.0f / 9.0f, m[25]);
-        m[5] += ay; m[21] += ay; m[23] = fmaf(hy, 4.0f / 9.0f, m[23]);
-        m[11] += az; m[15] += az; m[17] = fmaf(hz, 4.0f / 9.0f, m[17]);
+// The same collision when omega_3 = omega_4 = omega_5 = omega_6 = 1: the
+// central moments of orders 3..6 land on their targets, so only the raw
+// moments of order <= 2 are formed and the forward shift reduces to the
+// first- and second-order central moments.
+__device__ __forceinline__ void collide27_w1(float (&m)[27], float rref, const float (&F)[3], const float (&Fq)[3],
+                                             const Rates27f &w)
+{
+    along<0>(m, [](float &a, float &b, float &c) { raw_fwd(a, b, c); });
+    // Line (b, c) along x holds M0, M1, M2 at m[3b + 9c + 0..2]; e_y = b - 1, e_z = c - 1.
+    float Y0[3], Y1[3], Y2[3], X0[3], X1[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float s = m[9 * c + 6] + m[9 * c], d = m[9 * c + 6] - m[9 * c];
+        Y0[c] = s + m[9 * c + 3];
+        Y1[c] = d;
+        Y2[c] = s;
+        X0[c] = (m[9 * c + 7] + m[9 * c + 1]) + m[9 * c + 4];
+        X1[c] = m[9 * c + 7] - m[9 * c + 1];
     }
+    const float drho = (Y0[2] + Y0[0]) + Y0[1];
+    const float jz = fmaf(0.5f, F[2], Y0[2] - Y0[0]);
+    const float kzz = Y0[2] + Y0[0];
+    const float jy = fmaf(0.5f, F[1], (Y1[2] + Y1[0]) + Y1[1]);
+    const float kyz = Y1[2] - Y1[0];
+    const float kyy = (Y2[2] + Y2[0]) + Y2[1];
+    const float jx = fmaf(0.5f, F[0], (X0[2] + X0[0]) + X0[1]);
+    const float kxz = X0[2] - X0[0];
+    const float kxy = (X1[2] + X1[0]) + X1[1];
+    const float kxx = ((m[2] + m[5]) + (m[8] + m[11])) + ((m[14] + m[17]) + (m[20] + m[23])) + m[26];
 
-    along<2>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
-    along<1>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
-    along<0>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    const float rho = rref + drho;
+    const float rinv = __frcp_rn(rho);
+    const float ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+
+    // first-order central moments of the deviations (k1 = m1 - u m0)
+    const float k100 = fmaf(-ux, drho, jx), k010 = fmaf(-uy, drho, jy), k001 = fmaf(-uz, drho, jz);
+    // second-order central moments (k2 = m2 - u (m1 + k1); mixed: k_ab = m_ab - u_a m_b - u_b k_a)
+    const float cxx = fmaf(-ux, jx + k100, kxx), cyy = fmaf(-uy, jy + k010, kyy), czz = fmaf(-uz, jz + k001, kzz);
+    const float cxy = fmaf(-uy, k100, fmaf(-ux, jy, kxy));
+    const float cxz = fmaf(-uz, k100, fmaf(-ux, jz, kxz));
+    const float cyz = fmaf(-uz, k010, fmaf(-uy, jz, kyz));
+
+    const float Tn = cxx + cyy + czz;
+    const float Ts = fmaf(w.wb, drho - rref * (ux2 + uy2 + uz2) - Tn, Tn);
+    const float D1 = cxx - cyy, D2 = cxx - czz;
+    const float rs = 1.0f - w.ws;
+    const float D1s = rs * D1 - w.ws * rref * (ux2 - uy2);
+    const float D2s = rs * D2 - w.ws * rref * (ux2 - uz2);
+    const float sxx = (Ts + D1s + D2s) * (1.0f / 3.0f);
+#pragma unroll
+    for (int k = 0; k < 27; k++) {
+        const int n = k % 3 + (k / 3) % 3 + k / 9;
+        if (n >= 3) m[k] = high_target(k, drho, rref, ux, uy, uz);
+    }
+    m[0] = drho;
+    m[1] = k100;
+    m[3] = k010;
+    m[9] = k001;
+    m[2] = sxx;
+    m[6] = sxx - D1s;
+    m[18] = sxx - D2s;
+    m[4] = rs * cxy - w.ws * rref * (ux * uy);
+    m[10] = rs * cxz - w.ws * rref * (ux * uz);
+    m[12] = rs * cyz - w.ws * rref * (uy * uz);
+    finish27(m, ux, uy, uz, F, Fq);
 }
 
 // 4 resident blocks per SM (<= 64 registers): the reduced-precision D3Q27
 // step is memory-bound, so occupancy to cover load latency matters more than
 // registers.
-template <class T, int FK>
+template <class T, int FK, bool W1>
 __global__ void __launch_bounds__(kBlock, 4)
 k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, float apre, float apost,
          Rates27f w, float rref)
@@ -349,32 +431,14 @@ k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, f
             Fq[d] = apost * P;
         }
     }
-    collide27(m, rref, F, Fq, w);
+    if (W1) collide27_w1(m, rref, F, Fq, w);
+    else collide27(m, rref, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
 }
 
 // --------------------------------------------------------------- batched ---
-//
-// A batched launch covers the tiles of every member lattice (TB nodes per
-// tile, TB threads per block, tiles numbered member after member).  Either
-// each block takes one tile, or (persistent grid) each block takes a
-// contiguous run of tiles, so that consecutive tiles mostly belong to the same
-// member and its descriptor is staged into shared memory once per run.
-
-// Member owning tile `tile`: `cur` if it still does (tiles ascend within a
-// block), else a binary search for the last i with first[i] <= tile.
-__device__ __forceinline__ int tile_item(const int *__restrict__ first, int count, int tile, int cur)
-{
-    if (cur >= 0 && (cur + 1 == count || tile < __ldg(first + cur + 1))) return cur;
-    int lo = cur < 0 ? 0 : cur, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(first + mid) <= tile) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
+// (tile loop: lbm_tiles.cuh)
 
 template <class T>
 __device__ __forceinline__ void node9(const BatchItem &B, const BatchLaunch &L, int it, int i)
@@ -459,53 +523,31 @@ __device__ __forceinline__ void node27(const BatchItem &B, const BatchLaunch &L,
         }
     }
     const Rates27f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
-    collide27(m, B.frho_ref, F, Fq, w);
+    if (B.variant == 1) collide27_w1(m, B.frho_ref, F, Fq, w);  // uniform over the block's tile
+    else collide27(m, B.frho_ref, F, Fq, w);
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
 }
 
-// Tile loop shared by the three lattices; NODE is node9 / node5 / node27.
-template <int TB, class Node>
-__device__ __forceinline__ void batch_tiles(const BatchLaunch &L, Node node)
-{
-    __shared__ BatchItem B;
-    int t0 = blockIdx.x, t1 = blockIdx.x + 1;
-    if (L.chunk > 0) {
-        t0 = blockIdx.x * L.chunk;
-        t1 = min(t0 + L.chunk, L.ntiles);
-    }
-    int cur = -1;
-    for (int tile = t0; tile < t1; tile++) {
-        const int it = tile_item(L.first, L.count, tile, cur);
-        if (it != cur) {  // block-uniform
-            if (cur >= 0) __syncthreads();
-            stage_to_shared(B, L.items[it]);
-            __syncthreads();
-            cur = it;
-        }
-        const int i = (tile - __ldg(L.first + it)) * TB + (int)threadIdx.x;
-        if (i < B.g.N) node(B, L, it, i);
-    }
-}
-
-template <class T, int TB>
+template <class T, int TB, bool PERSIST>
 __global__ void __launch_bounds__(TB) k_batch9(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node9<T>(B, L2, it, i); });
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node9<T>(B, L2, it, i); });
 }
 
-template <class T, int TB>
+template <class T, int TB, bool PERSIST>
 __global__ void __launch_bounds__(TB) k_batch5(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node5<T>(B, L2, it, i); });
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node5<T>(B, L2, it, i); });
 }
 
 // 1024 / TB blocks per SM keep the D3Q27 kernel at <= 64 registers.
-template <class T, int TB>
+template <class T, int TB, bool PERSIST>
 __global__ void __launch_bounds__(TB, 1024 / TB) k_batch27(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node27<T>(B, L2, it, i); });
+    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node27<T>(B, L2, it, i); });
 }
+
 
 template <class T>
 cudaError_t step_t(int lattice, const LaunchArgs &a)
@@ -542,20 +584,35 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
     } else {
         const Rates27f w{(float)a.omega[1], (float)a.omega[2], (float)a.omega[3],
                          (float)a.omega[4], (float)a.omega[5], (float)a.omega[6]};
-        if (a.fkind == FK_NONE) k_step27<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
-        else if (a.fkind == FK_CONST) k_step27<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
-        else k_step27<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, (float)a.apre, (float)a.apost, w, rref);
+        const bool w1 = a.omega[3] == 1.0 && a.omega[4] == 1.0 && a.omega[5] == 1.0 && a.omega[6] == 1.0;
+        const float ap = (float)a.apre, aq = (float)a.apost;
+        if (a.fkind == FK_NONE) {
+            if (w1) k_step27<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+        } else if (a.fkind == FK_CONST) {
+            if (w1) k_step27<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+        } else {
+            if (w1) k_step27<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+        }
     }
+    return cudaGetLastError();
+}
+
+template <class T, int TB, bool P>
+cudaError_t batch_tbp(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
+{
+    if (lattice == LD2Q9::ID) k_batch9<T, TB, P><<<nblocks, TB, 0, s>>>(L);
+    else if (lattice == LD2Q5::ID) k_batch5<T, TB, P><<<nblocks, TB, 0, s>>>(L);
+    else k_batch27<T, TB, P><<<nblocks, TB, 0, s>>>(L);
     return cudaGetLastError();
 }
 
 template <class T, int TB>
 cudaError_t batch_tb(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    if (lattice == LD2Q9::ID) k_batch9<T, TB><<<nblocks, TB, 0, s>>>(L);
-    else if (lattice == LD2Q5::ID) k_batch5<T, TB><<<nblocks, TB, 0, s>>>(L);
-    else k_batch27<T, TB><<<nblocks, TB, 0, s>>>(L);
-    return cudaGetLastError();
+    return L.chunk > 0 ? batch_tbp<T, TB, true>(lattice, L, nblocks, s) : batch_tbp<T, TB, false>(lattice, L, nblocks, s);
 }
 
 template <class T>
@@ -572,19 +629,9 @@ cudaError_t batch_t(int lattice, const BatchLaunch &L, int nblocks, int tile, cu
 template <class T, int TB>
 int resident_tb(int lattice)
 {
-    int per_sm = 0;
-    cudaError_t e;
-    if (lattice == LD2Q9::ID) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch9<T, TB>, TB, 0);
-    else if (lattice == LD2Q5::ID) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch5<T, TB>, TB, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch27<T, TB>, TB, 0);
-    int dev = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return per_sm * sms;
+    if (lattice == LD2Q9::ID) return resident_blocks(k_batch9<T, TB, true>, TB);
+    if (lattice == LD2Q5::ID) return resident_blocks(k_batch5<T, TB, true>, TB);
+    return resident_blocks(k_batch27<T, TB, true>, TB);
 }
 
 template <class T>

@@ -14,7 +14,7 @@
 // each tile its own block or runs a persistent grid (as many blocks as are
 // resident on the GPU at once) whose blocks take contiguous runs of tiles.
 // lbm_batch_autotune times every combination on the batch itself and keeps the
-// fastest.  FP64 batches always use 256-node tiles, one block per tile.
+// fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -244,6 +244,7 @@ int refresh_descriptors(lbm_batch *b, int *parity)
         for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
         it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
         it.frho_ref = (float)it.rho_ref;
+        it.variant = batch_variant(c->lattice, c->omega);
         b->item_version[i] = c->version;
         b->item_buf0[i] = c->A;
     }
@@ -257,29 +258,31 @@ int refresh_descriptors(lbm_batch *b, int *parity)
 
 bool reduced_precision(const lbm_batch *b) { return b->ctx[0]->storage != LBM_FP64; }
 
-// One batched launch with the batch's tiling: fills in the tile map of L.
+int resident_for(lbm_batch *b, int tile_idx)
+{
+    if (b->resident[tile_idx] == 0)
+        b->resident[tile_idx] = reduced_precision(b)
+                                    ? rp_batch_resident(b->lattice, b->ctx[0]->storage, kTiles[tile_idx])
+                                    : batch_resident(b->lattice, kTiles[tile_idx]);
+    return b->resident[tile_idx];
+}
+
+// One batched launch with the given tiling: fills in the tile map of L.
 cudaError_t launch_tiled(lbm_batch *b, BatchLaunch L, int tile_idx, bool persistent, cudaStream_t s)
 {
-    if (!reduced_precision(b)) {
-        L.first = b->d_first[1];
-        L.ntiles = (int)b->ntiles[1];
-        L.chunk = 0;
-        return batch_step(b->lattice, L, (int)b->ntiles[1], s);
-    }
     const int nt = (int)b->ntiles[tile_idx];
     int grid = nt;
     L.first = b->d_first[tile_idx];
     L.ntiles = nt;
     L.chunk = 0;
     if (persistent) {
-        if (b->resident[tile_idx] == 0)
-            b->resident[tile_idx] = rp_batch_resident(b->lattice, b->ctx[0]->storage, kTiles[tile_idx]);
-        const int r = b->resident[tile_idx];
+        const int r = resident_for(b, tile_idx);
         if (r > 0 && r < nt) {
             L.chunk = (nt + r - 1) / r;
             grid = (nt + L.chunk - 1) / L.chunk;
         }
     }
+    if (!reduced_precision(b)) return batch_step(b->lattice, L, grid, kTiles[tile_idx], s);
     return rp_batch_step(b->lattice, b->ctx[0]->storage, L, grid, kTiles[tile_idx], s);
 }
 
@@ -495,8 +498,6 @@ int lbm_batch_set_tiling(lbm_batch *b, int tile, int persistent)
         if (kTiles[k] == tile) j = k;
     if (j < 0 || (persistent != 0 && persistent != 1))
         return bfail(b, LBM_EINVAL, "lbm_batch_set_tiling: tile must be 128, 256 or 512 and persistent 0 or 1");
-    if (!reduced_precision(b) && (tile != 256 || persistent))
-        return bfail(b, LBM_EINVAL, "lbm_batch_set_tiling: FP64 batches use 256-node tiles, one block per tile");
     if (j != b->tile_idx || (persistent != 0) != b->persistent) {
         drop_graph(b);
         b->tile_idx = j;
@@ -514,9 +515,7 @@ int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid)
     if (grid) {
         long long g = b->ntiles[b->tile_idx];
         if (b->persistent) {
-            if (b->resident[b->tile_idx] == 0)
-                b->resident[b->tile_idx] = rp_batch_resident(b->lattice, b->ctx[0]->storage, kTiles[b->tile_idx]);
-            const long long r = b->resident[b->tile_idx];
+            const long long r = resident_for(b, b->tile_idx);
             if (r > 0 && r < g) {
                 const long long chunk = (g + r - 1) / r;
                 g = (g + chunk - 1) / chunk;
@@ -557,7 +556,6 @@ int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *a
     bool best_p = b->persistent;
     for (int j = 0; j < 3 && e == cudaSuccess; j++)
         for (int p = 0; p < 2 && e == cudaSuccess; p++) {
-            if (!reduced_precision(b) && (j != 1 || p)) continue;
             e = launch_tiled(b, L, j, p != 0, b->stream);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
             for (int r = 0; r < trial_steps && e == cudaSuccess; r++) e = launch_tiled(b, L, j, p != 0, b->stream);
@@ -582,6 +580,53 @@ int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *a
         b->persistent = best_p;
     }
     if (best_us) *best_us = 1000.0 * best / trial_steps;
+    return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int where, int half_forced)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    if (!rho) return bfail(b, LBM_EINVAL, "lbm_batch_moments: rho is NULL");
+    if (where != 0 && where != 1) return bfail(b, LBM_EINVAL, "lbm_batch_moments: where must be 0 or 1");
+    const bool scalar = b->lattice == LBM_D2Q5_CDE;
+    for (int i = 0; i < b->count; i++) {
+        if (!b->ctx[i]->initialised)
+            return bfail(b, LBM_ESTATE, "lbm_batch_moments: context %d not initialised", i);
+        if (!rho[i] || (!scalar && (!u || !u[i])))
+            return bfail(b, LBM_EINVAL, "lbm_batch_moments: NULL output for context %d", i);
+    }
+    // Every member's fields are formed into its scratch buffer (the second
+    // population buffer, or the staging buffer of a reduced-precision context)
+    // and copied out on the shared stream; one synchronisation at the end.
+    for (int i = 0; i < b->count; i++) {
+        lbm_ctx *c = b->ctx[i];
+        double apre, apost;
+        lbmc::envelope_pair(c, c->t, apre, apost);
+        LaunchArgs a = lbmc::launch_args(c, c->A, nullptr, apre, apost);
+        const size_t N = (size_t)c->g.N;
+        double *drho = rho[i], *du = scalar ? nullptr : u[i];
+        if (where == 0) {
+            double *st = c->B;
+            if (c->storage != LBM_FP64) {
+                int rc = lbmc::ensure_stage(c);
+                if (rc != LBM_OK) return bfail(b, rc, "lbm_batch_moments: %s", c->err.c_str());
+                st = c->stage;
+            }
+            drho = st;
+            du = st + N;
+        }
+        BCK(moments(c->lattice, a, drho, du, half_forced ? 1 : 0), "lbm_batch_moments: moments kernel");
+        c->launches++;
+        if (where == 0) {
+            BCK(cudaMemcpyAsync(rho[i], drho, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+                "lbm_batch_moments: copy rho");
+            if (!scalar)
+                BCK(cudaMemcpyAsync(u[i], du, (size_t)c->dim * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+                    "lbm_batch_moments: copy u");
+        }
+    }
+    if (where == 0) BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments");
     return LBM_OK;
 }
 

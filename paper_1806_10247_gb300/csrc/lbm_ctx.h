@@ -58,6 +58,8 @@ int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what);
 // Envelope averages (a_pre, a_post) of step t (trapezoid rule of Sec. 6.3).
 void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost);
 bool envelope_covers(const lbm_ctx *c, long t, long n);
+// Reduced-precision contexts: allocate the FP64 host-I/O staging buffer on first use.
+int ensure_stage(lbm_ctx *c);
 // Launch arguments of the context's kernels.
 lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
 

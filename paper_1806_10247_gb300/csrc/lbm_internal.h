@@ -53,6 +53,7 @@ struct BatchItem {
     float fcoef[20];  // FP32 copies for the reduced-precision kernels (FP64 runs at 1/64 rate);
                       // D2Q5: [16] holds P3 + (2/3) S3 of the uniform-velocity form
     float frho_ref;
+    int variant;      // collision variant of this member (batch_variant)
 };
 
 // Host: fill item.coef from the relaxation rates (and, for the scalar lattice
@@ -82,13 +83,18 @@ struct BatchLaunch {
     float2 inlf[kInlinePairs];
 };
 
-// One launch advancing every item of a batch by one step.
-cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s);
+// One launch advancing every item of a batch by one step (FP64 storage);
+// tile = nodes per tile = threads per block: 128, 256 or 512.
+cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
+// Blocks of the FP64 batch kernel resident on the whole GPU at once.
+int batch_resident(int lattice, int tile);
+// Collision variant of a batch member (BatchItem::variant): D3Q27 1 when
+// omega_3..omega_6 = 1 (the same choice the single-lattice launch makes).
+int batch_variant(int lattice, const double omega[9]);
 // tile = nodes per tile = threads per block: 128, 256 or 512.
 cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
 // Blocks of the reduced-precision batch kernel resident on the whole GPU at once.
 int rp_batch_resident(int lattice, int storage, int tile);
-int batch_blocks(const Geom &g);
 
 // One fused stream + collide step (pull form): fin -> fout.
 cudaError_t d2q9_step(const LaunchArgs &a);

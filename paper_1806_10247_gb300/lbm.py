@@ -32,7 +32,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
-           "lbm_batch_autotune")
+           "lbm_batch_autotune", "lbm_batch_moments")
 
 
 class LBMError(RuntimeError):
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_set_tiling.argtypes = [vp, ip, ip]
     L.lbm_batch_get_tiling.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.lbm_batch_autotune.argtypes = [vp, ip, dp, dp]
+    L.lbm_batch_moments.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, ip]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
     L.lbm_batch_destroy.argtypes = [vp]
@@ -351,6 +352,30 @@ class Batch:
         v = ctypes.c_longlong()
         self._check(self._L.lbm_batch_graph_replays(self.h, ctypes.byref(v)))
         return v.value
+
+    def moments_into(self, rho_ptrs, u_ptrs=None, where=0, half_forced=True):
+        """Fields of every member into caller buffers given as raw addresses
+        (host when where = 0, e.g. pinned torch tensors' data_ptr(); device
+        when where = 1); one synchronisation for the whole batch."""
+        n = len(self.members)
+        r = (ctypes.c_void_p * n)(*[int(p) for p in rho_ptrs])
+        u = None if u_ptrs is None else (ctypes.c_void_p * n)(*[int(p) for p in u_ptrs])
+        self._check(self._L.lbm_batch_moments(self.h, r, u, int(where), int(bool(half_forced))))
+
+    def moments(self, half_forced=True):
+        """Fields of every member as numpy arrays: phi [N] (scalar lattice) or
+        (rho [N], u [dim][N]) per member."""
+        outs = []
+        for m in self.members:
+            if m.lattice == D2Q5_CDE:
+                outs.append(np.empty(m.N))
+            else:
+                outs.append((np.empty(m.N), np.empty((m.dim, m.N))))
+        if self.members[0].lattice == D2Q5_CDE:
+            self.moments_into([o.ctypes.data for o in outs], None, 0, half_forced)
+        else:
+            self.moments_into([o[0].ctypes.data for o in outs], [o[1].ctypes.data for o in outs], 0, half_forced)
+        return outs
 
     def set_tiling(self, tile, persistent=False):
         """Tile of 128/256/512 nodes per block; persistent grid or one block per tile."""

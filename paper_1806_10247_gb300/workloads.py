@@ -179,6 +179,85 @@ def duct(n: int = 128, nx: int = 3, F0: float = 1e-6, nu: float = 0.05, seed: in
         meta={"F0": F0, "nu": nu})
 
 
+def hartmann(ny: int = 33, nx: int = 3, Ha: float = 3.0, tau: float = 0.8, Fb: float = 1e-6) -> Workload:
+    """Hartmann flow (Sec. 6.2): channel with halfway bounce-back walls at
+    y = -1/2 and ny - 1/2 (half-width L = ny/2), driven by F_b and retarded by
+    the Lorentz force of a transverse field; the total force is
+    F_x(y) = F_b Ha cosh(Ha y'/L) / sinh(Ha), y' = y + 1/2 - L (a per-y table)."""
+    L = ny / 2.0
+    yc = np.arange(ny, dtype=np.float64) + 0.5 - L
+    py = Fb * Ha * np.cosh(Ha * yc / L) / math.sinh(Ha)
+    one = np.array([1.0])
+    return Workload(
+        name=f"hartmann_d2q9_{nx}x{ny}_Ha{Ha:g}", lattice=D2Q9, shape=(nx, ny, 1), wall=(0, 1, 0),
+        omega=d2q9_omega(tau), rho0=1.0, u0=(0.0, 0.0, 0.0),
+        tables=[(one, py, one), (np.array([0.0]), one, one)],
+        meta={"Ha": Ha, "Fb": Fb, "tau": tau, "nu": (tau - 0.5) / 3.0, "L": L})
+
+
+def hartmann_profile(w: Workload) -> np.ndarray:
+    """Analytic Hartmann velocity u_x(y) = F_b L^2 coth(Ha) / (Ha nu) [1 - cosh(Ha y'/L)/cosh(Ha)]
+    (Sec. 6.2 with eta = B0^2 L^2 / (Ha^2 nu))."""
+    m = w.meta
+    L, Ha, nu = m["L"], m["Ha"], m["nu"]
+    yc = np.arange(w.shape[1], dtype=np.float64) + 0.5 - L
+    return m["Fb"] * L * L / (Ha * nu) / math.tanh(Ha) * (1.0 - np.cosh(Ha * yc / L) / math.cosh(Ha))
+
+
+def womersley(ny: int = 32, nx: int = 3, tau: float = 1.0, period: int = 2000, Fm: float = 1e-5) -> Workload:
+    """Womersley flow (Sec. 6.3): channel with halfway bounce-back walls driven
+    by F_x = F_m cos(2 pi t / T) (a constant shape with a time envelope)."""
+    om = 2.0 * math.pi / period
+    one = np.array([1.0])
+    return Workload(
+        name=f"womersley_d2q9_{nx}x{ny}_T{period}", lattice=D2Q9, shape=(nx, ny, 1), wall=(0, 1, 0),
+        omega=d2q9_omega(tau), rho0=1.0, u0=(0.0, 0.0, 0.0),
+        tables=[(np.array([Fm]), one, one), (np.array([0.0]), one, one)],
+        envelope=lambda t, om=om: math.cos(om * t),
+        meta={"Fm": Fm, "period": period, "tau": tau, "nu": (tau - 0.5) / 3.0, "L": ny / 2.0,
+              "Wo": ny / 2.0 * math.sqrt(om / ((tau - 0.5) / 3.0))})
+
+
+def womersley_profile(w: Workload, t: float) -> np.ndarray:
+    """Periodic-state solution of u_t = nu u_yy + F_m cos(omega t), u(+-L) = 0:
+    u = Re{ F_m/(i omega) [1 - cosh(k y')/cosh(k L)] e^{i omega t} }, k = sqrt(i omega / nu)
+    (the solution Sec. 6.3 prints, written with k instead of gamma = i k L)."""
+    m = w.meta
+    om = 2.0 * math.pi / m["period"]
+    L = m["L"]
+    k = np.sqrt(1j * om / m["nu"])
+    yc = np.arange(w.shape[1], dtype=np.float64) + 0.5 - L
+    U = m["Fm"] / (1j * om) * (1.0 - np.cosh(k * yc) / np.cosh(k * L))
+    return np.real(U * np.exp(1j * om * t))
+
+
+def four_rolls(N: int = 48, u0: float = 0.01, nu96: float = 0.0011 * 96 / (2.0 * math.pi)) -> Workload:
+    """Four-rolls mill (Sec. 6.5): periodic N x N lattice covering [0, 2 pi)^2,
+    F_x = 2 nu k^2 u0 sin(kx) sin(ky), F_y = 2 nu k^2 u0 cos(kx) cos(ky),
+    k = 2 pi / N, whose steady solution is u = u0 (sin kx sin ky, cos kx cos ky).
+    Convective scaling: u0 fixed in lattice units, nu = nu96 N / 96 (nu = 0.0011 in
+    units where the domain is 2 pi wide), so tau_N = 1/2 + 3 nu."""
+    nu = nu96 * N / 96.0
+    tau = 0.5 + 3.0 * nu
+    k = 2.0 * math.pi / N
+    x = np.arange(N, dtype=np.float64)
+    A = 2.0 * nu * k * k * u0
+    one = np.array([1.0])
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    start = np.stack([(u0 * np.sin(k * X) * np.sin(k * Y)).reshape(-1), (u0 * np.cos(k * X) * np.cos(k * Y)).reshape(-1)])
+    return Workload(
+        name=f"four_rolls_d2q9_{N}x{N}", lattice=D2Q9, shape=(N, N, 1), wall=(0, 0, 0),
+        omega=d2q9_omega(tau), rho0=1.0, u0=start,
+        tables=[(A * np.sin(k * x), np.sin(k * x), one), (A * np.cos(k * x), np.cos(k * x), one)],
+        meta={"u0": u0, "nu": nu, "tau": tau, "k": k})
+
+
+def four_rolls_velocity(w: Workload) -> np.ndarray:
+    """Analytic steady velocity [2][N] of the four-rolls mill, node order x fastest
+    (also the workload's initial velocity)."""
+    return np.array(w.u0, copy=True)
+
+
 def batched_sweep(count: int = 2048, seed: int = SEED, nx_range=(32, 512), ny_range=(32, 256)):
     """Parameter sweep of many small, unevenly sized 2D lattices.
 

@@ -62,7 +62,38 @@ def test_create_fails_cleanly_without_gpu_or_on_bad_args():
     assert rc == lbm.EINVAL
     rc = L.lbm_create(ctypes.byref(h), lbm.D2Q9, 4, 4, 1, ctypes.byref(r), None, 7, None)
     assert rc == lbm.EINVAL and b"storage" in L.lbm_last_error(None)
+    # node count beyond the 32-bit index range of the kernels
+    rc = L.lbm_create(ctypes.byref(h), lbm.D3Q27, 2048, 1024, 1025, ctypes.byref(r), None, 0, None)
+    assert rc == lbm.EINVAL and b"2^31-1" in L.lbm_last_error(None)
+    # D3Q15 stores FP64 only; walls on z for a 2D lattice; unknown boundary kind
+    rc = L.lbm_create(ctypes.byref(h), lbm.D3Q15, 4, 4, 4, ctypes.byref(r), None, lbm.FP32_DEV, None)
+    assert rc == lbm.EINVAL and b"D3Q15" in L.lbm_last_error(None)
+    bc = lbm._Boundary()
+    bc.axis[2] = lbm.BOUNCE_BACK
+    rc = L.lbm_create(ctypes.byref(h), lbm.D2Q9, 4, 4, 1, ctypes.byref(r), ctypes.byref(bc), 0, None)
+    assert rc == lbm.EINVAL and b"walls on z" in L.lbm_last_error(None)
+    bc.axis[2] = 0
+    bc.axis[0] = 7
+    rc = L.lbm_create(ctypes.byref(h), lbm.D2Q9, 4, 4, 1, ctypes.byref(r), ctypes.byref(bc), 0, None)
+    assert rc == lbm.EINVAL and b"boundary kind" in L.lbm_last_error(None)
+    # D3Q15 validates its four rates (omega[1..4])
+    r.omega[3] = 0.0
+    rc = L.lbm_create(ctypes.byref(h), lbm.D3Q15, 4, 4, 4, ctypes.byref(r), None, 0, None)
+    assert rc == lbm.EINVAL and b"omega[3]" in L.lbm_last_error(None)
     assert h.value is None
+
+
+def test_batch_and_nn_entry_points_reject_null_handles():
+    """The batch and network entry points validate their handles and
+    arguments on the host."""
+    L = lbm.load()
+    h = ctypes.c_void_p()
+    assert L.lbm_batch_create(ctypes.byref(h), None, 0) == lbm.EINVAL
+    assert b"at least one context" in L.lbm_batch_last_error(None)
+    assert L.lbm_batch_step(None, 1) == lbm.EINVAL
+    assert L.lbm_batch_autotune(None, 1, None, None) == lbm.EINVAL
+    assert L.lbm_batch_set_tiling(None, 256, 0) == lbm.EINVAL
+    assert L.lbm_batch_moments(None, None, None, 0, 1) == lbm.EINVAL
 
 
 def test_oracle_and_product_share_no_code():

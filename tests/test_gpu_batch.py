@@ -252,19 +252,49 @@ def test_autotune_leaves_the_state_unchanged_and_picks_a_tiling():
         assert np.abs(a.get_populations() - b.get_populations()).max() <= 1e-6 * scale
 
 
-def test_fp64_batch_tiling_is_fixed():
+def test_fp64_batch_every_tiling_and_autotune():
+    """FP64 batches take every tiling too; all give the populations of the
+    default tiling to FP64 rounding, and the autotuner leaves the state alone."""
     ws, fulls = _members("d2q5")
-    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
-    B = lbm.Batch(Gs)
+    ref = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(ref)
+    B.step(4)
+    want = [G.get_populations() for G in ref]
+    for tile in (128, 256, 512):
+        for persistent in (False, True):
+            Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+            Bt = lbm.Batch(Gs)
+            Bt.set_tiling(tile, persistent)
+            Bt.step(4)
+            for a, G in zip(want, Gs):
+                assert np.abs(G.get_populations() - a).max() <= 4 * 4 * 2.0 ** -53
+    n0 = B.launch_count()
+    before = [G.get_populations() for G in ref]
+    us, tried = B.autotune(2, all_timings=True)
+    assert B.launch_count() == n0 + 6 * 3 and len(tried) == 6
+    for G, f in zip(ref, before):
+        assert np.array_equal(G.get_populations(), f)
     with pytest.raises(lbm.LBMError) as e:
-        B.set_tiling(128, False)
+        B.set_tiling(64, False)
     assert e.value.code == lbm.EINVAL
     with pytest.raises(lbm.LBMError):
-        B.set_tiling(256, True)
-    B.set_tiling(256, False)
-    n0 = B.launch_count()
-    B.autotune(2)
-    assert B.launch_count() == n0 + 3
-    assert B.tiling()[:2] == (256, False)
-    with pytest.raises(lbm.LBMError):
         B.autotune(0)
+
+
+def test_batch_moments_equal_member_moments():
+    for kind in ("d2q5", "d2q9", "d3q27"):
+        ws, fulls = _members(kind)
+        Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+        B = lbm.Batch(Gs)
+        B.step(3)
+        got = B.moments()
+        for G, g in zip(Gs, got):
+            want = G.moments()
+            if kind == "d2q5":
+                assert np.array_equal(g, want)
+            else:
+                assert np.array_equal(g[0], want[0]) and np.array_equal(g[1], want[1])
+        got0 = B.moments(half_forced=False)
+        for G, g in zip(Gs, got0):
+            want = G.moments(half_forced=False)
+            assert np.array_equal(g if kind == "d2q5" else g[1], want if kind == "d2q5" else want[1])
