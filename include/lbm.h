@@ -194,6 +194,29 @@ int lbm_step(lbm_ctx *ctx, long n);
  * Errors: LBM_ESTATE, LBM_EINVAL (NULL output), LBM_ECUDA. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int where, int half_forced);
 
+/* Strain-rate tensor of the current state (flow lattices) from the
+ * non-equilibrium second moments, Sec. 6.6: with Pi_ab = sum f e_a e_b -
+ * rho u_a u_b - rho c_s^2 delta_ab about the half-forced velocity of lbm_moments,
+ *   S_ab = -(3 omega_s / (2 rho0)) Pi_ab   (a != b; the formula of Sec. 6.6)
+ *   S_aa = -(3 / (2 rho0)) (omega_d D_a + omega_b T / dim),
+ * T = sum_a Pi_aa, D_a = Pi_aa - T / dim.  Rates: D2Q9 omega_s = omega[5],
+ * omega_d = omega[4], omega_b = omega[3]; D3Q27 and D3Q15 omega_s = omega_d =
+ * omega[2], omega_b = omega[1].  S receives [ncomp][N]: 2D xx, yy, xy; 3D xx,
+ * yy, zz, xy, xz, yz.  where = 0 host (synchronises), 1 device.  rho0 is the
+ * reference density of the formula (> 0).  Errors: LBM_EINVAL (scalar lattice,
+ * NULL output, rho0 <= 0), LBM_ESTATE, LBM_ECUDA. */
+int lbm_strain_rate(lbm_ctx *ctx, double rho0, double *S, int where);
+
+/* Viscous-heating source of a scalar lattice from a flow lattice on the same
+ * grid and stream (Sec. 6.6, S_r = (2 nu / C_v) S:S): sets the scalar's source
+ * shape to the full field coef * S:S of the flow's current state (computed on
+ * the device, S as in lbm_strain_rate; coef = 2 nu / C_v).  The envelope of
+ * the scalar still multiplies it.  Asynchronous on the shared stream.
+ * Errors: LBM_EINVAL (wrong lattice kinds, grids, streams or devices; rho0
+ * <= 0), LBM_ESTATE (flow not initialised), LBM_ENOMEM, LBM_ECUDA; the
+ * message is on the scalar context. */
+int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, double coef);
+
 /* Global sums over the lattice, computed on the GPU in FP64 with a fixed
  * (deterministic) reduction order:
  *   out[0] = sum rho (flow) or sum phi^o (scalar)
@@ -269,7 +292,9 @@ int lbm_batch_step(lbm_batch *b, long n);
 
 /* Kernel launches issued so far: one per step of lbm_batch_step (whether
  * launched directly or as a node of a replayed graph) plus the trial launches
- * of lbm_batch_autotune. */
+ * of lbm_batch_autotune.  A batch of one member steps outside graph replays
+ * with the member's own single-lattice kernel; those launches are counted by
+ * the member (lbm_launch_count), not here. */
 int lbm_batch_launch_count(const lbm_batch *b, long long *count);
 
 /* Tiling of the batched launch.  The nodes of every member are cut into tiles

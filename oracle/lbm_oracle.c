@@ -710,3 +710,57 @@ int orc_moments(const orc_params *p, const double *f, const double *P, double a_
     }
     return 0;
 }
+
+int orc_strain_rate(const orc_params *p, const double *f, const double *P, double a_pre, double rho0, double *S)
+{
+    basis B;
+    if (check_params(p) || basis_build(p->lattice, &B) || p->lattice == ORC_D2Q5) return -1;
+    long N = (long)p->n[0] * p->n[1] * p->n[2];
+    int dim = orc_dim(p->lattice);
+    double ws, wd, wb;
+    if (p->lattice == ORC_D2Q9) {
+        ws = p->omega[5];
+        wd = p->omega[4];
+        wb = p->omega[3];
+    } else {
+        ws = p->omega[2];
+        wd = p->omega[2];
+        wb = p->omega[1];
+    }
+    const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+    const int ncomp = dim == 2 ? 3 : 6;
+    for (long i = 0; i < N; i++) {
+        double rho = 0.0, j[3] = {0, 0, 0}, m2[3][3] = {{0}};
+        for (int a = 0; a < B.q; a++) {
+            const double fa = f[a * N + i];
+            rho += fa;
+            for (int d = 0; d < dim; d++) {
+                j[d] += fa * B.e[a][d];
+                for (int e = 0; e < dim; e++) m2[d][e] += fa * B.e[a][d] * B.e[a][e];
+            }
+        }
+        double u[3] = {0, 0, 0};
+        for (int d = 0; d < dim; d++) u[d] = (P ? j[d] + a_pre * P[d * N + i] / 2.0 : j[d]) / rho;
+        double Pi[3][3];
+        for (int d = 0; d < dim; d++)
+            for (int e = 0; e < dim; e++)
+                Pi[d][e] = m2[d][e] - rho * u[d] * u[e] - (d == e ? rho / 3.0 : 0.0);
+        double T = 0.0;
+        for (int d = 0; d < dim; d++) T += Pi[d][d];
+        for (int c = 0; c < ncomp; c++) {
+            int a, b;
+            if (dim == 2) {
+                a = c == 2 ? 0 : c;
+                b = c == 2 ? 1 : c;
+            } else {
+                a = pa[c];
+                b = pb[c];
+            }
+            double v;
+            if (a != b) v = -1.5 * ws / rho0 * Pi[a][b];
+            else v = -1.5 / rho0 * (wd * (Pi[a][a] - T / dim) + wb * T / dim);
+            S[c * N + i] = v;
+        }
+    }
+    return 0;
+}

@@ -81,6 +81,17 @@ int orc_run(const orc_params *p, double *f, double *work, long nsteps,
 int orc_moments(const orc_params *p, const double *f, const double *P, double a_pre,
                 double *rho, double *u);
 
+/* Strain-rate tensor from the non-equilibrium second moments (Sec. 6.6):
+ * Pi_ab = sum f e_a e_b - rho u_a u_b - rho c_s^2 delta_ab about the half-forced
+ * velocity u of Eq. 25 / 8A (the a_pre * P / 2 term as in orc_moments), and
+ *   S_ab = -(3 omega_s / (2 rho0)) Pi_ab            (a != b; the formula of Sec. 6.6)
+ *   S_aa = -(3 / (2 rho0)) (omega_d D_a + omega_b T / dim)
+ * with T = sum_a Pi_aa, D_a = Pi_aa - T / dim (trace and deviatoric parts relax
+ * with their own rates: D2Q9 omega_d = omega_4, omega_s = omega_5, omega_b =
+ * omega_3; D3Q27 and D3Q15 omega_d = omega_s = omega[2], omega_b = omega[1]).
+ * Output S[ncomp][N]: 2D xx, yy, xy; 3D xx, yy, zz, xy, xz, yz.  Flow lattices only. */
+int orc_strain_rate(const orc_params *p, const double *f, const double *P, double a_pre, double rho0, double *S);
+
 /* One collision (no streaming) of a single node's populations, for the unit
  * tests: fin[q] -> fout[q], with pre/post force (or source) values and, for
  * D2Q5, the advecting velocity.  Fpre/Fpost have dim entries (flow) or 1 (D2Q5). */

@@ -77,8 +77,9 @@ def lib():
         L.orc_collide_node.argtypes = [pp, dp, dp, dp, dp, dp]
         L.orc_collide_node_generic.argtypes = [pp, dp, dp, dp, dp]
         L.orc_velocities.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.orc_strain_rate.argtypes = [pp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         for fn in ("orc_run", "orc_moments", "orc_equilibrium", "orc_collide_node",
-                   "orc_collide_node_generic", "orc_velocities"):
+                   "orc_collide_node_generic", "orc_velocities", "orc_strain_rate"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -211,6 +212,16 @@ class OracleLattice:
         if self.lattice == D2Q5:
             return rho
         return rho, u
+
+    def strain_rate(self, rho0=1.0):
+        """Strain-rate tensor [ncomp][N] from the non-equilibrium second moments
+        (Sec. 6.6; 2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz)."""
+        ncomp = 3 if self.dim == 2 else 6
+        S = np.empty((ncomp, self.N))
+        rc = lib().orc_strain_rate(ctypes.byref(self.params), _dp(self.f), _dp(self.P), self.a_pre_now(),
+                                   float(rho0), _dp(S))
+        assert rc == 0
+        return S
 
     def collide_node(self, fin, Fpre, Fpost, uadv=None, generic=False):
         fin = np.ascontiguousarray(fin, np.float64)

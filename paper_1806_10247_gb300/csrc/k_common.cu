@@ -371,6 +371,116 @@ k_moments_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, Field
     }
 }
 
+// Strain rate from the non-equilibrium second moments (Sec. 6.6): with
+// Pi = sum f e e - rho u u - rho c_s^2 I about the half-forced u,
+// S_ab = -(3 ws / (2 rho0)) Pi_ab (a != b) and, splitting the diagonal into
+// trace T and deviatoric parts D_a = Pi_aa - T/dim,
+// S_aa = -(3 / (2 rho0)) (wd D_a + wb T/dim).  Order: xx, yy, (zz,) xy, (xz, yz).
+struct StrainRates {
+    double ws, wd, wb;
+};
+
+template <class L>
+__device__ __forceinline__ void strain_node(const double (&f)[L::Q], const double (&Fh)[3], double rho0,
+                                            const StrainRates &r, double *__restrict__ out, int N, int i)
+{
+    double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        const double ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+        rho += f[a];
+        j[0] += ex * f[a];
+        j[1] += ey * f[a];
+        j[2] += ez * f[a];
+        m[0] += ex * ex * f[a];
+        m[1] += ey * ey * f[a];
+        m[2] += ez * ez * f[a];
+        m[3] += ex * ey * f[a];
+        m[4] += ex * ez * f[a];
+        m[5] += ey * ez * f[a];
+    }
+    const double ux = (j[0] + Fh[0]) / rho, uy = (j[1] + Fh[1]) / rho, uz = (j[2] + Fh[2]) / rho;
+    const double c = rho / 3.0;
+    const double pxx = m[0] - rho * ux * ux - c, pyy = m[1] - rho * uy * uy - c;
+    const double pxy = m[3] - rho * ux * uy;
+    const double k = -1.5 / rho0;
+    if (L::DIM == 2) {
+        const double T = pxx + pyy;
+        out[i] = k * (r.wd * (pxx - 0.5 * T) + r.wb * 0.5 * T);
+        out[N + i] = k * (r.wd * (pyy - 0.5 * T) + r.wb * 0.5 * T);
+        out[2 * N + i] = k * r.ws * pxy;
+    } else {
+        const double pzz = m[2] - rho * uz * uz - c;
+        const double pxz = m[4] - rho * ux * uz, pyz = m[5] - rho * uy * uz;
+        const double T = pxx + pyy + pzz;
+        out[i] = k * (r.wd * (pxx - T / 3.0) + r.wb * T / 3.0);
+        out[N + i] = k * (r.wd * (pyy - T / 3.0) + r.wb * T / 3.0);
+        out[2 * N + i] = k * (r.wd * (pzz - T / 3.0) + r.wb * T / 3.0);
+        out[3 * N + i] = k * r.ws * pxy;
+        out[4 * N + i] = k * r.ws * pxz;
+        out[5 * N + i] = k * r.ws * pyz;
+    }
+}
+
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_strain(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, double apre, double rho0, StrainRates r,
+         double *__restrict__ out)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    double f[L::Q];
+    load_pulled<L>(fin, g, x, y, z, i, f);
+    double Fh[3] = {0.0, 0.0, 0.0};
+    if (fkind != FK_NONE)
+        for (int d = 0; d < L::DIM; d++) Fh[d] = 0.5 * (apre * field_value(F, fkind, d, x, y, z, i));
+    strain_node<L>(f, Fh, rho0, r, out, g.N, i);
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_strain_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, FieldDev F, double apre, double rho0,
+            StrainRates r, double *__restrict__ out)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    float d[L::Q];
+    load_pulled_dev<L, T>(fin, g, x, y, z, i, d);
+    double f[L::Q];
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) f[a] = L::w(a) * rho_ref + (double)d[a];
+    double Fh[3] = {0.0, 0.0, 0.0};
+    if (fkind != FK_NONE)
+        for (int dd = 0; dd < L::DIM; dd++) Fh[dd] = 0.5 * (apre * field_value(F, fkind, dd, x, y, z, i));
+    strain_node<L>(f, Fh, rho0, r, out, g.N, i);
+}
+
+// Viscous heating source coef * S:S (Sec. 6.6, S_r = (2 nu / C_v) S:S) from the
+// strain components; written as a full source field (FP64 and FP32 copy).
+__global__ void __launch_bounds__(kBlock)
+k_viscous_source(int N, int dim, const double *__restrict__ S, double coef, double *__restrict__ out,
+                 float *__restrict__ fout)
+{
+    int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= N) return;
+    double v;
+    if (dim == 2) {
+        const double a = S[i], b = S[N + i], c = S[2 * N + i];
+        v = a * a + b * b + 2.0 * c * c;
+    } else {
+        double d2 = 0.0, o2 = 0.0;
+        for (int k = 0; k < 3; k++) d2 += S[k * N + i] * S[k * N + i];
+        for (int k = 3; k < 6; k++) o2 += S[k * N + i] * S[k * N + i];
+        v = d2 + 2.0 * o2;
+    }
+    out[i] = coef * v;
+    if (fout) fout[i] = (float)(coef * v);
+}
+
 template <class Fn>
 cudaError_t by_storage(int storage, Fn &&fn)
 {
@@ -452,6 +562,37 @@ cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, in
                                                                 rho, u);
         return cudaGetLastError();
     });
+}
+
+cudaError_t strain_rate(int lattice, const LaunchArgs &a, double rho0, double *out)
+{
+    StrainRates r;
+    if (lattice == LD2Q9::ID) r = StrainRates{a.omega[5], a.omega[4], a.omega[3]};
+    else r = StrainRates{a.omega[2], a.omega[2], a.omega[1]};
+    if (lattice == LD2Q5::ID) return cudaErrorInvalidValue;
+    if (a.storage != 0)
+        return by_lattice(lattice, [&](auto L) {
+            using LT = decltype(L);
+            if (LT::Q == 5) return cudaErrorInvalidValue;
+            return by_storage(a.storage, [&](auto T) {
+                using TT = decltype(T);
+                k_strain_rp<LT, TT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(
+                    a.g, reinterpret_cast<const TT *>(a.fin), a.rho_ref, a.fkind, a.F, a.apre, rho0, r, out);
+                return cudaGetLastError();
+            });
+        });
+    return by_lattice64(lattice, [&](auto L) {
+        using LT = decltype(L);
+        if (LT::Q == 5) return cudaErrorInvalidValue;
+        k_strain<LT><<<grid_for(a.g.N), kBlock, 0, a.stream>>>(a.g, a.fin, a.fkind, a.F, a.apre, rho0, r, out);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t viscous_source(int N, int dim, const double *S, double coef, double *out, float *fout, cudaStream_t s)
+{
+    k_viscous_source<<<grid_for(N), kBlock, 0, s>>>(N, dim, S, coef, out, fout);
+    return cudaGetLastError();
 }
 
 int reduce_blocks(const Geom &g)

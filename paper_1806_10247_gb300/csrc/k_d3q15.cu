@@ -168,11 +168,11 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     for (int a = 0; a < 15; a++) fout[a * g.Np + i] = f[a];
 }
 
-template <int TB, bool PERSIST>
+template <int TB, int MODE>
 __global__ void __launch_bounds__(TB)
 k_batch(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+    batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
 }
 
 }  // namespace

@@ -270,10 +270,10 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
 }
 
-template <int TB, bool PERSIST>
+template <int TB, int MODE>
 __global__ void __launch_bounds__(TB) k_batch(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
+    batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
 }
 
 bool high_rates_one(const double *om) { return om[3] == 1.0 && om[4] == 1.0 && om[5] == 1.0 && om[6] == 1.0; }

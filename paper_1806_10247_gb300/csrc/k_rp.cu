@@ -529,23 +529,23 @@ __device__ __forceinline__ void node27(const BatchItem &B, const BatchLaunch &L,
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
 }
 
-template <class T, int TB, bool PERSIST>
+template <class T, int TB, int MODE>
 __global__ void __launch_bounds__(TB) k_batch9(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node9<T>(B, L2, it, i); });
+    batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node9<T>(B, L2, it, i); });
 }
 
-template <class T, int TB, bool PERSIST>
+template <class T, int TB, int MODE>
 __global__ void __launch_bounds__(TB) k_batch5(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node5<T>(B, L2, it, i); });
+    batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node5<T>(B, L2, it, i); });
 }
 
 // 1024 / TB blocks per SM keep the D3Q27 kernel at <= 64 registers.
-template <class T, int TB, bool PERSIST>
+template <class T, int TB, int MODE>
 __global__ void __launch_bounds__(TB, 1024 / TB) k_batch27(const __grid_constant__ BatchLaunch L)
 {
-    batch_tiles<TB, PERSIST>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node27<T>(B, L2, it, i); });
+    batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { node27<T>(B, L2, it, i); });
 }
 
 
@@ -600,19 +600,22 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
     return cudaGetLastError();
 }
 
-template <class T, int TB, bool P>
-cudaError_t batch_tbp(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
+template <class T, int TB, int M>
+cudaError_t batch_tbm(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    if (lattice == LD2Q9::ID) k_batch9<T, TB, P><<<nblocks, TB, 0, s>>>(L);
-    else if (lattice == LD2Q5::ID) k_batch5<T, TB, P><<<nblocks, TB, 0, s>>>(L);
-    else k_batch27<T, TB, P><<<nblocks, TB, 0, s>>>(L);
+    if (lattice == LD2Q9::ID) k_batch9<T, TB, M><<<nblocks, TB, 0, s>>>(L);
+    else if (lattice == LD2Q5::ID) k_batch5<T, TB, M><<<nblocks, TB, 0, s>>>(L);
+    else k_batch27<T, TB, M><<<nblocks, TB, 0, s>>>(L);
     return cudaGetLastError();
 }
 
 template <class T, int TB>
 cudaError_t batch_tb(int lattice, const BatchLaunch &L, int nblocks, cudaStream_t s)
 {
-    return L.chunk > 0 ? batch_tbp<T, TB, true>(lattice, L, nblocks, s) : batch_tbp<T, TB, false>(lattice, L, nblocks, s);
+    const int m = tile_mode(L);
+    if (m == TILE_SINGLE) return batch_tbm<T, TB, TILE_SINGLE>(lattice, L, nblocks, s);
+    if (m == TILE_PERSIST) return batch_tbm<T, TB, TILE_PERSIST>(lattice, L, nblocks, s);
+    return batch_tbm<T, TB, TILE_ONE>(lattice, L, nblocks, s);
 }
 
 template <class T>
@@ -629,9 +632,9 @@ cudaError_t batch_t(int lattice, const BatchLaunch &L, int nblocks, int tile, cu
 template <class T, int TB>
 int resident_tb(int lattice)
 {
-    if (lattice == LD2Q9::ID) return resident_blocks(k_batch9<T, TB, true>, TB);
-    if (lattice == LD2Q5::ID) return resident_blocks(k_batch5<T, TB, true>, TB);
-    return resident_blocks(k_batch27<T, TB, true>, TB);
+    if (lattice == LD2Q9::ID) return resident_blocks(k_batch9<T, TB, TILE_PERSIST>, TB);
+    if (lattice == LD2Q5::ID) return resident_blocks(k_batch5<T, TB, TILE_PERSIST>, TB);
+    return resident_blocks(k_batch27<T, TB, TILE_PERSIST>, TB);
 }
 
 template <class T>

@@ -226,6 +226,12 @@ int refresh_descriptors(lbm_batch *b, int *parity)
         *parity = p0;
         return LBM_OK;
     }
+    if (b->gexec) {
+        // a captured graph may hold the old descriptors by value: capture again
+        BCK(cudaStreamSynchronize(b->stream), "lbm_batch_step: sync before dropping the graph");
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
     BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
     for (int i = 0; i < b->count; i++) {
         const lbm_ctx *c = b->ctx[i];
@@ -275,6 +281,13 @@ cudaError_t launch_tiled(lbm_batch *b, BatchLaunch L, int tile_idx, bool persist
     L.first = b->d_first[tile_idx];
     L.ntiles = nt;
     L.chunk = 0;
+    L.single = 0;
+    if (b->count == 1) {
+        // one member: its descriptor goes in the launch arguments
+        L.single = 1;
+        L.one = b->h_items[0];
+        persistent = false;
+    }
     if (persistent) {
         const int r = resident_for(b, tile_idx);
         if (r > 0 && r < nt) {
@@ -444,6 +457,13 @@ int lbm_batch_step(lbm_batch *b, long n)
         if (n == 0) return LBM_OK;
     }
 
+    if (b->count == 1) {
+        // One member outside graph replays: its own single-lattice step kernel
+        // (launch arguments by value, no descriptor), counted by the member.
+        rc = lbm_step(b->ctx[0], n);
+        if (rc != LBM_OK) return bfail(b, rc, "lbm_batch_step: %s", lbm_last_error(b->ctx[0]));
+        return LBM_OK;
+    }
     BatchLaunch L{};
     L.items = b->d_items;
     L.count = b->count;
@@ -514,7 +534,7 @@ int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid)
     if (persistent) *persistent = b->persistent ? 1 : 0;
     if (grid) {
         long long g = b->ntiles[b->tile_idx];
-        if (b->persistent) {
+        if (b->persistent && b->count > 1) {
             const long long r = resident_for(b, b->tile_idx);
             if (r > 0 && r < g) {
                 const long long chunk = (g + r - 1) / r;

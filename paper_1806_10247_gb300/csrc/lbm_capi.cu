@@ -488,6 +488,94 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
     return LBM_OK;
 }
 
+int lbm_strain_rate(lbm_ctx *c, double rho0, double *S, int where)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->lattice == LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_strain_rate: flow lattices only");
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_strain_rate: populations not initialised");
+    if (S == nullptr) return fail(c, LBM_EINVAL, "lbm_strain_rate: NULL output");
+    if (where != 0 && where != 1) return fail(c, LBM_EINVAL, "lbm_strain_rate: where must be 0 or 1");
+    if (!(rho0 > 0.0)) return fail(c, LBM_EINVAL, "lbm_strain_rate: rho0 must be positive");
+    double apre, apost;
+    envelope_pair(c, c->t, apre, apost);
+    LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
+    const size_t N = (size_t)c->g.N;
+    const int ncomp = c->dim == 2 ? 3 : 6;
+    double *dst = S;
+    if (where == 0) {
+        dst = c->B;
+        if (c->storage != LBM_FP64) {
+            int rc = ensure_stage(c);
+            if (rc != LBM_OK) return rc;
+            dst = c->stage;
+        }
+    }
+    CK(strain_rate(c->lattice, a, rho0, dst), "strain-rate kernel");
+    c->launches++;
+    if (where == 0) {
+        CK(cudaMemcpyAsync(S, dst, ncomp * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy strain");
+        CK(cudaStreamSynchronize(c->stream), "lbm_strain_rate");
+    }
+    return LBM_OK;
+}
+
+int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, double coef)
+{
+    if (!scalar || !flow) return LBM_EINVAL;
+    lbm_ctx *c = scalar;  // errors are reported on the scalar context
+    c->err.clear();
+    if (scalar->lattice != LBM_D2Q5_CDE || flow->lattice == LBM_D2Q5_CDE)
+        return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: needs a scalar and a flow lattice");
+    if (scalar->g.nx != flow->g.nx || scalar->g.ny != flow->g.ny || scalar->g.nz != flow->g.nz)
+        return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: grids differ");
+    if (scalar->stream != flow->stream || scalar->device != flow->device)
+        return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: lattices on different streams or devices");
+    if (!flow->initialised) return fail(scalar, LBM_ESTATE, "lbm_set_source_from_strain: flow not initialised");
+    if (!(rho0 > 0.0)) return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: rho0 must be positive");
+    const size_t N = (size_t)scalar->g.N;
+    DeviceField &out = scalar->force;
+    const bool want_f = scalar->storage != LBM_FP64;
+    if (!(out.kind == FK_GENERAL && out.dev && out.cap >= N && !out.d.sep && (!want_f || out.fdev))) {
+        DeviceField nf;
+        CK(cudaMalloc(&nf.dev, N * sizeof(double)), "cudaMalloc(source field)");
+        if (want_f) {
+            cudaError_t ef = cudaMalloc(&nf.fdev, N * sizeof(float));
+            if (ef != cudaSuccess) {
+                cudaFree(nf.dev);
+                return cuda_fail(scalar, ef, "cudaMalloc(source field, FP32 copy)");
+            }
+        }
+        nf.cap = N;
+        nf.kind = FK_GENERAL;
+        nf.d.sep = 0;
+        nf.d.cstride = (long long)N;
+        nf.d.data = nf.dev;
+        nf.d.fdata = nf.fdev;
+        CK(cudaStreamSynchronize(scalar->stream), "lbm_set_source_from_strain: sync");
+        if (out.dev) cudaFree(out.dev);
+        if (out.fdev) cudaFree(out.fdev);
+        out = nf;
+    }
+    // the flow's strain into its own scratch buffer, then coef * S:S into the source field
+    double apre, apost;
+    envelope_pair(flow, flow->t, apre, apost);
+    LaunchArgs a = launch_args(flow, flow->A, nullptr, apre, apost);
+    double *tmp = flow->B;
+    if (flow->storage != LBM_FP64) {
+        int rc = ensure_stage(flow);
+        if (rc != LBM_OK) return fail(scalar, rc, "lbm_set_source_from_strain: %s", flow->err.c_str());
+        tmp = flow->stage;
+    }
+    cudaError_t e = strain_rate(flow->lattice, a, rho0, tmp);
+    if (e == cudaSuccess) e = viscous_source((int)N, flow->dim, tmp, coef, out.dev, out.fdev, scalar->stream);
+    if (e != cudaSuccess) return cuda_fail(scalar, e, "lbm_set_source_from_strain kernels");
+    flow->launches++;
+    scalar->launches++;
+    scalar->version++;
+    return LBM_OK;
+}
+
 int lbm_reduce(lbm_ctx *c, double out[5])
 {
     if (!c) return LBM_EINVAL;

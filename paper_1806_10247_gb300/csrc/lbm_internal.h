@@ -69,11 +69,15 @@ struct BatchLaunch {
     const BatchItem *items;
     const int *first;  // first tile of each item (ascending, first[0] = 0)
     int count;
-    // Reduced-precision kernels only: the launch covers ntiles tiles of the
-    // kernel's tile size; with chunk > 0 block b takes tiles
-    // [b*chunk, min((b+1)*chunk, ntiles)) (persistent grid), else tile b.
+    // The launch covers ntiles tiles of the kernel's tile size; with
+    // chunk > 0 block b takes tiles [b*chunk, min((b+1)*chunk, ntiles))
+    // (persistent grid), else tile b.
     int ntiles;
     int chunk;
+    // single = 1: the batch has one member, whose descriptor travels here in
+    // the launch arguments (read from the constant bank, nothing staged).
+    int single;
+    BatchItem one;
     int k;
     int parity;
     const double2 *pairs;
@@ -95,6 +99,12 @@ int batch_variant(int lattice, const double omega[9]);
 cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
 // Blocks of the reduced-precision batch kernel resident on the whole GPU at once.
 int rp_batch_resident(int lattice, int storage, int tile);
+
+// Strain-rate tensor of the current state (flow lattices): out [ncomp][N],
+// ncomp = 3 (2D: xx, yy, xy) or 6 (3D: xx, yy, zz, xy, xz, yz).
+cudaError_t strain_rate(int lattice, const LaunchArgs &a, double rho0, double *out);
+// out[i] = coef * S:S from strain components S [ncomp][N]; fout (may be NULL) its FP32 copy.
+cudaError_t viscous_source(int N, int dim, const double *S, double coef, double *out, float *fout, cudaStream_t s);
 
 // One fused stream + collide step (pull form): fin -> fout.
 cudaError_t d2q9_step(const LaunchArgs &a);

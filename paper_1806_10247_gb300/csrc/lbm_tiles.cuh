@@ -28,15 +28,23 @@ __device__ __forceinline__ int tile_item(const int *__restrict__ first, int coun
     return lo;
 }
 
+// Kernel forms: one tile per block, persistent (a run of L.chunk tiles per
+// block), single member (descriptor in the launch arguments, one tile per block).
+enum { TILE_ONE = 0, TILE_PERSIST = 1, TILE_SINGLE = 2 };
+
 // Runs node(B, L, member, node index) for every node of the block's tiles,
-// with B the member's descriptor staged in shared memory.  PERSIST selects
-// the persistent form (L.chunk > 0: a run of tiles per block); the one-tile
-// form has no loop, so that it costs no registers.
-template <int TB, bool PERSIST, class Node>
+// with B the member's descriptor (staged in shared memory, or the launch
+// argument copy for a single member).
+template <int TB, int MODE, class Node>
 __device__ __forceinline__ void batch_tiles(const BatchLaunch &L, Node node)
 {
+    if (MODE == TILE_SINGLE) {
+        const int i = blockIdx.x * TB + (int)threadIdx.x;
+        if (i < L.one.g.N) node(L.one, L, 0, i);
+        return;
+    }
     __shared__ BatchItem B;
-    if (!PERSIST) {
+    if (MODE == TILE_ONE) {
         const int tile = blockIdx.x;
         const int it = tile_item(L.first, L.count, tile, -1);
         stage_to_shared(B, L.items[it]);
@@ -76,18 +84,23 @@ int resident_blocks(K kernel, int tb)
     return per_sm * sms;
 }
 
-// Launch of a batched kernel template K<TB, PERSIST> for tile sizes 128,
-// 256, 512; the persistent form when L.chunk > 0.
+// Form of a launch from its arguments.
+inline int tile_mode(const BatchLaunch &L) { return L.single ? TILE_SINGLE : (L.chunk > 0 ? TILE_PERSIST : TILE_ONE); }
+
+// Launch of a batched kernel template K<TB, MODE> for tile sizes 128, 256, 512.
 #define LBM_TILED_LAUNCH(KERNEL, L, nblocks, tile, s)                                              \
     do {                                                                                           \
-        const bool p_ = (L).chunk > 0;                                                             \
+        const int m_ = tile_mode(L);                                                               \
         switch (tile) {                                                                            \
-        case 128: if (p_) KERNEL<128, true><<<(nblocks), 128, 0, (s)>>>(L);                         \
-                  else KERNEL<128, false><<<(nblocks), 128, 0, (s)>>>(L); break;                    \
-        case 256: if (p_) KERNEL<256, true><<<(nblocks), 256, 0, (s)>>>(L);                         \
-                  else KERNEL<256, false><<<(nblocks), 256, 0, (s)>>>(L); break;                    \
-        case 512: if (p_) KERNEL<512, true><<<(nblocks), 512, 0, (s)>>>(L);                         \
-                  else KERNEL<512, false><<<(nblocks), 512, 0, (s)>>>(L); break;                    \
+        case 128: if (m_ == TILE_SINGLE) KERNEL<128, TILE_SINGLE><<<(nblocks), 128, 0, (s)>>>(L);   \
+                  else if (m_ == TILE_PERSIST) KERNEL<128, TILE_PERSIST><<<(nblocks), 128, 0, (s)>>>(L); \
+                  else KERNEL<128, TILE_ONE><<<(nblocks), 128, 0, (s)>>>(L); break;                 \
+        case 256: if (m_ == TILE_SINGLE) KERNEL<256, TILE_SINGLE><<<(nblocks), 256, 0, (s)>>>(L);   \
+                  else if (m_ == TILE_PERSIST) KERNEL<256, TILE_PERSIST><<<(nblocks), 256, 0, (s)>>>(L); \
+                  else KERNEL<256, TILE_ONE><<<(nblocks), 256, 0, (s)>>>(L); break;                 \
+        case 512: if (m_ == TILE_SINGLE) KERNEL<512, TILE_SINGLE><<<(nblocks), 512, 0, (s)>>>(L);   \
+                  else if (m_ == TILE_PERSIST) KERNEL<512, TILE_PERSIST><<<(nblocks), 512, 0, (s)>>>(L); \
+                  else KERNEL<512, TILE_ONE><<<(nblocks), 512, 0, (s)>>>(L); break;                 \
         default: return cudaErrorInvalidValue;                                                     \
         }                                                                                          \
         return cudaGetLastError();                                                                 \
@@ -97,9 +110,9 @@ int resident_blocks(K kernel, int tb)
 #define LBM_TILED_RESIDENT(KERNEL, tile)                                                           \
     do {                                                                                           \
         switch (tile) {                                                                            \
-        case 128: return resident_blocks(KERNEL<128, true>, 128);                                  \
-        case 256: return resident_blocks(KERNEL<256, true>, 256);                                  \
-        case 512: return resident_blocks(KERNEL<512, true>, 512);                                  \
+        case 128: return resident_blocks(KERNEL<128, TILE_PERSIST>, 128);                          \
+        case 256: return resident_blocks(KERNEL<256, TILE_PERSIST>, 256);                          \
+        case 512: return resident_blocks(KERNEL<512, TILE_PERSIST>, 512);                          \
         default: return 0;                                                                         \
         }                                                                                          \
     } while (0)

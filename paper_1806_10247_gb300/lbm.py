@@ -32,7 +32,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
-           "lbm_batch_autotune", "lbm_batch_moments")
+           "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain")
 
 
 class LBMError(RuntimeError):
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_get_tiling.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.lbm_batch_autotune.argtypes = [vp, ip, dp, dp]
     L.lbm_batch_moments.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, ip]
+    L.lbm_strain_rate.argtypes = [vp, ctypes.c_double, dp, ip]
+    L.lbm_set_source_from_strain.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
     L.lbm_batch_destroy.argtypes = [vp]
@@ -278,6 +280,17 @@ class Lattice:
         out = np.empty(5)
         self._check(self._L.lbm_reduce(self.h, _dp(out)))
         return out
+
+    def strain_rate(self, rho0=1.0):
+        """Strain-rate tensor [ncomp][N] (2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz)
+        from the non-equilibrium second moments (Sec. 6.6)."""
+        S = np.empty((3 if self.dim == 2 else 6, self.N))
+        self._check(self._L.lbm_strain_rate(self.h, float(rho0), _dp(S), 0))
+        return S
+
+    def set_source_from_strain(self, flow, coef, rho0=1.0):
+        """Source shape of this scalar lattice := coef * S:S of `flow` (viscous heating)."""
+        self._check(self._L.lbm_set_source_from_strain(self.h, flow.h, float(rho0), float(coef)))
 
     def reduce_sums_noalloc(self):
         """[sum rho, sum jx, sum jy, sum jz] like :meth:`reduce`, computed with the
