@@ -39,49 +39,60 @@ FALLBACK_HBM_GBS = 6800.0
 # traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum), from the
 # ncu captures summarised under profiles/.  FP64 counts are thread-level
 # instructions from ncu's per-opcode table (DFMA, DADD, DMUL); flops count an
-# FMA as two.  The traffic is reported only while the kernel sources still hash
-# to the value it was measured on.
-_H = ["paper_1806_10247_gb300/csrc/lbm_lattices.cuh", "paper_1806_10247_gb300/csrc/lbm_internal.h",
-      "paper_1806_10247_gb300/csrc/lbm_device.cuh"]
+# FMA as two.  The traffic is reported only while the kernel sources (the
+# kernel's file and the device headers it inlines) still hash to the value it
+# was measured on.
+_C = "paper_1806_10247_gb300/csrc/"
+_H = [_C + "lbm_lattices.cuh", _C + "lbm_device.cuh"]
 KERNEL_FACTS = {
     ("cde_sweep", "fp64"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_d2q5.cu"] + _H,
-        "fp64_inst_per_node": 38, "fp64_flops_per_node": 48,
-        "traffic_bytes_per_launch": 14.002176e6, "traffic_src_sha": "5fe048d974140251",
+        "src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H,
+        "fp64_inst_per_node": 30, "fp64_flops_per_node": 56,
+        "traffic_bytes_per_launch": 14.007040e6, "traffic_src_sha": "af1e387d1730d330",
         "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md",
     },
-    ("kolmogorov96", "fp64"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 426, "fp64_flops_per_node": 621,
-        "traffic_bytes_per_launch": (191.174144 + 142.945536) * 1e6, "traffic_src_sha": "890a81d687f85b7f",
-        "profile": "profiles/k_batch_d3q27_kolmogorov96_fp64.md",
-    },
-    ("channel2048", "fp64"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_d2q9.cu"] + _H,
-        "fp64_inst_per_node": 134, "fp64_flops_per_node": 171,
-        "traffic_bytes_per_launch": (151.023616 + 105.353728) * 1e6, "traffic_src_sha": "bf2bab403965bd53",
-        "profile": "profiles/k_batch_d2q9_channel2048_fp64.md",
-    },
     ("kolmogorov96", "fp32"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (95.602176 + 51.792128) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
-        "profile": "profiles/k_batch27_kolmogorov96_fp32_fp16.md",
+        "src": [_C + "k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (95.596288 + 51.692032) * 1e6, "traffic_src_sha": "2ac04432c86724b4",
+        "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov96", "fp16"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (47.818496 + 8.367872) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
-        "profile": "profiles/k_batch27_kolmogorov96_fp32_fp16.md",
+        "src": [_C + "k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (47.817728 + 7.982336) * 1e6, "traffic_src_sha": "2ac04432c86724b4",
+        "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
-    ("channel2048", "fp32"): {
-        "src": ["paper_1806_10247_gb300/csrc/k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (75.518976 + 31.702016) * 1e6, "traffic_src_sha": "104107b6e5fb10f7",
-        "profile": "profiles/k_batch9_channel2048_fp32.md",
+    ("batched_sweep256", "fp32"): {
+        "src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh"] + _H,
+        "traffic_bytes_per_launch": (382.250496 + 336.566016) * 1e6, "traffic_src_sha": "42e6da8fb6b3c246",
+        "profile": "profiles/k_batch9_batched_sweep_fp32.md",
+    },
+    ("kolmogorov96", "fp64"): {
+        "src": [_C + "k_d3q27.cu"] + _H,
+        "fp64_inst_per_node": 311, "fp64_flops_per_node": 448,
+        "traffic_bytes_per_launch": (191.164416 + 138.094592) * 1e6, "traffic_src_sha": "229967383d07e4e6",
+        "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
+    },
+    ("channel2048", "fp64"): {
+        "src": [_C + "k_d2q9.cu"] + _H,
+        "fp64_inst_per_node": 132, "fp64_flops_per_node": 176,
+        "traffic_bytes_per_launch": (151.017472 + 103.077120) * 1e6, "traffic_src_sha": "203f25328b41ef91",
+        "profile": "profiles/k_step_d2q9_channel2048_fp64.md",
+    },
+    ("duct15_96", "fp64"): {
+        "src": [_C + "k_d3q15.cu", _C + "lbm_d3q15.cuh"] + _H,
+        "fp64_inst_per_node": 234, "fp64_flops_per_node": 321,
+        "traffic_bytes_per_launch": (106.208256 + 59.245312) * 1e6, "traffic_src_sha": "c08b40db6129f77b",
+        "profile": "profiles/k_step_d3q15_duct_fp64.md",
     },
 }
-# The same FP64 kernels run the 256^3 / 512^3 Kolmogorov workloads.
-for _w in ("kolmogorov256", "kolmogorov512"):
-    KERNEL_FACTS[(_w, "fp64")] = {k: v for k, v in KERNEL_FACTS[("kolmogorov96", "fp64")].items()
-                                  if k != "traffic_bytes_per_launch"}
+# The same kernels run the larger forms of these workloads (traffic scales with
+# the node count and is not carried over).
+for _w, _base, _st in (("kolmogorov256", "kolmogorov96", "fp64"), ("kolmogorov512", "kolmogorov96", "fp64"),
+                       ("duct15_128", "duct15_96", "fp64"), ("kolmogorov256", "kolmogorov96", "fp32"),
+                       ("kolmogorov512", "kolmogorov96", "fp32"), ("kolmogorov512", "kolmogorov96", "fp16"),
+                       ("batched_sweep", "batched_sweep256", "fp32")):
+    KERNEL_FACTS[(_w, _st)] = {k: v for k, v in KERNEL_FACTS[(_base, _st)].items()
+                               if k != "traffic_bytes_per_launch"}
 # FP64 pipe of the GB300: 2 FMA lanes per clock per SM (the recipe's 1.25 TFLOP/s
 # divided by 2 flop x 152 SMs x 2.07 GHz), 152 SMs, 2.07 GHz maximum SM clock.
 FP64_LANES_PER_SM, N_SMS, SM_GHZ = 2, 152, 2.07

@@ -52,9 +52,8 @@ __device__ __forceinline__ void collide(double (&g)[5], double S, double H0, dou
 }
 
 // With a uniform advecting velocity, Eq. 41 is linear in (phi, kx, ky,
-// kxx + kyy, kxx - kyy) with coefficients fixed for the whole launch; they are
-// formed once on the host (Coef5) and the node update needs ~35 FP64
-// operations instead of ~48.  Same values as `collide` up to rounding.
+// kxx + kyy, kxx - kyy) with coefficients fixed for the whole launch (Coef5,
+// formed on the host; the reduced-precision kernels use them directly).
 struct Coef5 {
     double A1, c1, A2, c2;      // h1 = A1 phi - c1 kx,  h2 = A2 phi - c2 ky
     double P3, X3, Y3, S3;      // h3 = P3 phi + X3 kx + Y3 ky + S3 (kxx + kyy)
@@ -82,45 +81,74 @@ Coef5 make_coef(const Rates5 &w, double ux, double uy)
     return k;
 }
 
-__device__ __forceinline__ void collide_uniform(double (&g)[5], double S, double H0, const Coef5 &k)
+
+// With a uniform advecting velocity the whole step is linear in the pulled
+// populations: writing g0* = g0 + S_pre/2 (phi of Eq. 43 enters only through
+// g0 + S_pre/2), g'_a = sum_b M_ab g*_b + H0 for a = 1..4 and
+// g'_0 = sum_b M_0b g*_b + H0 - S_pre/2, with H0 = (S_pre + S_post)/10
+// (Eqs. 44-48).  M is formed once per launch on the host by applying Eqs. 41
+// and 48 to the unit vectors, so a node costs 25 multiply-adds plus the
+// source terms.
+struct Mat5 {
+    double m[25];
+};
+
+Mat5 make_mat(const Coef5 &k)
 {
-    const double kx = g[1] - g[3], ky = g[2] - g[4];
-    const double kxx = g[1] + g[3], kyy = g[2] + g[4];
-    const double Sg = kxx + kyy, Dg = kxx - kyy;
-    const double phi = fma(0.5, S, g[0] + Sg);  // Eqs. 42-43
-    const double h1 = fma(k.A1, phi, -k.c1 * kx);
-    const double h2 = fma(k.A2, phi, -k.c2 * ky);
-    const double h3 = fma(k.P3, phi, fma(k.X3, kx, fma(k.Y3, ky, k.S3 * Sg)));
-    const double h4 = fma(k.P4, phi, fma(k.X4, kx, fma(k.Y4, ky, k.D4 * Dg)));
-    const double c = H0 + h3;  // Eq. 48
-    const double e1 = c + h4, e2 = c - h4;
-    g[0] += fma(-4.0, h3, H0);
-    g[1] += e1 + h1;
-    g[2] += e2 + h2;
-    g[3] += e1 - h1;
-    g[4] += e2 - h2;
+    Mat5 M;
+    for (int b = 0; b < 5; b++) {
+        double g[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        g[b] = 1.0;
+        const double kx = g[1] - g[3], ky = g[2] - g[4];
+        const double Sg = (g[1] + g[3]) + (g[2] + g[4]), Dg = (g[1] + g[3]) - (g[2] + g[4]);
+        const double phi = g[0] + Sg;
+        const double h1 = k.A1 * phi - k.c1 * kx;
+        const double h2 = k.A2 * phi - k.c2 * ky;
+        const double h3 = k.P3 * phi + k.X3 * kx + k.Y3 * ky + k.S3 * Sg;
+        const double h4 = k.P4 * phi + k.X4 * kx + k.Y4 * ky + k.D4 * Dg;
+        const double out[5] = {g[0] - 4.0 * h3, g[1] + h3 + h1 + h4, g[2] + h3 + h2 - h4, g[3] + h3 - h1 + h4,
+                               g[4] + h3 - h2 - h4};
+        for (int a = 0; a < 5; a++) M.m[5 * a + b] = out[a];
+    }
+    return M;
+}
+
+//   ahalf = a_pre / 2;  hsum = (a_pre + a_post)/10;  P = source shape at the node (0 without one)
+template <bool SRC>
+__device__ __forceinline__ void collide_mat(double (&g)[5], double P, double ahalf, double hsum, const double *M)
+{
+    double gs[5] = {g[0], g[1], g[2], g[3], g[4]};
+    double h = 0.0, h0 = 0.0;
+    if (SRC) {
+        gs[0] = fma(ahalf, P, g[0]);
+        h = hsum * P;
+        h0 = (hsum - ahalf) * P;
+    }
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+        double acc = SRC ? (a == 0 ? h0 : h) : M[5 * a] * gs[0];
+#pragma unroll
+        for (int b = SRC ? 0 : 1; b < 5; b++) acc = fma(M[5 * a + b], gs[b], acc);
+        g[a] = acc;
+    }
 }
 
 template <int SK>
 __global__ void __launch_bounds__(kBlock)
-k_step_uniform(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, double apre,
-               double hsum, Coef5 k)
+k_step_mat(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, double ahalf,
+           double hsum, Mat5 M)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
     const int x = i % g.nx, y = i / g.nx;
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
-    double Spre = 0.0, H0 = 0.0;
-    if (SK != FK_NONE) {
-        const double P = field_value(S, SK, 0, x, y, 0, i);
-        Spre = apre * P;
-        H0 = hsum * P;
-    }
-    collide_uniform(f, Spre, H0, k);
+    if (SK != FK_NONE) collide_mat<true>(f, field_value(S, SK, 0, x, y, 0, i), ahalf, hsum, M.m);
+    else collide_mat<false>(f, 0.0, ahalf, hsum, M.m);
 #pragma unroll
     for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
 }
+
 
 template <int SK, int VK>
 __global__ void __launch_bounds__(kBlock)
@@ -154,15 +182,16 @@ void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
     if (a.vkind != FK_GENERAL) {
         const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0;
         const double uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
-        k_step_uniform<SK><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, hsum,
-                                                           make_coef(w, ux, uy));
+        k_step_mat<SK><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, 0.5 * a.apre, hsum,
+                                                       make_mat(make_coef(w, ux, uy)));
         return;
     }
     k_step<SK, FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w);
 }
 
 // Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
-// coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5.
+// coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5,
+// mat = the step matrix of a uniform advecting velocity.
 // One node of a batched launch (member `it`, node i; B staged in shared memory).
 __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
@@ -174,17 +203,18 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     const int x = i % g.nx, y = i / g.nx;
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
-    double Spre = 0.0, H0 = 0.0;
-    if (B.fkind != FK_NONE) {
-        const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
-        Spre = ap.x * P;
-        H0 = ap.y * P;
-    }
     if (B.vkind != FK_GENERAL) {
-        const Coef5 c{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5],
-                      B.coef[6], B.coef[7], B.coef[8], B.coef[9], B.coef[10], B.coef[11]};
-        collide_uniform(f, Spre, H0, c);
+        if (B.fkind != FK_NONE)
+            collide_mat<true>(f, field_value(B.F, B.fkind, 0, x, y, 0, i), 0.5 * ap.x, ap.y, B.mat);
+        else
+            collide_mat<false>(f, 0.0, 0.0, 0.0, B.mat);
     } else {
+        double Spre = 0.0, H0 = 0.0;
+        if (B.fkind != FK_NONE) {
+            const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
+            Spre = ap.x * P;
+            H0 = ap.y * P;
+        }
         const Rates5 w{B.coef[12], B.coef[13], B.coef[14], B.coef[15]};
         const double ux = field_value(B.V, FK_GENERAL, 0, x, y, 0, i);
         const double uy = field_value(B.V, FK_GENERAL, 1, x, y, 0, i);
@@ -212,6 +242,8 @@ void d2q5_batch_coef(const double omega[9], BatchItem &item)
     const double v[16] = {c.A1, c.c1, c.A2, c.c2, c.P3, c.X3, c.Y3, c.S3,
                           c.P4, c.X4, c.Y4, c.D4, w.c1, w.c2, w.c3, w.c4};
     for (int k = 0; k < 16; k++) item.coef[k] = v[k];
+    const Mat5 M = make_mat(c);
+    for (int k = 0; k < 25; k++) item.mat[k] = M.m[k];
 }
 
 cudaError_t d2q5_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStream_t s)

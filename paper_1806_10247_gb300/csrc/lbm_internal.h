@@ -54,6 +54,7 @@ struct BatchItem {
                       // D2Q5: [16] holds P3 + (2/3) S3 of the uniform-velocity form
     float frho_ref;
     int variant;      // collision variant of this member (batch_variant)
+    double mat[25];   // D2Q5 with a uniform advecting velocity, FP64: step matrix M (row-major)
 };
 
 // Host: fill item.coef from the relaxation rates (and, for the scalar lattice
