@@ -627,21 +627,19 @@ def main():
             raise RuntimeError("skipped in --profile runs")
         for b in batches:
             b.set_graph(0)
-        pinned_out = []
-        for w in wl:
-            nout = 1 if w.lattice == W.D2Q5 else 1 + (3 if w.lattice in (W.D3Q27, W.D3Q15) else 2)
-            pinned_out.append(torch.empty(w.nodes * nout, dtype=torch.float64, pin_memory=True))
-        gout = [[p_ for p_, w in zip(pinned_out, wl) if w.lattice == k] for k in kinds]
+        pinned_out = []  # per lattice kind: packed rho/phi and u of all members
+        for k, ws_ in zip(kinds, gwl):
+            n = sum(w.nodes for w in ws_)
+            dim = 0 if k == W.D2Q5 else (3 if k in (W.D3Q27, W.D3Q15) else 2)
+            pinned_out.append((torch.empty(n, dtype=torch.float64, pin_memory=True),
+                               torch.empty(max(dim * n, 1), dtype=torch.float64, pin_memory=True) if dim else None))
 
         def read_back():
-            for b, k, outs, ws_ in zip(batches, kinds, gout, gwl):
-                if k == W.D2Q5:
-                    b.moments_into([o.data_ptr() for o in outs])
-                else:
-                    b.moments_into([o.data_ptr() for o in outs], [o.data_ptr() + 8 * w.nodes for o, w in zip(outs, ws_)])
+            for b, (r_, u_) in zip(batches, pinned_out):
+                b.moments_packed_into(r_.data_ptr(), None if u_ is None else u_.data_ptr())
 
         ke = e2e_steps
-        d2h = sum(t.numel() * 8 for t in pinned_out)
+        d2h = sum(r_.numel() * 8 + (0 if u_ is None else u_.numel() * 8) for r_, u_ in pinned_out)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -652,7 +650,7 @@ def main():
         e2e = {"value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 16 * len(wl),
                "d2h_bytes_per_step": d2h, "steps": ke,
                "path": "per step: lbm_batch_step(1) per lattice kind (the step's envelope pairs from the host), "
-                       "lbm_batch_moments into pinned host memory per lattice kind"}
+                       "lbm_batch_moments_packed into pinned host memory per lattice kind (one kernel, one sync)"}
         pinned_src = []
         for w in wl:
             from_tables = [((np.asarray(px)[None, None, :] * np.asarray(py)[None, :, None]) * np.asarray(pz)[:, None, None])

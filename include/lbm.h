@@ -345,6 +345,15 @@ int lbm_batch_set_graph(lbm_batch *b, int steps_per_graph);
  * output), LBM_ESTATE, LBM_ECUDA. */
 int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int where, int half_forced);
 
+/* The same fields for every member in one kernel launch, packed member after
+ * member in the batch's order: rho receives N_0 + N_1 + ... values (phi for the
+ * scalar lattice); u (flow lattices) receives member i's [dim][N_i] block
+ * starting at dim * (N_0 + ... + N_{i-1}).  where = 0: host pointers (two
+ * copies and one synchronisation in all); where = 1: device pointers,
+ * asynchronous.  Errors: LBM_EINVAL (NULL output), LBM_ESTATE, LBM_ENOMEM,
+ * LBM_ECUDA. */
+int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced);
+
 /* Graph replays issued so far. */
 int lbm_batch_graph_replays(const lbm_batch *b, long long *count);
 

@@ -61,6 +61,13 @@ struct lbm_batch {
     double2 *d_gpairs = nullptr;
     bool gpairs_filled = false;        // constant envelopes: pairs written once
     cudaEvent_t ev_graph = nullptr;    // recorded after each replay
+    // packed moments (lbm_batch_moments_packed)
+    long long total_nodes = 0;
+    long long *d_off = nullptr;        // first node of each member in the packed output
+    double *h_apre = nullptr;          // pinned a_pre of each member, and its device copy
+    double *d_apre = nullptr;
+    cudaEvent_t ev_apre = nullptr;     // recorded after the a_pre copy
+    double *d_mom = nullptr;           // device staging of the packed output (host destinations)
     std::string err;
 };
 
@@ -157,6 +164,17 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count)
     b->item_buf0.assign(count, nullptr);
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < 3 && e == cudaSuccess; j++) e = cudaMalloc(&b->d_first[j], count * sizeof(int));
+    std::vector<long long> off(count);
+    for (int i = 0; i < count; i++) {
+        off[i] = b->total_nodes;
+        b->total_nodes += ctxs[i]->g.N;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_off, count * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_apre, count * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_apre, count * sizeof(double));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_apre, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_off, off.data(), count * sizeof(long long), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_items, count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, count * sizeof(BatchItem));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_items, cudaEventDisableTiming);
@@ -185,6 +203,11 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaFreeHost(b->h_gpairs);
     cudaFree(b->d_gpairs);
     for (int j = 0; j < 3; j++) cudaFree(b->d_first[j]);
+    cudaFree(b->d_off);
+    cudaFree(b->d_apre);
+    cudaFreeHost(b->h_apre);
+    cudaFree(b->d_mom);
+    if (b->ev_apre) cudaEventDestroy(b->ev_apre);
     cudaFree(b->d_items);
     cudaFreeHost(b->h_items);
     if (b->ev_items) cudaEventDestroy(b->ev_items);
@@ -647,6 +670,61 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
         }
     }
     if (where == 0) BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments");
+    return LBM_OK;
+}
+
+int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    const bool scalar = b->lattice == LBM_D2Q5_CDE;
+    if (!rho || (!scalar && !u)) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: NULL output");
+    if (where != 0 && where != 1) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where must be 0 or 1");
+    for (int i = 0; i < b->count; i++)
+        if (!b->ctx[i]->initialised)
+            return bfail(b, LBM_ESTATE, "lbm_batch_moments_packed: context %d not initialised", i);
+    int parity = 0;
+    int rc = refresh_descriptors(b, &parity);
+    if (rc != LBM_OK) return rc;
+    const int dim = b->ctx[0]->dim;
+    const size_t nrho = (size_t)b->total_nodes, nu = scalar ? 0 : (size_t)dim * b->total_nodes;
+    double *drho = rho, *du = u;
+    if (where == 0) {
+        if (!b->d_mom) BCK(cudaMalloc(&b->d_mom, (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
+        drho = b->d_mom;
+        du = b->d_mom + nrho;
+    }
+    // a_pre of each member's current step; the previous copy has read the pinned slot by ev_apre
+    BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
+    for (int i = 0; i < b->count; i++) {
+        double apre, apost;
+        lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t, apre, apost);
+        b->h_apre[i] = apre;
+    }
+    BCK(cudaMemcpyAsync(b->d_apre, b->h_apre, b->count * sizeof(double), cudaMemcpyHostToDevice, b->stream),
+        "lbm_batch_moments_packed: copy a_pre");
+    BCK(cudaEventRecord(b->ev_apre, b->stream), "lbm_batch_moments_packed: record");
+    BatchMoments M{};
+    M.items = b->d_items;
+    M.first = b->d_first[1];
+    M.count = b->count;
+    M.parity = parity;
+    M.half = half_forced ? 1 : 0;
+    M.apre = b->d_apre;
+    M.off = b->d_off;
+    M.rho = drho;
+    M.u = du;
+    BCK(batch_moments(b->lattice, b->ctx[0]->storage, M, (int)b->ntiles[1], b->stream),
+        "lbm_batch_moments_packed: kernel");
+    b->launches++;
+    if (where == 0) {
+        BCK(cudaMemcpyAsync(rho, drho, nrho * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+            "lbm_batch_moments_packed: copy rho");
+        if (!scalar)
+            BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+                "lbm_batch_moments_packed: copy u");
+        BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments_packed");
+    }
     return LBM_OK;
 }
 

@@ -88,6 +88,20 @@ struct BatchLaunch {
     float2 inlf[kInlinePairs];
 };
 
+// Packed fields of every member of a batch (one launch, tiles of 256 nodes).
+struct BatchMoments {
+    const BatchItem *items;
+    const int *first;        // first 256-node tile of each member
+    int count;
+    int parity;              // buffer parity of the current state relative to the descriptors
+    int half;                // add the pre-collision half force / source
+    const double *apre;      // a_pre of each member's current step
+    const long long *off;    // first node of each member in the packed output
+    double *rho;             // [sum N_i]
+    double *u;               // [sum dim N_i], member i's [dim][N_i] block at dim * off_i
+};
+cudaError_t batch_moments(int lattice, int storage, const BatchMoments &M, int nblocks, cudaStream_t s);
+
 // One launch advancing every item of a batch by one step (FP64 storage);
 // tile = nodes per tile = threads per block: 128, 256 or 512.
 cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);

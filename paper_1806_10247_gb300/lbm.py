@@ -32,7 +32,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_launch_count", "lbm_reduce_sums_noalloc", "lbm_set_envelope_table", "lbm_batch_create",
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
-           "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain")
+           "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
+           "lbm_batch_moments_packed")
 
 
 class LBMError(RuntimeError):
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_autotune.argtypes = [vp, ip, dp, dp]
     L.lbm_batch_moments.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, ip]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_double, dp, ip]
+    L.lbm_batch_moments_packed.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_set_source_from_strain.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
@@ -389,6 +391,25 @@ class Batch:
         else:
             self.moments_into([o[0].ctypes.data for o in outs], [o[1].ctypes.data for o in outs], 0, half_forced)
         return outs
+
+    def moments_packed_into(self, rho_ptr, u_ptr=None, where=0, half_forced=True):
+        """Fields of every member, packed member after member, into one buffer
+        each (raw addresses: host when where = 0, device when where = 1); one
+        kernel launch for the whole batch."""
+        self._check(self._L.lbm_batch_moments_packed(self.h, ctypes.c_void_p(int(rho_ptr)),
+                                                     None if u_ptr is None else ctypes.c_void_p(int(u_ptr)),
+                                                     int(where), int(bool(half_forced))))
+
+    def moments_packed(self, half_forced=True):
+        """(rho or phi [sum N], u [sum dim*N] or None) packed member after member."""
+        n = sum(m.N for m in self.members)
+        rho = np.empty(n)
+        if self.members[0].lattice == D2Q5_CDE:
+            self.moments_packed_into(rho.ctypes.data, None, 0, half_forced)
+            return rho, None
+        u = np.empty(self.members[0].dim * n)
+        self.moments_packed_into(rho.ctypes.data, u.ctypes.data, 0, half_forced)
+        return rho, u
 
     def set_tiling(self, tile, persistent=False):
         """Tile of 128/256/512 nodes per block; persistent grid or one block per tile."""

@@ -298,3 +298,26 @@ def test_batch_moments_equal_member_moments():
         for G, g in zip(Gs, got0):
             want = G.moments(half_forced=False)
             assert np.array_equal(g if kind == "d2q5" else g[1], want if kind == "d2q5" else want[1])
+
+
+def test_packed_moments_equal_member_moments():
+    for kind, storage in (("d2q5", lbm.FP64), ("d2q9", lbm.FP64), ("d3q27", lbm.FP64), ("d3q27", lbm.FP32_DEV)):
+        ws, fulls = _members(kind)
+        if storage == lbm.FP64:
+            Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+        else:
+            Gs = [lbm.from_workload(w, storage=storage) for w in ws]
+        B = lbm.Batch(Gs)
+        B.step(3)
+        Gs[0].step(1)  # one member out of lockstep: packed readback follows each member's own state
+        for half in (True, False):
+            rho, u = B.moments_packed(half_forced=half)
+            off = 0
+            for G in Gs:
+                want = G.moments(half_forced=half)
+                if kind == "d2q5":
+                    assert np.array_equal(rho[off:off + G.N], want)
+                else:
+                    assert np.array_equal(rho[off:off + G.N], want[0])
+                    assert np.array_equal(u[G.dim * off:G.dim * (off + G.N)].reshape(G.dim, G.N), want[1])
+                off += G.N
