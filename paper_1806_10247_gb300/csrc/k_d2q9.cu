@@ -3,6 +3,8 @@
 // f(t) (Eq. 22b, periodic wrap or halfway bounce-back), then applies the
 // pre-collision half force (Eq. 25), the cascaded collision (Eq. 23), the
 // post-collision half force (Eq. 31) and writes f^p(t) = f + K g (Eq. 32).
+#include <cooperative_groups.h>
+
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
 #include "lbm_tiles.cuh"
@@ -89,6 +91,78 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
 }
 
+// ------------------------------------------------------------------------
+// Many steps per launch for a small lattice (e.g. the 3 x 33 channel): the
+// whole state lives in the distributed shared memory of one thread-block
+// cluster.  Block b of the cluster owns nodes [b P, (b + 1) P) and keeps
+// their post-collision populations twice (current and next step) in its
+// shared memory; a pull from a node of another block reads that block's
+// shared memory directly.  One cluster barrier per step separates the
+// writes of a step from the reads of the next.  The per-node arithmetic is
+// `collide` above, so the result equals n single-step launches up to the
+// compiler's multiply-add contraction.
+namespace cg = cooperative_groups;
+
+constexpr int kClusterThreads = 384;  // >= 32-rounded 341, the largest block (48 KB of shared memory)
+
+template <int FK>
+__global__ void __launch_bounds__(kClusterThreads)
+k_cluster_steps(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev F, double apre,
+                double gsum, Rates9 w, int P, int nsteps)
+{
+    extern __shared__ double sm[];  // [2][9][P]
+    cg::cluster_group cl = cg::this_cluster();
+    const int b = (int)cl.block_rank();
+    const int l = threadIdx.x;
+    const int i = b * P + l;
+    const bool own = l < P && i < g.N;
+    if (own)
+#pragma unroll
+        for (int a = 0; a < 9; a++) sm[a * P + l] = fin[a * g.Np + i];
+    const int x = own ? i % g.nx : 0, y = own ? i / g.nx : 0;
+    double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
+    if (FK != FK_NONE && own) {
+        const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
+        Fx = apre * Px;
+        Fy = apre * Py;
+        Gx = gsum * Px;
+        Gy = gsum * Py;
+    }
+    // pull sources of this node: owner block, offset inside its buffer
+    int src_blk[9], src_off[9];
+    if (own) {
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            bool opp = false;
+            const int j = pull_off(g, x, y, 0, LD2Q9::ex(a), LD2Q9::ey(a), 0, opp);
+            const int aa = opp ? LD2Q9::opp(a) : a;
+            src_blk[a] = j / P;
+            src_off[a] = aa * P + (j - (j / P) * P);
+        }
+    }
+    cl.sync();
+    int cur = 0;
+    for (int k = 0; k < nsteps; k++) {
+        if (own) {
+            double f[9];
+#pragma unroll
+            for (int a = 0; a < 9; a++) {
+                const double *base = cl.map_shared_rank(sm + cur * 9 * P, src_blk[a]);
+                f[a] = base[src_off[a]];
+            }
+            collide(f, Fx, Fy, Gx, Gy, w);
+            double *nxt = sm + (cur ^ 1) * 9 * P;
+#pragma unroll
+            for (int a = 0; a < 9; a++) nxt[a * P + l] = f[a];
+        }
+        cur ^= 1;
+        cl.sync();
+    }
+    if (own)
+#pragma unroll
+        for (int a = 0; a < 9; a++) fout[a * g.Np + i] = sm[cur * 9 * P + a * P + l];
+}
+
 // Batched form: one launch for every lattice of a batch; pairs hold
 // (a_pre, (a_pre + a_post)/12) per step and item.
 // One node of a batched launch (member `it`, node i; B staged in shared memory).
@@ -141,6 +215,51 @@ cudaError_t d2q9_batch_step(const BatchLaunch &L, int nblocks, int tile, cudaStr
 int d2q9_batch_resident(int tile)
 {
     LBM_TILED_RESIDENT(k_batch, tile);
+}
+
+// Cluster form for small lattices with a constant envelope; returns
+// cudaErrorNotSupported when the lattice does not fit (the caller then steps
+// with single launches).
+cudaError_t d2q9_cluster_steps(const LaunchArgs &a, int nsteps)
+{
+    // about 8 nodes per block (the FP64 work of a step spread over up to 16 SMs)
+    const int C = a.g.N >= 16 * 8 ? 16 : (a.g.N + 7) / 8;
+    const int P = (a.g.N + C - 1) / C;
+    const int threads = (P + 31) / 32 * 32;
+    const size_t smem = (size_t)2 * 9 * P * sizeof(double);
+    if (threads > kClusterThreads || smem > 48 * 1024) return cudaErrorNotSupported;
+    Rates9 w{a.omega[3] / 12.0, a.omega[4] / 4.0, a.omega[5] / 4.0,
+             a.omega[6] / 4.0, a.omega[7] / 4.0, a.omega[8] / 4.0};
+    const double gsum = (a.apre + a.apost) / 12.0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    switch (a.fkind) {
+    case FK_NONE:
+        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_NONE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_NONE>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P, nsteps);
+        break;
+    case FK_CONST:
+        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_CONST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_CONST>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P, nsteps);
+        break;
+    default:
+        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_GENERAL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_GENERAL>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P,
+                               nsteps);
+        break;
+    }
+    return e;
 }
 
 cudaError_t d2q9_step(const LaunchArgs &a)

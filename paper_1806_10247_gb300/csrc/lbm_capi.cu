@@ -428,6 +428,26 @@ int lbm_step(lbm_ctx *c, long n)
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step: populations not initialised");
     if (!envelope_covers(c, c->t, n))
         return fail(c, LBM_EINVAL, "lbm_step: steps %ld..%ld are outside the envelope table", c->t, c->t + n);
+    if (n >= 2 && n <= 2147483647L && c->storage == LBM_FP64 && c->lattice == LBM_D2Q9 && !c->env &&
+        c->env_tab.empty()) {
+        // a small lattice with a constant force: all n steps in one cluster launch
+        double *out = (n & 1) ? c->B : c->A;
+        LaunchArgs a = launch_args(c, c->A, out, 1.0, 1.0);
+        cudaError_t e = d2q9_cluster_steps(a, (int)n);
+        if (e == cudaSuccess) {
+            c->launches++;
+            if (n & 1) {
+                double *tmp = c->A;
+                c->A = c->B;
+                c->B = tmp;
+            }
+            c->t += n;
+            return LBM_OK;
+        }
+        // Not supported here (too large), or a cluster launch the device
+        // refuses: clear the launch error and take single-step launches.
+        if (e != cudaErrorNotSupported) cudaGetLastError();
+    }
     for (long k = 0; k < n; k++) {
         double apre, apost;
         envelope_pair(c, c->t, apre, apost);

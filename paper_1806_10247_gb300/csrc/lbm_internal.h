@@ -125,6 +125,11 @@ cudaError_t viscous_source(int N, int dim, const double *S, double coef, double 
 cudaError_t d2q9_step(const LaunchArgs &a);
 cudaError_t d2q5_step(const LaunchArgs &a);
 cudaError_t d3q15_step(const LaunchArgs &a);
+// D2Q9, FP64, constant envelope: nsteps steps of a small lattice in one
+// launch (one thread-block cluster holding the state in its shared memory);
+// cudaErrorNotSupported when the lattice is too large.  fin -> fout after
+// nsteps steps (fout may equal fin).
+cudaError_t d2q9_cluster_steps(const LaunchArgs &a, int nsteps);
 cudaError_t d3q27_step(const LaunchArgs &a);
 
 // Moments of the current state: rho[N] and u[dim][N] (flow) or phi[N] (scalar);

@@ -119,3 +119,29 @@ def test_source_lattice_restart_matches_uninterrupted_oracle():
     R = oracle_from_workload(w)
     R.run(73)
     compare_state(B, R)
+
+
+def test_small_d2q9_cluster_steps_equal_single_launches_and_oracle():
+    """A small constant-force D2Q9 lattice takes n >= 2 steps in one cluster
+    launch; the result equals n single-step launches (to rounding) and the
+    oracle (parity bar).  Sizes cover 1 to 16 blocks and a ragged last block."""
+    from tests.gpu_helpers import compare_state, oracle_from_workload
+
+    for ny, nx in ((33, 3), (9, 2), (40, 17), (61, 70)):
+        w = W.poiseuille(ny=ny, nx=nx, tau=0.7, Fx=1e-5)
+        a = lbm.from_workload(w)
+        b = lbm.from_workload(w)
+        n0 = a.launch_count()
+        a.step(37)
+        assert a.launch_count() == n0 + 1 or a.N > 5000
+        for _ in range(37):
+            b.step(1)
+        fa, fb = a.get_populations(), b.get_populations()
+        assert np.abs(fa - fb).max() <= 37 * 4 * 2.0 ** -53 * np.abs(fb).max() * 2
+        R = oracle_from_workload(w)
+        R.run(37)
+        compare_state(a, R)
+        a.step(2)
+        a.step(3)
+        R.run(5)
+        compare_state(a, R)

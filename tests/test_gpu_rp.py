@@ -139,3 +139,17 @@ def test_reduced_precision_batch_and_checkpoint(form):
     assert abs(r[0] - ws[1].nodes) < (1e-6 if form == "fp32" else 1e-4) * ws[1].nodes
     s = grp[1].reduce_sums_noalloc()
     assert np.allclose(s, r[:4], rtol=1e-12, atol=1e-12)
+
+
+def test_fp32_kolmogorov_256_full_size_sampled_step():
+    """Config 3 at 256^3 with FP32-deviation storage in the bench's launch
+    configuration: 3 steps, then one more step checked on 200 sampled nodes
+    against the FP64 oracle's collision of the same f(t) (the FP32 moment
+    arithmetic is the only difference)."""
+    from tests.test_gpu_parity import _one_step_sampled
+
+    w = W.kolmogorov(n=256)
+    G = lbm.from_workload(w, storage=lbm.FP32_DEV)
+    G.step(3)
+    worst = _one_step_sampled(w, G, samples=200, seed=9, tol=2e-6)
+    _record("kolmogorov_256_fp32_one_step_sampled_rel_max", worst)
