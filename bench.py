@@ -634,30 +634,55 @@ def main():
             raise RuntimeError("skipped in --profile runs")
         for b in batches:
             b.set_graph(0)
-        pinned_out = []  # per lattice kind: packed rho/phi and u of all members
+        pinned_out = []  # per lattice kind, two slots: packed rho/phi and u of all members
         for k, ws_ in zip(kinds, gwl):
             n = sum(w.nodes for w in ws_)
             dim = 0 if k == W.D2Q5 else (3 if k in (W.D3Q27, W.D3Q15) else 2)
-            pinned_out.append((torch.empty(n, dtype=torch.float64, pin_memory=True),
-                               torch.empty(max(dim * n, 1), dtype=torch.float64, pin_memory=True) if dim else None))
+            pinned_out.append([(torch.empty(n, dtype=torch.float64, pin_memory=True),
+                                torch.empty(dim * n, dtype=torch.float64, pin_memory=True) if dim else None)
+                               for _ in range(2)])
 
-        def read_back():
-            for b, (r_, u_) in zip(batches, pinned_out):
+        def read_back(slot):
+            for b, slots in zip(batches, pinned_out):
+                r_, u_ = slots[slot]
                 b.moments_packed_into(r_.data_ptr(), None if u_ is None else u_.data_ptr())
 
+        def read_back_async(slot):
+            # kernel on the lattice stream, copy on the library's copy stream;
+            # step k's copy overlaps step k + 1, and step k - 1's fields are on
+            # the host before the loop moves on
+            for b, slots in zip(batches, pinned_out):
+                r_, u_ = slots[slot]
+                b.moments_packed_into(r_.data_ptr(), None if u_ is None else u_.data_ptr(), where=2)
+            for b in batches:
+                b.wait_moments(keep=1)
+
         ke = e2e_steps
-        d2h = sum(r_.numel() * 8 + (0 if u_ is None else u_.numel() * 8) for r_, u_ in pinned_out)
+        d2h = sum(r_.numel() * 8 + (0 if u_ is None else u_.numel() * 8) for r_, u_ in (sl[0] for sl in pinned_out))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(ke):
+        for k in range(ke):
             for b in batches:
                 b.step(1)
-            read_back()
+            read_back_async(k % 2)
+        for b in batches:
+            b.wait_moments(keep=0)
         el = time.perf_counter() - t0
         e2e = {"value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": 16 * len(wl),
                "d2h_bytes_per_step": d2h, "steps": ke,
                "path": "per step: lbm_batch_step(1) per lattice kind (the step's envelope pairs from the host), "
-                       "lbm_batch_moments_packed into pinned host memory per lattice kind (one kernel, one sync)"}
+                       "lbm_batch_moments_packed(where=2) into pinned host memory (copy overlapped with the next "
+                       "step, double-buffered), every step's fields on the host before the timer stops"}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(ke):
+            for b in batches:
+                b.step(1)
+            read_back(k % 2)
+        el = time.perf_counter() - t0
+        e2e["synchronous_readback"] = {
+            "value": nodes * ke / el / 1e6, "unit": "MLUPS",
+            "path": "as above, but lbm_batch_moments_packed(where=0): one synchronisation per step"}
         pinned_src = []
         for w in wl:
             from_tables = [((np.asarray(px)[None, None, :] * np.asarray(py)[None, :, None]) * np.asarray(pz)[:, None, None])
@@ -676,7 +701,7 @@ def main():
                     L.set_force(full=s_.numpy())
             for b in batches:
                 b.step(1)
-            read_back()
+            read_back(0)
         el = time.perf_counter() - t0
         e2e["full_field_upload"] = {
             "value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": sum(t.numel() * 8 for t in pinned_src),

@@ -354,9 +354,19 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
  * scalar lattice); u (flow lattices) receives member i's [dim][N_i] block
  * starting at dim * (N_0 + ... + N_{i-1}).  where = 0: host pointers (two
  * copies and one synchronisation in all); where = 1: device pointers,
- * asynchronous.  Errors: LBM_EINVAL (NULL output), LBM_ESTATE, LBM_ENOMEM,
- * LBM_ECUDA. */
+ * asynchronous; where = 2: host pointers (pinned memory for a true overlap),
+ * asynchronous: the kernel runs on the batch's stream into one of two
+ * staging slots and the copies run on a private copy stream, so that they
+ * overlap the steps queued after this call; the host buffers are valid after
+ * lbm_batch_wait_moments.  Errors: LBM_EINVAL (NULL output), LBM_ESTATE,
+ * LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced);
+
+/* Wait for the asynchronous readbacks (where = 2): keep = 0 waits for all of
+ * them, keep = 1 for all but the most recent one (double buffering: the
+ * previous step's fields are in host memory while the latest copy is still
+ * in flight).  Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_batch_wait_moments(lbm_batch *b, int keep);
 
 /* Graph replays issued so far. */
 int lbm_batch_graph_replays(const lbm_batch *b, long long *count);

@@ -68,6 +68,14 @@ struct lbm_batch {
     double *d_apre = nullptr;
     cudaEvent_t ev_apre = nullptr;     // recorded after the a_pre copy
     double *d_mom = nullptr;           // device staging of the packed output (host destinations)
+    // asynchronous packed readback (where = 2): two staging slots, copies on a
+    // private stream so that they overlap the next steps
+    double *d_momq[2] = {nullptr, nullptr};
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // slot filled (recorded on the batch stream)
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};  // slot copied out (recorded on the copy stream)
+    int qslot = 0;
+    bool copies_pending = false;
     std::string err;
 };
 
@@ -207,6 +215,13 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaFree(b->d_apre);
     cudaFreeHost(b->h_apre);
     cudaFree(b->d_mom);
+    if (b->cstream) cudaStreamSynchronize(b->cstream);
+    for (int k = 0; k < 2; k++) {
+        cudaFree(b->d_momq[k]);
+        if (b->ev_ready[k]) cudaEventDestroy(b->ev_ready[k]);
+        if (b->ev_copied[k]) cudaEventDestroy(b->ev_copied[k]);
+    }
+    if (b->cstream) cudaStreamDestroy(b->cstream);
     if (b->ev_apre) cudaEventDestroy(b->ev_apre);
     cudaFree(b->d_items);
     cudaFreeHost(b->h_items);
@@ -679,7 +694,7 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
     b->err.clear();
     const bool scalar = b->lattice == LBM_D2Q5_CDE;
     if (!rho || (!scalar && !u)) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: NULL output");
-    if (where != 0 && where != 1) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where must be 0 or 1");
+    if (where < 0 || where > 2) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where must be 0, 1 or 2");
     for (int i = 0; i < b->count; i++)
         if (!b->ctx[i]->initialised)
             return bfail(b, LBM_ESTATE, "lbm_batch_moments_packed: context %d not initialised", i);
@@ -689,10 +704,26 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
     const int dim = b->ctx[0]->dim;
     const size_t nrho = (size_t)b->total_nodes, nu = scalar ? 0 : (size_t)dim * b->total_nodes;
     double *drho = rho, *du = u;
+    int slot = 0;
     if (where == 0) {
         if (!b->d_mom) BCK(cudaMalloc(&b->d_mom, (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
         drho = b->d_mom;
         du = b->d_mom + nrho;
+    } else if (where == 2) {
+        if (!b->cstream) {
+            BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
+            for (int k = 0; k < 2; k++) {
+                BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
+                BCK(cudaEventCreateWithFlags(&b->ev_ready[k], cudaEventDisableTiming), "event");
+                BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
+            }
+        }
+        slot = b->qslot;
+        b->qslot ^= 1;
+        // the slot's previous copy must have left it before the kernel refills it
+        BCK(cudaStreamWaitEvent(b->stream, b->ev_copied[slot], 0), "lbm_batch_moments_packed: wait");
+        drho = b->d_momq[slot];
+        du = b->d_momq[slot] + nrho;
     }
     // a_pre of each member's current step; the previous copy has read the pinned slot by ev_apre
     BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
@@ -724,6 +755,32 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
             BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
                 "lbm_batch_moments_packed: copy u");
         BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments_packed");
+    } else if (where == 2) {
+        BCK(cudaEventRecord(b->ev_ready[slot], b->stream), "lbm_batch_moments_packed: record");
+        BCK(cudaStreamWaitEvent(b->cstream, b->ev_ready[slot], 0), "lbm_batch_moments_packed: wait");
+        BCK(cudaMemcpyAsync(rho, drho, nrho * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
+            "lbm_batch_moments_packed: copy rho");
+        if (!scalar)
+            BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
+                "lbm_batch_moments_packed: copy u");
+        BCK(cudaEventRecord(b->ev_copied[slot], b->cstream), "lbm_batch_moments_packed: record");
+        b->copies_pending = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_wait_moments(lbm_batch *b, int keep)
+{
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    if (keep != 0 && keep != 1) return bfail(b, LBM_EINVAL, "lbm_batch_wait_moments: keep must be 0 or 1");
+    if (!b->copies_pending) return LBM_OK;
+    if (keep == 0) {
+        BCK(cudaStreamSynchronize(b->cstream), "lbm_batch_wait_moments");
+        b->copies_pending = false;
+    } else {
+        // the readback before the latest used slot qslot (the slots alternate)
+        BCK(cudaEventSynchronize(b->ev_copied[b->qslot]), "lbm_batch_wait_moments");
     }
     return LBM_OK;
 }

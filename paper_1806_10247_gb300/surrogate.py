@@ -256,8 +256,10 @@ def generate(n: int, count: int, seed: int, storage=lbm.FP64, tol=1e-10):
     return X, Y, params, {"steps": steps, "seconds": sec}
 
 
-def train(net: ConvNet, X, Y, iters=1500, batch=32, lr=2e-3, seed=0, log_every=0):
-    """Adam on minibatches; X, Y numpy.  Returns the loss history."""
+def train(net: ConvNet, X, Y, iters=1500, batch=32, lr=2e-3, seed=0, log_every=0, lr_final=None):
+    """Adam on minibatches; X, Y numpy.  With lr_final the step size follows a
+    cosine from lr down to lr_final over the iterations (a stable end point
+    instead of the last noisy minibatch).  Returns the loss history."""
     torch = net.torch
     Xd = torch.tensor(X, device="cuda")
     Yd = torch.tensor(Y, device="cuda")
@@ -267,7 +269,10 @@ def train(net: ConvNet, X, Y, iters=1500, batch=32, lr=2e-3, seed=0, log_every=0
     for it in range(iters):
         idx = torch.tensor(rng.choice(S, size=min(batch, S), replace=False), device="cuda")
         loss, grads = net.loss_and_grads(Xd[idx], Yd[idx])
-        net.adam_step(grads, lr=lr)
+        step = lr
+        if lr_final is not None:
+            step = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * it / max(iters - 1, 1)))
+        net.adam_step(grads, lr=step)
         hist.append(loss)
         if log_every and it % log_every == 0:
             print(f"iter {it} loss {loss:.3e}")
@@ -310,7 +315,7 @@ def warm_start_study(net: ConvNet, n: int, cases, tol=1e-10, storage=lbm.FP64):
     return out
 
 
-def study(n=64, train_count=192, test_count=8, iters=3000, seed=10247, gen_storage=lbm.FP32_DEV,
+def study(n=64, train_count=192, test_count=8, iters=4000, seed=10247, gen_storage=lbm.FP32_DEV,
           gen_tol=1e-7, tol=1e-10):
     """The full warm-start experiment: method-generated training fields (FP32
     storage, residual gen_tol), training on the GPU, then for held-out
@@ -321,7 +326,7 @@ def study(n=64, train_count=192, test_count=8, iters=3000, seed=10247, gen_stora
     t_gen = time.perf_counter() - t0
     net = ConvNet(seed=0, bf16=True)
     t0 = time.perf_counter()
-    hist = train(net, X, Y, iters=iters, batch=32, lr=2e-3, seed=seed)
+    hist = train(net, X, Y, iters=iters, batch=32, lr=2e-3, seed=seed, lr_final=2e-5)
     net.torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     cases = draw_params(test_count, n, seed + 1)

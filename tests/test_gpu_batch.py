@@ -359,3 +359,35 @@ def test_full_batched_sweep_in_the_bench_configuration():
         B.close()
         for G in Gs:
             G.close()
+
+
+def test_asynchronous_packed_readback_double_buffered():
+    """where = 2: the copies overlap later steps; after wait_moments the host
+    buffers hold exactly the fields of the step they were queued at."""
+    import torch
+
+    ws, fulls = _members("d2q9")
+    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+    twins = [_make(w, f) for w, f in zip(ws, fulls)]
+    B = lbm.Batch(Gs)
+    T = lbm.Batch(twins)
+    n = sum(G.N for G in Gs)
+    bufs = [(torch.empty(n, dtype=torch.float64, pin_memory=True),
+             torch.empty(2 * n, dtype=torch.float64, pin_memory=True)) for _ in range(2)]
+    history = []
+    for k in range(6):
+        B.step(1)
+        T.step(1)
+        history.append(T.moments_packed())
+        r_, u_ = bufs[k % 2]
+        B.moments_packed_into(r_.data_ptr(), u_.data_ptr(), where=2)
+        B.wait_moments(keep=1)
+        if k >= 1:
+            r_prev, u_prev = bufs[(k - 1) % 2]
+            assert np.array_equal(r_prev.numpy(), history[k - 1][0])
+            assert np.array_equal(u_prev.numpy(), history[k - 1][1])
+    B.wait_moments(keep=0)
+    r_, u_ = bufs[5 % 2]
+    assert np.array_equal(r_.numpy(), history[5][0]) and np.array_equal(u_.numpy(), history[5][1])
+    with pytest.raises(lbm.LBMError):
+        B.wait_moments(keep=3)
