@@ -426,6 +426,9 @@ def main():
     ap.add_argument("--graph", type=int, default=None,
                     help="steps per CUDA-graph replay in the timed region (even; 0 = plain launches; "
                          "default 0, 10 for batched_sweep)")
+    ap.add_argument("--chunk", type=int, default=1,
+                    help="steps per lbm_batch_step call in the timed region without graphs (a one-member "
+                         "batch of a small FP64 D2Q9 lattice then runs them in one cluster launch)")
     ap.add_argument("--tune", type=int, default=None, choices=[0, 1],
                     help="autotune the batch tiling before the warm-up (default 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -504,7 +507,9 @@ def main():
             t, p, g = b.tiling()
             tuning.append({"lattice": Q_NAME[k], "tile": t, "persistent": p, "grid": g, "trial_us_per_launch": us,
                            "trials_us": {f"{tt}{'p' if pp else ''}": v for (tt, pp), v in tried.items()}})
-    unit = args.graph if args.graph else 1
+    unit = args.graph if args.graph else max(1, args.chunk)
+    if args.steps % unit:
+        raise SystemExit(f"--steps must be a multiple of {unit}")
     for b in batches:
         b.set_graph(args.graph)
     need_flush = state_bytes(wl, elem) < 2 * L2_BYTES
@@ -575,7 +580,8 @@ def main():
             "kernel": f"batched {Q_NAME[kinds[dom]]} step kernel ({nb} nodes)",
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
             "bytes_per_node": 2 * elem * q, "kernel_us": kavg_s * 1e6,
-            "timing": "CUDA events around each batch's launches" + (f" (graph replays of {unit} steps)" if args.graph else "")}
+            "timing": "CUDA events around each batch's launches" + (f" (graph replays of {unit} steps)" if args.graph else
+                                                                  (f" ({unit} steps per call)" if unit > 1 else ""))}
     if facts.get("fp64_flops_per_node"):
         tf = facts["fp64_flops_per_node"] * nb / kavg_s / 1e12
         gi = facts["fp64_inst_per_node"] * nb / kavg_s / 1e9

@@ -198,6 +198,13 @@ int lbm_step(lbm_ctx *ctx, long n);
  * Errors: LBM_ESTATE, LBM_EINVAL (NULL output), LBM_ECUDA. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int where, int half_forced);
 
+/* Debug aid: fill the context's second population buffer (the destination
+ * of the next step) with NaN.  Every node of every plane is written by a
+ * step, so after it the state holds no NaN; a node a kernel failed to write
+ * would keep the NaN and make lbm_reduce return LBM_EUNSTABLE.  Asynchronous.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+int lbm_debug_poison(lbm_ctx *ctx);
+
 /* Strain-rate tensor of the current state (flow lattices) from the
  * non-equilibrium second moments, Sec. 6.6: with Pi_ab = sum f e_a e_b -
  * rho u_a u_b - rho c_s^2 delta_ab about the half-forced velocity of lbm_moments,

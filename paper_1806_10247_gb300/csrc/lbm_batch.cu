@@ -460,6 +460,7 @@ int capture_graph(lbm_batch *b, int parity)
 
 int lbm_batch_step(lbm_batch *b, long n)
 {
+    lbmc::NvtxRange nvtx_("lbm_batch_step");
     if (!b) return LBM_EINVAL;
     b->err.clear();
     if (n < 0) return bfail(b, LBM_EINVAL, "lbm_batch_step: n < 0");
@@ -586,6 +587,7 @@ int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid)
 
 int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *all_us)
 {
+    lbmc::NvtxRange nvtx_("lbm_batch_autotune");
     if (!b) return LBM_EINVAL;
     b->err.clear();
     if (trial_steps < 1 || trial_steps > 1000)
@@ -690,6 +692,7 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
 
 int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced)
 {
+    lbmc::NvtxRange nvtx_("lbm_batch_moments_packed");
     if (!b) return LBM_EINVAL;
     b->err.clear();
     const bool scalar = b->lattice == LBM_D2Q5_CDE;

@@ -422,6 +422,7 @@ int lbm_set_envelope_table(lbm_ctx *c, const double *a, long count, double t0)
 
 int lbm_step(lbm_ctx *c, long n)
 {
+    NvtxRange nvtx_("lbm_step");
     if (!c) return LBM_EINVAL;
     c->err.clear();
     if (n < 0) return fail(c, LBM_EINVAL, "lbm_step: n < 0");
@@ -475,6 +476,7 @@ int lbm_step(lbm_ctx *c, long n)
 
 int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
 {
+    NvtxRange nvtx_("lbm_moments");
     if (!c) return LBM_EINVAL;
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_moments: populations not initialised");
@@ -505,6 +507,15 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
                "copy u");
         CK(cudaStreamSynchronize(c->stream), "lbm_moments");
     }
+    return LBM_OK;
+}
+
+int lbm_debug_poison(lbm_ctx *c)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    // all-ones bytes are a NaN in every storage type (FP64, FP32, FP16, BF16)
+    CK(cudaMemsetAsync(c->B, 0xFF, (size_t)c->q * c->g.Np * c->elem, c->stream), "poison");
     return LBM_OK;
 }
 
@@ -598,6 +609,7 @@ int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, doub
 
 int lbm_reduce(lbm_ctx *c, double out[5])
 {
+    NvtxRange nvtx_("lbm_reduce");
     if (!c) return LBM_EINVAL;
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_reduce: populations not initialised");

@@ -49,7 +49,17 @@ struct lbm_ctx {
     std::string err;
 };
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace lbmc {
+
+// NVTX range for the duration of a scope (no cost unless a profiler attaches).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Record a failure on c (or, for c == NULL, the process-wide lbm_create error)
 // and return code.

@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
            "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
-           "lbm_batch_moments_packed", "lbm_batch_wait_moments")
+           "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison")
 
 
 class LBMError(RuntimeError):
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_double, dp, ip]
     L.lbm_batch_moments_packed.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_batch_wait_moments.argtypes = [vp, ip]
+    L.lbm_debug_poison.argtypes = [vp]
     L.lbm_set_source_from_strain.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
@@ -177,6 +178,7 @@ class Lattice:
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
         self.q = Q[lattice]
         self.dim = DIM[lattice]
+        self.storage = int(storage)
         r = _Relax()
         for k in range(9):
             r.omega[k] = float(omega[k])
@@ -283,6 +285,24 @@ class Lattice:
         out = np.empty(5)
         self._check(self._L.lbm_reduce(self.h, _dp(out)))
         return out
+
+    def debug_poison(self):
+        """Fill the destination buffer of the next step with NaN (debug aid)."""
+        self._check(self._L.lbm_debug_poison(self.h))
+
+    def save_checkpoint(self, path):
+        """Write f(t), the step counter and the lattice description to an .npz file."""
+        np.savez(path, f=self.get_populations(), t=self.t, lattice=self.lattice, shape=np.array(self.shape),
+                 storage=self.storage)
+
+    def load_checkpoint(self, path):
+        """Restore a checkpoint written by save_checkpoint on a lattice of the
+        same kind, shape and storage (bitwise resume)."""
+        with np.load(path) as z:
+            if int(z["lattice"]) != self.lattice or tuple(z["shape"]) != tuple(self.shape) or \
+                    int(z["storage"]) != self.storage:
+                raise ValueError("checkpoint does not match this lattice")
+            self.set_populations(np.ascontiguousarray(z["f"]), step=int(z["t"]))
 
     def strain_rate(self, rho0=1.0):
         """Strain-rate tensor [ncomp][N] (2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz)

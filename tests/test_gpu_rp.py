@@ -153,3 +153,25 @@ def test_fp32_kolmogorov_256_full_size_sampled_step():
     G.step(3)
     worst = _one_step_sampled(w, G, samples=200, seed=9, tol=2e-6)
     _record("kolmogorov_256_fp32_one_step_sampled_rel_max", worst)
+
+
+def test_config3_kolmogorov_256_1000_steps_error_per_form():
+    """Config 3 as stated: Kolmogorov 256^3, 1000 steps, the FP64 run (which
+    matches the oracle to 1e-12 in the parity tests) against each
+    reduced-precision form.  FP32 must stay within 1e-4 relative l2 in u;
+    the 16-bit errors are recorded."""
+    w = W.kolmogorov(n=256)
+    ref = lbm.from_workload(w)
+    ref.step(1000)
+    _, u_ref = ref.moments()
+    ref.close()
+    for form in ("fp32", "fp16", "bf16"):
+        G = lbm.from_workload(w, storage=STORAGES[form])
+        G.step(1000)
+        _, u = G.moments()
+        G.close()
+        err = _l2(u, u_ref)
+        _record(f"kolmogorov_d3q27_256cubed_1000_{form}", err)
+        assert np.isfinite(err) and err < 1.0, (form, err)
+        if form == "fp32":
+            assert err <= 1e-4, err
