@@ -320,14 +320,10 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
     def l2(a, b):
         return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
 
-    # FP64: lbm_step(100) runs the 100 steps of this 99-node lattice in one
-    # thread-block-cluster launch; FP32: a CUDA graph of 100 single-step launches.
+    # lbm_step(100) runs the 100 steps of this 99-node lattice in one
+    # thread-block-cluster launch (FP64 and FP32 storage alike).
     def stepper(L, st):
-        if st == "fp64":
-            return (lambda n: L.step(n)), None, "one cluster launch of 100 steps (lbm_step) between checks"
-        G = lbm.Batch([L])
-        G.set_graph(100)
-        return (lambda n: G.step(n)), G, "CUDA graph of 100 single-step launches between checks"
+        return (lambda n: L.step(n)), None, "one cluster launch of 100 steps (lbm_step) between checks"
 
     L = lbm.from_workload(w, stream=stream.cuda_stream, storage=lbm.FP64)
     step, G, how = stepper(L, "fp64")

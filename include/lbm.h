@@ -182,8 +182,8 @@ int lbm_set_envelope_table(lbm_ctx *ctx, const double *a, long count, double t0)
  * halfway bounce-back), moments (Eq. 24 / 42), pre-collision half force or
  * source (Eq. 25 / 43), cascaded collision (Eq. 23 / 41 / generic D3Q27),
  * post-collision half step (Eq. 31 / 47) and the post-collision populations
- * (Eq. 32 / 48).  Exception: a small FP64 D2Q9 lattice (up to ~5000 nodes)
- * with a constant force envelope takes all n >= 2 steps in ONE launch of a
+ * (Eq. 32 / 48).  Exception: a small D2Q9 lattice (up to ~5000 nodes, any
+ * storage) with a constant force envelope takes all n >= 2 steps in ONE launch of a
  * thread-block cluster that holds the state in its distributed shared memory
  * (same per-node arithmetic, one cluster barrier per step; counted as one
  * launch).  Asynchronous on the context's stream.

@@ -6,6 +6,8 @@
 // arithmetic is the same method as the FP64 kernels (Eqs. 23/25/31/32 for
 // D2Q9, Eqs. 41-48 for D2Q5, the generic central-moment procedure for D3Q27),
 // rearranged around the rest state.
+#include <cooperative_groups.h>
+
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
 #include "lbm_tiles.cuh"
@@ -91,6 +93,111 @@ k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, flo
     collide9(d, rref, Fx, Fy, Gx, Gy, w);
 #pragma unroll
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+// Many steps per launch for a small D2Q9 lattice (the FP32 / 16-bit form of
+// the FP64 cluster kernel): the stored deviations of block b's nodes live in
+// its shared memory (as the storage type, so every step rounds exactly as a
+// single-step launch does); pulls from other blocks read their shared memory
+// through the cluster; one cluster barrier per step.
+namespace cg = cooperative_groups;
+constexpr int kClusterThreads = 384;
+
+template <class T, int FK>
+__global__ void __launch_bounds__(kClusterThreads)
+k_cluster9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, float apre, float gsum, Rates9f w,
+           float rref, int P, int nsteps)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);  // [2][9][P]
+    cg::cluster_group cl = cg::this_cluster();
+    const int b = (int)cl.block_rank();
+    const int l = threadIdx.x;
+    const int i = b * P + l;
+    const bool own = l < P && i < g.N;
+    if (own)
+#pragma unroll
+        for (int a = 0; a < 9; a++) sm[a * P + l] = fin[a * g.Np + i];
+    const int x = own ? i % g.nx : 0, y = own ? i / g.nx : 0;
+    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
+    if (FK != FK_NONE && own) {
+        const float Px = field_value_f(F, FK, 0, x, y, 0, i), Py = field_value_f(F, FK, 1, x, y, 0, i);
+        Fx = apre * Px;
+        Fy = apre * Py;
+        Gx = gsum * Px;
+        Gy = gsum * Py;
+    }
+    int src_blk[9], src_off[9];
+    if (own) {
+#pragma unroll
+        for (int a = 0; a < 9; a++) {
+            bool opp = false;
+            const int j = pull_off(g, x, y, 0, LD2Q9::ex(a), LD2Q9::ey(a), 0, opp);
+            const int aa = opp ? LD2Q9::opp(a) : a;
+            src_blk[a] = j / P;
+            src_off[a] = aa * P + (j - (j / P) * P);
+        }
+    }
+    cl.sync();
+    int cur = 0;
+    for (int k = 0; k < nsteps; k++) {
+        if (own) {
+            float d[9];
+#pragma unroll
+            for (int a = 0; a < 9; a++) {
+                const T *base = cl.map_shared_rank(sm + cur * 9 * P, src_blk[a]);
+                d[a] = (float)base[src_off[a]];
+            }
+            collide9(d, rref, Fx, Fy, Gx, Gy, w);
+            T *nxt = sm + (cur ^ 1) * 9 * P;
+#pragma unroll
+            for (int a = 0; a < 9; a++) nxt[a * P + l] = Dev<T>::to_store(d[a]);
+        }
+        cur ^= 1;
+        cl.sync();
+    }
+    if (own)
+#pragma unroll
+        for (int a = 0; a < 9; a++) fout[a * g.Np + i] = sm[cur * 9 * P + a * P + l];
+}
+
+template <class T>
+cudaError_t cluster9_t(const LaunchArgs &a, int nsteps)
+{
+    const int C = a.g.N >= 16 * 8 ? 16 : (a.g.N + 7) / 8;
+    const int P = (a.g.N + C - 1) / C;
+    const int threads = (P + 31) / 32 * 32;
+    const size_t smem = (size_t)2 * 9 * P * sizeof(T);
+    if (threads > kClusterThreads || smem > 48 * 1024) return cudaErrorNotSupported;
+    const Rates9f w{(float)(a.omega[3] / 12.0), (float)(a.omega[4] / 4.0), (float)(a.omega[5] / 4.0),
+                    (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
+    const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre, rref = (float)a.rho_ref;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const T *fin = reinterpret_cast<const T *>(a.fin);
+    T *fout = reinterpret_cast<T *>(a.fout);
+    switch (a.fkind) {
+    case FK_NONE:
+        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_NONE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_NONE>, fin, fout, a.g, a.F, apre, gsum, w, rref, P, nsteps);
+    case FK_CONST:
+        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_CONST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_CONST>, fin, fout, a.g, a.F, apre, gsum, w, rref, P, nsteps);
+    default:
+        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_GENERAL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_GENERAL>, fin, fout, a.g, a.F, apre, gsum, w, rref, P,
+                                  nsteps);
+    }
 }
 
 // ------------------------------------------------------------------ D2Q5 ---
@@ -656,6 +763,16 @@ cudaError_t rp_step(int lattice, const LaunchArgs &a)
     case 1: return step_t<float>(lattice, a);
     case 2: return step_t<__half>(lattice, a);
     case 3: return step_t<__nv_bfloat16>(lattice, a);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t rp_cluster_steps9(const LaunchArgs &a, int nsteps)
+{
+    switch (a.storage) {
+    case 1: return cluster9_t<float>(a, nsteps);
+    case 2: return cluster9_t<__half>(a, nsteps);
+    case 3: return cluster9_t<__nv_bfloat16>(a, nsteps);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -429,12 +429,11 @@ int lbm_step(lbm_ctx *c, long n)
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step: populations not initialised");
     if (!envelope_covers(c, c->t, n))
         return fail(c, LBM_EINVAL, "lbm_step: steps %ld..%ld are outside the envelope table", c->t, c->t + n);
-    if (n >= 2 && n <= 2147483647L && c->storage == LBM_FP64 && c->lattice == LBM_D2Q9 && !c->env &&
-        c->env_tab.empty()) {
+    if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty()) {
         // a small lattice with a constant force: all n steps in one cluster launch
         double *out = (n & 1) ? c->B : c->A;
         LaunchArgs a = launch_args(c, c->A, out, 1.0, 1.0);
-        cudaError_t e = d2q9_cluster_steps(a, (int)n);
+        cudaError_t e = c->storage == LBM_FP64 ? d2q9_cluster_steps(a, (int)n) : rp_cluster_steps9(a, (int)n);
         if (e == cudaSuccess) {
             c->launches++;
             if (n & 1) {

@@ -130,6 +130,8 @@ cudaError_t d3q15_step(const LaunchArgs &a);
 // cudaErrorNotSupported when the lattice is too large.  fin -> fout after
 // nsteps steps (fout may equal fin).
 cudaError_t d2q9_cluster_steps(const LaunchArgs &a, int nsteps);
+// The same for reduced-precision storage (deviations kept in the storage type).
+cudaError_t rp_cluster_steps9(const LaunchArgs &a, int nsteps);
 cudaError_t d3q27_step(const LaunchArgs &a);
 
 // Moments of the current state: rho[N] and u[dim][N] (flow) or phi[N] (scalar);

@@ -175,3 +175,22 @@ def test_config3_kolmogorov_256_1000_steps_error_per_form():
         assert np.isfinite(err) and err < 1.0, (form, err)
         if form == "fp32":
             assert err <= 1e-4, err
+
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16"])
+def test_small_d2q9_cluster_steps_reduced_precision(form):
+    """The cluster form of a small reduced-precision D2Q9 lattice rounds to the
+    storage type every step, as single-step launches do."""
+    for ny, nx in ((33, 3), (40, 17)):
+        w = W.poiseuille(ny=ny, nx=nx, tau=0.7, Fx=1e-5)
+        a = lbm.from_workload(w, storage=STORAGES[form])
+        b = lbm.from_workload(w, storage=STORAGES[form])
+        n0 = a.launch_count()
+        a.step(40)
+        assert a.launch_count() == n0 + 1
+        for _ in range(40):
+            b.step(1)
+        fa, fb = a.get_populations(), b.get_populations()
+        tol = 1e-6 if form == "fp32" else 4 * EPS["fp16"]
+        assert np.abs(fa - fb).max() <= tol * np.abs(fb).max(), np.abs(fa - fb).max()
