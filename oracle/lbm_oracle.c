@@ -764,3 +764,257 @@ int orc_strain_rate(const orc_params *p, const double *f, const double *P, doubl
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Context API (lbmref_*): the oracle behind the same calls as the library   */
+/* ------------------------------------------------------------------------ */
+
+struct lbmref_ctx {
+    orc_params p;
+    long N;
+    int q, dim;
+    double *f, *work;  /* f(t), [q][N]; scratch */
+    double *P;         /* force shape [dim][N] or source shape [N]; NULL = none */
+    double *uadv;      /* D2Q5 advecting velocity [2][N] (zero by default) */
+    double *uprev;     /* velocity (flow) or scalar (D2Q5) at the previous lbmref_reduce */
+    int have_prev, initialised;
+    lbmref_envelope_fn env;
+    void *user;
+    long step;
+};
+
+static double env_at(const lbmref_ctx *c, double t) { return c->env ? c->env(t, c->user) : 1.0; }
+
+int lbmref_create(lbmref_ctx **out, int lattice, int nx, int ny, int nz, const double omega[9],
+                  const int wall[3])
+{
+    if (!out) return LBMREF_EINVAL;
+    *out = NULL;
+    if (orc_q(lattice) == 0 || nx < 1 || ny < 1 || nz < 1 || !omega) return LBMREF_EINVAL;
+    if (orc_dim(lattice) == 2 && nz != 1) return LBMREF_EINVAL;
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; d++) {
+        const int w = wall ? wall[d] : 0;
+        if (w != 0 && w != 1) return LBMREF_EINVAL;
+        if (w && (n[d] < 2 || (orc_dim(lattice) == 2 && d == 2))) return LBMREF_EINVAL;
+    }
+    for (int k = 0; k < 9; k++)
+        if (!(omega[k] >= 0.0 && omega[k] < 2.0)) return LBMREF_EINVAL;
+    lbmref_ctx *c = (lbmref_ctx *)calloc(1, sizeof(lbmref_ctx));
+    if (!c) return LBMREF_ENOMEM;
+    c->p.lattice = lattice;
+    for (int d = 0; d < 3; d++) {
+        c->p.n[d] = n[d];
+        c->p.wall[d] = wall ? wall[d] : 0;
+    }
+    for (int k = 0; k < 9; k++) c->p.omega[k] = omega[k];
+    c->N = (long)nx * ny * nz;
+    c->q = orc_q(lattice);
+    c->dim = orc_dim(lattice);
+    c->f = (double *)calloc((size_t)c->q * c->N, sizeof(double));
+    c->work = (double *)calloc((size_t)c->q * c->N, sizeof(double));
+    c->uprev = (double *)calloc((size_t)3 * c->N, sizeof(double));
+    if (lattice == ORC_D2Q5) c->uadv = (double *)calloc((size_t)2 * c->N, sizeof(double));
+    if (!c->f || !c->work || !c->uprev || (lattice == ORC_D2Q5 && !c->uadv)) {
+        lbmref_destroy(c);
+        return LBMREF_ENOMEM;
+    }
+    *out = c;
+    return LBMREF_OK;
+}
+
+void lbmref_destroy(lbmref_ctx *c)
+{
+    if (!c) return;
+    free(c->f);
+    free(c->work);
+    free(c->P);
+    free(c->uadv);
+    free(c->uprev);
+    free(c);
+}
+
+int lbmref_init_equilibrium(lbmref_ctx *c, double rho0, const double u0[3], const double *rho, const double *u)
+{
+    if (!c || (c->p.lattice != ORC_D2Q5 && !rho && !(rho0 > 0.0))) return LBMREF_EINVAL;
+    const long N = c->N;
+    double *r = (double *)malloc((size_t)N * sizeof(double));
+    double *v = (double *)malloc((size_t)3 * N * sizeof(double));
+    if (!r || !v) {
+        free(r);
+        free(v);
+        return LBMREF_ENOMEM;
+    }
+    for (long i = 0; i < N; i++) r[i] = rho ? rho[i] : rho0;
+    for (int d = 0; d < c->dim; d++)
+        for (long i = 0; i < N; i++) v[d * N + i] = u ? u[d * N + i] : (u0 ? u0[d] : 0.0);
+    const int rc = orc_equilibrium(&c->p, r, v, c->f);
+    free(r);
+    free(v);
+    if (rc) return LBMREF_EINVAL;
+    c->step = 0;
+    c->have_prev = 0;
+    c->initialised = 1;
+    return LBMREF_OK;
+}
+
+static int set_shape(lbmref_ctx *c, const double *S, int ncomp)
+{
+    if (!S) {
+        free(c->P);
+        c->P = NULL;
+        return LBMREF_OK;
+    }
+    double *P = (double *)malloc((size_t)ncomp * c->N * sizeof(double));
+    if (!P) return LBMREF_ENOMEM;
+    memcpy(P, S, (size_t)ncomp * c->N * sizeof(double));
+    free(c->P);
+    c->P = P;
+    return LBMREF_OK;
+}
+
+int lbmref_set_force(lbmref_ctx *c, const double *P)
+{
+    if (!c || c->p.lattice == ORC_D2Q5) return LBMREF_EINVAL;
+    return set_shape(c, P, c->dim);
+}
+
+int lbmref_set_source(lbmref_ctx *c, const double *S)
+{
+    if (!c || c->p.lattice != ORC_D2Q5) return LBMREF_EINVAL;
+    return set_shape(c, S, 1);
+}
+
+int lbmref_set_velocity(lbmref_ctx *c, const double *u)
+{
+    if (!c || c->p.lattice != ORC_D2Q5) return LBMREF_EINVAL;
+    if (u) memcpy(c->uadv, u, (size_t)2 * c->N * sizeof(double));
+    else memset(c->uadv, 0, (size_t)2 * c->N * sizeof(double));
+    return LBMREF_OK;
+}
+
+int lbmref_set_envelope(lbmref_ctx *c, lbmref_envelope_fn fn, void *user)
+{
+    if (!c) return LBMREF_EINVAL;
+    c->env = fn;
+    c->user = user;
+    return LBMREF_OK;
+}
+
+/* Trapezoid averages of the envelope over the two half steps (Sec. 6.3):
+ * a_pre = (a(t) + a(t+1/2))/2, a_post = (a(t+1/2) + a(t+1))/2. */
+int lbmref_step(lbmref_ctx *c, long n)
+{
+    if (!c || n < 0) return LBMREF_EINVAL;
+    if (!c->initialised) return LBMREF_ESTATE;
+    if (n == 0) return LBMREF_OK;
+    double *a = (double *)malloc((size_t)2 * n * sizeof(double));
+    if (!a) return LBMREF_ENOMEM;
+    for (long k = 0; k < n; k++) {
+        const double t = (double)(c->step + k);
+        const double a0 = env_at(c, t), ah = env_at(c, t + 0.5), a1 = env_at(c, t + 1.0);
+        a[2 * k] = 0.5 * (a0 + ah);
+        a[2 * k + 1] = 0.5 * (ah + a1);
+    }
+    const int rc = orc_run(&c->p, c->f, c->work, n, c->P, a, c->uadv);
+    free(a);
+    if (rc) return LBMREF_EINVAL;
+    c->step += n;
+    return LBMREF_OK;
+}
+
+static double a_pre_now(const lbmref_ctx *c)
+{
+    const double t = (double)c->step;
+    return 0.5 * (env_at(c, t) + env_at(c, t + 0.5));
+}
+
+int lbmref_moments(lbmref_ctx *c, double *rho, double *u, int half_forced)
+{
+    if (!c || !rho || (c->p.lattice != ORC_D2Q5 && !u)) return LBMREF_EINVAL;
+    if (!c->initialised) return LBMREF_ESTATE;
+    double *uu = u;
+    if (!uu) {
+        uu = (double *)malloc((size_t)c->dim * c->N * sizeof(double));
+        if (!uu) return LBMREF_ENOMEM;
+    }
+    const int rc = orc_moments(&c->p, c->f, half_forced ? c->P : NULL, a_pre_now(c), rho, uu);
+    if (uu != u) free(uu);
+    return rc ? LBMREF_EINVAL : LBMREF_OK;
+}
+
+int lbmref_reduce(lbmref_ctx *c, double out[5])
+{
+    if (!c || !out) return LBMREF_EINVAL;
+    if (!c->initialised) return LBMREF_ESTATE;
+    const long N = c->N;
+    const int flow = c->p.lattice != ORC_D2Q5;
+    double *rho = (double *)malloc((size_t)N * sizeof(double));
+    double *u = (double *)malloc((size_t)c->dim * N * sizeof(double));
+    if (!rho || !u) {
+        free(rho);
+        free(u);
+        return LBMREF_ENOMEM;
+    }
+    orc_moments(&c->p, c->f, c->P, a_pre_now(c), rho, u);
+    int ev[MAXQ * 3];
+    orc_velocities(c->p.lattice, ev);
+    double mass = 0.0, mom[3] = {0.0, 0.0, 0.0}, du = 0.0;
+    int unstable = 0;
+    for (long i = 0; i < N; i++) {
+        /* mass sum f (phi^o for the scalar) and momentum sum f e (flow), Eq. 24 / 42 */
+        double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < c->q; a++) {
+            r += c->f[a * N + i];
+            if (flow)
+                for (int d = 0; d < c->dim; d++) j[d] += c->f[a * N + i] * ev[3 * a + d];
+        }
+        mass += r;
+        for (int d = 0; d < 3; d++) mom[d] += j[d];
+        if (!isfinite(rho[i]) || (flow && !(rho[i] > 0.0))) unstable = 1;
+        if (flow) {
+            for (int d = 0; d < c->dim; d++) {
+                const double v = u[d * N + i];
+                if (c->have_prev) du = fmax(du, fabs(v - c->uprev[d * N + i]));
+                c->uprev[d * N + i] = v;
+            }
+        } else {
+            if (c->have_prev) du = fmax(du, fabs(rho[i] - c->uprev[i]));
+            c->uprev[i] = rho[i];
+        }
+    }
+    free(rho);
+    free(u);
+    out[0] = mass;
+    out[1] = mom[0];
+    out[2] = mom[1];
+    out[3] = mom[2];
+    out[4] = c->have_prev ? du : INFINITY;
+    c->have_prev = 1;
+    return unstable ? LBMREF_EUNSTABLE : LBMREF_OK;
+}
+
+int lbmref_get_populations(const lbmref_ctx *c, double *dst, size_t count)
+{
+    if (!c || !dst || count != (size_t)c->q * (size_t)c->N) return LBMREF_EINVAL;
+    if (!c->initialised) return LBMREF_ESTATE;
+    memcpy(dst, c->f, count * sizeof(double));
+    return LBMREF_OK;
+}
+
+int lbmref_set_populations(lbmref_ctx *c, const double *src, size_t count, long step)
+{
+    if (!c || !src || count != (size_t)c->q * (size_t)c->N || step < 0) return LBMREF_EINVAL;
+    memcpy(c->f, src, count * sizeof(double));
+    c->step = step;
+    c->have_prev = 0;
+    c->initialised = 1;
+    return LBMREF_OK;
+}
+
+int lbmref_get_step(const lbmref_ctx *c, long *step)
+{
+    if (!c || !step) return LBMREF_EINVAL;
+    *step = c->step;
+    return LBMREF_OK;
+}

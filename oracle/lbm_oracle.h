@@ -20,6 +20,8 @@
 #ifndef LBM_ORACLE_H
 #define LBM_ORACLE_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -102,6 +104,45 @@ int orc_collide_node(const orc_params *p, const double *fin, const double *Fpre,
  * lattices D2Q9 and D3Q27 only). */
 int orc_collide_node_generic(const orc_params *p, const double *fin, const double *Fpre,
                              const double *Fpost, double *fout);
+
+/* ---- Context API -----------------------------------------------------------
+ * The oracle behind the same calls as the library's C ABI (lbm_* there,
+ * lbmref_* here), with host pointers only: a context owns f(t) and steps it
+ * with orc_run.  Status codes mirror the library's; fields are full node
+ * arrays (expand a separable shape first).  Relaxation rates as in
+ * orc_params.omega; wall[d] = 1 puts halfway bounce-back walls on axis d. */
+#define LBMREF_OK 0
+#define LBMREF_EINVAL -1
+#define LBMREF_ENOMEM -2
+#define LBMREF_EUNSTABLE -4
+#define LBMREF_ESTATE -6
+
+typedef struct lbmref_ctx lbmref_ctx;
+typedef double (*lbmref_envelope_fn)(double t, void *user);
+
+int lbmref_create(lbmref_ctx **out, int lattice, int nx, int ny, int nz, const double omega[9],
+                  const int wall[3]);
+void lbmref_destroy(lbmref_ctx *c);
+/* f = equilibrium at (rho, u): host rho [N] (NULL = rho0), u [dim][N] (NULL = u0);
+ * step counter to 0. */
+int lbmref_init_equilibrium(lbmref_ctx *c, double rho0, const double u0[3], const double *rho, const double *u);
+/* Force shape [dim][N] (flow) / source shape [N] (D2Q5) / advecting velocity
+ * [2][N] (D2Q5); copied; NULL removes it (zero velocity). */
+int lbmref_set_force(lbmref_ctx *c, const double *P);
+int lbmref_set_source(lbmref_ctx *c, const double *S);
+int lbmref_set_velocity(lbmref_ctx *c, const double *u);
+/* Envelope a(t) (NULL = 1); each step uses the trapezoid averages of Sec. 6.3. */
+int lbmref_set_envelope(lbmref_ctx *c, lbmref_envelope_fn fn, void *user);
+int lbmref_step(lbmref_ctx *c, long n);
+/* rho [N] (phi for D2Q5) and u [dim][N] of f(t); half_forced as in orc_moments. */
+int lbmref_moments(lbmref_ctx *c, double *rho, double *u, int half_forced);
+/* out[0] = sum rho (sum phi^o), out[1..3] = sum of sum f e (flow), out[4] = max
+ * |u - u_prev| (|phi - phi_prev|) since the previous call, +inf on the first;
+ * LBMREF_EUNSTABLE if a density is non-finite or (flow) not positive. */
+int lbmref_reduce(lbmref_ctx *c, double out[5]);
+int lbmref_get_populations(const lbmref_ctx *c, double *dst, size_t count);
+int lbmref_set_populations(lbmref_ctx *c, const double *src, size_t count, long step);
+int lbmref_get_step(const lbmref_ctx *c, long *step);
 
 #ifdef __cplusplus
 }

@@ -62,6 +62,9 @@ class _Params(ctypes.Structure):
 
 
 _lib = None
+ENVELOPE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_double, ctypes.c_void_p)
+# status codes of the lbmref_* context API
+REF_OK, REF_EINVAL, REF_ENOMEM, REF_EUNSTABLE, REF_ESTATE = 0, -1, -2, -4, -6
 
 
 def lib():
@@ -80,6 +83,26 @@ def lib():
         L.orc_strain_rate.argtypes = [pp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         for fn in ("orc_run", "orc_moments", "orc_equilibrium", "orc_collide_node",
                    "orc_collide_node_generic", "orc_velocities", "orc_strain_rate"):
+            getattr(L, fn).restype = ctypes.c_int
+        vp = ctypes.c_void_p
+        L.lbmref_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    dp, ctypes.POINTER(ctypes.c_int)]
+        L.lbmref_destroy.argtypes = [vp]
+        L.lbmref_destroy.restype = None
+        L.lbmref_init_equilibrium.argtypes = [vp, ctypes.c_double, dp, dp, dp]
+        L.lbmref_set_force.argtypes = [vp, dp]
+        L.lbmref_set_source.argtypes = [vp, dp]
+        L.lbmref_set_velocity.argtypes = [vp, dp]
+        L.lbmref_set_envelope.argtypes = [vp, ENVELOPE_FN, vp]
+        L.lbmref_step.argtypes = [vp, ctypes.c_long]
+        L.lbmref_moments.argtypes = [vp, dp, dp, ctypes.c_int]
+        L.lbmref_reduce.argtypes = [vp, dp]
+        L.lbmref_get_populations.argtypes = [vp, dp, ctypes.c_size_t]
+        L.lbmref_set_populations.argtypes = [vp, dp, ctypes.c_size_t, ctypes.c_long]
+        L.lbmref_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
+        for fn in ("lbmref_create", "lbmref_init_equilibrium", "lbmref_set_force", "lbmref_set_source",
+                   "lbmref_set_velocity", "lbmref_set_envelope", "lbmref_step", "lbmref_moments",
+                   "lbmref_reduce", "lbmref_get_populations", "lbmref_set_populations", "lbmref_get_step"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -237,3 +260,79 @@ class OracleLattice:
                                         _dp(Fpost), _dp(ua), _dp(out))
         assert rc == 0
         return out
+
+
+class OracleContext:
+    """The oracle behind the library's call shape (``lbmref_*`` in
+    ``lbm_oracle.c``): create / init_equilibrium / set_force / set_source /
+    set_velocity / set_envelope / step / moments / reduce / populations.
+    Methods return the C status code; arrays are host numpy arrays."""
+
+    def __init__(self, lattice, shape, omega=(1.0,) * 9, wall=(0, 0, 0)):
+        self.lattice = lattice
+        self.shape = tuple(int(v) for v in shape)
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        self.q, self.dim = Q.get(lattice, 0), DIM.get(lattice, 0)
+        self._h = ctypes.c_void_p()
+        om = np.ascontiguousarray(np.asarray(omega, np.float64))
+        w = (ctypes.c_int * 3)(*[int(v) for v in wall])
+        self.status = lib().lbmref_create(ctypes.byref(self._h), lattice, *self.shape, _dp(om), w)
+        self._keep = None
+
+    def close(self):
+        if self._h:
+            lib().lbmref_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_equilibrium(self, rho0=1.0, u0=(0.0, 0.0, 0.0), rho=None, u=None):
+        u0a = np.ascontiguousarray(np.asarray(u0, np.float64))
+        r = None if rho is None else np.ascontiguousarray(rho, np.float64)
+        v = None if u is None else np.ascontiguousarray(u, np.float64)
+        return lib().lbmref_init_equilibrium(self._h, float(rho0), _dp(u0a), _dp(r), _dp(v))
+
+    def set_force(self, P):
+        return lib().lbmref_set_force(self._h, _dp(None if P is None else np.ascontiguousarray(P, np.float64)))
+
+    def set_source(self, S):
+        return lib().lbmref_set_source(self._h, _dp(None if S is None else np.ascontiguousarray(S, np.float64)))
+
+    def set_velocity(self, u):
+        return lib().lbmref_set_velocity(self._h, _dp(None if u is None else np.ascontiguousarray(u, np.float64)))
+
+    def set_envelope(self, fn):
+        self._keep = None if fn is None else ENVELOPE_FN(lambda t, _u: float(fn(t)))
+        return lib().lbmref_set_envelope(self._h, self._keep if fn is not None else ENVELOPE_FN(), None)
+
+    def step(self, n):
+        return lib().lbmref_step(self._h, int(n))
+
+    def moments(self, half_forced=True):
+        rho = np.empty(self.N)
+        u = np.empty((self.dim, self.N))
+        rc = lib().lbmref_moments(self._h, _dp(rho), _dp(u), int(half_forced))
+        return rc, rho, u
+
+    def reduce(self):
+        out = np.empty(5)
+        rc = lib().lbmref_reduce(self._h, _dp(out))
+        return rc, out
+
+    def populations(self):
+        f = np.empty((self.q, self.N))
+        rc = lib().lbmref_get_populations(self._h, _dp(f), f.size)
+        return rc, f
+
+    def set_populations(self, f, step):
+        f = np.ascontiguousarray(f, np.float64)
+        return lib().lbmref_set_populations(self._h, _dp(f), f.size, int(step))
+
+    def get_step(self):
+        s = ctypes.c_long()
+        rc = lib().lbmref_get_step(self._h, ctypes.byref(s))
+        return rc, s.value
