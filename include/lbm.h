@@ -365,14 +365,19 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
  * asynchronous: the kernel runs on the batch's stream into one of two
  * staging slots and the copies run on a private copy stream, so that they
  * overlap the steps queued after this call; the host buffers are valid after
- * lbm_batch_wait_moments.  Errors: LBM_EINVAL (NULL output), LBM_ESTATE,
- * LBM_ENOMEM, LBM_ECUDA. */
+ * lbm_batch_wait_moments.  where = 3: host pointers into memory the device
+ * can address (pinned by cudaHostAlloc / cudaMallocHost, or registered with
+ * cudaHostRegisterMapped): the kernel writes the fields straight into host
+ * memory (over NVLink-C2C on a Grace system), with no staging copy;
+ * asynchronous, valid after lbm_batch_wait_moments.  Errors: LBM_EINVAL (NULL
+ * output; for where = 3 also a pointer the device cannot address, e.g.
+ * pageable memory), LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced);
 
-/* Wait for the asynchronous readbacks (where = 2): keep = 0 waits for all of
- * them, keep = 1 for all but the most recent one (double buffering: the
- * previous step's fields are in host memory while the latest copy is still
- * in flight).  Errors: LBM_EINVAL, LBM_ECUDA. */
+/* Wait for the asynchronous readbacks (where = 2 or 3): keep = 0 waits for all
+ * of them, keep = 1 for all but the most recent one (double buffering: the
+ * previous step's fields are in host memory while the latest one is still
+ * on its way).  Errors: LBM_EINVAL, LBM_ECUDA. */
 int lbm_batch_wait_moments(lbm_batch *b, int keep);
 
 /* Graph replays issued so far. */

@@ -701,10 +701,13 @@ cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile,
 }
 
 bool d3q27_high_rates_one(const double omega[9]);
+bool d2q9_high_rates_one(const double omega[9]);
 
 int batch_variant(int lattice, const double omega[9])
 {
-    return (lattice == LD3Q27::ID && d3q27_high_rates_one(omega)) ? 1 : 0;
+    if (lattice == LD3Q27::ID) return d3q27_high_rates_one(omega) ? 1 : 0;
+    if (lattice == LD2Q9::ID) return d2q9_high_rates_one(omega) ? 1 : 0;
+    return 0;
 }
 
 int batch_resident(int lattice, int tile)

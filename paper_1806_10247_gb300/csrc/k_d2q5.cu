@@ -135,31 +135,32 @@ __device__ __forceinline__ void collide_mat(double (&g)[5], double P, double aha
 
 template <int SK>
 __global__ void __launch_bounds__(kBlock)
-k_step_mat(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, double ahalf,
-           double hsum, Mat5 M)
+k_step_mat(const __grid_constant__ Planes<double, 5> P, Geom g, FieldDev S, double ahalf, double hsum, Mat5 M)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     double f[5];
-    load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
+    load_pulled<LD2Q5>(P, g, x, y, 0, i, f);
     if (SK != FK_NONE) collide_mat<true>(f, field_value(S, SK, 0, x, y, 0, i), ahalf, hsum, M.m);
     else collide_mat<false>(f, 0.0, ahalf, hsum, M.m);
 #pragma unroll
-    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
+    for (int a = 0; a < 5; a++) P.out[a][i] = f[a];
 }
 
 
 template <int SK, int VK>
 __global__ void __launch_bounds__(kBlock)
-k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev S, FieldDev V,
-       double apre, double hsum, Rates5 w)
+k_step(const __grid_constant__ Planes<double, 5> P, Geom g, FieldDev S, FieldDev V, double apre, double hsum,
+       Rates5 w)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     double f[5];
-    load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
+    load_pulled<LD2Q5>(P, g, x, y, 0, i, f);
     double Spre = 0.0, H0 = 0.0;
     if (SK != FK_NONE) {
         const double P = field_value(S, SK, 0, x, y, 0, i);
@@ -173,7 +174,7 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     }
     collide(f, Spre, H0, ux, uy, w);
 #pragma unroll
-    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = f[a];
+    for (int a = 0; a < 5; a++) P.out[a][i] = f[a];
 }
 
 template <int SK>
@@ -182,11 +183,12 @@ void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
     if (a.vkind != FK_GENERAL) {
         const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0;
         const double uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
-        k_step_mat<SK><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, 0.5 * a.apre, hsum,
-                                                       make_mat(make_coef(w, ux, uy)));
+        k_step_mat<SK><<<grid, kBlock, 0, a.stream>>>(make_planes<double, 5>(a.fin, a.fout, a.g.Np), a.g, a.F,
+                                                       0.5 * a.apre, hsum, make_mat(make_coef(w, ux, uy)));
         return;
     }
-    k_step<SK, FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.V, a.apre, hsum, w);
+    k_step<SK, FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(make_planes<double, 5>(a.fin, a.fout, a.g.Np), a.g, a.F,
+                                                          a.V, a.apre, hsum, w);
 }
 
 // Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
@@ -200,7 +202,8 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
     const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
     if (B.vkind != FK_GENERAL) {

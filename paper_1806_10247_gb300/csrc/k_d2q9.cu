@@ -68,16 +68,83 @@ __device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, do
     f[8] += c + (Gx - Gy) + (-g5 + g6 - g7);
 }
 
-template <int FK>
+// The same step when omega_6 = omega_7 = omega_8 = 1 (the paper's choice for
+// the higher moments, Sec. 6).  Eq. 23 is the relaxation of the central
+// moments (trace towards 2 rho / 3 with omega_3, xx - yy and xy towards 0
+// with omega_4, omega_5, each higher one towards its equilibrium value with
+// its own rate); at unit rates the third- and fourth-order central moments
+// land on 0 and rho / 9, so the post-collision populations follow from rho,
+// u and the three relaxed second-order central moments.  They are built by
+// the factorised back-shift and inverse transform on HALVED moments (each
+// axis on which a moment has order 1 or 2 contributes a factor 1/2, so that
+// the inverse 1D transform of (m0, m1/2, m2/2) is m2/2 - m1/2, m0 - m2,
+// m2/2 + m1/2), with the post-collision force K_1 g_1, K_2 g_2 of Eq. 31
+// added to the raw moments: e_x changes m_10 by 6 g_1 (of which F_pre / 2 is
+// already in j) and m_12 by 4 g_1.  The first raw moments are carried as j
+// itself (not rebuilt as rho (j / rho)), so the step transports momentum
+// without a rounding of its own.  About 80 FP64 operations instead of 132.
+__device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy, double Gx, double Gy,
+                                           const Rates9 &w)
+{
+    // raw moments of order <= 2 per axis (Eq. 21)
+    const double s0 = f[1] + f[3], d0 = f[1] - f[3];  // row ey = 0
+    const double s1 = f[5] + f[6], d1 = f[5] - f[6];  // row ey = +1
+    const double s2 = f[8] + f[7], d2 = f[8] - f[7];  // row ey = -1
+    const double B0 = f[2] + s1, C0 = f[4] + s2;
+    const double rho = (f[0] + s0) + (B0 + C0);
+    const double jx = fma(0.5, Fx, d0 + (d1 + d2)), jy = fma(0.5, Fy, B0 - C0);  // Eq. 25
+    const double mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;
+    const double rinv = __drcp_rn(rho);
+    const double ux = jx * rinv, uy = jy * rinv;
+
+    // second-order central moments, relaxed and halved (xx, yy by 1/2 ... of
+    // the trace and difference: k_xx = (T + D) / 2 halved is (T + D) / 4)
+    const double cxx = fma(-jx, ux, mxx), cyy = fma(-jy, uy, myy), cxy = fma(-jx, uy, mxy);
+    const double T = cxx + cyy, D = cxx - cyy;
+    const double Tq = fma(3.0 * w.c3, fma(2.0 / 3.0, rho, -T), 0.25 * T);  // (T + omega_3 (2 rho/3 - T)) / 4
+    const double Dq = (0.25 - w.c4) * D;                                      // (1 - omega_4) D / 4
+    const double kxx = Tq + Dq, kyy = Tq - Dq, kxy = (0.25 - w.c5) * cxy;    // kxy: (1 - omega_5) k_xy / 4
+    const double k22 = rho * (1.0 / 36.0);                                    // rho / 9, quartered
+
+    // back-shift along x of the lines of y-order 0, 1, 2: (rho, 0, kxx), (0, kxy, 0), (kyy, 0, k22)
+    const double hx = 0.5 * ux, hy = 0.5 * uy;
+    const double M10 = 0.5 * jx, M20 = fma(ux, M10, kxx);  // m_10 = rho u_x = j_x
+    const double M11 = kxy, M21 = (kxy + kxy) * ux;
+    const double M12 = hx * kyy, M22 = fma(ux, M12, k22);
+    // back-shift along y of the lines of x-order 0, 1, 2
+    double N00 = rho, N01 = 0.5 * jy, N02 = fma(uy, N01, kyy);  // m_01 = j_y
+    double N10 = M10, N11 = fma(hy, M10, M11), N12 = fma(uy, M11 + N11, M12);
+    double N20 = M20, N21 = fma(hy, M20, M21), N22 = fma(uy, M21 + N21, M22);
+    // post-collision force (Eq. 31), halved: m_10 gains F_post / 2 = 6 Gx - Fx / 2, m_12 gains 4 Gx
+    N10 = fma(3.0, Gx, fma(-0.25, Fx, N10));
+    N12 += Gx;
+    N01 = fma(3.0, Gy, fma(-0.25, Fy, N01));
+    N21 += Gy;
+    // inverse transform along y, then along x
+    const double P0m = N02 - N01, P00 = fma(-2.0, N02, N00), P0p = N02 + N01;  // x-order 0; e_y = -1, 0, +1
+    const double P1m = N12 - N11, P10 = fma(-2.0, N12, N10), P1p = N12 + N11;
+    const double P2m = N22 - N21, P20 = fma(-2.0, N22, N20), P2p = N22 + N21;
+    f[0] = fma(-2.0, P20, P00);
+    f[1] = P20 + P10;
+    f[3] = P20 - P10;
+    f[2] = fma(-2.0, P2p, P0p);
+    f[5] = P2p + P1p;
+    f[6] = P2p - P1p;
+    f[4] = fma(-2.0, P2m, P0m);
+    f[8] = P2m + P1m;
+    f[7] = P2m - P1m;
+}
+
+template <int FK, bool W1>
 __global__ void __launch_bounds__(kBlock)
-k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev F, double apre,
-       double gsum, Rates9 w)
+k_step(const __grid_constant__ Planes<double, 9> P, Geom g, FieldDev F, double apre, double gsum, Rates9 w)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     double f[9];
-    load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
+    load_pulled<LD2Q9>(P, g, x, y, 0, i, f);
     double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
     if (FK != FK_NONE) {
         const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
@@ -86,9 +153,10 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
         Gx = gsum * Px;
         Gy = gsum * Py;
     }
-    collide(f, Fx, Fy, Gx, Gy, w);
+    if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w);
+    else collide(f, Fx, Fy, Gx, Gy, w);
 #pragma unroll
-    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
+    for (int a = 0; a < 9; a++) P.out[a][i] = f[a];
 }
 
 // ------------------------------------------------------------------------
@@ -105,7 +173,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kClusterThreads = 384;  // >= 32-rounded 341, the largest block (48 KB of shared memory)
 
-template <int FK>
+template <int FK, bool W1>
 __global__ void __launch_bounds__(kClusterThreads)
 k_cluster_steps(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev F, double apre,
                 double gsum, Rates9 w, int P, int nsteps)
@@ -150,7 +218,8 @@ k_cluster_steps(const double *__restrict__ fin, double *__restrict__ fout, Geom 
                 const double *base = cl.map_shared_rank(sm + cur * 9 * P, src_blk[a]);
                 f[a] = base[src_off[a]];
             }
-            collide(f, Fx, Fy, Gx, Gy, w);
+            if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w);
+            else collide(f, Fx, Fy, Gx, Gy, w);
             double *nxt = sm + (cur ^ 1) * 9 * P;
 #pragma unroll
             for (int a = 0; a < 9; a++) nxt[a * P + l] = f[a];
@@ -173,7 +242,8 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     const double *fin = B.buf[p & 1];
     double *fout = B.buf[(p + 1) & 1];
     const double2 ap = L.pairs ? L.pairs[(size_t)L.k * L.count + it] : L.inl[it];
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     double f[9];
     load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
     double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
@@ -186,7 +256,8 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
         Gy = ap.y * Py;
     }
     const Rates9 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
-    collide(f, Fx, Fy, Gx, Gy, w);
+    if (B.variant == 1) collide_w1(f, Fx, Fy, Gx, Gy, w);  // uniform over the member
+    else collide(f, Fx, Fy, Gx, Gy, w);
 #pragma unroll
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
 }
@@ -198,7 +269,45 @@ k_batch(const __grid_constant__ BatchLaunch L)
     batch_tiles<TB, MODE>(L, [](const BatchItem &B, const BatchLaunch &L2, int it, int i) { batch_node(B, L2, it, i); });
 }
 
+template <bool W1>
+cudaError_t cluster_launch(cudaLaunchConfig_t &cfg, int C, const LaunchArgs &a, double gsum, const Rates9 &w, int P,
+                           int nsteps)
+{
+    switch (a.fkind) {
+    case FK_NONE:
+        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_NONE, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_NONE, W1>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P,
+                                  nsteps);
+    case FK_CONST:
+        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_CONST, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_CONST, W1>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P,
+                                  nsteps);
+    default:
+        if (C > 8)
+            cudaFuncSetAttribute(k_cluster_steps<FK_GENERAL, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_GENERAL, W1>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w,
+                                  P, nsteps);
+    }
+}
+
+template <bool W1>
+void step_launch(const LaunchArgs &a, int grid, double gsum, const Rates9 &w)
+{
+    const Planes<double, 9> P = make_planes<double, 9>(a.fin, a.fout, a.g.Np);
+    switch (a.fkind) {
+    case FK_NONE: k_step<FK_NONE, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
+    case FK_CONST: k_step<FK_CONST, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
+    default: k_step<FK_GENERAL, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
+    }
+}
+
 }  // namespace
+
+// omega_6 = omega_7 = omega_8 = 1: the step takes collide_w1.
+bool d2q9_high_rates_one(const double omega[9])
+{
+    return omega[6] == 1.0 && omega[7] == 1.0 && omega[8] == 1.0;
+}
 
 void d2q9_batch_coef(const double omega[9], BatchItem &item)
 {
@@ -243,23 +352,8 @@ cudaError_t d2q9_cluster_steps(const LaunchArgs &a, int nsteps)
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    switch (a.fkind) {
-    case FK_NONE:
-        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_NONE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_NONE>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P, nsteps);
-        break;
-    case FK_CONST:
-        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_CONST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_CONST>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P, nsteps);
-        break;
-    default:
-        if (C > 8) cudaFuncSetAttribute(k_cluster_steps<FK_GENERAL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        e = cudaLaunchKernelEx(&cfg, k_cluster_steps<FK_GENERAL>, a.fin, a.fout, a.g, a.F, a.apre, gsum, w, P,
-                               nsteps);
-        break;
-    }
-    return e;
+    return d2q9_high_rates_one(a.omega) ? cluster_launch<true>(cfg, C, a, gsum, w, P, nsteps)
+                                        : cluster_launch<false>(cfg, C, a, gsum, w, P, nsteps);
 }
 
 cudaError_t d2q9_step(const LaunchArgs &a)
@@ -268,11 +362,8 @@ cudaError_t d2q9_step(const LaunchArgs &a)
              a.omega[6] / 4.0, a.omega[7] / 4.0, a.omega[8] / 4.0};
     const double gsum = (a.apre + a.apost) / 12.0;
     const int grid = (a.g.N + kBlock - 1) / kBlock;
-    switch (a.fkind) {
-    case FK_NONE: k_step<FK_NONE><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
-    case FK_CONST: k_step<FK_CONST><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
-    default: k_step<FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, gsum, w); break;
-    }
+    if (d2q9_high_rates_one(a.omega)) step_launch<true>(a, grid, gsum, w);
+    else step_launch<false>(a, grid, gsum, w);
     return cudaGetLastError();
 }
 

@@ -117,15 +117,14 @@ __device__ __forceinline__ void collide(double (&f)[15], const double (&F)[3], c
 
 template <int FK>
 __global__ void __launch_bounds__(kBlock)
-k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev Fd, double apre,
-       double apost, Rates15 w)
+k_step(const __grid_constant__ Planes<double, 15> P, Geom g, FieldDev Fd, double apre, double apost, Rates15 w)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
     double f[15];
-    load_pulled<LD3Q15>(fin, g, x, y, z, i, f);
+    load_pulled<LD3Q15>(P, g, x, y, z, i, f);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (FK != FK_NONE) {
 #pragma unroll
@@ -137,7 +136,7 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     }
     collide(f, F, Fq, w);
 #pragma unroll
-    for (int a = 0; a < 15; a++) fout[a * g.Np + i] = f[a];
+    for (int a = 0; a < 15; a++) P.out[a][i] = f[a];
 }
 
 // Batched form; pairs hold (a_pre, a_post) per step and item.
@@ -199,10 +198,11 @@ cudaError_t d3q15_step(const LaunchArgs &a)
 {
     const Rates15 w{a.omega[2], a.omega[1], a.omega[3], a.omega[4]};
     const int grid = (a.g.N + kBlock - 1) / kBlock;
+    const Planes<double, 15> P = make_planes<double, 15>(a.fin, a.fout, a.g.Np);
     switch (a.fkind) {
-    case FK_NONE: k_step<FK_NONE><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
-    case FK_CONST: k_step<FK_CONST><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
-    default: k_step<FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w); break;
+    case FK_NONE: k_step<FK_NONE><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w); break;
+    case FK_CONST: k_step<FK_CONST><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w); break;
+    default: k_step<FK_GENERAL><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w); break;
     }
     return cudaGetLastError();
 }

@@ -38,15 +38,6 @@ __device__ __forceinline__ void raw_fwd(double &a, double &b, double &c)
     b = d;
     c = s;
 }
-// Raw moments of order 0, 1, 2 -> populations at -1, 0, +1.
-__device__ __forceinline__ void raw_bwd(double &m0, double &m1, double &m2)
-{
-    const double h = 0.5 * m2;
-    const double fm = fma(-0.5, m1, h), fp = fma(0.5, m1, h), f0 = m0 - m2;
-    m0 = fm;
-    m1 = f0;
-    m2 = fp;
-}
 // Raw moments -> central moments about u (binomial shift, one axis).
 __device__ __forceinline__ void shift_fwd(double m0, double &m1, double &m2, double u)
 {
@@ -54,10 +45,27 @@ __device__ __forceinline__ void shift_fwd(double m0, double &m1, double &m2, dou
     m2 = fma(-u, m1 + k1, m2);
     m1 = k1;
 }
-// Central moments about u -> raw moments (one axis).
-__device__ __forceinline__ void shift_bwd(double k0, double &k1, double &k2, double u)
+
+// The way back runs on HALVED moments: every axis on which a moment has order
+// 1 or 2 contributes a factor 1/2 (m~_abc = m_abc / 2^(#nonzero orders)).  The
+// inverse 1D transform of a halved triple (m0, m1/2, m2/2) is then
+// f_-1 = m2/2 - m1/2, f_0 = m0 - m2, f_+1 = m2/2 + m1/2: three operations per
+// line instead of four, and the factors cost nothing where they land on
+// constants (relaxation rates, equilibrium values, force coefficients).
+//
+// Halved raw moments of order 0, 1, 2 -> populations at -1, 0, +1.
+__device__ __forceinline__ void raw_bwd_h(double &m0, double &m1, double &m2)
 {
-    const double m1 = fma(u, k0, k1);
+    const double fm = m2 - m1, fp = m2 + m1, f0 = fma(-2.0, m2, m0);
+    m0 = fm;
+    m1 = f0;
+    m2 = fp;
+}
+// Halved central moments about u -> halved raw moments (one axis; uh = u / 2):
+// m1 = k1 + u k0 and m2 = k2 + 2 u k1 + u^2 k0 with the halves carried along.
+__device__ __forceinline__ void shift_bwd_h(double k0, double &k1, double &k2, double u, double uh)
+{
+    const double m1 = fma(uh, k0, k1);
     k2 = fma(u, k1 + m1, k2);
     k1 = m1;
 }
@@ -75,31 +83,33 @@ __device__ __forceinline__ void along(double (&m)[27], Op op)
     }
 }
 
-// Central moments about u (post-collision) -> populations: back-shift, the
-// post-collision force in moment space, inverse raw transform.
+// Halved post-collision central moments about u -> populations: back-shift,
+// the post-collision force in moment space, inverse raw transform.
 __device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, double uz, const double (&F)[3],
                                        const double (&Fq)[3])
 {
-    along<0>(m, [ux](double &a, double &b, double &c) { shift_bwd(a, b, c, ux); });
-    along<1>(m, [uy](double &a, double &b, double &c) { shift_bwd(a, b, c, uy); });
-    along<2>(m, [uz](double &a, double &b, double &c) { shift_bwd(a, b, c, uz); });
+    const double hx = 0.5 * ux, hy = 0.5 * uy, hz = 0.5 * uz;
+    along<0>(m, [ux, hx](double &a, double &b, double &c) { shift_bwd_h(a, b, c, ux, hx); });
+    along<1>(m, [uy, hy](double &a, double &b, double &c) { shift_bwd_h(a, b, c, uy, hy); });
+    along<2>(m, [uz, hz](double &a, double &b, double &c) { shift_bwd_h(a, b, c, uz, hz); });
 
-    // Undo the pre-collision moment shift and add K_1 g_1 in moment space:
-    // e_x changes m_100 by 18 g, m_120 and m_102 by 12 g, m_122 by 8 g.
+    // K_1 g_1 in moment space, g = (F_pre + F_post) / 36: e_x changes m_100 by
+    // 18 g, m_120 and m_102 by 12 g, m_122 by 8 g (halved: 9 g, 3 g, 3 g, g).
+    // m_100 = rho u already carries F_pre / 2 (the pre-collision shift), so
+    // only F_post / 2 is added to it.
     {
-        const double hx = 0.5 * (F[0] + Fq[0]), hy = 0.5 * (F[1] + Fq[1]), hz = 0.5 * (F[2] + Fq[2]);
-        m[1] = fma(0.5, Fq[0], m[1]);
-        m[3] = fma(0.5, Fq[1], m[3]);
-        m[9] = fma(0.5, Fq[2], m[9]);
-        const double ax = hx * (2.0 / 3.0), ay = hy * (2.0 / 3.0), az = hz * (2.0 / 3.0);
-        m[7] += ax; m[19] += ax; m[25] = fma(hx, 4.0 / 9.0, m[25]);
-        m[5] += ay; m[21] += ay; m[23] = fma(hy, 4.0 / 9.0, m[23]);
-        m[11] += az; m[15] += az; m[17] = fma(hz, 4.0 / 9.0, m[17]);
+        const double sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+        m[1] = fma(0.25, Fq[0], m[1]);
+        m[3] = fma(0.25, Fq[1], m[3]);
+        m[9] = fma(0.25, Fq[2], m[9]);
+        m[7] = fma(sx, 1.0 / 12.0, m[7]); m[19] = fma(sx, 1.0 / 12.0, m[19]); m[25] = fma(sx, 1.0 / 36.0, m[25]);
+        m[5] = fma(sy, 1.0 / 12.0, m[5]); m[21] = fma(sy, 1.0 / 12.0, m[21]); m[23] = fma(sy, 1.0 / 36.0, m[23]);
+        m[11] = fma(sz, 1.0 / 12.0, m[11]); m[15] = fma(sz, 1.0 / 12.0, m[15]); m[17] = fma(sz, 1.0 / 36.0, m[17]);
     }
 
-    along<2>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
-    along<1>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
-    along<0>(m, [](double &a, double &b, double &c) { raw_bwd(a, b, c); });
+    along<2>(m, [](double &a, double &b, double &c) { raw_bwd_h(a, b, c); });
+    along<1>(m, [](double &a, double &b, double &c) { raw_bwd_h(a, b, c); });
+    along<0>(m, [](double &a, double &b, double &c) { raw_bwd_h(a, b, c); });
 }
 
 // F: pre-collision force a_pre P; Fq: post-collision force a_post P.
@@ -122,32 +132,36 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
     along<1>(m, [uy](double &a, double &b, double &c) { shift_fwd(a, b, c, uy); });
     along<2>(m, [uz](double &a, double &b, double &c) { shift_fwd(a, b, c, uz); });
 
-    // Relaxation of the central moments.
+    // Relaxation of the central moments; the results are written halved.
     {
         const double T = m[2] + m[6] + m[18];
         const double D1 = m[2] - m[6], D2 = m[2] - m[18];
         const double Ts = fma(w.wb, rho - T, T);
         const double rs = 1.0 - w.ws;
-        const double D1s = rs * D1, D2s = rs * D2;
-        const double kxx = (Ts + D1s + D2s) * (1.0 / 3.0);
+        const double rh = 0.5 * rs, rq = 0.25 * rs;
+        const double D1h = rh * D1, D2h = rh * D2;  // halved relaxed deviatoric parts
+        const double kxx = fma(Ts, 1.0 / 6.0, (D1h + D2h) * (1.0 / 3.0));
         m[2] = kxx;
-        m[6] = kxx - D1s;
-        m[18] = kxx - D2s;
-        m[4] *= rs;   // 110
-        m[10] *= rs;  // 101
-        m[12] *= rs;  // 011
+        m[6] = kxx - D1h;
+        m[18] = kxx - D2h;
+        m[4] *= rq;   // 110
+        m[10] *= rq;  // 101
+        m[12] *= rq;  // 011
         m[1] = 0.0;   // first central moments vanish after the half force
         m[3] = 0.0;
         m[9] = 0.0;
         const double r3 = 1.0 - w.w3, r4 = 1.0 - w.w4, r5 = 1.0 - w.w5;
-        m[5] *= r3; m[7] *= r3; m[11] *= r3; m[15] *= r3; m[19] *= r3; m[21] *= r3; m[13] *= r3;
-        const double e4 = rho * (1.0 / 9.0);
-        m[8] = fma(w.w4, e4 - m[8], m[8]);
-        m[20] = fma(w.w4, e4 - m[20], m[20]);
-        m[24] = fma(w.w4, e4 - m[24], m[24]);
-        m[14] *= r4; m[16] *= r4; m[22] *= r4;
-        m[17] *= r5; m[23] *= r5; m[25] *= r5;
-        m[26] = fma(w.w6, rho * (1.0 / 27.0) - m[26], m[26]);
+        const double r3q = 0.25 * r3, r3e = 0.125 * r3;
+        m[5] *= r3q; m[7] *= r3q; m[11] *= r3q; m[15] *= r3q; m[19] *= r3q; m[21] *= r3q; m[13] *= r3e;
+        // m~_220 = (1 - w4) m_220 / 4 + w4 (rho / 9) / 4
+        const double r4q = 0.25 * r4, e4 = (w.w4 * (1.0 / 36.0)) * rho;
+        m[8] = fma(r4q, m[8], e4);
+        m[20] = fma(r4q, m[20], e4);
+        m[24] = fma(r4q, m[24], e4);
+        const double r4e = 0.125 * r4, r5e = 0.125 * r5;
+        m[14] *= r4e; m[16] *= r4e; m[22] *= r4e;
+        m[17] *= r5e; m[23] *= r5e; m[25] *= r5e;
+        m[26] = fma(0.125 * (1.0 - w.w6), m[26], (w.w6 * (1.0 / 216.0)) * rho);
     }
 
     finish(m, ux, uy, uz, F, Fq);
@@ -196,36 +210,37 @@ __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3]
     const double D1 = cxx - cyy, D2 = cxx - czz;
     const double Ts = fma(w.wb, rho - T, T);
     const double rs = 1.0 - w.ws;
-    const double D1s = rs * D1, D2s = rs * D2;
-    const double sxx = (Ts + D1s + D2s) * (1.0 / 3.0);
+    const double rh = 0.5 * rs, rq = 0.25 * rs;
+    const double D1h = rh * D1, D2h = rh * D2;
+    const double sxx = fma(Ts, 1.0 / 6.0, (D1h + D2h) * (1.0 / 3.0));
+    // halved post-collision central moments (orders 3..6 at their Maxwellian values)
 #pragma unroll
     for (int k = 0; k < 27; k++) m[k] = 0.0;
     m[0] = rho;
     m[2] = sxx;
-    m[6] = sxx - D1s;
-    m[18] = sxx - D2s;
-    m[4] = rs * fma(-jx, uy, kxy);
-    m[10] = rs * fma(-jx, uz, kxz);
-    m[12] = rs * fma(-jy, uz, kyz);
-    const double e4 = rho * (1.0 / 9.0);
+    m[6] = sxx - D1h;
+    m[18] = sxx - D2h;
+    m[4] = rq * fma(-jx, uy, kxy);
+    m[10] = rq * fma(-jx, uz, kxz);
+    m[12] = rq * fma(-jy, uz, kyz);
+    const double e4 = rho * (1.0 / 36.0);
     m[8] = e4;
     m[20] = e4;
     m[24] = e4;
-    m[26] = rho * (1.0 / 27.0);
+    m[26] = rho * (1.0 / 216.0);
     finish(m, ux, uy, uz, F, Fq);
 }
 
 template <int FK, bool W1>
 __global__ void __launch_bounds__(kBlock)
-k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldDev Fd, double apre,
-       double apost, Rates27 w)
+k_step(const __grid_constant__ Planes<double, 27> P, Geom g, FieldDev Fd, double apre, double apost, Rates27 w)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
     double m[27];
-    load_pulled<LD3Q27>(fin, g, x, y, z, i, m);
+    load_pulled<LD3Q27>(P, g, x, y, z, i, m);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (FK != FK_NONE) {
 #pragma unroll
@@ -238,7 +253,7 @@ k_step(const double *__restrict__ fin, double *__restrict__ fout, Geom g, FieldD
     if (W1) collide_w1(m, F, Fq, w);
     else collide(m, F, Fq, w);
 #pragma unroll
-    for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
+    for (int a = 0; a < 27; a++) P.out[a][i] = m[a];
 }
 
 // Batched form; pairs hold (a_pre, a_post) per step and item.
@@ -303,18 +318,19 @@ cudaError_t d3q27_step(const LaunchArgs &a)
     Rates27 w{a.omega[1], a.omega[2], a.omega[3], a.omega[4], a.omega[5], a.omega[6]};
     const int grid = (a.g.N + kBlock - 1) / kBlock;
     const bool w1 = high_rates_one(a.omega);
+    const Planes<double, 27> P = make_planes<double, 27>(a.fin, a.fout, a.g.Np);
     switch (a.fkind) {
     case FK_NONE:
-        if (w1) k_step<FK_NONE, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_NONE, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        if (w1) k_step<FK_NONE, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_NONE, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     case FK_CONST:
-        if (w1) k_step<FK_CONST, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_CONST, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        if (w1) k_step<FK_CONST, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_CONST, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     default:
-        if (w1) k_step<FK_GENERAL, true><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_GENERAL, false><<<grid, kBlock, 0, a.stream>>>(a.fin, a.fout, a.g, a.F, a.apre, a.apost, w);
+        if (w1) k_step<FK_GENERAL, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_GENERAL, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     }
     return cudaGetLastError();

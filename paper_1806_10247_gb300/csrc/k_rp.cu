@@ -72,16 +72,86 @@ __device__ __forceinline__ void collide9(float (&d)[9], float rref, float Fx, fl
     d[8] += c + (Gx - Gy) + (-g5 + g6 - g7);
 }
 
-template <class T, int FK>
+// The same step when omega_6 = omega_7 = omega_8 = 1, as the FP64 kernel's
+// collide_w1: the post-collision deviations follow from drho, u and the three
+// relaxed second-order central moments, through the halved back-shift and
+// inverse transform.  The transform is linear and maps the rest state's
+// central moments about u, rho_ref prod(1, -u, 1/3 + u^2), to w rho_ref, so
+// it is applied to the DEVIATIONS of the post-collision central moments from
+// those: first order rho_ref u (the total is 0), second order the relaxed
+// moments minus rho_ref (1/3 + u^2) (resp. rho_ref u_x u_y), third order
+// rho_ref (1/3 + u_x^2) u_y (the total is 0), fourth order
+// drho / 9 - rho_ref (u_x^2 / 3 + u_y^2 / 3 + u_x^2 u_y^2).  No O(1)
+// quantity is subtracted.  The first raw moments come back as j itself, not
+// as rho (j / rho): in FP32 that round trip would change the momentum by the
+// same rounding every step of a steady flow, and the error would add up.
+__device__ __forceinline__ void collide9_w1(float (&d)[9], float rref, float Fx, float Fy, float Gx, float Gy,
+                                            const Rates9f &w)
+{
+    const float s0 = d[1] + d[3], d0 = d[1] - d[3];
+    const float s1 = d[5] + d[6], d1 = d[5] - d[6];
+    const float s2 = d[8] + d[7], d2 = d[8] - d[7];
+    const float B0 = d[2] + s1, C0 = d[4] + s2;
+    const float drho = (d[0] + s0) + (B0 + C0);
+    const float jx = fmaf(0.5f, Fx, d0 + (d1 + d2)), jy = fmaf(0.5f, Fy, B0 - C0);  // Eq. 25
+    const float mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;  // deviations: m_xx - rho_ref / 3 etc.
+    const float rho = rref + drho;
+    const float rinv = __frcp_rn(rho);
+    const float ux = jx * rinv, uy = jy * rinv;
+    const float ux2 = ux * ux, uy2 = uy * uy;
+
+    // second-order central moments minus rho_ref / 3 (xx, yy), relaxed; then
+    // their deviations from the rest state's, halved
+    const float cxx = fmaf(-jx, ux, mxx), cyy = fmaf(-jy, uy, myy), cxy = fmaf(-jx, uy, mxy);
+    const float T = cxx + cyy, D = cxx - cyy;
+    const float Tq = fmaf(3.0f * w.c3, fmaf(2.0f / 3.0f, drho, -T), 0.25f * T);
+    const float Dq = (0.25f - w.c4) * D;
+    const float rh = 0.5f * rref, rq = 0.25f * rref;
+    const float kxx = fmaf(-rh, ux2, Tq + Dq), kyy = fmaf(-rh, uy2, Tq - Dq);
+    const float kxy = fmaf(-rq, ux * uy, (0.25f - w.c5) * cxy);
+    // halved first central moments of the deviations, j - u drho (= rho_ref u)
+    const float k10 = 0.5f * fmaf(-ux, drho, jx), k01 = 0.5f * fmaf(-uy, drho, jy);
+    const float k21 = rq * fmaf(ux, ux, 1.0f / 3.0f) * uy, k12 = rq * ux * fmaf(uy, uy, 1.0f / 3.0f);
+    const float k22 = fmaf(1.0f / 36.0f, drho, -rq * (fmaf(ux2 + uy2, 1.0f / 3.0f, ux2 * uy2)));
+
+    // back-shift along x of the lines of y-order 0, 1, 2, then along y
+    const float hx = 0.5f * ux, hy = 0.5f * uy;
+    const float M10 = 0.5f * jx, M20 = fmaf(ux, k10 + M10, kxx);  // m_10 = j_x exactly
+    const float M01 = k01, M11 = fmaf(hx, k01, kxy), M21 = fmaf(ux, kxy + M11, k21);
+    const float M02 = kyy, M12 = fmaf(hx, kyy, k12), M22 = fmaf(ux, k12 + M12, k22);
+    const float N00 = drho, N01 = 0.5f * jy, N02 = fmaf(uy, M01 + N01, M02);  // m_01 = j_y exactly
+    float N10 = M10, N11 = fmaf(hy, M10, M11), N12 = fmaf(uy, M11 + N11, M12);
+    const float N20 = M20;
+    float N21 = fmaf(hy, M20, M21);
+    const float N22 = fmaf(uy, M21 + N21, M22);
+    float N01f = fmaf(3.0f, Gy, fmaf(-0.25f, Fy, N01));  // post-collision force (Eq. 31), halved
+    N10 = fmaf(3.0f, Gx, fmaf(-0.25f, Fx, N10));
+    N12 += Gx;
+    N21 += Gy;
+    const float P0m = N02 - N01f, P00 = fmaf(-2.0f, N02, N00), P0p = N02 + N01f;
+    const float P1m = N12 - N11, P10 = fmaf(-2.0f, N12, N10), P1p = N12 + N11;
+    const float P2m = N22 - N21, P20 = fmaf(-2.0f, N22, N20), P2p = N22 + N21;
+    d[0] = fmaf(-2.0f, P20, P00);
+    d[1] = P20 + P10;
+    d[3] = P20 - P10;
+    d[2] = fmaf(-2.0f, P2p, P0p);
+    d[5] = P2p + P1p;
+    d[6] = P2p - P1p;
+    d[4] = fmaf(-2.0f, P2m, P0m);
+    d[8] = P2m + P1m;
+    d[7] = P2m - P1m;
+}
+
+template <class T, int FK, bool W1>
 __global__ void __launch_bounds__(kBlock)
-k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, float apre, float gsum, Rates9f w,
-        float rref)
+k_step9(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     float d[9];
-    load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
+    load_pulled_dev<LD2Q9, T>(P, g, x, y, 0, i, d);
     float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
     if (FK != FK_NONE) {
         const float Px = field_value_f(F, FK, 0, x, y, 0, i), Py = field_value_f(F, FK, 1, x, y, 0, i);
@@ -90,9 +160,10 @@ k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, flo
         Gx = gsum * Px;
         Gy = gsum * Py;
     }
-    collide9(d, rref, Fx, Fy, Gx, Gy, w);
+    if (W1) collide9_w1(d, rref, Fx, Fy, Gx, Gy, w);
+    else collide9(d, rref, Fx, Fy, Gx, Gy, w);
 #pragma unroll
-    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+    for (int a = 0; a < 9; a++) P.out[a][i] = Dev<T>::to_store(d[a]);
 }
 
 // Many steps per launch for a small D2Q9 lattice (the FP32 / 16-bit form of
@@ -103,7 +174,7 @@ k_step9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, flo
 namespace cg = cooperative_groups;
 constexpr int kClusterThreads = 384;
 
-template <class T, int FK>
+template <class T, int FK, bool W1>
 __global__ void __launch_bounds__(kClusterThreads)
 k_cluster9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, float apre, float gsum, Rates9f w,
            float rref, int P, int nsteps)
@@ -148,7 +219,8 @@ k_cluster9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, 
                 const T *base = cl.map_shared_rank(sm + cur * 9 * P, src_blk[a]);
                 d[a] = (float)base[src_off[a]];
             }
-            collide9(d, rref, Fx, Fy, Gx, Gy, w);
+            if (W1) collide9_w1(d, rref, Fx, Fy, Gx, Gy, w);
+            else collide9(d, rref, Fx, Fy, Gx, Gy, w);
             T *nxt = sm + (cur ^ 1) * 9 * P;
 #pragma unroll
             for (int a = 0; a < 9; a++) nxt[a * P + l] = Dev<T>::to_store(d[a]);
@@ -159,6 +231,27 @@ k_cluster9(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev F, 
     if (own)
 #pragma unroll
         for (int a = 0; a < 9; a++) fout[a * g.Np + i] = sm[cur * 9 * P + a * P + l];
+}
+
+template <class T, bool W1>
+cudaError_t cluster9_launch(cudaLaunchConfig_t &cfg, int C, const LaunchArgs &a, const T *fin, T *fout, float apre,
+                            float gsum, const Rates9f &w, float rref, int P, int nsteps)
+{
+    switch (a.fkind) {
+    case FK_NONE:
+        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_NONE, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_NONE, W1>, fin, fout, a.g, a.F, apre, gsum, w, rref, P,
+                                  nsteps);
+    case FK_CONST:
+        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_CONST, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_CONST, W1>, fin, fout, a.g, a.F, apre, gsum, w, rref, P,
+                                  nsteps);
+    default:
+        if (C > 8)
+            cudaFuncSetAttribute(k_cluster9<T, FK_GENERAL, W1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_GENERAL, W1>, fin, fout, a.g, a.F, apre, gsum, w, rref, P,
+                                  nsteps);
+    }
 }
 
 template <class T>
@@ -186,18 +279,9 @@ cudaError_t cluster9_t(const LaunchArgs &a, int nsteps)
     cfg.numAttrs = 1;
     const T *fin = reinterpret_cast<const T *>(a.fin);
     T *fout = reinterpret_cast<T *>(a.fout);
-    switch (a.fkind) {
-    case FK_NONE:
-        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_NONE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_NONE>, fin, fout, a.g, a.F, apre, gsum, w, rref, P, nsteps);
-    case FK_CONST:
-        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_CONST>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_CONST>, fin, fout, a.g, a.F, apre, gsum, w, rref, P, nsteps);
-    default:
-        if (C > 8) cudaFuncSetAttribute(k_cluster9<T, FK_GENERAL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        return cudaLaunchKernelEx(&cfg, k_cluster9<T, FK_GENERAL>, fin, fout, a.g, a.F, apre, gsum, w, rref, P,
-                                  nsteps);
-    }
+    return (a.omega[6] == 1.0 && a.omega[7] == 1.0 && a.omega[8] == 1.0)
+               ? cluster9_launch<T, true>(cfg, C, a, fin, fout, apre, gsum, w, rref, P, nsteps)
+               : cluster9_launch<T, false>(cfg, C, a, fin, fout, apre, gsum, w, rref, P, nsteps);
 }
 
 // ------------------------------------------------------------------ D2Q5 ---
@@ -281,19 +365,20 @@ Coef5f make_coef5f(const double omega[9], double ux, double uy)
 
 template <class T, int SK, bool UNIFORM>
 __global__ void __launch_bounds__(kBlock)
-k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, FieldDev V, float apre, float hsum,
-        Rates5f w, Coef5f k, float rref)
+k_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, FieldDev V, float apre, float hsum, Rates5f w,
+        Coef5f k, float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     float d[5];
-    load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
+    load_pulled_dev<LD2Q5, T>(P, g, x, y, 0, i, d);
     float Sp = 0.f, H0 = 0.f;
     if (SK != FK_NONE) {
-        const float P = field_value_f(S, SK, 0, x, y, 0, i);
-        Sp = apre * P;
-        H0 = hsum * P;
+        const float Ps = field_value_f(S, SK, 0, x, y, 0, i);
+        Sp = apre * Ps;
+        H0 = hsum * Ps;
     }
     if (UNIFORM) {
         collide5u(d, rref, Sp, H0, k);
@@ -303,7 +388,7 @@ k_step5(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev S, Fie
         collide5(d, rref, Sp, H0, ux, uy, w);
     }
 #pragma unroll
-    for (int a = 0; a < 5; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+    for (int a = 0; a < 5; a++) P.out[a][i] = Dev<T>::to_store(d[a]);
 }
 
 // ----------------------------------------------------------------- D3Q27 ---
@@ -319,10 +404,13 @@ __device__ __forceinline__ void raw_fwd(float &a, float &b, float &c)
     b = dd;
     c = s;
 }
-__device__ __forceinline__ void raw_bwd(float &m0, float &m1, float &m2)
+// The way back runs on HALVED moments (each axis on which a moment has order 1
+// or 2 contributes a factor 1/2), as in the FP64 kernel: the inverse 1D
+// transform of (m0, m1/2, m2/2) is f_-1 = m2/2 - m1/2, f_0 = m0 - m2,
+// f_+1 = m2/2 + m1/2, three operations per line instead of four.
+__device__ __forceinline__ void raw_bwd_h(float &m0, float &m1, float &m2)
 {
-    const float h = 0.5f * m2;
-    const float fm = fmaf(-0.5f, m1, h), fp = fmaf(0.5f, m1, h), f0 = m0 - m2;
+    const float fm = m2 - m1, fp = m2 + m1, f0 = fmaf(-2.0f, m2, m0);
     m0 = fm;
     m1 = f0;
     m2 = fp;
@@ -333,9 +421,10 @@ __device__ __forceinline__ void shift_fwd(float m0, float &m1, float &m2, float 
     m2 = fmaf(-u, m1 + k1, m2);
     m1 = k1;
 }
-__device__ __forceinline__ void shift_bwd(float k0, float &k1, float &k2, float u)
+// Halved central moments about u -> halved raw moments (one axis; uh = u / 2).
+__device__ __forceinline__ void shift_bwd_h(float k0, float &k1, float &k2, float u, float uh)
 {
-    const float m1 = fmaf(u, k0, k1);
+    const float m1 = fmaf(uh, k0, k1);
     k2 = fmaf(u, k1 + m1, k2);
     k1 = m1;
 }
@@ -350,34 +439,43 @@ __device__ __forceinline__ void along(float (&m)[27], Op op)
     }
 }
 
-// Central moments of the deviations about u (post-collision) -> deviations:
-// back-shift, post-collision force in moment space, inverse raw transform.
+// Halved post-collision central moments of the deviations about u ->
+// deviations: back-shift, post-collision force in moment space (K_1 g_1 with
+// g = (F_pre + F_post) / 36; m_100 already carries F_pre / 2), inverse raw
+// transform.
 __device__ __forceinline__ void finish27(float (&m)[27], float ux, float uy, float uz, const float (&F)[3],
                                          const float (&Fq)[3])
 {
-    along<0>(m, [ux](float &a, float &b, float &c) { shift_bwd(a, b, c, ux); });
-    along<1>(m, [uy](float &a, float &b, float &c) { shift_bwd(a, b, c, uy); });
-    along<2>(m, [uz](float &a, float &b, float &c) { shift_bwd(a, b, c, uz); });
+    const float hx = 0.5f * ux, hy = 0.5f * uy, hz = 0.5f * uz;
+    along<0>(m, [ux, hx](float &a, float &b, float &c) { shift_bwd_h(a, b, c, ux, hx); });
+    along<1>(m, [uy, hy](float &a, float &b, float &c) { shift_bwd_h(a, b, c, uy, hy); });
+    along<2>(m, [uz, hz](float &a, float &b, float &c) { shift_bwd_h(a, b, c, uz, hz); });
 
     {
-        const float hx = 0.5f * (F[0] + Fq[0]), hy = 0.5f * (F[1] + Fq[1]), hz = 0.5f * (F[2] + Fq[2]);
-        m[1] = fmaf(0.5f, Fq[0], m[1]);
-        m[3] = fmaf(0.5f, Fq[1], m[3]);
-        m[9] = fmaf(0.5f, Fq[2], m[9]);
-        const float ax = hx * (2.0f / 3.0f), ay = hy * (2.0f / 3.0f), az = hz * (2.0f / 3.0f);
-        m[7] += ax; m[19] += ax; m[25] = fmaf(hx, 4.0f / 9.0f, m[25]);
-        m[5] += ay; m[21] += ay; m[23] = fmaf(hy, 4.0f / 9.0f, m[23]);
-        m[11] += az; m[15] += az; m[17] = fmaf(hz, 4.0f / 9.0f, m[17]);
+        const float sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+        m[1] = fmaf(0.25f, Fq[0], m[1]);
+        m[3] = fmaf(0.25f, Fq[1], m[3]);
+        m[9] = fmaf(0.25f, Fq[2], m[9]);
+        m[7] = fmaf(sx, 1.0f / 12.0f, m[7]); m[19] = fmaf(sx, 1.0f / 12.0f, m[19]); m[25] = fmaf(sx, 1.0f / 36.0f, m[25]);
+        m[5] = fmaf(sy, 1.0f / 12.0f, m[5]); m[21] = fmaf(sy, 1.0f / 12.0f, m[21]); m[23] = fmaf(sy, 1.0f / 36.0f, m[23]);
+        m[11] = fmaf(sz, 1.0f / 12.0f, m[11]); m[15] = fmaf(sz, 1.0f / 12.0f, m[15]); m[17] = fmaf(sz, 1.0f / 36.0f, m[17]);
     }
 
-    along<2>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
-    along<1>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
-    along<0>(m, [](float &a, float &b, float &c) { raw_bwd(a, b, c); });
+    along<2>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
+    along<1>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
+    along<0>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
+}
+
+// Halving factor of moment k = a + 3b + 9c: 2^-(number of nonzero a, b, c).
+__host__ __device__ constexpr float halving(int k)
+{
+    return ((k % 3) ? 0.5f : 1.0f) * (((k / 3) % 3) ? 0.5f : 1.0f) * ((k / 9) ? 0.5f : 1.0f);
 }
 
 // Deviation target of the central moment k = a + 3b + 9c of order n >= 3: its
-// Maxwellian value minus the rest state's central moment about u.
-__device__ __forceinline__ float high_target(int k, float drho, float rref, float ux, float uy, float uz)
+// Maxwellian value minus the rest state's central moment about u, times the
+// factor h that dr = h drho and rr = h rref carry (h = halving(k)).
+__device__ __forceinline__ float high_target(int k, float dr, float rr, float ux, float uy, float uz)
 {
     const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
     const int a = k % 3, b = (k / 3) % 3, c = k / 9;
@@ -385,15 +483,15 @@ __device__ __forceinline__ float high_target(int k, float drho, float rref, floa
     const float hx[3] = {1.0f, -ux, (1.0f / 3.0f) + ux2};
     const float hy[3] = {1.0f, -uy, (1.0f / 3.0f) + uy2};
     const float hz[3] = {1.0f, -uz, (1.0f / 3.0f) + uz2};
-    if (a == 1 || b == 1 || c == 1) return -rref * (hx[a] * hy[b] * hz[c]);  // equilibrium 0
+    if (a == 1 || b == 1 || c == 1) return -rr * (hx[a] * hy[b] * hz[c]);  // equilibrium 0
     if (n == 4) {
         const float p = (a == 2 ? ux2 : 0.f) + (b == 2 ? uy2 : 0.f) + (c == 2 ? uz2 : 0.f);
         const float q = (a == 2 ? ux2 : 1.f) * (b == 2 ? uy2 : 1.f) * (c == 2 ? uz2 : 1.f);
-        return drho * (1.0f / 9.0f) - rref * (p * (1.0f / 3.0f) + q);
+        return dr * (1.0f / 9.0f) - rr * (p * (1.0f / 3.0f) + q);
     }
-    return drho * (1.0f / 27.0f) -
-           rref * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f) +
-                   ux2 * uy2 * uz2);
+    return dr * (1.0f / 27.0f) -
+           rr * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f) +
+                 ux2 * uy2 * uz2);
 }
 
 // Deviation form of the generic central-moment collision: m holds the raw
@@ -420,27 +518,36 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
 
     const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
     {
-        // second order: trace towards rho, deviatoric and off-diagonal towards 0
+        // second order: trace towards rho, deviatoric and off-diagonal towards
+        // 0; results halved
         const float Tn = m[2] + m[6] + m[18];
         const float Ts = fmaf(w.wb, drho - rref * (ux2 + uy2 + uz2) - Tn, Tn);
         const float D1 = m[2] - m[6], D2 = m[2] - m[18];
         const float rs = 1.0f - w.ws;
-        const float D1s = rs * D1 - w.ws * rref * (ux2 - uy2);
-        const float D2s = rs * D2 - w.ws * rref * (ux2 - uz2);
-        const float kxx = (Ts + D1s + D2s) * (1.0f / 3.0f);
+        const float rh = 0.5f * rs, rq = 0.25f * rs, wh = 0.5f * w.ws * rref, wq = 0.25f * w.ws * rref;
+        const float D1h = rh * D1 - wh * (ux2 - uy2);
+        const float D2h = rh * D2 - wh * (ux2 - uz2);
+        const float kxx = fmaf(Ts, 1.0f / 6.0f, (D1h + D2h) * (1.0f / 3.0f));
         m[2] = kxx;
-        m[6] = kxx - D1s;
-        m[18] = kxx - D2s;
-        m[4] = rs * m[4] - w.ws * rref * (ux * uy);
-        m[10] = rs * m[10] - w.ws * rref * (ux * uz);
-        m[12] = rs * m[12] - w.ws * rref * (uy * uz);
-        // orders 3..6 towards the Maxwellian central moments
+        m[6] = kxx - D1h;
+        m[18] = kxx - D2h;
+        m[4] = rq * m[4] - wq * (ux * uy);
+        m[10] = rq * m[10] - wq * (ux * uz);
+        m[12] = rq * m[12] - wq * (uy * uz);
+        m[1] *= 0.5f;
+        m[3] *= 0.5f;
+        m[9] *= 0.5f;
+        // orders 3..6 towards the Maxwellian central moments:
+        // h (m + om (t - m)) = h (1 - om) m + om (h t)
+        const float d4 = 0.25f * drho, r4 = 0.25f * rref, d8 = 0.125f * drho, r8 = 0.125f * rref;
 #pragma unroll
         for (int k = 0; k < 27; k++) {
             const int n = k % 3 + (k / 3) % 3 + k / 9;
             if (n < 3) continue;
             const float om = n == 3 ? w.w3 : (n == 4 ? w.w4 : (n == 5 ? w.w5 : w.w6));
-            m[k] = fmaf(om, high_target(k, drho, rref, ux, uy, uz) - m[k], m[k]);
+            const bool quarter = halving(k) == 0.25f;
+            const float t = high_target(k, quarter ? d4 : d8, quarter ? r4 : r8, ux, uy, uz);
+            m[k] = fmaf(halving(k) * (1.0f - om), m[k], om * t);
         }
     }
 
@@ -490,28 +597,32 @@ __device__ __forceinline__ void collide27_w1(float (&m)[27], float rref, const f
     const float cxz = fmaf(-uz, k100, fmaf(-ux, jz, kxz));
     const float cyz = fmaf(-uz, k010, fmaf(-uy, jz, kyz));
 
+    // relaxed central moments, halved
     const float Tn = cxx + cyy + czz;
     const float Ts = fmaf(w.wb, drho - rref * (ux2 + uy2 + uz2) - Tn, Tn);
     const float D1 = cxx - cyy, D2 = cxx - czz;
     const float rs = 1.0f - w.ws;
-    const float D1s = rs * D1 - w.ws * rref * (ux2 - uy2);
-    const float D2s = rs * D2 - w.ws * rref * (ux2 - uz2);
-    const float sxx = (Ts + D1s + D2s) * (1.0f / 3.0f);
+    const float rh = 0.5f * rs, rq = 0.25f * rs, wh = 0.5f * w.ws * rref, wq = 0.25f * w.ws * rref;
+    const float D1h = rh * D1 - wh * (ux2 - uy2);
+    const float D2h = rh * D2 - wh * (ux2 - uz2);
+    const float sxx = fmaf(Ts, 1.0f / 6.0f, (D1h + D2h) * (1.0f / 3.0f));
+    const float d4 = 0.25f * drho, r4 = 0.25f * rref, d8 = 0.125f * drho, r8 = 0.125f * rref;
 #pragma unroll
     for (int k = 0; k < 27; k++) {
         const int n = k % 3 + (k / 3) % 3 + k / 9;
-        if (n >= 3) m[k] = high_target(k, drho, rref, ux, uy, uz);
+        const bool quarter = halving(k) == 0.25f;
+        if (n >= 3) m[k] = high_target(k, quarter ? d4 : d8, quarter ? r4 : r8, ux, uy, uz);
     }
     m[0] = drho;
-    m[1] = k100;
-    m[3] = k010;
-    m[9] = k001;
+    m[1] = 0.5f * k100;
+    m[3] = 0.5f * k010;
+    m[9] = 0.5f * k001;
     m[2] = sxx;
-    m[6] = sxx - D1s;
-    m[18] = sxx - D2s;
-    m[4] = rs * cxy - w.ws * rref * (ux * uy);
-    m[10] = rs * cxz - w.ws * rref * (ux * uz);
-    m[12] = rs * cyz - w.ws * rref * (uy * uz);
+    m[6] = sxx - D1h;
+    m[18] = sxx - D2h;
+    m[4] = rq * cxy - wq * (ux * uy);
+    m[10] = rq * cxz - wq * (ux * uz);
+    m[12] = rq * cyz - wq * (uy * uz);
     finish27(m, ux, uy, uz, F, Fq);
 }
 
@@ -520,28 +631,28 @@ __device__ __forceinline__ void collide27_w1(float (&m)[27], float rref, const f
 // registers.
 template <class T, int FK, bool W1>
 __global__ void __launch_bounds__(kBlock, 4)
-k_step27(const T *__restrict__ fin, T *__restrict__ fout, Geom g, FieldDev Fd, float apre, float apost,
-         Rates27f w, float rref)
+k_step27(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apre, float apost, Rates27f w,
+         float rref)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
     float m[27];
-    load_pulled_dev<LD3Q27, T>(fin, g, x, y, z, i, m);
+    load_pulled_dev<LD3Q27, T>(P, g, x, y, z, i, m);
     float F[3] = {0.f, 0.f, 0.f}, Fq[3] = {0.f, 0.f, 0.f};
     if (FK != FK_NONE) {
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            const float P = field_value_f(Fd, FK, d, x, y, z, i);
-            F[d] = apre * P;
-            Fq[d] = apost * P;
+            const float Pd = field_value_f(Fd, FK, d, x, y, z, i);
+            F[d] = apre * Pd;
+            Fq[d] = apost * Pd;
         }
     }
     if (W1) collide27_w1(m, rref, F, Fq, w);
     else collide27(m, rref, F, Fq, w);
 #pragma unroll
-    for (int a = 0; a < 27; a++) fout[a * g.Np + i] = Dev<T>::to_store(m[a]);
+    for (int a = 0; a < 27; a++) P.out[a][i] = Dev<T>::to_store(m[a]);
 }
 
 // --------------------------------------------------------------- batched ---
@@ -555,7 +666,8 @@ __device__ __forceinline__ void node9(const BatchItem &B, const BatchLaunch &L, 
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
     const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     float d[9];
     load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
     float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
@@ -567,7 +679,8 @@ __device__ __forceinline__ void node9(const BatchItem &B, const BatchLaunch &L, 
         Gy = ap.y * Py;
     }
     const Rates9f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
-    collide9(d, B.frho_ref, Fx, Fy, Gx, Gy, w);
+    if (B.variant == 1) collide9_w1(d, B.frho_ref, Fx, Fy, Gx, Gy, w);  // uniform over the member
+    else collide9(d, B.frho_ref, Fx, Fy, Gx, Gy, w);
 #pragma unroll
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
 }
@@ -581,7 +694,8 @@ __device__ __forceinline__ void node5(const BatchItem &B, const BatchLaunch &L, 
     const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
     T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
     const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
-    const int x = i % g.nx, y = i / g.nx;
+    int x, y;
+    node_xy(g, i, x, y);
     float d[5];
     load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
     float Sp = 0.f, H0 = 0.f;
@@ -656,21 +770,29 @@ __global__ void __launch_bounds__(TB, 1024 / TB) k_batch27(const __grid_constant
 }
 
 
+template <class T, bool W1>
+void step9_launch(const Planes<T, 9> &fin, const LaunchArgs &a, int grid, float apre, float gsum, const Rates9f &w,
+                  float rref, cudaStream_t s)
+{
+    if (a.fkind == FK_NONE) k_step9<T, FK_NONE, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
+    else if (a.fkind == FK_CONST) k_step9<T, FK_CONST, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
+    else k_step9<T, FK_GENERAL, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
+}
+
 template <class T>
 cudaError_t step_t(int lattice, const LaunchArgs &a)
 {
-    const T *fin = reinterpret_cast<const T *>(a.fin);
-    T *fout = reinterpret_cast<T *>(a.fout);
     const int grid = (a.g.N + kBlock - 1) / kBlock;
     const float rref = (float)a.rho_ref;
     const cudaStream_t s = a.stream;
     if (lattice == LD2Q9::ID) {
+        const Planes<T, 9> fin = make_planes<T, 9>(a.fin, a.fout, a.g.Np);
         const Rates9f w{(float)(a.omega[3] / 12.0), (float)(a.omega[4] / 4.0), (float)(a.omega[5] / 4.0),
                         (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
         const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre;
-        if (a.fkind == FK_NONE) k_step9<T, FK_NONE><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
-        else if (a.fkind == FK_CONST) k_step9<T, FK_CONST><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
-        else k_step9<T, FK_GENERAL><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, apre, gsum, w, rref);
+        const bool w1 = a.omega[6] == 1.0 && a.omega[7] == 1.0 && a.omega[8] == 1.0;
+        if (w1) step9_launch<T, true>(fin, a, grid, apre, gsum, w, rref, s);
+        else step9_launch<T, false>(fin, a, grid, apre, gsum, w, rref, s);
     } else if (lattice == LD2Q5::ID) {
         const Rates5f w{(float)(a.omega[1] / 2.0), (float)(a.omega[2] / 2.0), (float)(a.omega[3] / 4.0),
                         (float)(a.omega[4] / 4.0)};
@@ -678,30 +800,32 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
         const Coef5f k = make_coef5f(a.omega, ux, uy);
         const float hsum = (float)((a.apre + a.apost) / 10.0), apre = (float)a.apre;
         const bool uni = a.vkind != FK_GENERAL;
+        const Planes<T, 5> fin = make_planes<T, 5>(a.fin, a.fout, a.g.Np);
         if (a.fkind == FK_NONE) {
-            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
         } else if (a.fkind == FK_CONST) {
-            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
         } else {
-            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
+            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
         }
     } else {
         const Rates27f w{(float)a.omega[1], (float)a.omega[2], (float)a.omega[3],
                          (float)a.omega[4], (float)a.omega[5], (float)a.omega[6]};
         const bool w1 = a.omega[3] == 1.0 && a.omega[4] == 1.0 && a.omega[5] == 1.0 && a.omega[6] == 1.0;
         const float ap = (float)a.apre, aq = (float)a.apost;
+        const Planes<T, 27> fin = make_planes<T, 27>(a.fin, a.fout, a.g.Np);
         if (a.fkind == FK_NONE) {
-            if (w1) k_step27<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            if (w1) k_step27<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
         } else if (a.fkind == FK_CONST) {
-            if (w1) k_step27<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            if (w1) k_step27<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
         } else {
-            if (w1) k_step27<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, fout, a.g, a.F, ap, aq, w, rref);
+            if (w1) k_step27<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
+            else k_step27<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
         }
     }
     return cudaGetLastError();

@@ -74,6 +74,7 @@ struct lbm_batch {
     cudaStream_t cstream = nullptr;
     cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // slot filled (recorded on the batch stream)
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};  // slot copied out (recorded on the copy stream)
+    cudaEvent_t ev_host[2] = {nullptr, nullptr};    // the fields of slot k are in host memory
     int qslot = 0;
     bool copies_pending = false;
     std::string err;
@@ -697,7 +698,7 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
     b->err.clear();
     const bool scalar = b->lattice == LBM_D2Q5_CDE;
     if (!rho || (!scalar && !u)) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: NULL output");
-    if (where < 0 || where > 2) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where must be 0, 1 or 2");
+    if (where < 0 || where > 3) return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where must be 0, 1, 2 or 3");
     for (int i = 0; i < b->count; i++)
         if (!b->ctx[i]->initialised)
             return bfail(b, LBM_ESTATE, "lbm_batch_moments_packed: context %d not initialised", i);
@@ -712,21 +713,43 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
         if (!b->d_mom) BCK(cudaMalloc(&b->d_mom, (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
         drho = b->d_mom;
         du = b->d_mom + nrho;
-    } else if (where == 2) {
+    } else if (where >= 2) {
         if (!b->cstream) {
             BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
             for (int k = 0; k < 2; k++) {
-                BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
                 BCK(cudaEventCreateWithFlags(&b->ev_ready[k], cudaEventDisableTiming), "event");
                 BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
             }
         }
+        if (where == 3) {
+            // host memory the device can address (pinned by cudaHostAlloc, or
+            // registered as mapped): the kernel writes the fields into it
+            double *outs[2] = {rho, u};
+            double *devs[2] = {nullptr, nullptr};
+            for (int k = 0; k < (scalar ? 1 : 2); k++) {
+                cudaPointerAttributes pa{};
+                const cudaError_t e = cudaPointerGetAttributes(&pa, outs[k]);
+                if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+                    cudaGetLastError();
+                    return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where = 3 needs host memory mapped into "
+                                                "the device's address space");
+                }
+                devs[k] = static_cast<double *>(pa.devicePointer);
+            }
+            drho = devs[0];
+            du = devs[1];
+        } else if (!b->d_momq[0]) {
+            for (int k = 0; k < 2; k++)
+                BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
+        }
         slot = b->qslot;
         b->qslot ^= 1;
-        // the slot's previous copy must have left it before the kernel refills it
-        BCK(cudaStreamWaitEvent(b->stream, b->ev_copied[slot], 0), "lbm_batch_moments_packed: wait");
-        drho = b->d_momq[slot];
-        du = b->d_momq[slot] + nrho;
+        if (where == 2) {
+            // the slot's previous copy must have left it before the kernel refills it
+            BCK(cudaStreamWaitEvent(b->stream, b->ev_copied[slot], 0), "lbm_batch_moments_packed: wait");
+            drho = b->d_momq[slot];
+            du = b->d_momq[slot] + nrho;
+        }
     }
     // a_pre of each member's current step; the previous copy has read the pinned slot by ev_apre
     BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
@@ -767,6 +790,11 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
             BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
                 "lbm_batch_moments_packed: copy u");
         BCK(cudaEventRecord(b->ev_copied[slot], b->cstream), "lbm_batch_moments_packed: record");
+        b->ev_host[slot] = b->ev_copied[slot];
+        b->copies_pending = true;
+    } else if (where == 3) {
+        BCK(cudaEventRecord(b->ev_ready[slot], b->stream), "lbm_batch_moments_packed: record");
+        b->ev_host[slot] = b->ev_ready[slot];
         b->copies_pending = true;
     }
     return LBM_OK;
@@ -778,12 +806,12 @@ int lbm_batch_wait_moments(lbm_batch *b, int keep)
     b->err.clear();
     if (keep != 0 && keep != 1) return bfail(b, LBM_EINVAL, "lbm_batch_wait_moments: keep must be 0 or 1");
     if (!b->copies_pending) return LBM_OK;
+    // the slots alternate: qslot is the slot of the readback before the latest
+    const int older = b->qslot, latest = b->qslot ^ 1;
+    if (b->ev_host[older]) BCK(cudaEventSynchronize(b->ev_host[older]), "lbm_batch_wait_moments");
     if (keep == 0) {
-        BCK(cudaStreamSynchronize(b->cstream), "lbm_batch_wait_moments");
+        if (b->ev_host[latest]) BCK(cudaEventSynchronize(b->ev_host[latest]), "lbm_batch_wait_moments");
         b->copies_pending = false;
-    } else {
-        // the readback before the latest used slot qslot (the slots alternate)
-        BCK(cudaEventSynchronize(b->ev_copied[b->qslot]), "lbm_batch_wait_moments");
     }
     return LBM_OK;
 }

@@ -279,6 +279,8 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     c->g.N = (int)N;
     c->g.Np = (N + 127) / 128 * 128;  // every plane starts 256-byte aligned for any element size
     for (int d = 0; d < 3; d++) c->g.wall[d] = wall[d];
+    lbmk::div_magic(nx, c->g.mx, c->g.lx);
+    lbmk::div_magic(ny, c->g.my, c->g.ly);
     for (int k = 0; k < 9; k++) c->omega[k] = relax->omega[k];
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);

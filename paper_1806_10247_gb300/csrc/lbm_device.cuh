@@ -15,7 +15,28 @@ struct Geom {
     int N;          // nodes (validated < 2^31 on the host)
     long long Np;   // plane stride in doubles
     int wall[3];    // 1 = halfway bounce-back walls on that axis, 0 = periodic
+    // n / nx and n / ny for 0 <= n < 2^31 by multiply-high (see div_invariant)
+    unsigned mx, my;
+    int lx, ly;
 };
+
+// Quotient n / d of 0 <= n < 2^31 by an invariant divisor 1 <= d < 2^31,
+// after Granlund and Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), round-up method: with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l.  The sum
+// stays below 2^32 because umulhi(m, n) < n < 2^31.
+__device__ __forceinline__ int div_invariant(int n, unsigned m, int l)
+{
+    return (int)((__umulhi(m, (unsigned)n) + (unsigned)n) >> l);
+}
+
+// The (m, l) pair of div_invariant for divisor d (host side).
+inline void div_magic(int d, unsigned &m, int &l)
+{
+    l = 0;
+    while ((1LL << l) < (long long)d) l++;
+    m = (unsigned)(((unsigned long long)((1LL << l) - d) << 32) / (unsigned long long)d + 1ULL);
+}
 
 // Kinds of a force / source / velocity shape as seen by a kernel.
 enum FieldKind { FK_NONE = 0, FK_CONST = 1, FK_GENERAL = 2 };

@@ -68,35 +68,76 @@ __device__ __forceinline__ int pull_off(const Geom &g, int x, int y, int z, int 
     return sx + g.nx * (sy + g.ny * sz);
 }
 
-// A node none of whose pull sources leaves the domain: every population comes
-// from the fixed offset -(ex + nx ey + nx ny ez), no wrap or wall test needed.
-__device__ __forceinline__ bool interior(const Geom &g, int x, int y, int z)
+// Pulled populations of node i = (x, y, z): get(p, k) returns the stored
+// value of plane p at node k.  A node that has no wall beside it takes every
+// population along its wrapped periodic offset (no per-population test, so a
+// warp whose nodes straddle a periodic edge does not diverge); a node next to
+// a wall tests each population with pull_off.
+template <class L, class V, class Get>
+__device__ __forceinline__ void pull_node(const Geom &g, int x, int y, int z, int i, V (&f)[L::Q], Get get)
 {
-    return x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && (g.nz == 1 || (z > 0 && z < g.nz - 1));
-}
-
-template <class L>
-__device__ __forceinline__ void load_pulled(const double *__restrict__ fin, const Geom &g, int x, int y,
-                                            int z, int i, double (&f)[L::Q])
-{
-    if (interior(g, x, y, z)) {
-        const int sy = g.nx, sz = g.nx * g.ny;
+    const bool wall_x = g.wall[0] && (x == 0 || x == g.nx - 1);
+    const bool wall_y = g.wall[1] && (y == 0 || y == g.ny - 1);
+    const bool wall_z = L::DIM == 3 && g.wall[2] && (z == 0 || z == g.nz - 1);
+    if (!(wall_x || wall_y || wall_z)) {
+        // offset of the source node for e = +1 (coordinate - 1) and e = -1
+        // (coordinate + 1) along each axis, wrapped
+        const int sy = g.nx;
+        const int xm = x == 0 ? g.nx - 1 : -1, xp = x == g.nx - 1 ? 1 - g.nx : 1;
+        const int ym = y == 0 ? (g.ny - 1) * sy : -sy, yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+        int zm = 0, zp = 0;
+        if (L::DIM == 3) {
+            const int sz = g.nx * g.ny;
+            zm = z == 0 ? (g.nz - 1) * sz : -sz;
+            zp = z == g.nz - 1 ? (1 - g.nz) * sz : sz;
+        }
 #pragma unroll
-        for (int a = 0; a < L::Q; a++)
-            f[a] = __ldg(fin + a * g.Np + i - (L::ex(a) + L::ey(a) * sy + L::ez(a) * sz));
+        for (int a = 0; a < L::Q; a++) {
+            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+            const int row = i + (ey == 1 ? ym : (ey == -1 ? yp : 0)) + (ez == 1 ? zm : (ez == -1 ? zp : 0));
+            f[a] = get(a, row + (ex == 1 ? xm : (ex == -1 ? xp : 0)));
+        }
         return;
     }
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
         if (ex == 0 && ey == 0 && ez == 0) {
-            f[a] = __ldg(fin + a * g.Np + i);
+            f[a] = get(a, i);
         } else {
             bool opp;
-            int off = pull_off(g, x, y, z, ex, ey, ez, opp);
-            f[a] = __ldg(fin + (opp ? L::opp(a) : a) * g.Np + off);
+            const int off = pull_off(g, x, y, z, ex, ey, ez, opp);
+            f[a] = get(opp ? L::opp(a) : a, off);
         }
     }
+}
+
+template <class L>
+__device__ __forceinline__ void load_pulled(const double *__restrict__ fin, const Geom &g, int x, int y,
+                                            int z, int i, double (&f)[L::Q])
+{
+    pull_node<L>(g, x, y, z, i, f, [&](int p, int k) { return __ldg(fin + p * g.Np + k); });
+}
+
+// Base pointers of the Q population planes of a step's source and
+// destination buffers, passed in the launch arguments: a kernel then
+// addresses plane a of node k with one multiply-add on a parameter instead of
+// forming the 64-bit product a * Np per access.
+template <class T, int Q>
+struct Planes {
+    const T *in[Q];
+    T *out[Q];
+};
+
+template <class T, int Q>
+inline Planes<T, Q> make_planes(const void *fin, void *fout, long long Np)
+{
+    Planes<T, Q> P;
+    for (int a = 0; a < Q; a++) {
+        P.in[a] = static_cast<const T *>(fin) + a * Np;
+        P.out[a] = static_cast<T *>(fout) + a * Np;
+    }
+    return P;
 }
 
 // Reduced-precision storage: conversions of a stored deviation to/from float.
@@ -127,24 +168,21 @@ template <class L, class T>
 __device__ __forceinline__ void load_pulled_dev(const T *__restrict__ fin, const Geom &g, int x, int y, int z,
                                                 int i, float (&d)[L::Q])
 {
-    if (interior(g, x, y, z)) {
-        const int sy = g.nx, sz = g.nx * g.ny;
-#pragma unroll
-        for (int a = 0; a < L::Q; a++)
-            d[a] = Dev<T>::get(fin + a * g.Np + i - (L::ex(a) + L::ey(a) * sy + L::ez(a) * sz));
-        return;
-    }
-#pragma unroll
-    for (int a = 0; a < L::Q; a++) {
-        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-        if (ex == 0 && ey == 0 && ez == 0) {
-            d[a] = Dev<T>::get(fin + a * g.Np + i);
-        } else {
-            bool opp;
-            int off = pull_off(g, x, y, z, ex, ey, ez, opp);
-            d[a] = Dev<T>::get(fin + (opp ? L::opp(a) : a) * g.Np + off);
-        }
-    }
+    pull_node<L>(g, x, y, z, i, d, [&](int p, int k) { return Dev<T>::get(fin + p * g.Np + k); });
+}
+
+// The same pulls through a plane table in the launch arguments.
+template <class L>
+__device__ __forceinline__ void load_pulled(const Planes<double, L::Q> &P, const Geom &g, int x, int y, int z,
+                                            int i, double (&f)[L::Q])
+{
+    pull_node<L>(g, x, y, z, i, f, [&](int p, int k) { return __ldg(P.in[p] + k); });
+}
+template <class L, class T>
+__device__ __forceinline__ void load_pulled_dev(const Planes<T, L::Q> &P, const Geom &g, int x, int y, int z,
+                                                int i, float (&d)[L::Q])
+{
+    pull_node<L>(g, x, y, z, i, d, [&](int p, int k) { return Dev<T>::get(P.in[p] + k); });
 }
 
 // Zeroth and first moments of a node's populations.
@@ -191,12 +229,20 @@ __device__ __forceinline__ int batch_find(const int *__restrict__ first_block, i
     return lo;
 }
 
+// Coordinates of node i = x + nx (y + ny z).
 __device__ __forceinline__ void node_xyz(const Geom &g, int i, int &x, int &y, int &z)
 {
-    x = i % g.nx;
-    int r = i / g.nx;
-    y = r % g.ny;
-    z = r / g.ny;
+    const int r = div_invariant(i, g.mx, g.lx);
+    x = i - r * g.nx;
+    z = div_invariant(r, g.my, g.ly);
+    y = r - z * g.ny;
+}
+
+// Coordinates of node i = x + nx y of a 2D lattice.
+__device__ __forceinline__ void node_xy(const Geom &g, int i, int &x, int &y)
+{
+    y = div_invariant(i, g.mx, g.lx);
+    x = i - y * g.nx;
 }
 
 }  // namespace lbmk

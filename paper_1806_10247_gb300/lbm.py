@@ -415,15 +415,17 @@ class Batch:
 
     def moments_packed_into(self, rho_ptr, u_ptr=None, where=0, half_forced=True):
         """Fields of every member, packed member after member, into one buffer
-        each (raw addresses: host when where = 0, device when where = 1); one
-        kernel launch for the whole batch."""
+        each (raw addresses: host when where = 0 or 2, device when where = 1,
+        device-addressable pinned host memory when where = 3, which the kernel
+        writes directly); one kernel launch for the whole batch.  where = 2 and
+        3 are asynchronous (see wait_moments)."""
         self._check(self._L.lbm_batch_moments_packed(self.h, ctypes.c_void_p(int(rho_ptr)),
                                                      None if u_ptr is None else ctypes.c_void_p(int(u_ptr)),
                                                      int(where), int(bool(half_forced))))
 
     def wait_moments(self, keep=0):
-        """Wait for asynchronous readbacks (where = 2): all (keep = 0) or all
-        but the most recent one (keep = 1)."""
+        """Wait for asynchronous readbacks (where = 2 or 3): all (keep = 0) or
+        all but the most recent one (keep = 1)."""
         self._check(self._L.lbm_batch_wait_moments(self.h, int(keep)))
 
     def moments_packed(self, half_forced=True):

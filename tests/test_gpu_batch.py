@@ -361,9 +361,11 @@ def test_full_batched_sweep_in_the_bench_configuration():
             G.close()
 
 
-def test_asynchronous_packed_readback_double_buffered():
-    """where = 2: the copies overlap later steps; after wait_moments the host
-    buffers hold exactly the fields of the step they were queued at."""
+@pytest.mark.parametrize("where", [2, 3])
+def test_asynchronous_packed_readback_double_buffered(where):
+    """where = 2: the copies overlap later steps; where = 3: the kernel writes
+    the pinned host buffers directly.  After wait_moments the host buffers
+    hold exactly the fields of the step they were queued at."""
     import torch
 
     ws, fulls = _members("d2q9")
@@ -380,7 +382,7 @@ def test_asynchronous_packed_readback_double_buffered():
         T.step(1)
         history.append(T.moments_packed())
         r_, u_ = bufs[k % 2]
-        B.moments_packed_into(r_.data_ptr(), u_.data_ptr(), where=2)
+        B.moments_packed_into(r_.data_ptr(), u_.data_ptr(), where=where)
         B.wait_moments(keep=1)
         if k >= 1:
             r_prev, u_prev = bufs[(k - 1) % 2]
@@ -391,3 +393,8 @@ def test_asynchronous_packed_readback_double_buffered():
     assert np.array_equal(r_.numpy(), history[5][0]) and np.array_equal(u_.numpy(), history[5][1])
     with pytest.raises(lbm.LBMError):
         B.wait_moments(keep=3)
+    if where == 3:
+        # pageable memory is not addressable by the device: refused, nothing queued
+        r_np, u_np = np.empty(n), np.empty(2 * n)
+        with pytest.raises(lbm.LBMError):
+            B.moments_packed_into(r_np.ctypes.data, u_np.ctypes.data, where=3)
