@@ -48,48 +48,58 @@ KERNEL_FACTS = {
     ("cde_sweep", "fp64"): {
         "src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H,
         "fp64_inst_per_node": 30, "fp64_flops_per_node": 56,
-        "traffic_bytes_per_launch": 14.007040e6, "traffic_src_sha": "af1e387d1730d330",
+        "traffic_bytes_per_launch": 14.006528e6, "traffic_src_sha": "b69563316314b9cd",
         "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md",
     },
     ("kolmogorov96", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (95.596288 + 51.692032) * 1e6, "traffic_src_sha": "2ac04432c86724b4",
+        "traffic_bytes_per_launch": (95.587072 + 45.827072) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
+    },
+    ("kolmogorov256", "fp32"): {
+        "src": [_C + "k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (1812.101376 + 1756.919552) * 1e6, "traffic_src_sha": "2927ae77a413376a",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov96", "fp16"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (47.817728 + 7.982336) * 1e6, "traffic_src_sha": "2ac04432c86724b4",
+        "traffic_bytes_per_launch": (47.809024 + 7.182080) * 1e6, "traffic_src_sha": "2927ae77a413376a",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("batched_sweep256", "fp32"): {
         "src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh"] + _H,
-        "traffic_bytes_per_launch": (382.250496 + 336.566016) * 1e6, "traffic_src_sha": "42e6da8fb6b3c246",
+        "traffic_bytes_per_launch": (380.677120 + 335.904000) * 1e6, "traffic_src_sha": "541602c3f79a5ca1",
         "profile": "profiles/k_batch9_batched_sweep_fp32.md",
     },
     ("kolmogorov96", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 311, "fp64_flops_per_node": 448,
-        "traffic_bytes_per_launch": (191.164416 + 138.094592) * 1e6, "traffic_src_sha": "229967383d07e4e6",
+        "fp64_inst_per_node": 287, "fp64_flops_per_node": 396,
+        "traffic_bytes_per_launch": (191.157248 + 137.669632) * 1e6, "traffic_src_sha": "4a93369e8810592c",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("channel2048", "fp64"): {
         "src": [_C + "k_d2q9.cu"] + _H,
-        "fp64_inst_per_node": 132, "fp64_flops_per_node": 176,
-        "traffic_bytes_per_launch": (151.017472 + 103.077120) * 1e6, "traffic_src_sha": "203f25328b41ef91",
+        "fp64_inst_per_node": 85, "fp64_flops_per_node": 116,
+        "traffic_bytes_per_launch": (151.035392 + 100.336128) * 1e6, "traffic_src_sha": "1faf847cd140a813",
         "profile": "profiles/k_step_d2q9_channel2048_fp64.md",
+    },
+    ("channel2048", "fp32"): {
+        "src": [_C + "k_rp.cu"] + _H,
+        "traffic_bytes_per_launch": (75.510784 + 29.308160) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "profile": "profiles/k_step9_channel2048_fp32.md",
     },
     ("duct15_96", "fp64"): {
         "src": [_C + "k_d3q15.cu", _C + "lbm_d3q15.cuh"] + _H,
         "fp64_inst_per_node": 234, "fp64_flops_per_node": 321,
-        "traffic_bytes_per_launch": (106.208256 + 59.245312) * 1e6, "traffic_src_sha": "c08b40db6129f77b",
+        "traffic_bytes_per_launch": (106.206464 + 59.304704) * 1e6, "traffic_src_sha": "a985be2eb024ea08",
         "profile": "profiles/k_step_d3q15_duct_fp64.md",
     },
 }
 # The same kernels run the larger forms of these workloads (traffic scales with
 # the node count and is not carried over).
 for _w, _base, _st in (("kolmogorov256", "kolmogorov96", "fp64"), ("kolmogorov512", "kolmogorov96", "fp64"),
-                       ("duct15_128", "duct15_96", "fp64"), ("kolmogorov256", "kolmogorov96", "fp32"),
-                       ("kolmogorov512", "kolmogorov96", "fp32"), ("kolmogorov512", "kolmogorov96", "fp16"),
+                       ("duct15_128", "duct15_96", "fp64"), ("kolmogorov512", "kolmogorov96", "fp32"), ("kolmogorov512", "kolmogorov96", "fp16"),
+                       ("kolmogorov256", "kolmogorov96", "fp16"),
                        ("batched_sweep", "batched_sweep256", "fp32")):
     KERNEL_FACTS[(_w, _st)] = {k: v for k, v in KERNEL_FACTS[(_base, _st)].items()
                                if k != "traffic_bytes_per_launch"}
