@@ -68,13 +68,22 @@ struct lbm_batch {
     double *d_apre = nullptr;
     cudaEvent_t ev_apre = nullptr;     // recorded after the a_pre copy
     double *d_mom = nullptr;           // device staging of the packed output (host destinations)
-    // asynchronous packed readback (where = 2): two staging slots, copies on a
-    // private stream so that they overlap the next steps
+    // asynchronous packed readback (where = 2 / 3): two slots used in turn,
+    // kernel (and, for 2, copies) on a private stream so that they overlap
+    // the next steps
     double *d_momq[2] = {nullptr, nullptr};
     cudaStream_t cstream = nullptr;
-    cudaEvent_t ev_ready[2] = {nullptr, nullptr};   // slot filled (recorded on the batch stream)
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};  // slot copied out (recorded on the copy stream)
     cudaEvent_t ev_host[2] = {nullptr, nullptr};    // the fields of slot k are in host memory
+    // where >= 2 readbacks run their kernel on the copy stream, after the
+    // state it reads (ev_state on the batch stream) and overlapping the next
+    // step; ev_read[k] marks that slot k's kernel has read the populations
+    // (each member keeps it as a reader entry of the buffer it read)
+    cudaEvent_t ev_read[2] = {nullptr, nullptr};
+    bool read_recorded[2] = {false, false};
+    cudaEvent_t ev_state = nullptr;
+    double *h_apreq[2] = {nullptr, nullptr};  // pinned a_pre of each member, per slot
+    double *d_apreq[2] = {nullptr, nullptr};
     int qslot = 0;
     bool copies_pending = false;
     std::string err;
@@ -217,11 +226,21 @@ void lbm_batch_destroy(lbm_batch *b)
     cudaFreeHost(b->h_apre);
     cudaFree(b->d_mom);
     if (b->cstream) cudaStreamSynchronize(b->cstream);
+    // the readbacks are done: the members forget this batch's reader events
+    for (lbm_ctx *c : b->ctx)
+        for (int k = 0; k < 2; k++)
+            if (c->rd_buf[k] && (c->rd_ev[k] == b->ev_read[0] || c->rd_ev[k] == b->ev_read[1])) {
+                c->rd_buf[k] = nullptr;
+                c->rd_ev[k] = nullptr;
+            }
     for (int k = 0; k < 2; k++) {
         cudaFree(b->d_momq[k]);
-        if (b->ev_ready[k]) cudaEventDestroy(b->ev_ready[k]);
+        cudaFree(b->d_apreq[k]);
+        cudaFreeHost(b->h_apreq[k]);
         if (b->ev_copied[k]) cudaEventDestroy(b->ev_copied[k]);
+        if (b->ev_read[k]) cudaEventDestroy(b->ev_read[k]);
     }
+    if (b->ev_state) cudaEventDestroy(b->ev_state);
     if (b->cstream) cudaStreamDestroy(b->cstream);
     if (b->ev_apre) cudaEventDestroy(b->ev_apre);
     cudaFree(b->d_items);
@@ -251,6 +270,24 @@ bool has_envelope(const lbm_batch *b)
 
 // Make the device descriptors current; returns the buffer parity of the
 // current state relative to them (0 or 1) through *parity.
+// Before work on the batch stream writes the members' population buffers
+// (each member's second buffer, or both when `both`), make the stream wait for
+// the readbacks that may still read them (the members' reader entries; one
+// wait per distinct event).
+int wait_member_readers(lbm_batch *b, bool both)
+{
+    std::vector<cudaEvent_t> evs;
+    for (lbm_ctx *c : b->ctx)
+        for (int k = 0; k < 2; k++) {
+            if (!c->rd_buf[k] || (!both && c->rd_buf[k] != c->B)) continue;
+            if (std::find(evs.begin(), evs.end(), c->rd_ev[k]) == evs.end()) evs.push_back(c->rd_ev[k]);
+            c->rd_buf[k] = nullptr;
+            c->rd_ev[k] = nullptr;
+        }
+    for (cudaEvent_t e : evs) BCK(cudaStreamWaitEvent(b->stream, e, 0), "wait for a readback of the populations");
+    return LBM_OK;
+}
+
 int refresh_descriptors(lbm_batch *b, int *parity)
 {
     int p0 = 0;
@@ -272,6 +309,10 @@ int refresh_descriptors(lbm_batch *b, int *parity)
         b->gexec = nullptr;
     }
     BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
+    // readback kernels on the copy stream read the descriptors too
+    for (int k = 0; k < 2; k++)
+        if (b->read_recorded[k])
+            BCK(cudaStreamWaitEvent(b->stream, b->ev_read[k], 0), "lbm_batch_step: wait for a readback");
     for (int i = 0; i < b->count; i++) {
         const lbm_ctx *c = b->ctx[i];
         BatchItem &it = b->h_items[i];
@@ -457,6 +498,111 @@ int capture_graph(lbm_batch *b, int parity)
     return LBM_OK;
 }
 
+
+// where = 2 / 3 of lbm_batch_moments_packed: the moments kernel runs on the
+// copy stream after the state it reads (so it overlaps the next step on the
+// batch stream), then either copies the fields out of a device slot (2) or has
+// written them straight into mapped host memory (3).
+int packed_readback_async(lbm_batch *b, double *rho, double *u, int where, int half, int parity, size_t nrho,
+                          size_t nu)
+{
+    const bool scalar = b->lattice == LBM_D2Q5_CDE;
+    if (!b->cstream) {
+        BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
+        BCK(cudaEventCreateWithFlags(&b->ev_state, cudaEventDisableTiming), "event");
+        for (int k = 0; k < 2; k++) {
+            BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
+            BCK(cudaEventCreateWithFlags(&b->ev_read[k], cudaEventDisableTiming), "event");
+            BCK(cudaHostAlloc(&b->h_apreq[k], b->count * sizeof(double), cudaHostAllocDefault), "cudaHostAlloc(a_pre)");
+            BCK(cudaMalloc(&b->d_apreq[k], b->count * sizeof(double)), "cudaMalloc(a_pre)");
+        }
+    }
+    double *drho = nullptr, *du = nullptr;
+    if (where == 3) {
+        // host memory the device can address (pinned by cudaHostAlloc, or
+        // registered as mapped): the kernel writes the fields into it
+        double *outs[2] = {rho, u};
+        double *devs[2] = {nullptr, nullptr};
+        for (int k = 0; k < (scalar ? 1 : 2); k++) {
+            cudaPointerAttributes pa{};
+            const cudaError_t e = cudaPointerGetAttributes(&pa, outs[k]);
+            if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+                cudaGetLastError();
+                return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where = 3 needs host memory mapped into "
+                                            "the device's address space");
+            }
+            devs[k] = static_cast<double *>(pa.devicePointer);
+        }
+        drho = devs[0];
+        du = devs[1];
+    } else if (!b->d_momq[0]) {
+        for (int k = 0; k < 2; k++)
+            BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
+    }
+    const int slot = b->qslot;
+    b->qslot ^= 1;
+    // the slot's previous readback has finished: its a_pre staging (and device slot) can be reused
+    if (b->ev_host[slot]) BCK(cudaEventSynchronize(b->ev_host[slot]), "lbm_batch_moments_packed: wait for the slot");
+    if (where == 2) {
+        drho = b->d_momq[slot];
+        du = b->d_momq[slot] + nrho;
+    }
+    for (int i = 0; i < b->count; i++) {
+        double apre, apost;
+        lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t, apre, apost);
+        b->h_apreq[slot][i] = apre;
+    }
+    // order after the state on the batch stream; a member buffer already read
+    // by another batch's pending readback keeps that reader too (this copy
+    // stream waits for it, so the new reader event implies the old one)
+    BCK(cudaEventRecord(b->ev_state, b->stream), "lbm_batch_moments_packed: record");
+    BCK(cudaStreamWaitEvent(b->cstream, b->ev_state, 0), "lbm_batch_moments_packed: wait");
+    std::vector<cudaEvent_t> foreign;
+    for (lbm_ctx *c : b->ctx)
+        for (int k = 0; k < 2; k++)
+            if (c->rd_buf[k] == c->A && c->rd_ev[k] != b->ev_read[0] && c->rd_ev[k] != b->ev_read[1] &&
+                std::find(foreign.begin(), foreign.end(), c->rd_ev[k]) == foreign.end())
+                foreign.push_back(c->rd_ev[k]);
+    for (cudaEvent_t e : foreign) BCK(cudaStreamWaitEvent(b->cstream, e, 0), "lbm_batch_moments_packed: wait");
+    BCK(cudaMemcpyAsync(b->d_apreq[slot], b->h_apreq[slot], b->count * sizeof(double), cudaMemcpyHostToDevice,
+                        b->cstream),
+        "lbm_batch_moments_packed: copy a_pre");
+    BatchMoments M{};
+    M.items = b->d_items;
+    M.first = b->d_first[1];
+    M.count = b->count;
+    M.parity = parity;
+    M.half = half;
+    M.apre = b->d_apreq[slot];
+    M.off = b->d_off;
+    M.rho = drho;
+    M.u = du;
+    BCK(batch_moments(b->lattice, b->ctx[0]->storage, M, (int)b->ntiles[1], b->cstream),
+        "lbm_batch_moments_packed: kernel");
+    b->launches++;
+    BCK(cudaEventRecord(b->ev_read[slot], b->cstream), "lbm_batch_moments_packed: record");
+    b->read_recorded[slot] = true;
+    for (lbm_ctx *c : b->ctx) {
+        // one entry per buffer: the one already naming c->A, else a free one
+        const int k = c->rd_buf[0] == c->A ? 0 : (c->rd_buf[1] == c->A ? 1 : (c->rd_buf[0] ? 1 : 0));
+        c->rd_buf[k] = c->A;
+        c->rd_ev[k] = b->ev_read[slot];
+    }
+    if (where == 2) {
+        BCK(cudaMemcpyAsync(rho, drho, nrho * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
+            "lbm_batch_moments_packed: copy rho");
+        if (!scalar)
+            BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
+                "lbm_batch_moments_packed: copy u");
+        BCK(cudaEventRecord(b->ev_copied[slot], b->cstream), "lbm_batch_moments_packed: record");
+        b->ev_host[slot] = b->ev_copied[slot];
+    } else {
+        b->ev_host[slot] = b->ev_read[slot];
+    }
+    b->copies_pending = true;
+    return LBM_OK;
+}
+
 }  // namespace
 
 int lbm_batch_step(lbm_batch *b, long n)
@@ -468,6 +614,10 @@ int lbm_batch_step(lbm_batch *b, long n)
     if (n == 0) return LBM_OK;
     if (n > 2147483647L / b->count) return bfail(b, LBM_EINVAL, "lbm_batch_step: n too large");
     int rc = check_members(b, n, "lbm_batch_step");
+    if (rc != LBM_OK) return rc;
+    // one step writes each member's second buffer only (a readback of the
+    // current state may go on meanwhile); more steps write both
+    rc = wait_member_readers(b, n > 1);
     if (rc != LBM_OK) return rc;
     int parity = 0;
     rc = refresh_descriptors(b, &parity);
@@ -595,6 +745,8 @@ int lbm_batch_autotune(lbm_batch *b, int trial_steps, double *best_us, double *a
         return bfail(b, LBM_EINVAL, "lbm_batch_autotune: trial_steps must be in [1, 1000]");
     int rc = check_members(b, 1, "lbm_batch_autotune");
     if (rc != LBM_OK) return rc;
+    rc = wait_member_readers(b, true);
+    if (rc != LBM_OK) return rc;
     int parity = 0;
     rc = refresh_descriptors(b, &parity);
     if (rc != LBM_OK) return rc;
@@ -660,6 +812,10 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
     // Every member's fields are formed into its scratch buffer (the second
     // population buffer, or the staging buffer of a reduced-precision context)
     // and copied out on the shared stream; one synchronisation at the end.
+    if (where == 0) {
+        const int rc = wait_member_readers(b, false);
+        if (rc != LBM_OK) return rc;
+    }
     for (int i = 0; i < b->count; i++) {
         lbm_ctx *c = b->ctx[i];
         double apre, apost;
@@ -708,48 +864,12 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
     const int dim = b->ctx[0]->dim;
     const size_t nrho = (size_t)b->total_nodes, nu = scalar ? 0 : (size_t)dim * b->total_nodes;
     double *drho = rho, *du = u;
-    int slot = 0;
     if (where == 0) {
         if (!b->d_mom) BCK(cudaMalloc(&b->d_mom, (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
         drho = b->d_mom;
         du = b->d_mom + nrho;
     } else if (where >= 2) {
-        if (!b->cstream) {
-            BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
-            for (int k = 0; k < 2; k++) {
-                BCK(cudaEventCreateWithFlags(&b->ev_ready[k], cudaEventDisableTiming), "event");
-                BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
-            }
-        }
-        if (where == 3) {
-            // host memory the device can address (pinned by cudaHostAlloc, or
-            // registered as mapped): the kernel writes the fields into it
-            double *outs[2] = {rho, u};
-            double *devs[2] = {nullptr, nullptr};
-            for (int k = 0; k < (scalar ? 1 : 2); k++) {
-                cudaPointerAttributes pa{};
-                const cudaError_t e = cudaPointerGetAttributes(&pa, outs[k]);
-                if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
-                    cudaGetLastError();
-                    return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where = 3 needs host memory mapped into "
-                                                "the device's address space");
-                }
-                devs[k] = static_cast<double *>(pa.devicePointer);
-            }
-            drho = devs[0];
-            du = devs[1];
-        } else if (!b->d_momq[0]) {
-            for (int k = 0; k < 2; k++)
-                BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
-        }
-        slot = b->qslot;
-        b->qslot ^= 1;
-        if (where == 2) {
-            // the slot's previous copy must have left it before the kernel refills it
-            BCK(cudaStreamWaitEvent(b->stream, b->ev_copied[slot], 0), "lbm_batch_moments_packed: wait");
-            drho = b->d_momq[slot];
-            du = b->d_momq[slot] + nrho;
-        }
+        return packed_readback_async(b, rho, u, where, half_forced ? 1 : 0, parity, nrho, nu);
     }
     // a_pre of each member's current step; the previous copy has read the pinned slot by ev_apre
     BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
@@ -781,21 +901,6 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
             BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
                 "lbm_batch_moments_packed: copy u");
         BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments_packed");
-    } else if (where == 2) {
-        BCK(cudaEventRecord(b->ev_ready[slot], b->stream), "lbm_batch_moments_packed: record");
-        BCK(cudaStreamWaitEvent(b->cstream, b->ev_ready[slot], 0), "lbm_batch_moments_packed: wait");
-        BCK(cudaMemcpyAsync(rho, drho, nrho * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
-            "lbm_batch_moments_packed: copy rho");
-        if (!scalar)
-            BCK(cudaMemcpyAsync(u, du, nu * sizeof(double), cudaMemcpyDeviceToHost, b->cstream),
-                "lbm_batch_moments_packed: copy u");
-        BCK(cudaEventRecord(b->ev_copied[slot], b->cstream), "lbm_batch_moments_packed: record");
-        b->ev_host[slot] = b->ev_copied[slot];
-        b->copies_pending = true;
-    } else if (where == 3) {
-        BCK(cudaEventRecord(b->ev_ready[slot], b->stream), "lbm_batch_moments_packed: record");
-        b->ev_host[slot] = b->ev_ready[slot];
-        b->copies_pending = true;
     }
     return LBM_OK;
 }

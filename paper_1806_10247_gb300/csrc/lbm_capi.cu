@@ -41,6 +41,18 @@ int cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
     return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+int wait_readers(lbm_ctx *c, const void *buf)
+{
+    for (int k = 0; k < 2; k++) {
+        if (!c->rd_buf[k] || (buf && c->rd_buf[k] != buf)) continue;
+        const cudaError_t e = cudaStreamWaitEvent(c->stream, c->rd_ev[k], 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "wait for a readback of the populations");
+        c->rd_buf[k] = nullptr;
+        c->rd_ev[k] = nullptr;
+    }
+    return LBM_OK;
+}
+
 #define CK(call, what) LBM_CK(call, what)
 
 int lattice_q(int lattice)
@@ -303,6 +315,8 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
 void lbm_destroy(lbm_ctx *c)
 {
     if (!c) return;
+    for (int k = 0; k < 2; k++)
+        if (c->rd_buf[k]) cudaEventSynchronize(c->rd_ev[k]);
     if (c->stream || c->A) cudaStreamSynchronize(c->stream);
     cudaFree(c->A);
     cudaFree(c->B);
@@ -328,6 +342,10 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
     c->err.clear();
     if (c->lattice != LBM_D2Q5_CDE && rho == nullptr && !(rho0 > 0.0))
         return fail(c, LBM_EINVAL, "lbm_init_equilibrium: rho0 must be positive");
+    {
+        const int rc = wait_readers(c, nullptr);
+        if (rc != LBM_OK) return rc;
+    }
     double uu[3] = {0.0, 0.0, 0.0};
     if (u0)
         for (int d = 0; d < c->dim; d++) uu[d] = u0[d];
@@ -431,6 +449,12 @@ int lbm_step(lbm_ctx *c, long n)
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step: populations not initialised");
     if (!envelope_covers(c, c->t, n))
         return fail(c, LBM_EINVAL, "lbm_step: steps %ld..%ld are outside the envelope table", c->t, c->t + n);
+    if (n == 0) return LBM_OK;
+    {
+        // one step writes the second buffer only; more steps write both
+        const int rc = wait_readers(c, n == 1 ? c->B : nullptr);
+        if (rc != LBM_OK) return rc;
+    }
     if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty()) {
         // a small lattice with a constant force: all n steps in one cluster launch
         double *out = (n & 1) ? c->B : c->A;
@@ -495,6 +519,9 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
             int rc = ensure_stage(c);
             if (rc != LBM_OK) return rc;
             st = c->stage;
+        } else {
+            const int rc = wait_readers(c, c->B);
+            if (rc != LBM_OK) return rc;
         }
         drho = st;
         du = st + N;
@@ -515,6 +542,8 @@ int lbm_debug_poison(lbm_ctx *c)
 {
     if (!c) return LBM_EINVAL;
     c->err.clear();
+    const int rc = wait_readers(c, c->B);
+    if (rc != LBM_OK) return rc;
     // all-ones bytes are a NaN in every storage type (FP64, FP32, FP16, BF16)
     CK(cudaMemsetAsync(c->B, 0xFF, (size_t)c->q * c->g.Np * c->elem, c->stream), "poison");
     return LBM_OK;
@@ -536,6 +565,8 @@ int lbm_strain_rate(lbm_ctx *c, double rho0, double *S, int where)
     const int ncomp = c->dim == 2 ? 3 : 6;
     double *dst = S;
     if (where == 0) {
+        const int rw = wait_readers(c, c->B);
+        if (rw != LBM_OK) return rw;
         dst = c->B;
         if (c->storage != LBM_FP64) {
             int rc = ensure_stage(c);
@@ -594,6 +625,10 @@ int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, doub
     envelope_pair(flow, flow->t, apre, apost);
     LaunchArgs a = launch_args(flow, flow->A, nullptr, apre, apost);
     double *tmp = flow->B;
+    if (flow->storage == LBM_FP64) {
+        const int rw = wait_readers(flow, flow->B);
+        if (rw != LBM_OK) return fail(scalar, rw, "lbm_set_source_from_strain: %s", flow->err.c_str());
+    }
     if (flow->storage != LBM_FP64) {
         int rc = ensure_stage(flow);
         if (rc != LBM_OK) return fail(scalar, rc, "lbm_set_source_from_strain: %s", flow->err.c_str());
@@ -662,6 +697,10 @@ int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where)
         }
         return LBM_OK;
     }
+    {
+        const int rc = wait_readers(c, c->B);
+        if (rc != LBM_OK) return rc;
+    }
     CK(gather_from_stored(c->lattice, c->g, c->A, c->B, c->stream), "gather kernel");
     c->launches++;
     CK(cudaMemcpy2DAsync(dst, N * sizeof(double), c->B, (size_t)c->g.Np * sizeof(double), N * sizeof(double),
@@ -677,6 +716,10 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
     c->err.clear();
     if (!src || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_set_populations: count must be q*N");
     if (step < 0) return fail(c, LBM_EINVAL, "lbm_set_populations: step < 0");
+    {
+        const int rc = wait_readers(c, nullptr);
+        if (rc != LBM_OK) return rc;
+    }
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->storage != LBM_FP64) {

@@ -46,6 +46,12 @@ struct lbm_ctx {
     double *red_out = nullptr;
     long long launches = 0;
     long long version = 0;  // bumped by every change a batch descriptor depends on
+    // Readback kernels queued on another stream (a batch's copy stream) that
+    // may still read a population buffer: entry k says that buffer rd_buf[k]
+    // is read until event rd_ev[k] completes.  Work on this context's stream
+    // that writes a buffer waits for its entry first (lbmc::wait_readers).
+    const void *rd_buf[2] = {nullptr, nullptr};
+    cudaEvent_t rd_ev[2] = {nullptr, nullptr};
     std::string err;
 };
 
@@ -70,6 +76,9 @@ void envelope_pair(const lbm_ctx *c, long t, double &apre, double &apost);
 bool envelope_covers(const lbm_ctx *c, long t, long n);
 // Reduced-precision contexts: allocate the FP64 host-I/O staging buffer on first use.
 int ensure_stage(lbm_ctx *c);
+// Before work on c's stream writes population buffer `buf` (nullptr: either
+// buffer), make the stream wait for the readbacks that may still read it.
+int wait_readers(lbm_ctx *c, const void *buf);
 // Launch arguments of the context's kernels.
 lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
 

@@ -363,9 +363,10 @@ def test_full_batched_sweep_in_the_bench_configuration():
 
 @pytest.mark.parametrize("where", [2, 3])
 def test_asynchronous_packed_readback_double_buffered(where):
-    """where = 2: the copies overlap later steps; where = 3: the kernel writes
-    the pinned host buffers directly.  After wait_moments the host buffers
-    hold exactly the fields of the step they were queued at."""
+    """where = 2: kernel and copies on the library's copy stream; where = 3:
+    the kernel writes the pinned host buffers directly.  Both overlap the next
+    step.  After wait_moments the host buffers hold exactly the fields of the
+    step they were queued at."""
     import torch
 
     ws, fulls = _members("d2q9")
@@ -398,3 +399,15 @@ def test_asynchronous_packed_readback_double_buffered(where):
         r_np, u_np = np.empty(n), np.empty(2 * n)
         with pytest.raises(lbm.LBMError):
             B.moments_packed_into(r_np.ctypes.data, u_np.ctypes.data, where=3)
+    # member-level work while a readback may still read the populations: the
+    # readback sees the state it was queued at, the members their own work
+    r_, u_ = bufs[0]
+    B.moments_packed_into(r_.data_ptr(), u_.data_ptr(), where=where)
+    expect = T.moments_packed()
+    Gs[0].step(2)
+    Gs[1].set_populations(Gs[1].get_populations(), step=Gs[1].t)
+    Gs[2].debug_poison()
+    B.wait_moments(keep=0)
+    assert np.array_equal(r_.numpy(), expect[0]) and np.array_equal(u_.numpy(), expect[1])
+    twins[0].step(2)
+    assert np.array_equal(Gs[0].get_populations(), twins[0].get_populations())
