@@ -374,10 +374,12 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
  * pageable memory), LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced);
 
-/* Wait for the asynchronous readbacks (where = 2 or 3): keep = 0 waits for all
- * of them, keep = 1 for all but the most recent one (double buffering: the
- * previous step's fields are in host memory while the latest one is still
- * on its way).  Errors: LBM_EINVAL, LBM_ECUDA. */
+/* Wait for the asynchronous readbacks (where = 2 or 3), of which up to three
+ * are in flight (the library uses three slots in turn): keep = 0 waits for
+ * all of them, keep = 1 or 2 for all but the `keep` most recent ones (the
+ * caller's host buffers then rotate among keep + 1 or more destinations; the
+ * fields of the older readbacks are in host memory while the latest ones are
+ * still on their way).  Errors: LBM_EINVAL (keep outside 0..2), LBM_ECUDA. */
 int lbm_batch_wait_moments(lbm_batch *b, int keep);
 
 /* Graph replays issued so far. */

@@ -36,7 +36,7 @@ __device__ __forceinline__ void member_moments(const BatchItem &B, const BatchMo
         m0 += B.rho_ref;  // the rest state carries no momentum
     }
     const bool forced = M.half && B.fkind != FK_NONE;
-    const double apre = __ldg(M.apre + it);
+    const double apre = M.apre ? __ldg(M.apre + it) : M.apre_inl[it];
     const long long off = __ldg(M.off + it);
     if (L::Q == 5) {
         M.rho[off + i] = forced ? m0 + 0.5 * (apre * field_value(B.F, B.fkind, 0, x, y, z, i)) : m0;

@@ -28,6 +28,10 @@
 
 using namespace lbmk;
 
+// Asynchronous packed readbacks use their slots in turn (host destination,
+// device staging, a_pre staging, events), so up to three can be in flight.
+constexpr int kReadbackSlots = 3;
+
 struct lbm_batch {
     std::vector<lbm_ctx *> ctx;
     int lattice = 0;
@@ -71,20 +75,20 @@ struct lbm_batch {
     // asynchronous packed readback (where = 2 / 3): two slots used in turn,
     // kernel (and, for 2, copies) on a private stream so that they overlap
     // the next steps
-    double *d_momq[2] = {nullptr, nullptr};
+    double *d_momq[kReadbackSlots] = {};
     cudaStream_t cstream = nullptr;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr};  // slot copied out (recorded on the copy stream)
-    cudaEvent_t ev_host[2] = {nullptr, nullptr};    // the fields of slot k are in host memory
+    cudaEvent_t ev_copied[kReadbackSlots] = {};  // slot copied out (recorded on the copy stream)
+    cudaEvent_t ev_host[kReadbackSlots] = {};    // the fields of slot k are in host memory
     // where >= 2 readbacks run their kernel on the copy stream, after the
     // state it reads (ev_state on the batch stream) and overlapping the next
     // step; ev_read[k] marks that slot k's kernel has read the populations
     // (each member keeps it as a reader entry of the buffer it read)
-    cudaEvent_t ev_read[2] = {nullptr, nullptr};
-    bool read_recorded[2] = {false, false};
+    cudaEvent_t ev_read[kReadbackSlots] = {};
+    bool read_recorded[kReadbackSlots] = {};
     cudaEvent_t ev_state = nullptr;
-    double *h_apreq[2] = {nullptr, nullptr};  // pinned a_pre of each member, per slot
-    double *d_apreq[2] = {nullptr, nullptr};
-    int qslot = 0;
+    double *h_apreq[kReadbackSlots] = {};  // pinned a_pre of each member, per slot
+    double *d_apreq[kReadbackSlots] = {};
+    int qslot = 0;   // slot of the next readback (the slots are used in turn)
     bool copies_pending = false;
     std::string err;
 };
@@ -137,6 +141,14 @@ int grow_pairs(lbm_batch *b, int s, size_t need)
     BCK(cudaMalloc(&b->d_pairs[s], cap * sizeof(double2)), "cudaMalloc(pairs)");
     b->pairs_cap[s] = cap;
     return LBM_OK;
+}
+
+// Is e one of this batch's readback events?
+bool is_own_reader(const lbm_batch *b, cudaEvent_t e)
+{
+    for (int k = 0; k < kReadbackSlots; k++)
+        if (e == b->ev_read[k]) return true;
+    return false;
 }
 
 }  // namespace
@@ -229,11 +241,11 @@ void lbm_batch_destroy(lbm_batch *b)
     // the readbacks are done: the members forget this batch's reader events
     for (lbm_ctx *c : b->ctx)
         for (int k = 0; k < 2; k++)
-            if (c->rd_buf[k] && (c->rd_ev[k] == b->ev_read[0] || c->rd_ev[k] == b->ev_read[1])) {
+            if (c->rd_buf[k] && is_own_reader(b, c->rd_ev[k])) {
                 c->rd_buf[k] = nullptr;
                 c->rd_ev[k] = nullptr;
             }
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < kReadbackSlots; k++) {
         cudaFree(b->d_momq[k]);
         cudaFree(b->d_apreq[k]);
         cudaFreeHost(b->h_apreq[k]);
@@ -310,7 +322,7 @@ int refresh_descriptors(lbm_batch *b, int *parity)
     }
     BCK(cudaEventSynchronize(b->ev_items), "lbm_batch_step: wait for descriptor staging");
     // readback kernels on the copy stream read the descriptors too
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < kReadbackSlots; k++)
         if (b->read_recorded[k])
             BCK(cudaStreamWaitEvent(b->stream, b->ev_read[k], 0), "lbm_batch_step: wait for a readback");
     for (int i = 0; i < b->count; i++) {
@@ -510,7 +522,7 @@ int packed_readback_async(lbm_batch *b, double *rho, double *u, int where, int h
     if (!b->cstream) {
         BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
         BCK(cudaEventCreateWithFlags(&b->ev_state, cudaEventDisableTiming), "event");
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < kReadbackSlots; k++) {
             BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
             BCK(cudaEventCreateWithFlags(&b->ev_read[k], cudaEventDisableTiming), "event");
             BCK(cudaHostAlloc(&b->h_apreq[k], b->count * sizeof(double), cudaHostAllocDefault), "cudaHostAlloc(a_pre)");
@@ -536,21 +548,27 @@ int packed_readback_async(lbm_batch *b, double *rho, double *u, int where, int h
         drho = devs[0];
         du = devs[1];
     } else if (!b->d_momq[0]) {
-        for (int k = 0; k < 2; k++)
+        for (int k = 0; k < kReadbackSlots; k++)
             BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
     }
     const int slot = b->qslot;
-    b->qslot ^= 1;
-    // the slot's previous readback has finished: its a_pre staging (and device slot) can be reused
-    if (b->ev_host[slot]) BCK(cudaEventSynchronize(b->ev_host[slot]), "lbm_batch_moments_packed: wait for the slot");
+    b->qslot = (b->qslot + 1) % kReadbackSlots;
+    // a_pre of each member: in the launch arguments for small batches, else
+    // through the slot's pinned staging, which the slot's previous readback
+    // must have finished with
+    const bool inl = b->count <= kInlinePairs;
+    if (!inl && b->ev_host[slot])
+        BCK(cudaEventSynchronize(b->ev_host[slot]), "lbm_batch_moments_packed: wait for the slot");
     if (where == 2) {
         drho = b->d_momq[slot];
         du = b->d_momq[slot] + nrho;
     }
+    BatchMoments M{};
     for (int i = 0; i < b->count; i++) {
         double apre, apost;
         lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t, apre, apost);
-        b->h_apreq[slot][i] = apre;
+        if (inl) M.apre_inl[i] = apre;
+        else b->h_apreq[slot][i] = apre;
     }
     // order after the state on the batch stream; a member buffer already read
     // by another batch's pending readback keeps that reader too (this copy
@@ -560,20 +578,20 @@ int packed_readback_async(lbm_batch *b, double *rho, double *u, int where, int h
     std::vector<cudaEvent_t> foreign;
     for (lbm_ctx *c : b->ctx)
         for (int k = 0; k < 2; k++)
-            if (c->rd_buf[k] == c->A && c->rd_ev[k] != b->ev_read[0] && c->rd_ev[k] != b->ev_read[1] &&
+            if (c->rd_buf[k] == c->A && !is_own_reader(b, c->rd_ev[k]) &&
                 std::find(foreign.begin(), foreign.end(), c->rd_ev[k]) == foreign.end())
                 foreign.push_back(c->rd_ev[k]);
     for (cudaEvent_t e : foreign) BCK(cudaStreamWaitEvent(b->cstream, e, 0), "lbm_batch_moments_packed: wait");
-    BCK(cudaMemcpyAsync(b->d_apreq[slot], b->h_apreq[slot], b->count * sizeof(double), cudaMemcpyHostToDevice,
-                        b->cstream),
-        "lbm_batch_moments_packed: copy a_pre");
-    BatchMoments M{};
+    if (!inl)
+        BCK(cudaMemcpyAsync(b->d_apreq[slot], b->h_apreq[slot], b->count * sizeof(double), cudaMemcpyHostToDevice,
+                            b->cstream),
+            "lbm_batch_moments_packed: copy a_pre");
     M.items = b->d_items;
     M.first = b->d_first[1];
     M.count = b->count;
     M.parity = parity;
     M.half = half;
-    M.apre = b->d_apreq[slot];
+    M.apre = inl ? nullptr : b->d_apreq[slot];
     M.off = b->d_off;
     M.rho = drho;
     M.u = du;
@@ -871,23 +889,28 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
     } else if (where >= 2) {
         return packed_readback_async(b, rho, u, where, half_forced ? 1 : 0, parity, nrho, nu);
     }
-    // a_pre of each member's current step; the previous copy has read the pinned slot by ev_apre
-    BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
+    // a_pre of each member's current step: in the launch arguments for small
+    // batches, else through pinned staging (the previous copy has read it by ev_apre)
+    BatchMoments M{};
+    const bool inl = b->count <= kInlinePairs;
+    if (!inl) BCK(cudaEventSynchronize(b->ev_apre), "lbm_batch_moments_packed: wait for the previous copy");
     for (int i = 0; i < b->count; i++) {
         double apre, apost;
         lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t, apre, apost);
-        b->h_apre[i] = apre;
+        if (inl) M.apre_inl[i] = apre;
+        else b->h_apre[i] = apre;
     }
-    BCK(cudaMemcpyAsync(b->d_apre, b->h_apre, b->count * sizeof(double), cudaMemcpyHostToDevice, b->stream),
-        "lbm_batch_moments_packed: copy a_pre");
-    BCK(cudaEventRecord(b->ev_apre, b->stream), "lbm_batch_moments_packed: record");
-    BatchMoments M{};
+    if (!inl) {
+        BCK(cudaMemcpyAsync(b->d_apre, b->h_apre, b->count * sizeof(double), cudaMemcpyHostToDevice, b->stream),
+            "lbm_batch_moments_packed: copy a_pre");
+        BCK(cudaEventRecord(b->ev_apre, b->stream), "lbm_batch_moments_packed: record");
+    }
     M.items = b->d_items;
     M.first = b->d_first[1];
     M.count = b->count;
     M.parity = parity;
     M.half = half_forced ? 1 : 0;
-    M.apre = b->d_apre;
+    M.apre = inl ? nullptr : b->d_apre;
     M.off = b->d_off;
     M.rho = drho;
     M.u = du;
@@ -909,15 +932,16 @@ int lbm_batch_wait_moments(lbm_batch *b, int keep)
 {
     if (!b) return LBM_EINVAL;
     b->err.clear();
-    if (keep != 0 && keep != 1) return bfail(b, LBM_EINVAL, "lbm_batch_wait_moments: keep must be 0 or 1");
+    if (keep < 0 || keep >= kReadbackSlots)
+        return bfail(b, LBM_EINVAL, "lbm_batch_wait_moments: keep must be 0, 1 or 2");
     if (!b->copies_pending) return LBM_OK;
-    // the slots alternate: qslot is the slot of the readback before the latest
-    const int older = b->qslot, latest = b->qslot ^ 1;
-    if (b->ev_host[older]) BCK(cudaEventSynchronize(b->ev_host[older]), "lbm_batch_wait_moments");
-    if (keep == 0) {
-        if (b->ev_host[latest]) BCK(cudaEventSynchronize(b->ev_host[latest]), "lbm_batch_wait_moments");
-        b->copies_pending = false;
+    // the slots are used in turn: qslot is the oldest, qslot - 1 the latest;
+    // wait for all but the `keep` most recent readbacks
+    for (int age = kReadbackSlots - 1; age >= keep; age--) {
+        const int slot = (b->qslot + kReadbackSlots - 1 - age) % kReadbackSlots;
+        if (b->ev_host[slot]) BCK(cudaEventSynchronize(b->ev_host[slot]), "lbm_batch_wait_moments");
     }
+    if (keep == 0) b->copies_pending = false;
     return LBM_OK;
 }
 

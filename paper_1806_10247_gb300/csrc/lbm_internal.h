@@ -95,7 +95,8 @@ struct BatchMoments {
     int count;
     int parity;              // buffer parity of the current state relative to the descriptors
     int half;                // add the pre-collision half force / source
-    const double *apre;      // a_pre of each member's current step
+    const double *apre;      // a_pre of each member's current step (device), or NULL:
+    double apre_inl[kInlinePairs];  // ... then here (batches of at most kInlinePairs members)
     const long long *off;    // first node of each member in the packed output
     double *rho;             // [sum N_i]
     double *u;               // [sum dim N_i], member i's [dim][N_i] block at dim * off_i

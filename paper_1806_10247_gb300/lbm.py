@@ -425,7 +425,7 @@ class Batch:
 
     def wait_moments(self, keep=0):
         """Wait for asynchronous readbacks (where = 2 or 3): all (keep = 0) or
-        all but the most recent one (keep = 1)."""
+        all but the `keep` most recent ones (keep = 1 or 2)."""
         self._check(self._L.lbm_batch_wait_moments(self.h, int(keep)))
 
     def moments_packed(self, half_forced=True):

@@ -324,6 +324,70 @@ def test_packed_moments_equal_member_moments():
                 off += G.N
 
 
+@pytest.mark.parametrize("where", [2, 3])
+def test_readbacks_three_in_flight(where):
+    """Three host buffers in turn, wait_moments(keep=2) each step: the buffer
+    of step k - 2 is complete while two later readbacks may still be on their
+    way; a keep outside 0..2 is refused."""
+    import torch
+
+    ws, fulls = _members("d2q5")
+    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+    twins = [_make(w, f) for w, f in zip(ws, fulls)]
+    B, T = lbm.Batch(Gs), lbm.Batch(twins)
+    n = sum(G.N for G in Gs)
+    bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    history = []
+    for k in range(8):
+        B.step(1)
+        T.step(1)
+        history.append(T.moments_packed()[0])
+        B.moments_packed_into(bufs[k % 3].data_ptr(), None, where=where)
+        B.wait_moments(keep=2)
+        if k >= 2:
+            assert np.array_equal(bufs[(k - 2) % 3].numpy(), history[k - 2])
+    B.wait_moments(keep=0)
+    for k in (5, 6, 7):
+        assert np.array_equal(bufs[k % 3].numpy(), history[k])
+    for bad in (-1, 3):
+        with pytest.raises(lbm.LBMError):
+            B.wait_moments(keep=bad)
+    B.close()
+    T.close()
+
+
+def test_packed_moments_many_members_every_form():
+    """More members than travel in the launch arguments (their a_pre go
+    through a device table instead): every packed form equals the members'
+    own moments, the asynchronous ones after wait_moments."""
+    import torch
+
+    ws = [W.poiseuille(ny=5 + k % 7, nx=3 + k % 4, Fx=1e-5 * (1 + k)) for k in range(40)]
+    Gs = [lbm.from_workload(w) for w in ws]
+    B = lbm.Batch(Gs)
+    B.step(2)
+    n = sum(G.N for G in Gs)
+    want = [G.moments() for G in Gs]
+    for where in (0, 2, 3):
+        if where == 0:
+            rho, u = np.empty(n), np.empty(2 * n)
+            B.moments_packed_into(rho.ctypes.data, u.ctypes.data, where=0)
+        else:
+            rt = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            ut = torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
+            B.moments_packed_into(rt.data_ptr(), ut.data_ptr(), where=where)
+            B.wait_moments(keep=0)
+            rho, u = rt.numpy(), ut.numpy()
+        off = 0
+        for G, (r, v) in zip(Gs, want):
+            assert np.array_equal(rho[off:off + G.N], r)
+            assert np.array_equal(u[2 * off:2 * (off + G.N)].reshape(2, G.N), v)
+            off += G.N
+    B.close()
+    for G in Gs:
+        G.close()
+
+
 def test_full_batched_sweep_in_the_bench_configuration():
     """The bench's batched sweep (2048 D2Q9 channels + 2048 D2Q5 scalar
     lattices, FP32 deviations) in its launch configuration: autotuned tiling,
