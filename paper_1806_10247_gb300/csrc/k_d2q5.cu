@@ -87,8 +87,8 @@ Coef5 make_coef(const Rates5 &w, double ux, double uy)
 // g0 + S_pre/2), g'_a = sum_b M_ab g*_b + H0 for a = 1..4 and
 // g'_0 = sum_b M_0b g*_b + H0 - S_pre/2, with H0 = (S_pre + S_post)/10
 // (Eqs. 44-48).  M is formed once per launch on the host by applying Eqs. 41
-// and 48 to the unit vectors, so a node costs 25 multiply-adds plus the
-// source terms.
+// and 48 to the unit vectors; a node takes rows 1..4 (20 multiply-adds) and
+// the rest population from the zeroth moment (collide_mat).
 struct Mat5 {
     double m[25];
 };
@@ -114,23 +114,31 @@ Mat5 make_mat(const Coef5 &k)
 }
 
 //   ahalf = a_pre / 2;  hsum = (a_pre + a_post)/10;  P = source shape at the node (0 without one)
+// Rows 1..4 of the step matrix give g'_1..g'_4; the rest population comes
+// from the zeroth moment instead of row 0: sum_a g'_a = sum_a g_a + (S_pre +
+// S_post)/2 = sum_a g_a + 5 H0 (Eqs. 44-48), so g'_0 is that total minus the
+// other four.  The matrix entries are rounded on the host, so their column
+// sums differ from 1 by ~1e-16; taken through row 0 that would change the
+// total scalar by the same amount every step (1e-12 after ~10^4 steps).
 template <bool SRC>
 __device__ __forceinline__ void collide_mat(double (&g)[5], double P, double ahalf, double hsum, const double *M)
 {
+    const double phi0 = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
     double gs[5] = {g[0], g[1], g[2], g[3], g[4]};
-    double h = 0.0, h0 = 0.0;
+    double h = 0.0;
     if (SRC) {
         gs[0] = fma(ahalf, P, g[0]);
         h = hsum * P;
-        h0 = (hsum - ahalf) * P;
     }
 #pragma unroll
-    for (int a = 0; a < 5; a++) {
-        double acc = SRC ? (a == 0 ? h0 : h) : M[5 * a] * gs[0];
+    for (int a = 1; a < 5; a++) {
+        double acc = SRC ? fma(M[5 * a], gs[0], h) : M[5 * a] * gs[0];
 #pragma unroll
-        for (int b = SRC ? 0 : 1; b < 5; b++) acc = fma(M[5 * a + b], gs[b], acc);
+        for (int b = 1; b < 5; b++) acc = fma(M[5 * a + b], gs[b], acc);
         g[a] = acc;
     }
+    const double total = SRC ? fma(5.0, h, phi0) : phi0;
+    g[0] = total - ((g[1] + g[2]) + (g[3] + g[4]));
 }
 
 template <int SK>

@@ -131,6 +131,18 @@ def test_d2q5_cde_config_sweep_member_32():
     compare_state(G, R)
 
 
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_d2q5_cde_config_sweep_members_full_runs(N):
+    """Scalar sweep members N = 64, 128, 256 over their whole runs T_N (1,600,
+    6,400 and 25,600 steps), the whole grid compared at the end."""
+    c = W.cde_sweep_params(sizes=(N,))[0]
+    w = W.cde_workload(c)
+    G, R = _pair(w)
+    _advance(G, R, c.T)
+    assert G.t == c.T
+    compare_state(G, R)
+
+
 def test_d2q5_cde_config_512_full_grid():
     """The largest sweep member at full size, 20 steps, the whole grid compared."""
     c = W.cde_sweep_params(sizes=(512,))[0]
@@ -160,6 +172,16 @@ def test_d3q27_kolmogorov_small_100_steps():
     w = W.kolmogorov(shape=(24, 24, 24))
     G, R = _pair(w)
     _advance(G, R, 100)
+    compare_state(G, R)
+
+
+def test_d3q27_kolmogorov_1000_steps():
+    """Config 3's 1000-step run (seeded velocity noise, sinusoidal force) on a
+    32^3 grid, the whole state compared after the last step."""
+    w = W.kolmogorov(shape=(32, 32, 32))
+    G, R = _pair(w)
+    _advance(G, R, 1000)
+    assert G.t == 1000
     compare_state(G, R)
 
 
@@ -215,13 +237,13 @@ def _one_step_sampled(w, G, samples, seed, tol=1e-12):
 
 
 def test_d3q27_kolmogorov_256_full_size_sampled():
-    """Config 3 at 256^3 in the bench's launch configuration: 3 steps on the GPU,
-    then one more step checked on 300 sampled nodes by the oracle; plus exact
-    mass conservation and the momentum budget at full size."""
+    """Config 3 at 256^3 in the bench's launch configuration: 9 steps on the GPU,
+    then the 10th checked on 300 sampled nodes by the oracle; plus exact mass
+    conservation and the momentum budget at full size."""
     w = W.kolmogorov(n=256)
     G = lbm.from_workload(w)
     r0 = G.reduce()
-    G.step(3)
+    G.step(9)
     r1 = G.reduce()
     assert abs(r1[0] - r0[0]) <= 1e-12 * r0[0]
     # the Kolmogorov force sums to ~0 over y: total momentum changes only by roundoff
