@@ -47,8 +47,8 @@ _H = [_C + "lbm_lattices.cuh", _C + "lbm_device.cuh"]
 KERNEL_FACTS = {
     ("cde_sweep", "fp64"): {
         "src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H,
-        "fp64_inst_per_node": 30, "fp64_flops_per_node": 56,
-        "traffic_bytes_per_launch": 14.006528e6, "traffic_src_sha": "b69563316314b9cd",
+        "fp64_inst_per_node": 33, "fp64_flops_per_node": 55,
+        "traffic_bytes_per_launch": 14.007552e6, "traffic_src_sha": "26ceab1b36fcf385",
         "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md",
     },
     ("kolmogorov96", "fp32"): {
