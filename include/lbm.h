@@ -395,7 +395,7 @@ void lbm_batch_destroy(lbm_batch *b);
  *
  * The paper has no counterpart.  These kernels train and evaluate the small 3D
  * convolutional surrogate that predicts an initial velocity field for the LB
- * iteration (which stays the judge of the converged result).  All pointers are
+ * iteration (which alone decides the converged result).  All pointers are
  * device pointers; tensors are FP32 in [batch][channel][D][H][W] layout;
  * weights [Co][Ci][KD][KH][KW] are read as FP32 (w_bf16 = 0) or BF16
  * (w_bf16 = 1) and accumulated in FP32; kernels are odd, padding is "same"

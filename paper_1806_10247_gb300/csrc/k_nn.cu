@@ -3,7 +3,7 @@
 // FP32 in [batch][channel][D][H][W] layout; weights are read either as FP32 or
 // as BF16 (the trained network's storage form), always accumulated in FP32.
 // The paper has no counterpart: this supports the warm start of the LB
-// iteration, which itself stays the judge of the converged field.
+// iteration, which alone decides the converged field.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -5,7 +5,7 @@ body-force-driven square duct (x periodic, halfway bounce-back walls in y and
 z, F_x = F0 (1 + 0.5 sin(2 pi z / n))) from the force shape, the wall
 geometry and the relaxation time.  The prediction initialises the LB
 populations (equilibrium at the predicted velocity); the LB iteration then
-runs to the same convergence criterion as from rest and stays the judge of
+runs to the same convergence criterion as from rest and alone decides
 the converged field.
 
 Everything numeric runs in the library's CUDA kernels (``lbm_nn_*`` for the
