@@ -315,7 +315,7 @@ def warm_start_study(net: ConvNet, n: int, cases, tol=1e-10, storage=lbm.FP64):
     return out
 
 
-def study(n=64, train_count=192, test_count=8, iters=4000, seed=10247, gen_storage=lbm.FP32_DEV,
+def study(n=64, train_count=500, test_count=8, iters=4000, seed=10247, gen_storage=lbm.FP32_DEV,
           gen_tol=1e-7, tol=1e-10):
     """The full warm-start experiment: method-generated training fields (FP32
     storage, residual gen_tol), training on the GPU, then for held-out
