@@ -310,7 +310,7 @@ def config_block(wl, name, storage="fp64", elem=8):
     return c
 
 
-def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
+def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16")):
     """The metric's second half: wall time to the solution criterion.
     * config 1 (Poiseuille D2Q9 3 x 33), FP64: steps until
       max |u(t) - u(t-100)| < 1e-12 (checked every 100 steps with lbm_reduce);
@@ -321,8 +321,9 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
       relative l2 distance of u_x to u_ref is <= 1e-4 (checked every 100 steps,
       the checks inside the timed region);
     * config 2 (scalar sweep): every member run to its T_N, l2 error against the
-      closed form and the convergence order over the sweep."""
-    codes = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV}
+      closed form and the convergence order over the sweep, per storage form
+      (the 16-bit forms show how far their rounding moves the order)."""
+    codes = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
     out = {}
     w = W.poiseuille()
     ua = np.tile(W.poiseuille_parabola(w.shape[1], w.meta["tau"], w.meta["Fx"])[:, None], (1, w.shape[0])).reshape(-1)
@@ -370,7 +371,7 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32")):
                 break
         sec = time.perf_counter() - t0
         out[f"poiseuille_{st}_to_1e-4"] = {
-            "steps": steps, "seconds": sec, "l2_vs_fp64_steady": err,
+            "steps": steps, "seconds": sec, "l2_vs_fp64_steady": err, "reached": err <= 1e-4,
             "criterion": "relative l2 of u_x against the FP64 steady profile <= 1e-4 (lbm_moments every 100 steps)",
             "launch": how}
         if G is not None:
