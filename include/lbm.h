@@ -374,7 +374,22 @@ int lbm_batch_moments(lbm_batch *b, double *const *rho, double *const *u, int wh
  * pageable memory), LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, int half_forced);
 
-/* Wait for the asynchronous readbacks (where = 2 or 3), of which up to three
+/* One time step of every member (as lbm_batch_step(b, 1)) whose kernel also
+ * writes the packed fields of the state the step STARTS from — the fields
+ * lbm_batch_moments_packed(b, ..., half_forced) would have returned just
+ * before this call, bit for bit, in the same packed layout.  The step pulls
+ * exactly the populations those fields are sums of, so the readback costs the
+ * step a few operations per node and no separate kernel.  FP64 batches only.
+ * where = 1: device pointers; where = 3: host memory mapped into the device's
+ * address space (written over the host link).  Asynchronous on the batch's
+ * stream; the outputs are complete after lbm_batch_wait_moments (the call
+ * takes one of the three readback slots like where = 2 / 3 readbacks) or a
+ * synchronisation of the stream.  The state after the last call is read with
+ * lbm_batch_moments_packed.  Errors: LBM_EINVAL (NULL output, where not 1 or
+ * 3, reduced-precision batch, unmapped host memory), LBM_ESTATE, LBM_ECUDA. */
+int lbm_batch_step_read(lbm_batch *b, double *rho, double *u, int where, int half_forced);
+
+/* Wait for the asynchronous readbacks (where = 2 or 3, and lbm_batch_step_read), of which up to three
  * are in flight (the library uses three slots in turn): keep = 0 waits for
  * all of them, keep = 1 or 2 for all but the `keep` most recent ones (the
  * caller's host buffers then rotate among keep + 1 or more destinations; the

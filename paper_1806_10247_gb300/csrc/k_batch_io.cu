@@ -37,17 +37,7 @@ __device__ __forceinline__ void member_moments(const BatchItem &B, const BatchMo
     }
     const bool forced = M.half && B.fkind != FK_NONE;
     const double apre = M.apre ? __ldg(M.apre + it) : M.apre_inl[it];
-    const long long off = __ldg(M.off + it);
-    if (L::Q == 5) {
-        M.rho[off + i] = forced ? m0 + 0.5 * (apre * field_value(B.F, B.fkind, 0, x, y, z, i)) : m0;
-        return;
-    }
-    M.rho[off + i] = m0;
-#pragma unroll
-    for (int d = 0; d < L::DIM; d++) {
-        const double jd = forced ? j[d] + 0.5 * (apre * field_value(B.F, B.fkind, d, x, y, z, i)) : j[d];
-        M.u[L::DIM * off + (long long)d * g.N + i] = jd / m0;
-    }
+    store_fields<L>(m0, j, forced, apre, B.F, B.fkind, x, y, z, i, g.N, __ldg(M.off + it), M.rho, M.u);
 }
 
 template <class L, class T>

@@ -123,7 +123,7 @@ Mat5 make_mat(const Coef5 &k)
 template <bool SRC>
 __device__ __forceinline__ void collide_mat(double (&g)[5], double P, double ahalf, double hsum, const double *M)
 {
-    const double phi0 = ((g[0] + g[1]) + (g[2] + g[3])) + g[4];
+    const double phi0 = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];  // as zeroth_first sums it
     double gs[5] = {g[0], g[1], g[2], g[3], g[4]};
     double h = 0.0;
     if (SRC) {
@@ -214,6 +214,7 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xy(g, i, x, y);
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
+    if (L.mrho) fused_fields<LD2Q5>(B, L, it, i, x, y, 0, f, ap.x);
     if (B.vkind != FK_GENERAL) {
         if (B.fkind != FK_NONE)
             collide_mat<true>(f, field_value(B.F, B.fkind, 0, x, y, 0, i), 0.5 * ap.x, ap.y, B.mat);

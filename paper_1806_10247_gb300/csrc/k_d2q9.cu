@@ -246,6 +246,7 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xy(g, i, x, y);
     double f[9];
     load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
+    if (L.mrho) fused_fields<LD2Q9>(B, L, it, i, x, y, 0, f, ap.x);
     double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
     const int fk = B.fkind;
     if (fk != FK_NONE) {

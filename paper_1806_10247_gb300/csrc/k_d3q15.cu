@@ -152,6 +152,7 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xyz(g, i, x, y, z);
     double f[15];
     load_pulled<LD3Q15>(fin, g, x, y, z, i, f);
+    if (L.mrho) fused_fields<LD3Q15>(B, L, it, i, x, y, z, f, ap.x);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (B.fkind != FK_NONE) {
 #pragma unroll

@@ -269,6 +269,7 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xyz(g, i, x, y, z);
     double m[27];
     load_pulled<LD3Q27>(fin, g, x, y, z, i, m);
+    if (L.mrho) fused_fields<LD3Q27>(B, L, it, i, x, y, z, m, ap.x);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (B.fkind != FK_NONE) {
 #pragma unroll

@@ -511,6 +511,42 @@ int capture_graph(lbm_batch *b, int parity)
 }
 
 
+// Stream, events and staging of the asynchronous readbacks (on first use).
+int ensure_readback(lbm_batch *b)
+{
+    if (b->cstream) return LBM_OK;
+    BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
+    BCK(cudaEventCreateWithFlags(&b->ev_state, cudaEventDisableTiming), "event");
+    for (int k = 0; k < kReadbackSlots; k++) {
+        BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
+        BCK(cudaEventCreateWithFlags(&b->ev_read[k], cudaEventDisableTiming), "event");
+        BCK(cudaHostAlloc(&b->h_apreq[k], b->count * sizeof(double), cudaHostAllocDefault), "cudaHostAlloc(a_pre)");
+        BCK(cudaMalloc(&b->d_apreq[k], b->count * sizeof(double)), "cudaMalloc(a_pre)");
+    }
+    return LBM_OK;
+}
+
+// Device addresses of host outputs that the device can address (pinned by
+// cudaHostAlloc, or registered as mapped); refuses anything else.
+int mapped_outputs(lbm_batch *b, double *rho, double *u, double **drho, double **du, const char *what)
+{
+    const bool scalar = b->lattice == LBM_D2Q5_CDE;
+    double *outs[2] = {rho, u};
+    double *devs[2] = {nullptr, nullptr};
+    for (int k = 0; k < (scalar ? 1 : 2); k++) {
+        cudaPointerAttributes pa{};
+        const cudaError_t e = cudaPointerGetAttributes(&pa, outs[k]);
+        if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+            cudaGetLastError();
+            return bfail(b, LBM_EINVAL, "%s: where = 3 needs host memory mapped into the device's address space", what);
+        }
+        devs[k] = static_cast<double *>(pa.devicePointer);
+    }
+    *drho = devs[0];
+    *du = devs[1];
+    return LBM_OK;
+}
+
 // where = 2 / 3 of lbm_batch_moments_packed: the moments kernel runs on the
 // copy stream after the state it reads (so it overlaps the next step on the
 // batch stream), then either copies the fields out of a device slot (2) or has
@@ -519,34 +555,12 @@ int packed_readback_async(lbm_batch *b, double *rho, double *u, int where, int h
                           size_t nu)
 {
     const bool scalar = b->lattice == LBM_D2Q5_CDE;
-    if (!b->cstream) {
-        BCK(cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking), "copy stream");
-        BCK(cudaEventCreateWithFlags(&b->ev_state, cudaEventDisableTiming), "event");
-        for (int k = 0; k < kReadbackSlots; k++) {
-            BCK(cudaEventCreateWithFlags(&b->ev_copied[k], cudaEventDisableTiming), "event");
-            BCK(cudaEventCreateWithFlags(&b->ev_read[k], cudaEventDisableTiming), "event");
-            BCK(cudaHostAlloc(&b->h_apreq[k], b->count * sizeof(double), cudaHostAllocDefault), "cudaHostAlloc(a_pre)");
-            BCK(cudaMalloc(&b->d_apreq[k], b->count * sizeof(double)), "cudaMalloc(a_pre)");
-        }
-    }
+    int rc = ensure_readback(b);
+    if (rc != LBM_OK) return rc;
     double *drho = nullptr, *du = nullptr;
     if (where == 3) {
-        // host memory the device can address (pinned by cudaHostAlloc, or
-        // registered as mapped): the kernel writes the fields into it
-        double *outs[2] = {rho, u};
-        double *devs[2] = {nullptr, nullptr};
-        for (int k = 0; k < (scalar ? 1 : 2); k++) {
-            cudaPointerAttributes pa{};
-            const cudaError_t e = cudaPointerGetAttributes(&pa, outs[k]);
-            if (e != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
-                cudaGetLastError();
-                return bfail(b, LBM_EINVAL, "lbm_batch_moments_packed: where = 3 needs host memory mapped into "
-                                            "the device's address space");
-            }
-            devs[k] = static_cast<double *>(pa.devicePointer);
-        }
-        drho = devs[0];
-        du = devs[1];
+        rc = mapped_outputs(b, rho, u, &drho, &du, "lbm_batch_moments_packed");
+        if (rc != LBM_OK) return rc;
     } else if (!b->d_momq[0]) {
         for (int k = 0; k < kReadbackSlots; k++)
             BCK(cudaMalloc(&b->d_momq[k], (nrho + nu) * sizeof(double)), "cudaMalloc(packed moments)");
@@ -925,6 +939,57 @@ int lbm_batch_moments_packed(lbm_batch *b, double *rho, double *u, int where, in
                 "lbm_batch_moments_packed: copy u");
         BCK(cudaStreamSynchronize(b->stream), "lbm_batch_moments_packed");
     }
+    return LBM_OK;
+}
+
+int lbm_batch_step_read(lbm_batch *b, double *rho, double *u, int where, int half_forced)
+{
+    lbmc::NvtxRange nvtx_("lbm_batch_step_read");
+    if (!b) return LBM_EINVAL;
+    b->err.clear();
+    const bool scalar = b->lattice == LBM_D2Q5_CDE;
+    if (!rho || (!scalar && !u)) return bfail(b, LBM_EINVAL, "lbm_batch_step_read: NULL output");
+    if (where != 1 && where != 3) return bfail(b, LBM_EINVAL, "lbm_batch_step_read: where must be 1 or 3");
+    if (reduced_precision(b)) return bfail(b, LBM_EINVAL, "lbm_batch_step_read: FP64 batches only");
+    int rc = check_members(b, 1, "lbm_batch_step_read");
+    if (rc != LBM_OK) return rc;
+    rc = wait_member_readers(b, false);
+    if (rc != LBM_OK) return rc;
+    rc = ensure_readback(b);
+    if (rc != LBM_OK) return rc;
+    double *drho = rho, *du = u;
+    if (where == 3) {
+        rc = mapped_outputs(b, rho, u, &drho, &du, "lbm_batch_step_read");
+        if (rc != LBM_OK) return rc;
+    }
+    int parity = 0;
+    rc = refresh_descriptors(b, &parity);
+    if (rc != LBM_OK) return rc;
+    BatchLaunch L{};
+    L.items = b->d_items;
+    L.count = b->count;
+    L.k = 0;
+    L.parity = parity;
+    if (b->count <= kInlinePairs) inline_pairs_of_step(b, L, 0);
+    else if ((rc = stage_pairs(b, L, 1)) != LBM_OK) return rc;
+    L.mrho = drho;
+    L.mu = scalar ? nullptr : du;
+    L.moff = b->d_off;
+    L.mhalf = half_forced ? 1 : 0;
+    // the batched kernel even for a single member (the single-lattice kernel has no fused readback)
+    const cudaError_t e = launch_one(b, L, b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_step_read: kernel: %s", cudaGetErrorString(e));
+    b->launches++;
+    for (int i = 0; i < b->count; i++) {
+        lbm_ctx *c = b->ctx[i];
+        std::swap(c->A, c->B);
+        c->t += 1;
+    }
+    const int slot = b->qslot;
+    b->qslot = (b->qslot + 1) % kReadbackSlots;
+    BCK(cudaEventRecord(b->ev_read[slot], b->stream), "lbm_batch_step_read: record");
+    b->ev_host[slot] = b->ev_read[slot];
+    b->copies_pending = true;
     return LBM_OK;
 }
 

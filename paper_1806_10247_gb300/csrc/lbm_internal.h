@@ -86,6 +86,13 @@ struct BatchLaunch {
     // reduced-precision kernels read the same pairs in FP32
     const float2 *pairsf;
     float2 inlf[kInlinePairs];
+    // Fused readback (FP64 kernels, lbm_batch_step_read): when mrho is not
+    // NULL every node also writes the packed fields of the state its step
+    // starts from, member i at moff[i] (the layout of lbm_batch_moments_packed).
+    double *mrho;
+    double *mu;
+    const long long *moff;
+    int mhalf;
 };
 
 // Packed fields of every member of a batch (one launch, tiles of 256 nodes).

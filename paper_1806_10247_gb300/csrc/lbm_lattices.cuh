@@ -185,21 +185,45 @@ __device__ __forceinline__ void load_pulled_dev(const Planes<T, L::Q> &P, const 
     pull_node<L>(g, x, y, z, i, d, [&](int p, int k) { return Dev<T>::get(P.in[p] + k); });
 }
 
-// Zeroth and first moments of a node's populations.
+// Zeroth and first moments of a node's populations (summed in velocity order).
 template <class L>
 __device__ __forceinline__ void zeroth_first(const double (&f)[L::Q], double &m0, double (&j)[3])
 {
-    m0 = 0.0;
+    m0 = f[0];
     j[0] = j[1] = j[2] = 0.0;
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
-        m0 += f[a];
+        if (a > 0) m0 += f[a];
         if (L::ex(a) == 1) j[0] += f[a];
         if (L::ex(a) == -1) j[0] -= f[a];
         if (L::ey(a) == 1) j[1] += f[a];
         if (L::ey(a) == -1) j[1] -= f[a];
         if (L::ez(a) == 1) j[2] += f[a];
         if (L::ez(a) == -1) j[2] -= f[a];
+    }
+}
+
+// The packed fields of a node from its zeroth and first moments, as every
+// readback writes them: rho (phi for the scalar lattice) at rho[off + i],
+// velocity component d at u[dim * off + d * N + i]; with `forced` the
+// pre-collision half force / source a_pre P / 2 is included (Eq. 25 / 43).
+// Rounded operation by operation (no contraction), so that every kernel that
+// forms them gives the same bits.
+template <class L>
+__device__ __forceinline__ void store_fields(double m0, const double (&j)[3], bool forced, double apre, const FieldDev &F,
+                                             int fkind, int x, int y, int z, int i, int N, long long off, double *rho,
+                                             double *u)
+{
+    if (L::Q == 5) {
+        rho[off + i] = forced ? __dadd_rn(m0, __dmul_rn(0.5, __dmul_rn(apre, field_value(F, fkind, 0, x, y, z, i)))) : m0;
+        return;
+    }
+    rho[off + i] = m0;
+#pragma unroll
+    for (int d = 0; d < L::DIM; d++) {
+        const double jd =
+            forced ? __dadd_rn(j[d], __dmul_rn(0.5, __dmul_rn(apre, field_value(F, fkind, d, x, y, z, i)))) : j[d];
+        u[L::DIM * off + (long long)d * N + i] = __ddiv_rn(jd, m0);
     }
 }
 

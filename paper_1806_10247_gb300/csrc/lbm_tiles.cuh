@@ -69,6 +69,19 @@ __device__ __forceinline__ void batch_tiles(const BatchLaunch &L, Node node)
     }
 }
 
+// Fused readback of an FP64 batched step: the packed fields of the state the
+// step starts from, formed from the node's pulled populations f(t) exactly as
+// the packed readback kernel forms them.
+template <class L>
+__device__ __forceinline__ void fused_fields(const BatchItem &B, const BatchLaunch &Ln, int it, int i, int x, int y, int z,
+                                             const double (&f)[L::Q], double apre)
+{
+    double m0, j[3];
+    zeroth_first<L>(f, m0, j);
+    store_fields<L>(m0, j, Ln.mhalf && B.fkind != FK_NONE, apre, B.F, B.fkind, x, y, z, i, B.g.N, __ldg(Ln.moff + it),
+                    Ln.mrho, Ln.mu);
+}
+
 // Blocks of `kernel` (launched with tb threads) resident on the current GPU at once.
 template <class K>
 int resident_blocks(K kernel, int tb)

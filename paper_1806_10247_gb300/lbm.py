@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
            "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
-           "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison")
+           "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison", "lbm_batch_step_read")
 
 
 class LBMError(RuntimeError):
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True):
     L.lbm_batch_moments.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ip, ip]
     L.lbm_strain_rate.argtypes = [vp, ctypes.c_double, dp, ip]
     L.lbm_batch_moments_packed.argtypes = [vp, vp, vp, ip, ip]
+    L.lbm_batch_step_read.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_batch_wait_moments.argtypes = [vp, ip]
     L.lbm_debug_poison.argtypes = [vp]
     L.lbm_set_source_from_strain.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
@@ -422,6 +423,15 @@ class Batch:
         self._check(self._L.lbm_batch_moments_packed(self.h, ctypes.c_void_p(int(rho_ptr)),
                                                      None if u_ptr is None else ctypes.c_void_p(int(u_ptr)),
                                                      int(where), int(bool(half_forced))))
+
+    def step_read_into(self, rho_ptr, u_ptr=None, where=3, half_forced=True):
+        """One step of every member whose kernel also writes the packed fields
+        of the state it starts from (raw addresses: device when where = 1,
+        device-addressable pinned host memory when where = 3); asynchronous,
+        complete after wait_moments.  FP64 batches only."""
+        self._check(self._L.lbm_batch_step_read(self.h, ctypes.c_void_p(int(rho_ptr)),
+                                                None if u_ptr is None else ctypes.c_void_p(int(u_ptr)),
+                                                int(where), int(bool(half_forced))))
 
     def wait_moments(self, keep=0):
         """Wait for asynchronous readbacks (where = 2 or 3): all (keep = 0) or

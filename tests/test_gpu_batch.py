@@ -356,6 +356,64 @@ def test_readbacks_three_in_flight(where):
     T.close()
 
 
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+@pytest.mark.parametrize("where", [1, 3])
+def test_step_read_writes_the_fields_each_step_starts_from(kind, where):
+    """lbm_batch_step_read: each call steps the batch once and its kernel
+    writes the packed fields of the state the step started from, bit for bit
+    what lbm_batch_moments_packed returned just before (half-forced or not);
+    the stepped states equal plain batched steps bit for bit."""
+    import torch
+
+    ws, fulls = _members(kind)
+    Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+    twins = [_make(w, f) for w, f in zip(ws, fulls)]
+    B, T = lbm.Batch(Gs), lbm.Batch(twins)
+    n = sum(G.N for G in Gs)
+    dim = 0 if kind == "d2q5" else Gs[0].dim
+    kw = {"dtype": torch.float64}
+    kw.update({"device": "cuda"} if where == 1 else {"pin_memory": True})
+    bufs = [(torch.empty(n, **kw), torch.empty(max(dim, 1) * n, **kw)) for _ in range(3)]
+    for k in range(7):
+        half = k % 2 == 0
+        want = T.moments_packed(half_forced=half)
+        r_, u_ = bufs[k % 3]
+        B.step_read_into(r_.data_ptr(), u_.data_ptr() if dim else None, where=where, half_forced=half)
+        T.step(1)
+        B.wait_moments(keep=0)
+        torch.cuda.synchronize()
+        assert np.array_equal(r_.cpu().numpy(), want[0]), k
+        if dim:
+            assert np.array_equal(u_.cpu().numpy(), want[1]), k
+    for G, H in zip(Gs, twins):
+        assert G.t == H.t == 7
+        assert np.array_equal(G.get_populations(), H.get_populations())
+    with pytest.raises(lbm.LBMError):
+        B.step_read_into(bufs[0][0].data_ptr(), None if not dim else bufs[0][1].data_ptr(), where=2)
+    B.close()
+    T.close()
+
+
+def test_step_read_refuses_reduced_precision_and_pageable_memory():
+    import torch
+
+    ws, _ = _members("d2q5")
+    Gs = [lbm.from_workload(w, storage=lbm.FP32_DEV) for w in ws]
+    B = lbm.Batch(Gs)
+    n = sum(G.N for G in Gs)
+    d = torch.empty(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(lbm.LBMError):
+        B.step_read_into(d.data_ptr(), None, where=1)
+    B.close()
+    Hs = [lbm.from_workload(w) for w in ws]
+    C = lbm.Batch(Hs)
+    pageable = np.empty(n)
+    with pytest.raises(lbm.LBMError):
+        C.step_read_into(pageable.ctypes.data, None, where=3)
+    assert all(H.t == 0 for H in Hs)  # refused before stepping
+    C.close()
+
+
 def test_packed_moments_many_members_every_form():
     """More members than travel in the launch arguments (their a_pre go
     through a device table instead): every packed form equals the members'
