@@ -240,6 +240,22 @@ int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, doub
  * out is still written), LBM_ESTATE, LBM_ECUDA. */
 int lbm_reduce(lbm_ctx *ctx, double out[5]);
 
+/* Discrete relative l2 error of a macroscopic field against a reference,
+ * Eq. sca (Sec. 6.1, grid convergence study): sqrt(sum (q - q_ref)^2 /
+ * sum q_ref^2), the sums running over every node (and every component).
+ * q is the field lbm_moments returns with the same half_forced flag:
+ *   field 0: rho (flow) or phi (scalar), ref holds N doubles;
+ *   field 1: u (flow lattices only), ref holds dim*N doubles laid out [dim][N].
+ * ref is host memory (where = 0; copied in during the call) or device memory
+ * (where = 1), read only during the call.  Computed on the GPU in FP64 with a
+ * fixed reduction order (the same state and reference give the same bits):
+ *   out[0] = sum (q - q_ref)^2, out[1] = sum q_ref^2,
+ *   out[2] = sqrt(out[0] / out[1]); +inf when out[1] = 0 < out[0], 0 when both are 0.
+ * Uses the context's scratch buffer; synchronises the context's stream.
+ * Errors: LBM_EINVAL (NULL ref/out, where or field out of range, field 1 on
+ * the scalar lattice), LBM_ESTATE, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_l2_error(lbm_ctx *ctx, const double *ref, int where, int field, int half_forced, double out[3]);
+
 /* The sums out[0..3] of lbm_reduce (mass, then momentum) without allocating
  * any device memory.  The paper has no counterpart: this exists for callers
  * that cannot allocate when they want the sums, e.g. a process whose device
@@ -312,8 +328,10 @@ int lbm_batch_launch_count(const lbm_batch *b, long long *count);
  * of `tile` nodes (128, 256 or 512; one thread per node, `tile` threads per
  * block), numbered member after member.  persistent = 0: one block per tile;
  * persistent = 1: a grid of as many blocks as the GPU holds resident at once,
- * each block taking a contiguous run of tiles (so that it reloads a member's
- * descriptor only when the run crosses into the next member).  Default
+ * each block taking a contiguous run of tiles, the runs differing in length
+ * by at most one tile (a block reloads a member's descriptor only when its
+ * run crosses into the next member; the FP64 scalar-lattice kernel also
+ * loads each tile's operands while it computes the previous tile).  Default
  * 256 / 0.  The arithmetic per node does not depend on the tiling (up to the
  * compiler's multiply-add contraction in the different kernel instances).
  * A change drops a captured graph.  Errors: LBM_EINVAL. */

@@ -994,6 +994,38 @@ int lbmref_reduce(lbmref_ctx *c, double out[5])
     return unstable ? LBMREF_EUNSTABLE : LBMREF_OK;
 }
 
+int lbmref_l2_error(lbmref_ctx *c, const double *ref, int field, int half_forced, double out[3])
+{
+    if (!c || !ref || !out) return LBMREF_EINVAL;
+    const int flow = c->p.lattice != ORC_D2Q5;
+    if (field != 0 && !(field == 1 && flow)) return LBMREF_EINVAL;
+    if (!c->initialised) return LBMREF_ESTATE;
+    const long N = c->N;
+    double *rho = (double *)malloc((size_t)N * sizeof(double));
+    double *u = (double *)malloc((size_t)c->dim * N * sizeof(double));
+    if (!rho || !u) {
+        free(rho);
+        free(u);
+        return LBMREF_ENOMEM;
+    }
+    orc_moments(&c->p, c->f, half_forced ? c->P : NULL, a_pre_now(c), rho, u);
+    /* Eq. sca: the computed field u_c against the reference u_a, summed over
+       the flow domain (every node; every component of a vector field) */
+    const double *uc = field == 0 ? rho : u;
+    const long n = field == 0 ? N : (long)c->dim * N;
+    double num = 0.0, den = 0.0;
+    for (long k = 0; k < n; k++) {
+        num += (uc[k] - ref[k]) * (uc[k] - ref[k]);
+        den += ref[k] * ref[k];
+    }
+    free(rho);
+    free(u);
+    out[0] = num;
+    out[1] = den;
+    out[2] = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+    return LBMREF_OK;
+}
+
 int lbmref_get_populations(const lbmref_ctx *c, double *dst, size_t count)
 {
     if (!c || !dst || count != (size_t)c->q * (size_t)c->N) return LBMREF_EINVAL;

@@ -140,6 +140,12 @@ int lbmref_moments(lbmref_ctx *c, double *rho, double *u, int half_forced);
  * |u - u_prev| (|phi - phi_prev|) since the previous call, +inf on the first;
  * LBMREF_EUNSTABLE if a density is non-finite or (flow) not positive. */
 int lbmref_reduce(lbmref_ctx *c, double out[5]);
+/* Discrete relative l2 error of Eq. sca (Sec. 6.1) of a field of f(t) against
+ * a reference: field 0 = rho (phi for D2Q5), ref [N]; field 1 = u (flow),
+ * ref [dim][N]; half_forced as in lbmref_moments.  out[0] = sum over every
+ * node and component of (q - q_ref)^2, out[1] = sum q_ref^2, out[2] =
+ * sqrt(out[0] / out[1]) (+inf when out[1] = 0 < out[0], 0 when both are 0). */
+int lbmref_l2_error(lbmref_ctx *c, const double *ref, int field, int half_forced, double out[3]);
 int lbmref_get_populations(const lbmref_ctx *c, double *dst, size_t count);
 int lbmref_set_populations(lbmref_ctx *c, const double *src, size_t count, long step);
 int lbmref_get_step(const lbmref_ctx *c, long *step);

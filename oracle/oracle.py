@@ -97,12 +97,14 @@ def lib():
         L.lbmref_step.argtypes = [vp, ctypes.c_long]
         L.lbmref_moments.argtypes = [vp, dp, dp, ctypes.c_int]
         L.lbmref_reduce.argtypes = [vp, dp]
+        L.lbmref_l2_error.argtypes = [vp, dp, ctypes.c_int, ctypes.c_int, dp]
         L.lbmref_get_populations.argtypes = [vp, dp, ctypes.c_size_t]
         L.lbmref_set_populations.argtypes = [vp, dp, ctypes.c_size_t, ctypes.c_long]
         L.lbmref_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
         for fn in ("lbmref_create", "lbmref_init_equilibrium", "lbmref_set_force", "lbmref_set_source",
                    "lbmref_set_velocity", "lbmref_set_envelope", "lbmref_step", "lbmref_moments",
-                   "lbmref_reduce", "lbmref_get_populations", "lbmref_set_populations", "lbmref_get_step"):
+                   "lbmref_reduce", "lbmref_get_populations", "lbmref_set_populations", "lbmref_get_step",
+                   "lbmref_l2_error"):
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -321,6 +323,16 @@ class OracleContext:
     def reduce(self):
         out = np.empty(5)
         rc = lib().lbmref_reduce(self._h, _dp(out))
+        return rc, out
+
+    def l2_error(self, ref, field=0, half_forced=True):
+        """(rc, [sum (q - ref)^2, sum ref^2, relative l2 error]) of Eq. sca."""
+        ref = np.ascontiguousarray(ref, np.float64)
+        want = self.N * (1 if field == 0 else self.dim)
+        if ref.size != want:
+            return REF_EINVAL, None
+        out = np.empty(3)
+        rc = lib().lbmref_l2_error(self._h, _dp(ref), int(field), int(half_forced), _dp(out))
         return rc, out
 
     def populations(self):

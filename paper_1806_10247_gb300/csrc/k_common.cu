@@ -280,6 +280,20 @@ __global__ void __launch_bounds__(kBlock) k_reduce_final(const double *__restric
     block_reduce_store(v, out);
 }
 
+// Discrete l2 error terms of Eq. sca: per-block sums of (q - q_ref)^2 (slot 0)
+// and q_ref^2 (slot 1) over n values, grid-stride, fixed order.
+__global__ void __launch_bounds__(kBlock)
+k_l2_partial(const double *__restrict__ q, const double *__restrict__ ref, long long n, double *__restrict__ partials)
+{
+    double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long k = blockIdx.x * (long long)kBlock + threadIdx.x; k < n; k += (long long)gridDim.x * kBlock) {
+        const double r = ref[k], d = q[k] - r;
+        v[0] = fma(d, d, v[0]);
+        v[1] = fma(r, r, v[1]);
+    }
+    block_reduce_store(v, partials + (size_t)blockIdx.x * R_SLOTS);
+}
+
 // ---- reduced-precision storage: deviations d = f - w rho_ref in type T ----
 
 template <class L, class T>
@@ -599,6 +613,16 @@ int reduce_blocks(const Geom &g)
 {
     long long b = (g.N + kBlock - 1) / kBlock;
     return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);  // 152 SMs x 8 resident blocks
+}
+
+cudaError_t l2_terms(const double *q, const double *ref, long long n, double *partials, int nblocks, double *out,
+                     cudaStream_t s)
+{
+    k_l2_partial<<<nblocks, kBlock, 0, s>>>(q, ref, n, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, kBlock, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
 }
 
 cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,

@@ -199,7 +199,8 @@ void launch_v(const LaunchArgs &a, int grid, double hsum, const Rates5 &w)
                                                           a.V, a.apre, hsum, w);
 }
 
-// Batched form; pairs hold (a_pre, (a_pre + a_post)/10) per step and item.
+// Batched form; FP64 pairs hold (a_pre/2, (a_pre + a_post)/10) per step and
+// item (a_pre is halved on the host: one multiply fewer per node).
 // coef[0..11] = Coef5 of a uniform advecting velocity, coef[12..15] = Rates5,
 // mat = the step matrix of a uniform advecting velocity.
 // One node of a batched launch (member `it`, node i; B staged in shared memory).
@@ -214,17 +215,17 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xy(g, i, x, y);
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
-    if (L.mrho) fused_fields<LD2Q5>(B, L, it, i, x, y, 0, f, ap.x);
+    if (L.mrho) fused_fields<LD2Q5>(B, L, it, i, x, y, 0, f, 2.0 * ap.x);
     if (B.vkind != FK_GENERAL) {
         if (B.fkind != FK_NONE)
-            collide_mat<true>(f, field_value(B.F, B.fkind, 0, x, y, 0, i), 0.5 * ap.x, ap.y, B.mat);
+            collide_mat<true>(f, field_value(B.F, B.fkind, 0, x, y, 0, i), ap.x, ap.y, B.mat);
         else
             collide_mat<false>(f, 0.0, 0.0, 0.0, B.mat);
     } else {
         double Spre = 0.0, H0 = 0.0;
         if (B.fkind != FK_NONE) {
             const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);
-            Spre = ap.x * P;
+            Spre = (2.0 * ap.x) * P;
             H0 = ap.y * P;
         }
         const Rates5 w{B.coef[12], B.coef[13], B.coef[14], B.coef[15]};

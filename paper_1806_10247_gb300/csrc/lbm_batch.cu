@@ -127,6 +127,11 @@ double pair_second(int lattice, double apre, double apost)
     return apost;
 }
 
+// First value of an FP64 pair: a_pre, halved for D2Q5 (its step takes
+// g_0 + (a_pre/2) S; halving is exact, so a kernel that needs a_pre itself
+// doubles it back exactly).  Reduced-precision pairs carry a_pre.
+double pair_first(int lattice, double apre) { return lattice == LBM_D2Q5_CDE ? 0.5 * apre : apre; }
+
 int grow_pairs(lbm_batch *b, int s, size_t need)
 {
     if (need <= b->pairs_cap[s]) return LBM_OK;
@@ -372,7 +377,7 @@ cudaError_t launch_tiled(lbm_batch *b, BatchLaunch L, int tile_idx, bool persist
     int grid = nt;
     L.first = b->d_first[tile_idx];
     L.ntiles = nt;
-    L.chunk = 0;
+    L.persist = 0;
     L.single = 0;
     if (b->count == 1) {
         // one member: its descriptor goes in the launch arguments
@@ -382,9 +387,9 @@ cudaError_t launch_tiled(lbm_batch *b, BatchLaunch L, int tile_idx, bool persist
     }
     if (persistent) {
         const int r = resident_for(b, tile_idx);
-        if (r > 0 && r < nt) {
-            L.chunk = (nt + r - 1) / r;
-            grid = (nt + L.chunk - 1) / L.chunk;
+        if (r > 0 && r < nt) {  // one resident grid; runs of nt / r tiles
+            L.persist = 1;
+            grid = r;
         }
     }
     if (!reduced_precision(b)) return batch_step(b->lattice, L, grid, kTiles[tile_idx], s);
@@ -409,7 +414,7 @@ void fill_pairs(const lbm_batch *b, void *dst, long k)
             const double second = pair_second(b->lattice, apre, apost);
             const size_t at = (size_t)s * b->count + i;
             if (fp32) reinterpret_cast<float2 *>(dst)[at] = make_float2((float)apre, (float)second);
-            else reinterpret_cast<double2 *>(dst)[at] = make_double2(apre, second);
+            else reinterpret_cast<double2 *>(dst)[at] = make_double2(pair_first(b->lattice, apre), second);
         }
     }
 }
@@ -443,7 +448,7 @@ void inline_pairs_of_step(const lbm_batch *b, BatchLaunch &L, long k)
         double apre, apost;
         lbmc::envelope_pair(b->ctx[i], b->ctx[i]->t + k, apre, apost);
         const double second = pair_second(b->lattice, apre, apost);
-        L.inl[i] = make_double2(apre, second);
+        L.inl[i] = make_double2(pair_first(b->lattice, apre), second);
         L.inlf[i] = make_float2((float)apre, (float)second);
     }
 }
@@ -758,10 +763,7 @@ int lbm_batch_get_tiling(lbm_batch *b, int *tile, int *persistent, int *grid)
         long long g = b->ntiles[b->tile_idx];
         if (b->persistent && b->count > 1) {
             const long long r = resident_for(b, b->tile_idx);
-            if (r > 0 && r < g) {
-                const long long chunk = (g + r - 1) / r;
-                g = (g + chunk - 1) / chunk;
-            }
+            if (r > 0 && r < g) g = r;
         }
         *grid = (int)g;
     }

@@ -674,6 +674,53 @@ int lbm_reduce(lbm_ctx *c, double out[5])
     return LBM_OK;
 }
 
+int lbm_l2_error(lbm_ctx *c, const double *ref, int where, int field, int half_forced, double out[3])
+{
+    NvtxRange nvtx_("lbm_l2_error");
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_l2_error: populations not initialised");
+    if (!ref || !out) return fail(c, LBM_EINVAL, "lbm_l2_error: NULL argument");
+    if (where != 0 && where != 1) return fail(c, LBM_EINVAL, "lbm_l2_error: where must be 0 or 1");
+    const bool scalar = c->lattice == LBM_D2Q5_CDE;
+    if (field != 0 && (field != 1 || scalar))
+        return fail(c, LBM_EINVAL, "lbm_l2_error: field must be 0 (rho or phi) or 1 (u, flow lattices)");
+    const size_t N = (size_t)c->g.N;
+    const size_t n = field == 0 ? N : (size_t)c->dim * N;
+    // The field (and a host reference) go to the scratch buffer B (FP64) or the
+    // staging buffer: rho at [0, N), u at [N, (1 + dim) N), ref after them;
+    // (1 + 2 dim) N <= q N doubles for every lattice.
+    double *st = c->B;
+    if (c->storage != LBM_FP64) {
+        const int rc = ensure_stage(c);
+        if (rc != LBM_OK) return rc;
+        st = c->stage;
+    } else {
+        const int rc = wait_readers(c, c->B);
+        if (rc != LBM_OK) return rc;
+    }
+    double apre, apost;
+    envelope_pair(c, c->t, apre, apost);
+    LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
+    CK(moments(c->lattice, a, st, st + N, half_forced ? 1 : 0), "moments kernel");
+    const double *dref = ref;
+    if (where == 0) {
+        double *r = st + (size_t)(1 + c->dim) * N;
+        CK(cudaMemcpyAsync(r, ref, n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy reference");
+        dref = r;
+    }
+    const int nb = reduce_blocks(c->g);
+    CK(l2_terms(field == 0 ? st : st + N, dref, (long long)n, c->partials, nb, c->red_out, c->stream), "l2 kernels");
+    c->launches += 3;
+    double r[8];
+    CK(cudaMemcpyAsync(r, c->red_out, sizeof r, cudaMemcpyDeviceToHost, c->stream), "copy l2 terms");
+    CK(cudaStreamSynchronize(c->stream), "lbm_l2_error");
+    out[0] = r[0];
+    out[1] = r[1];
+    out[2] = r[1] > 0.0 ? std::sqrt(r[0] / r[1]) : (r[0] > 0.0 ? std::numeric_limits<double>::infinity() : 0.0);
+    return LBM_OK;
+}
+
 int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where)
 {
     if (!c) return LBM_EINVAL;

@@ -71,10 +71,10 @@ struct BatchLaunch {
     const int *first;  // first tile of each item (ascending, first[0] = 0)
     int count;
     // The launch covers ntiles tiles of the kernel's tile size; with
-    // chunk > 0 block b takes tiles [b*chunk, min((b+1)*chunk, ntiles))
-    // (persistent grid), else tile b.
+    // persist = 1 (persistent grid of G blocks) block b takes tiles
+    // [b ntiles / G, (b + 1) ntiles / G), else tile b.
     int ntiles;
-    int chunk;
+    int persist;
     // single = 1: the batch has one member, whose descriptor travels here in
     // the launch arguments (read from the constant bank, nothing staged).
     int single;
@@ -151,6 +151,10 @@ cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, in
 cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
                    int nblocks, double *out);
 int reduce_blocks(const Geom &g);
+// Terms of the l2 error of Eq. sca over n values: out[0] = sum (q - ref)^2,
+// out[1] = sum ref^2 (per-block partials[nblocks][8], then one block; out[8]).
+cudaError_t l2_terms(const double *q, const double *ref, long long n, double *partials, int nblocks, double *out,
+                     cudaStream_t s);
 // Mass / momentum / instability-flag sums only (no snapshot): partials[nblocks][8], out[8].
 cudaError_t reduce_sums(int lattice, const LaunchArgs &a, double *partials, int nblocks, double *out);
 

@@ -1,10 +1,10 @@
 // Tile loop of the batched launches.  A batched launch covers the tiles of
 // every member lattice (TB nodes per tile, TB threads per block, tiles
 // numbered member after member; first[i] is member i's first tile).  Either
-// each block takes one tile, or (persistent grid, L.chunk > 0) each block
-// takes a contiguous run of L.chunk tiles, so that consecutive tiles mostly
-// belong to the same member and its descriptor is staged into shared memory
-// once per run.
+// each block takes one tile, or (persistent grid, L.persist = 1) each block
+// takes a contiguous run of tiles, the runs of the grid's blocks differing by
+// at most one tile, so that consecutive tiles mostly belong to the same
+// member and its descriptor is staged into shared memory once per run.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,9 +28,18 @@ __device__ __forceinline__ int tile_item(const int *__restrict__ first, int coun
     return lo;
 }
 
-// Kernel forms: one tile per block, persistent (a run of L.chunk tiles per
-// block), single member (descriptor in the launch arguments, one tile per block).
+// Kernel forms: one tile per block, persistent (a run of tiles per block),
+// single member (descriptor in the launch arguments, one tile per block).
 enum { TILE_ONE = 0, TILE_PERSIST = 1, TILE_SINGLE = 2 };
+
+// Run [t0, t1) of this block of a persistent grid: the ntiles tiles split
+// evenly over the grid's blocks.
+__device__ __forceinline__ void persist_run(const BatchLaunch &L, int &t0, int &t1)
+{
+    const long long nt = L.ntiles, G = gridDim.x, b = blockIdx.x;
+    t0 = (int)(b * nt / G);
+    t1 = (int)((b + 1) * nt / G);
+}
 
 // Runs node(B, L, member, node index) for every node of the block's tiles,
 // with B the member's descriptor (staged in shared memory, or the launch
@@ -53,8 +62,8 @@ __device__ __forceinline__ void batch_tiles(const BatchLaunch &L, Node node)
         if (i < B.g.N) node(B, L, it, i);
         return;
     }
-    const int t0 = blockIdx.x * L.chunk;
-    const int t1 = min(t0 + L.chunk, L.ntiles);
+    int t0, t1;
+    persist_run(L, t0, t1);
     int cur = -1;
     for (int tile = t0; tile < t1; tile++) {
         const int it = tile_item(L.first, L.count, tile, cur);
@@ -98,7 +107,7 @@ int resident_blocks(K kernel, int tb)
 }
 
 // Form of a launch from its arguments.
-inline int tile_mode(const BatchLaunch &L) { return L.single ? TILE_SINGLE : (L.chunk > 0 ? TILE_PERSIST : TILE_ONE); }
+inline int tile_mode(const BatchLaunch &L) { return L.single ? TILE_SINGLE : (L.persist ? TILE_PERSIST : TILE_ONE); }
 
 // Launch of a batched kernel template K<TB, MODE> for tile sizes 128, 256, 512.
 #define LBM_TILED_LAUNCH(KERNEL, L, nblocks, tile, s)                                              \

@@ -33,7 +33,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_batch_step", "lbm_batch_launch_count", "lbm_batch_last_error", "lbm_batch_destroy",
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
            "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
-           "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison", "lbm_batch_step_read")
+           "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison", "lbm_batch_step_read",
+           "lbm_l2_error")
 
 
 class LBMError(RuntimeError):
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.lbm_moments.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_reduce.argtypes = [vp, dp]
     L.lbm_reduce_sums_noalloc.argtypes = [vp, dp]
+    L.lbm_l2_error.argtypes = [vp, vp, ip, ip, ip, dp]
     L.lbm_get_populations.argtypes = [vp, vp, ctypes.c_size_t, ip]
     L.lbm_set_populations.argtypes = [vp, vp, ctypes.c_size_t, ip, ctypes.c_long]
     L.lbm_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
@@ -120,6 +122,12 @@ def load(build_if_missing: bool = True):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def _torch_float64():
+    import torch
+
+    return torch.float64
 
 
 def _dp(a):
@@ -286,6 +294,27 @@ class Lattice:
         out = np.empty(5)
         self._check(self._L.lbm_reduce(self.h, _dp(out)))
         return out
+
+    def l2_error(self, ref, field=0, half_forced=True):
+        """Eq. sca against a reference field, summed on the GPU: returns
+        (sum (q - ref)^2, sum ref^2, relative l2 error).  field 0: rho / phi
+        ([N]); field 1: u ([dim][N]).  ref: a numpy array (host) or a CUDA
+        tensor (anything with ``data_ptr`` and ``is_cuda``) of float64."""
+        out = np.empty(3)
+        if getattr(ref, "is_cuda", False):
+            n = ref.numel()
+            if ref.dtype != _torch_float64() or not ref.is_contiguous():
+                raise ValueError("reference tensor must be contiguous float64")
+            ptr, where = ctypes.c_void_p(ref.data_ptr()), 1
+        else:
+            ref = np.ascontiguousarray(ref, dtype=np.float64)
+            n = ref.size
+            ptr, where = ref.ctypes.data_as(ctypes.c_void_p), 0
+        want = self.N * (1 if field == 0 else self.dim)
+        if n != want:
+            raise ValueError(f"reference must hold {want} values, got {n}")
+        self._check(self._L.lbm_l2_error(self.h, ptr, where, int(field), int(bool(half_forced)), _dp(out)))
+        return float(out[0]), float(out[1]), float(out[2])
 
     def debug_poison(self):
         """Fill the destination buffer of the next step with NaN (debug aid)."""

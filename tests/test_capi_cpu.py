@@ -94,6 +94,7 @@ def test_batch_and_nn_entry_points_reject_null_handles():
     assert L.lbm_batch_autotune(None, 1, None, None) == lbm.EINVAL
     assert L.lbm_batch_set_tiling(None, 256, 0) == lbm.EINVAL
     assert L.lbm_batch_moments(None, None, None, 0, 1) == lbm.EINVAL
+    assert L.lbm_l2_error(None, None, 0, 0, 1, None) == lbm.EINVAL
 
 
 def test_oracle_and_product_share_no_code():

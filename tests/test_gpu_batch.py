@@ -1,6 +1,7 @@
 """Batched stepping (one launch per step for many lattices): bit-identical to
 stepping each member alone, and within the parity bar of the oracle; envelope
 tables equal envelope callbacks."""
+import dataclasses
 import math
 
 import numpy as np
@@ -280,6 +281,53 @@ def test_fp64_batch_every_tiling_and_autotune():
     assert e.value.code == lbm.EINVAL
     with pytest.raises(lbm.LBMError):
         B.autotune(0)
+
+
+def test_fp64_scalar_persistent_runs_cross_members():
+    """FP64 scalar batches large enough that the persistent grid holds fewer
+    blocks than there are tiles, so every block's run spans several tiles and
+    many runs cross from one member into the next; its members have a
+    uniform velocity with a separable source, a velocity field, a full source
+    field and no source.  Each tiling steps every member as the member's own
+    kernel does."""
+    _, sc = W.batched_sweep(count=60, seed=21, nx_range=(40, 200), ny_range=(32, 160))
+    ws, fulls = list(sc), [None] * len(sc)
+    rng = np.random.default_rng(3)
+    vel = {}
+    for k, (shape, wall, kind) in enumerate([((150, 97, 1), (0, 0, 0), "full"),
+                                             ((31, 200, 1), (1, 1, 0), "separable"),
+                                             ((64, 64, 1), (0, 1, 0), "full")]):
+        w, full = _random_workload(W.D2Q5, shape, wall, seed=40 + k, kind=kind)
+        ws.insert(5 * k + 3, w)
+        fulls.insert(5 * k + 3, full)
+        if k != 2:
+            vel[5 * k + 3] = 0.02 * rng.standard_normal((2, w.nodes))
+    nosrc = ws.index(sc[7])
+    ws[nosrc] = dataclasses.replace(sc[7], tables=None)
+    nodes = sum(w.nodes for w in ws)
+
+    def make_all():
+        Gs = [_make(w, f) for w, f in zip(ws, fulls)]
+        for i, v in vel.items():
+            Gs[i].set_velocity(full=v)
+        return Gs
+
+    solo = make_all()
+    for G in solo:
+        G.step(3)
+    want = [G.get_populations() for G in solo]
+    for tile in (128, 256, 512):
+        Gs = make_all()
+        B = lbm.Batch(Gs)
+        B.set_tiling(tile, True)
+        t, p, grid = B.tiling()
+        assert p and grid < -(-nodes // tile) // 2  # runs of two or more tiles
+        B.step(1)
+        B.step(2)
+        for a, G in zip(want, Gs):
+            assert G.t == 3
+            assert np.abs(G.get_populations() - a).max() <= 3 * 4 * 2.0 ** -53, (tile, G.shape)
+        B.close()
 
 
 def test_batch_moments_equal_member_moments():

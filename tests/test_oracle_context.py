@@ -127,3 +127,46 @@ def test_reduce_flags_a_non_positive_density():
     f[:, 4] = -f[:, 4]
     ctx.set_populations(f, 0)
     assert ctx.reduce()[0] == O.REF_EUNSTABLE
+
+
+def test_l2_error_invariants():
+    """Eq. sca on the context's own fields: zero against itself; exactly 1/2
+    against twice the field (sum (q - 2q)^2 = sum q^2 and sum (2q)^2 =
+    4 sum q^2, both exact in binary); a single perturbed value of one vector
+    component contributes its own square and nothing else; +inf against a
+    zero reference."""
+    w = W.womersley(ny=10, nx=4, tau=0.9, period=40)
+    _, ctx, P = _pair(w, envelope=w.envelope)
+    ctx.init_equilibrium(1.0, (0.01, -0.02, 0.0))
+    ctx.set_force(P)
+    ctx.set_envelope(w.envelope)
+    ctx.step(7)
+    for field in (0, 1):
+        _, rho, u = ctx.moments(half_forced=True)
+        q = rho if field == 0 else u
+        rc, out = ctx.l2_error(q, field)
+        assert rc == O.REF_OK and out[0] == 0.0 and out[2] == 0.0
+        rc, out = ctx.l2_error(2.0 * q, field)
+        assert out[1] == 4.0 * out[0] and out[2] == 0.5
+        ref = q.copy()
+        k = (field, 17) if field == 1 else (17,)
+        ref[k] = ref[k] * (1 + 1e-3)
+        d = q[k] - ref[k]
+        rc, out = ctx.l2_error(ref, field)
+        assert out[0] == d * d and out[1] > 0.0
+        rc, out = ctx.l2_error(np.zeros_like(q), field)
+        assert out[1] == 0.0 and math.isinf(out[2])
+    # the un-forced field differs from the half-forced one by a_pre F / (2 rho)
+    _, _, u0 = ctx.moments(half_forced=False)
+    rc, a = ctx.l2_error(u0, 1, half_forced=True)
+    rc, b = ctx.l2_error(u0, 1, half_forced=False)
+    assert a[0] > 0.0 and b[0] == 0.0
+
+
+def test_l2_error_argument_checks():
+    s = O.OracleContext(O.D2Q5, (4, 4, 1), omega=W.d2q5_omega(0.8))
+    assert s.l2_error(np.zeros(16))[0] == O.REF_ESTATE
+    s.init_equilibrium(1.0)
+    assert s.l2_error(np.zeros(16))[0] == O.REF_OK
+    assert s.l2_error(np.zeros(32), field=1)[0] == O.REF_EINVAL  # no velocity field on the scalar lattice
+    assert s.l2_error(np.zeros(15))[0] == O.REF_EINVAL

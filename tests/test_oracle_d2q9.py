@@ -195,6 +195,14 @@ def test_poiseuille_second_order_diffusive_scaling():
         uc = u[0].reshape(ny, 3)[:, 0]
         errs.append(np.sqrt(np.sum((uc - ua) ** 2) / np.sum(ua ** 2)))
         Hs.append(ny)
+        # the context API's l2 error of the whole velocity field (three
+        # identical columns, u_y ~ 0) against the parabola gives the same value
+        ctx = O.OracleContext(O.D2Q9, (3, ny, 1), omega=W.d2q9_omega(tau), wall=(0, 1, 0))
+        assert ctx.set_force(L.P) == O.REF_OK and ctx.set_populations(L.f, 0) == O.REF_OK
+        ref = np.zeros((2, 3 * ny))
+        ref[0] = np.repeat(ua, 3)
+        rc, out = ctx.l2_error(ref, field=1)
+        assert rc == O.REF_OK and abs(out[2] - errs[-1]) <= 1e-9 * errs[-1]
     slope = np.polyfit(np.log(Hs), np.log(errs), 1)[0]
     assert abs(-slope - float(golden["slope"])) < 0.1, (errs, slope)
 
