@@ -114,17 +114,7 @@ k_moments(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, double 
     load_pulled<L>(fin, g, x, y, z, i, f);
     double m0, j[3];
     zeroth_first<L>(f, m0, j);
-    const bool forced = half && fkind != FK_NONE;
-    if (L::Q == 5) {
-        rho[i] = forced ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
-        return;
-    }
-    rho[i] = m0;
-#pragma unroll
-    for (int d = 0; d < L::DIM; d++) {
-        double jd = forced ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
-        u[d * g.N + i] = jd / m0;
-    }
+    store_fields<L>(m0, j, half && fkind != FK_NONE, apre, F, fkind, x, y, z, i, g.N, 0, rho, u);
 }
 
 // Reduction slots.
@@ -372,17 +362,7 @@ k_moments_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, Field
     double dm0, j[3];
     dev_moments<L, T>(fin, g, x, y, z, i, dm0, j);
     const double m0 = rho_ref + dm0;
-    const bool forced = half && fkind != FK_NONE;
-    if (L::Q == 5) {
-        rho[i] = forced ? m0 + 0.5 * (apre * field_value(F, fkind, 0, x, y, z, i)) : m0;
-        return;
-    }
-    rho[i] = m0;
-#pragma unroll
-    for (int d = 0; d < L::DIM; d++) {
-        double jd = forced ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
-        u[d * g.N + i] = jd / m0;
-    }
+    store_fields<L>(m0, j, half && fkind != FK_NONE, apre, F, fkind, x, y, z, i, g.N, 0, rho, u);
 }
 
 // Strain rate from the non-equilibrium second moments (Sec. 6.6): with

@@ -120,10 +120,13 @@ Mat5 make_mat(const Coef5 &k)
 // other four.  The matrix entries are rounded on the host, so their column
 // sums differ from 1 by ~1e-16; taken through row 0 that would change the
 // total scalar by the same amount every step (1e-12 after ~10^4 steps).
+// phi0 receives the zeroth moment of the pulled populations, summed as
+// zeroth_first sums it (for a fused readback).
 template <bool SRC>
-__device__ __forceinline__ void collide_mat(double (&g)[5], double P, double ahalf, double hsum, const double *M)
+__device__ __forceinline__ void collide_mat(double (&g)[5], double P, double ahalf, double hsum, const double *M,
+                                            double &phi0)
 {
-    const double phi0 = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];  // as zeroth_first sums it
+    phi0 = (((g[0] + g[1]) + g[2]) + g[3]) + g[4];
     double gs[5] = {g[0], g[1], g[2], g[3], g[4]};
     double h = 0.0;
     if (SRC) {
@@ -149,10 +152,10 @@ k_step_mat(const __grid_constant__ Planes<double, 5> P, Geom g, FieldDev S, doub
     if (i >= g.N) return;
     int x, y;
     node_xy(g, i, x, y);
-    double f[5];
+    double f[5], phi0;
     load_pulled<LD2Q5>(P, g, x, y, 0, i, f);
-    if (SK != FK_NONE) collide_mat<true>(f, field_value(S, SK, 0, x, y, 0, i), ahalf, hsum, M.m);
-    else collide_mat<false>(f, 0.0, ahalf, hsum, M.m);
+    if (SK != FK_NONE) collide_mat<true>(f, field_value(S, SK, 0, x, y, 0, i), ahalf, hsum, M.m, phi0);
+    else collide_mat<false>(f, 0.0, ahalf, hsum, M.m, phi0);
 #pragma unroll
     for (int a = 0; a < 5; a++) P.out[a][i] = f[a];
 }
@@ -215,13 +218,21 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xy(g, i, x, y);
     double f[5];
     load_pulled<LD2Q5>(fin, g, x, y, 0, i, f);
-    if (L.mrho) fused_fields<LD2Q5>(B, L, it, i, x, y, 0, f, 2.0 * ap.x);
     if (B.vkind != FK_GENERAL) {
-        if (B.fkind != FK_NONE)
-            collide_mat<true>(f, field_value(B.F, B.fkind, 0, x, y, 0, i), ap.x, ap.y, B.mat);
-        else
-            collide_mat<false>(f, 0.0, 0.0, 0.0, B.mat);
+        const bool src = B.fkind != FK_NONE;
+        const double P = src ? field_value(B.F, B.fkind, 0, x, y, 0, i) : 0.0;
+        double phi0;
+        if (src) collide_mat<true>(f, P, ap.x, ap.y, B.mat, phi0);
+        else collide_mat<false>(f, 0.0, 0.0, 0.0, B.mat, phi0);
+        if (L.mrho) {
+            // fused readback of f(t)'s scalar from the step's own zeroth
+            // moment: phi0 + (a_pre/2) P, the bits store_fields forms
+            const double jd[3] = {0.0, 0.0, 0.0};
+            put_fields<LD2Q5>(L.mhalf && src ? __dadd_rn(phi0, __dmul_rn(ap.x, P)) : phi0, jd, 0.0, i, g.N,
+                              __ldg(L.moff + it), L.mrho, L.mu);
+        }
     } else {
+        if (L.mrho) fused_fields<LD2Q5>(B, L, it, i, x, y, 0, f, 2.0 * ap.x);
         double Spre = 0.0, H0 = 0.0;
         if (B.fkind != FK_NONE) {
             const double P = field_value(B.F, B.fkind, 0, x, y, 0, i);

@@ -18,11 +18,18 @@ struct Rates9 {
     double c3, c4, c5, c6, c7, c8;  // omega_3/12, omega_4/4, omega_5/4, omega_6/4, omega_7/4, omega_8/4
 };
 
+// Moments a collision forms on the way (for a fused readback): rho and the
+// un-forced j of the pulled populations, summed as zeroth_first<LD2Q9> sums
+// them, the half-forced j of Eq. 25 and 1/rho (__drcp_rn).
+struct Mom9 {
+    double rho, jx, jy, jfx, jfy, rinv;
+};
+
 // Post-collision populations of one node, in place.
 //   Fx, Fy : pre-collision force a_pre P (Eq. 25)
 //   Gx, Gy : first-moment coefficients g_1, g_2 = (F_pre + F_post)/12 (Eqs. 27-31)
 __device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, double Gx, double Gy,
-                                        const Rates9 &w)
+                                        const Rates9 &w, Mom9 &mo)
 {
     // Raw moments (Eq. 21) by 1D passes: x-moments of the three rows ey = 0,
     // +1, -1, then y-moments of those.
@@ -36,8 +43,10 @@ __device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, do
 
     // Eq. 25: velocity after the pre-collision half force step.
     const double rinv = __drcp_rn(rho);
-    const double ux = fma(0.5, Fx, jx) * rinv;
-    const double uy = fma(0.5, Fy, jy) * rinv;
+    const double jfx = fma(0.5, Fx, jx), jfy = fma(0.5, Fy, jy);
+    const double ux = jfx * rinv;
+    const double uy = jfy * rinv;
+    mo = Mom9{rho, jx, jy, jfx, jfy, rinv};
     const double ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
 
     // Eq. 23: cascaded change of moments.
@@ -84,7 +93,7 @@ __device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, do
 // itself (not rebuilt as rho (j / rho)), so the step transports momentum
 // without a rounding of its own.  About 80 FP64 operations instead of 132.
 __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy, double Gx, double Gy,
-                                           const Rates9 &w)
+                                           const Rates9 &w, Mom9 &mo)
 {
     // raw moments of order <= 2 per axis (Eq. 21)
     const double s0 = f[1] + f[3], d0 = f[1] - f[3];  // row ey = 0
@@ -92,10 +101,12 @@ __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy,
     const double s2 = f[8] + f[7], d2 = f[8] - f[7];  // row ey = -1
     const double B0 = f[2] + s1, C0 = f[4] + s2;
     const double rho = (f[0] + s0) + (B0 + C0);
-    const double jx = fma(0.5, Fx, d0 + (d1 + d2)), jy = fma(0.5, Fy, B0 - C0);  // Eq. 25
+    const double jx0 = d0 + (d1 + d2), jy0 = B0 - C0;
+    const double jx = fma(0.5, Fx, jx0), jy = fma(0.5, Fy, jy0);  // Eq. 25
     const double mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;
     const double rinv = __drcp_rn(rho);
     const double ux = jx * rinv, uy = jy * rinv;
+    mo = Mom9{rho, jx0, jy0, jx, jy, rinv};
 
     // second-order central moments, relaxed and halved (xx, yy by 1/2 ... of
     // the trace and difference: k_xx = (T + D) / 2 halved is (T + D) / 4)
@@ -153,8 +164,9 @@ k_step(const __grid_constant__ Planes<double, 9> P, Geom g, FieldDev F, double a
         Gx = gsum * Px;
         Gy = gsum * Py;
     }
-    if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w);
-    else collide(f, Fx, Fy, Gx, Gy, w);
+    Mom9 mo;
+    if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w, mo);
+    else collide(f, Fx, Fy, Gx, Gy, w, mo);
 #pragma unroll
     for (int a = 0; a < 9; a++) P.out[a][i] = f[a];
 }
@@ -218,8 +230,9 @@ k_cluster_steps(const double *__restrict__ fin, double *__restrict__ fout, Geom 
                 const double *base = cl.map_shared_rank(sm + cur * 9 * P, src_blk[a]);
                 f[a] = base[src_off[a]];
             }
-            if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w);
-            else collide(f, Fx, Fy, Gx, Gy, w);
+            Mom9 mo;
+            if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w, mo);
+            else collide(f, Fx, Fy, Gx, Gy, w, mo);
             double *nxt = sm + (cur ^ 1) * 9 * P;
 #pragma unroll
             for (int a = 0; a < 9; a++) nxt[a * P + l] = f[a];
@@ -246,7 +259,6 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xy(g, i, x, y);
     double f[9];
     load_pulled<LD2Q9>(fin, g, x, y, 0, i, f);
-    if (L.mrho) fused_fields<LD2Q9>(B, L, it, i, x, y, 0, f, ap.x);
     double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
     const int fk = B.fkind;
     if (fk != FK_NONE) {
@@ -257,8 +269,17 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
         Gy = ap.y * Py;
     }
     const Rates9 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
-    if (B.variant == 1) collide_w1(f, Fx, Fy, Gx, Gy, w);  // uniform over the member
-    else collide(f, Fx, Fy, Gx, Gy, w);
+    Mom9 mo;
+    if (B.variant == 1) collide_w1(f, Fx, Fy, Gx, Gy, w, mo);  // uniform over the member
+    else collide(f, Fx, Fy, Gx, Gy, w, mo);
+    if (L.mrho) {
+        // fused readback of f(t)'s fields from the collision's own moments;
+        // the same bits as store_fields (Fx = a_pre P, so fma(0.5, Fx, j) is
+        // j + (a_pre P)/2 rounded once)
+        const bool forced = L.mhalf && fk != FK_NONE;
+        const double jd[3] = {forced ? mo.jfx : mo.jx, forced ? mo.jfy : mo.jy, 0.0};
+        put_fields<LD2Q9>(mo.rho, jd, mo.rinv, i, g.N, __ldg(L.moff + it), L.mrho, L.mu);
+    }
 #pragma unroll
     for (int a = 0; a < 9; a++) fout[a * g.Np + i] = f[a];
 }

@@ -203,12 +203,42 @@ __device__ __forceinline__ void zeroth_first(const double (&f)[L::Q], double &m0
     }
 }
 
+// D2Q9: the same sums grouped as the collision groups them (x-moments of the
+// rows e_y = 0, +1, -1 first), so that a step kernel's own rho and j are
+// these bits and a fused readback can store them without summing again.
+template <>
+__device__ __forceinline__ void zeroth_first<LD2Q9>(const double (&f)[9], double &m0, double (&j)[3])
+{
+    const double s0 = f[1] + f[3], s1 = f[5] + f[6], s2 = f[8] + f[7];
+    const double B0 = f[2] + s1, C0 = f[4] + s2;
+    m0 = (f[0] + s0) + (B0 + C0);
+    j[0] = (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    j[1] = B0 - C0;
+    j[2] = 0.0;
+}
+
+// Stores the packed fields of a node: rho (phi for the scalar lattice) at
+// rho[off + i] and u_d = jd_d (1/rho) at u[dim * off + d * N + i], with rinv =
+// the correctly rounded 1/rho (__drcp_rn) and the product rounded on its own.
+template <class L>
+__device__ __forceinline__ void put_fields(double m0, const double (&jd)[3], double rinv, int i, int N, long long off,
+                                           double *rho, double *u)
+{
+    rho[off + i] = m0;
+    if (L::Q == 5) return;
+#pragma unroll
+    for (int d = 0; d < L::DIM; d++) u[L::DIM * off + (long long)d * N + i] = __dmul_rn(jd[d], rinv);
+}
+
 // The packed fields of a node from its zeroth and first moments, as every
 // readback writes them: rho (phi for the scalar lattice) at rho[off + i],
 // velocity component d at u[dim * off + d * N + i]; with `forced` the
 // pre-collision half force / source a_pre P / 2 is included (Eq. 25 / 43).
 // Rounded operation by operation (no contraction), so that every kernel that
-// forms them gives the same bits.
+// forms them gives the same bits.  A step kernel that has rho, the half-forced
+// j and 1/rho at hand stores them with put_fields instead: j + (a_pre P)/2
+// rounded once equals fma(0.5, a_pre P, j), and phi + (a_pre/2) P equals
+// phi + (a_pre P)/2 (halving is exact for products in the normal range).
 template <class L>
 __device__ __forceinline__ void store_fields(double m0, const double (&j)[3], bool forced, double apre, const FieldDev &F,
                                              int fkind, int x, int y, int z, int i, int N, long long off, double *rho,
@@ -218,13 +248,11 @@ __device__ __forceinline__ void store_fields(double m0, const double (&j)[3], bo
         rho[off + i] = forced ? __dadd_rn(m0, __dmul_rn(0.5, __dmul_rn(apre, field_value(F, fkind, 0, x, y, z, i)))) : m0;
         return;
     }
-    rho[off + i] = m0;
+    double jd[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int d = 0; d < L::DIM; d++) {
-        const double jd =
-            forced ? __dadd_rn(j[d], __dmul_rn(0.5, __dmul_rn(apre, field_value(F, fkind, d, x, y, z, i)))) : j[d];
-        u[L::DIM * off + (long long)d * N + i] = __ddiv_rn(jd, m0);
-    }
+    for (int d = 0; d < L::DIM; d++)
+        jd[d] = forced ? __dadd_rn(j[d], __dmul_rn(0.5, __dmul_rn(apre, field_value(F, fkind, d, x, y, z, i)))) : j[d];
+    put_fields<L>(m0, jd, __drcp_rn(m0), i, N, off, rho, u);
 }
 
 // Copy an object into shared memory cooperatively (word by word); the caller

@@ -414,8 +414,19 @@ def test_step_read_writes_the_fields_each_step_starts_from(kind, where):
     import torch
 
     ws, fulls = _members(kind)
+    if kind == "d2q5":
+        # plus a member without a source and one with an advecting-velocity field
+        ws += [dataclasses.replace(ws[0], tables=None), ws[1]]
+        fulls += [None, None]
+    elif kind == "d2q9":
+        ws.append(dataclasses.replace(ws[0], tables=None))  # plus a member without a force
+        fulls.append(None)
     Gs = [_make(w, f) for w, f in zip(ws, fulls)]
     twins = [_make(w, f) for w, f in zip(ws, fulls)]
+    if kind == "d2q5":
+        v = 0.02 * np.random.default_rng(9).standard_normal((2, Gs[-1].N))
+        Gs[-1].set_velocity(full=v)
+        twins[-1].set_velocity(full=v)
     B, T = lbm.Batch(Gs), lbm.Batch(twins)
     n = sum(G.N for G in Gs)
     dim = 0 if kind == "d2q5" else Gs[0].dim
