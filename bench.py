@@ -497,7 +497,7 @@ def main():
     stream = torch.cuda.Stream()
     nodes = sum(w.nodes for w in wl)
     big = nodes > 10_000_000
-    e2e_steps = 3 if big else max(3, min(args.steps, 50))
+    e2e_steps = 10 if big else max(3, min(args.steps, 50))
     env_steps = args.warmup + args.steps + e2e_steps + 20000  # envelope tables cover every step run here
     storage = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}[args.storage]
     elem = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[args.storage]

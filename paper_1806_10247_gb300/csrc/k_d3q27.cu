@@ -112,20 +112,35 @@ __device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, do
     along<0>(m, [](double &a, double &b, double &c) { raw_bwd_h(a, b, c); });
 }
 
+// Moments a collision forms on the way (for a fused readback): rho and the
+// un-forced j of the pulled populations, grouped as zeroth_first<LD3Q27>
+// groups them, the half-forced j and 1/rho (__drcp_rn).
+struct Mom27 {
+    double rho, j[3], jf[3], rinv;
+};
+
 // F: pre-collision force a_pre P; Fq: post-collision force a_post P.
 __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
-                                        const Rates27 &w)
+                                        const Rates27 &w, Mom27 &mo)
 {
     along<0>(m, [](double &a, double &b, double &c) { raw_fwd(a, b, c); });
     along<1>(m, [](double &a, double &b, double &c) { raw_fwd(a, b, c); });
     along<2>(m, [](double &a, double &b, double &c) { raw_fwd(a, b, c); });
 
     // Pre-collision half force on the first moments; velocity u = m_1 / rho.
+    mo.j[0] = m[1];
+    mo.j[1] = m[3];
+    mo.j[2] = m[9];
     m[1] = fma(0.5, F[0], m[1]);
     m[3] = fma(0.5, F[1], m[3]);
     m[9] = fma(0.5, F[2], m[9]);
     const double rho = m[0];
     const double rinv = __drcp_rn(rho);
+    mo.rho = rho;
+    mo.jf[0] = m[1];
+    mo.jf[1] = m[3];
+    mo.jf[2] = m[9];
+    mo.rinv = rinv;
     const double ux = m[1] * rinv, uy = m[3] * rinv, uz = m[9] * rinv;
 
     along<0>(m, [ux](double &a, double &b, double &c) { shift_fwd(a, b, c, ux); });
@@ -173,7 +188,7 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
 // order <= 2 are formed (partial transforms) and the forward shift reduces to
 // the six second-order central moments.
 __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
-                                           const Rates27 &w)
+                                           const Rates27 &w, Mom27 &mo)
 {
     along<0>(m, [](double &a, double &b, double &c) { raw_fwd(a, b, c); });
     // Line (b, c) along x holds M0, M1, M2 at m[3b + 9c + 0..2]; e_y = b - 1, e_z = c - 1.
@@ -198,10 +213,18 @@ __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3]
     const double kxy = (X1[2] + X1[0]) + X1[1];
     const double kxx = ((m[2] + m[5]) + (m[8] + m[11])) + ((m[14] + m[17]) + (m[20] + m[23])) + m[26];
 
+    mo.j[0] = jx;
+    mo.j[1] = jy;
+    mo.j[2] = jz;
     jx = fma(0.5, F[0], jx);
     jy = fma(0.5, F[1], jy);
     jz = fma(0.5, F[2], jz);
     const double rinv = __drcp_rn(rho);
+    mo.rho = rho;
+    mo.jf[0] = jx;
+    mo.jf[1] = jy;
+    mo.jf[2] = jz;
+    mo.rinv = rinv;
     const double ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
 
     // Second-order central moments (the first ones vanish) and their relaxation.
@@ -250,8 +273,9 @@ k_step(const __grid_constant__ Planes<double, 27> P, Geom g, FieldDev Fd, double
             Fq[d] = apost * P;
         }
     }
-    if (W1) collide_w1(m, F, Fq, w);
-    else collide(m, F, Fq, w);
+    Mom27 mo;
+    if (W1) collide_w1(m, F, Fq, w, mo);
+    else collide(m, F, Fq, w, mo);
 #pragma unroll
     for (int a = 0; a < 27; a++) P.out[a][i] = m[a];
 }
@@ -269,7 +293,6 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xyz(g, i, x, y, z);
     double m[27];
     load_pulled<LD3Q27>(fin, g, x, y, z, i, m);
-    if (L.mrho) fused_fields<LD3Q27>(B, L, it, i, x, y, z, m, ap.x);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (B.fkind != FK_NONE) {
 #pragma unroll
@@ -280,8 +303,17 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
         }
     }
     const Rates27 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
-    if (B.variant == 1) collide_w1(m, F, Fq, w);  // uniform over the block's tile
-    else collide(m, F, Fq, w);
+    Mom27 mo;
+    if (B.variant == 1) collide_w1(m, F, Fq, w, mo);  // uniform over the block's tile
+    else collide(m, F, Fq, w, mo);
+    if (L.mrho) {
+        // fused readback of f(t)'s fields from the collision's own moments;
+        // the same bits as store_fields (F = a_pre P, so fma(0.5, F, j) is
+        // j + (a_pre P)/2 rounded once)
+        const bool forced = L.mhalf && B.fkind != FK_NONE;
+        const double jd[3] = {forced ? mo.jf[0] : mo.j[0], forced ? mo.jf[1] : mo.j[1], forced ? mo.jf[2] : mo.j[2]};
+        put_fields<LD3Q27>(mo.rho, jd, mo.rinv, i, g.N, __ldg(L.moff + it), L.mrho, L.mu);
+    }
 #pragma unroll
     for (int a = 0; a < 27; a++) fout[a * g.Np + i] = m[a];
 }

@@ -217,6 +217,32 @@ __device__ __forceinline__ void zeroth_first<LD2Q9>(const double (&f)[9], double
     j[2] = 0.0;
 }
 
+// D3Q27: grouped as the factorised collision forms them — the 1D transform
+// (f_+ + f_-) + f_0 and f_+ - f_- along x on every line, then along y, then
+// along z — so that the collision's own rho and j are these bits.
+template <>
+__device__ __forceinline__ void zeroth_first<LD3Q27>(const double (&f)[27], double &m0, double (&j)[3])
+{
+    double Y0[3], Y1[3], XY[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        double X0[3], X1[3];
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const int k = 3 * b + 9 * c;  // velocities (-1, 0, +1) along x at k, k + 1, k + 2
+            X0[b] = (f[k + 2] + f[k]) + f[k + 1];
+            X1[b] = f[k + 2] - f[k];
+        }
+        Y0[c] = (X0[2] + X0[0]) + X0[1];
+        Y1[c] = X0[2] - X0[0];
+        XY[c] = (X1[2] + X1[0]) + X1[1];
+    }
+    m0 = (Y0[2] + Y0[0]) + Y0[1];
+    j[0] = (XY[2] + XY[0]) + XY[1];
+    j[1] = (Y1[2] + Y1[0]) + Y1[1];
+    j[2] = Y0[2] - Y0[0];
+}
+
 // Stores the packed fields of a node: rho (phi for the scalar lattice) at
 // rho[off + i] and u_d = jd_d (1/rho) at u[dim * off + d * N + i], with rinv =
 // the correctly rounded 1/rho (__drcp_rn) and the product rounded on its own.
