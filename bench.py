@@ -48,50 +48,50 @@ KERNEL_FACTS = {
     ("cde_sweep", "fp64"): {
         "src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H,
         "fp64_inst_per_node": 32, "fp64_flops_per_node": 54,
-        "traffic_bytes_per_launch": 14.008832e6, "traffic_src_sha": "4f6698f38c778af7",
+        "traffic_bytes_per_launch": 14.0096e6, "traffic_src_sha": "47b4fe221b263702",
         "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md",
     },
     ("kolmogorov96", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (95.587072 + 45.827072) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "traffic_bytes_per_launch": (95.585536 + 44.614656) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov256", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (1812.101376 + 1756.919552) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "traffic_bytes_per_launch": (1812.081920 + 1757.261056) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov96", "fp16"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (47.809024 + 7.182080) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "traffic_bytes_per_launch": (47.809536 + 6.978816) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("batched_sweep256", "fp32"): {
         "src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh"] + _H,
-        "traffic_bytes_per_launch": (380.677120 + 335.904000) * 1e6, "traffic_src_sha": "541602c3f79a5ca1",
+        "traffic_bytes_per_launch": (382.248960 + 335.472128) * 1e6, "traffic_src_sha": "3b3d6767a485aeb5",
         "profile": "profiles/k_batch9_batched_sweep_fp32.md",
     },
     ("kolmogorov96", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
         "fp64_inst_per_node": 287, "fp64_flops_per_node": 396,
-        "traffic_bytes_per_launch": (191.157248 + 137.669632) * 1e6, "traffic_src_sha": "4a93369e8810592c",
+        "traffic_bytes_per_launch": (191.155456 + 137.319680) * 1e6, "traffic_src_sha": "b8fd508d60dd017d",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("channel2048", "fp64"): {
         "src": [_C + "k_d2q9.cu"] + _H,
         "fp64_inst_per_node": 85, "fp64_flops_per_node": 116,
-        "traffic_bytes_per_launch": (151.035392 + 100.336128) * 1e6, "traffic_src_sha": "1faf847cd140a813",
+        "traffic_bytes_per_launch": (151.071232 + 100.027648) * 1e6, "traffic_src_sha": "a82db62a8045ce0b",
         "profile": "profiles/k_step_d2q9_channel2048_fp64.md",
     },
     ("channel2048", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (75.510784 + 29.308160) * 1e6, "traffic_src_sha": "2927ae77a413376a",
+        "traffic_bytes_per_launch": (75.519744 + 28.427008) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
         "profile": "profiles/k_step9_channel2048_fp32.md",
     },
     ("duct15_96", "fp64"): {
         "src": [_C + "k_d3q15.cu", _C + "lbm_d3q15.cuh"] + _H,
         "fp64_inst_per_node": 234, "fp64_flops_per_node": 321,
-        "traffic_bytes_per_launch": (106.206464 + 59.304704) * 1e6, "traffic_src_sha": "a985be2eb024ea08",
+        "traffic_bytes_per_launch": (106.206976 + 58.378496) * 1e6, "traffic_src_sha": "4ae3105173098402",
         "profile": "profiles/k_step_d3q15_duct_fp64.md",
     },
 }
