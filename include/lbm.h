@@ -193,8 +193,13 @@ int lbm_step(lbm_ctx *ctx, long n);
 /* Macroscopic fields of the current state f(t):
  *   flow : rho[N] = sum f (Eq. 24 / step (vi)); u[dim][N] = (sum f e + h a_pre P/2)/rho
  *   D2Q5 : rho[N] receives phi = sum g + h a_pre S/2 (Eqs. 42-43); u unused (may be NULL)
- * with h = 1 if half_forced, else 0 (u^o and phi^o).  where = 0: host
- * pointers (the call synchronises); where = 1: device pointers (asynchronous).
+ * with h = 1 if half_forced, else 0 (u^o and phi^o).  Rounding: the sums in a
+ * fixed grouping per lattice; j + a_pre P/2 rounded once; u = that times the
+ * correctly rounded 1/rho (each product rounded), so u is within two units in
+ * the last place of the exact quotient.  Every FP64 readback
+ * (lbm_batch_moments, lbm_batch_moments_packed, lbm_batch_step_read) returns
+ * these same bits.  where = 0: host pointers (the call synchronises);
+ * where = 1: device pointers (asynchronous).
  * Errors: LBM_ESTATE, LBM_EINVAL (NULL output), LBM_ECUDA. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, int where, int half_forced);
 
