@@ -658,51 +658,102 @@ k_step27(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apr
 // --------------------------------------------------------------- batched ---
 // (tile loop: lbm_tiles.cuh)
 
+// A batched node in two phases: fetch issues the node's global loads (pulled
+// populations, envelope pair, force or source and velocity values) before
+// finish does any arithmetic and the stores.
+struct In9 {
+    float d[9];
+    float Px, Py;  // force shape at the node (0 without a force)
+    float2 ap;     // (a_pre, (a_pre + a_post)/12)
+    int i;
+};
+
+template <class T>
+__device__ __forceinline__ void fetch9(const BatchItem &B, const BatchLaunch &L, int it, int i, In9 &s)
+{
+    const Geom &g = B.g;
+    s.i = i;
+    if (i >= g.N) return;
+    const T *fin = reinterpret_cast<const T *>(B.buf[(B.parity + L.parity) & 1]);
+    s.ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
+    int x, y;
+    node_xy(g, i, x, y);
+    load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, s.d);
+    s.Px = s.Py = 0.f;
+    if (B.fkind != FK_NONE) {
+        s.Px = field_value_f(B.F, B.fkind, 0, x, y, 0, i);
+        s.Py = field_value_f(B.F, B.fkind, 1, x, y, 0, i);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void finish9(const BatchItem &B, const BatchLaunch &L, int it, In9 &s)
+{
+    const Geom &g = B.g;
+    const int i = s.i;
+    if (i >= g.N) return;
+    T *fout = reinterpret_cast<T *>(B.buf[(B.parity + L.parity + 1) & 1]);
+    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
+    if (B.fkind != FK_NONE) {
+        Fx = s.ap.x * s.Px;
+        Fy = s.ap.x * s.Py;
+        Gx = s.ap.y * s.Px;
+        Gy = s.ap.y * s.Py;
+    }
+    const Rates9f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
+    if (B.variant == 1) collide9_w1(s.d, B.frho_ref, Fx, Fy, Gx, Gy, w);  // uniform over the member
+    else collide9(s.d, B.frho_ref, Fx, Fy, Gx, Gy, w);
+#pragma unroll
+    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(s.d[a]);
+}
+
 template <class T>
 __device__ __forceinline__ void node9(const BatchItem &B, const BatchLaunch &L, int it, int i)
 {
-    const Geom &g = B.g;
-    const int p = B.parity + L.parity;
-    const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
-    T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
-    const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
-    int x, y;
-    node_xy(g, i, x, y);
-    float d[9];
-    load_pulled_dev<LD2Q9, T>(fin, g, x, y, 0, i, d);
-    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
-    if (B.fkind != FK_NONE) {
-        const float Px = field_value_f(B.F, B.fkind, 0, x, y, 0, i), Py = field_value_f(B.F, B.fkind, 1, x, y, 0, i);
-        Fx = ap.x * Px;
-        Fy = ap.x * Py;
-        Gx = ap.y * Px;
-        Gy = ap.y * Py;
-    }
-    const Rates9f w{B.fcoef[0], B.fcoef[1], B.fcoef[2], B.fcoef[3], B.fcoef[4], B.fcoef[5]};
-    if (B.variant == 1) collide9_w1(d, B.frho_ref, Fx, Fy, Gx, Gy, w);  // uniform over the member
-    else collide9(d, B.frho_ref, Fx, Fy, Gx, Gy, w);
-#pragma unroll
-    for (int a = 0; a < 9; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+    In9 s;
+    fetch9<T>(B, L, it, i, s);
+    finish9<T>(B, L, it, s);
 }
 
 // D2Q5 items carry Coef5 (double) in coef[0..11] and the rates in coef[12..15].
+struct In5 {
+    float d[5];
+    float P;        // source shape at the node (0 without a source)
+    float ux, uy;   // advecting velocity (members with a velocity field)
+    float2 ap;      // (a_pre, (a_pre + a_post)/10)
+    int i;
+};
+
 template <class T>
-__device__ __forceinline__ void node5(const BatchItem &B, const BatchLaunch &L, int it, int i)
+__device__ __forceinline__ void fetch5(const BatchItem &B, const BatchLaunch &L, int it, int i, In5 &s)
 {
     const Geom &g = B.g;
-    const int p = B.parity + L.parity;
-    const T *fin = reinterpret_cast<const T *>(B.buf[p & 1]);
-    T *fout = reinterpret_cast<T *>(B.buf[(p + 1) & 1]);
-    const float2 ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
+    s.i = i;
+    if (i >= g.N) return;
+    const T *fin = reinterpret_cast<const T *>(B.buf[(B.parity + L.parity) & 1]);
+    s.ap = L.pairsf ? L.pairsf[(size_t)L.k * L.count + it] : L.inlf[it];
     int x, y;
     node_xy(g, i, x, y);
-    float d[5];
-    load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, d);
+    load_pulled_dev<LD2Q5, T>(fin, g, x, y, 0, i, s.d);
+    s.P = B.fkind != FK_NONE ? field_value_f(B.F, B.fkind, 0, x, y, 0, i) : 0.f;
+    if (B.vkind == FK_GENERAL) {
+        s.ux = field_value_f(B.V, FK_GENERAL, 0, x, y, 0, i);
+        s.uy = field_value_f(B.V, FK_GENERAL, 1, x, y, 0, i);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void finish5(const BatchItem &B, const BatchLaunch &L, int it, In5 &s)
+{
+    const Geom &g = B.g;
+    const int i = s.i;
+    if (i >= g.N) return;
+    T *fout = reinterpret_cast<T *>(B.buf[(B.parity + L.parity + 1) & 1]);
+    float (&d)[5] = s.d;
     float Sp = 0.f, H0 = 0.f;
     if (B.fkind != FK_NONE) {
-        const float P = field_value_f(B.F, B.fkind, 0, x, y, 0, i);
-        Sp = ap.x * P;
-        H0 = ap.y * P;
+        Sp = s.ap.x * s.P;
+        H0 = s.ap.y * s.P;
     }
     const float rref = B.frho_ref;
     if (B.vkind != FK_GENERAL) {
@@ -714,12 +765,18 @@ __device__ __forceinline__ void node5(const BatchItem &B, const BatchLaunch &L, 
         collide5u(d, rref, Sp, H0, k);
     } else {
         const Rates5f w{B.fcoef[12], B.fcoef[13], B.fcoef[14], B.fcoef[15]};
-        const float ux = field_value_f(B.V, FK_GENERAL, 0, x, y, 0, i);
-        const float uy = field_value_f(B.V, FK_GENERAL, 1, x, y, 0, i);
-        collide5(d, rref, Sp, H0, ux, uy, w);
+        collide5(d, rref, Sp, H0, s.ux, s.uy, w);
     }
 #pragma unroll
     for (int a = 0; a < 5; a++) fout[a * g.Np + i] = Dev<T>::to_store(d[a]);
+}
+
+template <class T>
+__device__ __forceinline__ void node5(const BatchItem &B, const BatchLaunch &L, int it, int i)
+{
+    In5 s;
+    fetch5<T>(B, L, it, i, s);
+    finish5<T>(B, L, it, s);
 }
 
 template <class T>
