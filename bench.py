@@ -108,7 +108,8 @@ for _w, _base, _st in (("kolmogorov256", "kolmogorov96", "fp64"), ("kolmogorov51
 FP64_LANES_PER_SM, N_SMS, SM_GHZ = 2, 152, 2.07
 FP64_PEAK_GINST = FP64_LANES_PER_SM * N_SMS * SM_GHZ          # 629.3 G FP64 instructions/s
 FP64_PEAK_TFLOPS = 2 * FP64_PEAK_GINST / 1e3                  # 1.259 TFLOP/s
-FP64_PEAK_NOTE = "derived: 2 FP64 FMA lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flop"
+FP64_PEAK_INST_NOTE = ("derived: 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz (one lane slot per DFMA, DADD or DMUL); "
+                       "measured on independent chains: 1.90 DFMA, 1.60 DADD/DMUL per clock per SM")
 
 
 def src_hash(paths):
@@ -594,14 +595,17 @@ def main():
             "timing": "CUDA events around each batch's launches" + (f" (graph replays of {unit} steps)" if args.graph else
                                                                   (f" ({unit} steps per call)" if unit > 1 else ""))}
     if facts.get("fp64_flops_per_node"):
+        # FP64 kernels: the FP64 unit takes one lane slot per instruction,
+        # whether an FMA (2 flops) or an add or multiply (1 flop), so the
+        # bound is its instruction rate; the flop rate is reported beside it
         tf = facts["fp64_flops_per_node"] * nb / kavg_s / 1e12
         gi = facts["fp64_inst_per_node"] * nb / kavg_s / 1e9
-        pipe = {"achieved": gi, "peak": FP64_PEAK_GINST, "unit": "G FP64 instr/s", "frac": gi / FP64_PEAK_GINST,
-                "inst_per_node": facts["fp64_inst_per_node"]}
-        if tf / FP64_PEAK_TFLOPS > roof["frac"]:
-            roof.update({"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": tf / FP64_PEAK_TFLOPS, "flops_per_node": facts["fp64_flops_per_node"],
-                         "peak_source": FP64_PEAK_NOTE, "fp64_pipe": pipe,
+        if gi / FP64_PEAK_GINST > roof["frac"]:
+            roof.update({"bound": "alu", "achieved": gi, "peak": FP64_PEAK_GINST, "unit": "G FP64 instr/s",
+                         "frac": gi / FP64_PEAK_GINST, "inst_per_node": facts["fp64_inst_per_node"],
+                         "peak_source": FP64_PEAK_INST_NOTE,
+                         "flops": {"achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": tf / FP64_PEAK_TFLOPS, "flops_per_node": facts["fp64_flops_per_node"]},
                          "hbm": {"achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm}})
     if facts.get("profile"):
         roof["profile"] = facts["profile"]
