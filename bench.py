@@ -812,6 +812,8 @@ def main():
             "value": nodes * ke / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": sum(t.numel() * 8 for t in pinned_src),
             "d2h_bytes_per_step": d2h,
             "path": "as above plus lbm_set_source/lbm_set_force(host, full field) per lattice every step"}
+        e2e["timing"] = ("host wall clock around the whole loop (steps back to back as a user runs them; L2 is "
+                         "not flushed between them, unlike the device-timed value)")
     except Exception as exc:  # pragma: no cover - reported, not hidden
         e2e = {"value": None, "error": repr(exc)}
 
