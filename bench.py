@@ -53,22 +53,22 @@ KERNEL_FACTS = {
     },
     ("kolmogorov96", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (95.585536 + 44.614656) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
+        "traffic_bytes_per_launch": (95.584768 + 44.992512) * 1e6, "traffic_src_sha": "6d77d00afbdc12a5",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov256", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (1812.081920 + 1757.261056) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
+        "traffic_bytes_per_launch": (1812.060928 + 1757.052160) * 1e6, "traffic_src_sha": "6d77d00afbdc12a5",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("kolmogorov96", "fp16"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (47.809536 + 6.978816) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
+        "traffic_bytes_per_launch": (47.810048 + 6.926080) * 1e6, "traffic_src_sha": "6d77d00afbdc12a5",
         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md",
     },
     ("batched_sweep256", "fp32"): {
         "src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh"] + _H,
-        "traffic_bytes_per_launch": (382.248960 + 335.472128) * 1e6, "traffic_src_sha": "3b3d6767a485aeb5",
+        "traffic_bytes_per_launch": (379.820800 + 335.240192) * 1e6, "traffic_src_sha": "4eb73b1594169389",
         "profile": "profiles/k_batch9_batched_sweep_fp32.md",
     },
     ("kolmogorov96", "fp64"): {
@@ -85,8 +85,14 @@ KERNEL_FACTS = {
     },
     ("channel2048", "fp32"): {
         "src": [_C + "k_rp.cu"] + _H,
-        "traffic_bytes_per_launch": (75.519744 + 28.427008) * 1e6, "traffic_src_sha": "b23ee6ba325cec50",
+        "traffic_bytes_per_launch": (75.515904 + 28.086272) * 1e6, "traffic_src_sha": "6d77d00afbdc12a5",
         "profile": "profiles/k_step9_channel2048_fp32.md",
+    },
+    ("duct128", "fp64"): {
+        "src": [_C + "k_d3q27.cu"] + _H,
+        "fp64_inst_per_node": 287, "fp64_flops_per_node": 396,
+        "traffic_bytes_per_launch": (453.22 + 398.88) * 1e6, "traffic_src_sha": "b8fd508d60dd017d",
+        "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("duct15_96", "fp64"): {
         "src": [_C + "k_d3q15.cu", _C + "lbm_d3q15.cuh"] + _H,
