@@ -29,9 +29,16 @@ struct Rates15 {
     double s, b, t, q;
 };
 
+// Moments the collision forms on the way (for a fused readback): rho and the
+// un-forced j, grouped as zeroth_first<LD3Q15> groups them, the half-forced
+// j of Eq. 8A and 1/rho (__drcp_rn).
+struct Mom15 {
+    double rho, j[3], jf[3], rinv;
+};
+
 // F = a_pre P (Eq. 8A), Fq = a_post P (second half step).
 __device__ __forceinline__ void collide(double (&f)[15], const double (&F)[3], const double (&Fq)[3],
-                                        const Rates15 &w)
+                                        const Rates15 &w, Mom15 &mo)
 {
     // Axis pairs and the corner sign transform: S_{ijk} = sum_c s_x^i s_y^j s_z^k f_c.
     const double axs = f[1] + f[2], axd = f[1] - f[2];
@@ -54,8 +61,10 @@ __device__ __forceinline__ void collide(double (&f)[15], const double (&F)[3], c
     const double kxyy = Sx, kxxy = Sy, kxxz = Sz, kxyz = Sxyz, kxxyy = S;
 
     // Eq. 8A: half-forced momentum J = rho u.
-    const double Jx = axd + Sx + 0.5 * F[0], Jy = ayd + Sy + 0.5 * F[1], Jz = azd + Sz + 0.5 * F[2];
+    const double jx0 = axd + Sx, jy0 = ayd + Sy, jz0 = azd + Sz;
+    const double Jx = fma(0.5, F[0], jx0), Jy = fma(0.5, F[1], jy0), Jz = fma(0.5, F[2], jz0);
     const double ir = __drcp_rn(rho);
+    mo = Mom15{rho, {jx0, jy0, jz0}, {Jx, Jy, Jz}, ir};
     const double ux = Jx * ir, uy = Jy * ir, uz = Jz * ir;
 
     // Eq. 6A.  Second order: central moments about u.
@@ -134,7 +143,8 @@ k_step(const __grid_constant__ Planes<double, 15> P, Geom g, FieldDev Fd, double
             Fq[d] = apost * P;
         }
     }
-    collide(f, F, Fq, w);
+    Mom15 mo;
+    collide(f, F, Fq, w, mo);
 #pragma unroll
     for (int a = 0; a < 15; a++) P.out[a][i] = f[a];
 }
@@ -152,7 +162,6 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     node_xyz(g, i, x, y, z);
     double f[15];
     load_pulled<LD3Q15>(fin, g, x, y, z, i, f);
-    if (L.mrho) fused_fields<LD3Q15>(B, L, it, i, x, y, z, f, ap.x);
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (B.fkind != FK_NONE) {
 #pragma unroll
@@ -163,7 +172,15 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
         }
     }
     const Rates15 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3]};
-    collide(f, F, Fq, w);
+    Mom15 mo;
+    collide(f, F, Fq, w, mo);
+    if (L.mrho) {
+        // fused readback of f(t)'s fields from the collision's own moments;
+        // the same bits as store_fields (F = a_pre P)
+        const bool forced = L.mhalf && B.fkind != FK_NONE;
+        const double jd[3] = {forced ? mo.jf[0] : mo.j[0], forced ? mo.jf[1] : mo.j[1], forced ? mo.jf[2] : mo.j[2]};
+        put_fields<LD3Q15>(mo.rho, jd, mo.rinv, i, g.N, __ldg(L.moff + it), L.mrho, L.mu);
+    }
 #pragma unroll
     for (int a = 0; a < 15; a++) fout[a * g.Np + i] = f[a];
 }

@@ -28,6 +28,26 @@ struct LD3Q15 {
     __host__ __device__ static constexpr double w(int a) { return a == 0 ? 2.0 / 9.0 : (a <= 6 ? 1.0 / 9.0 : 1.0 / 72.0); }
 };
 
+// Zeroth and first moments grouped as the D3Q15 collision forms them: the
+// axis pairs f_+ +/- f_-, then the corner sign transform (pairs along x, then
+// along y, then along z), so that the collision's own rho and j are these
+// bits (m0 = (((f_0 + ax) + ay) + az) + corners, j_d = axis difference +
+// corner sum).  Declared as a specialization of zeroth_first.
+template <class L>
+__device__ __forceinline__ void zeroth_first(const double (&f)[L::Q], double &m0, double (&j)[3]);
+template <>
+__device__ __forceinline__ void zeroth_first<LD3Q15>(const double (&f)[15], double &m0, double (&j)[3])
+{
+    const double A1 = f[7] + f[8], B1 = f[7] - f[8], A2 = f[9] + f[10], B2 = f[9] - f[10];
+    const double A3 = f[11] + f[12], B3 = f[11] - f[12], A4 = f[13] + f[14], B4 = f[13] - f[14];
+    const double P1 = A1 + A2, Q1 = A1 - A2, P2 = A3 + A4, Q2 = A3 - A4;
+    const double R1 = B1 + B2, R2 = B3 + B4;
+    m0 = (((f[0] + (f[1] + f[2])) + (f[3] + f[4])) + (f[5] + f[6])) + (P1 + P2);
+    j[0] = (f[1] - f[2]) + (R1 + R2);
+    j[1] = (f[3] - f[4]) + (Q1 + Q2);
+    j[2] = (f[5] - f[6]) + (P1 - P2);
+}
+
 // Equilibrium population a at (rho, u): the populations whose moments of the
 // fifteen monomials 1, e_x, e_y, e_z, e_x e_y, e_x e_z, e_y e_z, e_x^2, e_y^2,
 // e_z^2, e_x e_y^2, e_x^2 e_y, e_x^2 e_z, e_x e_y e_z, e_x^2 e_y^2 (a basis of

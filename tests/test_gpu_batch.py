@@ -27,6 +27,12 @@ def _members(kind):
         w2, _ = _random_workload(W.D2Q9, (40, 7, 1), (1, 0, 0), seed=6)
         ws += [w, w2]
         fulls = [None, None, None, full, None]
+    elif kind == "d3q15":
+        ws = [W.duct15(n=9, nx=4)]
+        w, full = _random_workload(W.D3Q15, (7, 6, 5), (1, 1, 1), seed=9, kind="full")
+        w2, _ = _random_workload(W.D3Q15, (5, 8, 6), (0, 1, 0), seed=10)
+        ws += [w, w2]
+        fulls = [None, full, None]
     else:
         ws = [W.kolmogorov(shape=(12, 10, 8)), W.duct(n=9, nx=4)]
         w, full = _random_workload(W.D3Q27, (7, 6, 5), (1, 1, 1), seed=8, kind="full")
@@ -45,7 +51,7 @@ def _make(w, full, envelope_steps=None):
     return G
 
 
-@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27", "d3q15"])
 def test_batch_equals_individual_steps_bitwise(kind):
     ws, fulls = _members(kind)
     solo = [_make(w, f) for w, f in zip(ws, fulls)]
@@ -94,7 +100,7 @@ def test_batch_after_a_member_stepped_alone():
         assert np.array_equal(a.get_populations(), b.get_populations())
 
 
-@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27", "d3q15"])
 def test_batch_matches_oracle(kind):
     ws, fulls = _members(kind)
     Gs = [_make(w, f) for w, f in zip(ws, fulls)]
@@ -331,7 +337,7 @@ def test_fp64_scalar_persistent_runs_cross_members():
 
 
 def test_batch_moments_equal_member_moments():
-    for kind in ("d2q5", "d2q9", "d3q27"):
+    for kind in ("d2q5", "d2q9", "d3q27", "d3q15"):
         ws, fulls = _members(kind)
         Gs = [_make(w, f) for w, f in zip(ws, fulls)]
         B = lbm.Batch(Gs)
@@ -404,7 +410,7 @@ def test_readbacks_three_in_flight(where):
     T.close()
 
 
-@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27"])
+@pytest.mark.parametrize("kind", ["d2q5", "d2q9", "d3q27", "d3q15"])
 @pytest.mark.parametrize("where", [1, 3])
 def test_step_read_writes_the_fields_each_step_starts_from(kind, where):
     """lbm_batch_step_read: each call steps the batch once and its kernel
@@ -418,7 +424,7 @@ def test_step_read_writes_the_fields_each_step_starts_from(kind, where):
         # plus a member without a source and one with an advecting-velocity field
         ws += [dataclasses.replace(ws[0], tables=None), ws[1]]
         fulls += [None, None]
-    elif kind == "d2q9":
+    else:
         ws.append(dataclasses.replace(ws[0], tables=None))  # plus a member without a force
         fulls.append(None)
     Gs = [_make(w, f) for w, f in zip(ws, fulls)]
