@@ -97,7 +97,7 @@ KERNEL_FACTS = {
     ("duct15_96", "fp64"): {
         "src": [_C + "k_d3q15.cu", _C + "lbm_d3q15.cuh"] + _H,
         "fp64_inst_per_node": 234, "fp64_flops_per_node": 321,
-        "traffic_bytes_per_launch": (106.206976 + 58.378496) * 1e6, "traffic_src_sha": "4ae3105173098402",
+        "traffic_bytes_per_launch": (106.21 + 59.05) * 1e6, "traffic_src_sha": "8edf4caea9b44f6a",
         "profile": "profiles/k_step_d3q15_duct_fp64.md",
     },
 }
