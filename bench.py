@@ -73,8 +73,8 @@ KERNEL_FACTS = {
     },
     ("kolmogorov96", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 287, "fp64_flops_per_node": 396,
-        "traffic_bytes_per_launch": (191.155456 + 137.319680) * 1e6, "traffic_src_sha": "b8fd508d60dd017d",
+        "fp64_inst_per_node": 271, "fp64_flops_per_node": 359,
+        "traffic_bytes_per_launch": (191.15 + 137.35) * 1e6, "traffic_src_sha": "75a9acce2ab190b0",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("channel2048", "fp64"): {
@@ -90,8 +90,8 @@ KERNEL_FACTS = {
     },
     ("duct128", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 287, "fp64_flops_per_node": 396,
-        "traffic_bytes_per_launch": (453.22 + 398.88) * 1e6, "traffic_src_sha": "b8fd508d60dd017d",
+        "fp64_inst_per_node": 271, "fp64_flops_per_node": 359,
+        "traffic_bytes_per_launch": (453.03 + 398.75) * 1e6, "traffic_src_sha": "75a9acce2ab190b0",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("duct15_96", "fp64"): {

@@ -17,6 +17,8 @@
 // node costs ~400 FP64 operations instead of the ~1500 of dense 27 x 27
 // transforms.  Moment index k = a + 3 b + 9 c matches the velocity index
 // alpha = (ex+1) + 3 (ey+1) + 9 (ez+1) position by position.
+#include <utility>
+
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
 #include "lbm_tiles.cuh"
@@ -83,15 +85,76 @@ __device__ __forceinline__ void along(double (&m)[27], Op op)
     }
 }
 
+// The back-shift with a compile-time zero pattern: bit k of Z set means m[k]
+// is exactly 0 on entry (the unit-rates collision leaves 16 of the 27 halved
+// central moments at 0).  An operation with a known-zero operand is left out
+// and its value taken as is: fma(a, 0, x) = x, fma(a, x, 0) = a x, x + 0 = x
+// (equal to the full operation up to the sign of a zero result).  Z = 0 is
+// shift_bwd_h on every line.
+template <int AX>
+__host__ __device__ constexpr int line_base(int t)
+{
+    return AX == 0 ? 3 * t : (AX == 1 ? (t % 3) + 9 * (t / 3) : t);
+}
+template <int AX>
+__host__ __device__ constexpr int line_stride()
+{
+    return AX == 0 ? 1 : (AX == 1 ? 3 : 9);
+}
+
+// Zero pattern after shift_bwd_h along AX: on a line (k0, k1, k2), the new k1
+// is 0 when k0 and k1 are, the new k2 when all three are.
+template <int AX>
+__host__ __device__ constexpr unsigned shift_zeros(unsigned z)
+{
+    unsigned r = z;
+    for (int t = 0; t < 9; t++) {
+        const int p0 = line_base<AX>(t), p1 = p0 + line_stride<AX>(), p2 = p0 + 2 * line_stride<AX>();
+        const bool z01 = ((z >> p0) & 1u) && ((z >> p1) & 1u), z012 = z01 && ((z >> p2) & 1u);
+        r = (r & ~(1u << p1) & ~(1u << p2)) | (z01 ? 1u << p1 : 0u) | (z012 ? 1u << p2 : 0u);
+    }
+    return r;
+}
+
+template <unsigned Z, int AX, int T>
+__device__ __forceinline__ void shift_line(double (&m)[27], double u, double uh)
+{
+    constexpr int p0 = line_base<AX>(T), p1 = p0 + line_stride<AX>(), p2 = p0 + 2 * line_stride<AX>();
+    constexpr bool z0 = (Z >> p0) & 1u, z1 = (Z >> p1) & 1u, z2 = (Z >> p2) & 1u;
+    if constexpr (z0 && z1) {
+        return;  // m1 = 0, and k2 keeps its value
+    } else {
+        double m1;
+        if constexpr (z0) m1 = m[p1];
+        else if constexpr (z1) m1 = uh * m[p0];
+        else m1 = fma(uh, m[p0], m[p1]);
+        double s;
+        if constexpr (z1) s = m1;
+        else s = m[p1] + m1;
+        if constexpr (z2) m[p2] = u * s;
+        else m[p2] = fma(u, s, m[p2]);
+        m[p1] = m1;
+    }
+}
+
+template <unsigned Z, int AX, int... T>
+__device__ __forceinline__ void shift_lines(double (&m)[27], double u, double uh, std::integer_sequence<int, T...>)
+{
+    (shift_line<Z, AX, T>(m, u, uh), ...);
+}
+
 // Halved post-collision central moments about u -> populations: back-shift,
-// the post-collision force in moment space, inverse raw transform.
+// the post-collision force in moment space, inverse raw transform.  Z: the
+// moments known to be exactly 0 on entry (see shift_line).
+template <unsigned Z>
 __device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, double uz, const double (&F)[3],
                                        const double (&Fq)[3])
 {
     const double hx = 0.5 * ux, hy = 0.5 * uy, hz = 0.5 * uz;
-    along<0>(m, [ux, hx](double &a, double &b, double &c) { shift_bwd_h(a, b, c, ux, hx); });
-    along<1>(m, [uy, hy](double &a, double &b, double &c) { shift_bwd_h(a, b, c, uy, hy); });
-    along<2>(m, [uz, hz](double &a, double &b, double &c) { shift_bwd_h(a, b, c, uz, hz); });
+    constexpr unsigned Zy = shift_zeros<0>(Z), Zz = shift_zeros<1>(Zy);
+    shift_lines<Z, 0>(m, ux, hx, std::make_integer_sequence<int, 9>{});
+    shift_lines<Zy, 1>(m, uy, hy, std::make_integer_sequence<int, 9>{});
+    shift_lines<Zz, 2>(m, uz, hz, std::make_integer_sequence<int, 9>{});
 
     // K_1 g_1 in moment space, g = (F_pre + F_post) / 36: e_x changes m_100 by
     // 18 g, m_120 and m_102 by 12 g, m_122 by 8 g (halved: 9 g, 3 g, 3 g, g).
@@ -179,8 +242,14 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
         m[26] = fma(0.125 * (1.0 - w.w6), m[26], (w.w6 * (1.0 / 216.0)) * rho);
     }
 
-    finish(m, ux, uy, uz, F, Fq);
+    finish<0u>(m, ux, uy, uz, F, Fq);
 }
+
+// Halved central moments the unit-rates collision leaves exactly 0: all but
+// 000, 200, 020, 002, 110, 101, 011, 220, 202, 022, 222 (index a + 3b + 9c).
+constexpr unsigned kNonZeroW1 = (1u << 0) | (1u << 2) | (1u << 6) | (1u << 18) | (1u << 4) | (1u << 10) | (1u << 12) |
+                                (1u << 8) | (1u << 20) | (1u << 24) | (1u << 26);
+constexpr unsigned kZeroW1 = ((1u << 27) - 1u) & ~kNonZeroW1;
 
 // The same collision when omega_3 = omega_4 = omega_5 = omega_6 = 1 (the
 // paper's choice for the higher moments, Sec. 6): every central moment of
@@ -251,7 +320,7 @@ __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3]
     m[20] = e4;
     m[24] = e4;
     m[26] = rho * (1.0 / 216.0);
-    finish(m, ux, uy, uz, F, Fq);
+    finish<kZeroW1>(m, ux, uy, uz, F, Fq);
 }
 
 template <int FK, bool W1>
