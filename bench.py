@@ -73,14 +73,14 @@ KERNEL_FACTS = {
     },
     ("kolmogorov96", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 271, "fp64_flops_per_node": 359,
-        "traffic_bytes_per_launch": (191.15 + 137.35) * 1e6, "traffic_src_sha": "75a9acce2ab190b0",
+        "fp64_inst_per_node": 255, "fp64_flops_per_node": 333,
+        "traffic_bytes_per_launch": (191.15 + 137.65) * 1e6, "traffic_src_sha": "cc3a97d2b58383ec",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("channel2048", "fp64"): {
         "src": [_C + "k_d2q9.cu"] + _H,
-        "fp64_inst_per_node": 85, "fp64_flops_per_node": 116,
-        "traffic_bytes_per_launch": (151.071232 + 100.027648) * 1e6, "traffic_src_sha": "a82db62a8045ce0b",
+        "fp64_inst_per_node": 79, "fp64_flops_per_node": 107,
+        "traffic_bytes_per_launch": (151.08 + 100.13) * 1e6, "traffic_src_sha": "b84c6a4d0aa9c3cc",
         "profile": "profiles/k_step_d2q9_channel2048_fp64.md",
     },
     ("channel2048", "fp32"): {
@@ -90,8 +90,8 @@ KERNEL_FACTS = {
     },
     ("duct128", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
-        "fp64_inst_per_node": 271, "fp64_flops_per_node": 359,
-        "traffic_bytes_per_launch": (453.03 + 398.75) * 1e6, "traffic_src_sha": "75a9acce2ab190b0",
+        "fp64_inst_per_node": 255, "fp64_flops_per_node": 333,
+        "traffic_bytes_per_launch": (453.09 + 398.94) * 1e6, "traffic_src_sha": "cc3a97d2b58383ec",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("duct15_96", "fp64"): {

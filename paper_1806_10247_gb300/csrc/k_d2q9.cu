@@ -92,6 +92,8 @@ __device__ __forceinline__ void collide(double (&f)[9], double Fx, double Fy, do
 // already in j) and m_12 by 4 g_1.  The first raw moments are carried as j
 // itself (not rebuilt as rho (j / rho)), so the step transports momentum
 // without a rounding of its own.  About 80 FP64 operations instead of 132.
+// XO: the force has no y component (its terms, additions of 0, are left out).
+template <bool XO = false>
 __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy, double Gx, double Gy,
                                            const Rates9 &w, Mom9 &mo)
 {
@@ -102,7 +104,7 @@ __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy,
     const double B0 = f[2] + s1, C0 = f[4] + s2;
     const double rho = (f[0] + s0) + (B0 + C0);
     const double jx0 = d0 + (d1 + d2), jy0 = B0 - C0;
-    const double jx = fma(0.5, Fx, jx0), jy = fma(0.5, Fy, jy0);  // Eq. 25
+    const double jx = fma(0.5, Fx, jx0), jy = XO ? jy0 : fma(0.5, Fy, jy0);  // Eq. 25
     const double mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;
     const double rinv = __drcp_rn(rho);
     const double ux = jx * rinv, uy = jy * rinv;
@@ -129,8 +131,10 @@ __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy,
     // post-collision force (Eq. 31), halved: m_10 gains F_post / 2 = 6 Gx - Fx / 2, m_12 gains 4 Gx
     N10 = fma(3.0, Gx, fma(-0.25, Fx, N10));
     N12 += Gx;
-    N01 = fma(3.0, Gy, fma(-0.25, Fy, N01));
-    N21 += Gy;
+    if constexpr (!XO) {
+        N01 = fma(3.0, Gy, fma(-0.25, Fy, N01));
+        N21 += Gy;
+    }
     // inverse transform along y, then along x
     const double P0m = N02 - N01, P00 = fma(-2.0, N02, N00), P0p = N02 + N01;  // x-order 0; e_y = -1, 0, +1
     const double P1m = N12 - N11, P10 = fma(-2.0, N12, N10), P1p = N12 + N11;
@@ -146,7 +150,8 @@ __device__ __forceinline__ void collide_w1(double (&f)[9], double Fx, double Fy,
     f[7] = P2m - P1m;
 }
 
-template <int FK, bool W1>
+// XO (unit higher rates only): the force has no y component (checked on the host).
+template <int FK, bool W1, bool XO>
 __global__ void __launch_bounds__(kBlock)
 k_step(const __grid_constant__ Planes<double, 9> P, Geom g, FieldDev F, double apre, double gsum, Rates9 w)
 {
@@ -158,14 +163,17 @@ k_step(const __grid_constant__ Planes<double, 9> P, Geom g, FieldDev F, double a
     load_pulled<LD2Q9>(P, g, x, y, 0, i, f);
     double Fx = 0.0, Fy = 0.0, Gx = 0.0, Gy = 0.0;
     if (FK != FK_NONE) {
-        const double Px = field_value(F, FK, 0, x, y, 0, i), Py = field_value(F, FK, 1, x, y, 0, i);
+        const double Px = field_value(F, FK, 0, x, y, 0, i);
         Fx = apre * Px;
-        Fy = apre * Py;
         Gx = gsum * Px;
-        Gy = gsum * Py;
+        if (!XO) {
+            const double Py = field_value(F, FK, 1, x, y, 0, i);
+            Fy = apre * Py;
+            Gy = gsum * Py;
+        }
     }
     Mom9 mo;
-    if (W1) collide_w1(f, Fx, Fy, Gx, Gy, w, mo);
+    if (W1) collide_w1<XO>(f, Fx, Fy, Gx, Gy, w, mo);
     else collide(f, Fx, Fy, Gx, Gy, w, mo);
 #pragma unroll
     for (int a = 0; a < 9; a++) P.out[a][i] = f[a];
@@ -316,10 +324,17 @@ template <bool W1>
 void step_launch(const LaunchArgs &a, int grid, double gsum, const Rates9 &w)
 {
     const Planes<double, 9> P = make_planes<double, 9>(a.fin, a.fout, a.g.Np);
+    const bool xo = W1 && force_x_only(a.fkind, a.F, 2);
     switch (a.fkind) {
-    case FK_NONE: k_step<FK_NONE, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
-    case FK_CONST: k_step<FK_CONST, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
-    default: k_step<FK_GENERAL, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
+    case FK_NONE: k_step<FK_NONE, W1, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w); break;
+    case FK_CONST:
+        if (xo) k_step<FK_CONST, W1, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w);
+        else k_step<FK_CONST, W1, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w);
+        break;
+    default:
+        if (xo) k_step<FK_GENERAL, W1, W1><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w);
+        else k_step<FK_GENERAL, W1, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, gsum, w);
+        break;
     }
 }
 

@@ -145,8 +145,9 @@ __device__ __forceinline__ void shift_lines(double (&m)[27], double u, double uh
 
 // Halved post-collision central moments about u -> populations: back-shift,
 // the post-collision force in moment space, inverse raw transform.  Z: the
-// moments known to be exactly 0 on entry (see shift_line).
-template <unsigned Z>
+// moments known to be exactly 0 on entry (see shift_line).  XO: the force has
+// no y and z components (their terms, additions of 0, are left out).
+template <unsigned Z, bool XO>
 __device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, double uz, const double (&F)[3],
                                        const double (&Fq)[3])
 {
@@ -161,13 +162,16 @@ __device__ __forceinline__ void finish(double (&m)[27], double ux, double uy, do
     // m_100 = rho u already carries F_pre / 2 (the pre-collision shift), so
     // only F_post / 2 is added to it.
     {
-        const double sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+        const double sx = F[0] + Fq[0];
         m[1] = fma(0.25, Fq[0], m[1]);
-        m[3] = fma(0.25, Fq[1], m[3]);
-        m[9] = fma(0.25, Fq[2], m[9]);
         m[7] = fma(sx, 1.0 / 12.0, m[7]); m[19] = fma(sx, 1.0 / 12.0, m[19]); m[25] = fma(sx, 1.0 / 36.0, m[25]);
-        m[5] = fma(sy, 1.0 / 12.0, m[5]); m[21] = fma(sy, 1.0 / 12.0, m[21]); m[23] = fma(sy, 1.0 / 36.0, m[23]);
-        m[11] = fma(sz, 1.0 / 12.0, m[11]); m[15] = fma(sz, 1.0 / 12.0, m[15]); m[17] = fma(sz, 1.0 / 36.0, m[17]);
+        if constexpr (!XO) {
+            const double sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+            m[3] = fma(0.25, Fq[1], m[3]);
+            m[9] = fma(0.25, Fq[2], m[9]);
+            m[5] = fma(sy, 1.0 / 12.0, m[5]); m[21] = fma(sy, 1.0 / 12.0, m[21]); m[23] = fma(sy, 1.0 / 36.0, m[23]);
+            m[11] = fma(sz, 1.0 / 12.0, m[11]); m[15] = fma(sz, 1.0 / 12.0, m[15]); m[17] = fma(sz, 1.0 / 36.0, m[17]);
+        }
     }
 
     along<2>(m, [](double &a, double &b, double &c) { raw_bwd_h(a, b, c); });
@@ -182,7 +186,9 @@ struct Mom27 {
     double rho, j[3], jf[3], rinv;
 };
 
-// F: pre-collision force a_pre P; Fq: post-collision force a_post P.
+// F: pre-collision force a_pre P; Fq: post-collision force a_post P; XO: the
+// force has no y and z components.
+template <bool XO = false>
 __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
                                         const Rates27 &w, Mom27 &mo)
 {
@@ -195,8 +201,10 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
     mo.j[1] = m[3];
     mo.j[2] = m[9];
     m[1] = fma(0.5, F[0], m[1]);
-    m[3] = fma(0.5, F[1], m[3]);
-    m[9] = fma(0.5, F[2], m[9]);
+    if constexpr (!XO) {
+        m[3] = fma(0.5, F[1], m[3]);
+        m[9] = fma(0.5, F[2], m[9]);
+    }
     const double rho = m[0];
     const double rinv = __drcp_rn(rho);
     mo.rho = rho;
@@ -242,7 +250,7 @@ __device__ __forceinline__ void collide(double (&m)[27], const double (&F)[3], c
         m[26] = fma(0.125 * (1.0 - w.w6), m[26], (w.w6 * (1.0 / 216.0)) * rho);
     }
 
-    finish<0u>(m, ux, uy, uz, F, Fq);
+    finish<0u, XO>(m, ux, uy, uz, F, Fq);
 }
 
 // Halved central moments the unit-rates collision leaves exactly 0: all but
@@ -256,6 +264,7 @@ constexpr unsigned kZeroW1 = ((1u << 27) - 1u) & ~kNonZeroW1;
 // order 3..6 lands exactly on its Maxwellian value, so only the raw moments of
 // order <= 2 are formed (partial transforms) and the forward shift reduces to
 // the six second-order central moments.
+template <bool XO = false>
 __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3], const double (&Fq)[3],
                                            const Rates27 &w, Mom27 &mo)
 {
@@ -286,8 +295,10 @@ __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3]
     mo.j[1] = jy;
     mo.j[2] = jz;
     jx = fma(0.5, F[0], jx);
-    jy = fma(0.5, F[1], jy);
-    jz = fma(0.5, F[2], jz);
+    if constexpr (!XO) {
+        jy = fma(0.5, F[1], jy);
+        jz = fma(0.5, F[2], jz);
+    }
     const double rinv = __drcp_rn(rho);
     mo.rho = rho;
     mo.jf[0] = jx;
@@ -320,10 +331,11 @@ __device__ __forceinline__ void collide_w1(double (&m)[27], const double (&F)[3]
     m[20] = e4;
     m[24] = e4;
     m[26] = rho * (1.0 / 216.0);
-    finish<kZeroW1>(m, ux, uy, uz, F, Fq);
+    finish<kZeroW1, XO>(m, ux, uy, uz, F, Fq);
 }
 
-template <int FK, bool W1>
+// XO: the force has no y and z components (checked on the host).
+template <int FK, bool W1, bool XO>
 __global__ void __launch_bounds__(kBlock)
 k_step(const __grid_constant__ Planes<double, 27> P, Geom g, FieldDev Fd, double apre, double apost, Rates27 w)
 {
@@ -336,15 +348,15 @@ k_step(const __grid_constant__ Planes<double, 27> P, Geom g, FieldDev Fd, double
     double F[3] = {0.0, 0.0, 0.0}, Fq[3] = {0.0, 0.0, 0.0};
     if (FK != FK_NONE) {
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
+        for (int d = 0; d < (XO ? 1 : 3); d++) {
             const double P = field_value(Fd, FK, d, x, y, z, i);
             F[d] = apre * P;
             Fq[d] = apost * P;
         }
     }
     Mom27 mo;
-    if (W1) collide_w1(m, F, Fq, w, mo);
-    else collide(m, F, Fq, w, mo);
+    if (W1) collide_w1<XO>(m, F, Fq, w, mo);
+    else collide<XO>(m, F, Fq, w, mo);
 #pragma unroll
     for (int a = 0; a < 27; a++) P.out[a][i] = m[a];
 }
@@ -421,18 +433,21 @@ cudaError_t d3q27_step(const LaunchArgs &a)
     const int grid = (a.g.N + kBlock - 1) / kBlock;
     const bool w1 = high_rates_one(a.omega);
     const Planes<double, 27> P = make_planes<double, 27>(a.fin, a.fout, a.g.Np);
+    const bool xo = force_x_only(a.fkind, a.F, 3);
     switch (a.fkind) {
     case FK_NONE:
-        if (w1) k_step<FK_NONE, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_NONE, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        if (w1) k_step<FK_NONE, true, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_NONE, false, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     case FK_CONST:
-        if (w1) k_step<FK_CONST, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_CONST, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        if (w1 && xo) k_step<FK_CONST, true, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else if (w1) k_step<FK_CONST, true, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_CONST, false, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     default:
-        if (w1) k_step<FK_GENERAL, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
-        else k_step<FK_GENERAL, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        if (w1 && xo) k_step<FK_GENERAL, true, true><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else if (w1) k_step<FK_GENERAL, true, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
+        else k_step<FK_GENERAL, false, false><<<grid, kBlock, 0, a.stream>>>(P, a.g, a.F, a.apre, a.apost, w);
         break;
     }
     return cudaGetLastError();

@@ -8,6 +8,19 @@
 
 namespace lbmk {
 
+// Host: a force of kind `fkind` has identically zero components 1 .. dim-1
+// (along x only), so that a step kernel may leave their terms out.
+inline bool force_x_only(int fkind, const FieldDev &F, int dim)
+{
+    bool zero = true;
+    for (int c = 1; c < dim; c++) {
+        if (fkind == FK_CONST) zero = zero && F.cval[c] == 0.0;
+        else if (fkind == FK_GENERAL) zero = zero && F.sep && ((F.zmask >> c) & 1);
+        else zero = false;
+    }
+    return zero;
+}
+
 // Everything one launch of a step / moments / reduction kernel needs.
 struct LaunchArgs {
     Geom g;
