@@ -74,13 +74,13 @@ KERNEL_FACTS = {
     ("kolmogorov96", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
         "fp64_inst_per_node": 255, "fp64_flops_per_node": 333,
-        "traffic_bytes_per_launch": (191.15 + 137.65) * 1e6, "traffic_src_sha": "cc3a97d2b58383ec",
+        "traffic_bytes_per_launch": (191.151104 + 137.880320) * 1e6, "traffic_src_sha": "4be8a09ad4918a7a",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("channel2048", "fp64"): {
         "src": [_C + "k_d2q9.cu"] + _H,
         "fp64_inst_per_node": 79, "fp64_flops_per_node": 107,
-        "traffic_bytes_per_launch": (151.08 + 100.13) * 1e6, "traffic_src_sha": "b84c6a4d0aa9c3cc",
+        "traffic_bytes_per_launch": (151.018240 + 99.837696) * 1e6, "traffic_src_sha": "018f6162beb1528d",
         "profile": "profiles/k_step_d2q9_channel2048_fp64.md",
     },
     ("channel2048", "fp32"): {
@@ -91,7 +91,7 @@ KERNEL_FACTS = {
     ("duct128", "fp64"): {
         "src": [_C + "k_d3q27.cu"] + _H,
         "fp64_inst_per_node": 255, "fp64_flops_per_node": 333,
-        "traffic_bytes_per_launch": (453.09 + 398.94) * 1e6, "traffic_src_sha": "cc3a97d2b58383ec",
+        "traffic_bytes_per_launch": (453.056768 + 399.132416) * 1e6, "traffic_src_sha": "4be8a09ad4918a7a",
         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md",
     },
     ("duct15_96", "fp64"): {

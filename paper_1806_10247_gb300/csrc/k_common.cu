@@ -707,11 +707,16 @@ cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile,
 bool d3q27_high_rates_one(const double omega[9]);
 bool d2q9_high_rates_one(const double omega[9]);
 
-int batch_variant(int lattice, const double omega[9])
+int batch_variant(int lattice, const double omega[9], int fkind, const FieldDev &F)
 {
-    if (lattice == LD3Q27::ID) return d3q27_high_rates_one(omega) ? 1 : 0;
-    if (lattice == LD2Q9::ID) return d2q9_high_rates_one(omega) ? 1 : 0;
-    return 0;
+    int w1 = 0, dim = 2;
+    if (lattice == LD3Q27::ID) {
+        w1 = d3q27_high_rates_one(omega) ? 1 : 0;
+        dim = 3;
+    } else if (lattice == LD2Q9::ID) {
+        w1 = d2q9_high_rates_one(omega) ? 1 : 0;
+    }
+    return w1 && force_x_only(fkind, F, dim) ? 3 : w1;
 }
 
 int batch_resident(int lattice, int tile)

@@ -278,7 +278,8 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     }
     const Rates9 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
     Mom9 mo;
-    if (B.variant == 1) collide_w1(f, Fx, Fy, Gx, Gy, w, mo);  // uniform over the member
+    if (B.variant == 3) collide_w1<true>(f, Fx, Fy, Gx, Gy, w, mo);  // uniform over the member
+    else if (B.variant == 1) collide_w1<false>(f, Fx, Fy, Gx, Gy, w, mo);
     else collide(f, Fx, Fy, Gx, Gy, w, mo);
     if (L.mrho) {
         // fused readback of f(t)'s fields from the collision's own moments;

@@ -385,7 +385,8 @@ __device__ __forceinline__ void batch_node(const BatchItem &B, const BatchLaunch
     }
     const Rates27 w{B.coef[0], B.coef[1], B.coef[2], B.coef[3], B.coef[4], B.coef[5]};
     Mom27 mo;
-    if (B.variant == 1) collide_w1(m, F, Fq, w, mo);  // uniform over the block's tile
+    if (B.variant == 3) collide_w1<true>(m, F, Fq, w, mo);  // uniform over the member
+    else if (B.variant == 1) collide_w1<false>(m, F, Fq, w, mo);
     else collide(m, F, Fq, w, mo);
     if (L.mrho) {
         // fused readback of f(t)'s fields from the collision's own moments;

@@ -347,7 +347,8 @@ int refresh_descriptors(lbm_batch *b, int *parity)
         for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
         it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
         it.frho_ref = (float)it.rho_ref;
-        it.variant = batch_variant(c->lattice, c->omega);
+        it.variant = batch_variant(c->lattice, c->omega, it.fkind, it.F);
+        if (c->storage != LBM_FP64) it.variant &= 1;  // the reduced-precision kernels have no force-along-x form
         b->item_version[i] = c->version;
         b->item_buf0[i] = c->A;
     }

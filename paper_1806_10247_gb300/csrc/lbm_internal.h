@@ -128,9 +128,11 @@ cudaError_t batch_moments(int lattice, int storage, const BatchMoments &M, int n
 cudaError_t batch_step(int lattice, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
 // Blocks of the FP64 batch kernel resident on the whole GPU at once.
 int batch_resident(int lattice, int tile);
-// Collision variant of a batch member (BatchItem::variant): D3Q27 1 when
-// omega_3..omega_6 = 1 (the same choice the single-lattice launch makes).
-int batch_variant(int lattice, const double omega[9]);
+// Collision variant of a batch member (BatchItem::variant): bit 0 set when
+// the higher-order rates are 1 (D3Q27 omega_3..omega_6, D2Q9 omega_6..omega_8),
+// bit 1 set as well when the force acts along x only (force_x_only) -- the
+// same choices the single-lattice launch makes.
+int batch_variant(int lattice, const double omega[9], int fkind, const FieldDev &F);
 // tile = nodes per tile = threads per block: 128, 256 or 512.
 cudaError_t rp_batch_step(int lattice, int storage, const BatchLaunch &L, int nblocks, int tile, cudaStream_t s);
 // Blocks of the reduced-precision batch kernel resident on the whole GPU at once.
