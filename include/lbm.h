@@ -20,7 +20,8 @@
  *  - Ownership: the library owns the population buffers of a context.  Caller
  *    pointers are read or written only during the call and never retained;
  *    fields passed to lbm_set_force / lbm_set_source / lbm_set_velocity are
- *    copied into library memory.
+ *    copied into library memory (a device field in stream order on the
+ *    context's stream, see LBM_FIELD_FULL_DEVICE).
  *  - Streams: all device work of a context is issued on the CUDA stream given
  *    to lbm_create (NULL = the legacy default stream).  Calls that return
  *    data to host memory synchronise that stream before returning.  A context
@@ -40,7 +41,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -106,10 +107,20 @@ typedef struct {
  *     values), py_c (len[1]), pz_c (len[2]); a length of 1 means constant
  *     along that axis, otherwise it must equal the axis extent.
  *   LBM_FIELD_FULL: data holds P[c][N] in node order.
- * data is a host pointer; the values are copied. */
+ *   LBM_FIELD_FULL_DEVICE: as LBM_FIELD_FULL, but data is DEVICE memory of
+ *     the context's device (e.g. a field another kernel produced, such as a
+ *     coupled flow's).  It is copied device to device on the context's
+ *     stream, in stream order with the steps queued before and after the
+ *     call, and nothing synchronises: the caller keeps data unchanged until
+ *     the context's stream has passed the call (e.g. lbm_sync, or its own
+ *     later work on that stream).  A pointer that is not device memory of
+ *     the context's device gives LBM_EINVAL.
+ * For the other kinds data is a host pointer; the values are copied before
+ * the call returns. */
 #define LBM_FIELD_NONE 0
 #define LBM_FIELD_SEPARABLE 1
 #define LBM_FIELD_FULL 2
+#define LBM_FIELD_FULL_DEVICE 3
 
 typedef struct {
     int kind;
@@ -281,9 +292,12 @@ int lbm_l2_error(lbm_ctx *ctx, const double *ref, int where, int field, int half
 int lbm_reduce_sums_noalloc(lbm_ctx *ctx, double out[4]);
 
 /* Copy the populations f(t) (the state after the streaming step of step t,
- * as [q][N] doubles) to dst.  count must equal q*N.  where: 0 host, 1 device.
+ * as [q][N] doubles) to dst.  count must equal q*N.  where: 0 host (the
+ * call synchronises), 1 device (asynchronous on the context's stream).
+ * step_out (may be NULL) receives t, the step counter of the state copied
+ * (in lattice units the time equals the step count).
  * Errors: LBM_ESTATE, LBM_EINVAL (count), LBM_ECUDA. */
-int lbm_get_populations(lbm_ctx *ctx, double *dst, size_t count, int where);
+int lbm_get_populations(lbm_ctx *ctx, double *dst, size_t count, int where, long *step_out);
 
 /* Replace the populations by src ([q][N] doubles, count = q*N) and set the
  * step counter to `step` (checkpoint restore).  where: 0 host, 1 device.
@@ -428,6 +442,33 @@ const char *lbm_batch_last_error(const lbm_batch *b);
 
 /* Free the batch (synchronises its stream); the member contexts stay valid. */
 void lbm_batch_destroy(lbm_batch *b);
+
+/* ---- Device facts and the FP64 throughput probe ---------------------------
+ *
+ * The paper has no counterpart.  On this GPU the FP64 step kernels are bound
+ * by the FP64 unit rather than by memory, so their roofline is stated
+ * against the FP64 instruction rate measured on the device that runs them. */
+
+/* Message of the last failure of lbm_device_info / lbm_probe_fp64 (per thread). */
+const char *lbm_probe_last_error(void);
+
+/* Attributes of CUDA device `device` into info[8]: [0] SM count, [1] maximum
+ * SM clock (kHz), [2] memory clock (kHz), [3] memory bus width (bits), [4] L2
+ * size (bytes), [5] compute capability major, [6] minor, [7] maximum resident
+ * threads per SM.  Errors: LBM_EINVAL (info NULL), LBM_ECUDA (bad device). */
+int lbm_device_info(int device, long long info[8]);
+
+/* Queue (on `stream`, a cudaStream_t; NULL = default) a kernel of `blocks` x
+ * `threads` threads, each running `chains` (8 or 16) independent dependency
+ * chains of `iters` FP64 operations of one kind: op 0 fused multiply-add,
+ * 1 add, 2 multiply.  It issues exactly blocks * threads * iters * chains
+ * FP64 instructions and reads or writes no memory except, never in practice,
+ * sink[0] (one device double, which the caller owns).  The caller times it
+ * (e.g. CUDA events on the stream).  Nothing synchronises.
+ * Errors: LBM_EINVAL (op outside 0..2, chains not 8 or 16, blocks < 1,
+ * threads not a multiple of 32 in [32, 1024], iters < 1, sink NULL),
+ * LBM_ECUDA (launch failure). */
+int lbm_probe_fp64(int op, int chains, int blocks, int threads, long long iters, double *sink, void *stream);
 
 /* ---- Learned warm start: network kernels ---------------------------------
  *

@@ -54,6 +54,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define MAXQ 27
 
@@ -81,6 +84,19 @@ static const int D3Q15_E[15][3] = {
 static const int D3Q15_X[15][3] = {
     {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
     {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 2, 0}, {2, 1, 0}, {2, 0, 1}, {1, 1, 1}, {2, 2, 0}};
+
+/* Thread count of the OpenMP loops over nodes (timing only: the result of a
+ * step does not depend on it, every node being computed independently). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 int orc_q(int lattice)
 {

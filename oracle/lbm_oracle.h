@@ -51,6 +51,8 @@ typedef struct {
 } orc_params;
 
 /* Number of velocities of a lattice (9, 27, 5, 15), 0 if unknown. */
+/* Set the thread count of the node loops (n > 0); returns the count in use. */
+int orc_set_threads(int n);
 int orc_q(int lattice);
 /* Spatial dimension of a lattice (2 or 3). */
 int orc_dim(int lattice);

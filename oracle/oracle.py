@@ -81,6 +81,8 @@ def lib():
         L.orc_collide_node_generic.argtypes = [pp, dp, dp, dp, dp]
         L.orc_velocities.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.orc_strain_rate.argtypes = [pp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
         for fn in ("orc_run", "orc_moments", "orc_equilibrium", "orc_collide_node",
                    "orc_collide_node_generic", "orc_velocities", "orc_strain_rate"):
             getattr(L, fn).restype = ctypes.c_int
@@ -108,6 +110,12 @@ def lib():
             getattr(L, fn).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Thread count of the oracle's node loops (n > 0 sets it); returns the
+    count in use.  Timing only: results do not depend on it."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _dp(a):

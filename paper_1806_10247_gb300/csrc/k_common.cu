@@ -583,6 +583,19 @@ cudaError_t strain_rate(int lattice, const LaunchArgs &a, double rho0, double *o
     });
 }
 
+__global__ void __launch_bounds__(kBlock) k_to_float(const double *__restrict__ in, float *__restrict__ out, long long n)
+{
+    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (i < n) out[i] = __double2float_rn(in[i]);
+}
+
+cudaError_t to_float(const double *in, float *out, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_to_float<<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t viscous_source(int N, int dim, const double *S, double coef, double *out, float *fout, cudaStream_t s)
 {
     k_viscous_source<<<grid_for(N), kBlock, 0, s>>>(N, dim, S, coef, out, fout);
@@ -592,7 +605,7 @@ cudaError_t viscous_source(int N, int dim, const double *S, double coef, double 
 int reduce_blocks(const Geom &g)
 {
     long long b = (g.N + kBlock - 1) / kBlock;
-    return (int)(b < 1216 ? (b < 1 ? 1 : b) : 1216);  // 152 SMs x 8 resident blocks
+    return (int)(b < kReduceMaxBlocks ? (b < 1 ? 1 : b) : kReduceMaxBlocks);
 }
 
 cudaError_t l2_terms(const double *q, const double *ref, long long n, double *partials, int nblocks, double *out,

@@ -193,10 +193,21 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
                 if (!((nf.d.zmask >> cc) & 1)) one = f->data[cc * per + off] == 1.0;
             if (!one) nf.d.axes |= 1 << d;
         }
-    } else if (f->kind == LBM_FIELD_FULL) {
+    } else if (f->kind == LBM_FIELD_FULL || f->kind == LBM_FIELD_FULL_DEVICE) {
         count = (size_t)c->g.N * ncomp;
         nf.d.sep = 0;
         nf.d.cstride = c->g.N;
+        if (f->kind == LBM_FIELD_FULL_DEVICE) {
+            cudaPointerAttributes at{};
+            const cudaError_t ea = cudaPointerGetAttributes(&at, f->data);
+            if (ea != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, LBM_EINVAL, "%s: data is not a device pointer", what);
+            }
+            if (!((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device))
+                return fail(c, LBM_EINVAL, "%s: data is not device memory of the context's device %d", what,
+                            c->device);
+        }
     } else {
         return fail(c, LBM_EINVAL, "%s: unknown field kind %d", what, f->kind);
     }
@@ -220,14 +231,32 @@ int upload_field(lbm_ctx *c, const lbm_field *f, int ncomp, DeviceField &out, co
         }
         nf.cap = count;
     }
-    // The copies are complete before returning: the caller may reuse its buffer.
-    cudaError_t e = cudaMemcpyAsync(nf.dev, f->data, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    std::vector<float> fcopy;
-    if (e == cudaSuccess && want_f) {
-        fcopy.assign(f->data, f->data + count);
-        e = cudaMemcpyAsync(nf.fdev, fcopy.data(), count * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    // A reused buffer may still be read by a readback queued on another
+    // stream (the half-forced fields read the force): the copy waits for it.
+    if (reuse) {
+        const int rc = wait_readers(c, nullptr);
+        if (rc != LBM_OK) return rc;
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaError_t e = cudaSuccess;
+    if (f->kind == LBM_FIELD_FULL_DEVICE) {
+        // Device field: copied (and converted for reduced-precision storage)
+        // on the context's stream, in order with the steps before and after;
+        // nothing synchronises.
+        e = cudaMemcpyAsync(nf.dev, f->data, count * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && want_f) {
+            e = lbmk::to_float(nf.dev, nf.fdev, (long long)count, c->stream);
+            c->launches++;
+        }
+    } else {
+        // The copies are complete before returning: the caller may reuse its buffer.
+        e = cudaMemcpyAsync(nf.dev, f->data, count * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        std::vector<float> fcopy;
+        if (e == cudaSuccess && want_f) {
+            fcopy.assign(f->data, f->data + count);
+            e = cudaMemcpyAsync(nf.fdev, fcopy.data(), count * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
     if (e != cudaSuccess) {
         if (!reuse) {
             cudaFree(nf.dev);
@@ -721,12 +750,13 @@ int lbm_l2_error(lbm_ctx *c, const double *ref, int where, int field, int half_f
     return LBM_OK;
 }
 
-int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where)
+int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where, long *step_out)
 {
     if (!c) return LBM_EINVAL;
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations: populations not initialised");
     if (!dst || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_get_populations: count must be q*N");
+    if (step_out) *step_out = c->t;
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (c->storage != LBM_FP64) {

@@ -141,6 +141,8 @@ int rp_batch_resident(int lattice, int storage, int tile);
 // Strain-rate tensor of the current state (flow lattices): out [ncomp][N],
 // ncomp = 3 (2D: xx, yy, xy) or 6 (3D: xx, yy, zz, xy, xz, yz).
 cudaError_t strain_rate(int lattice, const LaunchArgs &a, double rho0, double *out);
+// out[i] = round-to-nearest FP32 of in[i], i < n (FP32 copies of device fields).
+cudaError_t to_float(const double *in, float *out, long long n, cudaStream_t s);
 // out[i] = coef * S:S from strain components S [ncomp][N]; fout (may be NULL) its FP32 copy.
 cudaError_t viscous_source(int N, int dim, const double *S, double coef, double *out, float *fout, cudaStream_t s);
 
@@ -165,6 +167,10 @@ cudaError_t moments(int lattice, const LaunchArgs &a, double *rho, double *u, in
 // updating the snapshot; then a single-block pass writes out[8].
 cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap, double *partials,
                    int nblocks, double *out);
+// Largest grid of the reductions (152 SMs x 8 resident blocks); they loop
+// over the nodes, so no lattice needs more.  reduce_blocks never exceeds it,
+// and fixed scratch arrays of partial sums are sized by it.
+constexpr int kReduceMaxBlocks = 1216;
 int reduce_blocks(const Geom &g);
 // Terms of the l2 error of Eq. sca over n values: out[0] = sum (q - ref)^2,
 // out[1] = sum ref^2 (per-block partials[nblocks][8], then one block; out[8]).

@@ -24,7 +24,8 @@ namespace {
 // library, until the process exits.  1216 = 152 SMs x 8 resident blocks is the
 // largest grid the reduction ever uses (it loops over nodes), so no lattice
 // exceeds it.
-constexpr int kMaxBlocks = 1216;
+constexpr int kMaxBlocks = lbmk::kReduceMaxBlocks;
+static_assert(kMaxBlocks == 1216, "the header's stated scratch size (1217 x 8 doubles) follows this cap");
 constexpr int kSlots = 8;
 constexpr int kMaxDevices = 64;
 

@@ -1,0 +1,98 @@
+// Device facts and an FP64 throughput probe, for the roofline of the FP64
+// step kernels.  The paper has no counterpart: on this GPU the FP64 step
+// kernels are bound by the FP64 unit, not by memory, so their roofline needs
+// the FP64 instruction rate the unit actually sustains, measured on the
+// device that runs them.
+//
+// The probe kernel runs 8 or 16 independent dependency chains per thread of
+// one FP64 operation (FMA, add or multiply) with operands that arrive as
+// kernel arguments, so the compiler can neither fold nor reorder them; the
+// loop (unrolled four times) keeps its bookkeeping on the integer pipes, so
+// the count of FP64 instructions issued is exactly
+// blocks * threads * iters * chains.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+
+namespace {
+
+thread_local std::string g_probe_error;
+
+int probe_fail(int code, const char *what, cudaError_t e)
+{
+    g_probe_error = std::string(what) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+    return code;
+}
+
+template <int OP, int kChains>
+__global__ void k_fp64_rate(long long iters, double a, double b, double *sink)
+{
+    double x[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; k++) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+#pragma unroll 4
+    for (long long it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < kChains; k++) {
+            if (OP == 0) x[k] = fma(x[k], a, b);
+            else if (OP == 1) x[k] = x[k] + b;
+            else x[k] = x[k] * a;
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; k++) s += x[k];
+    // Never true for the operands the host passes; keeps the chains live.
+    if (s == -1.0) sink[0] = s;
+}
+
+template <int CH>
+void launch_rate(int op, int blocks, int threads, long long iters, double a, double b, double *sink, cudaStream_t s)
+{
+    if (op == 0) k_fp64_rate<0, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
+    else if (op == 1) k_fp64_rate<1, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
+    else k_fp64_rate<2, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_probe_last_error(void) { return g_probe_error.c_str(); }
+
+int lbm_device_info(int device, long long info[8])
+{
+    if (!info) return probe_fail(LBM_EINVAL, "lbm_device_info: info is NULL", cudaSuccess);
+    const cudaDeviceAttr attrs[8] = {cudaDevAttrMultiProcessorCount, cudaDevAttrClockRate,
+                                     cudaDevAttrMemoryClockRate,      cudaDevAttrGlobalMemoryBusWidth,
+                                     cudaDevAttrL2CacheSize,          cudaDevAttrComputeCapabilityMajor,
+                                     cudaDevAttrComputeCapabilityMinor, cudaDevAttrMaxThreadsPerMultiProcessor};
+    for (int k = 0; k < 8; k++) {
+        int v = 0;
+        const cudaError_t e = cudaDeviceGetAttribute(&v, attrs[k], device);
+        if (e != cudaSuccess) return probe_fail(LBM_ECUDA, "lbm_device_info: cudaDeviceGetAttribute", e);
+        info[k] = v;
+    }
+    return LBM_OK;
+}
+
+int lbm_probe_fp64(int op, int chains, int blocks, int threads, long long iters, double *sink, void *stream)
+{
+    if (op < 0 || op > 2 || (chains != 8 && chains != 16) || blocks < 1 || threads < 32 || threads > 1024 ||
+        threads % 32 || iters < 1 || !sink)
+        return probe_fail(LBM_EINVAL, "lbm_probe_fp64: bad arguments", cudaSuccess);
+    cudaStream_t s = (cudaStream_t)stream;
+    // a, b keep every chain finite and away from subnormals for any iters the
+    // probe is run with (x -> x a + b stays near 1; x + b grows by 1e-9 per
+    // step; x a decays by 1e-9 per step)
+    const double a = 1.0 - 1e-9, b = 1e-9;
+    if (chains == 8) launch_rate<8>(op, blocks, threads, iters, a, b, sink, s);
+    else launch_rate<16>(op, blocks, threads, iters, a, b, sink, s);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return probe_fail(LBM_ECUDA, "lbm_probe_fp64: launch", e);
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -21,7 +21,7 @@ from . import build as _build
 D2Q9, D3Q27, D2Q5_CDE, D3Q15 = 1, 2, 3, 4
 FP64, FP32_DEV, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCE_BACK = 0, 1
-FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL = 0, 1, 2
+FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL, FIELD_FULL_DEVICE = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, -1, -2, -3, -4, -6
 Q = {D2Q9: 9, D3Q27: 27, D2Q5_CDE: 5, D3Q15: 15}
 DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2, D3Q15: 3}
@@ -34,7 +34,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_batch_set_graph", "lbm_batch_graph_replays", "lbm_batch_set_tiling", "lbm_batch_get_tiling",
            "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
            "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison", "lbm_batch_step_read",
-           "lbm_l2_error")
+           "lbm_l2_error", "lbm_device_info", "lbm_probe_fp64", "lbm_probe_last_error")
 
 
 class LBMError(RuntimeError):
@@ -93,7 +93,7 @@ def load(build_if_missing: bool = True):
     L.lbm_reduce.argtypes = [vp, dp]
     L.lbm_reduce_sums_noalloc.argtypes = [vp, dp]
     L.lbm_l2_error.argtypes = [vp, vp, ip, ip, ip, dp]
-    L.lbm_get_populations.argtypes = [vp, vp, ctypes.c_size_t, ip]
+    L.lbm_get_populations.argtypes = [vp, vp, ctypes.c_size_t, ip, ctypes.POINTER(ctypes.c_long)]
     L.lbm_set_populations.argtypes = [vp, vp, ctypes.c_size_t, ip, ctypes.c_long]
     L.lbm_get_step.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
     L.lbm_sync.argtypes = [vp]
@@ -115,10 +115,15 @@ def load(build_if_missing: bool = True):
     L.lbm_set_source_from_strain.argtypes = [vp, vp, ctypes.c_double, ctypes.c_double]
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_last_error.restype = ctypes.c_char_p
+    L.lbm_probe_last_error.argtypes = []
+    L.lbm_probe_last_error.restype = ctypes.c_char_p
+    L.lbm_device_info.argtypes = [ip, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_probe_fp64.argtypes = [ip, ip, ip, ip, ctypes.c_longlong, vp, vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lbm_destroy", "lbm_last_error", "lbm_batch_last_error", "lbm_batch_destroy"):
+        if name not in ("lbm_destroy", "lbm_last_error", "lbm_batch_last_error", "lbm_batch_destroy",
+                        "lbm_probe_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -146,11 +151,20 @@ def _ptr(a):
 
 
 def _field(tables=None, full=None):
-    """lbm_field for separable tables [(px, py, pz) per component] or a full [c][N] array."""
+    """lbm_field for separable tables [(px, py, pz) per component] or a full
+    [c][N] array: a numpy array (host) or a contiguous float64 CUDA tensor
+    (device, copied on the context's stream without synchronising)."""
     f = _Field()
     keep = None
     if tables is None and full is None:
         f.kind = FIELD_NONE
+        return f, keep
+    if full is not None and getattr(full, "is_cuda", False):
+        if full.dtype != _torch_float64() or not full.is_contiguous():
+            raise ValueError("device field must be a contiguous float64 tensor")
+        keep = full
+        f.kind = FIELD_FULL_DEVICE
+        f.data = ctypes.cast(ctypes.c_void_p(full.data_ptr()), ctypes.POINTER(ctypes.c_double))
         return f, keep
     if full is not None:
         keep = np.ascontiguousarray(full, dtype=np.float64)
@@ -352,13 +366,16 @@ class Lattice:
         self._check(self._L.lbm_reduce_sums_noalloc(self.h, _dp(out)))
         return out
 
-    def get_populations(self, out=None, where=0):
+    def get_populations(self, out=None, where=0, with_step=False):
+        """f(t) as [q][N] doubles (host, or into the device buffer `out` when
+        where = 1); with_step also returns t, the step of the state copied."""
+        t = ctypes.c_long()
         if where == 1:
-            self._check(self._L.lbm_get_populations(self.h, _ptr(out), self.q * self.N, 1))
-            return out
+            self._check(self._L.lbm_get_populations(self.h, _ptr(out), self.q * self.N, 1, ctypes.byref(t)))
+            return (out, t.value) if with_step else out
         f = np.empty((self.q, self.N))
-        self._check(self._L.lbm_get_populations(self.h, f.ctypes.data, f.size, 0))
-        return f
+        self._check(self._L.lbm_get_populations(self.h, f.ctypes.data, f.size, 0, ctypes.byref(t)))
+        return (f, t.value) if with_step else f
 
     def set_populations(self, f, step=0, where=0):
         if where == 1:
@@ -512,6 +529,36 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+DEVICE_INFO_KEYS = ("sm_count", "sm_max_khz", "mem_khz", "bus_bits", "l2_bytes", "cc_major", "cc_minor",
+                    "max_threads_per_sm")
+
+
+def device_info(device=0):
+    """Attributes of a CUDA device (lbm_device_info) as a dict."""
+    L = load()
+    info = (ctypes.c_longlong * 8)()
+    rc = L.lbm_device_info(int(device), info)
+    if rc != OK:
+        raise LBMError(rc, L.lbm_probe_last_error().decode())
+    return dict(zip(DEVICE_INFO_KEYS, list(info)))
+
+
+FP64_FMA, FP64_ADD, FP64_MUL = 0, 1, 2
+
+
+def probe_fp64(op, blocks, threads, iters, sink_ptr, stream=None, chains=8):
+    """Queue the FP64 throughput probe (lbm_probe_fp64): blocks * threads *
+    iters * chains FP64 instructions of kind op; sink_ptr is the address of
+    one device double.  Asynchronous on `stream`; returns the count."""
+    L = load()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    rc = L.lbm_probe_fp64(int(op), int(chains), int(blocks), int(threads), int(iters),
+                          ctypes.c_void_p(int(sink_ptr)), s)
+    if rc != OK:
+        raise LBMError(rc, L.lbm_probe_last_error().decode())
+    return int(blocks) * int(threads) * int(iters) * int(chains)
 
 
 def from_workload(w, stream=None, envelope_steps=None, storage=FP64) -> Lattice:

@@ -4,17 +4,25 @@ CUDA library and through the oracle, and the FP64 parity metric.
 Parity metric (FP64), after the same number of steps from the same inputs:
   f   : max |f_gpu - f_ref|     <= 1e-12 * max |f_ref|
   rho : max |rho_gpu - rho_ref| <= 1e-12 * max |rho_ref|   (phi likewise)
-  u   : max |u_gpu - u_ref|     <= 1e-12 * U_ref,  U_ref = max(max |u_ref|, 0.01)
+  u   : max |u_gpu - u_ref|     <= 1e-12 * max(max |u_ref|, U_floor)
+        U_floor = 1e-3 for the 2D lattices, 5e-3 for the 3D ones
   phi - mean(phi): max |phi_gpu - phi_ref| <= 1e-12 * max(max |phi_ref - mean|, 0.01 |mean|)
 Populations are O(0.1) and every FP64 evaluation of the step rounds them; two
 correct evaluations in different operation orders (the oracle's dense moment
-matrices and the kernels' factorised transforms) differ by ~1e-16 (D2Q9, D2Q5)
-to ~1e-15 (D3Q27, 27-term sums) in f, and so by as much in u = sum f e / rho.
-A relative 1e-12 on u is resolvable only for |u| >~ 1e-3; the velocity is
-therefore measured against U_ref, which is never below 0.01 = the smallest
-velocity scale of the paper's benchmarks (four-rolls mill u0, Sec. 6.5).  The
-plain relative errors are returned as "u_rel" / "phi_var_rel".
+matrices and the kernels' factorised transforms) differ in u = sum f e / rho
+by a few units of eps * sum |f e| / rho (eps = 2^-53): one rounding of a
+velocity sum is ~1e-16 absolute, whatever |u| is.  So the plain relative
+1e-12 holds wherever |u| is large enough for 1e-12 |u| to exceed the
+accumulated rounding, and below that the velocity is measured against a
+floor set at that rounding: 1e-15 absolute (about 9 eps) for the 9-term sums
+of the 2D lattices, 5e-15 (about 45 eps) for the 15- and 27-term sums of the
+3D lattices over runs of up to 1000 steps.  Measured on the GB300 over every
+parity case: at most 3.7e-13 (2D, the Poiseuille channel after 10^4 steps)
+and 6.1e-13 (3D, Kolmogorov 64^3 after 1000 steps) of the bar.  The plain
+relative errors are returned as "u_rel" / "phi_var_rel".
 """
+import os
+
 import numpy as np
 
 from oracle import oracle as O
@@ -39,7 +47,8 @@ def oracle_from_workload(w, f0=None):
     return L
 
 
-U_FLOOR = 0.01
+U_FLOOR_2D, U_FLOOR_3D = 1e-3, 5e-3
+PHI_VAR_FLOOR = 0.01
 
 
 def compare_state(G, R, rho0=1.0, tol=TOL):
@@ -55,19 +64,40 @@ def compare_state(G, R, rho0=1.0, tol=TOL):
         pr = R.moments()
         err["phi"] = np.abs(pg - pr).max() / np.abs(pr).max()
         m = abs(pr.mean())
-        scale = max(np.abs(pr - pr.mean()).max(), U_FLOOR * m, 1e-300)
+        scale = max(np.abs(pr - pr.mean()).max(), PHI_VAR_FLOOR * m, 1e-300)
         err["phi_var"] = np.abs(pg - pr).max() / scale
         info["phi_var_rel"] = np.abs(pg - pr).max() / max(np.abs(pr - pr.mean()).max(), 1e-300)
+        info["phi_abs"] = np.abs(pg - pr).max()
+        info["phi_var_max"] = np.abs(pr - pr.mean()).max()
     else:
+        floor = U_FLOOR_3D if G.dim == 3 else U_FLOOR_2D
         rg, ug = G.moments()
         rr, ur = R.moments()
         err["rho"] = np.abs(rg - rr).max() / np.abs(rr).max()
-        err["u"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), U_FLOOR)
+        err["u"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), floor)
         info["u_rel"] = np.abs(ug - ur).max() / max(np.abs(ur).max(), 1e-300)
+        info["u_abs"] = np.abs(ug - ur).max()
+        info["u_max"] = np.abs(ur).max()
         rg0, ug0 = G.moments(half_forced=False)
         rr0, ur0 = R.moments(half_forced=False)
-        err["u_out"] = np.abs(ug0 - ur0).max() / max(np.abs(ur0).max(), U_FLOOR)
-    for k, v in err.items():
-        assert v <= tol, (k, v, err, info)
+        err["u_out"] = np.abs(ug0 - ur0).max() / max(np.abs(ur0).max(), floor)
+        info["u_out_abs"] = np.abs(ug0 - ur0).max()
     err.update(info)
+    record(err, tol)
+    for k, v in err.items():
+        if k in info:
+            continue
+        assert v <= tol, (k, v, err, info)
     return err
+
+
+# Every comparison's errors, in call order (written to a JSON file at the end
+# of the session when LBM_RESULTS_DIR is set; see conftest.py).
+RECORDS = []
+
+
+def record(err, tol, **extra):
+    r = {"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "tol": tol}
+    r.update({k: float(v) for k, v in err.items()})
+    r.update(extra)
+    RECORDS.append(r)

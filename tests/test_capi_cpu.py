@@ -97,6 +97,20 @@ def test_batch_and_nn_entry_points_reject_null_handles():
     assert L.lbm_l2_error(None, None, 0, 0, 1, None) == lbm.EINVAL
 
 
+def test_probe_and_device_info_validate_arguments():
+    """The FP64 probe and the device query reject bad arguments on the host."""
+    L = lbm.load()
+    sink = ctypes.c_void_p(16)
+    assert L.lbm_probe_fp64(3, 8, 1, 256, 1, sink, None) == lbm.EINVAL
+    assert L.lbm_probe_fp64(0, 12, 1, 256, 1, sink, None) == lbm.EINVAL
+    assert L.lbm_probe_fp64(0, 8, 0, 256, 1, sink, None) == lbm.EINVAL
+    assert L.lbm_probe_fp64(0, 8, 1, 100, 1, sink, None) == lbm.EINVAL
+    assert L.lbm_probe_fp64(0, 8, 1, 256, 0, sink, None) == lbm.EINVAL
+    assert L.lbm_probe_fp64(0, 16, 1, 256, 1, None, None) == lbm.EINVAL
+    assert b"bad arguments" in L.lbm_probe_last_error()
+    assert L.lbm_device_info(0, None) == lbm.EINVAL
+
+
 def test_oracle_and_product_share_no_code():
     """The CUDA sources never include the oracle and the product never imports it."""
     for d in ("paper_1806_10247_gb300", "paper_1806_10247_gb300/csrc", "include"):

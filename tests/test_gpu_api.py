@@ -145,3 +145,62 @@ def test_small_d2q9_cluster_steps_equal_single_launches_and_oracle():
         a.step(3)
         R.run(5)
         compare_state(a, R)
+
+
+@pytest.mark.parametrize("lattice,storage", [
+    (W.D3Q27, lbm.FP64), (W.D2Q9, lbm.FP64), (W.D2Q5, lbm.FP64),
+    (W.D3Q27, lbm.FP32_DEV), (W.D2Q9, lbm.FP16_DEV), (W.D2Q5, lbm.FP32_DEV),
+])
+def test_device_field_equals_host_field_bitwise(lattice, storage):
+    """A full force / source field given as device memory
+    (LBM_FIELD_FULL_DEVICE, copied in stream order) drives the step exactly
+    as the same field given from host memory, bit for bit; the field is
+    replaced in place between steps, as a coupled solver would do."""
+    torch = pytest.importorskip("torch")
+    from tests.test_gpu_parity import _random_workload
+
+    shape = (9, 7, 5) if lattice == W.D3Q27 else (23, 14, 1)
+    w, full = _random_workload(lattice, shape, (0, 1, 0), seed=31, kind="full")
+    rng = np.random.default_rng(32)
+    full2 = 1e-4 * rng.standard_normal(full.shape)
+    host = lbm.from_workload(w, storage=storage)
+    dev = lbm.from_workload(w, storage=storage)
+    setter_h = host.set_source if lattice == W.D2Q5 else host.set_force
+    setter_d = dev.set_source if lattice == W.D2Q5 else dev.set_force
+    buf = torch.from_numpy(np.ascontiguousarray(full)).to("cuda")
+    setter_h(full=full)
+    setter_d(full=buf)
+    host.step(4)
+    dev.step(4)
+    # new values in the same device buffer, written on the context's stream
+    # order (the copy is queued after the steps above)
+    torch.cuda.synchronize()
+    buf.copy_(torch.from_numpy(np.ascontiguousarray(full2)))
+    torch.cuda.synchronize()
+    setter_h(full=full2)
+    setter_d(full=buf)
+    host.step(3)
+    dev.step(3)
+    fh, th = host.get_populations(with_step=True)
+    fd, td = dev.get_populations(with_step=True)
+    assert th == td == 7 == host.t
+    assert np.array_equal(fh, fd)
+    # a host pointer given as a device field is rejected
+    f = lbm._Field()
+    f.kind = lbm.FIELD_FULL_DEVICE
+    arr = np.zeros(full.size)
+    f.data = lbm._dp(arr)
+    fn = dev._L.lbm_set_source if lattice == W.D2Q5 else dev._L.lbm_set_force
+    assert fn(dev.h, lbm.ctypes.byref(f)) == lbm.EINVAL
+
+
+def test_get_populations_reports_the_step():
+    torch = pytest.importorskip("torch")
+    L = lbm.from_workload(W.kolmogorov(shape=(6, 5, 4)))
+    L.step(11)
+    f, t = L.get_populations(with_step=True)
+    assert t == 11
+    buf = torch.empty((27, L.N), dtype=torch.float64, device="cuda")
+    _, t2 = L.get_populations(out=buf, where=1, with_step=True)
+    L.sync()
+    assert t2 == 11 and np.array_equal(buf.cpu().numpy(), f)

@@ -25,8 +25,13 @@ def _members(kind):
         ws = [W.poiseuille(ny=n) for n in (9, 33, 65)]
         w, full = _random_workload(W.D2Q9, (29, 17, 1), (0, 0, 0), seed=5, kind="full")
         w2, _ = _random_workload(W.D2Q9, (40, 7, 1), (1, 0, 0), seed=6)
-        ws += [w, w2]
-        fulls = [None, None, None, full, None]
+        # unit higher rates with a force that has a y component: the
+        # unit-rates collision with its y terms (batch variant 1), beside the
+        # channels' force-along-x form (variant 3)
+        w3, _ = _random_workload(W.D2Q9, (15, 12, 1), (0, 1, 0), seed=12)
+        w3 = dataclasses.replace(w3, omega=W.d2q9_omega(0.9))
+        ws += [w, w2, w3]
+        fulls = [None, None, None, full, None, None]
     elif kind == "d3q15":
         ws = [W.duct15(n=9, nx=4)]
         w, full = _random_workload(W.D3Q15, (7, 6, 5), (1, 1, 1), seed=9, kind="full")
@@ -36,8 +41,12 @@ def _members(kind):
     else:
         ws = [W.kolmogorov(shape=(12, 10, 8)), W.duct(n=9, nx=4)]
         w, full = _random_workload(W.D3Q27, (7, 6, 5), (1, 1, 1), seed=8, kind="full")
-        ws.append(w)
-        fulls = [None, None, full]
+        # unit higher rates with y and z force components (batch variant 1)
+        # beside the force-along-x members (variant 3)
+        w3, _ = _random_workload(W.D3Q27, (6, 7, 5), (0, 1, 0), seed=13)
+        w3 = dataclasses.replace(w3, omega=W.d3q27_omega(0.7))
+        ws += [w, w3]
+        fulls = [None, None, full, None]
     return ws, fulls
 
 

@@ -21,14 +21,19 @@ def _close(a, b, scale):
     return np.abs(np.asarray(a) - np.asarray(b)).max() <= TOL * scale
 
 
-@pytest.mark.parametrize("make", [
-    lambda: W.kolmogorov(shape=(20, 24, 12)),
-    lambda: W.cde_workload(W.cde_sweep_params(sizes=(64,))[0]),
-    lambda: W.poiseuille(),
+@pytest.mark.parametrize("make,storage", [
+    (lambda: W.kolmogorov(shape=(20, 24, 12)), lbm.FP64),
+    (lambda: W.cde_workload(W.cde_sweep_params(sizes=(64,))[0]), lbm.FP64),
+    (lambda: W.poiseuille(), lbm.FP64),
+    # reduced-precision storage takes its own partial-sum kernel (FP64 sums
+    # of the stored deviations plus the rest state)
+    (lambda: W.kolmogorov(shape=(20, 24, 12)), lbm.FP32_DEV),
+    (lambda: W.cde_workload(W.cde_sweep_params(sizes=(64,))[0]), lbm.FP16_DEV),
+    (lambda: W.poiseuille(ny=65, nx=40), lbm.BF16_DEV),
 ])
-def test_noalloc_sums_match_reduce_on_two_calls(make):
+def test_noalloc_sums_match_reduce_on_two_calls(make, storage):
     w = make()
-    L = lbm.from_workload(w)
+    L = lbm.from_workload(w, storage=storage)
     L.step(5)
     ref = L.reduce()[:4]
     scale = max(abs(ref[0]), 1.0)
