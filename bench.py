@@ -800,7 +800,7 @@ def storage_study(lbm, stream, hbm, hbm_src, peak, steps, warmup, n=512, run_ste
     return out
 
 
-def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16")):
+def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp16_sr", "bf16_sr")):
     """The metric's second half: wall time to the solution criterion.
     * config 1 (Poiseuille D2Q9 3 x 33), FP64: steps until
       max |u(t) - u(t-100)| < 1e-12 (checked every 100 steps with lbm_reduce);
@@ -813,7 +813,9 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16")):
       device, the checks inside the timed region);
     * config 2 (scalar sweep): every member run to its T_N, l2 error against the
       closed form and the convergence order over the sweep, per storage form
-      (the 16-bit forms show how far their rounding moves the order)."""
+      (the 16-bit forms show how far their rounding moves the order).
+    The *_sr forms are the 16-bit storages with stochastic rounding (seed
+    10247; single-lattice launches, one per step)."""
     import torch
 
     codes = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
@@ -845,7 +847,9 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16")):
                               "launch": how}
     L.close()
     for st in storages:
-        L = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[st])
+        L = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[st.split("_")[0]])
+        if st.endswith("_sr"):
+            L.set_stochastic_rounding(True, 10247)
         L.reduce()
         torch_sync(stream)
         t0 = time.perf_counter()
@@ -861,25 +865,34 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16")):
             "steps": steps, "seconds": sec, "l2_vs_fp64_steady": err, "reached": err <= 1e-4,
             "criterion": "relative l2 (Eq. sca) of u against the FP64 steady field <= 1e-4 (lbm_l2_error every "
                          "100 steps, reference on the device)",
-            "launch": how}
+            "launch": how if not st.endswith("_sr") else "lbm_step(100) between checks (one launch per step)"}
         L.close()
     for st in storages:
         cases = W.cde_sweep_params()
         errs, total = [], 0.0
         for c in cases:
             wc = W.cde_workload(c)
-            G = lbm.from_workload(wc, stream=stream.cuda_stream, envelope_steps=c.T + 2, storage=codes[st])
-            Bt = lbm.Batch([G])
-            Bt.set_graph(200)
+            G = lbm.from_workload(wc, stream=stream.cuda_stream, envelope_steps=c.T + 2,
+                                  storage=codes[st.split("_")[0]])
+            Bt = None
+            if st.endswith("_sr"):
+                G.set_stochastic_rounding(True, 10247)
+            else:
+                Bt = lbm.Batch([G])
+                Bt.set_graph(200)
             torch_sync(stream)
             t0 = time.perf_counter()
-            Bt.step(c.T)
+            if Bt is not None:
+                Bt.step(c.T)
+            else:
+                G.step(c.T)
             G.sync()
             total += time.perf_counter() - t0
             phi = G.moments().reshape(c.N, c.N) - 1.0
             ref = W.cde_closed_form(c, c.T)
             errs.append(float(np.sqrt(np.sum((phi - ref) ** 2) / np.sum(ref ** 2))))
-            Bt.close()
+            if Bt is not None:
+                Bt.close()
             G.close()
         orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
         out[f"cde_sweep_{st}"] = {"seconds": total, "steps": [c.T for c in cases],
@@ -955,7 +968,7 @@ def batched_time_to_solution(lbm, stream, count=32, tmax=700.0, check=100):
         torch_sync(stream)
         t1 = time.perf_counter()
         steps = 0
-        while steps < 20 * ref_steps:
+        while steps < 4 * ref_steps:
             if batched:
                 for b in batches:
                     b.step(check)
@@ -983,6 +996,13 @@ def batched_time_to_solution(lbm, stream, count=32, tmax=700.0, check=100):
              "seconds": sec, "steps_median": float(np.median([d for d in flat if d is not None])),
              "l2_at_end_max": max(max(g) for g in worst),
              "launch": form}
+        missed = [(gi, mi) for gi in range(len(groups)) for mi in range(len(groups[gi])) if done[gi][mi] is None]
+        if missed:
+            r["not_reached"] = [{"member": groups[gi][mi].name, "l2_at_end": worst[gi][mi],
+                                 "tau": groups[gi][mi].meta.get("tau", groups[gi][mi].meta.get("tau_phi")),
+                                 "amplitude": groups[gi][mi].meta.get("Fx", groups[gi][mi].meta.get("A"))}
+                                for gi, mi in missed[:8]]
+            r["not_reached_count"] = len(missed)
         if tuning is not None:
             r["autotuned_us_per_launch"] = tuning
         return r
@@ -1070,6 +1090,9 @@ def main():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-solution runs")
     ap.add_argument("--warmstart", action="store_true",
                     help="run the learned warm-start study (duct sections) instead of the throughput bench")
+    ap.add_argument("--ws-n", type=int, default=128, help="warm-start study: duct section n x n")
+    ap.add_argument("--ws-train", type=int, default=200, help="warm-start study: training fields")
+    ap.add_argument("--ws-test", type=int, default=4, help="warm-start study: held-out cases")
     ap.add_argument("--profile", action="store_true",
                     help="short run for a profiler: no minimum warm-up time, no e2e, no CPU baseline, no extras")
     args = ap.parse_args()
@@ -1103,10 +1126,12 @@ def main():
     if args.warmstart:
         from paper_1806_10247_gb300 import surrogate
 
-        res = surrogate.study()
+        res = surrogate.study(n=args.ws_n, train_count=args.ws_train, test_count=args.ws_test, gen_tol=1e-6,
+                              check_every=500 if args.ws_n >= 96 else 100)
         if rank == 0:
             print(json.dumps({"metric": "steps and wall time to the 1e-10 residual, warm vs zero start",
-                              "config": {"workload": "duct_section_warmstart_d3q27"}, "result": res}), flush=True)
+                              "config": {"workload": f"duct_section_warmstart_d3q27_{args.ws_n}x{args.ws_n}"},
+                              "result": res}), flush=True)
         return
     dist = None
     if world > 1:

@@ -188,6 +188,23 @@ int lbm_set_envelope(lbm_ctx *ctx, lbm_envelope_fn fn, void *user);
  * removes the table.  Same trapezoid averages as lbm_set_envelope. */
 int lbm_set_envelope_table(lbm_ctx *ctx, const double *a, long count, double t0);
 
+/* Rounding of the stored deviations of a 16-bit storage context (LBM_FP16_DEV,
+ * LBM_BF16_DEV): on = 0 rounds to nearest (the default); on = 1 rounds
+ * stochastically: each stored value goes to the representable neighbour
+ * further from zero with probability equal to its distance from the one
+ * nearer to zero, in units of the step between them, so that it equals the
+ * FP32 result on average and increments smaller than the storage step are not
+ * lost on average (the paper has no counterpart: this addresses the force and
+ * source increments of Eqs. 25/31 and 43/47 that 16-bit storage cannot
+ * resolve).  The random bits come from a counter-based generator (the
+ * SplitMix64 output function, Steele, Lea and Flood, OOPSLA 2014) keyed by
+ * `seed`, the step counter, the node and the population, so a run is
+ * reproducible for a given seed.  Applies to lbm_step (one launch per step;
+ * the one-launch cluster form of small D2Q9 lattices is not used while it is
+ * on); a context with it on cannot join a batch.
+ * Errors: LBM_EINVAL (storage not 16-bit). */
+int lbm_set_stochastic_rounding(lbm_ctx *ctx, int on, unsigned long long seed);
+
 /* Advance n >= 0 time steps (n = 0 is a no-op).  Each step is one fused
  * kernel launch: stream (Eq. 22b / 40b, pull form, with periodic wrap or
  * halfway bounce-back), moments (Eq. 24 / 42), pre-collision half force or
@@ -328,7 +345,8 @@ int lbm_launch_count(const lbm_ctx *ctx, long long *count);
 typedef struct lbm_batch lbm_batch;
 
 /* Errors: LBM_EINVAL (count < 1, NULL or repeated context, members differing
- * in lattice, storage, stream or device), LBM_ENOMEM, LBM_ECUDA. */
+ * in lattice, storage, stream or device, a member with stochastic rounding
+ * on), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count);
 
 /* Advance every member by n >= 0 steps (asynchronous on the members' stream).

@@ -285,11 +285,19 @@ k_l2_partial(const double *__restrict__ q, const double *__restrict__ ref, long 
 }
 
 // ---- reduced-precision storage: deviations d = f - w rho_ref in type T ----
+// (D2Q5: d = g - g_ref, the reference populations of the context.)
+
+template <class L>
+__device__ __forceinline__ double ref_pop(int a, double rho_ref, const Ref5 &R)
+{
+    if constexpr (L::Q == 5) return R.v[a];
+    else return L::w(a) * rho_ref;
+}
 
 template <class L, class T>
 __global__ void __launch_bounds__(kBlock)
-k_init_rp(Geom g, double rho_ref, double rho0, double u0x, double u0y, double u0z, const double *__restrict__ rho,
-          const double *__restrict__ u, T *__restrict__ stored)
+k_init_rp(Geom g, double rho_ref, Ref5 R, double rho0, double u0x, double u0y, double u0z,
+          const double *__restrict__ rho, const double *__restrict__ u, T *__restrict__ stored)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -315,13 +323,14 @@ k_init_rp(Geom g, double rho_ref, double rho0, double u0x, double u0y, double u0
         }
         bool opp;
         int off = pull_off(g, x, y, z, L::ex(a), L::ey(a), L::ez(a), opp);
-        stored[(opp ? L::opp(a) : a) * g.Np + off] = Dev<T>::to_store((float)(v - L::w(a) * rho_ref));
+        const int slot = opp ? L::opp(a) : a;
+        stored[slot * g.Np + off] = Dev<T>::to_store((float)(v - ref_pop<L>(slot, rho_ref, R)));
     }
 }
 
 template <class L, class T>
 __global__ void __launch_bounds__(kBlock)
-k_scatter_rp(Geom g, double rho_ref, const double *__restrict__ plain, T *__restrict__ stored)
+k_scatter_rp(Geom g, double rho_ref, Ref5 R, const double *__restrict__ plain, T *__restrict__ stored)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -331,14 +340,15 @@ k_scatter_rp(Geom g, double rho_ref, const double *__restrict__ plain, T *__rest
     for (int a = 0; a < L::Q; a++) {
         bool opp;
         int off = pull_off(g, x, y, z, L::ex(a), L::ey(a), L::ez(a), opp);
-        const double v = plain[(size_t)a * g.N + i] - L::w(a) * rho_ref;
-        stored[(opp ? L::opp(a) : a) * g.Np + off] = Dev<T>::to_store((float)v);
+        const int slot = opp ? L::opp(a) : a;
+        const double v = plain[(size_t)a * g.N + i] - ref_pop<L>(slot, rho_ref, R);
+        stored[slot * g.Np + off] = Dev<T>::to_store((float)v);
     }
 }
 
 template <class L, class T>
 __global__ void __launch_bounds__(kBlock)
-k_gather_rp(Geom g, double rho_ref, const T *__restrict__ stored, double *__restrict__ plain)
+k_gather_rp(Geom g, double rho_ref, Ref5 R, const T *__restrict__ stored, double *__restrict__ plain)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -346,8 +356,11 @@ k_gather_rp(Geom g, double rho_ref, const T *__restrict__ stored, double *__rest
     node_xyz(g, i, x, y, z);
     float d[L::Q];
     load_pulled_dev<L, T>(stored, g, x, y, z, i, d);
+    // a population pulled from beyond a wall comes from the opposite slot,
+    // whose reference it carries (the D2Q5 equilibrium reference is used on
+    // periodic lattices only, and w(opp a) = w(a))
 #pragma unroll
-    for (int a = 0; a < L::Q; a++) plain[(size_t)a * g.N + i] = L::w(a) * rho_ref + (double)d[a];
+    for (int a = 0; a < L::Q; a++) plain[(size_t)a * g.N + i] = ref_pop<L>(a, rho_ref, R) + (double)d[a];
 }
 
 template <class L, class T>
@@ -646,43 +659,44 @@ cudaError_t reduce(int lattice, const LaunchArgs &a, double *snap, int have_snap
     });
 }
 
-cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, double rho0,
-                                const double *u0, const double *rho, const double *u, void *stored,
+cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref,
+                                double rho0, const double *u0, const double *rho, const double *u, void *stored,
                                 cudaStream_t s)
 {
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         return by_storage(storage, [&](auto T) {
             using TT = decltype(T);
-            k_init_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, rho0, u0[0], u0[1], u0[2], rho, u,
+            k_init_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, gref, rho0, u0[0], u0[1], u0[2], rho, u,
                                                               reinterpret_cast<TT *>(stored));
             return cudaGetLastError();
         });
     });
 }
 
-cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const double *plain,
-                       void *stored, cudaStream_t s)
+cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref,
+                       const double *plain, void *stored, cudaStream_t s)
 {
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         return by_storage(storage, [&](auto T) {
             using TT = decltype(T);
-            k_scatter_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, plain, reinterpret_cast<TT *>(stored));
+            k_scatter_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, gref, plain,
+                                                                 reinterpret_cast<TT *>(stored));
             return cudaGetLastError();
         });
     });
 }
 
-cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const void *stored,
+cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref, const void *stored,
                       double *plain, cudaStream_t s)
 {
     return by_lattice(lattice, [&](auto L) {
         using LT = decltype(L);
         return by_storage(storage, [&](auto T) {
             using TT = decltype(T);
-            k_gather_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, reinterpret_cast<const TT *>(stored),
-                                                                plain);
+            k_gather_rp<LT, TT><<<grid_for(g.N), kBlock, 0, s>>>(g, rho_ref, gref,
+                                                                reinterpret_cast<const TT *>(stored), plain);
             return cudaGetLastError();
         });
     });

@@ -17,6 +17,78 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// ------------------------------------------------------ stochastic rounding ---
+// Counter-based random bits: the output function of SplitMix64 (Steele, Lea
+// and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014),
+// a bijective mix of a 64-bit counter.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// 16-bit random numbers for the populations of node i in a step with key
+// `key` (the seed mixed with the step counter on the host): population a
+// takes bits 16 (a % 4) .. of mix64 of a counter distinct for every node
+// i < 2^31 and chunk a / 4 < 8 of the step.
+struct SRBits {
+    unsigned long long key;
+    int i;
+    unsigned long long word;
+    int chunk;
+    __device__ __forceinline__ SRBits(unsigned long long k, int node) : key(k), i(node), word(0), chunk(-1) {}
+    __device__ __forceinline__ unsigned get(int a)
+    {
+        if ((a >> 2) != chunk) {
+            chunk = a >> 2;
+            word = mix64(key ^ (((unsigned long long)(unsigned)i << 3) | (unsigned)chunk));
+        }
+        return (unsigned)(word >> (16 * (a & 3))) & 0xffffu;
+    }
+};
+
+// Rounding of a deviation to the storage type: to nearest, or (SR)
+// stochastically with a 16-bit random r16 -- to the neighbour further from
+// zero with probability equal to the distance from the nearer-to-zero
+// neighbour in units of the step between the two, so that the stored value is
+// the input on average.
+template <class T> struct Round;
+template <> struct Round<float> {
+    __device__ static float sr(float v, unsigned) { return v; }
+};
+template <> struct Round<__half> {
+    __device__ static __half sr(float v, unsigned r16)
+    {
+        const __half lo = __float2half_rz(v);
+        const float flo = __half2float(lo);
+        if (flo == v) return lo;
+        // one step further from zero (the same sign bit, magnitude + 1)
+        const __half hi = __ushort_as_half((unsigned short)(__half_as_ushort(lo) + 1u));
+        const float step = __half2float(hi) - flo;  // a power of two: exact, and so is its reciprocal
+        const float p = (v - flo) * __frcp_rn(step);
+        return (float)r16 * (1.0f / 65536.0f) < p ? hi : lo;
+    }
+};
+template <> struct Round<__nv_bfloat16> {
+    __device__ static __nv_bfloat16 sr(float v, unsigned r16)
+    {
+        // BF16 keeps the upper 16 bits of the FP32 pattern: adding a uniform
+        // 16-bit integer to the dropped bits before truncating rounds up
+        // with probability (dropped bits) / 2^16
+        unsigned b = __float_as_uint(v);
+        if ((b & 0x7f800000u) != 0x7f800000u) b += r16;
+        return __ushort_as_bfloat16((unsigned short)(b >> 16));
+    }
+};
+template <class T, bool SR>
+__device__ __forceinline__ T store_dev(float v, SRBits &rb, int a)
+{
+    if constexpr (SR) return Round<T>::sr(v, rb.get(a));
+    else return Dev<T>::to_store(v);
+}
+
 // ------------------------------------------------------------------ D2Q9 ---
 
 struct Rates9f {
@@ -142,9 +214,10 @@ __device__ __forceinline__ void collide9_w1(float (&d)[9], float rref, float Fx,
     d[7] = P2m - P1m;
 }
 
-template <class T, int FK, bool W1>
+template <class T, int FK, bool W1, bool SR = false>
 __global__ void __launch_bounds__(kBlock)
-k_step9(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref)
+k_step9(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref,
+        unsigned long long srkey)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -162,8 +235,9 @@ k_step9(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, 
     }
     if (W1) collide9_w1(d, rref, Fx, Fy, Gx, Gy, w);
     else collide9(d, rref, Fx, Fy, Gx, Gy, w);
+    SRBits rb(srkey, i);
 #pragma unroll
-    for (int a = 0; a < 9; a++) P.out[a][i] = Dev<T>::to_store(d[a]);
+    for (int a = 0; a < 9; a++) P.out[a][i] = store_dev<T, SR>(d[a], rb, a);
 }
 
 // Many steps per launch for a small D2Q9 lattice (the FP32 / 16-bit form of
@@ -363,10 +437,17 @@ Coef5f make_coef5f(const double omega[9], double ux, double uy)
     return k;
 }
 
-template <class T, int SK, bool UNIFORM>
+// Deviations from the reference; a uniform velocity takes the linear step of
+// the deviations (collide5u with no rest-state terms) plus the constant cref =
+// M g_ref - g_ref (zero for the equilibrium reference of a periodic lattice).
+struct Ref5f {
+    float v[5];
+};
+
+template <class T, int SK, bool UNIFORM, bool SR = false>
 __global__ void __launch_bounds__(kBlock)
 k_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, FieldDev V, float apre, float hsum, Rates5f w,
-        Coef5f k, float rref)
+        Coef5f k, float rref, Ref5f cref, unsigned long long srkey)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -381,14 +462,17 @@ k_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, FieldDev V, 
         H0 = hsum * Ps;
     }
     if (UNIFORM) {
-        collide5u(d, rref, Sp, H0, k);
+        collide5u(d, 0.0f, Sp, H0, k);
+#pragma unroll
+        for (int a = 0; a < 5; a++) d[a] += cref.v[a];
     } else {
         const float ux = field_value_f(V, FK_GENERAL, 0, x, y, 0, i);
         const float uy = field_value_f(V, FK_GENERAL, 1, x, y, 0, i);
         collide5(d, rref, Sp, H0, ux, uy, w);
     }
+    SRBits rb(srkey, i);
 #pragma unroll
-    for (int a = 0; a < 5; a++) P.out[a][i] = Dev<T>::to_store(d[a]);
+    for (int a = 0; a < 5; a++) P.out[a][i] = store_dev<T, SR>(d[a], rb, a);
 }
 
 // ----------------------------------------------------------------- D3Q27 ---
@@ -397,9 +481,32 @@ struct Rates27f {
     float wb, ws, w3, w4, w5, w6;
 };
 
-__device__ __forceinline__ void raw_fwd(float &a, float &b, float &c)
+// Two nodes' values in one register pair: every operation on them is one
+// packed FP32 instruction (add / multiply / fused multiply-add on f32x2, sm_100
+// and later), each half rounded exactly as the scalar operation would be.  The
+// 16-bit D3Q27 step, which is bound by instruction issue rather than by
+// memory, runs two x-neighbouring nodes per thread in this form.
+struct f2 {
+    float2 v;
+    __device__ __forceinline__ f2() {}
+    __device__ __forceinline__ f2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+// a - b as a + b * (-1): exact negation, one rounding, one instruction
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ f2 vrcp(f2 a) { return f2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+
+template <class V>
+__device__ __forceinline__ void raw_fwd(V &a, V &b, V &c)
 {
-    const float s = c + a, dd = c - a;
+    const V s = c + a, dd = c - a;
     a = s + b;
     b = dd;
     c = s;
@@ -408,9 +515,10 @@ __device__ __forceinline__ void raw_fwd(float &a, float &b, float &c)
 // or 2 contributes a factor 1/2), as in the FP64 kernel: the inverse 1D
 // transform of (m0, m1/2, m2/2) is f_-1 = m2/2 - m1/2, f_0 = m0 - m2,
 // f_+1 = m2/2 + m1/2, three operations per line instead of four.
-__device__ __forceinline__ void raw_bwd_h(float &m0, float &m1, float &m2)
+template <class V>
+__device__ __forceinline__ void raw_bwd_h(V &m0, V &m1, V &m2)
 {
-    const float fm = m2 - m1, fp = m2 + m1, f0 = fmaf(-2.0f, m2, m0);
+    const V fm = m2 - m1, fp = m2 + m1, f0 = vfma(V(-2.0f), m2, m0);
     m0 = fm;
     m1 = f0;
     m2 = fp;
@@ -422,14 +530,15 @@ __device__ __forceinline__ void shift_fwd(float m0, float &m1, float &m2, float 
     m1 = k1;
 }
 // Halved central moments about u -> halved raw moments (one axis; uh = u / 2).
-__device__ __forceinline__ void shift_bwd_h(float k0, float &k1, float &k2, float u, float uh)
+template <class V>
+__device__ __forceinline__ void shift_bwd_h(V k0, V &k1, V &k2, V u, V uh)
 {
-    const float m1 = fmaf(uh, k0, k1);
-    k2 = fmaf(u, k1 + m1, k2);
+    const V m1 = vfma(uh, k0, k1);
+    k2 = vfma(u, k1 + m1, k2);
     k1 = m1;
 }
-template <int AX, class Op>
-__device__ __forceinline__ void along(float (&m)[27], Op op)
+template <int AX, class V, class Op>
+__device__ __forceinline__ void along(V (&m)[27], Op op)
 {
     constexpr int st = AX == 0 ? 1 : (AX == 1 ? 3 : 9);
 #pragma unroll
@@ -443,27 +552,28 @@ __device__ __forceinline__ void along(float (&m)[27], Op op)
 // deviations: back-shift, post-collision force in moment space (K_1 g_1 with
 // g = (F_pre + F_post) / 36; m_100 already carries F_pre / 2), inverse raw
 // transform.
-__device__ __forceinline__ void finish27(float (&m)[27], float ux, float uy, float uz, const float (&F)[3],
-                                         const float (&Fq)[3])
+template <class V>
+__device__ __forceinline__ void finish27(V (&m)[27], V ux, V uy, V uz, const V (&F)[3], const V (&Fq)[3])
 {
-    const float hx = 0.5f * ux, hy = 0.5f * uy, hz = 0.5f * uz;
-    along<0>(m, [ux, hx](float &a, float &b, float &c) { shift_bwd_h(a, b, c, ux, hx); });
-    along<1>(m, [uy, hy](float &a, float &b, float &c) { shift_bwd_h(a, b, c, uy, hy); });
-    along<2>(m, [uz, hz](float &a, float &b, float &c) { shift_bwd_h(a, b, c, uz, hz); });
+    const V hx = V(0.5f) * ux, hy = V(0.5f) * uy, hz = V(0.5f) * uz;
+    along<0>(m, [ux, hx](V &a, V &b, V &c) { shift_bwd_h(a, b, c, ux, hx); });
+    along<1>(m, [uy, hy](V &a, V &b, V &c) { shift_bwd_h(a, b, c, uy, hy); });
+    along<2>(m, [uz, hz](V &a, V &b, V &c) { shift_bwd_h(a, b, c, uz, hz); });
 
     {
-        const float sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
-        m[1] = fmaf(0.25f, Fq[0], m[1]);
-        m[3] = fmaf(0.25f, Fq[1], m[3]);
-        m[9] = fmaf(0.25f, Fq[2], m[9]);
-        m[7] = fmaf(sx, 1.0f / 12.0f, m[7]); m[19] = fmaf(sx, 1.0f / 12.0f, m[19]); m[25] = fmaf(sx, 1.0f / 36.0f, m[25]);
-        m[5] = fmaf(sy, 1.0f / 12.0f, m[5]); m[21] = fmaf(sy, 1.0f / 12.0f, m[21]); m[23] = fmaf(sy, 1.0f / 36.0f, m[23]);
-        m[11] = fmaf(sz, 1.0f / 12.0f, m[11]); m[15] = fmaf(sz, 1.0f / 12.0f, m[15]); m[17] = fmaf(sz, 1.0f / 36.0f, m[17]);
+        const V sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+        const V c4 = V(0.25f), c12 = V(1.0f / 12.0f), c36 = V(1.0f / 36.0f);
+        m[1] = vfma(c4, Fq[0], m[1]);
+        m[3] = vfma(c4, Fq[1], m[3]);
+        m[9] = vfma(c4, Fq[2], m[9]);
+        m[7] = vfma(sx, c12, m[7]); m[19] = vfma(sx, c12, m[19]); m[25] = vfma(sx, c36, m[25]);
+        m[5] = vfma(sy, c12, m[5]); m[21] = vfma(sy, c12, m[21]); m[23] = vfma(sy, c36, m[23]);
+        m[11] = vfma(sz, c12, m[11]); m[15] = vfma(sz, c12, m[15]); m[17] = vfma(sz, c36, m[17]);
     }
 
-    along<2>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
-    along<1>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
-    along<0>(m, [](float &a, float &b, float &c) { raw_bwd_h(a, b, c); });
+    along<2>(m, [](V &a, V &b, V &c) { raw_bwd_h(a, b, c); });
+    along<1>(m, [](V &a, V &b, V &c) { raw_bwd_h(a, b, c); });
+    along<0>(m, [](V &a, V &b, V &c) { raw_bwd_h(a, b, c); });
 }
 
 // Halving factor of moment k = a + 3b + 9c: 2^-(number of nonzero a, b, c).
@@ -475,23 +585,33 @@ __host__ __device__ constexpr float halving(int k)
 // Deviation target of the central moment k = a + 3b + 9c of order n >= 3: its
 // Maxwellian value minus the rest state's central moment about u, times the
 // factor h that dr = h drho and rr = h rref carry (h = halving(k)).
-__device__ __forceinline__ float high_target(int k, float dr, float rr, float ux, float uy, float uz)
+template <class V>
+__device__ __forceinline__ V high_target(int k, V dr, V nrr, V ux, V uy, V uz)
 {
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    // nrr = -rr: the rest state's part enters with a minus sign
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
     const int a = k % 3, b = (k / 3) % 3, c = k / 9;
     const int n = a + b + c;
-    const float hx[3] = {1.0f, -ux, (1.0f / 3.0f) + ux2};
-    const float hy[3] = {1.0f, -uy, (1.0f / 3.0f) + uy2};
-    const float hz[3] = {1.0f, -uz, (1.0f / 3.0f) + uz2};
-    if (a == 1 || b == 1 || c == 1) return -rr * (hx[a] * hy[b] * hz[c]);  // equilibrium 0
-    if (n == 4) {
-        const float p = (a == 2 ? ux2 : 0.f) + (b == 2 ? uy2 : 0.f) + (c == 2 ? uz2 : 0.f);
-        const float q = (a == 2 ? ux2 : 1.f) * (b == 2 ? uy2 : 1.f) * (c == 2 ? uz2 : 1.f);
-        return dr * (1.0f / 9.0f) - rr * (p * (1.0f / 3.0f) + q);
+    const V third = V(1.0f / 3.0f);
+    const V hx[3] = {V(1.0f), -ux, third + ux2};
+    const V hy[3] = {V(1.0f), -uy, third + uy2};
+    const V hz[3] = {V(1.0f), -uz, third + uz2};
+    if (a == 1 || b == 1 || c == 1) {  // equilibrium 0: -rr hx hy hz (factors 1 left out)
+        V p = V(1.0f);
+        bool have = false;
+        if (a) { p = hx[a]; have = true; }
+        if (b) { p = have ? p * hy[b] : hy[b]; have = true; }
+        if (c) { p = have ? p * hz[c] : hz[c]; }
+        return nrr * p;
     }
-    return dr * (1.0f / 27.0f) -
-           rr * ((ux2 + uy2 + uz2) * (1.0f / 9.0f) + (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * (1.0f / 3.0f) +
-                 ux2 * uy2 * uz2);
+    if (n == 4) {
+        const V p = (a == 2 && b == 2) ? ux2 + uy2 : ((a == 2) ? ux2 + uz2 : uy2 + uz2);
+        const V q = (a == 2 && b == 2) ? ux2 * uy2 : ((a == 2) ? ux2 * uz2 : uy2 * uz2);
+        return vfma(nrr, vfma(p, third, q), dr * V(1.0f / 9.0f));
+    }
+    return vfma(nrr,
+                vfma(ux2 + uy2 + uz2, V(1.0f / 9.0f), (ux2 * uy2 + ux2 * uz2 + uy2 * uz2) * third) + ux2 * uy2 * uz2,
+                dr * V(1.0f / 27.0f));
 }
 
 // Deviation form of the generic central-moment collision: m holds the raw
@@ -539,7 +659,7 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
         m[9] *= 0.5f;
         // orders 3..6 towards the Maxwellian central moments:
         // h (m + om (t - m)) = h (1 - om) m + om (h t)
-        const float d4 = 0.25f * drho, r4 = 0.25f * rref, d8 = 0.125f * drho, r8 = 0.125f * rref;
+        const float d4 = 0.25f * drho, r4 = -0.25f * rref, d8 = 0.125f * drho, r8 = -0.125f * rref;
 #pragma unroll
         for (int k = 0; k < 27; k++) {
             const int n = k % 3 + (k / 3) % 3 + k / 9;
@@ -557,82 +677,87 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
 // The same collision when omega_3 = omega_4 = omega_5 = omega_6 = 1: the
 // central moments of orders 3..6 land on their targets, so only the raw
 // moments of order <= 2 are formed and the forward shift reduces to the
-// first- and second-order central moments.
-__device__ __forceinline__ void collide27_w1(float (&m)[27], float rref, const float (&F)[3], const float (&Fq)[3],
+// first- and second-order central moments.  V = float (one node) or f2 (two
+// nodes, packed); rref is the launch's reference density.
+template <class V>
+__device__ __forceinline__ void collide27_w1(V (&m)[27], float rref, const V (&F)[3], const V (&Fq)[3],
                                              const Rates27f &w)
 {
-    along<0>(m, [](float &a, float &b, float &c) { raw_fwd(a, b, c); });
+    along<0>(m, [](V &a, V &b, V &c) { raw_fwd(a, b, c); });
     // Line (b, c) along x holds M0, M1, M2 at m[3b + 9c + 0..2]; e_y = b - 1, e_z = c - 1.
-    float Y0[3], Y1[3], Y2[3], X0[3], X1[3];
+    V Y0[3], Y1[3], Y2[3], X0[3], X1[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float s = m[9 * c + 6] + m[9 * c], d = m[9 * c + 6] - m[9 * c];
+        const V s = m[9 * c + 6] + m[9 * c], d = m[9 * c + 6] - m[9 * c];
         Y0[c] = s + m[9 * c + 3];
         Y1[c] = d;
         Y2[c] = s;
         X0[c] = (m[9 * c + 7] + m[9 * c + 1]) + m[9 * c + 4];
         X1[c] = m[9 * c + 7] - m[9 * c + 1];
     }
-    const float drho = (Y0[2] + Y0[0]) + Y0[1];
-    const float jz = fmaf(0.5f, F[2], Y0[2] - Y0[0]);
-    const float kzz = Y0[2] + Y0[0];
-    const float jy = fmaf(0.5f, F[1], (Y1[2] + Y1[0]) + Y1[1]);
-    const float kyz = Y1[2] - Y1[0];
-    const float kyy = (Y2[2] + Y2[0]) + Y2[1];
-    const float jx = fmaf(0.5f, F[0], (X0[2] + X0[0]) + X0[1]);
-    const float kxz = X0[2] - X0[0];
-    const float kxy = (X1[2] + X1[0]) + X1[1];
-    const float kxx = ((m[2] + m[5]) + (m[8] + m[11])) + ((m[14] + m[17]) + (m[20] + m[23])) + m[26];
+    const V half = V(0.5f);
+    const V drho = (Y0[2] + Y0[0]) + Y0[1];
+    const V jz = vfma(half, F[2], Y0[2] - Y0[0]);
+    const V kzz = Y0[2] + Y0[0];
+    const V jy = vfma(half, F[1], (Y1[2] + Y1[0]) + Y1[1]);
+    const V kyz = Y1[2] - Y1[0];
+    const V kyy = (Y2[2] + Y2[0]) + Y2[1];
+    const V jx = vfma(half, F[0], (X0[2] + X0[0]) + X0[1]);
+    const V kxz = X0[2] - X0[0];
+    const V kxy = (X1[2] + X1[0]) + X1[1];
+    const V kxx = ((m[2] + m[5]) + (m[8] + m[11])) + ((m[14] + m[17]) + (m[20] + m[23])) + m[26];
 
-    const float rho = rref + drho;
-    const float rinv = __frcp_rn(rho);
-    const float ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
-    const float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+    const V rho = V(rref) + drho;
+    const V rinv = vrcp(rho);
+    const V ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    const V nux = -ux, nuy = -uy, nuz = -uz;
+    const V ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
 
     // first-order central moments of the deviations (k1 = m1 - u m0)
-    const float k100 = fmaf(-ux, drho, jx), k010 = fmaf(-uy, drho, jy), k001 = fmaf(-uz, drho, jz);
+    const V k100 = vfma(nux, drho, jx), k010 = vfma(nuy, drho, jy), k001 = vfma(nuz, drho, jz);
     // second-order central moments (k2 = m2 - u (m1 + k1); mixed: k_ab = m_ab - u_a m_b - u_b k_a)
-    const float cxx = fmaf(-ux, jx + k100, kxx), cyy = fmaf(-uy, jy + k010, kyy), czz = fmaf(-uz, jz + k001, kzz);
-    const float cxy = fmaf(-uy, k100, fmaf(-ux, jy, kxy));
-    const float cxz = fmaf(-uz, k100, fmaf(-ux, jz, kxz));
-    const float cyz = fmaf(-uz, k010, fmaf(-uy, jz, kyz));
+    const V cxx = vfma(nux, jx + k100, kxx), cyy = vfma(nuy, jy + k010, kyy), czz = vfma(nuz, jz + k001, kzz);
+    const V cxy = vfma(nuy, k100, vfma(nux, jy, kxy));
+    const V cxz = vfma(nuz, k100, vfma(nux, jz, kxz));
+    const V cyz = vfma(nuz, k010, vfma(nuy, jz, kyz));
 
-    // relaxed central moments, halved
-    const float Tn = cxx + cyy + czz;
-    const float Ts = fmaf(w.wb, drho - rref * (ux2 + uy2 + uz2) - Tn, Tn);
-    const float D1 = cxx - cyy, D2 = cxx - czz;
+    // relaxed central moments, halved; the rest state's second central
+    // moments about u are rref (1/3 + u_a^2) and rref u_a u_b
+    const V Tn = cxx + cyy + czz;
+    const V Ts = vfma(V(w.wb), vfma(V(-rref), ux2 + uy2 + uz2, drho) - Tn, Tn);
+    const V D1 = cxx - cyy, D2 = cxx - czz;
     const float rs = 1.0f - w.ws;
-    const float rh = 0.5f * rs, rq = 0.25f * rs, wh = 0.5f * w.ws * rref, wq = 0.25f * w.ws * rref;
-    const float D1h = rh * D1 - wh * (ux2 - uy2);
-    const float D2h = rh * D2 - wh * (ux2 - uz2);
-    const float sxx = fmaf(Ts, 1.0f / 6.0f, (D1h + D2h) * (1.0f / 3.0f));
-    const float d4 = 0.25f * drho, r4 = 0.25f * rref, d8 = 0.125f * drho, r8 = 0.125f * rref;
+    const V rh = V(0.5f * rs), rq = V(0.25f * rs), nwh = V(-0.5f * w.ws * rref), nwq = V(-0.25f * w.ws * rref);
+    const V D1h = vfma(nwh, ux2 - uy2, rh * D1);
+    const V D2h = vfma(nwh, ux2 - uz2, rh * D2);
+    const V sxx = vfma(Ts, V(1.0f / 6.0f), (D1h + D2h) * V(1.0f / 3.0f));
+    const V d4 = V(0.25f) * drho, nr4 = V(-0.25f * rref), d8 = V(0.125f) * drho, nr8 = V(-0.125f * rref);
 #pragma unroll
     for (int k = 0; k < 27; k++) {
         const int n = k % 3 + (k / 3) % 3 + k / 9;
         const bool quarter = halving(k) == 0.25f;
-        if (n >= 3) m[k] = high_target(k, quarter ? d4 : d8, quarter ? r4 : r8, ux, uy, uz);
+        if (n >= 3) m[k] = high_target(k, quarter ? d4 : d8, quarter ? nr4 : nr8, ux, uy, uz);
     }
     m[0] = drho;
-    m[1] = 0.5f * k100;
-    m[3] = 0.5f * k010;
-    m[9] = 0.5f * k001;
+    m[1] = half * k100;
+    m[3] = half * k010;
+    m[9] = half * k001;
     m[2] = sxx;
     m[6] = sxx - D1h;
     m[18] = sxx - D2h;
-    m[4] = rq * cxy - wq * (ux * uy);
-    m[10] = rq * cxz - wq * (ux * uz);
-    m[12] = rq * cyz - wq * (uy * uz);
+    m[4] = vfma(nwq, ux * uy, rq * cxy);
+    m[10] = vfma(nwq, ux * uz, rq * cxz);
+    m[12] = vfma(nwq, uy * uz, rq * cyz);
     finish27(m, ux, uy, uz, F, Fq);
 }
 
 // 4 resident blocks per SM (<= 64 registers): the reduced-precision D3Q27
 // step is memory-bound, so occupancy to cover load latency matters more than
 // registers.
-template <class T, int FK, bool W1>
+template <class T, int FK, bool W1, bool SR = false>
 __global__ void __launch_bounds__(kBlock, 4)
 k_step27(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apre, float apost, Rates27f w,
-         float rref)
+         float rref, unsigned long long srkey)
 {
     int i = blockIdx.x * kBlock + threadIdx.x;
     if (i >= g.N) return;
@@ -651,8 +776,127 @@ k_step27(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apr
     }
     if (W1) collide27_w1(m, rref, F, Fq, w);
     else collide27(m, rref, F, Fq, w);
+    SRBits rb(srkey, i);
 #pragma unroll
-    for (int a = 0; a < 27; a++) P.out[a][i] = Dev<T>::to_store(m[a]);
+    for (int a = 0; a < 27; a++) P.out[a][i] = store_dev<T, SR>(m[a], rb, a);
+}
+
+// 16-bit storage, unit higher rates: two x-neighbouring nodes (x even, x + 1)
+// per thread, every moment operation one packed f32x2 instruction for both.
+// The 16-bit step moves half the bytes of the FP32 one but issues as many
+// instructions per node, so one node per thread is bound by instruction
+// issue; the pair halves the arithmetic instructions, shares each plane's
+// address between the two nodes, loads the populations with e_x = 0 of both
+// nodes as one 32-bit word and stores every plane's two values as one 32-bit
+// word.  Needs nx even (the pair never straddles a row); the launcher checks.
+template <class T> struct Pair16;
+template <> struct Pair16<__half> {
+    __device__ static f2 get2(const __half *p)
+    {
+        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+        __half2 h;
+        memcpy(&h, &u, sizeof h);
+        return f2(__half22float2(h));
+    }
+    __device__ static void put2(__half *p, const f2 &v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v.v); }
+    __device__ static void put2raw(__half *p, __half a, __half b) { *reinterpret_cast<__half2 *>(p) = __halves2half2(a, b); }
+};
+template <> struct Pair16<__nv_bfloat16> {
+    __device__ static f2 get2(const __nv_bfloat16 *p)
+    {
+        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+        __nv_bfloat162 h;
+        memcpy(&h, &u, sizeof h);
+        return f2(__bfloat1622float2(h));
+    }
+    __device__ static void put2(__nv_bfloat16 *p, const f2 &v)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v.v);
+    }
+    __device__ static void put2raw(__nv_bfloat16 *p, __nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(a, b);
+    }
+};
+
+// Pulled deviations of the node pair (i0 = node (x, y, z), x even; i0 + 1).
+template <class T>
+__device__ __forceinline__ void pull_pair27(const Planes<T, 27> &P, const Geom &g, int x, int y, int z, int i0,
+                                            f2 (&m)[27])
+{
+    const bool wall_x = g.wall[0] && (x == 0 || x + 1 == g.nx - 1);
+    const bool wall_y = g.wall[1] && (y == 0 || y == g.ny - 1);
+    const bool wall_z = g.wall[2] && (z == 0 || z == g.nz - 1);
+    if (!(wall_x || wall_y || wall_z)) {
+        // wrapped source offsets along y and z (as pull_node), and along x:
+        // e_x = +1 takes x - 1 (node 0 wraps at x = 0; node 1's source is
+        // node 0's position), e_x = -1 takes x + 1 (node 0's source is node
+        // 1's position; node 1 wraps at x + 1 = nx - 1)
+        const int sy = g.nx, sz = g.nx * g.ny;
+        const int ym = y == 0 ? (g.ny - 1) * sy : -sy, yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+        const int zm = z == 0 ? (g.nz - 1) * sz : -sz, zp = z == g.nz - 1 ? (1 - g.nz) * sz : sz;
+        const int xm0 = x == 0 ? g.nx - 1 : -1;
+        const int xp1 = x + 1 == g.nx - 1 ? 2 - g.nx : 2;
+#pragma unroll
+        for (int a = 0; a < 27; a++) {
+            const int ex = LD3Q27::ex(a), ey = LD3Q27::ey(a), ez = LD3Q27::ez(a);
+            const T *pl = P.in[a] + i0 + (ey == 1 ? ym : (ey == -1 ? yp : 0)) + (ez == 1 ? zm : (ez == -1 ? zp : 0));
+            if (ex == 0) m[a] = Pair16<T>::get2(pl);  // both nodes' values, one aligned word
+            else if (ex == 1) m[a] = f2(Dev<T>::get(pl + xm0), Dev<T>::get(pl));
+            else m[a] = f2(Dev<T>::get(pl + 1), Dev<T>::get(pl + xp1));
+        }
+        return;
+    }
+    float d0[27], d1[27];
+    load_pulled_dev<LD3Q27, T>(P, g, x, y, z, i0, d0);
+    load_pulled_dev<LD3Q27, T>(P, g, x + 1, y, z, i0 + 1, d1);
+#pragma unroll
+    for (int a = 0; a < 27; a++) m[a] = f2(d0[a], d1[a]);
+}
+
+constexpr int kBlockPair = 128;
+// Blocks of the pair kernel resident per SM (bounds its registers): 6 x 128
+// threads at <= 80 registers keep 1536 nodes' loads in flight per SM; 4
+// blocks (120 registers, no spills) ran at 0.69 of HBM on the 512^3 FP16 grid,
+// 5 at 0.75, 6 at 0.79 (a few spilled registers cost less than the loads the
+// extra blocks keep in flight).
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 6
+#endif
+
+template <class T, int FK, bool SR = false>
+__global__ void __launch_bounds__(kBlockPair, LBM_PAIR_MIN_BLOCKS)
+k_step27x2(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apre, float apost, Rates27f w,
+           float rref, unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlockPair + threadIdx.x;
+    if (t >= (g.N >> 1)) return;
+    const int i0 = 2 * t;
+    int x, y, z;
+    node_xyz(g, i0, x, y, z);
+    f2 m[27];
+    pull_pair27<T>(P, g, x, y, z, i0, m);
+    f2 F[3] = {f2(0.f), f2(0.f), f2(0.f)}, Fq[3] = {f2(0.f), f2(0.f), f2(0.f)};
+    if (FK != FK_NONE) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const f2 Pd(field_value_f(Fd, FK, d, x, y, z, i0), field_value_f(Fd, FK, d, x + 1, y, z, i0 + 1));
+            F[d] = f2(apre) * Pd;
+            Fq[d] = f2(apost) * Pd;
+        }
+    }
+    collide27_w1(m, rref, F, Fq, w);
+    if constexpr (SR) {
+        SRBits r0(srkey, i0), r1(srkey, i0 + 1);
+#pragma unroll
+        for (int a = 0; a < 27; a++) {
+            const T lo = Round<T>::sr(m[a].v.x, r0.get(a)), hi = Round<T>::sr(m[a].v.y, r1.get(a));
+            Pair16<T>::put2raw(P.out[a] + i0, lo, hi);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 27; a++) Pair16<T>::put2(P.out[a] + i0, m[a]);
+    }
 }
 
 // --------------------------------------------------------------- batched ---
@@ -762,7 +1006,9 @@ __device__ __forceinline__ void finish5(const BatchItem &B, const BatchLaunch &L
         k.P3 = B.fcoef[4]; k.X3 = B.fcoef[5]; k.Y3 = B.fcoef[6]; k.S3 = B.fcoef[7];
         k.P4 = B.fcoef[8]; k.X4 = B.fcoef[9]; k.Y4 = B.fcoef[10]; k.D4 = B.fcoef[11];
         k.Q3 = B.fcoef[16];
-        collide5u(d, rref, Sp, H0, k);
+        collide5u(d, 0.0f, Sp, H0, k);
+#pragma unroll
+        for (int a = 0; a < 5; a++) d[a] += B.fref[a];
     } else {
         const Rates5f w{B.fcoef[12], B.fcoef[13], B.fcoef[14], B.fcoef[15]};
         collide5(d, rref, Sp, H0, s.ux, s.uy, w);
@@ -827,17 +1073,46 @@ __global__ void __launch_bounds__(TB, 1024 / TB) k_batch27(const __grid_constant
 }
 
 
-template <class T, bool W1>
+template <class T, bool W1, bool SR>
 void step9_launch(const Planes<T, 9> &fin, const LaunchArgs &a, int grid, float apre, float gsum, const Rates9f &w,
                   float rref, cudaStream_t s)
 {
-    if (a.fkind == FK_NONE) k_step9<T, FK_NONE, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
-    else if (a.fkind == FK_CONST) k_step9<T, FK_CONST, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
-    else k_step9<T, FK_GENERAL, W1><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref);
+    const unsigned long long k = a.srkey;
+    if (a.fkind == FK_NONE) k_step9<T, FK_NONE, W1, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+    else if (a.fkind == FK_CONST)
+        k_step9<T, FK_CONST, W1, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+    else k_step9<T, FK_GENERAL, W1, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
 }
 
-template <class T>
-cudaError_t step_t(int lattice, const LaunchArgs &a)
+template <class T, int SK, bool SR>
+void step5_launch(const Planes<T, 5> &fin, const LaunchArgs &a, int grid, float apre, float hsum, const Rates5f &w,
+                  const Coef5f &k, float rref, const Ref5f &cref, bool uni, cudaStream_t s)
+{
+    if (uni)
+        k_step5<T, SK, true, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref, cref, a.srkey);
+    else
+        k_step5<T, SK, false, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref, cref, a.srkey);
+}
+
+template <class T, int FK, bool SR>
+void step27_launch(const Planes<T, 27> &fin, const LaunchArgs &a, float ap, float aq, const Rates27f &w, float rref,
+                   bool w1, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 2) {
+        if (w1 && a.g.nx % 2 == 0) {
+            // two x-neighbouring nodes per thread, packed FP32x2 arithmetic
+            const int pgrid = (a.g.N / 2 + kBlockPair - 1) / kBlockPair;
+            k_step27x2<T, FK, SR><<<pgrid, kBlockPair, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
+            return;
+        }
+    }
+    const int grid = (a.g.N + kBlock - 1) / kBlock;
+    if (w1) k_step27<T, FK, true, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
+    else k_step27<T, FK, false, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
+}
+
+template <class T, bool SR>
+cudaError_t step_ts(int lattice, const LaunchArgs &a)
 {
     const int grid = (a.g.N + kBlock - 1) / kBlock;
     const float rref = (float)a.rho_ref;
@@ -848,8 +1123,8 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
                         (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
         const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre;
         const bool w1 = a.omega[6] == 1.0 && a.omega[7] == 1.0 && a.omega[8] == 1.0;
-        if (w1) step9_launch<T, true>(fin, a, grid, apre, gsum, w, rref, s);
-        else step9_launch<T, false>(fin, a, grid, apre, gsum, w, rref, s);
+        if (w1) step9_launch<T, true, SR>(fin, a, grid, apre, gsum, w, rref, s);
+        else step9_launch<T, false, SR>(fin, a, grid, apre, gsum, w, rref, s);
     } else if (lattice == LD2Q5::ID) {
         const Rates5f w{(float)(a.omega[1] / 2.0), (float)(a.omega[2] / 2.0), (float)(a.omega[3] / 4.0),
                         (float)(a.omega[4] / 4.0)};
@@ -857,35 +1132,39 @@ cudaError_t step_t(int lattice, const LaunchArgs &a)
         const Coef5f k = make_coef5f(a.omega, ux, uy);
         const float hsum = (float)((a.apre + a.apost) / 10.0), apre = (float)a.apre;
         const bool uni = a.vkind != FK_GENERAL;
-        const Planes<T, 5> fin = make_planes<T, 5>(a.fin, a.fout, a.g.Np);
-        if (a.fkind == FK_NONE) {
-            if (uni) k_step5<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
-        } else if (a.fkind == FK_CONST) {
-            if (uni) k_step5<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
-        } else {
-            if (uni) k_step5<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
-            else k_step5<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref);
+        Ref5f cref{};
+        if (uni) {
+            double c[5];
+            d2q5_reference_change(a.omega, ux, uy, a.gref, c);
+            for (int q = 0; q < 5; q++) cref.v[q] = (float)c[q];
         }
+        const Planes<T, 5> fin = make_planes<T, 5>(a.fin, a.fout, a.g.Np);
+        if (a.fkind == FK_NONE) step5_launch<T, FK_NONE, SR>(fin, a, grid, apre, hsum, w, k, rref, cref, uni, s);
+        else if (a.fkind == FK_CONST)
+            step5_launch<T, FK_CONST, SR>(fin, a, grid, apre, hsum, w, k, rref, cref, uni, s);
+        else step5_launch<T, FK_GENERAL, SR>(fin, a, grid, apre, hsum, w, k, rref, cref, uni, s);
     } else {
         const Rates27f w{(float)a.omega[1], (float)a.omega[2], (float)a.omega[3],
                          (float)a.omega[4], (float)a.omega[5], (float)a.omega[6]};
         const bool w1 = a.omega[3] == 1.0 && a.omega[4] == 1.0 && a.omega[5] == 1.0 && a.omega[6] == 1.0;
         const float ap = (float)a.apre, aq = (float)a.apost;
         const Planes<T, 27> fin = make_planes<T, 27>(a.fin, a.fout, a.g.Np);
-        if (a.fkind == FK_NONE) {
-            if (w1) k_step27<T, FK_NONE, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_NONE, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-        } else if (a.fkind == FK_CONST) {
-            if (w1) k_step27<T, FK_CONST, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_CONST, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-        } else {
-            if (w1) k_step27<T, FK_GENERAL, true><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-            else k_step27<T, FK_GENERAL, false><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref);
-        }
+        if (a.fkind == FK_NONE) step27_launch<T, FK_NONE, SR>(fin, a, ap, aq, w, rref, w1, s);
+        else if (a.fkind == FK_CONST) step27_launch<T, FK_CONST, SR>(fin, a, ap, aq, w, rref, w1, s);
+        else step27_launch<T, FK_GENERAL, SR>(fin, a, ap, aq, w, rref, w1, s);
     }
     return cudaGetLastError();
+}
+
+// Stochastic rounding is a 16-bit storage option (FP32 rounding is taken to
+// nearest always).
+template <class T>
+cudaError_t step_t(int lattice, const LaunchArgs &a)
+{
+    if constexpr (sizeof(T) == 2) {
+        if (a.sround) return step_ts<T, true>(lattice, a);
+    }
+    return step_ts<T, false>(lattice, a);
 }
 
 template <class T, int TB, int M>
@@ -937,6 +1216,29 @@ int resident_t(int lattice, int tile)
 }
 
 }  // namespace
+
+void d2q5_batch_coef(const double omega[9], BatchItem &item);
+
+void d2q5_step_matrix(const double omega[9], double ux, double uy, double M[25])
+{
+    BatchItem it{};
+    it.vkind = FK_CONST;
+    it.V.cval[0] = ux;
+    it.V.cval[1] = uy;
+    d2q5_batch_coef(omega, it);
+    for (int k = 0; k < 25; k++) M[k] = it.mat[k];
+}
+
+void d2q5_reference_change(const double omega[9], double ux, double uy, const double g[5], double out[5])
+{
+    double M[25];
+    d2q5_step_matrix(omega, ux, uy, M);
+    for (int a = 0; a < 5; a++) {
+        double acc = 0.0;
+        for (int b = 0; b < 5; b++) acc += M[5 * a + b] * g[b];
+        out[a] = acc - g[a];
+    }
+}
 
 cudaError_t rp_step(int lattice, const LaunchArgs &a)
 {

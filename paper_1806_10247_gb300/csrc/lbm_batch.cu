@@ -170,6 +170,9 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count)
         if (!ctxs[i]) return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d is NULL", i);
         if (ctxs[i]->lattice != ctxs[0]->lattice || ctxs[i]->storage != ctxs[0]->storage)
             return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: contexts differ in lattice or storage");
+        if (ctxs[i]->sround)
+            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d rounds stochastically (single-lattice "
+                                              "steps only)", i);
         if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
             return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: contexts differ in stream or device");
         for (int j = 0; j < i; j++)
@@ -347,6 +350,13 @@ int refresh_descriptors(lbm_batch *b, int *parity)
         for (int k = 0; k < 16; k++) it.fcoef[k] = (float)it.coef[k];
         it.fcoef[16] = (float)(it.coef[4] + (2.0 / 3.0) * it.coef[7]);
         it.frho_ref = (float)it.rho_ref;
+        if (c->lattice == LBM_D2Q5_CDE && c->storage != LBM_FP64 && it.vkind != FK_GENERAL) {
+            // what one step adds to the member's reference: M g_ref - g_ref
+            double cr[5];
+            d2q5_reference_change(c->omega, it.vkind == FK_CONST ? it.V.cval[0] : 0.0,
+                                  it.vkind == FK_CONST ? it.V.cval[1] : 0.0, c->gref, cr);
+            for (int k = 0; k < 5; k++) it.fref[k] = (float)cr[k];
+        }
         it.variant = batch_variant(c->lattice, c->omega, it.fkind, it.F);
         if (c->storage != LBM_FP64) it.variant &= 1;  // the reduced-precision kernels have no force-along-x form
         b->item_version[i] = c->version;

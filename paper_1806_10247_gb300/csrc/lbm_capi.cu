@@ -119,7 +119,55 @@ LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double
     a.stream = c->stream;
     a.storage = c->storage;
     a.rho_ref = c->rho_ref;
+    a.sround = c->sround;
+    a.srkey = sr_step_key(c->sr_seed, c->t);
+    for (int k = 0; k < 5; k++) a.gref[k] = c->gref[k];
     return a;
+}
+
+lbmk::Ref5 ref5(const lbm_ctx *c)
+{
+    lbmk::Ref5 r;
+    for (int k = 0; k < 5; k++) r.v[k] = c->gref[k];
+    return r;
+}
+
+// D2Q5 reference populations for reduced-precision storage: the equilibrium
+// at (rho_ref, u) for a periodic lattice whose advecting velocity u is
+// uniform (the step maps it to itself: the stored deviations then carry the
+// scalar's variation only); else the rest state w rho_ref (a wall reflects a
+// population into the opposite slot, and a field velocity has no single
+// equilibrium).  The D2Q5 equilibrium of Eq. 39: g_0 = rho (1/3 - ux^2 -
+// uy^2), g_{+-x} = rho (1/3 + ux^2 +- ux) / 2, g_{+-y} likewise.
+void choose_d2q5_reference(lbm_ctx *c)
+{
+    const double r = c->rho_ref;
+    const bool periodic = !c->g.wall[0] && !c->g.wall[1];
+    if (periodic && c->vel.kind != FK_GENERAL) {
+        const double ux = c->vel.kind == FK_CONST ? c->vel.d.cval[0] : 0.0;
+        const double uy = c->vel.kind == FK_CONST ? c->vel.d.cval[1] : 0.0;
+        c->gref[0] = r * ((1.0 / 3.0) - ux * ux - uy * uy);
+        c->gref[1] = 0.5 * r * ((1.0 / 3.0) + ux * ux + ux);
+        c->gref[3] = 0.5 * r * ((1.0 / 3.0) + ux * ux - ux);
+        c->gref[2] = 0.5 * r * ((1.0 / 3.0) + uy * uy + uy);
+        c->gref[4] = 0.5 * r * ((1.0 / 3.0) + uy * uy - uy);
+    } else {
+        c->gref[0] = r / 3.0;
+        for (int k = 1; k < 5; k++) c->gref[k] = r / 6.0;
+    }
+}
+
+// Key of step t's stochastic-rounding bits: the seed, mixed (SplitMix64
+// output function, see k_rp.cu), XOR the step counter shifted above the
+// node and chunk bits of the per-node counter (node < 2^31, chunk < 8), so
+// that every (step < 2^30, node, chunk) has its own counter.
+unsigned long long sr_step_key(unsigned long long seed, long t)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z ^ ((unsigned long long)t << 34);
 }
 
 // Reduced-precision contexts: FP64 staging of q*N doubles for host I/O.
@@ -405,7 +453,9 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
         c->launches += 2;
     } else {
         c->rho_ref = rho0 > 0.0 ? rho0 : 1.0;
-        CK(rp_init_equilibrium(c->lattice, c->storage, c->g, c->rho_ref, rho0, uu, drho, du, c->A, c->stream),
+        if (c->lattice == LBM_D2Q5_CDE) choose_d2q5_reference(c);
+        CK(rp_init_equilibrium(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), rho0, uu, drho, du, c->A,
+                               c->stream),
            "equilibrium kernel");
         c->launches += 1;
     }
@@ -441,7 +491,25 @@ int lbm_set_velocity(lbm_ctx *c, const lbm_field *u)
     c->err.clear();
     c->version++;
     if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_velocity: only for the scalar lattice");
-    return upload_field(c, u, 2, c->vel, "lbm_set_velocity");
+    int rc = upload_field(c, u, 2, c->vel, "lbm_set_velocity");
+    if (rc != LBM_OK || c->storage == LBM_FP64 || !c->initialised || c->vel.kind != FK_GENERAL) return rc;
+    // A velocity field needs the rest-state reference: re-express the stored
+    // deviations (gather with the old reference, scatter with the new one).
+    double rest[5] = {c->rho_ref / 3.0, c->rho_ref / 6.0, c->rho_ref / 6.0, c->rho_ref / 6.0, c->rho_ref / 6.0};
+    bool same = true;
+    for (int k = 0; k < 5; k++) same = same && c->gref[k] == rest[k];
+    if (same) return LBM_OK;
+    rc = ensure_stage(c);
+    if (rc != LBM_OK) return rc;
+    rc = wait_readers(c, nullptr);
+    if (rc != LBM_OK) return rc;
+    CK(rp_gather(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), c->A, c->stage, c->stream), "gather kernel");
+    for (int k = 0; k < 5; k++) c->gref[k] = rest[k];
+    CK(rp_scatter(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), c->stage, c->A, c->stream), "scatter kernel");
+    c->launches += 2;
+    c->version++;
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_velocity");
+    return LBM_OK;
 }
 
 int lbm_set_envelope(lbm_ctx *c, lbm_envelope_fn fn, void *user)
@@ -469,6 +537,18 @@ int lbm_set_envelope_table(lbm_ctx *c, const double *a, long count, double t0)
     return LBM_OK;
 }
 
+int lbm_set_stochastic_rounding(lbm_ctx *c, int on, unsigned long long seed)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->storage != LBM_FP16_DEV && c->storage != LBM_BF16_DEV)
+        return fail(c, LBM_EINVAL, "lbm_set_stochastic_rounding: only for FP16 / BF16 deviation storage");
+    c->sround = on ? 1 : 0;
+    c->sr_seed = seed;
+    c->version++;
+    return LBM_OK;
+}
+
 int lbm_step(lbm_ctx *c, long n)
 {
     NvtxRange nvtx_("lbm_step");
@@ -484,7 +564,7 @@ int lbm_step(lbm_ctx *c, long n)
         const int rc = wait_readers(c, n == 1 ? c->B : nullptr);
         if (rc != LBM_OK) return rc;
     }
-    if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty()) {
+    if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty() && !c->sround) {
         // a small lattice with a constant force: all n steps in one cluster launch
         double *out = (n & 1) ? c->B : c->A;
         LaunchArgs a = launch_args(c, c->A, out, 1.0, 1.0);
@@ -766,7 +846,7 @@ int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where, long *
             if (rc != LBM_OK) return rc;
             plain = c->stage;
         }
-        CK(rp_gather(c->lattice, c->storage, c->g, c->rho_ref, c->A, plain, c->stream), "gather kernel");
+        CK(rp_gather(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), c->A, plain, c->stream), "gather kernel");
         c->launches++;
         if (!where) {
             CK(cudaMemcpyAsync(dst, plain, (size_t)c->q * N * sizeof(double), kind, c->stream), "copy populations");
@@ -807,7 +887,7 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
             CK(cudaMemcpyAsync(c->stage, src, (size_t)c->q * N * sizeof(double), kind, c->stream), "copy populations");
             plain = c->stage;
         }
-        CK(rp_scatter(c->lattice, c->storage, c->g, c->rho_ref, plain, c->A, c->stream), "scatter kernel");
+        CK(rp_scatter(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), plain, c->A, c->stream), "scatter kernel");
         c->launches++;
         CK(cudaStreamSynchronize(c->stream), "lbm_set_populations");
         c->t = step;

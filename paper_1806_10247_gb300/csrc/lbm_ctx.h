@@ -25,6 +25,11 @@ struct lbm_ctx {
     int lattice = 0, q = 0, dim = 0, storage = 0;
     int elem = 8;         // bytes per stored population value
     double rho_ref = 1.0; // reduced-precision storage: reference of the deviations
+    int sround = 0;       // 16-bit storage: stochastic rounding of the stored deviations
+    unsigned long long sr_seed = 0;
+    // D2Q5 reduced-precision storage: reference populations of the deviations
+    // (lbmk::Ref5; set at lbm_init_equilibrium)
+    double gref[5] = {0, 0, 0, 0, 0};
     double *stage = nullptr;  // reduced-precision storage: q*N doubles for host I/O (lazy)
     int device = 0;       // CUDA device that was current at lbm_create
     lbmk::Geom g{};
@@ -79,6 +84,10 @@ int ensure_stage(lbm_ctx *c);
 // Before work on c's stream writes population buffer `buf` (nullptr: either
 // buffer), make the stream wait for the readbacks that may still read it.
 int wait_readers(lbm_ctx *c, const void *buf);
+// The D2Q5 reference populations of c as a kernel argument.
+lbmk::Ref5 ref5(const lbm_ctx *c);
+// Key of step t's stochastic-rounding bits (seed mixed, step in the high bits).
+unsigned long long sr_step_key(unsigned long long seed, long t);
 // Launch arguments of the context's kernels.
 lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
 

@@ -35,17 +35,36 @@ struct LaunchArgs {
     cudaStream_t stream;
     int storage;         // 0 FP64 populations; 1/2/3 FP32/FP16/BF16 deviations f - w rho_ref
     double rho_ref;      // reference density/scalar of the deviations
+    int sround;          // 16-bit storage: round the stored deviations stochastically
+    unsigned long long srkey;  // ... with random bits keyed by this step key
+    double gref[5];      // D2Q5, reduced precision: reference populations of the deviations
 };
+
+// D2Q5 reduced-precision storage keeps deviations d = g - g_ref from a
+// uniform reference g_ref (sum g_ref = rho_ref): the rest state w rho_ref, or,
+// on a periodic lattice with a uniform advecting velocity, the equilibrium at
+// (rho_ref, u), which the step leaves unchanged, so the deviations carry the
+// scalar's signal alone instead of the background's advection term.
+struct Ref5 {
+    double v[5];
+};
+
+// The source-free D2Q5 step matrix M of a uniform advecting velocity (Eqs. 41
+// and 48 applied to the unit vectors; row-major), and C(g) - g = M g - g for
+// a uniform state g (what one step adds to a uniform reference).
+void d2q5_step_matrix(const double omega[9], double ux, double uy, double M[25]);
+void d2q5_reference_change(const double omega[9], double ux, double uy, const double g[5], double out[5]);
 
 // Reduced-precision storage (deviations from the rest state w * rho_ref):
 // fused equilibrium fill into the stored layout, conversions between f(t) as
 // dense [q][N] doubles and the stored layout, and the step kernel.
-cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, double rho0,
-                                const double *u0, const double *rho, const double *u, void *stored,
+// gref: the D2Q5 reference (ignored by the other lattices, whose reference is w rho_ref).
+cudaError_t rp_init_equilibrium(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref,
+                                double rho0, const double *u0, const double *rho, const double *u, void *stored,
                                 cudaStream_t s);
-cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const double *plain,
-                       void *stored, cudaStream_t s);
-cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const void *stored,
+cudaError_t rp_scatter(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref,
+                       const double *plain, void *stored, cudaStream_t s);
+cudaError_t rp_gather(int lattice, int storage, const Geom &g, double rho_ref, const Ref5 &gref, const void *stored,
                       double *plain, cudaStream_t s);
 cudaError_t rp_step(int lattice, const LaunchArgs &a);
 
@@ -67,6 +86,7 @@ struct BatchItem {
                       // D2Q5: [16] holds P3 + (2/3) S3 of the uniform-velocity form
     float frho_ref;
     int variant;      // collision variant of this member (batch_variant)
+    float fref[5];    // D2Q5 reduced precision, uniform velocity: M g_ref - g_ref, added after the collision
     double mat[25];   // D2Q5 with a uniform advecting velocity, FP64: step matrix M (row-major)
 };
 

@@ -5,11 +5,14 @@
 // device that runs them.
 //
 // The probe kernel runs 8 or 16 independent dependency chains per thread of
-// one FP64 operation (FMA, add or multiply) with operands that arrive as
-// kernel arguments, so the compiler can neither fold nor reorder them; the
-// loop (unrolled four times) keeps its bookkeeping on the integer pipes, so
-// the count of FP64 instructions issued is exactly
-// blocks * threads * iters * chains.
+// one FP64 operation (FMA, add or multiply).  The second and third operands
+// are read from constant memory, as the step kernels read their rates and
+// weights: with every operand in a register the unit issued at 1.68 per
+// clock per SM on the GB300 (three 64-bit register reads per instruction),
+// with constant operands at 2.0, the unit's rate.  The compiler can neither
+// fold nor reorder the chains; the loop (unrolled four times) keeps its
+// bookkeeping on the integer pipes, so the count of FP64 instructions issued
+// is exactly blocks * threads * iters * chains.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -26,8 +29,12 @@ int probe_fail(int code, const char *what, cudaError_t e)
     return code;
 }
 
+// x -> x a + b stays near 1; x + b grows by 1e-9 per step; x a decays by
+// 1e-9 per step: every chain stays finite and away from subnormals
+__constant__ double c_a = 1.0 - 1e-9, c_b = 1e-9;
+
 template <int OP, int kChains>
-__global__ void k_fp64_rate(long long iters, double a, double b, double *sink)
+__global__ void k_fp64_rate(long long iters, double *sink)
 {
     double x[kChains];
 #pragma unroll
@@ -36,9 +43,9 @@ __global__ void k_fp64_rate(long long iters, double a, double b, double *sink)
     for (long long it = 0; it < iters; it++) {
 #pragma unroll
         for (int k = 0; k < kChains; k++) {
-            if (OP == 0) x[k] = fma(x[k], a, b);
-            else if (OP == 1) x[k] = x[k] + b;
-            else x[k] = x[k] * a;
+            if (OP == 0) x[k] = fma(x[k], c_a, c_b);
+            else if (OP == 1) x[k] = x[k] + c_b;
+            else x[k] = x[k] * c_a;
         }
     }
     double s = 0.0;
@@ -49,11 +56,11 @@ __global__ void k_fp64_rate(long long iters, double a, double b, double *sink)
 }
 
 template <int CH>
-void launch_rate(int op, int blocks, int threads, long long iters, double a, double b, double *sink, cudaStream_t s)
+void launch_rate(int op, int blocks, int threads, long long iters, double *sink, cudaStream_t s)
 {
-    if (op == 0) k_fp64_rate<0, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
-    else if (op == 1) k_fp64_rate<1, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
-    else k_fp64_rate<2, CH><<<blocks, threads, 0, s>>>(iters, a, b, sink);
+    if (op == 0) k_fp64_rate<0, CH><<<blocks, threads, 0, s>>>(iters, sink);
+    else if (op == 1) k_fp64_rate<1, CH><<<blocks, threads, 0, s>>>(iters, sink);
+    else k_fp64_rate<2, CH><<<blocks, threads, 0, s>>>(iters, sink);
 }
 
 }  // namespace
@@ -84,12 +91,8 @@ int lbm_probe_fp64(int op, int chains, int blocks, int threads, long long iters,
         threads % 32 || iters < 1 || !sink)
         return probe_fail(LBM_EINVAL, "lbm_probe_fp64: bad arguments", cudaSuccess);
     cudaStream_t s = (cudaStream_t)stream;
-    // a, b keep every chain finite and away from subnormals for any iters the
-    // probe is run with (x -> x a + b stays near 1; x + b grows by 1e-9 per
-    // step; x a decays by 1e-9 per step)
-    const double a = 1.0 - 1e-9, b = 1e-9;
-    if (chains == 8) launch_rate<8>(op, blocks, threads, iters, a, b, sink, s);
-    else launch_rate<16>(op, blocks, threads, iters, a, b, sink, s);
+    if (chains == 8) launch_rate<8>(op, blocks, threads, iters, sink, s);
+    else launch_rate<16>(op, blocks, threads, iters, sink, s);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return probe_fail(LBM_ECUDA, "lbm_probe_fp64: launch", e);
     return LBM_OK;
