@@ -91,6 +91,12 @@ TRAFFIC = {
     ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
                              "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,
                              "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md"},
+    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "ca473d3af7e9177b", "above_l2": True,
+                        "bytes_per_node": (382.279680 + 334.776576) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+                        "profile": "profiles/k_step27x2_kolmogorov_fp16_pair.md"},
+    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "ca473d3af7e9177b", "above_l2": True,
+                       "bytes_per_node": (1208.092160 + 1154.119680) * 1e6 / (8192 * 4096),
+                       "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9_channel8192_fp32.md"},
     ("d2q9", "fp64"): {"src": [_C + "k_d2q9.cu"] + _H, "sha": "018f6162beb1528d",
                        "bytes_per_node": (151.018240 + 99.837696) * 1e6 / (2048 * 1024),
                        "captured_nodes": 2048 * 1024, "profile": "profiles/k_step_d2q9_channel2048_fp64.md"},
@@ -105,9 +111,15 @@ def src_hash(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(key, nodes):
+def traffic_per_launch(key, nodes, state=None):
+    """Traffic of one launch scaled from a capture by the node count, while
+    the kernel sources are unchanged; captures marked above_l2 (taken on a
+    state many times L2) apply only to states at least four times L2 (a
+    smaller launch leaves part of its writes in L2)."""
     t = TRAFFIC.get(key)
     if t is None or src_hash(t["src"]) != t["sha"]:
+        return None, None
+    if t.get("above_l2") and (state is None or state < 4 * L2_BYTES):
         return None, None
     return t["bytes_per_node"] * nodes, t
 
@@ -541,7 +553,7 @@ def roofline_block(kind, storage, nodes, kernel_s, hbm, hbm_src, peak, traffic_k
     q = {"d3q27": 27, "d2q9": 9, "d2q5": 5, "d3q15": 15}[kind]
     bpn = 2 * ELEM[storage] * q
     gbs = bpn * nodes / kernel_s / 1e9
-    traffic, tinfo = traffic_per_launch(traffic_key or (kind, storage), nodes)
+    traffic, tinfo = traffic_per_launch(traffic_key or (kind, storage), nodes, bpn * nodes)
     r = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
          "kernel": label or f"{kind} step kernel ({nodes} nodes, {storage})",
          "peak_source": (f"measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback"),

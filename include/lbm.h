@@ -501,6 +501,23 @@ int lbm_probe_fp64(int op, int chains, int blocks, int threads, long long iters,
  * (bad sizes or NULL pointers), LBM_ECUDA; message in lbm_nn_last_error(). */
 const char *lbm_nn_last_error(void);
 
+/* Tensor cores: with BF16 weights (w_bf16 = 1), a convolution whose padded
+ * shapes fit one tile (input channels x kernel taps <= 512 and output
+ * channels <= 64 for the forward pass; output channels x taps <= 512 and
+ * input channels <= 64 for the input gradient; input channels x taps <= 512
+ * and output channels <= 64 for the weight gradient) runs as an implicit
+ * GEMM on the tensor cores (tcgen05, 128-pixel tiles): the activations and
+ * incoming gradients are rounded to BF16 as they are staged, each product is
+ * exact and the sums are FP32; the weight gradient adds per-block partial
+ * sums in a fixed order (deterministic).  Other shapes, and FP32 weights,
+ * take CUDA-core kernels with FP32 operands. */
+
+/* Status of the tensor-core kernels since the last call: *status = 1 if a
+ * kernel's wait for its tensor-core work gave up after 2 s (its outputs are
+ * then not written), else 0; the flag is cleared.  Synchronises the device.
+ * Errors: LBM_EINVAL (status NULL), LBM_ECUDA. */
+int lbm_nn_tc_status(int *status);
+
 /* y = act(conv(x, w) + b); act 0 = identity, 1 = tanh. */
 int lbm_nn_conv3d_forward(const float *x, const void *w, int w_bf16, const float *b, float *y, int n, int ci, int co,
                           const int dhw[3], const int k[3], const int dil[3], int act, void *stream);

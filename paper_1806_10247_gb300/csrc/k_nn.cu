@@ -10,9 +10,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "../../include/lbm.h"
+#include "k_nn_tc.cuh"
 
 namespace {
 
@@ -228,6 +230,305 @@ __global__ void __launch_bounds__(kT) k_to_bf16(const float *__restrict__ p, __n
     if (i < count) pb[i] = __float2bfloat16_rn(p[i]);
 }
 
+int launched(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return nn_fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+unsigned grid_of(long long count, int block) { return (unsigned)((count + block - 1) / block); }
+
+// ------------------------------------------------ tensor-core convolutions ---
+// With BF16 weights (the trained network's storage form) the convolutions run
+// as implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32
+// accumulation in tensor memory): activations and incoming gradients are
+// rounded to BF16 as they are staged, every product is exact and the sums are
+// FP32.  Tiles: kM = 128 pixels (or weight rows) by up to kMaxKp padded K
+// values and kMaxNp padded output channels; one thread stages one row.
+
+// Bit 0 set when a tensor-core wait ran out (read and cleared by lbm_nn_tc_status).
+__device__ int g_tc_status;
+
+int round16(int v) { return (v + 15) / 16 * 16; }
+
+enum TcMode { TC_FWD = 0, TC_BWD_IN = 1 };
+
+// TC_FWD:    y[n,o,p] = act(b[o] + sum_{i,tap} w[o,i,tap] x[n,i,p + shift(tap)])
+//            rows: pixels of y; K = (i, tap); N = o.
+// TC_BWD_IN: gx[n,i,p] = sum_{o,tap} w[o,i,tap] gy[n,o,p - shift(tap)]
+//            rows: pixels of x; K = (o, tap); N = i.
+template <int MODE>
+__global__ void __launch_bounds__(nntc::kM)
+k_tc_conv(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ w, const float *__restrict__ b,
+          float *__restrict__ out, Shape s, int act, int Kp, int Np)
+{
+    using namespace nntc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    unsigned char *As = smem;
+    unsigned char *Bs = smem + kM * Kp * 2;
+    const int tid = threadIdx.x;
+    const int taps = s.kd * s.kh * s.kw;
+    const int cin = MODE == TC_FWD ? s.ci : s.co;    // channels of the gathered operand
+    const int cout = MODE == TC_FWD ? s.co : s.ci;   // channels of the result
+    const int K = cin * taps;
+    const int sgn = MODE == TC_FWD ? 1 : -1;
+    const long long sp = (long long)s.d * s.h * s.w, npix = (long long)s.n * sp;
+    const long long m = (long long)blockIdx.x * kM + tid;
+    const uint32_t ncols = tmem_cols(Np);
+    if (tid < 32) tmem_alloc(smem_u32(&tmem_base), ncols);
+    if (tid == 0) mbar_init(smem_u32(&mbar));
+    const bool valid = m < npix;
+    int n_ = 0, pd = 0, ph = 0, pw = 0;
+    long long p = 0;
+    if (valid) {
+        n_ = (int)(m / sp);
+        p = m % sp;
+        pw = (int)(p % s.w);
+        ph = (int)((p / s.w) % s.h);
+        pd = (int)(p / ((long long)s.w * s.h));
+    }
+    for (int k = 0; k < Kp; k++) {
+        float v = 0.f;
+        if (valid && k < K) {
+            const int c = k / taps, tap = k - c * taps;
+            const int e = tap % s.kw, f = (tap / s.kw) % s.kh, a = tap / (s.kw * s.kh);
+            const int zd = pd + sgn * s.dd * (a - (s.kd - 1) / 2);
+            const int zh = ph + sgn * s.dh * (f - (s.kh - 1) / 2);
+            const int zw = pw + sgn * s.dw * (e - (s.kw - 1) / 2);
+            if (zd >= 0 && zd < s.d && zh >= 0 && zh < s.h && zw >= 0 && zw < s.w)
+                v = in[((long long)n_ * cin + c) * sp + ((long long)zd * s.h + zh) * s.w + zw];
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(As + core_off(tid, k, kM)) = __float2bfloat16_rn(v);
+    }
+    for (int idx = tid; idx < Np * Kp; idx += kM) {
+        const int r = idx / Kp, k = idx - r * Kp;  // r: output channel, k: (input channel, tap)
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (r < cout && k < K) {
+            const int c = k / taps, tap = k - c * taps;
+            v = MODE == TC_FWD ? w[((long long)r * s.ci + c) * taps + tap] : w[((long long)c * s.ci + r) * taps + tap];
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(Bs + core_off(r, k, Np)) = v;
+    }
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        issue_tile(tmem, smem_u32(As), smem_u32(Bs), Kp, Np, false);
+        mma_commit(smem_u32(&mbar));
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(smem_u32(&mbar), 0));
+    fence_after_sync();
+    if (ok) {
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            float v[16];
+            tmem_load16(tmem + ((uint32_t)(32 * (tid >> 5)) << 16) + (uint32_t)c0, v);
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int o = c0 + j;
+                    if (o < cout) {
+                        float r = v[j];
+                        if (MODE == TC_FWD) {
+                            r += b[o];
+                            if (act == 1) r = tanhf(r);
+                        }
+                        out[((long long)n_ * cout + o) * sp + p] = r;
+                    }
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicOr(&g_tc_status, 1);
+        mbar_wait_bounded(smem_u32(&mbar), 0);  // the MMAs end before their accumulators are freed
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid < 32) tmem_dealloc(tmem, ncols);
+}
+
+// Weight gradient, partial sums: block (g, t) accumulates, over the 128-pixel
+// chunks c = g, g + G, ..., the rows r = 128 t .. 128 t + 127 of
+// part[g][r][o] = sum_p x[n,i,p + shift(tap)] gy[n,o,p], r = i * taps + tap
+// (rows: weight entries; K: pixels; N: o).  k_tc_reduce_w adds the G partial
+// sums in a fixed order.
+__global__ void __launch_bounds__(nntc::kM)
+k_tc_conv_bwd_w(const float *__restrict__ x, const float *__restrict__ gy, float *__restrict__ part, Shape s, int G,
+                int Mp, int Np)
+{
+    using namespace nntc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    unsigned char *As = smem;
+    unsigned char *Bs = smem + kM * kM * 2;
+    const int tid = threadIdx.x;
+    const int taps = s.kd * s.kh * s.kw, Kw = s.ci * taps;
+    const long long sp = (long long)s.d * s.h * s.w, npix = (long long)s.n * sp;
+    const long long nchunks = (npix + kM - 1) / kM;
+    const int g = blockIdx.x, row0 = blockIdx.y * kM;
+    const uint32_t ncols = tmem_cols(Np);
+    if (tid < 32) tmem_alloc(smem_u32(&tmem_base), ncols);
+    if (tid == 0) mbar_init(smem_u32(&mbar));
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    bool ok = true;
+    int round = 0;
+    for (long long c = g; c < nchunks && ok; c += G, round++) {
+        // this thread stages pixel j = tid of the chunk: column j of A and of B
+        const long long q = c * kM + tid;
+        const bool valid = q < npix;
+        int n_ = 0, pd = 0, ph = 0, pw = 0;
+        long long p = 0;
+        if (valid) {
+            n_ = (int)(q / sp);
+            p = q % sp;
+            pw = (int)(p % s.w);
+            ph = (int)((p / s.w) % s.h);
+            pd = (int)(p / ((long long)s.w * s.h));
+        }
+        for (int rr = 0; rr < kM; rr++) {
+            const int r = row0 + rr;
+            float v = 0.f;
+            if (valid && r < Kw) {
+                const int i = r / taps, tap = r - i * taps;
+                const int e = tap % s.kw, f = (tap / s.kw) % s.kh, a = tap / (s.kw * s.kh);
+                const int zd = pd + s.dd * (a - (s.kd - 1) / 2);
+                const int zh = ph + s.dh * (f - (s.kh - 1) / 2);
+                const int zw = pw + s.dw * (e - (s.kw - 1) / 2);
+                if (zd >= 0 && zd < s.d && zh >= 0 && zh < s.h && zw >= 0 && zw < s.w)
+                    v = x[((long long)n_ * s.ci + i) * sp + ((long long)zd * s.h + zh) * s.w + zw];
+            }
+            *reinterpret_cast<__nv_bfloat16 *>(As + core_off(rr, tid, kM)) = __float2bfloat16_rn(v);
+        }
+        for (int o = 0; o < Np; o++) {
+            const float v = (valid && o < s.co) ? gy[((long long)n_ * s.co + o) * sp + p] : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(Bs + core_off(o, tid, Np)) = __float2bfloat16_rn(v);
+        }
+        fence_smem_to_async();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        if (tid == 0) {
+            issue_tile(tmem, smem_u32(As), smem_u32(Bs), kM, Np, round > 0);
+            mma_commit(smem_u32(&mbar));
+        }
+        // the next chunk overwrites the operands: wait for this chunk's MMAs
+        ok = __syncthreads_and(mbar_wait_bounded(smem_u32(&mbar), (uint32_t)(round & 1)));
+        fence_after_sync();
+    }
+    if (ok) {
+        const int r = row0 + tid;
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            float v[16];
+            tmem_load16(tmem + ((uint32_t)(32 * (tid >> 5)) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) part[((long long)g * Mp + r) * Np + c0 + j] = round > 0 ? v[j] : 0.f;
+        }
+    } else {
+        if (tid == 0) atomicOr(&g_tc_status, 1);
+        mbar_wait_bounded(smem_u32(&mbar), (uint32_t)((round - 1) & 1));
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid < 32) tmem_dealloc(tmem, ncols);
+}
+
+// gw[o][i][tap] = sum_{g = 0..G-1} part[g][i * taps + tap][o], in order of g.
+__global__ void __launch_bounds__(kT)
+k_tc_reduce_w(const float *__restrict__ part, float *__restrict__ gw, int co, int Kw, int G, int Mp, int Np)
+{
+    const int idx = blockIdx.x * kT + threadIdx.x;
+    if (idx >= co * Kw) return;
+    const int o = idx / Kw, r = idx - o * Kw;
+    float acc = 0.f;
+    for (int g = 0; g < G; g++) acc += part[((long long)g * Mp + r) * Np + o];
+    gw[idx] = acc;
+}
+
+// gb[o] = sum_{n,p} gy[n,o,p] (one block per channel, fixed order).
+__global__ void __launch_bounds__(kT) k_bias_grad(const float *__restrict__ gy, float *__restrict__ gb, Shape s)
+{
+    const long long sp = (long long)s.d * s.h * s.w;
+    const int o = blockIdx.x;
+    float acc = 0.0f;
+    for (long long q = threadIdx.x; q < (long long)s.n * sp; q += kT) {
+        const int n = (int)(q / sp);
+        acc += gy[((long long)n * s.co + o) * sp + q % sp];
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) gb[o] = acc;
+}
+
+// Partial-sum workspace of the weight gradient, one per device, grown on
+// demand (cudaMalloc only when a larger one is needed).
+std::mutex g_ws_mu;
+float *g_ws[64] = {};
+size_t g_ws_cap[64] = {};
+
+float *tc_workspace(size_t floats)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    if (g_ws_cap[dev] < floats) {
+        if (g_ws[dev]) cudaFree(g_ws[dev]);
+        g_ws[dev] = nullptr;
+        g_ws_cap[dev] = 0;
+        if (cudaMalloc(&g_ws[dev], floats * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_ws_cap[dev] = floats;
+    }
+    return g_ws[dev];
+}
+
+bool tc_fits(int kdim, int ndim) { return round16(kdim) <= nntc::kMaxKp && round16(ndim) <= nntc::kMaxNp; }
+
+template <int MODE>
+int tc_conv_launch(const float *in, const void *w, const float *b, float *out, const Shape &s, int act,
+                   cudaStream_t st, const char *what)
+{
+    const int taps = s.kd * s.kh * s.kw;
+    const int K = (MODE == TC_FWD ? s.ci : s.co) * taps, Np = round16(MODE == TC_FWD ? s.co : s.ci);
+    const int Kp = round16(K);
+    const size_t smem = (size_t)(nntc::kM + Np) * Kp * 2 + nntc::kSlack;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_conv<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return nn_fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    const long long npix = (long long)s.n * s.d * s.h * s.w;
+    k_tc_conv<MODE><<<(unsigned)((npix + nntc::kM - 1) / nntc::kM), nntc::kM, smem, st>>>(
+        in, reinterpret_cast<const __nv_bfloat16 *>(w), b, out, s, act, Kp, Np);
+    return launched(what);
+}
+
+int tc_conv_bwd_w_launch(const float *x, const float *gy, float *gw, const Shape &s, cudaStream_t st)
+{
+    const int taps = s.kd * s.kh * s.kw, Kw = s.ci * taps;
+    const int Mp = (Kw + nntc::kM - 1) / nntc::kM * nntc::kM, Np = round16(s.co);
+    const long long npix = (long long)s.n * s.d * s.h * s.w;
+    const long long nchunks = (npix + nntc::kM - 1) / nntc::kM;
+    const int G = (int)(nchunks < 128 ? nchunks : 128);
+    float *part = tc_workspace((size_t)G * Mp * Np);
+    if (!part) return nn_fail(LBM_ENOMEM, "conv3d_backward: tensor-core workspace");
+    const size_t smem = (size_t)(nntc::kM + Np) * nntc::kM * 2 + nntc::kSlack;
+    cudaError_t e = cudaFuncSetAttribute(k_tc_conv_bwd_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return nn_fail(LBM_ECUDA, "conv3d_backward(weights): %s", cudaGetErrorString(e));
+    k_tc_conv_bwd_w<<<dim3((unsigned)G, (unsigned)(Mp / nntc::kM)), nntc::kM, smem, st>>>(x, gy, part, s, G, Mp, Np);
+    int rc = launched("conv3d_backward(weights)");
+    if (rc != LBM_OK) return rc;
+    k_tc_reduce_w<<<grid_of((long long)s.co * Kw, kT), kT, 0, st>>>(part, gw, s.co, Kw, G, Mp, Np);
+    return launched("conv3d_backward(weight reduction)");
+}
+
 int check_shape(const int *sp, const int *k, const int *dil, int n, int ci, int co, Shape &s)
 {
     if (!sp || !k || !dil) return nn_fail(LBM_EINVAL, "shape, kernel and dilation are required");
@@ -242,20 +543,22 @@ int check_shape(const int *sp, const int *k, const int *dil, int n, int ci, int 
     return LBM_OK;
 }
 
-int launched(const char *what)
-{
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return nn_fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-    return LBM_OK;
-}
-
-unsigned grid_of(long long count, int block) { return (unsigned)((count + block - 1) / block); }
-
 }  // namespace
 
 extern "C" {
 
 const char *lbm_nn_last_error(void) { return g_nn_error.c_str(); }
+
+int lbm_nn_tc_status(int *status)
+{
+    if (!status) return nn_fail(LBM_EINVAL, "tc_status: status is NULL");
+    int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_status, sizeof v);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof zero);
+    if (e != cudaSuccess) return nn_fail(LBM_ECUDA, "tc_status: %s", cudaGetErrorString(e));
+    *status = v;
+    return LBM_OK;
+}
 
 int lbm_nn_conv3d_forward(const float *x, const void *w, int w_bf16, const float *b, float *y, int n, int ci, int co,
                           const int dhw[3], const int k[3], const int dil[3], int act, void *stream)
@@ -265,6 +568,8 @@ int lbm_nn_conv3d_forward(const float *x, const void *w, int w_bf16, const float
     if (rc != LBM_OK) return rc;
     if (!x || !w || !b || !y) return nn_fail(LBM_EINVAL, "conv3d_forward: NULL pointer");
     if (act != 0 && act != 1) return nn_fail(LBM_EINVAL, "conv3d_forward: act must be 0 or 1");
+    if (w_bf16 && tc_fits(ci * s.kd * s.kh * s.kw, co))
+        return tc_conv_launch<TC_FWD>(x, w, b, y, s, act, (cudaStream_t)stream, "conv3d_forward");
     k_conv_fwd<<<grid_of(s.out_count(), kT), kT, 0, (cudaStream_t)stream>>>(x, w, w_bf16, b, y, s, act);
     return launched("conv3d_forward");
 }
@@ -277,12 +582,23 @@ int lbm_nn_conv3d_backward(const float *x, const void *w, int w_bf16, const floa
     if (rc != LBM_OK) return rc;
     if (!x || !w || !gy || !gw || !gb) return nn_fail(LBM_EINVAL, "conv3d_backward: NULL pointer");
     cudaStream_t st = (cudaStream_t)stream;
+    const int taps = s.kd * s.kh * s.kw;
     if (gx) {
-        k_conv_bwd_in<<<grid_of(s.in_count(), kT), kT, 0, st>>>(gy, w, w_bf16, gx, s);
-        rc = launched("conv3d_backward(input)");
+        if (w_bf16 && tc_fits(co * taps, ci)) {
+            rc = tc_conv_launch<TC_BWD_IN>(gy, w, nullptr, gx, s, 0, st, "conv3d_backward(input)");
+        } else {
+            k_conv_bwd_in<<<grid_of(s.in_count(), kT), kT, 0, st>>>(gy, w, w_bf16, gx, s);
+            rc = launched("conv3d_backward(input)");
+        }
         if (rc != LBM_OK) return rc;
     }
-    const long long blocks = (long long)co * ci * s.kd * s.kh * s.kw + co;
+    if (w_bf16 && ci * taps <= nntc::kMaxKp && round16(co) <= nntc::kMaxNp) {
+        rc = tc_conv_bwd_w_launch(x, gy, gw, s, st);
+        if (rc != LBM_OK) return rc;
+        k_bias_grad<<<(unsigned)co, kT, 0, st>>>(gy, gb, s);
+        return launched("conv3d_backward(bias)");
+    }
+    const long long blocks = (long long)co * ci * taps + co;
     k_conv_bwd_w<<<(unsigned)blocks, kT, 0, st>>>(x, gy, gw, gb, s);
     return launched("conv3d_backward(weights)");
 }
