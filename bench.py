@@ -85,16 +85,16 @@ TRAFFIC = {
     ("d3q27", "fp64"): {"src": [_C + "k_d3q27.cu"] + _H, "sha": "4be8a09ad4918a7a",
                         "bytes_per_node": (1529.134848 + 1477.492224) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md"},
-    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "6d77d00afbdc12a5",
-                        "bytes_per_node": (1812.060928 + 1757.052160) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
+    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
+                        "bytes_per_node": (1812.015104 + 1757.000448) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
                         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md"},
     ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
                              "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,
                              "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md"},
-    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "ca473d3af7e9177b", "above_l2": True,
-                        "bytes_per_node": (382.279680 + 334.776576) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
+                        "bytes_per_node": (382.271488 + 334.486272) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/k_step27x2_kolmogorov_fp16_pair.md"},
-    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "ca473d3af7e9177b", "above_l2": True,
+    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
                        "bytes_per_node": (1208.092160 + 1154.119680) * 1e6 / (8192 * 4096),
                        "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9_channel8192_fp32.md"},
     ("d2q9", "fp64"): {"src": [_C + "k_d2q9.cu"] + _H, "sha": "018f6162beb1528d",

@@ -552,7 +552,8 @@ __device__ __forceinline__ void along(V (&m)[27], Op op)
 // deviations: back-shift, post-collision force in moment space (K_1 g_1 with
 // g = (F_pre + F_post) / 36; m_100 already carries F_pre / 2), inverse raw
 // transform.
-template <class V>
+// XO: the force has no y and z components (their terms, additions of 0, are left out).
+template <class V, bool XO = false>
 __device__ __forceinline__ void finish27(V (&m)[27], V ux, V uy, V uz, const V (&F)[3], const V (&Fq)[3])
 {
     const V hx = V(0.5f) * ux, hy = V(0.5f) * uy, hz = V(0.5f) * uz;
@@ -561,14 +562,17 @@ __device__ __forceinline__ void finish27(V (&m)[27], V ux, V uy, V uz, const V (
     along<2>(m, [uz, hz](V &a, V &b, V &c) { shift_bwd_h(a, b, c, uz, hz); });
 
     {
-        const V sx = F[0] + Fq[0], sy = F[1] + Fq[1], sz = F[2] + Fq[2];
         const V c4 = V(0.25f), c12 = V(1.0f / 12.0f), c36 = V(1.0f / 36.0f);
+        const V sx = F[0] + Fq[0];
         m[1] = vfma(c4, Fq[0], m[1]);
-        m[3] = vfma(c4, Fq[1], m[3]);
-        m[9] = vfma(c4, Fq[2], m[9]);
         m[7] = vfma(sx, c12, m[7]); m[19] = vfma(sx, c12, m[19]); m[25] = vfma(sx, c36, m[25]);
-        m[5] = vfma(sy, c12, m[5]); m[21] = vfma(sy, c12, m[21]); m[23] = vfma(sy, c36, m[23]);
-        m[11] = vfma(sz, c12, m[11]); m[15] = vfma(sz, c12, m[15]); m[17] = vfma(sz, c36, m[17]);
+        if constexpr (!XO) {
+            const V sy = F[1] + Fq[1], sz = F[2] + Fq[2];
+            m[3] = vfma(c4, Fq[1], m[3]);
+            m[9] = vfma(c4, Fq[2], m[9]);
+            m[5] = vfma(sy, c12, m[5]); m[21] = vfma(sy, c12, m[21]); m[23] = vfma(sy, c36, m[23]);
+            m[11] = vfma(sz, c12, m[11]); m[15] = vfma(sz, c12, m[15]); m[17] = vfma(sz, c36, m[17]);
+        }
     }
 
     along<2>(m, [](V &a, V &b, V &c) { raw_bwd_h(a, b, c); });
@@ -679,7 +683,7 @@ __device__ __forceinline__ void collide27(float (&m)[27], float rref, const floa
 // moments of order <= 2 are formed and the forward shift reduces to the
 // first- and second-order central moments.  V = float (one node) or f2 (two
 // nodes, packed); rref is the launch's reference density.
-template <class V>
+template <class V, bool XO = false>
 __device__ __forceinline__ void collide27_w1(V (&m)[27], float rref, const V (&F)[3], const V (&Fq)[3],
                                              const Rates27f &w)
 {
@@ -697,9 +701,9 @@ __device__ __forceinline__ void collide27_w1(V (&m)[27], float rref, const V (&F
     }
     const V half = V(0.5f);
     const V drho = (Y0[2] + Y0[0]) + Y0[1];
-    const V jz = vfma(half, F[2], Y0[2] - Y0[0]);
+    const V jz = XO ? Y0[2] - Y0[0] : vfma(half, F[2], Y0[2] - Y0[0]);
     const V kzz = Y0[2] + Y0[0];
-    const V jy = vfma(half, F[1], (Y1[2] + Y1[0]) + Y1[1]);
+    const V jy = XO ? (Y1[2] + Y1[0]) + Y1[1] : vfma(half, F[1], (Y1[2] + Y1[0]) + Y1[1]);
     const V kyz = Y1[2] - Y1[0];
     const V kyy = (Y2[2] + Y2[0]) + Y2[1];
     const V jx = vfma(half, F[0], (X0[2] + X0[0]) + X0[1]);
@@ -748,7 +752,7 @@ __device__ __forceinline__ void collide27_w1(V (&m)[27], float rref, const V (&F
     m[4] = vfma(nwq, ux * uy, rq * cxy);
     m[10] = vfma(nwq, ux * uz, rq * cxz);
     m[12] = vfma(nwq, uy * uz, rq * cyz);
-    finish27(m, ux, uy, uz, F, Fq);
+    finish27<V, XO>(m, ux, uy, uz, F, Fq);
 }
 
 // 4 resident blocks per SM (<= 64 registers): the reduced-precision D3Q27
@@ -864,7 +868,8 @@ constexpr int kBlockPair = 128;
 #define LBM_PAIR_MIN_BLOCKS 6
 #endif
 
-template <class T, int FK, bool SR = false>
+// XO: the force acts along x only (checked on the host).
+template <class T, int FK, bool SR = false, bool XO = false>
 __global__ void __launch_bounds__(kBlockPair, LBM_PAIR_MIN_BLOCKS)
 k_step27x2(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apre, float apost, Rates27f w,
            float rref, unsigned long long srkey)
@@ -879,13 +884,13 @@ k_step27x2(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float a
     f2 F[3] = {f2(0.f), f2(0.f), f2(0.f)}, Fq[3] = {f2(0.f), f2(0.f), f2(0.f)};
     if (FK != FK_NONE) {
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
+        for (int d = 0; d < (XO ? 1 : 3); d++) {
             const f2 Pd(field_value_f(Fd, FK, d, x, y, z, i0), field_value_f(Fd, FK, d, x + 1, y, z, i0 + 1));
             F[d] = f2(apre) * Pd;
             Fq[d] = f2(apost) * Pd;
         }
     }
-    collide27_w1(m, rref, F, Fq, w);
+    collide27_w1<f2, XO>(m, rref, F, Fq, w);
     if constexpr (SR) {
         SRBits r0(srkey, i0), r1(srkey, i0 + 1);
 #pragma unroll
@@ -1102,7 +1107,10 @@ void step27_launch(const Planes<T, 27> &fin, const LaunchArgs &a, float ap, floa
         if (w1 && a.g.nx % 2 == 0) {
             // two x-neighbouring nodes per thread, packed FP32x2 arithmetic
             const int pgrid = (a.g.N / 2 + kBlockPair - 1) / kBlockPair;
-            k_step27x2<T, FK, SR><<<pgrid, kBlockPair, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
+            if (FK != FK_NONE && force_x_only(FK, a.F, 3))
+                k_step27x2<T, FK, SR, true><<<pgrid, kBlockPair, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
+            else
+                k_step27x2<T, FK, SR, false><<<pgrid, kBlockPair, 0, s>>>(fin, a.g, a.F, ap, aq, w, rref, a.srkey);
             return;
         }
     }
