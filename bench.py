@@ -498,13 +498,16 @@ def fp64_peak(lbm, stream, info):
     independent dependency chains of one operation (8 or 16 per thread, the
     loop unrolled four times), 4 or 8 blocks of 256 threads per SM, CUDA
     events, best of 3 after a warm-up launch; the peak of each operation is
-    the fastest configuration."""
+    the fastest configuration.  Block 0 of every probe launch also reports its
+    own SM cycles and nanoseconds, which give the SM clock the rates were
+    taken at (the cycles of one block are not the launch's: blocks beyond the
+    resident ones run in later waves)."""
     import torch
 
-    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sink = torch.zeros(3, dtype=torch.float64, device="cuda")
     sms = int(info["sm_count"])
     threads = 256
-    rates, tried = {}, {}
+    rates, tried, mhz_seen = {}, {}, []
     for op, name in ((lbm.FP64_FMA, "fma"), (lbm.FP64_ADD, "add"), (lbm.FP64_MUL, "mul")):
         best_rate = 0.0
         for chains in (8, 16):
@@ -521,19 +524,24 @@ def fp64_peak(lbm, stream, info):
                     e1.record(stream)
                     e1.synchronize()
                     best = min(best, e0.elapsed_time(e1) * 1e-3)
+                    cyc, ns = (float(v) for v in sink[:2].cpu())
+                    if ns > 0:
+                        mhz_seen.append(cyc / ns * 1e3)
                 r = n / best / 1e9
                 tried[f"{name}_chains{chains}_blocks{per_sm}xSM"] = r
                 best_rate = max(best_rate, r)
         rates[name] = best_rate
-    ghz = info["sm_max_khz"] / 1e6
+    mhz = float(np.median(mhz_seen)) if mhz_seen else info["sm_max_khz"] / 1e3
     return {
         "fma_ginst_per_s": rates["fma"], "add_ginst_per_s": rates["add"], "mul_ginst_per_s": rates["mul"],
         "tflops_fma": 2 * rates["fma"] / 1e3,
-        "per_clock_per_sm_at_max_clock": {k: v / (sms * ghz) for k, v in rates.items()},
+        "per_clock_per_sm": {k: v * 1e3 / (sms * mhz) for k, v in rates.items()},
+        "probe_sm_mhz": mhz, "probe_sm_mhz_range": [min(mhz_seen), max(mhz_seen)] if mhz_seen else None,
         "sm_count": sms, "sm_max_mhz": info["sm_max_khz"] / 1e3, "all_configurations_ginst_per_s": tried,
-        "how": f"lbm_probe_fp64: 8 or 16 independent chains of one FP64 operation per thread (operands from "
-               f"kernel arguments, loop unrolled 4x), 4 or 8 blocks of {threads} threads per SM, CUDA events, best "
-               "of 3 after a warm-up launch; the fastest configuration per operation",
+        "how": f"lbm_probe_fp64: 8 or 16 independent chains of one FP64 operation per thread (second and third "
+               f"operands in constant memory, loop unrolled 4x), 4 or 8 blocks of {threads} threads per SM, CUDA "
+               "events, best of 3 after a warm-up launch, the fastest configuration per operation; the SM clock "
+               "from block 0's own cycles and nanoseconds (median over the probe launches)",
     }
 
 
@@ -570,7 +578,8 @@ def roofline_block(kind, storage, nodes, kernel_s, hbm, hbm_src, peak, traffic_k
         if gops / pk > r["frac"]:
             r.update({"bound": "alu", "achieved": gops, "peak": pk, "unit": "G FP64 op/s", "frac": gops / pk,
                       "peak_source": "measured in this run (lbm_probe_fp64): the FMA and add/multiply rates of the "
-                                     "FP64 unit weighted by this formulation's mix",
+                                     "FP64 unit weighted by this formulation's mix (SM clock during the probe "
+                                     f"{peak['probe_sm_mhz']:.0f} MHz)",
                       "ops_per_node": alg["ops"], "fma_per_node": alg["fma"], "formulation": alg["form"],
                       "hbm": hbm_part})
         r["flops"] = {"achieved": tf, "peak": peak["tflops_fma"], "unit": "TFLOP/s", "frac": tf / peak["tflops_fma"],

@@ -43,6 +43,9 @@ extern "C" {
 
 #define LBM_ABI_VERSION 2
 
+/* Largest lattice of one context: 2^31 - 2^16 nodes (e.g. 65536 x 32767). */
+#define LBM_MAX_NODES 2147418112LL
+
 typedef struct lbm_ctx lbm_ctx;
 
 /* Lattices. */
@@ -138,8 +141,12 @@ typedef double (*lbm_envelope_fn)(double t, void *user);
  * 2 bytes each by `storage`) on the current CUDA device (N = nx*ny*nz; nz must
  * be 1 for the 2D lattices).
  * `stream` is a cudaStream_t (NULL = legacy default stream).
- * Errors: LBM_EINVAL (unknown lattice or storage, extent < 1, omega outside
- * (0,2), bad boundary kind), LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
+ * At most LBM_MAX_NODES nodes: node indices are 32-bit in the kernels, and
+ * this bound keeps every thread's index, rounded up to a whole block, below
+ * 2^31 (component offsets of [dim][N] and [q][N] arrays are 64-bit).
+ * Errors: LBM_EINVAL (unknown lattice or storage, extent < 1, more than
+ * LBM_MAX_NODES nodes, omega outside (0,2), bad boundary kind), LBM_ENOMEM,
+ * LBM_ECUDA.  *out is NULL on error. */
 int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_relax *relax,
                const lbm_boundary *bc, int storage, void *stream);
 
@@ -480,9 +487,13 @@ int lbm_device_info(int device, long long info[8]);
  * `threads` threads, each running `chains` (8 or 16) independent dependency
  * chains of `iters` FP64 operations of one kind: op 0 fused multiply-add,
  * 1 add, 2 multiply.  It issues exactly blocks * threads * iters * chains
- * FP64 instructions and reads or writes no memory except, never in practice,
- * sink[0] (one device double, which the caller owns).  The caller times it
- * (e.g. CUDA events on the stream).  Nothing synchronises.
+ * FP64 instructions.  sink (three device doubles, owned by the caller)
+ * receives sink[0] = the SM clock cycles and sink[1] = the nanoseconds of
+ * block 0's run: its SM clock in MHz is sink[0] / sink[1] * 1000 (the run
+ * of one block is not the launch's when more blocks are launched than the
+ * GPU holds resident).  sink[2] is never written in practice.  The caller
+ * times the launch (e.g. CUDA events on the stream) for the rate.  Nothing
+ * synchronises.
  * Errors: LBM_EINVAL (op outside 0..2, chains not 8 or 16, blocks < 1,
  * threads not a multiple of 32 in [32, 1024], iters < 1, sink NULL),
  * LBM_ECUDA (launch failure). */

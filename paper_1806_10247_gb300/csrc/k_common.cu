@@ -47,8 +47,8 @@ k_equilibrium(Geom g, double rho0, double u0x, double u0y, double u0z, const dou
     if (i >= g.N) return;
     double r = rho ? rho[i] : rho0;
     double ux = u ? u[i] : u0x;
-    double uy = u ? u[g.N + i] : u0y;
-    double uz = (u && L::DIM == 3) ? u[2 * g.N + i] : u0z;
+    double uy = u ? u[(long long)g.N + i] : u0y;
+    double uz = (u && L::DIM == 3) ? u[2LL * g.N + i] : u0z;
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         double v;
@@ -166,7 +166,8 @@ k_reduce_partial(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, 
                  double *__restrict__ snap, int have_snap, double *__restrict__ partials)
 {
     double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+    for (long long n = blockIdx.x * (long long)kBlock + threadIdx.x; n < g.N; n += (long long)gridDim.x * kBlock) {
+        const int i = (int)n;
         int x, y, z;
         node_xyz(g, i, x, y, z);
         double f[L::Q];
@@ -186,8 +187,8 @@ k_reduce_partial(Geom g, const double *__restrict__ fin, int fkind, FieldDev F, 
                 double jd = fkind != FK_NONE ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
                 double ud = jd / m0;
                 bad = bad || !isfinite(ud);
-                if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[d * g.N + i]));
-                snap[d * g.N + i] = ud;
+                if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[(long long)d * g.N + i]));
+                snap[(long long)d * g.N + i] = ud;
             }
         }
         if (bad) v[R_BAD] = 1.0;
@@ -202,7 +203,8 @@ __global__ void __launch_bounds__(kBlock)
 k_reduce_partial_sums(Geom g, const double *__restrict__ fin, double *__restrict__ partials)
 {
     double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+    for (long long n = blockIdx.x * (long long)kBlock + threadIdx.x; n < g.N; n += (long long)gridDim.x * kBlock) {
+        const int i = (int)n;
         int x, y, z;
         node_xyz(g, i, x, y, z);
         double f[L::Q];
@@ -225,7 +227,8 @@ k_reduce_partial_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind
                     double *__restrict__ snap, int have_snap, int with_snap, double *__restrict__ partials)
 {
     double v[R_SLOTS] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = blockIdx.x * kBlock + threadIdx.x; i < g.N; i += gridDim.x * kBlock) {
+    for (long long n = blockIdx.x * (long long)kBlock + threadIdx.x; n < g.N; n += (long long)gridDim.x * kBlock) {
+        const int i = (int)n;
         int x, y, z;
         node_xyz(g, i, x, y, z);
         double dm0, j[3];
@@ -247,8 +250,8 @@ k_reduce_partial_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind
                     double jd = fkind != FK_NONE ? j[d] + 0.5 * (apre * field_value(F, fkind, d, x, y, z, i)) : j[d];
                     double ud = jd / m0;
                     bad = bad || !isfinite(ud);
-                    if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[d * g.N + i]));
-                    snap[d * g.N + i] = ud;
+                    if (have_snap) v[R_DU] = fmax(v[R_DU], fabs(ud - snap[(long long)d * g.N + i]));
+                    snap[(long long)d * g.N + i] = ud;
                 }
             }
         }
@@ -305,8 +308,8 @@ k_init_rp(Geom g, double rho_ref, Ref5 R, double rho0, double u0x, double u0y, d
     node_xyz(g, i, x, y, z);
     double r = rho ? rho[i] : rho0;
     double ux = u ? u[i] : u0x;
-    double uy = u ? u[g.N + i] : u0y;
-    double uz = (u && L::DIM == 3) ? u[2 * g.N + i] : u0z;
+    double uy = u ? u[(long long)g.N + i] : u0y;
+    double uz = (u && L::DIM == 3) ? u[2LL * g.N + i] : u0z;
 #pragma unroll
     for (int a = 0; a < L::Q; a++) {
         double v;
@@ -389,7 +392,7 @@ struct StrainRates {
 
 template <class L>
 __device__ __forceinline__ void strain_node(const double (&f)[L::Q], const double (&Fh)[3], double rho0,
-                                            const StrainRates &r, double *__restrict__ out, int N, int i)
+                                            const StrainRates &r, double *__restrict__ out, long long N, int i)
 {
     double rho = 0.0, j[3] = {0.0, 0.0, 0.0}, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -469,11 +472,12 @@ k_strain_rp(Geom g, const T *__restrict__ fin, double rho_ref, int fkind, FieldD
 // Viscous heating source coef * S:S (Sec. 6.6, S_r = (2 nu / C_v) S:S) from the
 // strain components; written as a full source field (FP64 and FP32 copy).
 __global__ void __launch_bounds__(kBlock)
-k_viscous_source(int N, int dim, const double *__restrict__ S, double coef, double *__restrict__ out,
+k_viscous_source(int n, int dim, const double *__restrict__ S, double coef, double *__restrict__ out,
                  float *__restrict__ fout)
 {
-    int i = blockIdx.x * kBlock + threadIdx.x;
-    if (i >= N) return;
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= n) return;
+    const long long N = n;  // component stride: 64-bit offsets
     double v;
     if (dim == 2) {
         const double a = S[i], b = S[N + i], c = S[2 * N + i];

@@ -341,7 +341,7 @@ int lbm_create(lbm_ctx **out, int lattice, int nx, int ny, int nz, const lbm_rel
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: extents must be >= 1");
     if (lattice_dim(lattice) == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nz must be 1 for a 2D lattice");
     const long long N = (long long)nx * ny * nz;
-    if (N > 2147483647LL) return fail(nullptr, LBM_EINVAL, "lbm_create: more than 2^31-1 nodes");
+    if (N > LBM_MAX_NODES) return fail(nullptr, LBM_EINVAL, "lbm_create: %lld nodes, more than LBM_MAX_NODES", N);
     if (relax == nullptr) return fail(nullptr, LBM_EINVAL, "lbm_create: relax is NULL");
     for (int k = 0; k < 9; k++)
         if (omega_used(lattice, k) && !(relax->omega[k] > 0.0 && relax->omega[k] < 2.0))

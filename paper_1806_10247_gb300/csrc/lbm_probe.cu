@@ -36,6 +36,13 @@ __constant__ double c_a = 1.0 - 1e-9, c_b = 1e-9;
 template <int OP, int kChains>
 __global__ void k_fp64_rate(long long iters, double *sink)
 {
+    // block 0 times its own run in SM cycles and in nanoseconds: the ratio is
+    // the SM clock the probe ran at (the rate itself is timed by the caller)
+    long long c0 = 0, t0 = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c0 = clock64();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    }
     double x[kChains];
 #pragma unroll
     for (int k = 0; k < kChains; k++) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
@@ -51,8 +58,14 @@ __global__ void k_fp64_rate(long long iters, double *sink)
     double s = 0.0;
 #pragma unroll
     for (int k = 0; k < kChains; k++) s += x[k];
-    // Never true for the operands the host passes; keeps the chains live.
-    if (s == -1.0) sink[0] = s;
+    // Never true for these operands; keeps the chains live.
+    if (s == -1.0) sink[2] = s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        sink[0] = (double)(clock64() - c0);
+        sink[1] = (double)(t1 - t0);
+    }
 }
 
 template <int CH>

@@ -23,6 +23,7 @@ FP64, FP32_DEV, FP16_DEV, BF16_DEV = 0, 1, 2, 3
 PERIODIC, BOUNCE_BACK = 0, 1
 FIELD_NONE, FIELD_SEPARABLE, FIELD_FULL, FIELD_FULL_DEVICE = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ESTATE = 0, -1, -2, -3, -4, -6
+MAX_NODES = 2 ** 31 - 2 ** 16  # LBM_MAX_NODES: largest lattice of one context
 Q = {D2Q9: 9, D3Q27: 27, D2Q5_CDE: 5, D3Q15: 15}
 DIM = {D2Q9: 2, D3Q27: 3, D2Q5_CDE: 2, D3Q15: 3}
 
@@ -558,7 +559,8 @@ FP64_FMA, FP64_ADD, FP64_MUL = 0, 1, 2
 def probe_fp64(op, blocks, threads, iters, sink_ptr, stream=None, chains=8):
     """Queue the FP64 throughput probe (lbm_probe_fp64): blocks * threads *
     iters * chains FP64 instructions of kind op; sink_ptr is the address of
-    one device double.  Asynchronous on `stream`; returns the count."""
+    three device doubles (block 0's SM cycles and nanoseconds land in the
+    first two).  Asynchronous on `stream`; returns the count."""
     L = load()
     s = None if stream is None else ctypes.c_void_p(int(stream))
     rc = L.lbm_probe_fp64(int(op), int(chains), int(blocks), int(threads), int(iters),

@@ -62,9 +62,16 @@ def test_create_fails_cleanly_without_gpu_or_on_bad_args():
     assert rc == lbm.EINVAL
     rc = L.lbm_create(ctypes.byref(h), lbm.D2Q9, 4, 4, 1, ctypes.byref(r), None, 7, None)
     assert rc == lbm.EINVAL and b"storage" in L.lbm_last_error(None)
-    # node count beyond the 32-bit index range of the kernels
+    # node counts beyond the 32-bit index range of the kernels, and between
+    # LBM_MAX_NODES = 2^31 - 2^16 and 2^31 - 1 (a last block's thread indices
+    # would pass 2^31)
     rc = L.lbm_create(ctypes.byref(h), lbm.D3Q27, 2048, 1024, 1025, ctypes.byref(r), None, 0, None)
-    assert rc == lbm.EINVAL and b"2^31-1" in L.lbm_last_error(None)
+    assert rc == lbm.EINVAL and b"LBM_MAX_NODES" in L.lbm_last_error(None)
+    hdr = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    assert f"#define LBM_MAX_NODES {lbm.MAX_NODES}LL" in hdr
+    assert 65537 * 32767 > lbm.MAX_NODES and 65537 * 32767 < 2 ** 31 - 1
+    rc = L.lbm_create(ctypes.byref(h), lbm.D2Q5_CDE, 65537, 32767, 1, ctypes.byref(r), None, lbm.FP32_DEV, None)
+    assert rc == lbm.EINVAL and b"LBM_MAX_NODES" in L.lbm_last_error(None)
     # D3Q15 stores FP64 only; walls on z for a 2D lattice; unknown boundary kind
     rc = L.lbm_create(ctypes.byref(h), lbm.D3Q15, 4, 4, 4, ctypes.byref(r), None, lbm.FP32_DEV, None)
     assert rc == lbm.EINVAL and b"D3Q15" in L.lbm_last_error(None)

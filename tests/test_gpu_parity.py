@@ -276,7 +276,10 @@ def _one_step_sampled(w, G, samples, seed, tol=1e-12, device=False):
     nx, ny, nz = w.shape
     opp = [int(np.where((E == -E[a]).all(1))[0][0]) for a in range(q)]
     rng = np.random.default_rng(seed)
-    idx = rng.integers(0, w.nodes, samples)
+    nxy = nx * ny
+    edges = np.array([0, w.nodes - 1, nx - 1, w.nodes - nx, nx * (ny // 2)], dtype=np.int64)
+    idx = np.concatenate([edges[edges < w.nodes], rng.integers(0, w.nodes, samples)])
+    samples = len(idx)
     # pull source (node, component) of every sampled node and population
     src = np.empty((samples, q), dtype=np.int64)
     comp = np.empty((samples, q), dtype=np.int64)
@@ -304,11 +307,13 @@ def _one_step_sampled(w, G, samples, seed, tol=1e-12, device=False):
         buf = torch.empty((q, w.nodes), dtype=torch.float64, device="cuda")
         sel = torch.from_numpy(need).to("cuda")
         G.get_populations(out=buf, where=1)
+        G.sync()
         ft = buf[:, sel].cpu().numpy()
         G.step(1)
         G.get_populations(out=buf, where=1)
+        G.sync()
         ft1 = buf[:, sel].cpu().numpy()
-        scale = float(buf.abs().max().item())
+        scale = max(float(buf.max().item()), -float(buf.min().item()))  # no |f| temporary
         del buf
         torch.cuda.empty_cache()
     else:

@@ -348,3 +348,31 @@ def test_d2q5_reference_rebased_for_a_velocity_field(form):
     err = _l2(G.moments() - 1.0, R.moments() - 1.0)
     _record(f"d2q5_rebased_velocity_field_{form}", err)
     assert err <= (1e-5 if form == "fp32" else 3e-2), err
+
+
+def test_maximum_node_count_d2q5_fp32():
+    """The largest lattice a context takes (N = 65536 x 32767 = LBM_MAX_NODES
+    = 2^31 - 2^16, so that 32-bit thread indices of every launch stay below
+    2^31 and [q][N] offsets need 64 bits): a periodic D2Q5 scalar lattice
+    with a uniform advecting velocity and a separable source, FP32 deviation
+    storage (86 GB of populations).  One step, checked on sampled nodes -- the
+    first and last nodes and both x edges among them -- by the oracle's
+    collision of the GPU's f(t), streamed in; plus exact scalar accounting."""
+    from tests.test_gpu_parity import _one_step_sampled
+
+    nx, ny = 65536, 32767
+    one = np.array([1.0])
+    x, y = np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64)
+    w = W.Workload(name="max_d2q5", lattice=W.D2Q5, shape=(nx, ny, 1), wall=(0, 0, 0),
+                   omega=W.d2q5_omega(0.9), rho0=1.0, u0=(0.01, -0.02, 0.0),
+                   tables=[(1e-3 * np.sin(2 * math.pi * x / nx), np.cos(2 * math.pi * y / ny), one)])
+    assert w.nodes == lbm.MAX_NODES
+    G = lbm.from_workload(w, storage=lbm.FP32_DEV)
+    r0 = G.reduce()
+    G.step(2)
+    r1 = G.reduce()
+    # the source sums to ~0 over the lattice: the total scalar changes only by rounding
+    assert abs(r1[0] - r0[0]) <= 1e-6 * r0[0]
+    worst = _one_step_sampled(w, G, samples=64, seed=17, tol=2e-6, device=True)
+    _record("max_nodes_d2q5_fp32_one_step_sampled_rel_max", worst)
+    G.close()
