@@ -149,6 +149,9 @@ WORKLOADS = {
     "kolmogorov192": ("kolmogorov_d3q27_192cubed", lambda: [W.kolmogorov(n=192)], None),
     "channel2048": ("channel_d2q9_2048x1024", lambda: [W.poiseuille(ny=1024, nx=2048)], None),
     "channel8192": ("channel_d2q9_8192x4096", lambda: [W.poiseuille(ny=4096, nx=8192)], None),
+    # the scalar sweep's manufactured-source problem on one 8192^2 grid (a
+    # state many times L2), for the D2Q5 kernels' throughput
+    "cde8192": ("cde_d2q5_8192x8192", lambda: [W.cde_workload(W.cde_sweep_params(sizes=(8192,))[0])], None),
     "batched_sweep": ("batched_sweep_2048_d2q9_channels_2048_d2q5_scalars", batched_sweep_workloads, None),
     "duct15_128": ("duct_d3q15_128x128x128", lambda: [W.duct15(n=128, nx=128)], None),
     # smaller forms of the workloads above, for profiler captures
@@ -1062,7 +1065,8 @@ def extras(lbm, stream, hbm, hbm_src, peak):
     wk = {}
     plan = [("kolmogorov256", "fp64", 20, {}), ("kolmogorov256", "fp32", 20, {}),
             ("channel2048", "fp64", 50, {}), ("channel2048", "fp32", 50, {}),
-            ("channel8192", "fp32", 20, {}),
+            ("channel8192", "fp32", 20, {}), ("channel8192", "fp16", 20, {}), ("channel8192", "bf16", 20, {}),
+            ("cde8192", "fp64", 20, {}), ("cde8192", "fp32", 20, {}), ("cde8192", "fp16", 20, {}),
             ("cde_sweep", "fp64", 100, {}), ("cde_sweep", "fp32", 100, {}),
             ("batched_sweep", "fp32", 20, {"graph": 10, "tune": True})]
     for name, st, steps, kw in plan:

@@ -593,6 +593,7 @@ int orc_collide_node(const orc_params *p, const double *fin, const double *Fpre,
         return 0;
     }
     if (p->lattice == ORC_D2Q5) {
+        if (!uadv) return -1; /* the scalar's collision needs the advecting velocity */
         collide_d2q5_paper(p->omega, p->as_printed, fin, Fpre[0], Fpost[0], uadv[0], uadv[1], fout);
         return 0;
     }

@@ -265,6 +265,8 @@ class OracleLattice:
             rc = lib().orc_collide_node_generic(ctypes.byref(self.params), _dp(fin), _dp(Fpre),
                                                 _dp(Fpost), _dp(out))
         else:
+            if self.lattice == D2Q5 and uadv is None:
+                raise ValueError("collide_node: the D2Q5 collision needs the advecting velocity uadv")
             ua = None if uadv is None else np.ascontiguousarray(uadv, np.float64)
             rc = lib().orc_collide_node(ctypes.byref(self.params), _dp(fin), _dp(Fpre),
                                         _dp(Fpost), _dp(ua), _dp(out))

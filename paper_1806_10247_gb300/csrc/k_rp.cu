@@ -17,6 +17,29 @@ namespace {
 
 constexpr int kBlock = 256;
 
+// Two nodes' values in one register pair: every operation on them is one
+// packed FP32 instruction (add / multiply / fused multiply-add on f32x2, sm_100
+// and later), each half rounded exactly as the scalar operation would be.  The
+// 16-bit steps at unit higher rates run two x-neighbouring nodes per thread in
+// this form (D3Q27: fewer instructions per node; D2Q9 / D2Q5: twice the bytes
+// of loads in flight per thread).
+struct f2 {
+    float2 v;
+    __device__ __forceinline__ f2() {}
+    __device__ __forceinline__ f2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+// a - b as a + b * (-1): exact negation, one rounding, one instruction
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ f2 vrcp(f2 a) { return f2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+
 // ------------------------------------------------------ stochastic rounding ---
 // Counter-based random bits: the output function of SplitMix64 (Steele, Lea
 // and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014),
@@ -157,59 +180,59 @@ __device__ __forceinline__ void collide9(float (&d)[9], float rref, float Fx, fl
 // quantity is subtracted.  The first raw moments come back as j itself, not
 // as rho (j / rho): in FP32 that round trip would change the momentum by the
 // same rounding every step of a steady flow, and the error would add up.
-__device__ __forceinline__ void collide9_w1(float (&d)[9], float rref, float Fx, float Fy, float Gx, float Gy,
-                                            const Rates9f &w)
+template <class V>
+__device__ __forceinline__ void collide9_w1(V (&d)[9], float rref, V Fx, V Fy, V Gx, V Gy, const Rates9f &w)
 {
-    const float s0 = d[1] + d[3], d0 = d[1] - d[3];
-    const float s1 = d[5] + d[6], d1 = d[5] - d[6];
-    const float s2 = d[8] + d[7], d2 = d[8] - d[7];
-    const float B0 = d[2] + s1, C0 = d[4] + s2;
-    const float drho = (d[0] + s0) + (B0 + C0);
-    const float jx = fmaf(0.5f, Fx, d0 + (d1 + d2)), jy = fmaf(0.5f, Fy, B0 - C0);  // Eq. 25
-    const float mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;  // deviations: m_xx - rho_ref / 3 etc.
-    const float rho = rref + drho;
-    const float rinv = __frcp_rn(rho);
-    const float ux = jx * rinv, uy = jy * rinv;
-    const float ux2 = ux * ux, uy2 = uy * uy;
+    const V s0 = d[1] + d[3], d0 = d[1] - d[3];
+    const V s1 = d[5] + d[6], d1 = d[5] - d[6];
+    const V s2 = d[8] + d[7], d2 = d[8] - d[7];
+    const V B0 = d[2] + s1, C0 = d[4] + s2;
+    const V drho = (d[0] + s0) + (B0 + C0);
+    const V jx = vfma(V(0.5f), Fx, d0 + (d1 + d2)), jy = vfma(V(0.5f), Fy, B0 - C0);  // Eq. 25
+    const V mxx = s0 + (s1 + s2), myy = B0 + C0, mxy = d1 - d2;  // deviations: m_xx - rho_ref / 3 etc.
+    const V rho = V(rref) + drho;
+    const V rinv = vrcp(rho);
+    const V ux = jx * rinv, uy = jy * rinv;
+    const V ux2 = ux * ux, uy2 = uy * uy;
 
     // second-order central moments minus rho_ref / 3 (xx, yy), relaxed; then
     // their deviations from the rest state's, halved
-    const float cxx = fmaf(-jx, ux, mxx), cyy = fmaf(-jy, uy, myy), cxy = fmaf(-jx, uy, mxy);
-    const float T = cxx + cyy, D = cxx - cyy;
-    const float Tq = fmaf(3.0f * w.c3, fmaf(2.0f / 3.0f, drho, -T), 0.25f * T);
-    const float Dq = (0.25f - w.c4) * D;
+    const V cxx = vfma(-jx, ux, mxx), cyy = vfma(-jy, uy, myy), cxy = vfma(-jx, uy, mxy);
+    const V T = cxx + cyy, D = cxx - cyy;
+    const V Tq = vfma(V(3.0f * w.c3), vfma(V(2.0f / 3.0f), drho, -T), V(0.25f) * T);
+    const V Dq = V(0.25f - w.c4) * D;
     const float rh = 0.5f * rref, rq = 0.25f * rref;
-    const float kxx = fmaf(-rh, ux2, Tq + Dq), kyy = fmaf(-rh, uy2, Tq - Dq);
-    const float kxy = fmaf(-rq, ux * uy, (0.25f - w.c5) * cxy);
+    const V kxx = vfma(V(-rh), ux2, Tq + Dq), kyy = vfma(V(-rh), uy2, Tq - Dq);
+    const V kxy = vfma(V(-rq), ux * uy, V(0.25f - w.c5) * cxy);
     // halved first central moments of the deviations, j - u drho (= rho_ref u)
-    const float k10 = 0.5f * fmaf(-ux, drho, jx), k01 = 0.5f * fmaf(-uy, drho, jy);
-    const float k21 = rq * fmaf(ux, ux, 1.0f / 3.0f) * uy, k12 = rq * ux * fmaf(uy, uy, 1.0f / 3.0f);
-    const float k22 = fmaf(1.0f / 36.0f, drho, -rq * (fmaf(ux2 + uy2, 1.0f / 3.0f, ux2 * uy2)));
+    const V k10 = V(0.5f) * vfma(-ux, drho, jx), k01 = V(0.5f) * vfma(-uy, drho, jy);
+    const V k21 = V(rq) * vfma(ux, ux, V(1.0f / 3.0f)) * uy, k12 = V(rq) * ux * vfma(uy, uy, V(1.0f / 3.0f));
+    const V k22 = vfma(V(1.0f / 36.0f), drho, V(-rq) * (vfma(ux2 + uy2, V(1.0f / 3.0f), ux2 * uy2)));
 
     // back-shift along x of the lines of y-order 0, 1, 2, then along y
-    const float hx = 0.5f * ux, hy = 0.5f * uy;
-    const float M10 = 0.5f * jx, M20 = fmaf(ux, k10 + M10, kxx);  // m_10 = j_x exactly
-    const float M01 = k01, M11 = fmaf(hx, k01, kxy), M21 = fmaf(ux, kxy + M11, k21);
-    const float M02 = kyy, M12 = fmaf(hx, kyy, k12), M22 = fmaf(ux, k12 + M12, k22);
-    const float N00 = drho, N01 = 0.5f * jy, N02 = fmaf(uy, M01 + N01, M02);  // m_01 = j_y exactly
-    float N10 = M10, N11 = fmaf(hy, M10, M11), N12 = fmaf(uy, M11 + N11, M12);
-    const float N20 = M20;
-    float N21 = fmaf(hy, M20, M21);
-    const float N22 = fmaf(uy, M21 + N21, M22);
-    float N01f = fmaf(3.0f, Gy, fmaf(-0.25f, Fy, N01));  // post-collision force (Eq. 31), halved
-    N10 = fmaf(3.0f, Gx, fmaf(-0.25f, Fx, N10));
-    N12 += Gx;
-    N21 += Gy;
-    const float P0m = N02 - N01f, P00 = fmaf(-2.0f, N02, N00), P0p = N02 + N01f;
-    const float P1m = N12 - N11, P10 = fmaf(-2.0f, N12, N10), P1p = N12 + N11;
-    const float P2m = N22 - N21, P20 = fmaf(-2.0f, N22, N20), P2p = N22 + N21;
-    d[0] = fmaf(-2.0f, P20, P00);
+    const V hx = V(0.5f) * ux, hy = V(0.5f) * uy;
+    const V M10 = V(0.5f) * jx, M20 = vfma(ux, k10 + M10, kxx);  // m_10 = j_x exactly
+    const V M01 = k01, M11 = vfma(hx, k01, kxy), M21 = vfma(ux, kxy + M11, k21);
+    const V M02 = kyy, M12 = vfma(hx, kyy, k12), M22 = vfma(ux, k12 + M12, k22);
+    const V N00 = drho, N01 = V(0.5f) * jy, N02 = vfma(uy, M01 + N01, M02);  // m_01 = j_y exactly
+    V N10 = M10, N11 = vfma(hy, M10, M11), N12 = vfma(uy, M11 + N11, M12);
+    const V N20 = M20;
+    V N21 = vfma(hy, M20, M21);
+    const V N22 = vfma(uy, M21 + N21, M22);
+    const V N01f = vfma(V(3.0f), Gy, vfma(V(-0.25f), Fy, N01));  // post-collision force (Eq. 31), halved
+    N10 = vfma(V(3.0f), Gx, vfma(V(-0.25f), Fx, N10));
+    N12 = N12 + Gx;
+    N21 = N21 + Gy;
+    const V P0m = N02 - N01f, P00 = vfma(V(-2.0f), N02, N00), P0p = N02 + N01f;
+    const V P1m = N12 - N11, P10 = vfma(V(-2.0f), N12, N10), P1p = N12 + N11;
+    const V P2m = N22 - N21, P20 = vfma(V(-2.0f), N22, N20), P2p = N22 + N21;
+    d[0] = vfma(V(-2.0f), P20, P00);
     d[1] = P20 + P10;
     d[3] = P20 - P10;
-    d[2] = fmaf(-2.0f, P2p, P0p);
+    d[2] = vfma(V(-2.0f), P2p, P0p);
     d[5] = P2p + P1p;
     d[6] = P2p - P1p;
-    d[4] = fmaf(-2.0f, P2m, P0m);
+    d[4] = vfma(V(-2.0f), P2m, P0m);
     d[8] = P2m + P1m;
     d[7] = P2m - P1m;
 }
@@ -394,24 +417,25 @@ struct Coef5f {
     float A1, c1, A2, c2, P3, X3, Y3, S3, P4, X4, Y4, D4, Q3;
 };
 
-__device__ __forceinline__ void collide5u(float (&d)[5], float rref, float S, float H0, const Coef5f &k)
+template <class V>
+__device__ __forceinline__ void collide5u(V (&d)[5], float rref, V S, V H0, const Coef5f &k)
 {
-    const float kx = d[1] - d[3], ky = d[2] - d[4];
-    const float mxx = d[1] + d[3], myy = d[2] + d[4];
-    const float Sg = mxx + myy, Dg = mxx - myy;
-    const float dphi = fmaf(0.5f, S, d[0] + Sg);
-    const float phi = rref + dphi;
-    const float h1 = fmaf(k.A1, phi, -k.c1 * kx);
-    const float h2 = fmaf(k.A2, phi, -k.c2 * ky);
-    const float h3 = fmaf(k.Q3, rref, fmaf(k.P3, dphi, fmaf(k.X3, kx, fmaf(k.Y3, ky, k.S3 * Sg))));
-    const float h4 = fmaf(k.P4, phi, fmaf(k.X4, kx, fmaf(k.Y4, ky, k.D4 * Dg)));
-    const float c = H0 + h3;
-    const float e1 = c + h4, e2 = c - h4;
-    d[0] += fmaf(-4.0f, h3, H0);
-    d[1] += e1 + h1;
-    d[2] += e2 + h2;
-    d[3] += e1 - h1;
-    d[4] += e2 - h2;
+    const V kx = d[1] - d[3], ky = d[2] - d[4];
+    const V mxx = d[1] + d[3], myy = d[2] + d[4];
+    const V Sg = mxx + myy, Dg = mxx - myy;
+    const V dphi = vfma(V(0.5f), S, d[0] + Sg);
+    const V phi = V(rref) + dphi;
+    const V h1 = vfma(V(k.A1), phi, V(-k.c1) * kx);
+    const V h2 = vfma(V(k.A2), phi, V(-k.c2) * ky);
+    const V h3 = vfma(V(k.Q3), V(rref), vfma(V(k.P3), dphi, vfma(V(k.X3), kx, vfma(V(k.Y3), ky, V(k.S3) * Sg))));
+    const V h4 = vfma(V(k.P4), phi, vfma(V(k.X4), kx, vfma(V(k.Y4), ky, V(k.D4) * Dg)));
+    const V c = H0 + h3;
+    const V e1 = c + h4, e2 = c - h4;
+    d[0] = d[0] + vfma(V(-4.0f), h3, H0);
+    d[1] = d[1] + (e1 + h1);
+    d[2] = d[2] + (e2 + h2);
+    d[3] = d[3] + (e1 - h1);
+    d[4] = d[4] + (e2 - h2);
 }
 
 // Coefficients of a uniform velocity (double on the host, then float).
@@ -480,28 +504,6 @@ k_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, FieldDev V, 
 struct Rates27f {
     float wb, ws, w3, w4, w5, w6;
 };
-
-// Two nodes' values in one register pair: every operation on them is one
-// packed FP32 instruction (add / multiply / fused multiply-add on f32x2, sm_100
-// and later), each half rounded exactly as the scalar operation would be.  The
-// 16-bit D3Q27 step, which is bound by instruction issue rather than by
-// memory, runs two x-neighbouring nodes per thread in this form.
-struct f2 {
-    float2 v;
-    __device__ __forceinline__ f2() {}
-    __device__ __forceinline__ f2(float s) : v(make_float2(s, s)) {}
-    __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
-    __device__ __forceinline__ explicit f2(float2 x) : v(x) {}
-};
-__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
-// a - b as a + b * (-1): exact negation, one rounding, one instruction
-__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
-__device__ __forceinline__ f2 operator-(f2 a) { return f2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
-__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ f2 vrcp(f2 a) { return f2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
-__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
 
 template <class V>
 __device__ __forceinline__ void raw_fwd(V &a, V &b, V &c)
@@ -795,33 +797,357 @@ k_step27(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float apr
 // word.  Needs nx even (the pair never straddles a row); the launcher checks.
 template <class T> struct Pair16;
 template <> struct Pair16<__half> {
-    __device__ static f2 get2(const __half *p)
+    // two stored values (low half: the lower address) as an FP32 pair, and back
+    __device__ static f2 from_bits(unsigned u)
     {
-        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
         __half2 h;
         memcpy(&h, &u, sizeof h);
         return f2(__half22float2(h));
     }
-    __device__ static void put2(__half *p, const f2 &v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v.v); }
-    __device__ static void put2raw(__half *p, __half a, __half b) { *reinterpret_cast<__half2 *>(p) = __halves2half2(a, b); }
+    __device__ static unsigned to_bits(const f2 &v)
+    {
+        const __half2 h = __float22half2_rn(v.v);
+        unsigned u;
+        memcpy(&u, &h, sizeof u);
+        return u;
+    }
+    __device__ static unsigned raw_bits(__half a, __half b)
+    {
+        return (unsigned)__half_as_ushort(a) | ((unsigned)__half_as_ushort(b) << 16);
+    }
+    __device__ static f2 get2(const __half *p) { return from_bits(__ldg(reinterpret_cast<const unsigned *>(p))); }
+    __device__ static void put2(__half *p, const f2 &v) { *reinterpret_cast<unsigned *>(p) = to_bits(v); }
+    __device__ static void put2raw(__half *p, __half a, __half b) { *reinterpret_cast<unsigned *>(p) = raw_bits(a, b); }
 };
 template <> struct Pair16<__nv_bfloat16> {
-    __device__ static f2 get2(const __nv_bfloat16 *p)
+    __device__ static f2 from_bits(unsigned u)
     {
-        const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
         __nv_bfloat162 h;
         memcpy(&h, &u, sizeof h);
         return f2(__bfloat1622float2(h));
     }
-    __device__ static void put2(__nv_bfloat16 *p, const f2 &v)
+    __device__ static unsigned to_bits(const f2 &v)
     {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v.v);
+        const __nv_bfloat162 h = __float22bfloat162_rn(v.v);
+        unsigned u;
+        memcpy(&u, &h, sizeof u);
+        return u;
     }
+    __device__ static unsigned raw_bits(__nv_bfloat16 a, __nv_bfloat16 b)
+    {
+        return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+    }
+    __device__ static f2 get2(const __nv_bfloat16 *p)
+    {
+        return from_bits(__ldg(reinterpret_cast<const unsigned *>(p)));
+    }
+    __device__ static void put2(__nv_bfloat16 *p, const f2 &v) { *reinterpret_cast<unsigned *>(p) = to_bits(v); }
     __device__ static void put2raw(__nv_bfloat16 *p, __nv_bfloat16 a, __nv_bfloat16 b)
     {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __halves2bfloat162(a, b);
+        *reinterpret_cast<unsigned *>(p) = raw_bits(a, b);
     }
 };
+
+// Four consecutive stored 16-bit values (8-byte aligned) as FP32.
+template <class T>
+__device__ __forceinline__ void get4(const T *p, float (&w)[4])
+{
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    const f2 lo = Pair16<T>::from_bits(u.x), hi = Pair16<T>::from_bits(u.y);
+    w[0] = lo.v.x;
+    w[1] = lo.v.y;
+    w[2] = hi.v.x;
+    w[3] = hi.v.y;
+}
+
+// The FP32 shape of component c at the K consecutive nodes (x0 + j, y) of one
+// row of a 2D lattice (z = 0), i0 the node index of (x0, y): each value formed
+// as field_value_f forms it, (px * py) * pz, with py and pz loaded once.
+template <int K>
+__device__ __forceinline__ void field_row_f(const FieldDev &F, int kind, int c, int x0, int y, int i0,
+                                            float (&v)[K])
+{
+    if (kind == FK_CONST) {
+#pragma unroll
+        for (int j = 0; j < K; j++) v[j] = F.fcval[c];
+        return;
+    }
+    if ((F.zmask >> c) & 1) {
+#pragma unroll
+        for (int j = 0; j < K; j++) v[j] = 0.0f;
+        return;
+    }
+    const float *t = F.fdata + c * F.cstride;
+    if (!F.sep) {
+#pragma unroll
+        for (int j = 0; j < K; j++) v[j] = __ldg(t + i0 + j);
+        return;
+    }
+    const bool ax = F.axes & 1, ay = F.axes & 2, az = F.axes & 4;
+    const float py = ay ? __ldg(t + F.len[0] + (F.len[1] > 1 ? y : 0)) : 1.0f;
+    const float pz = az ? __ldg(t + F.len[0] + F.len[1]) : 1.0f;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        float w = 1.0f;
+        bool have = false;
+        if (ax) {
+            w = __ldg(t + (F.len[0] > 1 ? x0 + j : 0));
+            have = true;
+        }
+        if (ay) {
+            w = have ? w * py : py;
+            have = true;
+        }
+        if (az) w = have ? w * pz : pz;
+        v[j] = w;
+    }
+}
+
+// Pulled deviations of a 2D node pair (i0 = node (x, y), x even; i0 + 1), as
+// pull_pair27 below: wrapped offsets along y, along x node 0's e_x = +1 source
+// wraps at x = 0 and node 1's e_x = -1 source at x + 1 = nx - 1; the e_x = 0
+// values of both nodes are one aligned 32-bit word.  A pair next to a wall
+// takes the general per-node pull.
+template <class L, class T>
+__device__ __forceinline__ void pull_pair2d(const Planes<T, L::Q> &P, const Geom &g, int x, int y, int i0,
+                                            f2 (&d)[L::Q])
+{
+    const bool wall_x = g.wall[0] && (x == 0 || x + 1 == g.nx - 1);
+    const bool wall_y = g.wall[1] && (y == 0 || y == g.ny - 1);
+    if (!(wall_x || wall_y)) {
+        const int sy = g.nx;
+        const int ym = y == 0 ? (g.ny - 1) * sy : -sy, yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+        const int xm0 = x == 0 ? g.nx - 1 : -1;
+        const int xp1 = x + 1 == g.nx - 1 ? 2 - g.nx : 2;
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) {
+            const int ex = L::ex(a), ey = L::ey(a);
+            const T *pl = P.in[a] + i0 + (ey == 1 ? ym : (ey == -1 ? yp : 0));
+            if (ex == 0) d[a] = Pair16<T>::get2(pl);
+            else if (ex == 1) d[a] = f2(Dev<T>::get(pl + xm0), Dev<T>::get(pl));
+            else d[a] = f2(Dev<T>::get(pl + 1), Dev<T>::get(pl + xp1));
+        }
+        return;
+    }
+    float d0[L::Q], d1[L::Q];
+    load_pulled_dev<L, T>(P, g, x, y, 0, i0, d0);
+    load_pulled_dev<L, T>(P, g, x + 1, y, 0, i0 + 1, d1);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) d[a] = f2(d0[a], d1[a]);
+}
+
+// Store a 16-bit node pair's deviations (rounded to nearest, or stochastically
+// with each node's own bits).
+template <class T, bool SR, int Q>
+__device__ __forceinline__ void store_pair(T *const (&out)[Q], int i0, const f2 (&m)[Q], unsigned long long srkey)
+{
+    if constexpr (SR) {
+        SRBits r0(srkey, i0), r1(srkey, i0 + 1);
+#pragma unroll
+        for (int a = 0; a < Q; a++) {
+            const T lo = Round<T>::sr(m[a].v.x, r0.get(a)), hi = Round<T>::sr(m[a].v.y, r1.get(a));
+            Pair16<T>::put2raw(out[a] + i0, lo, hi);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; a++) Pair16<T>::put2(out[a] + i0, m[a]);
+    }
+}
+
+// 16-bit D2Q9 storage, unit higher rates: two x-neighbouring nodes per thread
+// in packed FP32x2 arithmetic (nx even; the launcher checks).  One node per
+// thread keeps only 9 two-byte loads in flight per thread; the pair doubles
+// that and halves the arithmetic instructions.
+template <class T, int FK, bool SR = false>
+__global__ void __launch_bounds__(kBlock)
+k_step9x2(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref,
+          unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 1)) return;
+    const int i0 = 2 * t;
+    int x, y;
+    node_xy(g, i0, x, y);
+    f2 d[9];
+    pull_pair2d<LD2Q9, T>(P, g, x, y, i0, d);
+    f2 Fx(0.f), Fy(0.f), Gx(0.f), Gy(0.f);
+    if (FK != FK_NONE) {
+        float px[2], py[2];
+        field_row_f<2>(F, FK, 0, x, y, i0, px);
+        field_row_f<2>(F, FK, 1, x, y, i0, py);
+        const f2 Px(px[0], px[1]), Py(py[0], py[1]);
+        Fx = f2(apre) * Px;
+        Fy = f2(apre) * Py;
+        Gx = f2(gsum) * Px;
+        Gy = f2(gsum) * Py;
+    }
+    collide9_w1<f2>(d, rref, Fx, Fy, Gx, Gy, w);
+    store_pair<T, SR, 9>(P.out, i0, d, srkey);
+}
+
+// 16-bit D2Q5 storage, uniform advecting velocity: two x-neighbouring nodes
+// per thread in packed FP32x2 arithmetic (nx even), the linear step of the
+// deviations plus cref as the one-node kernel does.
+template <class T, int SK, bool SR = false>
+__global__ void __launch_bounds__(kBlock)
+k_step5x2(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, float apre, float hsum, Coef5f k, Ref5f cref,
+          unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 1)) return;
+    const int i0 = 2 * t;
+    int x, y;
+    node_xy(g, i0, x, y);
+    f2 d[5];
+    pull_pair2d<LD2Q5, T>(P, g, x, y, i0, d);
+    f2 Sp(0.f), H0(0.f);
+    if (SK != FK_NONE) {
+        float ps[2];
+        field_row_f<2>(S, SK, 0, x, y, i0, ps);
+        Sp = f2(apre) * f2(ps[0], ps[1]);
+        H0 = f2(hsum) * f2(ps[0], ps[1]);
+    }
+    collide5u<f2>(d, 0.0f, Sp, H0, k);
+#pragma unroll
+    for (int a = 0; a < 5; a++) d[a] = d[a] + f2(cref.v[a]);
+    store_pair<T, SR, 5>(P.out, i0, d, srkey);
+}
+
+// Pulled deviations of four consecutive nodes of a 2D row (i0 = node (x0, y),
+// x0 a multiple of 4; nodes x0, x0 + 1 in dA, x0 + 2, x0 + 3 in dB).  Every
+// plane is one aligned 64-bit load of the four values at the source row; a
+// plane with e_x = +1 adds the value at x0 - 1, one with e_x = -1 the value at
+// x0 + 4 (both wrapped).  Next to a wall: the general per-node pull.
+template <class L, class T>
+__device__ __forceinline__ void pull_quad2d(const Planes<T, L::Q> &P, const Geom &g, int x0, int y, int i0,
+                                            f2 (&dA)[L::Q], f2 (&dB)[L::Q])
+{
+    const bool wall_x = g.wall[0] && (x0 == 0 || x0 + 3 == g.nx - 1);
+    const bool wall_y = g.wall[1] && (y == 0 || y == g.ny - 1);
+    if (!(wall_x || wall_y)) {
+        const int sy = g.nx;
+        const int ym = y == 0 ? (g.ny - 1) * sy : -sy, yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+        const int xm = x0 == 0 ? g.nx - 1 : -1;       // node x0 - 1, wrapped
+        const int xp = x0 + 4 == g.nx ? 4 - g.nx : 4;  // node x0 + 4, wrapped
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) {
+            const int ex = L::ex(a), ey = L::ey(a);
+            const T *pl = P.in[a] + i0 + (ey == 1 ? ym : (ey == -1 ? yp : 0));
+            float w[4];
+            get4<T>(pl, w);
+            if (ex == 0) {
+                dA[a] = f2(w[0], w[1]);
+                dB[a] = f2(w[2], w[3]);
+            } else if (ex == 1) {
+                dA[a] = f2(Dev<T>::get(pl + xm), w[0]);
+                dB[a] = f2(w[1], w[2]);
+            } else {
+                dA[a] = f2(w[1], w[2]);
+                dB[a] = f2(w[3], Dev<T>::get(pl + xp));
+            }
+        }
+        return;
+    }
+    float d0[L::Q], d1[L::Q], d2[L::Q], d3[L::Q];
+    load_pulled_dev<L, T>(P, g, x0, y, 0, i0, d0);
+    load_pulled_dev<L, T>(P, g, x0 + 1, y, 0, i0 + 1, d1);
+    load_pulled_dev<L, T>(P, g, x0 + 2, y, 0, i0 + 2, d2);
+    load_pulled_dev<L, T>(P, g, x0 + 3, y, 0, i0 + 3, d3);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        dA[a] = f2(d0[a], d1[a]);
+        dB[a] = f2(d2[a], d3[a]);
+    }
+}
+
+// Store four consecutive nodes' deviations as one 64-bit word per plane.
+template <class T, bool SR, int Q>
+__device__ __forceinline__ void store_quad(T *const (&out)[Q], int i0, const f2 (&A)[Q], const f2 (&B)[Q],
+                                           unsigned long long srkey)
+{
+    if constexpr (SR) {
+        SRBits r0(srkey, i0), r1(srkey, i0 + 1), r2(srkey, i0 + 2), r3(srkey, i0 + 3);
+#pragma unroll
+        for (int a = 0; a < Q; a++) {
+            const unsigned lo = Pair16<T>::raw_bits(Round<T>::sr(A[a].v.x, r0.get(a)), Round<T>::sr(A[a].v.y, r1.get(a)));
+            const unsigned hi = Pair16<T>::raw_bits(Round<T>::sr(B[a].v.x, r2.get(a)), Round<T>::sr(B[a].v.y, r3.get(a)));
+            *reinterpret_cast<uint2 *>(out[a] + i0) = make_uint2(lo, hi);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < Q; a++)
+            *reinterpret_cast<uint2 *>(out[a] + i0) = make_uint2(Pair16<T>::to_bits(A[a]), Pair16<T>::to_bits(B[a]));
+    }
+}
+
+// 16-bit D2Q9 (unit higher rates) and D2Q5 (uniform velocity) storage, four
+// consecutive nodes of a row per thread (nx a multiple of 4; the launchers
+// check): two packed pairs, the plane addresses and the y / z factors of the
+// force or source shared by the four, 64-bit loads and stores.  One or two
+// nodes per thread spend most of their instructions on addressing.
+template <class T, int FK, bool SR = false>
+__global__ void __launch_bounds__(kBlock)
+k_step9x4(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref,
+          unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 2)) return;
+    const int i0 = 4 * t;
+    int x0, y;
+    node_xy(g, i0, x0, y);
+    f2 dA[9], dB[9];
+    pull_quad2d<LD2Q9, T>(P, g, x0, y, i0, dA, dB);
+    f2 FxA(0.f), FyA(0.f), GxA(0.f), GyA(0.f), FxB(0.f), FyB(0.f), GxB(0.f), GyB(0.f);
+    if (FK != FK_NONE) {
+        float px[4], py[4];
+        field_row_f<4>(F, FK, 0, x0, y, i0, px);
+        field_row_f<4>(F, FK, 1, x0, y, i0, py);
+        const f2 PxA(px[0], px[1]), PyA(py[0], py[1]), PxB(px[2], px[3]), PyB(py[2], py[3]);
+        FxA = f2(apre) * PxA;
+        FyA = f2(apre) * PyA;
+        GxA = f2(gsum) * PxA;
+        GyA = f2(gsum) * PyA;
+        FxB = f2(apre) * PxB;
+        FyB = f2(apre) * PyB;
+        GxB = f2(gsum) * PxB;
+        GyB = f2(gsum) * PyB;
+    }
+    collide9_w1<f2>(dA, rref, FxA, FyA, GxA, GyA, w);
+    collide9_w1<f2>(dB, rref, FxB, FyB, GxB, GyB, w);
+    store_quad<T, SR, 9>(P.out, i0, dA, dB, srkey);
+}
+
+template <class T, int SK, bool SR = false>
+__global__ void __launch_bounds__(kBlock)
+k_step5x4(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, float apre, float hsum, Coef5f k, Ref5f cref,
+          unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 2)) return;
+    const int i0 = 4 * t;
+    int x0, y;
+    node_xy(g, i0, x0, y);
+    f2 dA[5], dB[5];
+    pull_quad2d<LD2Q5, T>(P, g, x0, y, i0, dA, dB);
+    f2 SpA(0.f), H0A(0.f), SpB(0.f), H0B(0.f);
+    if (SK != FK_NONE) {
+        float ps[4];
+        field_row_f<4>(S, SK, 0, x0, y, i0, ps);
+        const f2 PA(ps[0], ps[1]), PB(ps[2], ps[3]);
+        SpA = f2(apre) * PA;
+        H0A = f2(hsum) * PA;
+        SpB = f2(apre) * PB;
+        H0B = f2(hsum) * PB;
+    }
+    collide5u<f2>(dA, 0.0f, SpA, H0A, k);
+    collide5u<f2>(dB, 0.0f, SpB, H0B, k);
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+        dA[a] = dA[a] + f2(cref.v[a]);
+        dB[a] = dB[a] + f2(cref.v[a]);
+    }
+    store_quad<T, SR, 5>(P.out, i0, dA, dB, srkey);
+}
 
 // Pulled deviations of the node pair (i0 = node (x, y, z), x even; i0 + 1).
 template <class T>
@@ -891,17 +1217,7 @@ k_step27x2(const __grid_constant__ Planes<T, 27> P, Geom g, FieldDev Fd, float a
         }
     }
     collide27_w1<f2, XO>(m, rref, F, Fq, w);
-    if constexpr (SR) {
-        SRBits r0(srkey, i0), r1(srkey, i0 + 1);
-#pragma unroll
-        for (int a = 0; a < 27; a++) {
-            const T lo = Round<T>::sr(m[a].v.x, r0.get(a)), hi = Round<T>::sr(m[a].v.y, r1.get(a));
-            Pair16<T>::put2raw(P.out[a] + i0, lo, hi);
-        }
-    } else {
-#pragma unroll
-        for (int a = 0; a < 27; a++) Pair16<T>::put2(P.out[a] + i0, m[a]);
-    }
+    store_pair<T, SR, 27>(P.out, i0, m, srkey);
 }
 
 // --------------------------------------------------------------- batched ---
@@ -1083,6 +1399,28 @@ void step9_launch(const Planes<T, 9> &fin, const LaunchArgs &a, int grid, float 
                   float rref, cudaStream_t s)
 {
     const unsigned long long k = a.srkey;
+    if constexpr (sizeof(T) == 2 && W1) {
+        if (a.g.nx % 4 == 0) {
+            // four consecutive nodes of a row per thread
+            const int qgrid = (a.g.N / 4 + kBlock - 1) / kBlock;
+            if (a.fkind == FK_NONE)
+                k_step9x4<T, FK_NONE, SR><<<qgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            else if (a.fkind == FK_CONST)
+                k_step9x4<T, FK_CONST, SR><<<qgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            else k_step9x4<T, FK_GENERAL, SR><<<qgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            return;
+        }
+        if (a.g.nx % 2 == 0) {
+            // two x-neighbouring nodes per thread, packed FP32x2 arithmetic
+            const int pgrid = (a.g.N / 2 + kBlock - 1) / kBlock;
+            if (a.fkind == FK_NONE)
+                k_step9x2<T, FK_NONE, SR><<<pgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            else if (a.fkind == FK_CONST)
+                k_step9x2<T, FK_CONST, SR><<<pgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            else k_step9x2<T, FK_GENERAL, SR><<<pgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
+            return;
+        }
+    }
     if (a.fkind == FK_NONE) k_step9<T, FK_NONE, W1, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
     else if (a.fkind == FK_CONST)
         k_step9<T, FK_CONST, W1, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, apre, gsum, w, rref, k);
@@ -1093,6 +1431,20 @@ template <class T, int SK, bool SR>
 void step5_launch(const Planes<T, 5> &fin, const LaunchArgs &a, int grid, float apre, float hsum, const Rates5f &w,
                   const Coef5f &k, float rref, const Ref5f &cref, bool uni, cudaStream_t s)
 {
+    if constexpr (sizeof(T) == 2) {
+        if (uni && a.g.nx % 4 == 0) {
+            // four consecutive nodes of a row per thread
+            const int qgrid = (a.g.N / 4 + kBlock - 1) / kBlock;
+            k_step5x4<T, SK, SR><<<qgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, hsum, k, cref, a.srkey);
+            return;
+        }
+        if (uni && a.g.nx % 2 == 0) {
+            // two x-neighbouring nodes per thread, packed FP32x2 arithmetic
+            const int pgrid = (a.g.N / 2 + kBlock - 1) / kBlock;
+            k_step5x2<T, SK, SR><<<pgrid, kBlock, 0, s>>>(fin, a.g, a.F, apre, hsum, k, cref, a.srkey);
+            return;
+        }
+    }
     if (uni)
         k_step5<T, SK, true, SR><<<grid, kBlock, 0, s>>>(fin, a.g, a.F, a.V, apre, hsum, w, k, rref, cref, a.srkey);
     else

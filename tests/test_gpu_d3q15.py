@@ -8,7 +8,8 @@ import pytest
 from paper_1806_10247_gb300 import lbm
 from paper_1806_10247_gb300 import workloads as W
 from tests.gpu_helpers import compare_state, oracle_from_workload
-from tests.test_gpu_parity import _advance, _one_step_sampled, _pair, _pair_full, _random_workload
+from tests.gpu_helpers import one_step_sampled
+from tests.test_gpu_parity import _advance, _pair, _pair_full, _random_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -81,4 +82,4 @@ def test_d3q15_duct_128_full_size_sampled():
     G.step(3)
     r1 = G.reduce()
     assert abs(r1[0] - r0[0]) <= 1e-12 * r0[0]
-    _one_step_sampled(w, G, samples=300, seed=6)
+    one_step_sampled(w, G, samples=300, seed=6)

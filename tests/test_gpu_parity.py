@@ -9,7 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_1806_10247_gb300 import lbm
 from paper_1806_10247_gb300 import workloads as W
-from tests.gpu_helpers import compare_state, oracle_from_workload
+from tests.gpu_helpers import compare_state, one_step_sampled, oracle_from_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -250,97 +250,6 @@ def test_d3q27_duct_small():
     compare_state(G, R)
 
 
-def _separable_at(tables, shape, nodes):
-    """Separable shape (px[x] * py[y]) * pz[z] at the given node indices
-    ([ncomp][len(nodes)]), in the product order of the full field."""
-    nx, ny, nz = shape
-    x, y, z = nodes % nx, (nodes // nx) % ny, nodes // (nx * ny)
-    out = []
-    for px, py, pz in tables:
-        px = np.broadcast_to(np.asarray(px, np.float64), (nx,))
-        py = np.broadcast_to(np.asarray(py, np.float64), (ny,))
-        pz = np.broadcast_to(np.asarray(pz, np.float64), (nz,))
-        out.append((px[x] * py[y]) * pz[z])
-    return np.stack(out)
-
-
-def _one_step_sampled(w, G, samples, seed, tol=1e-12, device=False):
-    """Full-size check for grids too large for a whole-grid oracle run: take the
-    GPU's f(t), let the oracle collide the pull-neighbours of sampled nodes and
-    stream them in, and compare with the GPU's f(t+1) at those nodes.  With
-    device=True the two states stay in device memory and only the columns the
-    check needs come to the host (for grids whose f does not fit host memory
-    comfortably)."""
-    E = O.velocities(w.lattice)
-    q = E.shape[0]
-    nx, ny, nz = w.shape
-    opp = [int(np.where((E == -E[a]).all(1))[0][0]) for a in range(q)]
-    rng = np.random.default_rng(seed)
-    nxy = nx * ny
-    edges = np.array([0, w.nodes - 1, nx - 1, w.nodes - nx, nx * (ny // 2)], dtype=np.int64)
-    idx = np.concatenate([edges[edges < w.nodes], rng.integers(0, w.nodes, samples)])
-    samples = len(idx)
-    # pull source (node, component) of every sampled node and population
-    src = np.empty((samples, q), dtype=np.int64)
-    comp = np.empty((samples, q), dtype=np.int64)
-    for k, i in enumerate(idx):
-        x, y, z = i % nx, (i // nx) % ny, i // (nx * ny)
-        for a in range(q):
-            s_ = [x - E[a, 0], y - E[a, 1], z - E[a, 2]]
-            n = [nx, ny, nz]
-            out = False
-            for d in range(3):
-                if s_[d] < 0 or s_[d] >= n[d]:
-                    if w.wall[d]:
-                        out = True
-                    else:
-                        s_[d] %= n[d]
-            # pulled value: post-collision population a of the source node, or
-            # the opposite population of this node beyond a wall
-            src[k, a], comp[k, a] = (i, opp[a]) if out else (s_[0] + nx * (s_[1] + ny * s_[2]), a)
-    need = np.unique(np.concatenate([src.reshape(-1), idx]))
-    pos = {int(v): j for j, v in enumerate(need)}
-    t = G.t
-    if device:
-        import torch
-
-        buf = torch.empty((q, w.nodes), dtype=torch.float64, device="cuda")
-        sel = torch.from_numpy(need).to("cuda")
-        G.get_populations(out=buf, where=1)
-        G.sync()
-        ft = buf[:, sel].cpu().numpy()
-        G.step(1)
-        G.get_populations(out=buf, where=1)
-        G.sync()
-        ft1 = buf[:, sel].cpu().numpy()
-        scale = max(float(buf.max().item()), -float(buf.min().item()))  # no |f| temporary
-        del buf
-        torch.cuda.empty_cache()
-    else:
-        f_t = G.get_populations()
-        G.step(1)
-        f_t1 = G.get_populations()
-        ft, ft1, scale = f_t[:, need], f_t1[:, need], np.abs(f_t1).max()
-    R = O.OracleLattice(w.lattice, (1, 1, 1), omega=w.omega)  # single-node collisions only
-    P = _separable_at(w.tables, w.shape, need) if w.tables is not None else None
-    pre, post = (O.envelope_pairs(w.envelope, t, 1) if w.envelope else (1.0, 1.0))
-    dim = 3 if w.lattice in (O.D3Q27, O.D3Q15) else 2
-    worst = 0.0
-    for k, i in enumerate(idx):
-        want = np.empty(q)
-        for a in range(q):
-            j = pos[int(src[k, a])]
-            Fpre = pre * P[:, j] if P is not None else np.zeros(dim)
-            Fpost = post * P[:, j] if P is not None else np.zeros(dim)
-            want[a] = R.collide_node(ft[:, j], Fpre, Fpost)[comp[k, a]]
-        worst = max(worst, np.abs(ft1[:, pos[int(i)]] - want).max() / scale)
-    from tests.gpu_helpers import record
-
-    record({"f": worst}, tol, samples=samples, nodes=w.nodes)
-    assert worst <= tol, worst
-    return worst
-
-
 def test_d3q27_kolmogorov_256_full_size_sampled():
     """Config 3 at 256^3 in the bench's launch configuration: 9 steps on the GPU,
     then the 10th checked on 300 sampled nodes by the oracle; plus exact mass
@@ -353,7 +262,7 @@ def test_d3q27_kolmogorov_256_full_size_sampled():
     assert abs(r1[0] - r0[0]) <= 1e-12 * r0[0]
     # the Kolmogorov force sums to ~0 over y: total momentum changes only by roundoff
     assert np.abs(r1[1:4] - r0[1:4]).max() < 1e-9
-    _one_step_sampled(w, G, samples=300, seed=5)
+    one_step_sampled(w, G, samples=300, seed=5)
 
 
 def test_d3q27_kolmogorov_512_full_size_sampled():
@@ -368,7 +277,7 @@ def test_d3q27_kolmogorov_512_full_size_sampled():
     r1 = G.reduce()
     assert abs(r1[0] - r0[0]) <= 1e-12 * r0[0]
     assert np.abs(r1[1:4] - r0[1:4]).max() < 1e-8
-    _one_step_sampled(w, G, samples=200, seed=9, device=True)
+    one_step_sampled(w, G, samples=200, seed=9, device=True)
     G.close()
 
 

@@ -14,7 +14,7 @@ import pytest
 from oracle import oracle as O
 from paper_1806_10247_gb300 import lbm
 from paper_1806_10247_gb300 import workloads as W
-from tests.gpu_helpers import oracle_from_workload
+from tests.gpu_helpers import one_step_sampled, oracle_from_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -146,12 +146,10 @@ def test_fp32_kolmogorov_256_full_size_sampled_step():
     configuration: 3 steps, then one more step checked on 200 sampled nodes
     against the FP64 oracle's collision of the same f(t) (the FP32 moment
     arithmetic is the only difference)."""
-    from tests.test_gpu_parity import _one_step_sampled
-
     w = W.kolmogorov(n=256)
     G = lbm.from_workload(w, storage=lbm.FP32_DEV)
     G.step(3)
-    worst = _one_step_sampled(w, G, samples=200, seed=9, tol=2e-6)
+    worst = one_step_sampled(w, G, samples=200, seed=9, tol=2e-6)
     _record("kolmogorov_256_fp32_one_step_sampled_rel_max", worst)
 
 
@@ -232,6 +230,100 @@ def test_d3q27_16bit_pair_kernel(form, shape, wall):
     _, ug = G.moments()
     err = _l2(ug, ur)
     _record(f"d3q27_pair_{form}_{nx}x{ny}x{nz}_walls{''.join(map(str, wall))}", err)
+    assert err <= (2e-3 if form == "fp16" else 2e-2), err
+
+
+def _pair2d_workload(lattice, shape, wall, seed):
+    """A 2D lattice for the 16-bit pair kernels: x-dependent force or source
+    (each node of a pair takes its own), a 0.05-sized initial signal."""
+    rng = np.random.default_rng(seed)
+    nx, ny, _ = shape
+    N = nx * ny
+    if lattice == W.D2Q9:
+        tables = [(1e-4 * (1 + 0.3 * rng.standard_normal(nx)), 1 + 0.2 * rng.standard_normal(ny), np.array([1.0]))
+                  for _ in range(2)]
+        return W.Workload(name="pair9", lattice=W.D2Q9, shape=shape, wall=wall, omega=W.d2q9_omega(0.7), rho0=1.0,
+                          u0=0.05 * rng.standard_normal((2, N)), tables=tables)
+    tables = [(1e-4 * (1 + 0.3 * rng.standard_normal(nx)), 1 + 0.2 * rng.standard_normal(ny), np.array([1.0]))]
+    return W.Workload(name="pair5", lattice=W.D2Q5, shape=shape, wall=wall, omega=W.d2q5_omega(0.8),
+                      rho0=1.0 + 0.05 * rng.standard_normal(N), u0=(0.03, -0.02, 0.0), tables=tables)
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("lattice", [W.D2Q9, W.D2Q5], ids=["d2q9", "d2q5"])
+@pytest.mark.parametrize("shape,wall", [
+    ((12, 10, 1), (0, 0, 0)),   # nx % 4 = 0, periodic: four nodes per thread, 64-bit pulls, x wrap
+    ((4, 5, 1), (0, 0, 0)),     # nx = 4: one quad per row, both x edges wrap onto it
+    ((12, 10, 1), (1, 0, 0)),   # walls on x: quads at x = 0 and x = nx - 4 take the per-node pulls
+    ((16, 9, 1), (0, 1, 0)),    # channel walls on y
+    ((14, 6, 1), (0, 0, 0)),    # nx % 4 = 2: two nodes per thread, x wrap of both nodes
+    ((2, 7, 1), (0, 0, 0)),     # nx = 2: one pair per row, each node the other's x source
+    ((10, 5, 1), (1, 1, 0)),    # pairs next to walls on x and y
+    ((9, 8, 1), (0, 0, 0)),     # odd nx: the one-node kernel
+])
+def test_2d_16bit_pair_kernels(form, lattice, shape, wall):
+    """16-bit D2Q9 (unit higher rates) and D2Q5 (uniform velocity) storage step
+    four consecutive nodes of a row per thread (nx a multiple of 4) or two
+    (nx even) in packed FP32x2 arithmetic.  Against the batched kernel (one
+    node per thread, scalar FP32) to a few units of the storage precision
+    after 5 steps, and against the FP64 oracle within the 16-bit error bound."""
+    w = _pair2d_workload(lattice, shape, wall, 7 + shape[0] + 5 * wall[0] + wall[1])
+    G = _gpu(w, STORAGES[form], 5)
+    a = lbm.from_workload(w, storage=STORAGES[form])
+    b = lbm.from_workload(w, storage=STORAGES[form])
+    B = lbm.Batch([a, b])
+    B.step(5)
+    fg, fa = G.get_populations(), a.get_populations()
+    assert np.abs(fg - fa).max() <= 8 * EPS[form] * 0.05, np.abs(fg - fa).max()
+    R = oracle_from_workload(w)
+    R.run(5)
+    if lattice == W.D2Q9:
+        _, ur = R.moments()
+        _, ug = G.moments()
+        err = _l2(ug, ur)
+    else:
+        pr = R.moments()
+        pg = G.moments()
+        err = _l2(pg - pr.mean(), pr - pr.mean())
+    _record(f"{'d2q9' if lattice == W.D2Q9 else 'd2q5'}_pair_{form}_{shape[0]}x{shape[1]}_walls{''.join(map(str, wall))}",
+            err)
+    assert err <= (3e-3 if form == "fp16" else 3e-2), err
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_2d_pair_kernels_stochastic_rounding(form):
+    """Stochastic rounding in the 2D multi-node kernels (nx = 16: four nodes
+    per thread; 14: two): seeded (same seed, same bits), each node its own
+    bits (equal nodes do not round alike everywhere), and unbiased against
+    the FP64 oracle."""
+    for nx in (16, 14):
+        _sr_multi_node_case(form, nx)
+
+
+def _sr_multi_node_case(form, nx):
+    ny = 12
+    w9 = W.Workload(name="sr_pair9", lattice=W.D2Q9, shape=(nx, ny, 1), wall=(0, 0, 0), omega=W.d2q9_omega(0.7),
+                    rho0=1.0, u0=np.stack([np.full(nx * ny, 0.031), np.full(nx * ny, -0.017)]))
+    runs = []
+    for seed in (3, 3):
+        G = lbm.from_workload(w9, storage=STORAGES[form])
+        G.set_stochastic_rounding(True, seed)
+        G.step(7)
+        runs.append(G.get_populations())
+    assert np.array_equal(runs[0], runs[1])
+    f = runs[0].reshape(9, ny, nx)
+    # a uniform state: round to nearest would keep every node equal; own bits per node do not
+    assert not np.array_equal(f[:, :, 0::2], f[:, :, 1::2])
+    assert not np.array_equal(f[:, :, 0:nx - 2], f[:, :, 2:nx])
+    R = oracle_from_workload(w9)
+    R.run(7)
+    _, ur = R.moments()
+    G = lbm.from_workload(w9, storage=STORAGES[form])
+    G.set_stochastic_rounding(True, 11)
+    G.step(7)
+    _, ug = G.moments()
+    err = _l2(ug, ur)
+    _record(f"d2q9_multi_node_sr_{form}_nx{nx}", err)
     assert err <= (2e-3 if form == "fp16" else 2e-2), err
 
 
@@ -358,8 +450,6 @@ def test_maximum_node_count_d2q5_fp32():
     storage (86 GB of populations).  One step, checked on sampled nodes -- the
     first and last nodes and both x edges among them -- by the oracle's
     collision of the GPU's f(t), streamed in; plus exact scalar accounting."""
-    from tests.test_gpu_parity import _one_step_sampled
-
     nx, ny = 65536, 32767
     one = np.array([1.0])
     x, y = np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64)
@@ -373,6 +463,6 @@ def test_maximum_node_count_d2q5_fp32():
     r1 = G.reduce()
     # the source sums to ~0 over the lattice: the total scalar changes only by rounding
     assert abs(r1[0] - r0[0]) <= 1e-6 * r0[0]
-    worst = _one_step_sampled(w, G, samples=64, seed=17, tol=2e-6, device=True)
+    worst = one_step_sampled(w, G, samples=64, seed=17, tol=2e-6, device=True)
     _record("max_nodes_d2q5_fp32_one_step_sampled_rel_max", worst)
     G.close()
