@@ -85,21 +85,44 @@ TRAFFIC = {
     ("d3q27", "fp64"): {"src": [_C + "k_d3q27.cu"] + _H, "sha": "4be8a09ad4918a7a",
                         "bytes_per_node": (1529.134848 + 1477.492224) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md"},
-    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
-                        "bytes_per_node": (1812.015104 + 1757.000448) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
+    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                        "bytes_per_node": (1812.021504 + 1756.456448) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
                         "profile": "profiles/k_step27_kolmogorov96_fp32_fp16.md"},
-    ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
-                             "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,
-                             "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md"},
-    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
-                        "bytes_per_node": (382.271488 + 334.486272) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                        "bytes_per_node": (382.344960 + 334.191616) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/k_step27x2_kolmogorov_fp16_pair.md"},
-    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "3e0152d5cf74f322", "above_l2": True,
-                       "bytes_per_node": (1208.092160 + 1154.119680) * 1e6 / (8192 * 4096),
-                       "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9_channel8192_fp32.md"},
+    ("d3q27", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                        "bytes_per_node": (382.285312 + 333.663488) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+                        "profile": "profiles/k_step27x2_kolmogorov_fp16_pair.md"},
     ("d2q9", "fp64"): {"src": [_C + "k_d2q9.cu"] + _H, "sha": "018f6162beb1528d",
                        "bytes_per_node": (151.018240 + 99.837696) * 1e6 / (2048 * 1024),
                        "captured_nodes": 2048 * 1024, "profile": "profiles/k_step_d2q9_channel2048_fp64.md"},
+    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (1207.991296 + 1153.961728) * 1e6 / (8192 * 4096),
+                       "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9_channel8192_fp32.md"},
+    ("d2q9", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (604.019712 + 551.184384) * 1e6 / (8192 * 4096),
+                       "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9x4_k_step5x4_16bit_rows.md"},
+    ("d2q9", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (604.020480 + 551.063040) * 1e6 / (8192 * 4096),
+                       "captured_nodes": 8192 * 4096, "profile": "profiles/k_step9x4_k_step5x4_16bit_rows.md"},
+    ("d2q5", "fp64"): {"src": [_C + "k_d2q5.cu"] + _H, "sha": "80d05b85abca33c6", "above_l2": True,
+                       "bytes_per_node": (2684.653056 + 2632.778752) * 1e6 / 8192 ** 2,
+                       "captured_nodes": 8192 ** 2, "profile": "profiles/k_step5_k_step_mat_cde8192.md"},
+    ("d2q5", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (1342.272000 + 1290.788608) * 1e6 / 8192 ** 2,
+                       "captured_nodes": 8192 ** 2, "profile": "profiles/k_step5_k_step_mat_cde8192.md"},
+    ("d2q5", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (671.184640 + 621.116672) * 1e6 / 8192 ** 2,
+                       "captured_nodes": 8192 ** 2, "profile": "profiles/k_step9x4_k_step5x4_16bit_rows.md"},
+    ("d2q5", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "dc985a5e8c0c8f89", "above_l2": True,
+                       "bytes_per_node": (671.183616 + 621.553920) * 1e6 / 8192 ** 2,
+                       "captured_nodes": 8192 ** 2, "profile": "profiles/k_step9x4_k_step5x4_16bit_rows.md"},
+    # batched kernels (keys of the batched launches; the single-lattice
+    # captures above do not describe them)
+    ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
+                             "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,
+                             "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md"},
 }
 
 
@@ -610,7 +633,8 @@ def measure(lbm, stream, name, storage, steps, warmup, hbm, hbm_src, peak, graph
         for k, g, m in zip(R.kinds, R.gwl, ms):
             n = sum(w.nodes for w in g)
             kname = Q_NAME[k]
-            tkey = ("d2q5_sweep", storage) if (kname == "d2q5" and len(g) > 1 and name == "cde_sweep") else None
+            # a batched launch has its own traffic entry (none: null), not the single-lattice kernel's
+            tkey = None if len(g) == 1 else (("d2q5_sweep" if name == "cde_sweep" else f"{kname}_batch"), storage)
             kernels.append(roofline_block(kname, storage, n, m / steps * 1e-3, hbm, hbm_src, peak, tkey,
                                           label=f"{kname} {'batched ' if len(g) > 1 else ''}step kernel "
                                                 f"({len(g)} lattice{'s' if len(g) > 1 else ''}, {n} nodes, {storage})"))
@@ -1209,7 +1233,8 @@ def main():
     dom = max(range(len(R.batches)), key=lambda i: per_batch_ms[i])
     nb = sum(w.nodes for w in R.gwl[dom])
     kname = Q_NAME[R.kinds[dom]]
-    tkey = ("d2q5_sweep", args.storage) if args.workload == "cde_sweep" else None
+    tkey = None if len(R.gwl[dom]) == 1 else \
+        (("d2q5_sweep" if args.workload == "cde_sweep" else f"{kname}_batch"), args.storage)
     roof = roofline_block(kname, args.storage, nb, per_batch_ms[dom] / args.steps * 1e-3, hbm, hbm_src, peak, tkey,
                           label=f"{kname} {'batched ' if len(R.gwl[dom]) > 1 else ''}step kernel ({nb} nodes)")
     roof["timing"] = ("CUDA events around each step's launch" + (f" (graph replays of {unit} steps)" if args.graph
