@@ -120,6 +120,14 @@ TRAFFIC = {
                        "captured_nodes": 8192 ** 2, "profile": "profiles/k_step9x4_k_step5x4_16bit_rows.md"},
     # batched kernels (keys of the batched launches; the single-lattice
     # captures above do not describe them)
+    ("d2q9_batch", "fp32"): {"src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh", _C + "lbm_batch.cu"] + _H,
+                             "sha": "46fbea4274464db2", "above_l2": True,
+                             "bytes_per_node": (379.264000 + 335.258624) * 1e6 / 10521531, "captured_nodes": 10521531,
+                             "profile": "profiles/k_batch9_batched_sweep_fp32.md"},
+    ("d2q5_batch", "fp32"): {"src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh", _C + "lbm_batch.cu"] + _H,
+                             "sha": "46fbea4274464db2", "above_l2": True,
+                             "bytes_per_node": (211.177984 + 168.022272) * 1e6 / 10521531, "captured_nodes": 10521531,
+                             "profile": "profiles/k_batch9_batched_sweep_fp32.md"},
     ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
                              "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,
                              "profile": "profiles/k_batch_d2q5_cde_sweep_fp64.md"},
