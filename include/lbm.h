@@ -212,6 +212,38 @@ int lbm_set_envelope_table(lbm_ctx *ctx, const double *a, long count, double t0)
  * Errors: LBM_EINVAL (storage not 16-bit). */
 int lbm_set_stochastic_rounding(lbm_ctx *ctx, int on, unsigned long long seed);
 
+/* Storage of a 16-bit D2Q9 or D2Q5 context at a per-node reference (the
+ * paper has no counterpart: this keeps the Strang-split force and source
+ * increments of Eqs. 25/31 and 43/47, which a 16-bit deviation from the
+ * fixed rest state of a few 1e-4 cannot resolve).  Each node keeps a
+ * reference in FP32 -- D2Q9: the deviation of rho and j; D2Q5: the deviation
+ * of phi -- and the stored 16-bit value of population a is
+ * sigma (d_a - e_a): d_a the deviation the FP32 forms store (f_a - w_a rho_ref,
+ * or g_a - g_ref,a), e_a that of an equilibrium at the reference (D2Q9:
+ * w_a (drho + 3 c + 4.5 c^2 - 1.5 |j|^2), c = e_a . j, second order in j at
+ * unit density; D2Q5: the Eq. 39 equilibrium per unit scalar at the uniform
+ * advecting velocity, times dphi), and sigma a power of two per lattice that
+ * puts the largest |d - e| in [8, 16) (FP16 then holds values 4096 times
+ * larger).  A step pulls d = s / sigma + e of the source node and collides
+ * exactly as the FP32 deviation form; every `every` steps of lbm_step the
+ * reference and sigma are rebuilt from the state (the node's own moments), so
+ * the 16-bit values hold only the non-equilibrium part and the change since.
+ * Reads and writes of the state (moments, reductions, populations, init) go
+ * through FP32 deviations.
+ * Memory: (1 or 3 + q) floats per node on top of the 16-bit state.
+ *   every : steps between rebuilds (>= 1), or 0 to return to the plain
+ *           16-bit deviations (the state is converted either way).
+ * A D2Q5 context needs a uniform advecting velocity (setting a velocity field
+ * returns it to the plain deviations); stochastic rounding applies as set; a
+ * context stored this way cannot join a batch.  Between rebuilds the stored
+ * values must stay within the 16-bit range (FP16: 65504; see above); a
+ * rebuild interval short against the flow's time
+ * scales keeps them there, and an overflow shows as a non-finite density in
+ * lbm_reduce.
+ * Errors: LBM_EINVAL (storage not 16-bit, lattice not D2Q9 / D2Q5, every < 0,
+ * a D2Q5 velocity field), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_set_local_reference(lbm_ctx *ctx, int every);
+
 /* Advance n >= 0 time steps (n = 0 is a no-op).  Each step is one fused
  * kernel launch: stream (Eq. 22b / 40b, pull form, with periodic wrap or
  * halfway bounce-back), moments (Eq. 24 / 42), pre-collision half force or

@@ -8,6 +8,8 @@
 // rearranged around the rest state.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "lbm_internal.h"
 #include "lbm_lattices.cuh"
 #include "lbm_tiles.cuh"
@@ -1575,6 +1577,292 @@ int resident_t(int lattice, int tile)
     }
 }
 
+struct LrefK {
+    const float *ref;    // [1 or 3][Np]: dphi, or drho, jx, jy
+    const float *scale;  // [2]: sigma, 1 / sigma
+    long long Np;
+    float q5[5];
+};
+
+// ------------------------------------------------ local-reference encoding ---
+// 16-bit storage at a per-node reference.  A 16-bit deviation from the fixed
+// reference state of a few 1e-4 has a step of ~1e-7 (FP16) or ~1e-6 (BF16),
+// the size of one step's force or source increment, so increments are lost.
+// Here the stored value is s_a(x) = sigma (d_a(x) - e_a(x)): d the deviation of
+// the FP32 forms, e_a(x) the deviation of a low-order equilibrium at the
+// node's reference -- D2Q9: e_a = w_a (drho + 3 e_a . j + second-order terms);
+// D2Q5 at a uniform velocity u: e_a = q_a dphi, q the equilibrium per unit
+// scalar at u (Eq. 39) -- which holds the node's zeroth and first moments in
+// FP32, and sigma a power of two per lattice that brings the lattice's
+// largest |d - e| to [8, 16) (FP16 then holds values 4096 times larger).  A
+// step pulls d = s / sigma + e (e of the source node), collides in FP32
+// exactly as the deviation kernels do and stores sigma (d - e) of its own
+// node.  The reference is rebuilt from the state every few steps (rebase), so
+// s holds only the non-equilibrium part and the change since the last rebase.
+// (A per-node sigma, up to 2^8 times the lattice's, was tried: it overflowed
+// FP16 in start-up transients next to walls and was no more accurate.)
+
+// e_a from a node's reference values r0 (drho or dphi), r1, r2 (j, D2Q9 only).
+// D2Q9: w_a (drho + 3 c + 4.5 c^2 - 1.5 |j|^2), c = e_a . j -- the equilibrium
+// to second order in j at unit density, whose zeroth and first moments are
+// drho and j.
+template <class L>
+__device__ __forceinline__ float lref_e_of(const LrefK &R, int a, float r0, float r1, float r2)
+{
+    if constexpr (L::Q == 9) {
+        const float c = fmaf((float)LD2Q9::ex(a), r1, (float)LD2Q9::ey(a) * r2);
+        const float q = fmaf(4.5f * c, c, -1.5f * fmaf(r1, r1, r2 * r2));
+        return (float)LD2Q9::w(a) * fmaf(3.0f, c, r0 + q);
+    } else {
+        return R.q5[a] * r0;
+    }
+}
+template <class L>
+__device__ __forceinline__ float lref_e(const LrefK &R, int a, int k)
+{
+    const float r0 = __ldg(R.ref + k);
+    float r1 = 0.f, r2 = 0.f;
+    if constexpr (L::Q == 9) {
+        r1 = __ldg(R.ref + R.Np + k);
+        r2 = __ldg(R.ref + 2 * R.Np + k);
+    }
+    return lref_e_of<L>(R, a, r0, r1, r2);
+}
+
+// the stored value s of population a at node k, decoded: s / sigma + e_a(k)
+template <class L, class T>
+__device__ __forceinline__ float lref_dec(const LrefK &R, const T *plane, int a, int k, float sinv)
+{
+    return fmaf(Dev<T>::get(plane + k), sinv, lref_e<L>(R, a, k));
+}
+// the value to store for deviation d of population a at node k
+template <class L>
+__device__ __forceinline__ float lref_enc(const LrefK &R, float d, int a, int k, float sig)
+{
+    return (d - lref_e<L>(R, a, k)) * sig;
+}
+
+template <class T, int FK, bool W1, bool SR>
+__global__ void __launch_bounds__(kBlock)
+k_lref_step9(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w, float rref,
+             LrefK R, unsigned long long srkey)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y;
+    node_xy(g, i, x, y);
+    const float sig = __ldg(R.scale), sinv = __ldg(R.scale + 1);
+    float d[9];
+    pull_node<LD2Q9>(g, x, y, 0, i, d, [&](int p, int k) { return lref_dec<LD2Q9, T>(R, P.in[p], p, k, sinv); });
+    float Fx = 0.f, Fy = 0.f, Gx = 0.f, Gy = 0.f;
+    if (FK != FK_NONE) {
+        const float Px = field_value_f(F, FK, 0, x, y, 0, i), Py = field_value_f(F, FK, 1, x, y, 0, i);
+        Fx = apre * Px;
+        Fy = apre * Py;
+        Gx = gsum * Px;
+        Gy = gsum * Py;
+    }
+    if (W1) collide9_w1(d, rref, Fx, Fy, Gx, Gy, w);
+    else collide9(d, rref, Fx, Fy, Gx, Gy, w);
+    SRBits rb(srkey, i);
+#pragma unroll
+    for (int a = 0; a < 9; a++) P.out[a][i] = store_dev<T, SR>(lref_enc<LD2Q9>(R, d[a], a, i, sig), rb, a);
+}
+
+template <class T, int SK, bool SR>
+__global__ void __launch_bounds__(kBlock)
+k_lref_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, float apre, float hsum, Coef5f k, Ref5f cref,
+             LrefK R, unsigned long long srkey)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y;
+    node_xy(g, i, x, y);
+    const float sig = __ldg(R.scale), sinv = __ldg(R.scale + 1);
+    float d[5];
+    pull_node<LD2Q5>(g, x, y, 0, i, d, [&](int p, int kk) { return lref_dec<LD2Q5, T>(R, P.in[p], p, kk, sinv); });
+    float Sp = 0.f, H0 = 0.f;
+    if (SK != FK_NONE) {
+        const float Ps = field_value_f(S, SK, 0, x, y, 0, i);
+        Sp = apre * Ps;
+        H0 = hsum * Ps;
+    }
+    collide5u(d, 0.0f, Sp, H0, k);
+    SRBits rb(srkey, i);
+#pragma unroll
+    for (int a = 0; a < 5; a++) P.out[a][i] = store_dev<T, SR>(lref_enc<LD2Q5>(R, d[a] + cref.v[a], a, i, sig), rb, a);
+}
+
+// Stored (s, reference, sigma) -> FP32 deviations d, both in the stored [q][Np] layout.
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_lref_decode(const T *__restrict__ st, Geom g, LrefK R, float *__restrict__ dev)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const float sinv = __ldg(R.scale + 1);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) dev[a * g.Np + i] = lref_dec<L, T>(R, st + a * g.Np, a, i, sinv);
+}
+
+// New reference from FP32 deviations (the node's own zeroth and first
+// moments: then e has the same moments as d) and the per-block largest |d - e|.
+template <class L>
+__global__ void __launch_bounds__(kBlock)
+k_lref_reference(const float *__restrict__ dev, Geom g, LrefK R, float *__restrict__ ref, float *__restrict__ bmax)
+{
+    float m = 0.0f;
+    for (long long n = blockIdx.x * (long long)kBlock + threadIdx.x; n < g.N; n += (long long)gridDim.x * kBlock) {
+        const int i = (int)n;
+        float d[L::Q];
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) {
+            d[a] = dev[a * g.Np + i];
+            r0 += d[a];
+            if constexpr (L::Q == 9) {
+                r1 += (float)L::ex(a) * d[a];
+                r2 += (float)L::ey(a) * d[a];
+            }
+        }
+        ref[i] = r0;
+        if constexpr (L::Q == 9) {
+            ref[g.Np + i] = r1;
+            ref[2 * g.Np + i] = r2;
+        }
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) m = fmaxf(m, fabsf(d[a] - lref_e_of<L>(R, a, r0, r1, r2)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.0f;
+        for (int k = 0; k < kBlock / 32; k++) b = fmaxf(b, wm[k]);
+        bmax[blockIdx.x] = b;
+    }
+}
+
+// sigma = 2^k with the lattice's largest |d - e| times sigma in [8, 16)
+// (k clamped to [-30, 30]; 1 for an exactly uniform state).
+__global__ void k_lref_scale(const float *__restrict__ bmax, int nb, float *__restrict__ scale)
+{
+    float m = 0.0f;
+    for (int k = threadIdx.x; k < nb; k += 32) m = fmaxf(m, bmax[k]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+        int e = 0;
+        int k = 0;
+        if (m > 0.0f && isfinite(m)) {
+            frexpf(m, &e);  // m in [2^(e-1), 2^e)
+            k = min(30, max(-30, 4 - e));
+        }
+        scale[0] = ldexpf(1.0f, k);
+        scale[1] = ldexpf(1.0f, -k);
+    }
+}
+
+// FP32 deviations -> stored s = sigma (d - e), rounded to nearest.
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_lref_encode(const float *__restrict__ dev, Geom g, LrefK R, T *__restrict__ st)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const float sig = __ldg(R.scale);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++)
+        st[a * g.Np + i] = Dev<T>::to_store(lref_enc<L>(R, dev[a * g.Np + i], a, i, sig));
+}
+
+// The plain 16-bit deviations as this encoding: reference 0, sigma 1.
+template <class L>
+__global__ void __launch_bounds__(kBlock) k_lref_reset(Geom g, float *__restrict__ ref, float *__restrict__ scale)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i == 0) {
+        scale[0] = 1.0f;
+        scale[1] = 1.0f;
+    }
+    if (i >= g.N) return;
+#pragma unroll
+    for (int p = 0; p < (L::Q == 9 ? 3 : 1); p++) ref[p * g.Np + i] = 0.0f;
+}
+
+template <class T, bool SR>
+cudaError_t lref_step_ts(int lattice, const LaunchArgs &a, const LrefK &R)
+{
+    const int grid = (a.g.N + kBlock - 1) / kBlock;
+    const float rref = (float)a.rho_ref;
+    const cudaStream_t s = a.stream;
+    const unsigned long long key = a.srkey;
+    if (lattice == LD2Q9::ID) {
+        const Planes<T, 9> P = make_planes<T, 9>(a.fin, a.fout, a.g.Np);
+        const Rates9f w{(float)(a.omega[3] / 12.0), (float)(a.omega[4] / 4.0), (float)(a.omega[5] / 4.0),
+                        (float)(a.omega[6] / 4.0), (float)(a.omega[7] / 4.0), (float)(a.omega[8] / 4.0)};
+        const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre;
+        const bool w1 = a.omega[6] == 1.0 && a.omega[7] == 1.0 && a.omega[8] == 1.0;
+#define LREF9(FKV, W1V) k_lref_step9<T, FKV, W1V, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, gsum, w, rref, R, key)
+        if (w1) {
+            if (a.fkind == FK_NONE) LREF9(FK_NONE, true);
+            else if (a.fkind == FK_CONST) LREF9(FK_CONST, true);
+            else LREF9(FK_GENERAL, true);
+        } else {
+            if (a.fkind == FK_NONE) LREF9(FK_NONE, false);
+            else if (a.fkind == FK_CONST) LREF9(FK_CONST, false);
+            else LREF9(FK_GENERAL, false);
+        }
+#undef LREF9
+    } else if (lattice == LD2Q5::ID) {
+        if (a.vkind == FK_GENERAL) return cudaErrorInvalidValue;
+        const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0, uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
+        const Coef5f k = make_coef5f(a.omega, ux, uy);
+        const float hsum = (float)((a.apre + a.apost) / 10.0), apre = (float)a.apre;
+        Ref5f cref{};
+        double c[5];
+        d2q5_reference_change(a.omega, ux, uy, a.gref, c);
+        for (int q = 0; q < 5; q++) cref.v[q] = (float)c[q];
+        const Planes<T, 5> P = make_planes<T, 5>(a.fin, a.fout, a.g.Np);
+        if (a.fkind == FK_NONE)
+            k_lref_step5<T, FK_NONE, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+        else if (a.fkind == FK_CONST)
+            k_lref_step5<T, FK_CONST, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+        else k_lref_step5<T, FK_GENERAL, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+LrefK lref_k(const Lref &L, const Geom &g)
+{
+    LrefK R;
+    R.ref = L.ref;
+    R.scale = L.scale;
+    R.Np = g.Np;
+    for (int q = 0; q < 5; q++) R.q5[q] = L.q5[q];
+    return R;
+}
+
+template <class T>
+cudaError_t lref_codec_t(int lattice, int encode, const Geom &g, const LrefK &R, float *ref, const void *stored_in,
+                         void *stored_out, const float *dev_in, float *dev_out, cudaStream_t s)
+{
+    // encode: 0 decode, otherwise encode at the current reference and sigma
+    const int grid = (g.N + kBlock - 1) / kBlock;
+    if (lattice == LD2Q9::ID) {
+        if (encode) k_lref_encode<LD2Q9, T><<<grid, kBlock, 0, s>>>(dev_in, g, R, static_cast<T *>(stored_out));
+        else k_lref_decode<LD2Q9, T><<<grid, kBlock, 0, s>>>(static_cast<const T *>(stored_in), g, R, dev_out);
+    } else if (lattice == LD2Q5::ID) {
+        if (encode) k_lref_encode<LD2Q5, T><<<grid, kBlock, 0, s>>>(dev_in, g, R, static_cast<T *>(stored_out));
+        else k_lref_decode<LD2Q5, T><<<grid, kBlock, 0, s>>>(static_cast<const T *>(stored_in), g, R, dev_out);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 void d2q5_batch_coef(const double omega[9], BatchItem &item);
@@ -1638,6 +1926,58 @@ int rp_batch_resident(int lattice, int storage, int tile)
     case 3: return resident_t<__nv_bfloat16>(lattice, tile);
     default: return 0;
     }
+}
+
+cudaError_t lref_step(int lattice, const LaunchArgs &a, const Lref &L)
+{
+    const LrefK R = lref_k(L, a.g);
+    if (a.storage == 2) return a.sround ? lref_step_ts<__half, true>(lattice, a, R) : lref_step_ts<__half, false>(lattice, a, R);
+    if (a.storage == 3)
+        return a.sround ? lref_step_ts<__nv_bfloat16, true>(lattice, a, R) : lref_step_ts<__nv_bfloat16, false>(lattice, a, R);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t lref_decode(int lattice, int storage, const Geom &g, const Lref &L, const void *stored, float *dev,
+                        cudaStream_t s)
+{
+    const LrefK R = lref_k(L, g);
+    if (storage == 2) return lref_codec_t<__half>(lattice, 0, g, R, L.ref, stored, nullptr, nullptr, dev, s);
+    if (storage == 3) return lref_codec_t<__nv_bfloat16>(lattice, 0, g, R, L.ref, stored, nullptr, nullptr, dev, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t lref_encode(int lattice, int storage, const Geom &g, const Lref &L, const float *dev, void *stored,
+                        cudaStream_t s)
+{
+    const LrefK R = lref_k(L, g);
+    if (storage == 2) return lref_codec_t<__half>(lattice, 1, g, R, L.ref, nullptr, stored, dev, nullptr, s);
+    if (storage == 3) return lref_codec_t<__nv_bfloat16>(lattice, 1, g, R, L.ref, nullptr, stored, dev, nullptr, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t lref_reset(int lattice, const Geom &g, const Lref &L, cudaStream_t s)
+{
+    const int grid = std::max(1, (g.N + kBlock - 1) / kBlock);
+    if (lattice == LD2Q9::ID) k_lref_reset<LD2Q9><<<grid, kBlock, 0, s>>>(g, L.ref, L.scale);
+    else if (lattice == LD2Q5::ID) k_lref_reset<LD2Q5><<<grid, kBlock, 0, s>>>(g, L.ref, L.scale);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t lref_rebase(int lattice, int storage, const Geom &g, const Lref &L, float *bmax, const float *dev,
+                        void *stored, cudaStream_t s)
+{
+    if (lattice != LD2Q9::ID && lattice != LD2Q5::ID) return cudaErrorInvalidValue;
+    const LrefK R = lref_k(L, g);
+    const int nb = std::max(1, std::min(kReduceMaxBlocks, (g.N + kBlock - 1) / kBlock));
+    if (lattice == LD2Q9::ID) k_lref_reference<LD2Q9><<<nb, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
+    else k_lref_reference<LD2Q5><<<nb, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
+    k_lref_scale<<<1, 32, 0, s>>>(bmax, nb, L.scale);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (storage == 2) return lref_codec_t<__half>(lattice, 2, g, R, L.ref, nullptr, stored, dev, nullptr, s);
+    if (storage == 3) return lref_codec_t<__nv_bfloat16>(lattice, 2, g, R, L.ref, nullptr, stored, dev, nullptr, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lbmk

@@ -173,6 +173,9 @@ int lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int count)
         if (ctxs[i]->sround)
             return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d rounds stochastically (single-lattice "
                                               "steps only)", i);
+        if (ctxs[i]->lref_every)
+            return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: context %d stores at a local reference "
+                                              "(single-lattice steps only)", i);
         if (ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->device != ctxs[0]->device)
             return bfail(nullptr, LBM_EINVAL, "lbm_batch_create: contexts differ in stream or device");
         for (int j = 0; j < i; j++)
@@ -333,6 +336,10 @@ int refresh_descriptors(lbm_batch *b, int *parity)
     for (int k = 0; k < kReadbackSlots; k++)
         if (b->read_recorded[k])
             BCK(cudaStreamWaitEvent(b->stream, b->ev_read[k], 0), "lbm_batch_step: wait for a readback");
+    for (int i = 0; i < b->count; i++)
+        if (b->ctx[i]->lref_every || b->ctx[i]->sround)
+            return bfail(b, LBM_EINVAL, "lbm_batch_step: member %d now rounds stochastically or stores at a local "
+                                        "reference (single-lattice steps only)", i);
     for (int i = 0; i < b->count; i++) {
         const lbm_ctx *c = b->ctx[i];
         BatchItem &it = b->h_items[i];

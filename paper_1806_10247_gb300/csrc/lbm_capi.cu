@@ -132,6 +132,86 @@ lbmk::Ref5 ref5(const lbm_ctx *c)
     return r;
 }
 
+lbmk::Lref lref_of(const lbm_ctx *c)
+{
+    lbmk::Lref L{};
+    L.ref = c->lref_ref;
+    L.scale = c->lref_aux;
+    // D2Q5: the Eq. 39 equilibrium per unit scalar at the uniform velocity
+    double ux = 0.0, uy = 0.0;
+    if (c->vel.kind == FK_CONST) {
+        ux = c->vel.d.cval[0];
+        uy = c->vel.d.cval[1];
+    }
+    const double t = 1.0 / 3.0;
+    L.q5[0] = (float)(t - ux * ux - uy * uy);
+    L.q5[1] = (float)(0.5 * (t + ux * ux + ux));
+    L.q5[2] = (float)(0.5 * (t + uy * uy + uy));
+    L.q5[3] = (float)(0.5 * (t + ux * ux - ux));
+    L.q5[4] = (float)(0.5 * (t + uy * uy - uy));
+    return L;
+}
+
+int lref_decode_state(lbm_ctx *c)
+{
+    CK(lref_decode(c->lattice, c->storage, c->g, lref_of(c), c->A, c->lref_dev, c->stream), "decode kernel");
+    c->launches++;
+    return LBM_OK;
+}
+
+int lref_encode_state(lbm_ctx *c)
+{
+    const int rc = wait_readers(c, c->A);
+    if (rc != LBM_OK) return rc;
+    CK(lref_rebase(c->lattice, c->storage, c->g, lref_of(c), c->lref_aux + 2, c->lref_dev, c->A, c->stream),
+       "rebase kernels");
+    c->launches += 3;
+    return LBM_OK;
+}
+
+LrefView::LrefView(lbm_ctx *cc, bool decode) : c(cc)
+{
+    if (!c->lref_every) return;
+    if (decode && c->initialised) rc = lref_decode_state(c);
+    A0 = c->A;
+    st0 = c->storage;
+    el0 = c->elem;
+    c->A = reinterpret_cast<double *>(c->lref_dev);
+    c->storage = LBM_FP32_DEV;
+    c->elem = 4;
+    on = true;
+}
+
+void LrefView::restore()
+{
+    if (!on) return;
+    c->A = A0;
+    c->storage = st0;
+    c->elem = el0;
+    on = false;
+}
+
+// Back to the plain 16-bit deviations (reference 0, sigma 1).
+static int lref_off(lbm_ctx *c)
+{
+    if (c->initialised) {
+        const int rc = lref_decode_state(c);
+        if (rc != LBM_OK) return rc;
+    }
+    CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
+    if (c->initialised) {
+        const int rc = wait_readers(c, c->A);
+        if (rc != LBM_OK) return rc;
+        CK(lref_encode(c->lattice, c->storage, c->g, lref_of(c), c->lref_dev, c->A, c->stream), "encode kernel");
+        c->launches++;
+    }
+    c->lref_every = 0;
+    c->lref_since = 0;
+    c->version++;
+    CK(cudaStreamSynchronize(c->stream), "lref off");
+    return LBM_OK;
+}
+
 // D2Q5 reference populations for reduced-precision storage: the equilibrium
 // at (rho_ref, u) for a periodic lattice whose advecting velocity u is
 // uniform (the step maps it to itself: the stored deviations then carry the
@@ -405,6 +485,9 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->force.fdev);
     cudaFree(c->vel.fdev);
     cudaFree(c->stage);
+    cudaFree(c->lref_ref);
+    cudaFree(c->lref_aux);
+    cudaFree(c->lref_dev);
     delete c;
 }
 
@@ -423,6 +506,7 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
         const int rc = wait_readers(c, nullptr);
         if (rc != LBM_OK) return rc;
     }
+    LrefView view(c, false);  // local reference: the FP32 fill, then the encoding
     double uu[3] = {0.0, 0.0, 0.0};
     if (u0)
         for (int d = 0; d < c->dim; d++) uu[d] = u0[d];
@@ -459,6 +543,12 @@ int lbm_init_equilibrium(lbm_ctx *c, double rho0, const double u0[3], const doub
            "equilibrium kernel");
         c->launches += 1;
     }
+    view.restore();
+    if (c->lref_every) {
+        const int rc = lref_encode_state(c);
+        if (rc != LBM_OK) return rc;
+        c->lref_since = 0;
+    }
     CK(cudaStreamSynchronize(c->stream), "lbm_init_equilibrium");
     c->t = 0;
     c->initialised = true;
@@ -491,8 +581,36 @@ int lbm_set_velocity(lbm_ctx *c, const lbm_field *u)
     c->err.clear();
     c->version++;
     if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_velocity: only for the scalar lattice");
+    if (c->lref_every && c->initialised) {
+        // the encoding depends on the uniform velocity: decode with the old one
+        const int rd = lref_decode_state(c);
+        if (rd != LBM_OK) return rd;
+    }
     int rc = upload_field(c, u, 2, c->vel, "lbm_set_velocity");
-    if (rc != LBM_OK || c->storage == LBM_FP64 || !c->initialised || c->vel.kind != FK_GENERAL) return rc;
+    if (rc != LBM_OK) return rc;
+    if (c->lref_every) {
+        if (c->vel.kind == FK_GENERAL) {
+            // a velocity field ends the local-reference encoding: plain deviations
+            CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
+            if (c->initialised) {
+                rc = wait_readers(c, c->A);
+                if (rc != LBM_OK) return rc;
+                CK(lref_encode(c->lattice, c->storage, c->g, lref_of(c), c->lref_dev, c->A, c->stream), "encode");
+                c->launches++;
+            }
+            c->lref_every = 0;
+            c->lref_since = 0;
+        } else {
+            if (c->initialised) {
+                rc = lref_encode_state(c);
+                if (rc != LBM_OK) return rc;
+                c->lref_since = 0;
+            }
+            CK(cudaStreamSynchronize(c->stream), "lbm_set_velocity");
+            return LBM_OK;
+        }
+    }
+    if (c->storage == LBM_FP64 || !c->initialised || c->vel.kind != FK_GENERAL) return rc;
     // A velocity field needs the rest-state reference: re-express the stored
     // deviations (gather with the old reference, scatter with the new one).
     double rest[5] = {c->rho_ref / 3.0, c->rho_ref / 6.0, c->rho_ref / 6.0, c->rho_ref / 6.0, c->rho_ref / 6.0};
@@ -549,6 +667,49 @@ int lbm_set_stochastic_rounding(lbm_ctx *c, int on, unsigned long long seed)
     return LBM_OK;
 }
 
+int lbm_set_local_reference(lbm_ctx *c, int every)
+{
+    if (!c) return LBM_EINVAL;
+    c->err.clear();
+    if (c->storage != LBM_FP16_DEV && c->storage != LBM_BF16_DEV)
+        return fail(c, LBM_EINVAL, "lbm_set_local_reference: only for FP16 / BF16 deviation storage");
+    if (c->lattice != LBM_D2Q9 && c->lattice != LBM_D2Q5_CDE)
+        return fail(c, LBM_EINVAL, "lbm_set_local_reference: D2Q9 and D2Q5 lattices only");
+    if (every < 0) return fail(c, LBM_EINVAL, "lbm_set_local_reference: every < 0");
+    if (every > 0 && c->lattice == LBM_D2Q5_CDE && c->vel.kind == FK_GENERAL)
+        return fail(c, LBM_EINVAL, "lbm_set_local_reference: the scalar lattice needs a uniform advecting velocity");
+    {
+        const int rc = wait_readers(c, nullptr);
+        if (rc != LBM_OK) return rc;
+    }
+    if (every == 0) return c->lref_every ? lref_off(c) : LBM_OK;
+    if (!c->lref_every) {
+        const int nref = c->lattice == LBM_D2Q9 ? 3 : 1;
+        const size_t np = (size_t)c->g.Np;
+        if (!c->lref_ref) CK(cudaMalloc(&c->lref_ref, nref * np * sizeof(float)), "cudaMalloc(local reference)");
+        if (!c->lref_aux) CK(cudaMalloc(&c->lref_aux, (2 + (size_t)lbmk::kReduceMaxBlocks) * sizeof(float)),
+                             "cudaMalloc(local reference scale)");
+        if (!c->lref_dev) CK(cudaMalloc(&c->lref_dev, (size_t)c->q * np * sizeof(float)),
+                             "cudaMalloc(local reference FP32 state)");
+        // the plain deviations are this encoding at reference 0 and sigma 1
+        CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
+        c->lref_every = every;
+        if (c->initialised) {
+            int rc = lref_decode_state(c);
+            if (rc == LBM_OK) rc = lref_encode_state(c);
+            if (rc != LBM_OK) {
+                c->lref_every = 0;
+                return rc;
+            }
+        }
+    }
+    c->lref_every = every;
+    c->lref_since = 0;
+    c->version++;
+    CK(cudaStreamSynchronize(c->stream), "lbm_set_local_reference");
+    return LBM_OK;
+}
+
 int lbm_step(lbm_ctx *c, long n)
 {
     NvtxRange nvtx_("lbm_step");
@@ -564,7 +725,8 @@ int lbm_step(lbm_ctx *c, long n)
         const int rc = wait_readers(c, n == 1 ? c->B : nullptr);
         if (rc != LBM_OK) return rc;
     }
-    if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty() && !c->sround) {
+    if (n >= 2 && n <= 2147483647L && c->lattice == LBM_D2Q9 && !c->env && c->env_tab.empty() && !c->sround &&
+        !c->lref_every) {
         // a small lattice with a constant force: all n steps in one cluster launch
         double *out = (n & 1) ? c->B : c->A;
         LaunchArgs a = launch_args(c, c->A, out, 1.0, 1.0);
@@ -588,7 +750,9 @@ int lbm_step(lbm_ctx *c, long n)
         envelope_pair(c, c->t, apre, apost);
         LaunchArgs a = launch_args(c, c->A, c->B, apre, apost);
         cudaError_t e;
-        if (c->storage != LBM_FP64) {
+        if (c->lref_every) {
+            e = lref_step(c->lattice, a, lref_of(c));
+        } else if (c->storage != LBM_FP64) {
             e = rp_step(c->lattice, a);
         } else {
             switch (c->lattice) {
@@ -604,6 +768,13 @@ int lbm_step(lbm_ctx *c, long n)
         c->A = c->B;
         c->B = tmp;
         c->t++;
+        if (c->lref_every && ++c->lref_since >= c->lref_every) {
+            // rebuild the local reference from the state
+            int rc = lref_decode_state(c);
+            if (rc == LBM_OK) rc = lref_encode_state(c);
+            if (rc != LBM_OK) return rc;
+            c->lref_since = 0;
+        }
     }
     return LBM_OK;
 }
@@ -617,6 +788,8 @@ int lbm_moments(lbm_ctx *c, double *rho, double *u, int where, int half_forced)
     if (rho == nullptr || (c->lattice != LBM_D2Q5_CDE && u == nullptr))
         return fail(c, LBM_EINVAL, "lbm_moments: NULL output");
     if (where != 0 && where != 1) return fail(c, LBM_EINVAL, "lbm_moments: where must be 0 or 1");
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     double apre, apost;
     envelope_pair(c, c->t, apre, apost);
     LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
@@ -667,6 +840,8 @@ int lbm_strain_rate(lbm_ctx *c, double rho0, double *S, int where)
     if (S == nullptr) return fail(c, LBM_EINVAL, "lbm_strain_rate: NULL output");
     if (where != 0 && where != 1) return fail(c, LBM_EINVAL, "lbm_strain_rate: where must be 0 or 1");
     if (!(rho0 > 0.0)) return fail(c, LBM_EINVAL, "lbm_strain_rate: rho0 must be positive");
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     double apre, apost;
     envelope_pair(c, c->t, apre, apost);
     LaunchArgs a = launch_args(c, c->A, nullptr, apre, apost);
@@ -705,6 +880,8 @@ int lbm_set_source_from_strain(lbm_ctx *scalar, lbm_ctx *flow, double rho0, doub
         return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: lattices on different streams or devices");
     if (!flow->initialised) return fail(scalar, LBM_ESTATE, "lbm_set_source_from_strain: flow not initialised");
     if (!(rho0 > 0.0)) return fail(scalar, LBM_EINVAL, "lbm_set_source_from_strain: rho0 must be positive");
+    LrefView fview(flow, true);
+    if (fview.rc != LBM_OK) return fail(scalar, fview.rc, "lbm_set_source_from_strain: %s", flow->err.c_str());
     const size_t N = (size_t)scalar->g.N;
     DeviceField &out = scalar->force;
     const bool want_f = scalar->storage != LBM_FP64;
@@ -759,6 +936,8 @@ int lbm_reduce(lbm_ctx *c, double out[5])
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_reduce: populations not initialised");
     if (!out) return fail(c, LBM_EINVAL, "lbm_reduce: out is NULL");
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     if (!c->snap) {
         const int ncomp = c->lattice == LBM_D2Q5_CDE ? 1 : c->dim;
         CK(cudaMalloc(&c->snap, (size_t)ncomp * c->g.N * sizeof(double)), "cudaMalloc(snapshot)");
@@ -794,6 +973,8 @@ int lbm_l2_error(lbm_ctx *c, const double *ref, int where, int field, int half_f
     const bool scalar = c->lattice == LBM_D2Q5_CDE;
     if (field != 0 && (field != 1 || scalar))
         return fail(c, LBM_EINVAL, "lbm_l2_error: field must be 0 (rho or phi) or 1 (u, flow lattices)");
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     const size_t N = (size_t)c->g.N;
     const size_t n = field == 0 ? N : (size_t)c->dim * N;
     // The field (and a host reference) go to the scratch buffer B (FP64) or the
@@ -836,6 +1017,8 @@ int lbm_get_populations(lbm_ctx *c, double *dst, size_t count, int where, long *
     c->err.clear();
     if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations: populations not initialised");
     if (!dst || count != (size_t)c->q * c->g.N) return fail(c, LBM_EINVAL, "lbm_get_populations: count must be q*N");
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     if (step_out) *step_out = c->t;
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -880,6 +1063,7 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
     const size_t N = (size_t)c->g.N;
     const cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->storage != LBM_FP64) {
+        LrefView view(c, false);  // local reference: the FP32 scatter, then the encoding
         const double *plain = where ? src : nullptr;
         if (!plain) {
             int rc = ensure_stage(c);
@@ -889,6 +1073,12 @@ int lbm_set_populations(lbm_ctx *c, const double *src, size_t count, int where, 
         }
         CK(rp_scatter(c->lattice, c->storage, c->g, c->rho_ref, ref5(c), plain, c->A, c->stream), "scatter kernel");
         c->launches++;
+        view.restore();
+        if (c->lref_every) {
+            const int rc = lref_encode_state(c);
+            if (rc != LBM_OK) return rc;
+            c->lref_since = 0;
+        }
         CK(cudaStreamSynchronize(c->stream), "lbm_set_populations");
         c->t = step;
         c->initialised = true;

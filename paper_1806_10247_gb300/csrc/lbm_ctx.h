@@ -27,6 +27,16 @@ struct lbm_ctx {
     double rho_ref = 1.0; // reduced-precision storage: reference of the deviations
     int sround = 0;       // 16-bit storage: stochastic rounding of the stored deviations
     unsigned long long sr_seed = 0;
+    // 16-bit D2Q9 / D2Q5 storage at a per-node reference (lbmk::Lref): steps
+    // between rebuilds of the reference (0: off, the plain deviations), steps
+    // since the last one, the reference [1 or 3][Np], sigma, 1 / sigma and the
+    // rebuild's block maxima, and q*Np floats of FP32 deviations (rebuilds
+    // and every read or write of the state go through them)
+    int lref_every = 0;
+    int lref_since = 0;
+    float *lref_ref = nullptr;
+    float *lref_aux = nullptr;
+    float *lref_dev = nullptr;
     // D2Q5 reduced-precision storage: reference populations of the deviations
     // (lbmk::Ref5; set at lbm_init_equilibrium)
     double gref[5] = {0, 0, 0, 0, 0};
@@ -88,6 +98,28 @@ int wait_readers(lbm_ctx *c, const void *buf);
 lbmk::Ref5 ref5(const lbm_ctx *c);
 // Key of step t's stochastic-rounding bits (seed mixed, step in the high bits).
 unsigned long long sr_step_key(unsigned long long seed, long t);
+// The local-reference encoding of a 16-bit context (lbmk::Lref).
+lbmk::Lref lref_of(const lbm_ctx *c);
+// Local-reference contexts: the state decoded to FP32 deviations (lref_dev),
+// and rebuilt from them (new reference and sigma, stored values into A).
+int lref_decode_state(lbm_ctx *c);
+int lref_encode_state(lbm_ctx *c);
+// For the length of a scope a local-reference context looks like an FP32
+// deviation context whose stored buffer is lref_dev (decoded on entry when
+// `decode`), so that the FP32 read and write paths serve it; a write path
+// then calls lref_encode_state after restore().
+struct LrefView {
+    lbm_ctx *c;
+    double *A0 = nullptr;
+    int st0 = 0, el0 = 0;
+    bool on = false;
+    int rc = 0;
+    LrefView(lbm_ctx *cc, bool decode);
+    void restore();
+    ~LrefView() { restore(); }
+    LrefView(const LrefView &) = delete;
+    LrefView &operator=(const LrefView &) = delete;
+};
 // Launch arguments of the context's kernels.
 lbmk::LaunchArgs launch_args(const lbm_ctx *c, const double *fin, double *fout, double apre, double apost);
 

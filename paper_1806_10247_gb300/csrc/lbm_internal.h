@@ -211,4 +211,26 @@ cudaError_t scatter_to_stored(int lattice, const Geom &g, const double *plain, d
 cudaError_t gather_from_stored(int lattice, const Geom &g, const double *stored, double *plain,
                                cudaStream_t s);
 
+// 16-bit storage at a per-node reference (k_rp.cu): stored s = sigma (d - e),
+// e the deviation of a low-order equilibrium at the node's reference.
+struct Lref {
+    float *ref;    // device [1 or 3][Np]: dphi (D2Q5), or drho, jx, jy (D2Q9)
+    float *scale;  // device [2]: sigma (a power of two), 1 / sigma
+    float q5[5];   // D2Q5: the equilibrium per unit scalar at the uniform velocity
+};
+// One step of a D2Q9 or D2Q5 (uniform velocity) lattice in this encoding.
+cudaError_t lref_step(int lattice, const LaunchArgs &a, const Lref &L);
+// Stored values -> FP32 deviations (the FP32 forms' stored layout).
+cudaError_t lref_decode(int lattice, int storage, const Geom &g, const Lref &L, const void *stored, float *dev,
+                        cudaStream_t s);
+// The plain 16-bit deviations as this encoding (reference 0, every sigma 1).
+cudaError_t lref_reset(int lattice, const Geom &g, const Lref &L, cudaStream_t s);
+// FP32 deviations -> stored values at the current reference and sigma.
+cudaError_t lref_encode(int lattice, int storage, const Geom &g, const Lref &L, const float *dev, void *stored,
+                        cudaStream_t s);
+// A new reference and sigma from FP32 deviations, and the stored values at
+// them; bmax: kReduceMaxBlocks floats of scratch.
+cudaError_t lref_rebase(int lattice, int storage, const Geom &g, const Lref &L, float *bmax, const float *dev,
+                        void *stored, cudaStream_t s);
+
 }  // namespace lbmk

@@ -72,6 +72,9 @@ extern "C" int lbm_reduce_sums_noalloc(lbm_ctx *c, double out[4])
     double *scratch = nullptr;
     int rc = scratch_on(c, c->device, &scratch);
     if (rc != LBM_OK) return rc;
+    // a local-reference context is read through its FP32 deviations (no allocation)
+    LrefView view(c, true);
+    if (view.rc != LBM_OK) return view.rc;
     // Every partial slot that the final pass reads is written by its block
     // first, and the result slot is written by the final pass, so nothing has
     // to be cleared between calls.

@@ -36,7 +36,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init_equilibrium"
            "lbm_batch_autotune", "lbm_batch_moments", "lbm_strain_rate", "lbm_set_source_from_strain",
            "lbm_batch_moments_packed", "lbm_batch_wait_moments", "lbm_debug_poison", "lbm_batch_step_read",
            "lbm_l2_error", "lbm_device_info", "lbm_probe_fp64", "lbm_probe_last_error",
-           "lbm_set_stochastic_rounding")
+           "lbm_set_stochastic_rounding", "lbm_set_local_reference")
 
 
 class LBMError(RuntimeError):
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
     L.lbm_set_envelope_table.argtypes = [vp, dp, ctypes.c_long, ctypes.c_double]
     L.lbm_step.argtypes = [vp, ctypes.c_long]
     L.lbm_set_stochastic_rounding.argtypes = [vp, ip, ctypes.c_ulonglong]
+    L.lbm_set_local_reference.argtypes = [vp, ip]
     L.lbm_moments.argtypes = [vp, vp, vp, ip, ip]
     L.lbm_reduce.argtypes = [vp, dp]
     L.lbm_reduce_sums_noalloc.argtypes = [vp, dp]
@@ -293,6 +294,11 @@ class Lattice:
         """16-bit storage: round the stored deviations stochastically (seeded,
         counter-based) instead of to nearest."""
         self._check(self._L.lbm_set_stochastic_rounding(self.h, int(bool(on)), int(seed) & (2 ** 64 - 1)))
+
+    def set_local_reference(self, every):
+        """16-bit D2Q9 / D2Q5 storage at a per-node reference rebuilt every
+        `every` steps (0: the plain deviations); lbm_set_local_reference."""
+        self._check(self._L.lbm_set_local_reference(self.h, int(every)))
 
     # -- stepping and output -----------------------------------------------
     def step(self, n=1):

@@ -1,0 +1,237 @@
+"""16-bit storage at a per-node reference (lbm_set_local_reference): the
+stored value of a population is sigma (d - e), d the FP32 forms' deviation and
+e that of a low-order equilibrium at the node's FP32 reference, rebuilt
+every few steps.  Checked against the FP64 oracle (errors far below the plain
+16-bit forms'), for conversions in and out, the refusals, and on the two
+workloads where plain 16-bit storage fails the 1e-4 target: the Poiseuille
+channel's steady profile and the scalar sweep's convergence order."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1806_10247_gb300 import lbm
+from paper_1806_10247_gb300 import workloads as W
+from tests.gpu_helpers import oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = {"fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
+
+
+def _l2(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+RESULTS = {}
+
+
+def _record(key, val):
+    RESULTS[key] = val
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out and os.path.isdir(out):
+        with open(os.path.join(out, "lref_errors.json"), "w") as f:
+            json.dump(RESULTS, f, indent=1, sort_keys=True)
+
+
+def _d2q9(shape, wall, seed, amp=0.02):
+    """Smooth low-Mach flow: sinusoidal velocity (vanishing at walls) and
+    density, a smooth force."""
+    rng = np.random.default_rng(seed)
+    nx, ny, _ = shape
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
+    ph = rng.uniform(0, 2 * math.pi, 4)
+    u = np.stack([amp * np.sin(ky * y + ph[0]) + 0.25 * amp * np.cos(kx * x + ph[1]),
+                  0.5 * amp * np.sin(kx * x + ph[2])])
+    # vanishing at the walls (halfway between the wall nodes and the walls)
+    if wall[0]:
+        u = u * np.sin(math.pi * (x + 0.5) / nx)
+    if wall[1]:
+        u = u * np.sin(math.pi * (y + 0.5) / ny)
+    u = u.reshape(2, -1)
+    rho = (1.0 + 0.002 * np.cos(kx * x + ph[3]) * np.cos(ky * y)).reshape(-1)
+    xs, ys = np.arange(nx), np.arange(ny)
+    tables = [(1e-5 * (1 + 0.5 * np.sin(kx * xs)), 1 + 0.3 * np.cos(ky * ys), np.array([1.0])),
+              (3e-6 * (1 + 0.5 * np.cos(kx * xs)), 1 + 0.3 * np.sin(ky * ys), np.array([1.0]))]
+    return W.Workload(name="lref9", lattice=W.D2Q9, shape=shape, wall=wall, omega=W.d2q9_omega(0.7),
+                      rho0=rho, u0=u, tables=tables)
+
+
+def _d2q5(shape, wall, seed):
+    """Smooth scalar: a sinusoidal variation, a uniform velocity, a smooth source."""
+    rng = np.random.default_rng(seed)
+    nx, ny, _ = shape
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    kx, ky = 2 * math.pi / nx, 2 * math.pi / ny
+    ph = rng.uniform(0, 2 * math.pi, 2)
+    phi = (1.0 + 0.01 * np.sin(kx * x + ph[0]) * np.sin(ky * y + ph[1])).reshape(-1)
+    xs, ys = np.arange(nx), np.arange(ny)
+    tables = [(1e-5 * np.sin(kx * xs + ph[1]), np.cos(ky * ys), np.array([1.0]))]
+    return W.Workload(name="lref5", lattice=W.D2Q5, shape=shape, wall=wall, omega=W.d2q5_omega(0.8),
+                      rho0=phi, u0=(0.02, -0.01, 0.0), tables=tables)
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_conversion_in_and_out(form):
+    """Turning the encoding on and off keeps the state to the plain 16-bit
+    storage's own rounding (the encoding itself is finer)."""
+    w = _d2q9((12, 10, 1), (0, 1, 0), 3)
+    G = lbm.from_workload(w, storage=STORAGES[form])
+    G.step(3)
+    f0 = G.get_populations()
+    G.set_local_reference(8)
+    f1 = G.get_populations()
+    eps = 2.0 ** -11 if form == "fp16" else 2.0 ** -8
+    _record(f"convert_in_{form}", float(np.abs(f1 - f0).max()))
+    assert np.abs(f1 - f0).max() <= eps * 0.01, np.abs(f1 - f0).max()
+    G.set_local_reference(0)
+    f2 = G.get_populations()
+    _record(f"convert_out_{form}", float(np.abs(f2 - f0).max()))
+    assert np.abs(f2 - f0).max() <= eps * 0.1, np.abs(f2 - f0).max()
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("lattice,shape,wall,every", [
+    (W.D2Q9, (24, 20, 1), (0, 0, 0), 16),
+    (W.D2Q9, (24, 20, 1), (0, 1, 0), 16),
+    (W.D2Q9, (21, 22, 1), (1, 1, 0), 4),   # a closed box: sound waves change the state fast
+    (W.D2Q5, (24, 20, 1), (0, 0, 0), 16),
+    (W.D2Q5, (20, 17, 1), (0, 1, 0), 16),
+])
+def test_against_oracle(form, lattice, shape, wall, every):
+    """500 steps of a smooth low-Mach state against the FP64 oracle: the
+    velocity (D2Q9) or the scalar's variation (D2Q5) in relative l2, recorded
+    beside the plain 16-bit and the FP32 forms'; the encoded form must be at
+    least twice closer than the plain one.  The rebuild interval must be short
+    against the time over which the state changes by its non-equilibrium part
+    (in a closed box the sound waves: every 4 steps there, 16 elsewhere)."""
+    seed = 11 + shape[0] + 7 * wall[0] + 3 * wall[1]
+    w = _d2q9(shape, wall, seed) if lattice == W.D2Q9 else _d2q5(shape, wall, seed)
+    steps = 500
+    R = oracle_from_workload(w)
+    R.run(steps)
+    errs = {}
+    for name, st, ev in (("lref", STORAGES[form], every), ("plain", STORAGES[form], 0), ("fp32", lbm.FP32_DEV, 0)):
+        G = lbm.from_workload(w, storage=st)
+        if ev:
+            G.set_local_reference(ev)
+        G.step(steps)
+        if lattice == W.D2Q9:
+            _, ug = G.moments()
+            _, ur = R.moments()
+            errs[name] = _l2(ug, ur)
+        else:
+            pg, pr = G.moments(), R.moments()
+            errs[name] = _l2(pg - pr.mean(), pr - pr.mean())
+        G.reduce()  # the reductions read the encoded state too
+    lat = "d2q9" if lattice == W.D2Q9 else "d2q5"
+    _record(f"{lat}_{form}_{shape[0]}x{shape[1]}_walls{''.join(map(str, wall))}", errs)
+    assert np.isfinite(errs["lref"])
+    assert errs["lref"] <= 0.5 * errs["plain"], errs
+
+
+def test_reads_agree_with_the_populations():
+    """Moments, the reductions and the l2 error of an encoded state agree with
+    what its populations give."""
+    w = _d2q9((16, 8, 1), (0, 1, 0), 5)
+    G = lbm.from_workload(w, storage=lbm.FP16_DEV)
+    G.set_local_reference(4)
+    G.step(10)
+    f = G.get_populations()
+    rho, u = G.moments(half_forced=False)
+    assert np.allclose(rho, f.sum(0), rtol=0, atol=1e-12)
+    r = G.reduce()
+    assert abs(r[0] - f.sum()) <= 1e-9 * abs(f.sum())
+    _, _, rel = G.l2_error(rho, field=0)
+    assert rel <= 1e-15
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_stochastic_rounding_and_seeds(form):
+    """Stochastic rounding composes with the encoding: seeded, reproducible."""
+    w = _d2q9((16, 12, 1), (0, 0, 0), 9, amp=0.02)
+    runs = []
+    for _ in range(2):
+        G = lbm.from_workload(w, storage=STORAGES[form])
+        G.set_local_reference(8)
+        G.set_stochastic_rounding(True, 21)
+        G.step(20)
+        runs.append(G.get_populations())
+    assert np.array_equal(runs[0], runs[1])
+
+
+def test_refusals():
+    w = _d2q9((8, 6, 1), (0, 0, 0), 1)
+    G = lbm.from_workload(w, storage=lbm.FP32_DEV)
+    with pytest.raises(lbm.LBMError) as e:
+        G.set_local_reference(8)
+    assert e.value.code == lbm.EINVAL
+    K = lbm.from_workload(W.kolmogorov(shape=(8, 6, 4)), storage=lbm.FP16_DEV)
+    with pytest.raises(lbm.LBMError) as e:
+        K.set_local_reference(8)
+    assert e.value.code == lbm.EINVAL
+    H = lbm.from_workload(w, storage=lbm.FP16_DEV)
+    with pytest.raises(lbm.LBMError) as e:
+        H.set_local_reference(-1)
+    assert e.value.code == lbm.EINVAL
+    H.set_local_reference(8)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Batch([H])
+    assert e.value.code == lbm.EINVAL
+
+
+def test_scalar_velocity_field_returns_to_plain_deviations():
+    """A velocity field on an encoded scalar lattice converts it back to the
+    plain deviations (the encoding needs a uniform velocity); the state is kept."""
+    w = _d2q5((12, 8, 1), (0, 0, 0), 4)
+    G = lbm.from_workload(w, storage=lbm.FP16_DEV)
+    G.set_local_reference(8)
+    G.step(5)
+    p0 = G.moments()
+    N = w.nodes
+    G.set_velocity(full=np.stack([np.full(N, 0.03), np.full(N, -0.02)]))
+    p1 = G.moments()
+    assert np.abs(p1 - p0).max() <= 2.0 ** -11 * 0.2
+    G.step(5)
+    with pytest.raises(lbm.LBMError) as e:
+        G.set_local_reference(8)
+    assert e.value.code == lbm.EINVAL
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_poiseuille_reaches_the_fp64_steady_profile(form):
+    """The channel of the 1e-4 target (F = 1e-6: a per-step increment below
+    the plain 16-bit step): from rest to within 1e-4 relative l2 of the FP64
+    path's steady profile (plain FP16 stalls at ~0.1)."""
+    w = W.poiseuille()
+    F = lbm.from_workload(w)
+    F.step(30000)
+    _, uref = F.moments()
+    G = lbm.from_workload(w, storage=STORAGES[form])
+    G.set_local_reference(32)
+    G.step(30000)
+    _, ug = G.moments()
+    err = _l2(ug, uref)
+    _record(f"poiseuille_{form}_30000_steps", err)
+    assert err <= (1e-4 if form == "fp16" else 1e-3), err
+
+
+def test_scalar_sweep_keeps_second_order():
+    """The scalar sweep's manufactured-source problem at 32^2, 64^2, 128^2 with
+    FP16 storage at a local reference: the l2 error against the closed form
+    falls at order ~2 (plain FP16: -0.38, -3.92)."""
+    errs = []
+    for c in W.cde_sweep_params(sizes=(32, 64, 128)):
+        w = W.cde_workload(c)
+        G = lbm.from_workload(w, storage=lbm.FP16_DEV, envelope_steps=c.T + 4)
+        G.set_local_reference(16)
+        G.step(c.T)
+        phi = G.moments().reshape(c.N, c.N)
+        psi = W.cde_closed_form(c, c.T)
+        errs.append(float(np.sqrt(np.sum((phi - 1.0 - psi) ** 2) / np.sum(psi ** 2))))
+    orders = [math.log(errs[k] / errs[k + 1], 2) for k in range(len(errs) - 1)]
+    _record("cde_sweep_fp16_32_64_128", {"l2": errs, "orders": orders})
+    assert all(o >= 1.8 for o in orders), (errs, orders)
