@@ -856,7 +856,11 @@ def storage_study(lbm, stream, hbm, hbm_src, peak, steps, warmup, n=512, run_ste
     return out
 
 
-def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp16_sr", "bf16_sr")):
+LREF_EVERY = {"poiseuille": 32, "cde": 16}  # rebuild intervals of the local-reference forms
+
+
+def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp16_sr", "bf16_sr", "fp16_lref",
+                                            "bf16_lref", "fp16_lref_sr", "bf16_lref_sr")):
     """The metric's second half: wall time to the solution criterion.
     * config 1 (Poiseuille D2Q9 3 x 33), FP64: steps until
       max |u(t) - u(t-100)| < 1e-12 (checked every 100 steps with lbm_reduce);
@@ -871,7 +875,10 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp1
       closed form and the convergence order over the sweep, per storage form
       (the 16-bit forms show how far their rounding moves the order).
     The *_sr forms are the 16-bit storages with stochastic rounding (seed
-    10247; single-lattice launches, one per step)."""
+    10247; single-lattice launches, one per step); the *_lref forms store them
+    at a per-node reference (lbm_set_local_reference, rebuilt every 32 steps
+    for the channel and 16 for the scalar sweep; single-lattice launches plus
+    the rebuild's kernels); *_lref_sr both."""
     import torch
 
     codes = {"fp64": lbm.FP64, "fp32": lbm.FP32_DEV, "fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
@@ -906,6 +913,8 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp1
         L = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[st.split("_")[0]])
         if st.endswith("_sr"):
             L.set_stochastic_rounding(True, 10247)
+        if "_lref" in st:
+            L.set_local_reference(LREF_EVERY["poiseuille"])
         L.reduce()
         torch_sync(stream)
         t0 = time.perf_counter()
@@ -921,7 +930,7 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp1
             "steps": steps, "seconds": sec, "l2_vs_fp64_steady": err, "reached": err <= 1e-4,
             "criterion": "relative l2 (Eq. sca) of u against the FP64 steady field <= 1e-4 (lbm_l2_error every "
                          "100 steps, reference on the device)",
-            "launch": how if not st.endswith("_sr") else "lbm_step(100) between checks (one launch per step)"}
+            "launch": how if st.split("_")[-1] not in ("sr", "lref") else "lbm_step(100) between checks (one launch per step)"}
         L.close()
     for st in storages:
         cases = W.cde_sweep_params()
@@ -931,9 +940,11 @@ def time_to_solution(lbm, stream, storages=("fp64", "fp32", "fp16", "bf16", "fp1
             G = lbm.from_workload(wc, stream=stream.cuda_stream, envelope_steps=c.T + 2,
                                   storage=codes[st.split("_")[0]])
             Bt = None
+            if "_lref" in st:
+                G.set_local_reference(LREF_EVERY["cde"])
             if st.endswith("_sr"):
                 G.set_stochastic_rounding(True, 10247)
-            else:
+            if st.split("_")[-1] not in ("sr", "lref"):
                 Bt = lbm.Batch([G])
                 Bt.set_graph(200)
             torch_sync(stream)
@@ -1085,6 +1096,51 @@ def whole_job_mlups(world, nodes_per_rank, steps, max_ms):
     return world * nodes_per_rank * steps / (max_ms * 1e-3) / 1e6
 
 
+def measure_lref(lbm, stream, name, storage, every, steps, warmup, hbm, hbm_src):
+    """Throughput of a single lattice stored at a per-node reference
+    (lbm_set_local_reference): CUDA events around every lbm_step, the
+    rebuilds (every `every` steps) inside; the roofline of the step kernel
+    with its algorithmic bytes (the 16-bit populations read and written plus
+    the FP32 reference of every node read once)."""
+    import torch
+
+    w = WORKLOADS[name][1]()[0]
+    codes = {"fp16": lbm.FP16_DEV, "bf16": lbm.BF16_DEV}
+    G = lbm.from_workload(w, stream=stream.cuda_stream, storage=codes[storage], envelope_steps=warmup + steps + 8)
+    try:
+        G.set_local_reference(every)
+        for _ in range(warmup):
+            G.step(1)
+        torch_sync(stream)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for k in range(steps):
+            G.step(1)
+            evs[k + 1].record(stream)
+        torch_sync(stream)
+        ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    finally:
+        G.close()
+    q = {W.D2Q9: 9, W.D2Q5: 5}[w.lattice]
+    nref = 3 if w.lattice == W.D2Q9 else 1
+    per_node = 2 * 2 * q + 4 * nref
+    rebuild = [m for k, m in enumerate(ms) if (warmup + k + 1) % every == 0]
+    plain = sorted(m for k, m in enumerate(ms) if (warmup + k + 1) % every != 0)
+    step_ms = plain[len(plain) // 2] if plain else float("nan")
+    total = sum(ms)
+    gbs = per_node * w.nodes / (step_ms * 1e-3) / 1e9
+    return {"mlups": w.nodes * steps / (total * 1e-3) / 1e6, "ms_per_step": total / steps, "steps": steps,
+            "nodes": w.nodes, "every": every,
+            "step_kernel": {"ms": step_ms, "mlups": w.nodes / (step_ms * 1e-3) / 1e6,
+                            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                         "frac": gbs / hbm, "traffic": None, "bytes_per_node": per_node,
+                                         "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)"}},
+            "rebuild_ms": (sum(rebuild) / len(rebuild)) if rebuild else None,
+            "timing": "CUDA events around every lbm_step; mlups over all steps (rebuild steps included), "
+                      "the step kernel's rate from the median step without a rebuild",
+            "workload": WORKLOADS[name][0]}
+
+
 def extras(lbm, stream, hbm, hbm_src, peak):
     """Per-lattice and per-storage sub-results of the metric (each its own
     lattices, created, timed and freed in turn)."""
@@ -1107,6 +1163,12 @@ def extras(lbm, stream, hbm, hbm_src, peak):
             res, _ = measure(lbm, stream, name, st, steps, 5, hbm, hbm_src, peak, **kw)
             res["workload"] = WORKLOADS[name][0]
             wk[key] = res
+        except Exception as exc:  # pragma: no cover - reported, not hidden
+            wk[key] = {"error": repr(exc)}
+    for name, st, every in (("channel8192", "fp16", 32), ("cde8192", "fp16", 16)):
+        key = f"{name}_{st}_lref"
+        try:
+            wk[key] = measure_lref(lbm, stream, name, st, every, 40, 5, hbm, hbm_src)
         except Exception as exc:  # pragma: no cover - reported, not hidden
             wk[key] = {"error": repr(exc)}
     out["workloads"] = wk
