@@ -1693,6 +1693,245 @@ k_lref_step5(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, float a
     for (int a = 0; a < 5; a++) P.out[a][i] = store_dev<T, SR>(lref_enc<LD2Q5>(R, d[a] + cref.v[a], a, i, sig), rb, a);
 }
 
+// Four consecutive nodes of a row per thread (nx a multiple of 4), as the
+// plain 16-bit row kernels: every population plane and every reference plane
+// of a source row is one aligned 64-bit (populations) or 128-bit (reference)
+// load, plus the values at x0 - 1 and x0 + 4; e of a source node is formed
+// once per row position, in packed pairs, with the same operations as
+// lref_e_of (so decode and encode agree to the bit).  Next to a wall: the
+// general per-node pull.
+template <int NR>
+struct RowRef {
+    float r[NR][6];  // [plane][x0 - 1 .. x0 + 4] of one source row
+};
+template <int NR>
+struct OwnRef {
+    float r[NR][4];  // [plane][x0 .. x0 + 3]: the four nodes' own reference
+};
+template <int NR>
+__device__ __forceinline__ void load_rowref(const LrefK &R, int base, int xm, int xp, RowRef<NR> &Rr)
+{
+#pragma unroll
+    for (int p = 0; p < NR; p++) {
+        const float *b = R.ref + p * R.Np + base;
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(b));
+        Rr.r[p][0] = __ldg(b + xm);
+        Rr.r[p][1] = v.x;
+        Rr.r[p][2] = v.y;
+        Rr.r[p][3] = v.z;
+        Rr.r[p][4] = v.w;
+        Rr.r[p][5] = __ldg(b + xp);
+    }
+}
+// e_a from the reference values of two positions (packed), the same
+// operations as lref_e_of
+template <class L>
+__device__ __forceinline__ f2 lref_e2v(const LrefK &R, int a, f2 r0, f2 r1, f2 r2)
+{
+    if constexpr (L::Q == 9) {
+        const f2 c = vfma(f2((float)LD2Q9::ex(a)), r1, f2((float)LD2Q9::ey(a)) * r2);
+        const f2 q = vfma(f2(4.5f) * c, c, f2(-1.5f) * vfma(r1, r1, r2 * r2));
+        return f2((float)LD2Q9::w(a)) * vfma(f2(3.0f), c, r0 + q);
+    } else {
+        return f2(R.q5[a]) * r0;
+    }
+}
+template <class L, int NR>
+__device__ __forceinline__ f2 lref_e2(const LrefK &R, const RowRef<NR> &Rr, int a, int k)
+{
+    const f2 r0(Rr.r[0][k], Rr.r[0][k + 1]);
+    if constexpr (NR == 3)
+        return lref_e2v<L>(R, a, r0, f2(Rr.r[1][k], Rr.r[1][k + 1]), f2(Rr.r[2][k], Rr.r[2][k + 1]));
+    else
+        return lref_e2v<L>(R, a, r0, f2(0.f), f2(0.f));
+}
+// The pulled and decoded deviations of four consecutive nodes (see above);
+// source row by source row, so that one row's reference is live at a time;
+// the centre row's reference is kept for the encode.
+template <class L, class T>
+__device__ __forceinline__ void lref_pull_quad(const Planes<T, L::Q> &P, const Geom &g, const LrefK &R, int x0, int y,
+                                               int i0, float sinv, f2 (&dA)[L::Q], f2 (&dB)[L::Q],
+                                               OwnRef<(L::Q == 9 ? 3 : 1)> &Own, bool &interior)
+{
+    constexpr int NR = L::Q == 9 ? 3 : 1;
+    const bool wall_x = g.wall[0] && (x0 == 0 || x0 + 3 == g.nx - 1);
+    const bool wall_y = g.wall[1] && (y == 0 || y == g.ny - 1);
+    interior = !(wall_x || wall_y);
+    if (interior) {
+        const int sy = g.nx;
+        const int ym = y == 0 ? (g.ny - 1) * sy : -sy, yp = y == g.ny - 1 ? (1 - g.ny) * sy : sy;
+        const int xm = x0 == 0 ? g.nx - 1 : -1;
+        const int xp = x0 + 4 == g.nx ? 4 - g.nx : 4;
+        const f2 si(sinv);
+        const int roffs[3] = {ym, 0, yp};  // source rows of e_y = +1, 0, -1
+        // the stored pair values of population a (pulled from row offset roff)
+        auto pulled = [&](int a, int roff, f2 &sA, f2 &sB) {
+            const int ex = L::ex(a);
+            const T *pl = P.in[a] + i0 + roff;
+            float wv[4];
+            get4<T>(pl, wv);
+            if (ex == 0) {
+                sA = f2(wv[0], wv[1]);
+                sB = f2(wv[2], wv[3]);
+            } else if (ex == 1) {
+                sA = f2(Dev<T>::get(pl + xm), wv[0]);
+                sB = f2(wv[1], wv[2]);
+            } else {
+                sA = f2(wv[1], wv[2]);
+                sB = f2(wv[3], Dev<T>::get(pl + xp));
+            }
+        };
+        if constexpr (NR == 1) {
+            // one reference plane: every row's reference loaded first, populations in order
+            RowRef<NR> Rr[3];
+#pragma unroll
+            for (int r = 0; r < 3; r++) load_rowref<NR>(R, i0 + roffs[r], xm, xp, Rr[r]);
+#pragma unroll
+            for (int j = 0; j < 4; j++) Own.r[0][j] = Rr[1].r[0][j + 1];
+#pragma unroll
+            for (int a = 0; a < L::Q; a++) {
+                const int ex = L::ex(a), r = 1 - L::ey(a);
+                f2 sA, sB;
+                pulled(a, roffs[r], sA, sB);
+                // source positions of nodes x0 + j: row index 1 + j - e_x (0 = x0 - 1)
+                dA[a] = vfma(sA, si, lref_e2<L, NR>(R, Rr[r], a, 1 - ex));
+                dB[a] = vfma(sB, si, lref_e2<L, NR>(R, Rr[r], a, 3 - ex));
+            }
+        } else {
+            // three reference planes: one source row at a time (fewer registers)
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                RowRef<NR> Rr;
+                load_rowref<NR>(R, i0 + roffs[r], xm, xp, Rr);
+                if (r == 1)
+#pragma unroll
+                    for (int p = 0; p < NR; p++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) Own.r[p][j] = Rr.r[p][j + 1];
+#pragma unroll
+                for (int a = 0; a < L::Q; a++) {
+                    if (L::ey(a) != 1 - r) continue;
+                    const int ex = L::ex(a);
+                    f2 sA, sB;
+                    pulled(a, roffs[r], sA, sB);
+                    dA[a] = vfma(sA, si, lref_e2<L, NR>(R, Rr, a, 1 - ex));
+                    dB[a] = vfma(sB, si, lref_e2<L, NR>(R, Rr, a, 3 - ex));
+                }
+            }
+        }
+        return;
+    }
+    float d[4][L::Q];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        pull_node<L>(g, x0 + j, y, 0, i0 + j, d[j],
+                     [&](int p, int k) { return lref_dec<L, T>(R, P.in[p], p, k, sinv); });
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        dA[a] = f2(d[0][a], d[1][a]);
+        dB[a] = f2(d[2][a], d[3][a]);
+    }
+}
+// sigma (d - e) of the four nodes themselves, in place
+template <class L, class T>
+__device__ __forceinline__ void lref_encode_quad(const LrefK &R, const OwnRef<(L::Q == 9 ? 3 : 1)> &Own,
+                                                 bool interior, int i0, float sig, f2 (&dA)[L::Q], f2 (&dB)[L::Q])
+{
+    constexpr int NR = L::Q == 9 ? 3 : 1;
+    const f2 sg(sig);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        f2 eA, eB;
+        if (interior) {
+            const f2 z(0.f);
+            eA = lref_e2v<L>(R, a, f2(Own.r[0][0], Own.r[0][1]), NR == 3 ? f2(Own.r[1 % NR][0], Own.r[1 % NR][1]) : z,
+                             NR == 3 ? f2(Own.r[2 % NR][0], Own.r[2 % NR][1]) : z);
+            eB = lref_e2v<L>(R, a, f2(Own.r[0][2], Own.r[0][3]), NR == 3 ? f2(Own.r[1 % NR][2], Own.r[1 % NR][3]) : z,
+                             NR == 3 ? f2(Own.r[2 % NR][2], Own.r[2 % NR][3]) : z);
+        } else {
+            eA = f2(lref_e<L>(R, a, i0), lref_e<L>(R, a, i0 + 1));
+            eB = f2(lref_e<L>(R, a, i0 + 2), lref_e<L>(R, a, i0 + 3));
+        }
+        dA[a] = (dA[a] - eA) * sg;
+        dB[a] = (dB[a] - eB) * sg;
+    }
+}
+
+#ifndef LBM_LREF9X4_MIN_BLOCKS
+#define LBM_LREF9X4_MIN_BLOCKS 1
+#endif
+template <class T, int FK, bool SR>
+__global__ void __launch_bounds__(kBlock, LBM_LREF9X4_MIN_BLOCKS)
+k_lref_step9x4(const __grid_constant__ Planes<T, 9> P, Geom g, FieldDev F, float apre, float gsum, Rates9f w,
+               float rref, LrefK R, unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 2)) return;
+    const int i0 = 4 * t;
+    int x0, y;
+    node_xy(g, i0, x0, y);
+    const float sig = __ldg(R.scale), sinv = __ldg(R.scale + 1);
+    f2 dA[9], dB[9];
+    OwnRef<3> Own;
+    bool interior;
+    lref_pull_quad<LD2Q9, T>(P, g, R, x0, y, i0, sinv, dA, dB, Own, interior);
+    f2 FxA(0.f), FyA(0.f), GxA(0.f), GyA(0.f), FxB(0.f), FyB(0.f), GxB(0.f), GyB(0.f);
+    if (FK != FK_NONE) {
+        float px[4], py[4];
+        field_row_f<4>(F, FK, 0, x0, y, i0, px);
+        field_row_f<4>(F, FK, 1, x0, y, i0, py);
+        const f2 PxA(px[0], px[1]), PyA(py[0], py[1]), PxB(px[2], px[3]), PyB(py[2], py[3]);
+        FxA = f2(apre) * PxA;
+        FyA = f2(apre) * PyA;
+        GxA = f2(gsum) * PxA;
+        GyA = f2(gsum) * PyA;
+        FxB = f2(apre) * PxB;
+        FyB = f2(apre) * PyB;
+        GxB = f2(gsum) * PxB;
+        GyB = f2(gsum) * PyB;
+    }
+    collide9_w1<f2>(dA, rref, FxA, FyA, GxA, GyA, w);
+    collide9_w1<f2>(dB, rref, FxB, FyB, GxB, GyB, w);
+    lref_encode_quad<LD2Q9, T>(R, Own, interior, i0, sig, dA, dB);
+    store_quad<T, SR, 9>(P.out, i0, dA, dB, srkey);
+}
+
+template <class T, int SK, bool SR>
+__global__ void __launch_bounds__(kBlock)
+k_lref_step5x4(const __grid_constant__ Planes<T, 5> P, Geom g, FieldDev S, float apre, float hsum, Coef5f k,
+               Ref5f cref, LrefK R, unsigned long long srkey)
+{
+    const int t = blockIdx.x * kBlock + threadIdx.x;
+    if (t >= (g.N >> 2)) return;
+    const int i0 = 4 * t;
+    int x0, y;
+    node_xy(g, i0, x0, y);
+    const float sig = __ldg(R.scale), sinv = __ldg(R.scale + 1);
+    f2 dA[5], dB[5];
+    OwnRef<1> Own;
+    bool interior;
+    lref_pull_quad<LD2Q5, T>(P, g, R, x0, y, i0, sinv, dA, dB, Own, interior);
+    f2 SpA(0.f), H0A(0.f), SpB(0.f), H0B(0.f);
+    if (SK != FK_NONE) {
+        float ps[4];
+        field_row_f<4>(S, SK, 0, x0, y, i0, ps);
+        const f2 PA(ps[0], ps[1]), PB(ps[2], ps[3]);
+        SpA = f2(apre) * PA;
+        H0A = f2(hsum) * PA;
+        SpB = f2(apre) * PB;
+        H0B = f2(hsum) * PB;
+    }
+    collide5u<f2>(dA, 0.0f, SpA, H0A, k);
+    collide5u<f2>(dB, 0.0f, SpB, H0B, k);
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+        dA[a] = dA[a] + f2(cref.v[a]);
+        dB[a] = dB[a] + f2(cref.v[a]);
+    }
+    lref_encode_quad<LD2Q5, T>(R, Own, interior, i0, sig, dA, dB);
+    store_quad<T, SR, 5>(P.out, i0, dA, dB, srkey);
+}
+
 // Stored (s, reference, sigma) -> FP32 deviations d, both in the stored [q][Np] layout.
 template <class L, class T>
 __global__ void __launch_bounds__(kBlock)
@@ -1804,7 +2043,13 @@ cudaError_t lref_step_ts(int lattice, const LaunchArgs &a, const LrefK &R)
         const float gsum = (float)((a.apre + a.apost) / 12.0), apre = (float)a.apre;
         const bool w1 = a.omega[6] == 1.0 && a.omega[7] == 1.0 && a.omega[8] == 1.0;
 #define LREF9(FKV, W1V) k_lref_step9<T, FKV, W1V, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, gsum, w, rref, R, key)
-        if (w1) {
+#define LREF9X4(FKV) k_lref_step9x4<T, FKV, SR><<<qgrid, kBlock, 0, s>>>(P, a.g, a.F, apre, gsum, w, rref, R, key)
+        const int qgrid = (a.g.N / 4 + kBlock - 1) / kBlock;
+        if (w1 && a.g.nx % 4 == 0) {
+            if (a.fkind == FK_NONE) LREF9X4(FK_NONE);
+            else if (a.fkind == FK_CONST) LREF9X4(FK_CONST);
+            else LREF9X4(FK_GENERAL);
+        } else if (w1) {
             if (a.fkind == FK_NONE) LREF9(FK_NONE, true);
             else if (a.fkind == FK_CONST) LREF9(FK_CONST, true);
             else LREF9(FK_GENERAL, true);
@@ -1814,6 +2059,7 @@ cudaError_t lref_step_ts(int lattice, const LaunchArgs &a, const LrefK &R)
             else LREF9(FK_GENERAL, false);
         }
 #undef LREF9
+#undef LREF9X4
     } else if (lattice == LD2Q5::ID) {
         if (a.vkind == FK_GENERAL) return cudaErrorInvalidValue;
         const double ux = a.vkind == FK_CONST ? a.V.cval[0] : 0.0, uy = a.vkind == FK_CONST ? a.V.cval[1] : 0.0;
@@ -1824,7 +2070,14 @@ cudaError_t lref_step_ts(int lattice, const LaunchArgs &a, const LrefK &R)
         d2q5_reference_change(a.omega, ux, uy, a.gref, c);
         for (int q = 0; q < 5; q++) cref.v[q] = (float)c[q];
         const Planes<T, 5> P = make_planes<T, 5>(a.fin, a.fout, a.g.Np);
-        if (a.fkind == FK_NONE)
+        if (a.g.nx % 4 == 0) {
+            const int qgrid = (a.g.N / 4 + kBlock - 1) / kBlock;
+            if (a.fkind == FK_NONE)
+                k_lref_step5x4<T, FK_NONE, SR><<<qgrid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+            else if (a.fkind == FK_CONST)
+                k_lref_step5x4<T, FK_CONST, SR><<<qgrid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+            else k_lref_step5x4<T, FK_GENERAL, SR><<<qgrid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
+        } else if (a.fkind == FK_NONE)
             k_lref_step5<T, FK_NONE, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
         else if (a.fkind == FK_CONST)
             k_lref_step5<T, FK_CONST, SR><<<grid, kBlock, 0, s>>>(P, a.g, a.F, apre, hsum, k, cref, R, key);
