@@ -85,48 +85,48 @@ TRAFFIC = {
     ("d3q27", "fp64"): {"src": [_C + "k_d3q27.cu"] + _H, "sha": "4be8a09ad4918a7a",
                         "bytes_per_node": (1529.134848 + 1477.492224) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/k_step_d3q27_kolmogorov_fp64.md"},
-    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                        "bytes_per_node": (1812.100096 + 1757.166592) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
+    ("d3q27", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                        "bytes_per_node": (1812.015360 + 1756.774400) * 1e6 / 256 ** 3, "captured_nodes": 256 ** 3,
                         "profile": "profiles/reduced_precision_traffic.md"},
-    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                        "bytes_per_node": (382.291456 + 334.291712) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+    ("d3q27", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                        "bytes_per_node": (382.343680 + 333.836032) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/reduced_precision_traffic.md"},
-    ("d3q27", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                        "bytes_per_node": (382.267904 + 333.928960) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
+    ("d3q27", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                        "bytes_per_node": (382.267392 + 333.867776) * 1e6 / 192 ** 3, "captured_nodes": 192 ** 3,
                         "profile": "profiles/reduced_precision_traffic.md"},
     ("d2q9", "fp64"): {"src": [_C + "k_d2q9.cu"] + _H, "sha": "018f6162beb1528d",
                        "bytes_per_node": (151.018240 + 99.837696) * 1e6 / (2048 * 1024),
                        "captured_nodes": 2048 * 1024, "profile": "profiles/k_step_d2q9_channel2048_fp64.md"},
-    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (1208.064512 + 1153.999872) * 1e6 / (8192 * 4096),
+    ("d2q9", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (1207.990016 + 1153.966848) * 1e6 / (8192 * 4096),
                        "captured_nodes": 8192 * 4096, "profile": "profiles/reduced_precision_traffic.md"},
-    ("d2q9", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (604.019200 + 550.888448) * 1e6 / (8192 * 4096),
+    ("d2q9", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (604.020736 + 551.098112) * 1e6 / (8192 * 4096),
                        "captured_nodes": 8192 * 4096, "profile": "profiles/reduced_precision_traffic.md"},
-    ("d2q9", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (604.088576 + 550.706176) * 1e6 / (8192 * 4096),
+    ("d2q9", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (604.019712 + 551.259904) * 1e6 / (8192 * 4096),
                        "captured_nodes": 8192 * 4096, "profile": "profiles/reduced_precision_traffic.md"},
     ("d2q5", "fp64"): {"src": [_C + "k_d2q5.cu"] + _H, "sha": "80d05b85abca33c6", "above_l2": True,
                        "bytes_per_node": (2684.653056 + 2632.778752) * 1e6 / 8192 ** 2,
                        "captured_nodes": 8192 ** 2, "profile": "profiles/k_step5_k_step_mat_cde8192.md"},
-    ("d2q5", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (1342.272512 + 1290.838272) * 1e6 / 8192 ** 2,
+    ("d2q5", "fp32"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (1342.345984 + 1290.611200) * 1e6 / 8192 ** 2,
                        "captured_nodes": 8192 ** 2, "profile": "profiles/reduced_precision_traffic.md"},
-    ("d2q5", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (671.184128 + 620.978432) * 1e6 / 8192 ** 2,
+    ("d2q5", "fp16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (671.200256 + 620.869632) * 1e6 / 8192 ** 2,
                        "captured_nodes": 8192 ** 2, "profile": "profiles/reduced_precision_traffic.md"},
-    ("d2q5", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "86ce6eb18668be87", "above_l2": True,
-                       "bytes_per_node": (671.183104 + 621.499648) * 1e6 / 8192 ** 2,
+    ("d2q5", "bf16"): {"src": [_C + "k_rp.cu"] + _H, "sha": "93ac4523479a40ea", "above_l2": True,
+                       "bytes_per_node": (671.203840 + 621.302016) * 1e6 / 8192 ** 2,
                        "captured_nodes": 8192 ** 2, "profile": "profiles/reduced_precision_traffic.md"},
     # batched kernels (keys of the batched launches; the single-lattice
     # captures above do not describe them)
     ("d2q9_batch", "fp32"): {"src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh", _C + "lbm_batch.cu"] + _H,
-                             "sha": "ed1ba8c7ea91e071", "above_l2": True,
-                             "bytes_per_node": (379.281664 + 335.246592) * 1e6 / 10521531, "captured_nodes": 10521531,
+                             "sha": "a4c28ce2b40de990", "above_l2": True,
+                             "bytes_per_node": (379.160576 + 335.486720) * 1e6 / 10521531, "captured_nodes": 10521531,
                              "profile": "profiles/reduced_precision_traffic.md"},
     ("d2q5_batch", "fp32"): {"src": [_C + "k_rp.cu", _C + "lbm_tiles.cuh", _C + "lbm_batch.cu"] + _H,
-                             "sha": "ed1ba8c7ea91e071", "above_l2": True,
-                             "bytes_per_node": (211.179520 + 167.843328) * 1e6 / 10521531, "captured_nodes": 10521531,
+                             "sha": "a4c28ce2b40de990", "above_l2": True,
+                             "bytes_per_node": (211.178752 + 167.969792) * 1e6 / 10521531, "captured_nodes": 10521531,
                              "profile": "profiles/reduced_precision_traffic.md"},
     ("d2q5_sweep", "fp64"): {"src": [_C + "k_d2q5.cu", _C + "lbm_tiles.cuh"] + _H, "sha": "47b4fe221b263702",
                              "bytes_per_node": 14.0096e6 / 349184, "captured_nodes": 349184,

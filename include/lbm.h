@@ -227,10 +227,13 @@ int lbm_set_stochastic_rounding(lbm_ctx *ctx, int on, unsigned long long seed);
  * larger).  A step pulls d = s / sigma + e of the source node and collides
  * exactly as the FP32 deviation form; every `every` steps of lbm_step the
  * reference and sigma are rebuilt from the state (the node's own moments), so
- * the 16-bit values hold only the non-equilibrium part and the change since.
- * Reads and writes of the state (moments, reductions, populations, init) go
- * through FP32 deviations.
- * Memory: (1 or 3 + q) floats per node on top of the 16-bit state.
+ * the 16-bit values hold only the non-equilibrium part and the change since
+ * (the rebuild runs in place: two passes over the stored values).  Reads and
+ * writes of the state (moments, reductions, populations, init) go through
+ * FP32 deviations.
+ * Memory: 2 x (1 or 3) floats per node on top of the 16-bit state (two
+ * references), and q floats per node from the first read or write of the
+ * state on.
  *   every : steps between rebuilds (>= 1), or 0 to return to the plain
  *           16-bit deviations (the state is converted either way).
  * A D2Q5 context needs a uniform advecting velocity (setting a velocity field

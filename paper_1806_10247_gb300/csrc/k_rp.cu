@@ -1944,15 +1944,29 @@ k_lref_decode(const T *__restrict__ st, Geom g, LrefK R, float *__restrict__ dev
     for (int a = 0; a < L::Q; a++) dev[a * g.Np + i] = lref_dec<L, T>(R, st + a * g.Np, a, i, sinv);
 }
 
+// The block's largest m into bmax[blockIdx.x].
+__device__ __forceinline__ void block_max_to(float m, float *bmax)
+{
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.0f;
+        for (int k = 0; k < kBlock / 32; k++) b = fmaxf(b, wm[k]);
+        bmax[blockIdx.x] = b;
+    }
+}
+
 // New reference from FP32 deviations (the node's own zeroth and first
-// moments: then e has the same moments as d) and the per-block largest |d - e|.
+// moments: then e has the same moments as d) and each block's largest |d - e|.
 template <class L>
 __global__ void __launch_bounds__(kBlock)
 k_lref_reference(const float *__restrict__ dev, Geom g, LrefK R, float *__restrict__ ref, float *__restrict__ bmax)
 {
+    const int i = blockIdx.x * kBlock + threadIdx.x;
     float m = 0.0f;
-    for (long long n = blockIdx.x * (long long)kBlock + threadIdx.x; n < g.N; n += (long long)gridDim.x * kBlock) {
-        const int i = (int)n;
+    if (i < g.N) {
         float d[L::Q];
         float r0 = 0.f, r1 = 0.f, r2 = 0.f;
 #pragma unroll
@@ -1972,25 +1986,81 @@ k_lref_reference(const float *__restrict__ dev, Geom g, LrefK R, float *__restri
 #pragma unroll
         for (int a = 0; a < L::Q; a++) m = fmaxf(m, fabsf(d[a] - lref_e_of<L>(R, a, r0, r1, r2)));
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wm[kBlock / 32];
-    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float b = 0.0f;
-        for (int k = 0; k < kBlock / 32; k++) b = fmaxf(b, wm[k]);
-        bmax[blockIdx.x] = b;
+    block_max_to(m, bmax);
+}
+
+__device__ __forceinline__ float plain_val(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float plain_val(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+// The rebuild without an FP32 copy of the state, in two passes over the
+// stored values: the new reference (the node's own moments of its decoded
+// deviations, into the second reference buffer) with the per-block largest
+// |d - e_new|, then, once sigma_new is known, every value decoded at the old
+// reference and sigma and stored at the new ones, in place (each thread
+// touches its own node only).  Old and new may differ in q5 too (a D2Q5
+// velocity change).
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_lref_newref(const T *__restrict__ st, Geom g, LrefK Ro, LrefK Rn, float *__restrict__ ref_new,
+              float *__restrict__ bmax)
+{
+    const float sinv = __ldg(Ro.scale + 1);
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    float m = 0.0f;
+    if (i < g.N) {
+        float d[L::Q];
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) {
+            d[a] = lref_dec<L, T>(Ro, st + a * g.Np, a, i, sinv);
+            r0 += d[a];
+            if constexpr (L::Q == 9) {
+                r1 += (float)L::ex(a) * d[a];
+                r2 += (float)L::ey(a) * d[a];
+            }
+        }
+        ref_new[i] = r0;
+        if constexpr (L::Q == 9) {
+            ref_new[g.Np + i] = r1;
+            ref_new[2 * g.Np + i] = r2;
+        }
+#pragma unroll
+        for (int a = 0; a < L::Q; a++) m = fmaxf(m, fabsf(d[a] - lref_e_of<L>(Rn, a, r0, r1, r2)));
+    }
+    block_max_to(m, bmax);
+}
+
+template <class L, class T>
+__global__ void __launch_bounds__(kBlock)
+k_lref_reencode(T *__restrict__ st, Geom g, LrefK Ro, LrefK Rn)
+{
+    const int i = blockIdx.x * kBlock + threadIdx.x;
+    if (i >= g.N) return;
+    const float sinv = __ldg(Ro.scale + 1), sig = __ldg(Rn.scale);
+#pragma unroll
+    for (int a = 0; a < L::Q; a++) {
+        // plain loads: this kernel writes the values it reads
+        const float sv = plain_val(st + a * g.Np + i);
+        const float d = fmaf(sv, sinv, lref_e<L>(Ro, a, i));
+        st[a * g.Np + i] = Dev<T>::to_store(lref_enc<L>(Rn, d, a, i, sig));
     }
 }
 
-// sigma = 2^k with the lattice's largest |d - e| times sigma in [8, 16)
-// (k clamped to [-30, 30]; 1 for an exactly uniform state).
-__global__ void k_lref_scale(const float *__restrict__ bmax, int nb, float *__restrict__ scale)
+// sigma = 2^k with the lattice's largest |d - e| (the largest of the nb block
+// maxima) times sigma in [8, 16) (k clamped to [-30, 30]; 1 for an exactly
+// uniform state).
+constexpr int kScaleThreads = 1024;
+__global__ void __launch_bounds__(kScaleThreads) k_lref_scale(const float *__restrict__ bmax, int nb,
+                                                              float *__restrict__ scale)
 {
     float m = 0.0f;
-    for (int k = threadIdx.x; k < nb; k += 32) m = fmaxf(m, bmax[k]);
+    for (int k = threadIdx.x; k < nb; k += kScaleThreads) m = fmaxf(m, bmax[k]);
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[kScaleThreads / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        for (int k = 0; k < kScaleThreads / 32; k++) m = fmaxf(m, wm[k]);
         int e = 0;
         int k = 0;
         if (m > 0.0f && isfinite(m)) {
@@ -2217,15 +2287,62 @@ cudaError_t lref_reset(int lattice, const Geom &g, const Lref &L, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t lref_rebuild_t(int lattice, const Geom &g, const LrefK &Ro, const LrefK &Rn, float *ref_new,
+                           float *scale_new, float *bmax, void *stored, cudaStream_t s)
+{
+    const int grid = (g.N + kBlock - 1) / kBlock;
+    T *st = static_cast<T *>(stored);
+    if (lattice == LD2Q9::ID) {
+        k_lref_newref<LD2Q9, T><<<grid, kBlock, 0, s>>>(st, g, Ro, Rn, ref_new, bmax);
+        k_lref_scale<<<1, kScaleThreads, 0, s>>>(bmax, grid, scale_new);
+        k_lref_reencode<LD2Q9, T><<<grid, kBlock, 0, s>>>(st, g, Ro, Rn);
+    } else if (lattice == LD2Q5::ID) {
+        k_lref_newref<LD2Q5, T><<<grid, kBlock, 0, s>>>(st, g, Ro, Rn, ref_new, bmax);
+        k_lref_scale<<<1, kScaleThreads, 0, s>>>(bmax, grid, scale_new);
+        k_lref_reencode<LD2Q5, T><<<grid, kBlock, 0, s>>>(st, g, Ro, Rn);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t lref_reencode(int lattice, int storage, const Geom &g, const Lref &Lold, const Lref &Lnew, void *stored,
+                          cudaStream_t s)
+{
+    const LrefK Ro = lref_k(Lold, g), Rn = lref_k(Lnew, g);
+    const int grid = (g.N + kBlock - 1) / kBlock;
+    if (lattice == LD2Q9::ID && storage == 2)
+        k_lref_reencode<LD2Q9, __half><<<grid, kBlock, 0, s>>>(static_cast<__half *>(stored), g, Ro, Rn);
+    else if (lattice == LD2Q9::ID && storage == 3)
+        k_lref_reencode<LD2Q9, __nv_bfloat16><<<grid, kBlock, 0, s>>>(static_cast<__nv_bfloat16 *>(stored), g, Ro, Rn);
+    else if (lattice == LD2Q5::ID && storage == 2)
+        k_lref_reencode<LD2Q5, __half><<<grid, kBlock, 0, s>>>(static_cast<__half *>(stored), g, Ro, Rn);
+    else if (lattice == LD2Q5::ID && storage == 3)
+        k_lref_reencode<LD2Q5, __nv_bfloat16><<<grid, kBlock, 0, s>>>(static_cast<__nv_bfloat16 *>(stored), g, Ro, Rn);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t lref_rebuild(int lattice, int storage, const Geom &g, const Lref &Lold, const Lref &Lnew, float *bmax,
+                         void *stored, cudaStream_t s)
+{
+    const LrefK Ro = lref_k(Lold, g), Rn = lref_k(Lnew, g);
+    if (storage == 2) return lref_rebuild_t<__half>(lattice, g, Ro, Rn, Lnew.ref, Lnew.scale, bmax, stored, s);
+    if (storage == 3) return lref_rebuild_t<__nv_bfloat16>(lattice, g, Ro, Rn, Lnew.ref, Lnew.scale, bmax, stored, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t lref_rebase(int lattice, int storage, const Geom &g, const Lref &L, float *bmax, const float *dev,
                         void *stored, cudaStream_t s)
 {
     if (lattice != LD2Q9::ID && lattice != LD2Q5::ID) return cudaErrorInvalidValue;
     const LrefK R = lref_k(L, g);
-    const int nb = std::max(1, std::min(kReduceMaxBlocks, (g.N + kBlock - 1) / kBlock));
-    if (lattice == LD2Q9::ID) k_lref_reference<LD2Q9><<<nb, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
-    else k_lref_reference<LD2Q5><<<nb, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
-    k_lref_scale<<<1, 32, 0, s>>>(bmax, nb, L.scale);
+    const int grid = (g.N + kBlock - 1) / kBlock;
+    if (lattice == LD2Q9::ID) k_lref_reference<LD2Q9><<<grid, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
+    else k_lref_reference<LD2Q5><<<grid, kBlock, 0, s>>>(dev, g, R, L.ref, bmax);
+    k_lref_scale<<<1, kScaleThreads, 0, s>>>(bmax, grid, L.scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (storage == 2) return lref_codec_t<__half>(lattice, 2, g, R, L.ref, nullptr, stored, dev, nullptr, s);

@@ -10,6 +10,7 @@
 #include <limits>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lbm_ctx.h"
@@ -154,8 +155,24 @@ lbmk::Lref lref_of(const lbm_ctx *c)
 
 int lref_decode_state(lbm_ctx *c)
 {
+    if (!c->lref_dev)
+        CK(cudaMalloc(&c->lref_dev, (size_t)c->q * c->g.Np * sizeof(float)), "cudaMalloc(local reference FP32 state)");
     CK(lref_decode(c->lattice, c->storage, c->g, lref_of(c), c->A, c->lref_dev, c->stream), "decode kernel");
     c->launches++;
+    return LBM_OK;
+}
+
+int lref_rebuild_state(lbm_ctx *c, const lbmk::Lref &old)
+{
+    const int rc = wait_readers(c, c->A);
+    if (rc != LBM_OK) return rc;
+    lbmk::Lref nw = lref_of(c);
+    nw.ref = c->lref_ref2;
+    nw.scale = c->lref_aux2;
+    CK(lref_rebuild(c->lattice, c->storage, c->g, old, nw, c->lref_aux + 2, c->A, c->stream), "rebuild kernels");
+    c->launches += 3;
+    std::swap(c->lref_ref, c->lref_ref2);
+    std::swap(c->lref_aux, c->lref_aux2);
     return LBM_OK;
 }
 
@@ -172,7 +189,13 @@ int lref_encode_state(lbm_ctx *c)
 LrefView::LrefView(lbm_ctx *cc, bool decode) : c(cc)
 {
     if (!c->lref_every) return;
-    if (decode && c->initialised) rc = lref_decode_state(c);
+    if (decode && c->initialised) {
+        rc = lref_decode_state(c);
+    } else if (!c->lref_dev) {
+        const cudaError_t e = cudaMalloc(&c->lref_dev, (size_t)c->q * c->g.Np * sizeof(float));
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "cudaMalloc(local reference FP32 state)");
+    }
+    if (rc != LBM_OK) return;
     A0 = c->A;
     st0 = c->storage;
     el0 = c->elem;
@@ -192,19 +215,21 @@ void LrefView::restore()
 }
 
 // Back to the plain 16-bit deviations (reference 0, sigma 1).
-static int lref_off(lbm_ctx *c)
+// old: the encoding the state is in (its q5 may differ from the current velocity's).
+static int lref_off(lbm_ctx *c, const lbmk::Lref &old)
 {
-    if (c->initialised) {
-        const int rc = lref_decode_state(c);
-        if (rc != LBM_OK) return rc;
-    }
-    CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
+    lbmk::Lref plain = lref_of(c);
+    plain.ref = c->lref_ref2;
+    plain.scale = c->lref_aux2;
+    CK(lref_reset(c->lattice, c->g, plain, c->stream), "lref reset");
     if (c->initialised) {
         const int rc = wait_readers(c, c->A);
         if (rc != LBM_OK) return rc;
-        CK(lref_encode(c->lattice, c->storage, c->g, lref_of(c), c->lref_dev, c->A, c->stream), "encode kernel");
+        CK(lref_reencode(c->lattice, c->storage, c->g, old, plain, c->A, c->stream), "re-encode kernel");
         c->launches++;
     }
+    std::swap(c->lref_ref, c->lref_ref2);
+    std::swap(c->lref_aux, c->lref_aux2);
     c->lref_every = 0;
     c->lref_since = 0;
     c->version++;
@@ -488,6 +513,8 @@ void lbm_destroy(lbm_ctx *c)
     cudaFree(c->lref_ref);
     cudaFree(c->lref_aux);
     cudaFree(c->lref_dev);
+    cudaFree(c->lref_ref2);
+    cudaFree(c->lref_aux2);
     delete c;
 }
 
@@ -581,28 +608,18 @@ int lbm_set_velocity(lbm_ctx *c, const lbm_field *u)
     c->err.clear();
     c->version++;
     if (c->lattice != LBM_D2Q5_CDE) return fail(c, LBM_EINVAL, "lbm_set_velocity: only for the scalar lattice");
-    if (c->lref_every && c->initialised) {
-        // the encoding depends on the uniform velocity: decode with the old one
-        const int rd = lref_decode_state(c);
-        if (rd != LBM_OK) return rd;
-    }
+    // the encoding depends on the uniform velocity: the state's, before the change
+    const lbmk::Lref old_enc = lref_of(c);
     int rc = upload_field(c, u, 2, c->vel, "lbm_set_velocity");
     if (rc != LBM_OK) return rc;
     if (c->lref_every) {
         if (c->vel.kind == FK_GENERAL) {
             // a velocity field ends the local-reference encoding: plain deviations
-            CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
-            if (c->initialised) {
-                rc = wait_readers(c, c->A);
-                if (rc != LBM_OK) return rc;
-                CK(lref_encode(c->lattice, c->storage, c->g, lref_of(c), c->lref_dev, c->A, c->stream), "encode");
-                c->launches++;
-            }
-            c->lref_every = 0;
-            c->lref_since = 0;
+            rc = lref_off(c, old_enc);
+            if (rc != LBM_OK) return rc;
         } else {
             if (c->initialised) {
-                rc = lref_encode_state(c);
+                rc = lref_rebuild_state(c, old_enc);
                 if (rc != LBM_OK) return rc;
                 c->lref_since = 0;
             }
@@ -682,21 +699,20 @@ int lbm_set_local_reference(lbm_ctx *c, int every)
         const int rc = wait_readers(c, nullptr);
         if (rc != LBM_OK) return rc;
     }
-    if (every == 0) return c->lref_every ? lref_off(c) : LBM_OK;
+    if (every == 0) return c->lref_every ? lref_off(c, lref_of(c)) : LBM_OK;
     if (!c->lref_every) {
         const int nref = c->lattice == LBM_D2Q9 ? 3 : 1;
-        const size_t np = (size_t)c->g.Np;
+        // sigma, 1 / sigma, the rebuild's largest |d - e| per block of 256 nodes
+        const size_t np = (size_t)c->g.Np, naux = 2 + ((size_t)c->g.N + 255) / 256;
         if (!c->lref_ref) CK(cudaMalloc(&c->lref_ref, nref * np * sizeof(float)), "cudaMalloc(local reference)");
-        if (!c->lref_aux) CK(cudaMalloc(&c->lref_aux, (2 + (size_t)lbmk::kReduceMaxBlocks) * sizeof(float)),
-                             "cudaMalloc(local reference scale)");
-        if (!c->lref_dev) CK(cudaMalloc(&c->lref_dev, (size_t)c->q * np * sizeof(float)),
-                             "cudaMalloc(local reference FP32 state)");
+        if (!c->lref_ref2) CK(cudaMalloc(&c->lref_ref2, nref * np * sizeof(float)), "cudaMalloc(local reference)");
+        if (!c->lref_aux) CK(cudaMalloc(&c->lref_aux, naux * sizeof(float)), "cudaMalloc(local reference scale)");
+        if (!c->lref_aux2) CK(cudaMalloc(&c->lref_aux2, naux * sizeof(float)), "cudaMalloc(local reference scale)");
         // the plain deviations are this encoding at reference 0 and sigma 1
         CK(lref_reset(c->lattice, c->g, lref_of(c), c->stream), "lref reset");
         c->lref_every = every;
         if (c->initialised) {
-            int rc = lref_decode_state(c);
-            if (rc == LBM_OK) rc = lref_encode_state(c);
+            const int rc = lref_rebuild_state(c, lref_of(c));
             if (rc != LBM_OK) {
                 c->lref_every = 0;
                 return rc;
@@ -769,9 +785,8 @@ int lbm_step(lbm_ctx *c, long n)
         c->B = tmp;
         c->t++;
         if (c->lref_every && ++c->lref_since >= c->lref_every) {
-            // rebuild the local reference from the state
-            int rc = lref_decode_state(c);
-            if (rc == LBM_OK) rc = lref_encode_state(c);
+            // rebuild the local reference from the state, in place
+            const int rc = lref_rebuild_state(c, lref_of(c));
             if (rc != LBM_OK) return rc;
             c->lref_since = 0;
         }

@@ -29,14 +29,17 @@ struct lbm_ctx {
     unsigned long long sr_seed = 0;
     // 16-bit D2Q9 / D2Q5 storage at a per-node reference (lbmk::Lref): steps
     // between rebuilds of the reference (0: off, the plain deviations), steps
-    // since the last one, the reference [1 or 3][Np], sigma, 1 / sigma and the
-    // rebuild's block maxima, and q*Np floats of FP32 deviations (rebuilds
-    // and every read or write of the state go through them)
+    // since the last one, the reference [1 or 3][Np], {sigma, 1 / sigma, the
+    // rebuild's largest |d - e| per block}, and q*Np floats of FP32 deviations (every read
+    // or write of the state goes through them; the step's rebuilds do not)
     int lref_every = 0;
     int lref_since = 0;
     float *lref_ref = nullptr;
     float *lref_aux = nullptr;
-    float *lref_dev = nullptr;
+    float *lref_dev = nullptr;  // allocated at the first read or write of the state
+    // the rebuild's target (swapped with lref_ref / lref_aux after each)
+    float *lref_ref2 = nullptr;
+    float *lref_aux2 = nullptr;
     // D2Q5 reduced-precision storage: reference populations of the deviations
     // (lbmk::Ref5; set at lbm_init_equilibrium)
     double gref[5] = {0, 0, 0, 0, 0};
@@ -104,6 +107,10 @@ lbmk::Lref lref_of(const lbm_ctx *c);
 // and rebuilt from them (new reference and sigma, stored values into A).
 int lref_decode_state(lbm_ctx *c);
 int lref_encode_state(lbm_ctx *c);
+// The rebuild in place (new reference and sigma from the stored state, no
+// FP32 copy); `old` describes the encoding the state is in (its q5 may
+// differ from the context's current velocity's).
+int lref_rebuild_state(lbm_ctx *c, const lbmk::Lref &old);
 // For the length of a scope a local-reference context looks like an FP32
 // deviation context whose stored buffer is lref_dev (decoded on entry when
 // `decode`), so that the FP32 read and write paths serve it; a write path

@@ -228,8 +228,17 @@ cudaError_t lref_reset(int lattice, const Geom &g, const Lref &L, cudaStream_t s
 // FP32 deviations -> stored values at the current reference and sigma.
 cudaError_t lref_encode(int lattice, int storage, const Geom &g, const Lref &L, const float *dev, void *stored,
                         cudaStream_t s);
+// The rebuild in place, without an FP32 copy: a new reference (the node's
+// own moments) into Lnew.ref and sigma into Lnew.scale, and every stored value
+// decoded at Lold and stored at Lnew (Lnew.q5 may differ from Lold.q5);
+// bmax: ceil(N / 256) floats of scratch.  Lnew's buffers differ from Lold's.
+cudaError_t lref_rebuild(int lattice, int storage, const Geom &g, const Lref &Lold, const Lref &Lnew, float *bmax,
+                         void *stored, cudaStream_t s);
+// Every stored value decoded at Lold and stored at Lnew, in place (no new reference).
+cudaError_t lref_reencode(int lattice, int storage, const Geom &g, const Lref &Lold, const Lref &Lnew, void *stored,
+                          cudaStream_t s);
 // A new reference and sigma from FP32 deviations, and the stored values at
-// them; bmax: kReduceMaxBlocks floats of scratch.
+// them; bmax: ceil(N / 256) floats of scratch.
 cudaError_t lref_rebase(int lattice, int storage, const Geom &g, const Lref &L, float *bmax, const float *dev,
                         void *stored, cudaStream_t s);
 
