@@ -263,3 +263,45 @@ def test_scalar_sweep_with_stochastic_rounding_keeps_second_order_to_512():
     assert all(o >= 1.9 for o in orders), (errs, orders)
     assert errs["lref_sr"][-1] <= 1.1 * errs["fp32"][-1], errs
 
+
+
+@pytest.mark.parametrize("lattice", [W.D2Q9, W.D2Q5], ids=["d2q9", "d2q5"])
+def test_write_paths_on_an_encoded_lattice(lattice):
+    """The encoding switched on before the state exists: the equilibrium fill
+    and a checkpoint restore (set_populations) go through the FP32 deviations
+    and are stored at a fresh reference; the state reads back to FP32
+    rounding, and the same steps follow as from a plain FP32 lattice."""
+    w = _d2q9((16, 12, 1), (0, 1, 0), 8) if lattice == W.D2Q9 else _d2q5((16, 12, 1), (0, 1, 0), 8)
+    lat = lbm.D2Q9 if lattice == W.D2Q9 else lbm.D2Q5_CDE
+    G = lbm.Lattice(lat, w.shape, w.omega, wall=w.wall, storage=lbm.FP16_DEV)
+    G.set_local_reference(8)
+    if lattice == W.D2Q9:
+        G.set_force(tables=w.tables)
+    else:
+        G.set_source(tables=w.tables)
+        u = np.asarray(w.u0, np.float64)
+        G.set_velocity(tables=[(np.array([u[0]]), np.array([1.0]), np.array([1.0])),
+                               (np.array([u[1]]), np.array([1.0]), np.array([1.0]))])
+    G.init_equilibrium(w.rho0, w.u0)
+    H = lbm.from_workload(w, storage=lbm.FP32_DEV)
+    f0, h0 = G.get_populations(), H.get_populations()
+    # the stored part d - e of a fill: the equilibrium's terms beyond second
+    # order in u (D2Q9), or for a D2Q5 lattice with walls (rest-state
+    # reference) the uniform velocity's share of the equilibrium, ~u/2 = 0.01;
+    # FP16 keeps it to 2^-11 of that
+    tol = 2.0 ** -11 * 0.01
+    _record(f"write_paths_{'d2q9' if lattice == W.D2Q9 else 'd2q5'}_fill", float(np.abs(f0 - h0).max()))
+    assert np.abs(f0 - h0).max() <= tol, np.abs(f0 - h0).max()
+    G.set_populations(h0, step=0)
+    f1 = G.get_populations()
+    assert np.abs(f1 - h0).max() <= tol, np.abs(f1 - h0).max()
+    G.step(40)
+    H.step(40)
+    if lattice == W.D2Q9:
+        (_, ug), (_, uh) = G.moments(), H.moments()
+        err = _l2(ug, uh)
+    else:
+        pg, ph = G.moments(), H.moments()
+        err = _l2(pg - ph.mean(), ph - ph.mean())
+    _record(f"write_paths_{'d2q9' if lattice == W.D2Q9 else 'd2q5'}_vs_fp32", err)
+    assert err <= 1e-3, err
