@@ -346,7 +346,10 @@ int lbm_l2_error(lbm_ctx *ctx, const double *ref, int where, int field, int half
  * array: calls whose kernels overlap on the GPU race and may return wrong
  * sums, so serialise them (e.g. one stream).  Nothing in the array needs
  * clearing between calls.  Synchronises the context's stream; out is a host
- * array of 4 doubles.  Does not touch lbm_reduce's max-change snapshot.
+ * array of 4 doubles.  Does not touch lbm_reduce's max-change snapshot.  A
+ * context stored at a local reference (lbm_set_local_reference) is read
+ * through its FP32 working copy, which the first other read or write of its
+ * state allocates: before that, LBM_ESTATE.
  * Errors: LBM_ESTATE, LBM_EINVAL, LBM_EUNSTABLE (out still written), LBM_ECUDA. */
 int lbm_reduce_sums_noalloc(lbm_ctx *ctx, double out[4]);
 

@@ -72,7 +72,11 @@ extern "C" int lbm_reduce_sums_noalloc(lbm_ctx *c, double out[4])
     double *scratch = nullptr;
     int rc = scratch_on(c, c->device, &scratch);
     if (rc != LBM_OK) return rc;
-    // a local-reference context is read through its FP32 deviations (no allocation)
+    // a local-reference context is read through its FP32 deviations, whose
+    // buffer an earlier read or write of the state must have allocated
+    if (c->lref_every && !c->lref_dev)
+        return fail(c, LBM_ESTATE, "lbm_reduce_sums_noalloc: a context stored at a local reference needs one "
+                                   "allocating read of its state (e.g. lbm_reduce) first");
     LrefView view(c, true);
     if (view.rc != LBM_OK) return view.rc;
     // Every partial slot that the final pass reads is written by its block

@@ -58,3 +58,19 @@ def test_noalloc_sums_across_two_contexts():
     for _ in range(2):
         assert _close(a.reduce_sums_noalloc(), ra, abs(ra[0]))
         assert _close(b.reduce_sums_noalloc(), rb, abs(rb[0]))
+
+
+def test_noalloc_on_a_local_reference_context():
+    """A 16-bit lattice stored at a per-node reference is read through an FP32
+    working copy; the no-alloc call refuses (LBM_ESTATE) until an allocating
+    read has made it, then agrees with lbm_reduce."""
+    w = W.poiseuille(ny=17, nx=8, Fx=1e-4)
+    G = lbm.from_workload(w, storage=lbm.FP16_DEV)
+    G.set_local_reference(8)
+    G.step(20)
+    with pytest.raises(lbm.LBMError) as e:
+        G.reduce_sums_noalloc()
+    assert e.value.code == lbm.ESTATE
+    r = G.reduce()
+    s = G.reduce_sums_noalloc()
+    assert np.allclose(s, r[:4], rtol=1e-15, atol=1e-18), (s, r)
